@@ -1,0 +1,248 @@
+"""FP64 CPU oracle for direct measurement-equation prediction, peeling and its gradient.
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by ``__graft_entry__.smoke()`` and by the
+``cpu_baseline`` / ``--impl reference`` legs of bench.py, never by the library itself.
+
+The arithmetic lives in ``wn_oracle.c`` (plain C, FP64, loops in the paper's order); this module
+builds it with gcc, loads it with ctypes and marshals numpy arrays.  It also holds the oracle's own
+packers (triangular coefficient index, parity split of the (-i)^(n1+n2) phase, bf16 hi/lo split),
+written from the same definitions the CUDA packer follows, so the two can be compared bit for bit.
+
+Parity pins (tests/test_oracle_pins.py) tie every function here to closed forms, library
+routines, brute-force DFTs or finite differences; none is left unpinned.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "wn_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+C_LIGHT = 299792458.0
+
+
+def build(force: bool = False) -> str:
+    """Compile wn_oracle.c into liboracle.so (gcc, -O2, OpenMP, strict IEEE arithmetic)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fopenmp", "-fno-fast-math",
+                               "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = ctypes.CDLL(build())
+            d, i, P = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
+            _lib.or_n_minus_1.restype = d
+            _lib.or_n_minus_1.argtypes = [d, d]
+            _lib.or_spectrum.restype = d
+            _lib.or_spectrum.argtypes = [d, d, d, d]
+            _lib.or_gauss_env.restype = d
+            _lib.or_gauss_env.argtypes = [d, d, d, d, d]
+            _lib.or_hermite.restype = None
+            _lib.or_hermite.argtypes = [i, d, P]
+            _lib.or_shapelet_frame.restype = None
+            _lib.or_shapelet_frame.argtypes = [d, d, d, P]
+            _lib.or_max_threads.restype = i
+            _lib.or_predict.restype = None
+            _lib.or_predict.argtypes = [i, P, i, P, d, i, i, i] + [P] * 16 + [P, i]
+            _lib.or_peel.restype = None
+            _lib.or_peel.argtypes = [i, P, P, P, P, i, P, i, i, i, P, P, P]
+            _lib.or_grad.restype = None
+            _lib.or_grad.argtypes = [i, P, i, P, d, i, i, i] + [P] * 16 + [P, P, P, P, P]
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def max_threads() -> int:
+    return int(lib().or_max_threads())
+
+
+def n_minus_1(l: float, m: float) -> float:
+    return lib().or_n_minus_1(l, m)
+
+
+def spectrum(s_ref, alpha, nu_ref, nu) -> float:
+    return lib().or_spectrum(s_ref, alpha, nu_ref, nu)
+
+
+def gauss_env(u, v, maj, mn, pa) -> float:
+    return lib().or_gauss_env(u, v, maj, mn, pa)
+
+
+def hermite(nmax: int, x: float) -> np.ndarray:
+    out = np.zeros(nmax + 1)
+    lib().or_hermite(nmax, float(x), _p(out))
+    return out
+
+
+def shapelet_frame(l: float, m: float, dec0: float) -> np.ndarray:
+    out = np.zeros(9)
+    lib().or_shapelet_frame(float(l), float(m), float(dec0), _p(out))
+    return out.reshape(3, 3)
+
+
+class _SkyArgs:
+    """Keeps contiguous copies alive for the duration of a call."""
+
+    def __init__(self, sky):
+        self.keep = [_f64(sky.l), _f64(sky.m), _f64(sky.flux), _f64(sky.alpha), _f64(sky.nu_ref),
+                     _f64(sky.g_maj), _f64(sky.g_min), _f64(sky.g_pa), _f64(sky.s_beta1), _f64(sky.s_beta2),
+                     _f64(sky.s_pa), _i32(sky.s_nmax), _i32(sky.s_off), _i32(sky.s_n1), _i32(sky.s_n2),
+                     _f64(sky.s_coeff)]
+        # positional order of the C signature: l m s_ref alpha nu_ref g_maj g_min g_pa
+        # s_b1 s_b2 s_pa s_nmax s_off s_n1 s_n2 s_c
+        self.ptrs = [_p(a) for a in self.keep]
+
+
+def predict(uvw_rows: np.ndarray, freq: np.ndarray, dec0: float, sky, n_threads: int = 0) -> np.ndarray:
+    """Visibilities [R, F] complex128 for the rows of uvw_rows ([R, 3] metres)."""
+    uvw_rows = _f64(uvw_rows).reshape(-1, 3)
+    freq = _f64(freq)
+    R, F = uvw_rows.shape[0], freq.shape[0]
+    out = np.zeros((R, F, 2))
+    sa = _SkyArgs(sky)
+    lib().or_predict(R, _p(uvw_rows), F, _p(freq), float(dec0), int(sky.n_point), int(sky.n_gauss),
+                     int(sky.n_shape), *sa.ptrs, _p(out), int(n_threads))
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def peel(row_t, row_b, ant1, ant2, n_ant, gains, data, vis) -> np.ndarray:
+    """R = D - g[ant1] conj(g[ant2]) V for rows (row_t, row_b); gains [Tg, Fg, A] complex."""
+    row_t, row_b, ant1, ant2 = _i32(row_t), _i32(row_b), _i32(ant1), _i32(ant2)
+    g = np.ascontiguousarray(gains, dtype=np.complex128)
+    Tg, Fg = g.shape[0], g.shape[1]
+    d = np.ascontiguousarray(data, dtype=np.complex128)
+    v = np.ascontiguousarray(vis, dtype=np.complex128)
+    R, F = d.shape
+    out = np.zeros((R, F), dtype=np.complex128)
+    lib().or_peel(R, _p(row_t), _p(row_b), _p(ant1), _p(ant2), int(n_ant), _p(g.view(np.float64)), Tg, Fg, F,
+                  _p(d.view(np.float64)), _p(v.view(np.float64)), _p(out.view(np.float64)))
+    return out
+
+
+def gain_product(row_t, row_b, ant1, ant2, gains, n_chan) -> np.ndarray:
+    """G[r, f] = g[ant1] conj(g[ant2]) by direct indexing (used to form W = conj(G) R)."""
+    g = np.asarray(gains)
+    Tg, Fg = g.shape[0], g.shape[1]
+    t = np.zeros_like(row_t) if Tg == 1 else np.asarray(row_t)
+    f = np.arange(n_chan) if Fg > 1 else np.zeros(n_chan, dtype=int)
+    g1 = g[t[:, None], f[None, :], np.asarray(ant1)[row_b][:, None]]
+    g2 = g[t[:, None], f[None, :], np.asarray(ant2)[row_b][:, None]]
+    return g1 * np.conj(g2)
+
+
+def grad(uvw_rows, freq, dec0, sky, W):
+    """dL/dp for L = sum |D - G V|^2 given W = conj(G)(D - G V) ([R, F] complex)."""
+    uvw_rows = _f64(uvw_rows).reshape(-1, 3)
+    freq = _f64(freq)
+    R, F = uvw_rows.shape[0], freq.shape[0]
+    Wc = np.ascontiguousarray(W, dtype=np.complex128).reshape(R, F)
+    g_comp = np.zeros((sky.n_comp, 4))
+    g_gauss = np.zeros((sky.n_gauss, 3))
+    g_shape = np.zeros((sky.n_shape, 3))
+    g_coeff = np.zeros(int(sky.s_off[-1]) if sky.n_shape else 0)
+    sa = _SkyArgs(sky)
+    lib().or_grad(R, _p(uvw_rows), F, _p(freq), float(dec0), int(sky.n_point), int(sky.n_gauss),
+                  int(sky.n_shape), *sa.ptrs, _p(Wc.view(np.float64)), _p(g_comp), _p(g_gauss),
+                  _p(g_shape), _p(g_coeff))
+    return dict(flux=g_comp[:, 0].copy(), alpha=g_comp[:, 1].copy(), l=g_comp[:, 2].copy(),
+                m=g_comp[:, 3].copy(), g_maj=g_gauss[:, 0].copy(), g_min=g_gauss[:, 1].copy(),
+                g_pa=g_gauss[:, 2].copy(), s_beta1=g_shape[:, 0].copy(), s_beta2=g_shape[:, 1].copy(),
+                s_pa=g_shape[:, 2].copy(), s_coeff=g_coeff)
+
+
+def loss(uvw_rows, freq, dec0, sky, row_t, row_b, ant1, ant2, n_ant, gains, data) -> float:
+    """L = sum |D - G V|^2 over the given rows, V from the oracle."""
+    V = predict(uvw_rows, freq, dec0, sky)
+    R = peel(row_t, row_b, ant1, ant2, n_ant, gains, data, V)
+    return float(np.sum(np.abs(R) ** 2))
+
+
+# ------------------------------------------------------------------------------------------------
+# The oracle's own packers.  The CUDA library packs on the device; these restate the same layout
+# from its definition so the two can be compared bit for bit.
+# ------------------------------------------------------------------------------------------------
+
+def tri_index(n1, n2):
+    """k(n1, n2) = s (s + 1) / 2 + n2 with s = n1 + n2: all pairs with n1 + n2 <= n_max, by s."""
+    s = np.asarray(n1) + np.asarray(n2)
+    return s * (s + 1) // 2 + np.asarray(n2)
+
+
+def tri_unindex(k):
+    k = np.asarray(k, dtype=np.int64)
+    s = ((np.sqrt(8 * k + 1) - 1) // 2).astype(np.int64)
+    s = np.where(s * (s + 1) // 2 > k, s - 1, s)
+    s = np.where((s + 1) * (s + 2) // 2 <= k, s + 1, s)
+    n2 = k - s * (s + 1) // 2
+    return (s - n2).astype(np.int64), n2
+
+
+def p_tot(nmax: int) -> int:
+    """Number of basis functions with n1 + n2 <= n_max (Sec. 2)."""
+    return (nmax + 2) * (nmax + 1) // 2
+
+
+def parity_split(nmax, n1, n2, c):
+    """C (-i)^(n1+n2) as two real matrices [n1][n2]: (C_re, C_im)."""
+    re = np.zeros((nmax + 1, nmax + 1))
+    im = np.zeros((nmax + 1, nmax + 1))
+    for a, b, v in zip(np.asarray(n1), np.asarray(n2), np.asarray(c)):
+        k = (a + b) % 4
+        re[a, b] += v * (1.0, 0.0, -1.0, 0.0)[k]
+        im[a, b] += v * (0.0, -1.0, 0.0, 1.0)[k]
+    return re, im
+
+
+def f32_to_bf16_bits(x32: np.ndarray) -> np.ndarray:
+    """Round-to-nearest-even float32 -> bfloat16 bit patterns (finite inputs)."""
+    u = np.asarray(x32, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = (u + 0x7FFF + ((u >> 16) & 1)) >> 16
+    return r.astype(np.uint16)
+
+
+def bf16_bits_to_f32(b: np.ndarray) -> np.ndarray:
+    return (np.asarray(b, dtype=np.uint32) << 16).view(np.float32)
+
+
+def bf16_hi_lo(x) -> tuple[np.ndarray, np.ndarray]:
+    """hi = RN_bf16(float32(x)), lo = RN_bf16(float32(x) - hi): the split-precision operand pair."""
+    x32 = np.asarray(x, dtype=np.float64).astype(np.float32)
+    hi = f32_to_bf16_bits(x32)
+    lo = f32_to_bf16_bits((x32 - bf16_bits_to_f32(hi)).astype(np.float32))
+    return hi, lo
+
+
+def pack_coeff_bf16(nmax: int, n1, n2, c, k_pad: int, n_pad: int):
+    """Dense B operand of the shapelet contraction, as bf16 hi/lo bit patterns [n_pad][k_pad]:
+    row 2*n2 holds Re(C (-i)^(n1+n2))[n1, n2] over n1 (the K index), row 2*n2+1 the imaginary part."""
+    re, im = parity_split(nmax, n1, n2, c)
+    dense = np.zeros((n_pad, k_pad))
+    for b in range(nmax + 1):
+        dense[2 * b, :nmax + 1] = re[:, b]
+        dense[2 * b + 1, :nmax + 1] = im[:, b]
+    return bf16_hi_lo(dense)
