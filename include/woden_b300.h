@@ -1,0 +1,189 @@
+/*
+ * woden_b300.h -- C ABI of the B300 (sm_103a) visibility predictor and peeler.
+ *
+ * The library evaluates the direct measurement equation of Line et al. 2020 (arXiv 2005.09316),
+ * Sec. 3 (eq:measure_eq_discrete, eq:env_visi_def):
+ *
+ *     V(t,b,f) = sum_j S_j(nu_f) xi_j(u,v) exp(-2 pi i (u l_j + v m_j + w (n_j - 1)))
+ *
+ * with (u,v,w) = uvw(t,b) nu_f / c, S_j(nu) = S_ref,j (nu / nu_ref,j)^alpha_j (Sec. 4.1, Sec. 6),
+ * and the envelope xi_j = 1 for points, the elliptical-Gaussian transform (eq:gauss-env,
+ * eq:scale-gauss-x/y) for Gaussians, and the coefficient-weighted analytic shapelet transform
+ * (eq:shape-env, eq:scale-shape-x/y, eq:basis_FT) for shapelets.  The peel forms
+ * R = D - g_ant1 conj(g_ant2) V (Sec. 5.1).  The instrument beam is 1 (Sec. 3.1).
+ *
+ * Conventions
+ *  - Every array pointer in wn_obs, wn_sky and the call arguments is a DEVICE pointer (memory on
+ *    the context's GPU) owned by the caller, unless a comment says HOST.  The library never frees
+ *    caller memory and keeps no pointer to it after a call returns, except that wn_sky_upload
+ *    copies the sky into library-owned device memory (the resident model).
+ *  - Complex values are interleaved (re, im) float32 pairs ("complex64"), 8-byte aligned.
+ *  - Visibility arrays are [n_time][n_base][n_chan] complex64, channel fastest.
+ *  - Baselines are the pairs (ant1[b], ant2[b]) with ant1 < ant2; uvw(t,b) is in metres in the
+ *    phase-centre frame and points from ant1 to ant2 (X[ant2] - X[ant1]).
+ *  - Calls are asynchronous on the given stream (a cudaStream_t; NULL = the legacy default stream)
+ *    unless documented as synchronous.  A call that returns an error launches nothing.
+ *  - Return value: WN_OK (0) or a wn_status code; wn_last_error() gives a message for the last
+ *    failing call on the calling thread.
+ *  - Device-side faults of the inputs that host checks cannot see (an antenna index outside
+ *    [0, n_ant)) are not dereferenced: the kernels skip the access, write NaN for that output and
+ *    raise a flag that wn_device_errors() reports.
+ *  - Angles are radians; FWHM widths are full widths at half maximum; frequencies are Hz.
+ */
+#ifndef WODEN_B300_H
+#define WODEN_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define WN_API __attribute__((visibility("default")))
+#else
+#define WN_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wn_ctx wn_ctx;
+
+typedef enum {
+    WN_OK = 0,
+    WN_EINVAL = 1,    /* a size, pointer, index or parameter is out of range */
+    WN_ENOMEM = 2,    /* device or host allocation failed */
+    WN_ECUDA = 3,     /* a CUDA runtime call failed */
+    WN_ETIMEOUT = 4,  /* a bounded device-side wait gave up */
+    WN_EBUSY = 5,     /* admission refused (serving) */
+    WN_ENOTFOUND = 6  /* unknown model id or ticket */
+} wn_status;
+
+/* Precision of the point/Gaussian phasor sum. */
+typedef enum {
+    WN_PREC_MIXED = 0,   /* FP64 phase argument, FP32 phasors and sums (default) */
+    WN_PREC_FP64 = 1     /* every step in FP64: the plain reference form */
+} wn_precision;
+
+/* Precision of the tensor-core shapelet contraction (xi = A C B^T, Sec. 3.2 eq:shape-env). */
+typedef enum {
+    WN_SHAPE_BF16X3 = 0, /* bf16 hi+lo split of both operands, three products, FP32 accumulate (default) */
+    WN_SHAPE_BF16X1 = 1  /* plain bf16 operands, one product, FP32 accumulate */
+} wn_shape_mode;
+
+/* Device-side error flags (bit mask) reported by wn_device_errors. */
+#define WN_DEVERR_ANTENNA 0x1u  /* an ant1/ant2 entry outside [0, n_ant) met by a peel */
+#define WN_DEVERR_TIMEOUT 0x2u  /* a bounded mbarrier / queue wait gave up */
+#define WN_DEVERR_SKY     0x4u  /* a sky entry rejected during upload */
+
+/* An observation: baselines, time steps and channels (Sec. 3.2, last paragraph: uvw once per time
+ * step, scaled per channel). */
+typedef struct {
+    int32_t n_ant;          /* antennas, >= 2 */
+    int32_t n_base;         /* baselines, >= 1 */
+    int32_t n_time;         /* time steps, >= 1 */
+    int32_t n_chan;         /* channels, >= 1 */
+    const double* uvw;      /* DEVICE [n_time][n_base][3] metres */
+    const double* freq_hz;  /* DEVICE [n_chan] Hz, > 0 */
+    const int32_t* ant1;    /* DEVICE [n_base] */
+    const int32_t* ant2;    /* DEVICE [n_base] */
+    double dec0;            /* phase-centre declination (rad); fixes the shapelet re-phasing frame */
+    double chan_spacing_hz; /* HOST scalar: 0 for an arbitrary channel list, else the uniform spacing,
+                               freq_hz[f] == freq_hz[0] + f * chan_spacing_hz (enables the phasor
+                               recurrence across channels) */
+    double freq0_hz;        /* HOST scalar: freq_hz[0] (needed on the host to set up the kernels) */
+} wn_obs;
+
+/* A sky model: points first, then Gaussians, then shapelets (Sec. 3.1-3.2).  DEVICE pointers. */
+typedef struct {
+    int32_t n_point, n_gauss, n_shape;
+    const double* l;          /* [n_comp] direction cosine, l^2 + m^2 < 1 */
+    const double* m;          /* [n_comp] */
+    const double* flux;       /* [n_comp] S_ref (Jy); for shapelets the flux multiplying xi (Sec. 3.2) */
+    const double* alpha;      /* [n_comp] spectral index */
+    const double* nu_ref;     /* [n_comp] reference frequency (Hz), > 0 */
+    const double* g_maj;      /* [n_gauss] FWHM major axis (rad) */
+    const double* g_min;      /* [n_gauss] FWHM minor axis (rad) */
+    const double* g_pa;       /* [n_gauss] position angle, East of North (rad) */
+    const double* s_beta1;    /* [n_shape] beta_1 (rad), pairs with the major (PA) axis */
+    const double* s_beta2;    /* [n_shape] beta_2 (rad) */
+    const double* s_pa;       /* [n_shape] position angle (rad) */
+    const int32_t* s_nmax;    /* [n_shape] n_max in [0, 127] */
+    const int32_t* s_off;     /* [n_shape + 1] offsets into the coefficient triples, s_off[0] == 0 */
+    const int32_t* s_n1;      /* [nnz] basis order along x (beta_1) */
+    const int32_t* s_n2;      /* [nnz] basis order along y (beta_2); n1 + n2 <= n_max */
+    const double* s_coeff;    /* [nnz] C[n1,n2] already divided by the integrated flux (Sec. 3.2) */
+} wn_sky;
+
+/* Gradient output: DEVICE arrays laid out like wn_sky; entries for absent parts may be NULL. */
+typedef struct {
+    double* flux;      /* [n_comp] dL/dS_ref */
+    double* alpha;     /* [n_comp] dL/dalpha */
+    double* l;         /* [n_comp] dL/dl (shapelets: re-phasing frame held fixed) */
+    double* m;         /* [n_comp] dL/dm */
+    double* g_maj;     /* [n_gauss] */
+    double* g_min;     /* [n_gauss] */
+    double* g_pa;      /* [n_gauss] */
+    double* s_beta1;   /* [n_shape] */
+    double* s_beta2;   /* [n_shape] */
+    double* s_pa;      /* [n_shape] */
+    double* s_coeff;   /* [nnz] */
+} wn_sky_grad;
+
+/* ---- context ------------------------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device` (allocates a small device error word). Synchronous. */
+WN_API int wn_create(wn_ctx** out, int device);
+/* Destroy a context and every resident model it owns.  Synchronizes the device. */
+WN_API void wn_destroy(wn_ctx* ctx);
+/* Message for the last non-zero return on the calling thread ("" if none).  Never NULL. */
+WN_API const char* wn_last_error(void);
+/* Library version string. */
+WN_API const char* wn_version(void);
+/* Select the point/Gaussian precision (wn_precision) and the shapelet mode (wn_shape_mode). */
+WN_API int wn_set_precision(wn_ctx* ctx, int precision, int shape_mode);
+/* Read and clear the device error flags (WN_DEVERR_*).  Synchronizes the device. */
+WN_API int wn_device_errors(wn_ctx* ctx, uint32_t* flags_out);
+
+/* ---- resident sky models ------------------------------------------------------------------ */
+
+/* Validate and pack a sky into library-owned device memory; *model_id receives its handle.
+ * Packing runs in kernels on `stream` (n - 1 computed stably as -(l^2+m^2)/(1+sqrt(1-l^2-m^2)),
+ * log-flux, Gaussian quadratic forms, shapelet frames and the dense bf16 coefficient operands).
+ * Synchronous: it reads the shapelet sizes back and checks the sky on the device.
+ * Errors: WN_EINVAL for negative counts, NULL arrays that are needed, l^2+m^2 >= 1, nu_ref <= 0,
+ * n_max outside [0,127], a triple outside the triangle n1+n2 <= n_max, non-monotone s_off. */
+WN_API int wn_sky_upload(wn_ctx* ctx, const wn_sky* sky, int* model_id, void* stream);
+/* Release a resident model.  Synchronous. */
+WN_API int wn_sky_free(wn_ctx* ctx, int model_id);
+/* Bytes of device memory a resident model holds (admission accounting). */
+WN_API int wn_sky_bytes(wn_ctx* ctx, int model_id, size_t* bytes_out);
+
+/* ---- hot path ------------------------------------------------------------------------------ */
+
+/* Predict visibilities (eq:env_visi_def) of a resident model into vis_c64 [T][B][F].
+ * accumulate = 0 overwrites vis_c64, 1 adds to it. */
+WN_API int wn_predict(wn_ctx* ctx, const wn_obs* obs, int model_id, void* vis_c64, int accumulate, void* stream);
+
+/* Fused peel (Sec. 5.1): resid = data - g[ant1] conj(g[ant2]) V for the resident model.
+ * gains_c64 is [gains_t][gains_f][n_ant] complex64 with gains_t in {1, n_time} and gains_f in
+ * {1, n_chan} (broadcast when 1).  resid may alias data (each element is read before it is written). */
+WN_API int wn_peel(wn_ctx* ctx, const wn_obs* obs, int model_id, const void* gains_c64, int gains_t, int gains_f,
+            const void* data_c64, void* resid_c64, void* stream);
+
+/* Standalone streaming peel of an already predicted model: resid = data - g1 conj(g2) model.
+ * HBM-bound (24 bytes per visibility).  resid may alias data or model. */
+WN_API int wn_peel_model(wn_ctx* ctx, const wn_obs* obs, const void* gains_c64, int gains_t, int gains_f,
+                  const void* data_c64, const void* model_c64, void* resid_c64, void* stream);
+
+/* Gradient of L = sum |data - g1 conj(g2) V|^2 with respect to every sky parameter (analytic adjoint,
+ * phasors recomputed, not stored).  grad_out arrays are overwritten; loss_out (DEVICE, 1 double) may be
+ * NULL.  resid_c64 (DEVICE [T][B][F] complex64) receives the residual data - G V and serves as the
+ * adjoint's input; it must not alias data.  The library allocates its reduction workspace. */
+WN_API int wn_predict_grad(wn_ctx* ctx, const wn_obs* obs, int model_id, const void* gains_c64, int gains_t, int gains_f,
+                    const void* data_c64, void* resid_c64, const wn_sky_grad* grad_out, double* loss_out,
+                    void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WODEN_B300_H */

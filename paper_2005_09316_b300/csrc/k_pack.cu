@@ -1,0 +1,141 @@
+// Sky packing kernels: turn the caller's component tables into the resident device records the
+// prediction kernels read.  Runs once per model (wn_sky_upload).
+#include "wn_internal.cuh"
+
+namespace wn {
+
+// Point / Gaussian records (one thread per component).  n - 1 is formed without cancellation as
+// -(l^2 + m^2) / (1 + sqrt(1 - l^2 - m^2)) (Sec. 3.1, below eq:measure_eq).  The Gaussian envelope
+// (eq:gauss-env with eq:scale-gauss-x/y) is expanded into a quadratic form in (u, v):
+//   maj^2 (sin pa u + cos pa v)^2 + min^2 (cos pa u - sin pa v)^2 = ga u^2 + gb u v + gc v^2.
+__global__ void k_pack_pg(wn_sky s, PGRec* out, unsigned* err) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  int n = s.n_point + s.n_gauss;
+  if (j >= n) return;
+  double l = s.l[j], m = s.m[j], r2 = l * l + m * m;
+  double flux = s.flux[j], nuref = s.nu_ref[j];
+  PGRec r;
+  bool bad = !(r2 < 1.0) || !(nuref > 0.0) || !isfinite(flux) || !isfinite(s.alpha[j]);
+  r.l = l;
+  r.m = m;
+  r.nm1 = bad ? 0.0 : -r2 / (1.0 + sqrt(1.0 - r2));
+  r.lref = bad ? 0.0 : log2(nuref);
+  r.lS = flux == 0.0 ? 0.0f : (float)log2(fabs(flux));
+  r.alpha = (float)s.alpha[j];
+  r.sgn = bad ? 0.0f : (flux > 0.0 ? 1.0f : (flux < 0.0 ? -1.0f : 0.0f));
+  r.ga = r.gb = r.gc = 0.0f;
+  if (j >= s.n_point) {
+    int g = j - s.n_point;
+    double mj = s.g_maj[g], mn = s.g_min[g], pa = s.g_pa[g];
+    if (!(mj >= 0.0) || !(mn >= 0.0) || !isfinite(pa)) bad = true;
+    double sp = sin(pa), cp = cos(pa), a2 = mj * mj, b2 = mn * mn;
+    r.ga = (float)(a2 * sp * sp + b2 * cp * cp);
+    r.gb = (float)(2.0 * sp * cp * (a2 - b2));
+    r.gc = (float)(a2 * cp * cp + b2 * sp * sp);
+  }
+  r.pad0 = r.pad1 = 0.0f;
+  out[j] = r;
+  if (bad) atomicOr(err, WN_DEVERR_SKY);
+}
+
+// Shapelet headers (one thread per shapelet): n - 1, log-flux and the beta/PA-scaled axes of
+// eq:scale-shape-x/y, x = beta1 K (sin pa u' + cos pa v'), y = beta2 K (cos pa u' - sin pa v'), K = pi/sqrt(2 ln 2).
+__global__ void k_pack_shape(wn_sky s, const int* b_off, const int* k_pad, const int* n_pad,
+                             ShapeRec* out, unsigned* err) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= s.n_shape) return;
+  int j = s.n_point + s.n_gauss + q;
+  double l = s.l[j], m = s.m[j], r2 = l * l + m * m;
+  double flux = s.flux[j], nuref = s.nu_ref[j];
+  bool bad = !(r2 < 1.0) || !(nuref > 0.0) || !isfinite(flux);
+  ShapeRec r;
+  r.l = l;
+  r.m = m;
+  double n = bad ? 1.0 : sqrt(1.0 - r2);
+  r.nm1 = bad ? 0.0 : -r2 / (1.0 + n);
+  r.lref = bad ? 0.0 : log2(nuref);
+  r.lS = flux == 0.0 ? 0.0f : (float)log2(fabs(flux));
+  r.alpha = (float)s.alpha[j];
+  r.sgn = bad ? 0.0f : (flux > 0.0 ? 1.0f : (flux < 0.0 ? -1.0f : 0.0f));
+  double b1 = s.s_beta1[q], b2 = s.s_beta2[q], pa = s.s_pa[q];
+  r.kx_u = (float)(b1 * kShapeK * sin(pa));
+  r.kx_v = (float)(b1 * kShapeK * cos(pa));
+  r.ky_u = (float)(b2 * kShapeK * cos(pa));
+  r.ky_v = (float)(-b2 * kShapeK * sin(pa));
+  r.nmax = s.s_nmax[q];
+  r.k_pad = k_pad[q];
+  r.n_pad = n_pad[q];
+  r.b_off = b_off[q];
+  out[q] = r;
+  if (bad) atomicOr(err, WN_DEVERR_SKY);
+}
+
+// Dense B operand of the shapelet contraction: column n = 2*n2 + {0: real, 1: imaginary} of
+// C[n1,n2] (-i)^(n1+n2) (eq:shape-env with the phase of eq:basis_FT), row k = n1, stored as bf16
+// hi = RN(float(C)), lo = RN(float(C) - hi) in the tcgen05 canonical K-major layout without swizzle:
+// 8x8 core matrices, element (n, k) at ((k/8) * (n_pad/8) + n/8) * 64 + (n%8) * 8 + k%8.
+__global__ void k_pack_coeff(int nnz_total, const int* n1, const int* n2, const double* c, const int* s_off,
+                             const int* s_nmax, int n_shape, const int* b_off, const int* k_pad, const int* n_pad,
+                             __nv_bfloat16* bop, unsigned* err) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nnz_total) return;
+  int q = 0;  // shapelet owning triple t (s_off is validated monotone on the host)
+  while (q + 1 < n_shape && s_off[q + 1] <= t) ++q;
+  int a = n1[t], b = n2[t], nmax = s_nmax[q];
+  if (a < 0 || b < 0 || a + b > nmax) {
+    atomicOr(err, WN_DEVERR_SKY);
+    return;
+  }
+  int kk = (a + b) & 3;
+  float v = (float)c[t];
+  float re = kk == 0 ? v : (kk == 2 ? -v : 0.0f);
+  float im = kk == 1 ? -v : (kk == 3 ? v : 0.0f);
+  int np = n_pad[q], kp = k_pad[q];
+  __nv_bfloat16* hi = bop + b_off[q];
+  __nv_bfloat16* lo = hi + (size_t)np * kp;
+  auto at = [&](int n, int k) { return ((k >> 3) * (np >> 3) + (n >> 3)) * 64 + (n & 7) * 8 + (k & 7); };
+  // each (n1, n2) appears once per shapelet: duplicates are summed on the host check, so plain stores
+  __nv_bfloat16 rh = __float2bfloat16_rn(re), ih = __float2bfloat16_rn(im);
+  hi[at(2 * b, a)] = rh;
+  lo[at(2 * b, a)] = __float2bfloat16_rn(re - __bfloat162float(rh));
+  hi[at(2 * b + 1, a)] = ih;
+  lo[at(2 * b + 1, a)] = __float2bfloat16_rn(im - __bfloat162float(ih));
+}
+
+static int cuda_check(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return WN_OK;
+  return set_error(WN_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+int launch_pack(wn_ctx* ctx, const wn_sky* s, Model* M, cudaStream_t st) {
+  int npg = s->n_point + s->n_gauss;
+  if (npg > 0) {
+    k_pack_pg<<<(npg + 127) / 128, 128, 0, st>>>(*s, M->pg, ctx->d_err);
+    if (int r = cuda_check(cudaGetLastError(), "pack points")) return r;
+  }
+  if (s->n_shape > 0) {
+    std::vector<int> boff(s->n_shape), kp(s->n_shape), np(s->n_shape);
+    for (int q = 0; q < s->n_shape; ++q) {
+      boff[q] = M->sh_host[q].b_off;
+      kp[q] = M->sh_host[q].k_pad;
+      np[q] = M->sh_host[q].n_pad;
+    }
+    int* dtmp = nullptr;
+    if (int r = cuda_check(cudaMallocAsync(&dtmp, sizeof(int) * 3 * s->n_shape, st), "pack alloc")) return r;
+    cudaMemcpyAsync(dtmp, boff.data(), sizeof(int) * s->n_shape, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(dtmp + s->n_shape, kp.data(), sizeof(int) * s->n_shape, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(dtmp + 2 * s->n_shape, np.data(), sizeof(int) * s->n_shape, cudaMemcpyHostToDevice, st);
+    k_pack_shape<<<(s->n_shape + 63) / 64, 64, 0, st>>>(*s, dtmp, dtmp + s->n_shape, dtmp + 2 * s->n_shape,
+                                                        M->sh, ctx->d_err);
+    cudaMemsetAsync(M->bop, 0, M->bop_elems * sizeof(__nv_bfloat16), st);
+    if (M->nnz > 0)
+      k_pack_coeff<<<(M->nnz + 255) / 256, 256, 0, st>>>(M->nnz, s->s_n1, s->s_n2, s->s_coeff, s->s_off, s->s_nmax,
+                                                         s->n_shape, dtmp, dtmp + s->n_shape, dtmp + 2 * s->n_shape,
+                                                         M->bop, ctx->d_err);
+    cudaFreeAsync(dtmp, st);
+    if (int r = cuda_check(cudaGetLastError(), "pack shapelets")) return r;
+  }
+  return WN_OK;
+}
+
+}  // namespace wn

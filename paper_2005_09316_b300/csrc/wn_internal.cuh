@@ -1,0 +1,272 @@
+// Internal definitions shared by the CUDA translation units of libwoden_b300.
+// Device helpers: bounded mbarrier waits, TMA bulk copies, double-float phase reduction,
+// fast and accurate phasors.  Nothing here is exported.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "woden_b300.h"
+
+namespace wn {
+
+constexpr double kC = 299792458.0;
+constexpr double kPi = 3.14159265358979323846;
+// Gaussian envelope exponent pi^2 / (4 ln 2) (eq:gauss-env), and the shapelet scale pi / sqrt(2 ln 2)
+// (eq:scale-shape-x/y).
+constexpr double kGaussE = 3.5597074346203355;   // pi^2 / (4 ln 2)
+constexpr double kShapeK = 2.6682231827177734;   // pi / sqrt(2 ln 2)
+constexpr double kLog2e = 1.4426950408889634;
+constexpr int kNmaxLimit = 127;
+
+// Packed point / Gaussian component (64 bytes).  Points first, then Gaussians.
+struct __align__(16) PGRec {
+  double l, m, nm1;   // direction cosines and n - 1 = -(l^2+m^2)/(1+sqrt(1-l^2-m^2))
+  double lref;        // log2(nu_ref)
+  float lS;           // log2 |S_ref|
+  float alpha;        // spectral index
+  float sgn;          // sign of S_ref (+1, -1, or 0)
+  float ga, gb, gc;   // Gaussian: log2 xi = -(ga u^2 + gb u v + gc v^2) (nu/c)^2 * kGaussE*log2(e)
+  float pad0, pad1;
+};
+static_assert(sizeof(PGRec) == 64, "PGRec layout");
+
+// Packed shapelet header (64 bytes).  The re-phasing frame depends on the phase-centre declination
+// of the observation and is formed at launch (shapelet_frame).
+struct __align__(16) ShapeRec {
+  double l, m, nm1, lref;
+  float lS, alpha, sgn;
+  float kx_u, kx_v;     // x = (kx_u u' + kx_v v') nu/c : beta1 * K * (sin pa, cos pa)
+  float ky_u, ky_v;     // y = (ky_u u' + ky_v v') nu/c : beta2 * K * (cos pa, -sin pa)
+  int nmax, k_pad, n_pad;
+  int b_off;            // element offset of this shapelet's dense operand in the model's B buffer
+};
+static_assert(sizeof(ShapeRec) == 80, "ShapeRec layout");
+
+// A resident sky model (device memory owned by the context).
+struct Model {
+  int n_point = 0, n_gauss = 0, n_shape = 0, nnz = 0;
+  PGRec* pg = nullptr;             // [n_point + n_gauss]
+  ShapeRec* sh = nullptr;          // [n_shape]
+  std::vector<ShapeRec> sh_host;   // host copy of the headers (sizes, offsets)
+  __nv_bfloat16* bop = nullptr;    // dense shapelet B operands (hi then lo per shapelet), UMMA layout
+  size_t bop_elems = 0;
+  // raw FP64 copies for the FP64 form and the adjoint
+  double* raw = nullptr;           // l, m, flux, alpha, nu_ref [n_comp] each; g_maj,g_min,g_pa; s_b1,s_b2,s_pa
+  int* s_meta = nullptr;           // s_nmax [n_shape], s_off [n_shape+1], s_n1 [nnz], s_n2 [nnz]
+  double* s_coeff = nullptr;       // [nnz]
+  std::vector<int> s_off_host, s_nmax_host;
+  size_t bytes = 0;
+  int n_comp() const { return n_point + n_gauss + n_shape; }
+  const double* r_l() const { return raw; }
+  const double* r_m() const { return raw + n_comp(); }
+  const double* r_flux() const { return raw + 2 * n_comp(); }
+  const double* r_alpha() const { return raw + 3 * n_comp(); }
+  const double* r_nuref() const { return raw + 4 * n_comp(); }
+  const double* r_gmaj() const { return raw + 5 * n_comp(); }
+  const double* r_gmin() const { return raw + 5 * n_comp() + n_gauss; }
+  const double* r_gpa() const { return raw + 5 * n_comp() + 2 * n_gauss; }
+  const double* r_sb1() const { return raw + 5 * n_comp() + 3 * n_gauss; }
+  const double* r_sb2() const { return raw + 5 * n_comp() + 3 * n_gauss + n_shape; }
+  const double* r_spa() const { return raw + 5 * n_comp() + 3 * n_gauss + 2 * n_shape; }
+  const int* m_nmax() const { return s_meta; }
+  const int* m_off() const { return s_meta + n_shape; }
+  const int* m_n1() const { return s_meta + 2 * n_shape + 1; }
+  const int* m_n2() const { return s_meta + 2 * n_shape + 1 + nnz; }
+};
+
+}  // namespace wn
+
+struct wn_ctx {
+  int device = 0;
+  int num_sms = 148;
+  int precision = WN_PREC_MIXED;
+  int shape_mode = WN_SHAPE_BF16X3;
+  unsigned* d_err = nullptr;
+  std::map<int, wn::Model*> models;
+  int next_id = 1;
+  // growable workspace (adjoint partial sums)
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+};
+
+namespace wn {
+
+// Output modes of the prediction kernels: store V, add V, write the peel residual D - G V, or subtract
+// G V from what the output already holds (a second pass of a peel).
+enum OutMode { OUT_STORE = 0, OUT_ACCUM = 1, OUT_PEEL = 2, OUT_SUBG = 3 };
+
+// Gains / peel description passed to kernels.
+struct PeelArgs {
+  const float2* data = nullptr;   // [rows][F]
+  const float2* gains = nullptr;  // [gt][gf][n_ant]
+  const int* ant1 = nullptr;
+  const int* ant2 = nullptr;
+  int gt = 1, gf = 1, n_ant = 0;
+};
+
+int set_error(int code, const std::string& msg);
+
+// ---------------------------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------------------------
+
+// Row r = t * n_base + b of the peel: G = g[tg][fg][ant1] * conj(g[tg][fg][ant2]).  Returns false
+// (and G = NaN) when an antenna index is out of range; the access is then skipped.
+__device__ __forceinline__ bool gain_product(const PeelArgs& p, int row, int n_base, int f, float2& G) {
+  int b = row % n_base;
+  int t = row / n_base;
+  int a1 = __ldg(p.ant1 + b), a2 = __ldg(p.ant2 + b);
+  if (a1 < 0 || a1 >= p.n_ant || a2 < 0 || a2 >= p.n_ant) {
+    G = make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
+    return false;
+  }
+  int tg = p.gt == 1 ? 0 : t;
+  int fg = p.gf == 1 ? 0 : f;
+  const float2* gb = p.gains + ((size_t)tg * p.gf + fg) * p.n_ant;
+  float2 g1 = __ldg(gb + a1), g2 = __ldg(gb + a2);
+  // g1 * conj(g2)
+  G.x = g1.x * g2.x + g1.y * g2.y;
+  G.y = g1.y * g2.x - g1.x * g2.y;
+  return true;
+}
+
+// Phase reduction in double-float arithmetic: frac(t * a) in [-1/2, 1/2] turns, where t = th + tl and
+// a = ah + al are unevaluated float sums.  The product error is recovered exactly with an FMA; the
+// rounding to the nearest integer uses the 1.5*2^23 shifter (valid for |t*a| < 2^22).
+__device__ __forceinline__ float reduce_turns(float th, float tl, float ah, float al) {
+  float p = __fmul_rn(th, ah);
+  float e = __fmaf_rn(th, ah, -p);
+  e = __fmaf_rn(th, al, e);
+  e = __fmaf_rn(tl, ah, e);
+  const float kShift = 12582912.0f;
+  float n = __fsub_rn(__fadd_rn(p, kShift), kShift);
+  return __fadd_rn(__fsub_rn(p, n), e);
+}
+
+// Split a double into an unevaluated float pair hi + lo.
+__device__ __forceinline__ void split_double(double x, float& hi, float& lo) {
+  hi = __double2float_rn(x);
+  lo = __double2float_rn(x - (double)hi);
+}
+
+// Fast phasor exp(-2 pi i r) for r in turns, |r| <= 1/2 (MUFU sin/cos; absolute error ~2^-21).
+__device__ __forceinline__ float2 phasor_fast(float r) {
+  float s, c;
+  float a = r * 6.283185307179586f;
+  asm("sin.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(a));
+  asm("cos.approx.ftz.f32 %0, %1;" : "=f"(c) : "f"(a));
+  return make_float2(c, -s);
+}
+
+// Accurate phasor exp(-2 pi i r) via the library's sincospif.
+__device__ __forceinline__ float2 phasor_accurate(float r) {
+  float s, c;
+  sincospif(2.0f * r, &s, &c);
+  return make_float2(c, -s);
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Frame taking (u, v, w) about the phase centre (H0, dec0) to the frame of a component centred at
+// (l, m) (Sec. 3.2 after eq:scale-shape-y: the shapelet (u, v) are computed with the phase centre at
+// the shapelet's own RA_j, dec_j).  F = R(H_j, dec_j) R(H0, dec0)^T with R the XYZ -> uvw rotation,
+// sin dec_j = m cos dec0 + n sin dec0 and H_j - H0 = -atan2(l, n cos dec0 - m sin dec0); F does not
+// depend on H0, so H0 = 0.
+__device__ inline void shapelet_frame(double l, double m, double dec0, double F[9]) {
+  double n = sqrt(1.0 - l * l - m * m);
+  double decj = asin(m * cos(dec0) + n * sin(dec0));
+  double hj = -atan2(l, n * cos(dec0) - m * sin(dec0));
+  double shj = sin(hj), chj = cos(hj), sdj = sin(decj), cdj = cos(decj);
+  double sd0 = sin(dec0), cd0 = cos(dec0);
+  double rj[9] = {shj, chj, 0.0, -sdj * chj, sdj * shj, cdj, cdj * chj, -cdj * shj, sdj};
+  double r0[9] = {0.0, 1.0, 0.0, -sd0, 0.0, cd0, cd0, 0.0, sd0};
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      F[3 * a + b] = rj[3 * a] * r0[3 * b] + rj[3 * a + 1] * r0[3 * b + 1] + rj[3 * a + 2] * r0[3 * b + 2];
+}
+
+// ---- mbarrier / TMA bulk copy (sm_90+ PTX) ---------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: gives up after ~2^26 polls (each try_wait itself blocks for a hardware-defined
+// interval), raises WN_DEVERR_TIMEOUT and returns false so the kernel can wind down.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned* err) {
+  for (uint32_t it = 0; it < (1u << 26); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  if (err) atomicOr(err, WN_DEVERR_TIMEOUT);
+  return false;
+}
+
+// One-dimensional TMA bulk copy global -> shared, completing on an mbarrier (bytes multiple of 16,
+// both addresses 16-byte aligned).
+__device__ __forceinline__ void tma_bulk_g2s(void* smem_dst, const void* gmem_src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(smem_dst)),
+      "l"(gmem_src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+}  // namespace wn
+
+// Launchers (defined in the kernel translation units).
+namespace wn {
+struct ObsDev {
+  int n_ant, n_base, n_time, n_chan, n_rows;
+  const double* uvw;
+  const double* freq;
+  const int* ant1;
+  const int* ant2;
+  double dec0, dnu, nu0;
+  bool uniform;
+};
+int launch_pack(wn_ctx* ctx, const wn_sky* sky, Model* M, cudaStream_t st);
+int launch_phasor_mixed(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, int mode, const PeelArgs& pa,
+                        cudaStream_t st);
+int launch_phasor_fp64(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, int mode, const PeelArgs& pa,
+                       bool include_shapelets, cudaStream_t st);
+int launch_peel_model(wn_ctx* ctx, const ObsDev& o, const PeelArgs& pa, const float2* model, float2* resid,
+                      cudaStream_t st);
+int launch_shapelets(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, int mode, const PeelArgs& pa,
+                     cudaStream_t st);
+}  // namespace wn
