@@ -43,12 +43,16 @@ struct K1Args {
   unsigned* err;
 };
 
+constexpr int K1_FLUSH = 4;     // tiles (128 components) per register partial sum
+
 struct K1Smem {
   // offsets in bytes into dynamic shared memory
-  int stage, bars, uvw, rec, q, cs, total;
+  int stage, bars, uvw, rec, q, cs, acc, total;
 };
 
-__host__ __device__ inline K1Smem k1_smem_layout(int log2L) {
+// acc holds the second-level sums: every K1_FLUSH tiles the register partial sums (at most 128
+// components) are added into it, which keeps the FP32 rounding of a 25,000-term sum near 1e-7.
+__host__ __device__ inline K1Smem k1_smem_layout(int log2L, int K) {
   int groups = 32 >> log2L;
   int rpw = 2 * groups;  // rows per warp
   K1Smem s;
@@ -58,7 +62,8 @@ __host__ __device__ inline K1Smem k1_smem_layout(int log2L) {
   s.rec = s.uvw + K1_WARPS * rpw * 3 * 8;
   s.q = s.rec + K1_WARPS * K1_CT * rpw * 16;
   s.cs = s.q + K1_WARPS * K1_CT * rpw * 4;
-  s.total = s.cs + K1_WARPS * K1_CT * 16;
+  s.acc = s.cs + K1_WARPS * K1_CT * 16;
+  s.total = s.acc + K1_THREADS * 2 * K * 8;
   return s;
 }
 
@@ -76,7 +81,7 @@ __device__ __forceinline__ bool bounded_wait(uint64_t* bar, uint32_t parity, uns
 template <int K, bool UNIFORM>
 __global__ void __launch_bounds__(K1_THREADS, 2) k1_phasor(const K1Args a) {
   extern __shared__ __align__(128) unsigned char smem[];
-  const K1Smem lay = k1_smem_layout(a.log2L);
+  const K1Smem lay = k1_smem_layout(a.log2L, K);
   PGRec* stage = reinterpret_cast<PGRec*>(smem + lay.stage);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + lay.bars);
   uint64_t* empty = full + K1_NSTAGE;
@@ -93,6 +98,9 @@ __global__ void __launch_bounds__(K1_THREADS, 2) k1_phasor(const K1Args a) {
   float4* rec = reinterpret_cast<float4*>(smem + lay.rec) + warp * K1_CT * rpw;
   float* qs = reinterpret_cast<float*>(smem + lay.q) + warp * K1_CT * rpw;
   float4* cs = reinterpret_cast<float4*>(smem + lay.cs) + warp * K1_CT;
+  float2* acc = reinterpret_cast<float2*>(smem + lay.acc) + threadIdx.x;  // [2K][K1_THREADS]
+#pragma unroll
+  for (int i = 0; i < 2 * K; ++i) acc[i * K1_THREADS] = make_float2(0.f, 0.f);
 
   const int n_pt_tiles = (a.n_point + K1_CT - 1) / K1_CT;
   const int n_tiles = n_pt_tiles + (a.n_gauss + K1_CT - 1) / K1_CT;
@@ -195,19 +203,8 @@ __global__ void __launch_bounds__(K1_THREADS, 2) k1_phasor(const K1Args a) {
     for (int j = 0; j < cnt; ++j) {
       const float4 c = cs[j];
       const float4 R0 = rec[j * rpw + 2 * g], R1 = rec[j * rpw + 2 * g + 1];
-      float A0[K], A1[K];
-      if (gauss) {
-        const float q0 = qs[j * rpw + 2 * g], q1 = qs[j * rpw + 2 * g + 1];
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-          const float e = fmaf(c.y, lam[k], c.x);
-          A0[k] = ex2_approx(fmaf(-q0, wg[k], e));
-          A1[k] = ex2_approx(fmaf(-q1, wg[k], e));
-        }
-      } else {
-#pragma unroll
-        for (int k = 0; k < K; ++k) A0[k] = A1[k] = ex2_approx(fmaf(c.y, lam[k], c.x));
-      }
+      const float q0 = gauss ? qs[j * rpw + 2 * g] : 0.f;
+      const float q1 = gauss ? qs[j * rpw + 2 * g + 1] : 0.f;
       if (UNIFORM) {
         float2 P0 = phasor_fast(reduce_turns(R0.x, R0.y, a0h, a0l));
         float2 P1 = phasor_fast(reduce_turns(R1.x, R1.y, a0h, a0l));
@@ -215,10 +212,14 @@ __global__ void __launch_bounds__(K1_THREADS, 2) k1_phasor(const K1Args a) {
         P1.x *= c.z; P1.y *= c.z;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-          V0[k].x = fmaf(A0[k], P0.x, V0[k].x);
-          V0[k].y = fmaf(A0[k], P0.y, V0[k].y);
-          V1[k].x = fmaf(A1[k], P1.x, V1[k].x);
-          V1[k].y = fmaf(A1[k], P1.y, V1[k].y);
+          // amplitude: spectrum and (for Gaussians) envelope in one exp2
+          const float e = fmaf(c.y, lam[k], c.x);
+          const float A0 = ex2_approx(gauss ? fmaf(-q0, wg[k], e) : e);
+          const float A1 = gauss ? ex2_approx(fmaf(-q1, wg[k], e)) : A0;
+          V0[k].x = fmaf(A0, P0.x, V0[k].x);
+          V0[k].y = fmaf(A0, P0.y, V0[k].y);
+          V1[k].x = fmaf(A1, P1.x, V1[k].x);
+          V1[k].y = fmaf(A1, P1.y, V1[k].y);
           if (k + 1 < K) {
             const float x0 = P0.x * R0.z - P0.y * R0.w, y0 = P0.x * R0.w + P0.y * R0.z;
             const float x1 = P1.x * R1.z - P1.y * R1.w, y1 = P1.x * R1.w + P1.y * R1.z;
@@ -231,7 +232,9 @@ __global__ void __launch_bounds__(K1_THREADS, 2) k1_phasor(const K1Args a) {
         for (int k = 0; k < K; ++k) {
           const float2 P0 = phasor_fast(reduce_turns(R0.x, R0.y, ah[k], al[k]));
           const float2 P1 = phasor_fast(reduce_turns(R1.x, R1.y, ah[k], al[k]));
-          const float s0 = A0[k] * c.z, s1 = A1[k] * c.z;
+          const float e = fmaf(c.y, lam[k], c.x);
+          const float s0 = c.z * ex2_approx(gauss ? fmaf(-q0, wg[k], e) : e);
+          const float s1 = gauss ? c.z * ex2_approx(fmaf(-q1, wg[k], e)) : s0;
           V0[k].x = fmaf(s0, P0.x, V0[k].x);
           V0[k].y = fmaf(s0, P0.y, V0[k].y);
           V1[k].x = fmaf(s1, P1.x, V1[k].x);
@@ -240,6 +243,15 @@ __global__ void __launch_bounds__(K1_THREADS, 2) k1_phasor(const K1Args a) {
       }
     }
     __syncwarp();
+    if ((t + 1) % K1_FLUSH == 0) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        float2 x = acc[k * K1_THREADS], y = acc[(K + k) * K1_THREADS];
+        acc[k * K1_THREADS] = make_float2(x.x + V0[k].x, x.y + V0[k].y);
+        acc[(K + k) * K1_THREADS] = make_float2(y.x + V1[k].x, y.y + V1[k].y);
+        V0[k] = V1[k] = make_float2(0.f, 0.f);
+      }
+    }
   }
 
   // --- epilogue: each visibility written once
@@ -252,7 +264,9 @@ __global__ void __launch_bounds__(K1_THREADS, 2) k1_phasor(const K1Args a) {
       const int f = f0 + k;
       if (f >= a.n_chan) continue;
       const size_t idx = (size_t)row * a.n_chan + f;
-      float2 v = rr == 0 ? V0[k] : V1[k];
+      const float2 p = rr == 0 ? V0[k] : V1[k];
+      const float2 q = acc[(rr * K + k) * K1_THREADS];
+      float2 v = make_float2(q.x + p.x, q.y + p.y);
       if (!ok) v = make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
       if (a.mode == OUT_STORE) {
         a.out[idx] = v;
@@ -273,18 +287,21 @@ struct K1Choice {
   int log2L, K;
 };
 
+// Pick lanes-per-row L and channels-per-lane K: fewest padded channel slots, then the widest channel
+// block (each FP64 phase record per (component, row) then serves the most channels), then larger K.
 static K1Choice k1_choose(int F) {
   K1Choice best{5, 12};
-  long best_slots = -1;
-  const int Ks[4] = {16, 12, 8, 4};
+  long best_slots = -1, best_cb = 0;
+  const int Ks[4] = {12, 8, 16, 4};
   for (int li = 2; li <= 5; ++li) {
     for (int K : Ks) {
       long cb = (long)K << li;
       long slots = ((F + cb - 1) / cb) * cb;
-      bool better = best_slots < 0 || slots < best_slots ||
-                    (slots == best_slots && (K > best.K || (K == best.K && cb > ((long)best.K << best.log2L))));
+      bool better = best_slots < 0 || slots < best_slots || (slots == best_slots && cb > best_cb) ||
+                    (slots == best_slots && cb == best_cb && K > best.K && K <= 12);
       if (better) {
         best_slots = slots;
+        best_cb = cb;
         best = {li, K};
       }
     }
@@ -325,7 +342,7 @@ int launch_phasor_mixed(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* ou
   a.err = ctx->d_err;
   const int rows_per_cta = K1_WARPS * 2 * (32 >> ch.log2L);
   dim3 grid((o.n_rows + rows_per_cta - 1) / rows_per_cta, (o.n_chan + a.chan_block - 1) / a.chan_block);
-  const int smem = k1_smem_layout(ch.log2L).total;
+  const int smem = k1_smem_layout(ch.log2L, ch.K).total;
   cudaError_t e;
   switch (ch.K * 2 + (o.uniform ? 1 : 0)) {
     case 4 * 2 + 1: e = k1_launch<4, true>(a, grid, smem, st); break;
