@@ -9,17 +9,17 @@
 // per-row dot product xi = sum_n2 T[., n2] phi_n2(y).  The contribution S(nu) xi exp(-2 pi i tau nu/c)
 // is then stored, accumulated, or subtracted as G times it for the peel.
 //
-// Kernel organisation (persistent, one CTA per SM):
-//  * warps 0-3 and 4-7 are two producer/epilogue warpgroups; thread i of a group owns row i of a
-//    128-visibility tile: it computes phi_n(x) by the normalised Hermite recurrence (FP32, rescaled to
-//    stay in range) and writes them as bf16 hi/lo into the canonical K-major shared-memory layout
-//    (8x8 core matrices, no swizzle), then, after the MMA, reads its accumulator row from TMEM and
-//    forms the epilogue;
-//  * warp 8 allocates TMEM, loads the packed coefficient operand with one TMA bulk copy, and one of
+// Kernel organisation (persistent, one CTA per SM; tiles of 128 visibilities, two in flight):
+//  * producer warpgroups P0, P1 (warps 0-3, 4-7) take the even / odd tiles: thread i computes
+//    phi_n(x) of row i by the normalised Hermite recurrence (FP32, rescaled to stay in range) and
+//    writes them as bf16 hi/lo into that parity's A buffer in the canonical K-major shared-memory
+//    layout (8x8 core matrices, no swizzle);
+//  * warp 16 allocates TMEM, loads the packed coefficient operand with one TMA bulk copy, and one of
 //    its threads issues tcgen05.mma (kind::f16, bf16 x bf16 -> f32; three products hi*hi + hi*lo + lo*hi
-//    in the split mode) into the group's TMEM accumulator and commits to an mbarrier;
-//  * the two groups alternate tiles so that one group's Hermite production and epilogue overlap the
-//    other group's MMAs.
+//    in the split mode) into the parity's TMEM accumulator and commits to an mbarrier;
+//  * epilogue warpgroups E0, E1 (warps 8-11, 12-15) read their accumulator rows from TMEM (warp w
+//    reaches lanes 32 (w % 4) ..), stream phi_n(y) against them, release TMEM, and write the output.
+//  Per parity: P(k+2) waits for MMA(k) to finish reading A, MMA(k+2) for E(k) to release TMEM.
 // Every wait is bounded; on a timeout the kernel raises WN_DEVERR_TIMEOUT, drains its own commits and
 // frees TMEM before returning.
 #include "wn_internal.cuh"
@@ -27,9 +27,9 @@
 namespace wn {
 
 constexpr int K2_M = 128;
-constexpr int K2_GROUPS = 2;
-constexpr int K2_THREADS = 32 * (4 * K2_GROUPS + 1);
-constexpr int K2_SLACK = 32 * 1024;  // spare shared memory behind the operands
+constexpr int K2_GROUPS = 2;                     // tile parities in flight
+constexpr int K2_THREADS = 32 * (8 * K2_GROUPS + 1);
+constexpr int K2_MMA_WARP = 8 * K2_GROUPS;
 
 // sqrt(2/(n+1)) and sqrt(n/(n+1)) of the normalised Hermite recurrence
 //   phi_{n+1} = sqrt(2/(n+1)) x phi_n - sqrt(n/(n+1)) phi_{n-1}.
@@ -79,28 +79,35 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// 32 lanes x 32 bits, 16 consecutive columns per thread.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
+// tcgen05.ld of 32 lanes x 32 bits, 16 consecutive columns per thread.  The loaded registers are
+// undefined until tcgen05.wait::ld; tmem_wait16 names them as operands so no use of them can be
+// scheduled before the wait.
+__device__ __forceinline__ void tmem_issue16x(uint32_t taddr, uint32_t* r) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
         "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_wait16(uint32_t* r) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+               :
+               : "memory");
 }
 
 __device__ __forceinline__ bool k2_wait(uint64_t* bar, uint32_t parity, unsigned* err) {
-  long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > (1ll << 32)) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  for (uint32_t i = 1;; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 63) == 0 && clock64() - t0 > (1ll << 32)) {  // ~2 s: something is wrong
       atomicOr(err, WN_DEVERR_TIMEOUT);
       return false;
     }
   }
-  return true;
 }
 
 // Offset in bytes of element (row, k) in a canonical K-major no-swizzle tile with `rows` rows.
@@ -109,7 +116,7 @@ __host__ __device__ __forceinline__ uint32_t kmaj_off(int row, int k, int rows) 
 }
 
 struct K2Layout {
-  int b_bytes, a_bytes, a0, bars, total;
+  int b_bytes, a_bytes, a0, coef, bars, total;
 };
 
 __host__ __device__ inline K2Layout k2_layout(int kp, int n_pad, int passes, int groups) {
@@ -118,77 +125,142 @@ __host__ __device__ inline K2Layout k2_layout(int kp, int n_pad, int passes, int
   L.b_bytes = parts * kp * n_pad * 2;
   L.a_bytes = parts * kp * K2_M * 2;  // one group's A (hi [+ lo])
   L.a0 = (L.b_bytes + 1023) & ~1023;
-  L.bars = L.a0 + groups * L.a_bytes;
-  L.total = L.bars + 128 + K2_SLACK;
+  L.coef = L.a0 + groups * L.a_bytes;  // recurrence coefficients a_n, b_n: 2 x 128 floats
+  L.bars = L.coef + 2 * (kNmaxLimit + 1) * 4;
+  L.total = L.bars + 128;  // barriers (1 + 3 per parity) and the TMEM address slot
   return L;
 }
 
-// Hermite functions phi_0..phi_{KP-1}(x) (zero beyond nmax), FP32 with a running power-of-two scale
-// so the recurrence neither underflows (phi_0 = e^{-x^2/2} is far below FP32 range for |x| > 13)
-// nor overflows; written as bf16 hi (and lo) into row `row` of the K-major tile(s).
+// Hermite functions phi_0..phi_{KP-1}(x) by the normalised recurrence, written as bf16 hi (and lo)
+// into row `row` of the K-major tile(s).  Values past nmax meet zero rows of the coefficient operand;
+// they only need to be finite.  For |x| <= 12.5 every value stays in the normal FP32 range
+// (phi_0 >= e^-78, |phi_n| <~ 1) and no scaling is needed.  Beyond that phi_0 = e^{-x^2/2} underflows
+// FP32: the recurrence runs on values scaled by 2^E (E lowered by 64 whenever they pass 2^64) and is
+// scaled back on output.  Beyond xcut every phi_n, n <= nmax, is below 1e-20 and the row is zero.
+// Coefficients come from shared memory, four at a time.
+__device__ __forceinline__ void store_bf16_split(float (&v)[8], unsigned char* a_hi, unsigned char* a_lo, uint32_t off) {
+  __nv_bfloat162 h[4], l[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    h[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+    const float2 hf = __bfloat1622float2(h[i]);
+    l[i] = __floats2bfloat162_rn(v[2 * i] - hf.x, v[2 * i + 1] - hf.y);
+  }
+  *reinterpret_cast<uint4*>(a_hi + off) = *reinterpret_cast<uint4*>(h);
+  if (a_lo) *reinterpret_cast<uint4*>(a_lo + off) = *reinterpret_cast<uint4*>(l);
+}
+
 template <int KP>
 __device__ __forceinline__ void produce_row(float x, int nmax, bool valid, unsigned char* a_hi, unsigned char* a_lo,
-                                            int row) {
+                                            int row, const float4* ca, const float4* cb) {
   const float ax = fabsf(x);
-  const float xcut = sqrtf(2.0f * nmax + 1.0f) + 10.0f;  // beyond it every phi_n, n <= nmax, is < 1e-20
+  const float xcut = sqrtf(2.0f * nmax + 1.0f) + 10.0f;
   const bool zero = !valid || !(ax <= xcut);
   const float hx = 0.5f * x * x * 1.4426950408889634f;  // log2 of 1/phi_0
-  int E = zero ? 0 : max(0, (int)ceilf(hx) - 100);       // stored value = phi * 2^E
   float p_prev = 0.f;
-  float p = zero ? 0.f : exp2f((float)E - hx);
-  float scale = ldexpf(1.0f, -E);
+  if (zero || ax <= 12.5f) {
+    float p = zero ? 0.f : exp2f(-hx);
+#pragma unroll 1
+    for (int k0 = 0; k0 < KP; k0 += 8) {
+      const float4 A0 = ca[k0 >> 2], A1 = ca[(k0 >> 2) + 1], B0 = cb[k0 >> 2], B1 = cb[(k0 >> 2) + 1];
+      const float av[8] = {A0.x, A0.y, A0.z, A0.w, A1.x, A1.y, A1.z, A1.w};
+      const float bv[8] = {B0.x, B0.y, B0.z, B0.w, B1.x, B1.y, B1.z, B1.w};
+      float v[8];
 #pragma unroll
-  for (int k0 = 0; k0 < KP; k0 += 8) {
-    float v[8];
+      for (int i = 0; i < 8; ++i) {
+        v[i] = p;
+        const float pn = fmaf(av[i] * x, p, -bv[i] * p_prev);
+        p_prev = p;
+        p = pn;
+      }
+      store_bf16_split(v, a_hi, a_lo, kmaj_off(row, k0, K2_M));
+    }
+  } else {
+    int E = max(0, (int)ceilf(hx) - 100);  // stored value = phi * 2^E
+    float p = exp2f((float)E - hx);
+    float scale = __int_as_float(max(0, 127 - E) << 23);  // 2^-E (0 below 2^-126)
+#pragma unroll 1
+    for (int k0 = 0; k0 < KP; k0 += 8) {
+      const float4 A0 = ca[k0 >> 2], A1 = ca[(k0 >> 2) + 1], B0 = cb[k0 >> 2], B1 = cb[(k0 >> 2) + 1];
+      const float av[8] = {A0.x, A0.y, A0.z, A0.w, A1.x, A1.y, A1.z, A1.w};
+      const float bv[8] = {B0.x, B0.y, B0.z, B0.w, B1.x, B1.y, B1.z, B1.w};
+      float v[8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int n = k0 + i;
-      v[i] = (n <= nmax) ? p * scale : 0.f;
-      const float pn = fmaf(c_herm_a[n] * x, p, -c_herm_b[n] * p_prev);
-      p_prev = p;
-      p = pn;
-      if ((i & 3) == 3 && fabsf(p) > 1.8446744e19f) {  // 2^64: rescale by 2^-64
+      for (int i = 0; i < 8; ++i) {
+        v[i] = p * scale;
+        const float pn = fmaf(av[i] * x, p, -bv[i] * p_prev);
+        p_prev = p;
+        p = pn;
+      }
+      if (fabsf(p) > 1.8446744e19f) {  // 2^64: rescale (8 steps grow by at most 2^43)
         p *= 5.421011e-20f;
         p_prev *= 5.421011e-20f;
         E -= 64;
-        scale = ldexpf(1.0f, -E);
+        scale = __int_as_float(max(0, 127 - E) << 23);
       }
+      store_bf16_split(v, a_hi, a_lo, kmaj_off(row, k0, K2_M));
     }
-    __nv_bfloat162 h[4], l[4];
+  }
+}
+
+// Epilogue dot product of one accumulator chunk (16 n2 values: columns 2 n2, 2 n2 + 1 = Re, Im) with
+// phi_n2(y), advancing the y recurrence.  SCALED: values carry 2^E as in produce_row.
+template <bool SCALED>
+__device__ __forceinline__ void epi_chunk(const uint32_t* t, const float4* ca, const float4* cb, int n0, float y,
+                                          float& q, float& q_prev, float& xr, float& xi, int& E, float& scale) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      h[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-      const float2 hf = __bfloat1622float2(h[i]);
-      l[i] = __floats2bfloat162_rn(v[2 * i] - hf.x, v[2 * i + 1] - hf.y);
+  for (int g4 = 0; g4 < 2; ++g4) {
+    const float4 A = ca[(n0 >> 2) + g4], B = cb[(n0 >> 2) + g4];
+    const float av[4] = {A.x, A.y, A.z, A.w};
+    const float bv[4] = {B.x, B.y, B.z, B.w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = 4 * g4 + u;
+      const float ph = SCALED ? q * scale : q;
+      xr = fmaf(__uint_as_float(t[2 * i]), ph, xr);
+      xi = fmaf(__uint_as_float(t[2 * i + 1]), ph, xi);
+      const float qn = fmaf(av[u] * y, q, -bv[u] * q_prev);
+      q_prev = q;
+      q = qn;
     }
-    const uint32_t off = kmaj_off(row, k0, K2_M);
-    *reinterpret_cast<uint4*>(a_hi + off) = *reinterpret_cast<uint4*>(h);
-    if (a_lo) *reinterpret_cast<uint4*>(a_lo + off) = *reinterpret_cast<uint4*>(l);
+    if (SCALED && g4 == 1 && fabsf(q) > 1.8446744e19f) {
+      q *= 5.421011e-20f;
+      q_prev *= 5.421011e-20f;
+      E -= 64;
+      scale = __int_as_float(max(0, 127 - E) << 23);
+    }
   }
 }
 
 template <int KP>
 __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  const K2Layout lay = k2_layout(KP, a.n_pad, a.passes, a.groups);
+  const int ng = a.groups;  // tile parities in flight (2, or 1 when two A buffers do not fit)
+  const K2Layout lay = k2_layout(KP, a.n_pad, a.passes, ng);
   uint64_t* bfull = reinterpret_cast<uint64_t*>(smem + lay.bars);
-  uint64_t* afull = bfull + 1;             // [groups]
-  uint64_t* mdone = bfull + 1 + K2_GROUPS;  // [groups]
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bfull + 1 + 2 * K2_GROUPS);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int mma_warp = 4 * K2_GROUPS;
-  const uint32_t ncols = a.n_pad * a.groups <= 32 ? 32 : (a.n_pad * a.groups <= 64 ? 64 :
-                         (a.n_pad * a.groups <= 128 ? 128 : (a.n_pad * a.groups <= 256 ? 256 : 512)));
+  uint64_t* afull = bfull + 1;                // [parity] producer -> MMA: A written
+  uint64_t* mdone = afull + K2_GROUPS;        // [parity] MMA -> producer/epilogue: MMA complete
+  uint64_t* tfree = mdone + K2_GROUPS;        // [parity] epilogue -> MMA: TMEM read
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(tfree + K2_GROUPS);
+  const int warp = threadIdx.x >> 5;
+  const int acc_cols = a.n_pad * ng;
+  const uint32_t ncols = acc_cols <= 32 ? 32 : (acc_cols <= 64 ? 64 : (acc_cols <= 128 ? 128 : (acc_cols <= 256 ? 256 : 512)));
 
   if (threadIdx.x == 0) {
     mbar_init(bfull, 1);
     for (int g = 0; g < K2_GROUPS; ++g) {
       mbar_init(&afull[g], 128);
       mbar_init(&mdone[g], 1);
+      mbar_init(&tfree[g], 128);
     }
     fence_mbar_init();
   }
-  if (warp == mma_warp) {
+  if (threadIdx.x <= kNmaxLimit) {
+    float* cf = reinterpret_cast<float*>(smem + lay.coef);
+    cf[threadIdx.x] = c_herm_a[threadIdx.x];
+    cf[kNmaxLimit + 1 + threadIdx.x] = c_herm_b[threadIdx.x];
+  }
+  if (warp == K2_MMA_WARP) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
                  "r"(ncols)
                  : "memory");
@@ -198,30 +270,29 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
+  const float4* ca = reinterpret_cast<const float4*>(smem + lay.coef);
+  const float4* cb = ca + (kNmaxLimit + 1) / 4;
+  // tiles of this CTA: it = 0, 1, 2, ... -> tile blockIdx.x + it * gridDim.x; parity s = it % ng, j = it / ng
+  const int n_it = a.n_tiles > (int)blockIdx.x ? (a.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
-  if (warp == mma_warp) {
+  if (warp == K2_MMA_WARP) {
     // ---------------- TMA of the coefficient operand, then the MMA issue loop ----------------
-    if (lane == 0) {
+    if ((threadIdx.x & 31) == 0) {
       mbar_arrive_expect_tx(bfull, (uint32_t)lay.b_bytes);
       tma_bulk_g2s(smem, a.bop, (uint32_t)lay.b_bytes, bfull);
       const uint32_t idesc = umma_idesc_bf16(a.n_pad);
       const uint32_t b_hi = smem_u32(smem), b_lo = b_hi + (uint32_t)(KP * a.n_pad * 2);
       const uint32_t lbo_b = (uint32_t)(a.n_pad >> 3) << 7, lbo_a = (uint32_t)(K2_M >> 3) << 7;
       bool ok = k2_wait(bfull, 0, a.err);
-      int issued[K2_GROUPS] = {0, 0};
-      for (int it = 0; ok; ++it) {
-        const int g = it % a.groups;
-        const int tile = blockIdx.x + it * gridDim.x;
-        if (tile >= a.n_tiles) break;
-        const int kg = issued[g];
-        if (!k2_wait(&afull[g], kg & 1, a.err)) {
-          ok = false;
-          break;
-        }
+      int done = 0;
+      for (int it = 0; ok && it < n_it; ++it) {
+        const int sp = it % ng, j = it / ng;
+        if (!k2_wait(&afull[sp], j & 1, a.err)) break;
+        if (j > 0 && !k2_wait(&tfree[sp], (j - 1) & 1, a.err)) break;
         tc_fence_after();
-        const uint32_t a_hi = smem_u32(smem + lay.a0 + g * lay.a_bytes);
+        const uint32_t a_hi = smem_u32(smem + lay.a0 + sp * lay.a_bytes);
         const uint32_t a_lo = a_hi + (uint32_t)(KP * K2_M * 2);
-        const uint32_t d = tmem + (uint32_t)(g * a.n_pad);
+        const uint32_t d = tmem + (uint32_t)(sp * a.n_pad);
 #pragma unroll 1
         for (int p = 0; p < a.passes; ++p) {
           const uint32_t aa = (p == 2) ? a_lo : a_hi;  // hi*hi, hi*lo, lo*hi
@@ -233,93 +304,133 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
             umma_bf16(d, da, db, idesc, (p > 0 || kk > 0) ? 1u : 0u);
           }
         }
-        umma_commit(&mdone[g]);
-        issued[g] = kg + 1;
+        umma_commit(&mdone[sp]);
+        done = it + 1;
       }
-      // drain: wait for the last commit of each group so no MMA is in flight at teardown
-      for (int g = 0; g < a.groups; ++g)
-        if (issued[g] > 0) k2_wait(&mdone[g], (issued[g] - 1) & 1, a.err);
+      // drain: the last commit of each parity has landed before teardown
+      for (int sp = 0; sp < ng; ++sp) {
+        const int cnt = done > sp ? (done - 1 - sp) / ng + 1 : 0;  // commits issued on this parity
+        if (cnt > 0) k2_wait(&mdone[sp], (cnt - 1) & 1, a.err);
+      }
     }
     __syncwarp();
-  } else if (warp < 4 * a.groups) {
-    // ---------------- producer / epilogue warpgroups ----------------
-    const int g = warp >> 2;
-    const int m = threadIdx.x & 127;  // tile row == TMEM lane
-    unsigned char* a_hi = smem + lay.a0 + g * lay.a_bytes;
+  } else if (warp < 4 * K2_GROUPS) {
+    // ---------------- producers: phi_n(x) into the parity's A buffer ----------------
+    const int sp = warp >> 2;
+    if (sp >= ng) goto done;
+    const int m = threadIdx.x & 127;
+    unsigned char* a_hi = smem + lay.a0 + sp * lay.a_bytes;
     unsigned char* a_lo = a.passes > 1 ? a_hi + KP * K2_M * 2 : nullptr;
-    const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(g * a.n_pad);
-    int kg = 0;
-    for (int it = g;; it += a.groups, ++kg) {
-      const int tile = blockIdx.x + it * gridDim.x;
-      if (tile >= a.n_tiles) break;
-      const long long vis = (long long)tile * K2_M + m;
-      const bool valid = vis < a.n_vis;
-      const int row = valid ? (int)(vis / a.n_chan) : 0;
-      const int f = valid ? (int)(vis - (long long)row * a.n_chan) : 0;
-      const float4 ri = valid ? __ldg(a.rowinfo + row) : make_float4(0.f, 0.f, 0.f, 0.f);
-      const float4 ci = valid ? __ldg(a.chaninfo + f) : make_float4(0.f, 0.f, 0.f, 1.f);
-      const float x = ri.x * ci.w, y = ri.y * ci.w;
-      produce_row<KP>(x, a.nmax, valid, a_hi, a_lo, m);
+    // the next tile's (xs, nu) are loaded one tile ahead and multiplied only when used
+    auto load_x = [&](int it, bool& valid, float& xs, float& nu) {
+      const long long vis = (long long)(blockIdx.x + it * gridDim.x) * K2_M + m;
+      valid = it < n_it && vis < a.n_vis;
+      xs = 0.f;
+      nu = 0.f;
+      if (valid) {
+        const int row = (int)(vis / a.n_chan);
+        const int f = (int)(vis - (long long)row * a.n_chan);
+        xs = __ldg(&a.rowinfo[row].x);
+        nu = __ldg(&a.chaninfo[f].w);
+      }
+    };
+    bool valid;
+    float xs, nu;
+    load_x(sp, valid, xs, nu);
+    for (int it = sp, j = 0; it < n_it; it += ng, ++j) {
+      const float x = xs * nu;
+      const bool v0 = valid;
+      load_x(it + ng, valid, xs, nu);
+      if (j > 0 && !k2_wait(&mdone[sp], (j - 1) & 1, a.err)) break;  // MMA(j-1) has read A
+      produce_row<KP>(x, a.nmax, v0, a_hi, a_lo, m, ca, cb);
       fence_async_smem();
-      mbar_arrive(&afull[g]);
-      // phase and amplitude of this visibility while the MMA runs
+      mbar_arrive(&afull[sp]);
+    }
+  } else {
+    // ---------------- epilogues: xi = sum_n2 T[., n2] phi_n2(y), then S xi P into the output ----------------
+    const int sp = (warp - 4 * K2_GROUPS) >> 2;
+    if (sp >= ng) goto done;
+    const int m = threadIdx.x & 127;
+    const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(sp * a.n_pad);
+    const float ycut = sqrtf(2.0f * a.nmax + 1.0f) + 10.0f;
+    struct EpiIn {
+      float4 ri, ci;
+      float2 base;
+      long long vis;
+      int row, f;
+      bool valid;
+    };
+    auto load_epi = [&](int it) {
+      EpiIn e;
+      e.vis = (long long)(blockIdx.x + it * gridDim.x) * K2_M + m;
+      e.valid = it < n_it && e.vis < a.n_vis;
+      e.row = e.valid ? (int)(e.vis / a.n_chan) : 0;
+      e.f = e.valid ? (int)(e.vis - (long long)e.row * a.n_chan) : 0;
+      e.ri = e.valid ? __ldg(a.rowinfo + e.row) : make_float4(0.f, 0.f, 0.f, 0.f);
+      e.ci = e.valid ? __ldg(a.chaninfo + e.f) : make_float4(0.f, 0.f, 0.f, 1.f);
+      e.base = make_float2(0.f, 0.f);
+      if (e.valid && a.mode != OUT_STORE) e.base = a.mode == OUT_PEEL ? a.peel.data[e.vis] : a.out[e.vis];
+      return e;
+    };
+    EpiIn nxt = load_epi(sp);
+    for (int it = sp, j = 0; it < n_it; it += ng, ++j) {
+      const EpiIn cur = nxt;
+      if (!k2_wait(&mdone[sp], j & 1, a.err)) break;
+      nxt = load_epi(it + ng);  // next tile's inputs in flight while this one is formed
+      tc_fence_after();
+      const bool valid = cur.valid;
+      const int row = cur.row, f = cur.f;
+      const size_t idx = (size_t)(valid ? cur.vis : 0);
+      const float2 base = cur.base;
+      const float4 ri = cur.ri, ci = cur.ci;
+      const float y = ri.y * ci.w;
       const float2 P = phasor_fast(reduce_turns(ri.z, ri.w, ci.x, ci.y));
       const float amp = valid ? a.sgn * ex2_approx(fmaf(a.alpha, ci.z, a.c_amp)) : 0.f;
-      // y-direction Hermite functions streamed against the accumulator row
-      const float ay = fabsf(y);
-      const float ycut = sqrtf(2.0f * a.nmax + 1.0f) + 10.0f;
-      const bool yzero = !valid || !(ay <= ycut);
+      const bool yzero = !valid || !(fabsf(y) <= ycut);
+      const bool yfast = yzero || fabsf(y) <= 12.5f;
       const float hy = 0.5f * y * y * 1.4426950408889634f;
-      int E = yzero ? 0 : max(0, (int)ceilf(hy) - 100);
+      int E = yfast ? 0 : max(0, (int)ceilf(hy) - 100);
       float q_prev = 0.f, q = yzero ? 0.f : exp2f((float)E - hy);
-      float scale = ldexpf(1.0f, -E);
-      if (!k2_wait(&mdone[g], kg & 1, a.err)) break;
-      tc_fence_after();
+      float scale = __int_as_float(max(0, 127 - E) << 23);
       float xr = 0.f, xi = 0.f;
-#pragma unroll
-      for (int c0 = 0; c0 < 2 * KP; c0 += 16) {
-        if (c0 < a.n_pad) {
-          float t[16];
-          tmem_ld16(trow + (uint32_t)c0, t);
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int n = (c0 >> 1) + i;
-            const float ph = q * scale;
-            xr = fmaf(t[2 * i], ph, xr);
-            xi = fmaf(t[2 * i + 1], ph, xi);
-            const float qn = fmaf(c_herm_a[n] * y, q, -c_herm_b[n] * q_prev);
-            q_prev = q;
-            q = qn;
-            if ((i & 3) == 3 && fabsf(q) > 1.8446744e19f) {
-              q *= 5.421011e-20f;
-              q_prev *= 5.421011e-20f;
-              E -= 64;
-              scale = ldexpf(1.0f, -E);
-            }
-          }
+      // accumulator row in chunks of 16 columns (8 n2), the next chunk's load in flight while one is used
+      const int nch = a.n_pad >> 4;
+      uint32_t tb0[16], tb1[16];
+      tmem_issue16x(trow, tb0);
+      tmem_wait16(tb0);
+#pragma unroll 1
+      for (int c = 0; c < nch; c += 2) {
+        if (c + 1 < nch) tmem_issue16x(trow + (uint32_t)((c + 1) << 4), tb1);
+        if (yfast) epi_chunk<false>(tb0, ca, cb, c << 3, y, q, q_prev, xr, xi, E, scale);
+        else epi_chunk<true>(tb0, ca, cb, c << 3, y, q, q_prev, xr, xi, E, scale);
+        tmem_wait16(tb1);
+        if (c + 1 < nch) {
+          if (c + 2 < nch) tmem_issue16x(trow + (uint32_t)((c + 2) << 4), tb0);
+          if (yfast) epi_chunk<false>(tb1, ca, cb, (c + 1) << 3, y, q, q_prev, xr, xi, E, scale);
+          else epi_chunk<true>(tb1, ca, cb, (c + 1) << 3, y, q, q_prev, xr, xi, E, scale);
+          tmem_wait16(tb0);
         }
       }
       tc_fence_before();
+      mbar_arrive(&tfree[sp]);
       if (valid) {
         // Z = amp (xr + i xi) P
         const float zr = amp * (xr * P.x - xi * P.y), zi = amp * (xr * P.y + xi * P.x);
-        const size_t idx = (size_t)vis;
         if (a.mode == OUT_STORE) {
           a.out[idx] = make_float2(zr, zi);
         } else if (a.mode == OUT_ACCUM) {
-          const float2 o = a.out[idx];
-          a.out[idx] = make_float2(o.x + zr, o.y + zi);
+          a.out[idx] = make_float2(base.x + zr, base.y + zi);
         } else {
           float2 G;
           if (!gain_product(a.peel, row, a.n_base, f, G)) atomicOr(a.err, WN_DEVERR_ANTENNA);
-          const float2 base = a.mode == OUT_PEEL ? a.peel.data[idx] : a.out[idx];
           a.out[idx] = make_float2(base.x - (G.x * zr - G.y * zi), base.y - (G.x * zi + G.y * zr));
         }
       }
     }
   }
+done:
   __syncthreads();
-  if (warp == mma_warp) {
+  if (warp == K2_MMA_WARP) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
   }
@@ -425,7 +536,7 @@ int launch_shapelets(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, 
     a.mode = q == 0 ? mode : (mode == OUT_STORE ? OUT_ACCUM : (mode == OUT_PEEL ? OUT_SUBG : mode));
     a.groups = K2_GROUPS;
     K2Layout lay = k2_layout(h.k_pad, h.n_pad, passes, a.groups);
-    if (lay.total > 227 * 1024) {
+    if (lay.total > 227 * 1024) {  // large n_max in the split mode: one tile in flight
       a.groups = 1;
       lay = k2_layout(h.k_pad, h.n_pad, passes, 1);
     }
