@@ -183,6 +183,24 @@ WN_API int wn_predict_grad(wn_ctx* ctx, const wn_obs* obs, int model_id, const v
                     const void* data_c64, void* resid_c64, const wn_sky_grad* grad_out, double* loss_out,
                     void* stream);
 
+/* ---- allocation-free prediction ------------------------------------------------------------ */
+
+/* The paper has no counterpart to this call; it exists for callers that cannot allocate device memory
+ * at prediction time, for example a process whose device memory is fully reserved by another
+ * allocator (a framework's caching allocator or a fixed-size pool), or a latency-critical loop that
+ * cannot afford cudaMalloc's implicit device synchronisation.  It computes what wn_predict computes,
+ * but the shapelet launches take their per-channel and per-row tables from a file-scope device array
+ * of 2^18 float4 entries (4 MiB, held by every GPU that loads the library until exit) instead of the
+ * context's growable workspace, and nothing in the call allocates.
+ * Limits: n_chan rounded up to a multiple of 16, plus n_time * n_base, must not exceed 262144;
+ * larger observations are rejected with WN_EINVAL.
+ * The first call on a device looks up the array's device address (and uploads the Hermite recurrence
+ * constants) for that device; make that first call before any stream capture on the device.
+ * Every call in the process shares the array and it keeps the last call's contents; calls whose work
+ * overlaps on the GPU (concurrent streams, devices sharing the process) race on it, so order them.
+ * The model must already be resident (wn_sky_upload) and the context created beforehand. */
+WN_API int wn_predict_static(wn_ctx* ctx, const wn_obs* obs, int model_id, void* vis_c64, int accumulate, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

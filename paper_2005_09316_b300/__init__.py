@@ -26,7 +26,7 @@ WN_DEVERR_ANTENNA, WN_DEVERR_TIMEOUT, WN_DEVERR_SKY = 0x1, 0x2, 0x4
 
 EXPORTED = ("wn_create", "wn_destroy", "wn_last_error", "wn_version", "wn_set_precision", "wn_device_errors",
             "wn_sky_upload", "wn_sky_free", "wn_sky_bytes", "wn_predict", "wn_peel", "wn_peel_model",
-            "wn_predict_grad")
+            "wn_predict_grad", "wn_predict_static")
 
 
 class WnError(RuntimeError):
@@ -81,6 +81,7 @@ def load(build_if_missing: bool = True):
         L.wn_sky_free.argtypes = [P, i]
         L.wn_sky_bytes.argtypes = [P, i, ctypes.POINTER(ctypes.c_size_t)]
         L.wn_predict.argtypes = [P, ctypes.POINTER(WnObs), i, P, i, P]
+        L.wn_predict_static.argtypes = [P, ctypes.POINTER(WnObs), i, P, i, P]
         L.wn_peel.argtypes = [P, ctypes.POINTER(WnObs), i, P, i, i, P, P, P]
         L.wn_peel_model.argtypes = [P, ctypes.POINTER(WnObs), P, i, i, P, P, P, P]
         L.wn_predict_grad.argtypes = [P, ctypes.POINTER(WnObs), i, P, i, i, P, P, ctypes.POINTER(WnSkyGrad),
@@ -258,6 +259,14 @@ class Context:
         o = obs.struct()
         _check(load().wn_predict(self.h, ctypes.byref(o), model.id, out.data_ptr(), int(accumulate),
                                  _stream_handle(stream)))
+        return out
+
+    def predict_static(self, obs: DeviceObs, model: Model, out=None, accumulate: bool = False, stream=None):
+        """wn_predict_static: the same prediction without any device allocation (fixed-size scratch)."""
+        out = self._vis(obs, out)
+        o = obs.struct()
+        _check(load().wn_predict_static(self.h, ctypes.byref(o), model.id, out.data_ptr(), int(accumulate),
+                                        _stream_handle(stream)))
         return out
 
     def peel(self, obs: DeviceObs, model: Model, gains, data, out=None, stream=None):

@@ -22,6 +22,8 @@
 //  Per parity: P(k+2) waits for MMA(k) to finish reading A, MMA(k+2) for E(k) to release TMEM.
 // Every wait is bounded; on a timeout the kernel raises WN_DEVERR_TIMEOUT, drains its own commits and
 // frees TMEM before returning.
+#include <mutex>
+
 #include "wn_internal.cuh"
 
 namespace wn {
@@ -564,3 +566,98 @@ extern "C" int wn_predict_grad(wn_ctx*, const wn_obs*, int, const void*, int, in
                                const wn_sky_grad*, double*, void*) {
   return wn::set_error(WN_EINVAL, "adjoint not built yet");
 }
+
+// ------------------------------------------------------------------------------------------------
+// Allocation-free shapelet launches (wn_predict_static).  The per-channel and per-row constants
+// that launch_shapelets keeps in the context's growable workspace live here in a fixed device array
+// instead, so the call never allocates.  The array is shared by every call in the process and keeps
+// the last call's contents; both tables are fully rewritten by the prep kernels before the main
+// kernel reads them, so nothing needs clearing, but calls whose work overlaps on the GPU race on it.
+// ------------------------------------------------------------------------------------------------
+namespace wn {
+
+constexpr size_t kStaticScratchEntries = size_t(1) << 18;  // float4 entries (4 MiB): n_chan (padded to 16) + n_rows
+static __device__ __align__(256) float4 g_static_scratch[kStaticScratchEntries];
+static float4* g_static_scratch_addr[64] = {nullptr};
+static std::mutex g_static_scratch_mu;
+
+// Device address of the array for `device` (which must be current).  In host code the symbol is only
+// a host-side stand-in, so the address is looked up once per device and cached.
+static int static_scratch_address(int device, float4** out) {
+  std::lock_guard<std::mutex> lock(g_static_scratch_mu);
+  if (device < 0 || device >= 64) return set_error(WN_EINVAL, "device index out of range for the static scratch");
+  if (!g_static_scratch_addr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return set_error(WN_ECUDA, std::string("cudaGetSymbolAddress(static scratch): ") + cudaGetErrorString(e));
+    g_static_scratch_addr[device] = static_cast<float4*>(p);
+  }
+  *out = g_static_scratch_addr[device];
+  return WN_OK;
+}
+
+size_t static_scratch_entries() { return kStaticScratchEntries; }
+
+int launch_shapelets_static(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, int mode, const PeelArgs& pa,
+                            cudaStream_t st) {
+  const size_t chan_entries = ((size_t)o.n_chan + 15) & ~(size_t)15;
+  if (chan_entries + (size_t)o.n_rows > kStaticScratchEntries)
+    return set_error(WN_EINVAL, "wn_predict_static: n_chan (rounded up to 16) + n_time * n_base = " +
+                                    std::to_string(chan_entries + (size_t)o.n_rows) + " exceeds the static scratch of " +
+                                    std::to_string(kStaticScratchEntries) + " entries");
+  float4* base = nullptr;
+  if (int r = static_scratch_address(ctx->device, &base)) return r;
+  if (int r = k2_setup_constants(ctx->device, st)) return r;
+  float4* chaninfo = base;
+  float4* rowinfo = base + chan_entries;
+  k2_chaninfo<<<(o.n_chan + 255) / 256, 256, 0, st>>>(o.freq, o.n_chan, o.nu0, chaninfo);
+  const long long n_vis = (long long)o.n_rows * o.n_chan;
+  const int n_tiles = (int)((n_vis + K2_M - 1) / K2_M);
+  const int passes = ctx->shape_mode == WN_SHAPE_BF16X1 ? 1 : 3;
+  const double L0 = std::log2(o.nu0);
+  for (int q = 0; q < M->n_shape; ++q) {
+    const ShapeRec& h = M->sh_host[q];
+    k2_rowinfo<<<(o.n_rows + 255) / 256, 256, 0, st>>>(o.uvw, o.n_rows, M->sh + q, o.dec0, rowinfo);
+    K2Args a;
+    a.rowinfo = rowinfo;
+    a.chaninfo = chaninfo;
+    a.bop = M->bop + h.b_off;
+    a.n_pad = h.n_pad;
+    a.nmax = h.nmax;
+    a.passes = passes;
+    a.n_chan = o.n_chan;
+    a.n_base = o.n_base;
+    a.n_tiles = n_tiles;
+    a.n_vis = n_vis;
+    a.c_amp = (float)((double)h.lS + (double)h.alpha * (L0 - h.lref));
+    a.alpha = h.alpha;
+    a.sgn = h.sgn;
+    a.out = out;
+    a.peel = pa;
+    a.err = ctx->d_err;
+    a.mode = q == 0 ? mode : (mode == OUT_STORE ? OUT_ACCUM : (mode == OUT_PEEL ? OUT_SUBG : mode));
+    a.groups = K2_GROUPS;
+    K2Layout lay = k2_layout(h.k_pad, h.n_pad, passes, a.groups);
+    if (lay.total > 227 * 1024) {
+      a.groups = 1;
+      lay = k2_layout(h.k_pad, h.n_pad, passes, 1);
+    }
+    if (lay.total > 227 * 1024) return set_error(WN_EINVAL, "shapelet operand does not fit in shared memory");
+    const int grid = std::min(n_tiles, ctx->num_sms);
+    cudaError_t e;
+    switch (h.k_pad) {
+      case 16: e = k2_launch_t<16>(a, grid, lay.total, st); break;
+      case 32: e = k2_launch_t<32>(a, grid, lay.total, st); break;
+      case 48: e = k2_launch_t<48>(a, grid, lay.total, st); break;
+      case 64: e = k2_launch_t<64>(a, grid, lay.total, st); break;
+      case 80: e = k2_launch_t<80>(a, grid, lay.total, st); break;
+      case 96: e = k2_launch_t<96>(a, grid, lay.total, st); break;
+      case 112: e = k2_launch_t<112>(a, grid, lay.total, st); break;
+      default: e = k2_launch_t<128>(a, grid, lay.total, st); break;
+    }
+    if (e != cudaSuccess) return set_error(WN_ECUDA, std::string("shapelet kernel launch: ") + cudaGetErrorString(e));
+  }
+  return WN_OK;
+}
+
+}  // namespace wn

@@ -410,4 +410,30 @@ int wn_peel_model(wn_ctx* ctx, const wn_obs* obs, const void* gains_c64, int gai
   return r == WN_OK ? ok() : r;
 }
 
+// Allocation-free prediction: like wn_predict, but the shapelet launches take their per-row and
+// per-channel tables from a fixed device array instead of the context's workspace, so the call
+// makes no device allocation.  Points and Gaussians, and the FP64 form, need no scratch at all.
+int wn_predict_static(wn_ctx* ctx, const wn_obs* obs, int model_id, void* vis_c64, int accumulate, void* stream) {
+  if (!ctx || !vis_c64) return set_error(WN_EINVAL, "NULL argument");
+  ObsDev d;
+  if (int r = check_obs(obs, d)) return r;
+  Model* M = find_model(ctx, model_id);
+  if (!M) return set_error(WN_ENOTFOUND, "unknown model id");
+  if (accumulate != 0 && accumulate != 1) return set_error(WN_EINVAL, "accumulate must be 0 or 1");
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int mode = accumulate ? OUT_ACCUM : OUT_STORE;
+  PeelArgs pa;
+  int r = WN_OK;
+  if (ctx->precision == WN_PREC_FP64) {
+    r = launch_phasor_fp64(ctx, d, M, static_cast<float2*>(vis_c64), mode, pa, true, st);
+  } else {
+    const bool have_pg = M->n_point + M->n_gauss > 0;
+    if (have_pg || M->n_shape == 0) r = launch_phasor_mixed(ctx, d, M, static_cast<float2*>(vis_c64), mode, pa, st);
+    if (r == WN_OK && M->n_shape > 0)
+      r = launch_shapelets_static(ctx, d, M, static_cast<float2*>(vis_c64), have_pg ? OUT_ACCUM : mode, pa, st);
+  }
+  return r == WN_OK ? ok() : r;
+}
+
 }  // extern "C"

@@ -269,4 +269,7 @@ int launch_peel_model(wn_ctx* ctx, const ObsDev& o, const PeelArgs& pa, const fl
                       cudaStream_t st);
 int launch_shapelets(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, int mode, const PeelArgs& pa,
                      cudaStream_t st);
+int launch_shapelets_static(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, int mode, const PeelArgs& pa,
+                            cudaStream_t st);
+size_t static_scratch_entries();
 }  // namespace wn
