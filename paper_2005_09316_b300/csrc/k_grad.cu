@@ -1,0 +1,572 @@
+// K4: adjoint of the fused predict + peel.  For L = sum_vis |D - G V|^2 with G = g_ant1 conj(g_ant2),
+//   dL/dp = -2 sum_vis Re( conj(W) dV/dp ),   W = conj(G) R,   R = D - G V.
+// The paper fits in image space and gives no derivatives; they follow term by term from
+// eq:env_visi_def, eq:gauss-env and eq:shape-env (V_j = S_j xi_j e^{-2 pi i tau_j nu / c}):
+//   dV_j/dS_ref = V_j / S_ref,  dV_j/dalpha = ln(nu / nu_ref) V_j,
+//   dV_j/dl = -2 pi i (nu/c) (u - w l / n) V_j (likewise m; the shapelet re-phasing frame is held fixed),
+//   Gaussian: dxi/dmaj = -2E (nu/c)^2 maj kx^2 xi, dxi/dmin = -2E (nu/c)^2 min ky^2 xi,
+//             dxi/dpa = -2E (nu/c)^2 (maj^2 - min^2) kx ky xi   (kx, ky in metres, E = pi^2 / (4 ln 2)),
+//   Shapelet: x = beta1 kx, y = beta2 ky;  phi_n' = sqrt(n/2) phi_{n-1} - sqrt((n+1)/2) phi_{n+1};
+//             dxi/dbeta1 = sum c s phi_a'(x) (x / beta1) phi_b(y),  dxi/dbeta2 = sum c s phi_a(x) phi_b'(y) (y / beta2),
+//             dxi/dpa = sum c s [phi_a'(x) beta1 (y / beta2) phi_b(y) - phi_a(x) phi_b'(y) beta2 (x / beta1)],
+//             dxi/dc_k = s_k phi_a(x) phi_b(y),  s = (-i)^(a+b).
+// Phasors are recomputed, never stored.  Every sum is reduced in a fixed order (per-lane, warp
+// butterfly, per-warp slots, per-CTA partials, then FP64 over CTAs), so results are reproducible.
+#include <cmath>
+
+#include "wn_internal.cuh"
+
+namespace wn {
+
+constexpr int K4_CT = 32;     // components per CTA: lane j forms comp j's phase argument and sums
+constexpr int K4_WARPS = 8;
+constexpr int K4_KMAX = 16;   // most channels per lane per pass (strided by 32): 512 channels per pass
+constexpr int K4_NG = 7;      // gradient components per point/Gaussian: flux, alpha, l, m, maj, min, pa
+constexpr int K4_FLUSH = 8;   // rows per FP32 partial before it is added to the FP64 sum
+
+struct K4Args {
+  const double* uvw;
+  const double* freq;
+  int n_rows, n_chan, n_base;
+  int f_lo, f_cnt;            // channel pass
+  double nu0;
+  const PGRec* comps;
+  const double *flux, *nuref, *gmaj, *gmin, *gpa;  // raw FP64 tables (all components / Gaussians)
+  int n_point, n_gauss;
+  const float2* resid;
+  PeelArgs peel;              // gains and antenna indices (data unused)
+  int rows_per_chunk;
+  double* partials;           // [chunks][n_pg][K4_NG]
+  unsigned* err;
+};
+
+// Point / Gaussian gradients.  grid = (component tiles of 32, row chunks); warp w takes rows
+// r0 + w, r0 + w + 8, ...; lane l takes channels f_lo + l + 32 k of each row.
+template <int KM>
+__global__ void __launch_bounds__(K4_WARPS * 32) k4_grad_pg(const K4Args a) {
+  __shared__ PGRec comps[K4_CT];
+  __shared__ double gsum[K4_WARPS][K4_CT][K4_NG];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_pg = a.n_point + a.n_gauss;
+  const int c0 = blockIdx.x * K4_CT;
+  const int ncomp = min(K4_CT, n_pg - c0);
+  if (threadIdx.x < ncomp) comps[threadIdx.x] = a.comps[c0 + threadIdx.x];
+  __syncthreads();
+
+  // per-lane channel constants
+  float ah[KM], al[KM], lam[KM], nuc[KM], wg[KM];
+  int fch[KM];
+#pragma unroll
+  for (int k = 0; k < KM; ++k) {
+    const int fi = lane + 32 * k;
+    fch[k] = fi < a.f_cnt ? a.f_lo + fi : -1;
+    const double nu = a.freq[fch[k] >= 0 ? fch[k] : a.f_lo];
+    split_double(nu / kC, ah[k], al[k]);
+    lam[k] = (float)log2(nu / a.nu0);
+    nuc[k] = (float)(nu / kC);
+    wg[k] = (float)(kGaussE * kLog2e * (nu / kC) * (nu / kC));
+  }
+  const double L0 = log2(a.nu0);
+
+  // this lane's component (lane j <-> component c0 + j)
+  const bool mine = lane < ncomp;
+  const int jc = c0 + (mine ? lane : 0);
+  const PGRec& me = comps[mine ? lane : 0];
+  const bool my_gauss = mine && jc >= a.n_point;
+  const double my_n = 1.0 + me.nm1;
+  const float my_lnref = (float)((L0 - me.lref) * 0.6931471805599453);  // ln(nu0 / nu_ref)
+  const float my_S = mine ? (float)a.flux[jc] : 0.f;
+  float my_pa = 0.f, my_maj = 0.f, my_min = 0.f;
+  if (my_gauss) {
+    const int g = jc - a.n_point;
+    my_maj = (float)a.gmaj[g];
+    my_min = (float)a.gmin[g];
+    my_pa = (float)a.gpa[g];
+  }
+  const float sp = sinf(my_pa), cp = cosf(my_pa);
+
+  float acc32[K4_NG];
+  double acc64[K4_NG];
+#pragma unroll
+  for (int i = 0; i < K4_NG; ++i) {
+    acc32[i] = 0.f;
+    acc64[i] = 0.0;
+  }
+
+  const int r_lo = blockIdx.y * a.rows_per_chunk;
+  const int r_hi = min(a.n_rows, r_lo + a.rows_per_chunk);
+  int nrow = 0;
+  for (int row = r_lo + warp; row < r_hi; row += K4_WARPS) {
+    const double u = a.uvw[3 * (size_t)row], v = a.uvw[3 * (size_t)row + 1], w = a.uvw[3 * (size_t)row + 2];
+    // W = conj(G) R for this lane's channels
+    float2 W[KM];
+#pragma unroll
+    for (int k = 0; k < KM; ++k) {
+      W[k] = make_float2(0.f, 0.f);
+      if (fch[k] >= 0) {
+        float2 G;
+        if (!gain_product(a.peel, row, a.n_base, fch[k], G)) atomicOr(a.err, WN_DEVERR_ANTENNA);
+        const float2 R = a.resid[(size_t)row * a.n_chan + fch[k]];
+        W[k] = make_float2(G.x * R.x + G.y * R.y, G.x * R.y - G.y * R.x);
+      }
+    }
+    // this lane's component: phase argument (FP64), Gaussian form and the per-row factors
+    float th = 0.f, tl = 0.f, q = 0.f, fl = 0.f, fm = 0.f, fmaj = 0.f, fmin = 0.f, fpa = 0.f;
+    if (mine) {
+      split_double(fma(u, me.l, fma(v, me.m, w * me.nm1)), th, tl);
+      fl = (float)(-4.0 * kPi * (u - w * me.l / my_n));
+      fm = (float)(-4.0 * kPi * (v - w * me.m / my_n));
+      if (my_gauss) {
+        const float uf = (float)u, vf = (float)v;
+        q = me.ga * uf * uf + me.gb * uf * vf + me.gc * vf * vf;
+        const float kx = sp * uf + cp * vf, ky = cp * uf - sp * vf;
+        fmaj = 4.0f * (float)kGaussE * my_maj * kx * kx;
+        fmin = 4.0f * (float)kGaussE * my_min * ky * ky;
+        fpa = 4.0f * (float)kGaussE * (my_maj * my_maj - my_min * my_min) * kx * ky;
+      }
+    }
+    for (int j = 0; j < ncomp; ++j) {
+      const float tj = __shfl_sync(0xffffffffu, th, j), tlj = __shfl_sync(0xffffffffu, tl, j);
+      const float qj = __shfl_sync(0xffffffffu, q, j);
+      const PGRec& c = comps[j];
+      // channel sums use the amplitude without the flux: dV/dS_ref = V / S_ref holds for S_ref = 0 too
+      const float cj = c.alpha * (float)(L0 - c.lref);
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll
+      for (int k = 0; k < KM; ++k) {
+        if (fch[k] < 0) continue;
+        const float2 P = phasor_fast(reduce_turns(tj, tlj, ah[k], al[k]));
+        const float A = ex2_approx(fmaf(c.alpha, lam[k], cj) - qj * wg[k]);
+        const float vr = A * P.x, vi = A * P.y;
+        // z = conj(W) V
+        const float zr = W[k].x * vr + W[k].y * vi, zi = W[k].x * vi - W[k].y * vr;
+        s0 += zr;
+        s1 = fmaf(lam[k], zr, s1);
+        s2 = fmaf(nuc[k], zi, s2);
+        s3 = fmaf(nuc[k] * nuc[k], zr, s3);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        s3 += __shfl_xor_sync(0xffffffffu, s3, o);
+      }
+      if (lane == j) {
+        // s1 holds sum log2(nu/nu0) Re z: ln(nu/nu_ref) = ln2 log2(nu/nu0) + ln(nu0/nu_ref)
+        acc32[0] += -2.0f * s0;
+        acc32[1] += -2.0f * my_S * (0.6931471805599453f * s1 + my_lnref * s0);
+        acc32[2] += my_S * fl * s2;
+        acc32[3] += my_S * fm * s2;
+        acc32[4] += my_S * fmaj * s3;
+        acc32[5] += my_S * fmin * s3;
+        acc32[6] += my_S * fpa * s3;
+      }
+    }
+    if (++nrow == K4_FLUSH) {
+#pragma unroll
+      for (int i = 0; i < K4_NG; ++i) {
+        acc64[i] += (double)acc32[i];
+        acc32[i] = 0.f;
+      }
+      nrow = 0;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < K4_NG; ++i) gsum[warp][lane][i] = acc64[i] + (double)acc32[i];
+  __syncthreads();
+  for (int t = threadIdx.x; t < ncomp * K4_NG; t += blockDim.x) {
+    const int j = t / K4_NG, i = t % K4_NG;
+    double s = 0.0;
+    for (int ww = 0; ww < K4_WARPS; ++ww) s += gsum[ww][j][i];
+    a.partials[((size_t)blockIdx.y * n_pg + c0 + j) * K4_NG + i] = s;
+  }
+}
+
+// Sum the per-chunk partials in fixed order and scatter them into the gradient arrays.  Channel
+// passes accumulate (first pass writes).
+__global__ void k4_reduce_pg(const double* partials, int chunks, int n_point, int n_gauss, int first, double* gflux,
+                             double* galpha, double* gl, double* gm, double* gmaj, double* gmin, double* gpa) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n_pg = n_point + n_gauss;
+  if (j >= n_pg) return;
+  double s[K4_NG] = {0, 0, 0, 0, 0, 0, 0};
+  for (int c = 0; c < chunks; ++c)
+    for (int i = 0; i < K4_NG; ++i) s[i] += partials[((size_t)c * n_pg + j) * K4_NG + i];
+  auto put = [&](double* p, int idx, double v) {
+    if (p) p[idx] = first ? v : p[idx] + v;
+  };
+  put(gflux, j, s[0]);
+  put(galpha, j, s[1]);
+  put(gl, j, s[2]);
+  put(gm, j, s[3]);
+  if (j >= n_point) {
+    put(gmaj, j - n_point, s[4]);
+    put(gmin, j - n_point, s[5]);
+    put(gpa, j - n_point, s[6]);
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Shapelets: one launch per shapelet; persistent CTAs of 64 threads, one visibility per thread per
+// tile.  Each thread forms phi_n(x), phi_n(y) (n <= nmax+1) into shared memory, its W, S and phasor,
+// and the envelope derivatives by a loop over the coefficient triples; then the CTA reduces the
+// coefficient gradients sum_vis w phi_a(x) phi_b(y) for the tile (w = Re or Im of conj(W) S P by the
+// parity of a+b) into FP64 shared accumulators.
+// ---------------------------------------------------------------------------------------------
+constexpr int K4S_T = 64;
+constexpr int K4S_NS = 7;  // flux, alpha, l, m, beta1, beta2, pa
+
+struct K4SArgs {
+  const float4* rowinfo;   // per row: (xs, ys, tau hi, tau lo)
+  const float4* chaninfo;  // per channel: (nu/c hi, nu/c lo, log2(nu/nu0), nu)
+  const double* uvw;
+  int n_rows, n_chan, n_base;
+  long long n_vis;
+  int nmax, nnz;
+  const int *n1, *n2;
+  const double* coeff;
+  double l, m, nm1, lnref_nu0;   // ln(nu0 / nu_ref)
+  double flux, beta1, beta2, pa;
+  float c_amp, alpha, sgn;
+  const float2* resid;
+  PeelArgs peel;
+  double* part_s;   // [grid][K4S_NS]
+  double* part_c;   // [grid][nnz]
+  unsigned* err;
+};
+
+__device__ void hermite_scaled_row(float x, int nmax1, float* out) {
+  // phi_0..phi_nmax1(x) in FP32, running on values scaled by 2^E where phi_0 underflows
+  const float hx = 0.5f * x * x * 1.4426950408889634f;
+  int E = fabsf(x) <= 12.5f ? 0 : max(0, (int)ceilf(hx) - 100);
+  float p_prev = 0.f, p = exp2f((float)E - hx);
+  float scale = __int_as_float(max(0, 127 - E) << 23);
+  for (int n = 0; n <= nmax1; ++n) {
+    out[n] = p * scale;
+    const float pn = sqrtf(2.0f / (n + 1)) * x * p - sqrtf((float)n / (n + 1)) * p_prev;
+    p_prev = p;
+    p = pn;
+    if (fabsf(p) > 1.8446744e19f) {
+      p *= 5.421011e-20f;
+      p_prev *= 5.421011e-20f;
+      E -= 64;
+      scale = __int_as_float(max(0, 127 - E) << 23);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(K4S_T) k4_grad_shape(const K4SArgs a) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int ld = a.nmax + 3;  // phi_0 .. phi_{nmax+1}, padded
+  float* phx = reinterpret_cast<float*>(sm);
+  float* phy = phx + K4S_T * ld;
+  float* wre = phy + K4S_T * ld;
+  float* wim = wre + K4S_T;
+  double* accc = reinterpret_cast<double*>(wim + K4S_T + (K4S_T & 1));
+  for (int k = threadIdx.x; k < a.nnz; k += K4S_T) accc[k] = 0.0;
+  double accs[K4S_NS] = {0, 0, 0, 0, 0, 0, 0};
+  const int t = threadIdx.x;
+  const long long n_tiles = (a.n_vis + K4S_T - 1) / K4S_T;
+  for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const long long vis = tile * K4S_T + t;
+    const bool valid = vis < a.n_vis;
+    const int row = valid ? (int)(vis / a.n_chan) : 0;
+    const int f = valid ? (int)(vis - (long long)row * a.n_chan) : 0;
+    const float4 ri = a.rowinfo[row], ci = a.chaninfo[f];
+    const float x = ri.x * ci.w, y = ri.y * ci.w;
+    float* px = phx + t * ld;
+    float* py = phy + t * ld;
+    hermite_scaled_row(x, a.nmax + 1, px);
+    hermite_scaled_row(y, a.nmax + 1, py);
+    // W = conj(G) R, amplitude and phasor
+    float2 W = make_float2(0.f, 0.f);
+    if (valid) {
+      float2 G;
+      if (!gain_product(a.peel, row, a.n_base, f, G)) atomicOr(a.err, WN_DEVERR_ANTENNA);
+      const float2 R = a.resid[vis];
+      W = make_float2(G.x * R.x + G.y * R.y, G.x * R.y - G.y * R.x);
+    }
+    const float2 P = phasor_fast(reduce_turns(ri.z, ri.w, ci.x, ci.y));
+    // Y = conj(W) S' P with S' = (nu / nu_ref)^alpha (the flux multiplies every term below but the
+    // flux derivative); contributions are -2 S_ref Re(Y * dxi)
+    const float S = valid ? ex2_approx(fmaf(a.alpha, ci.z, a.c_amp)) : 0.f;
+    const float yr = S * (W.x * P.x + W.y * P.y), yi = S * (W.x * P.y - W.y * P.x);
+    wre[t] = yr;
+    wim[t] = yi;
+    // envelope and its derivatives by the coefficient triples; phase factor (-i)^(a+b)
+    float xr = 0.f, xi = 0.f, d1r = 0.f, d1i = 0.f, d2r = 0.f, d2i = 0.f, dpr = 0.f, dpi = 0.f;
+    const float rb = (float)(a.beta1 / a.beta2), rb2 = (float)(a.beta2 / a.beta1);
+    for (int k = 0; k < a.nnz; ++k) {
+      const int na = __ldg(a.n1 + k), nb = __ldg(a.n2 + k);
+      const float c = (float)__ldg(a.coeff + k);
+      const float fa = px[na], fb = py[nb];
+      const float dxa = (na > 0 ? sqrtf(0.5f * na) * px[na - 1] : 0.f) - sqrtf(0.5f * (na + 1)) * px[na + 1];
+      const float dyb = (nb > 0 ? sqrtf(0.5f * nb) * py[nb - 1] : 0.f) - sqrtf(0.5f * (nb + 1)) * py[nb + 1];
+      const float e0 = c * fa * fb;
+      const float e1 = c * dxa * fb;                       // times x / beta1 below
+      const float e2 = c * fa * dyb;                       // times y / beta2 below
+      const float e3 = c * (dxa * rb * y * fb - fa * dyb * rb2 * x);
+      switch ((na + nb) & 3) {
+        case 0: xr += e0; d1r += e1; d2r += e2; dpr += e3; break;
+        case 1: xi -= e0; d1i -= e1; d2i -= e2; dpi -= e3; break;
+        case 2: xr -= e0; d1r -= e1; d2r -= e2; dpr -= e3; break;
+        default: xi += e0; d1i += e1; d2i += e2; dpi += e3; break;
+      }
+    }
+    if (valid) {
+      const float fx = x / (float)a.beta1, fy = y / (float)a.beta2;
+      d1r *= fx; d1i *= fx;
+      d2r *= fy; d2i *= fy;
+      // Re(Y * (pr + i pi)) = yr pr - yi pi
+      const float re_xi = yr * xr - yi * xi;          // Re(conj(W) V)
+      const float im_xi = yr * xi + yi * xr;          // Im(conj(W) V)
+      const double nu = ci.w;
+      const double u = a.uvw[3 * (size_t)row], v = a.uvw[3 * (size_t)row + 1], w = a.uvw[3 * (size_t)row + 2];
+      const double n = 1.0 + a.nm1;
+      accs[0] += -2.0 * re_xi;
+      accs[1] += -2.0 * a.flux * re_xi * ((double)ci.z * 0.6931471805599453 + a.lnref_nu0);
+      accs[2] += -4.0 * kPi * a.flux * (nu / kC) * (u - w * a.l / n) * im_xi;
+      accs[3] += -4.0 * kPi * a.flux * (nu / kC) * (v - w * a.m / n) * im_xi;
+      accs[4] += -2.0 * a.flux * (yr * d1r - yi * d1i);
+      accs[5] += -2.0 * a.flux * (yr * d2r - yi * d2i);
+      accs[6] += -2.0 * a.flux * (yr * dpr - yi * dpi);
+    }
+    __syncthreads();
+    // coefficient gradients for this tile
+    const int nv = (int)min((long long)K4S_T, a.n_vis - tile * K4S_T);
+    for (int k = t; k < a.nnz; k += K4S_T) {
+      const int na = __ldg(a.n1 + k), nb = __ldg(a.n2 + k);
+      const int ph = (na + nb) & 3;
+      const float* wsel = (ph & 1) ? wim : wre;
+      float s = 0.f;
+      for (int vv = 0; vv < nv; ++vv) s = fmaf(wsel[vv] * phx[vv * ld + na], phy[vv * ld + nb], s);
+      // -2 Re(Y s_k) phi phi with s_k = 1, -i, -1, i: Re(Y) , Im(Y), -Re(Y), -Im(Y)
+      accc[k] += (ph >= 2 ? 2.0 : -2.0) * a.flux * (double)s;
+    }
+    __syncthreads();
+  }
+  // per-CTA partials
+  for (int k = t; k < a.nnz; k += K4S_T) a.part_c[(size_t)blockIdx.x * a.nnz + k] = accc[k];
+  __shared__ double red[K4S_T][K4S_NS];
+  for (int i = 0; i < K4S_NS; ++i) red[t][i] = accs[i];
+  __syncthreads();
+  if (t < K4S_NS) {
+    double s = 0.0;
+    for (int q = 0; q < K4S_T; ++q) s += red[q][t];
+    a.part_s[(size_t)blockIdx.x * K4S_NS + t] = s;
+  }
+}
+
+__global__ void k4_reduce_shape(const double* part_s, const double* part_c, int grid, int nnz, int j, int q,
+                                double* gflux, double* galpha, double* gl, double* gm, double* gb1, double* gb2,
+                                double* gpa, double* gcoeff, int coeff_off, int first) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  auto put = [&](double* p, int idx, double v) {
+    if (p) p[idx] = first ? v : p[idx] + v;
+  };
+  if (t < nnz) {
+    double s = 0.0;
+    for (int c = 0; c < grid; ++c) s += part_c[(size_t)c * nnz + t];
+    put(gcoeff, coeff_off + t, s);
+  }
+  if (t < K4S_NS) {
+    double s = 0.0;
+    for (int c = 0; c < grid; ++c) s += part_s[(size_t)c * K4S_NS + t];
+    switch (t) {
+      case 0: put(gflux, j, s); break;
+      case 1: put(galpha, j, s); break;
+      case 2: put(gl, j, s); break;
+      case 3: put(gm, j, s); break;
+      case 4: put(gb1, q, s); break;
+      case 5: put(gb2, q, s); break;
+      default: put(gpa, q, s); break;
+    }
+  }
+}
+
+// L = sum |R|^2: FP32 per thread over a grid-stride run, FP64 from there on, fixed order.
+__global__ void k4_loss_partial(const float2* r, size_t n, double* part) {
+  __shared__ double red[256];
+  double s = 0.0;
+  float f = 0.f;
+  int cnt = 0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float2 v = r[i];
+    f = fmaf(v.x, v.x, fmaf(v.y, v.y, f));
+    if (++cnt == 64) {
+      s += f;
+      f = 0.f;
+      cnt = 0;
+    }
+  }
+  red[threadIdx.x] = s + f;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void k4_loss_final(const double* part, int n, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += part[i];
+    *out = s;
+  }
+}
+
+int launch_shapelet_prep(wn_ctx* ctx, const ObsDev& o, const Model* M, int q, float4* chaninfo, float4* rowinfo,
+                         bool chan, cudaStream_t st);
+
+static int cuda_err(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(WN_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return WN_OK;
+}
+
+int run_model_peel(wn_ctx* ctx, const ObsDev& d, const Model* M, float2* out, const PeelArgs& pa, cudaStream_t st);
+
+int launch_grad(wn_ctx* ctx, const ObsDev& o, const Model* M, const PeelArgs& pa, float2* resid,
+                const wn_sky_grad* g, double* loss, cudaStream_t st) {
+  // 1. forward: resid = data - G V
+  if (int r = run_model_peel(ctx, o, M, resid, pa, st)) return r;
+  // workspace: loss partials, point/Gaussian partials, shapelet tables and partials
+  const int n_pg = M->n_point + M->n_gauss;
+  const int loss_blocks = ctx->num_sms * 2;
+  const int comp_tiles = (n_pg + K4_CT - 1) / K4_CT;
+  int chunks = 1;
+  if (n_pg > 0) {
+    // enough CTAs for ~4 waves, bounded so the partials stay small
+    chunks = std::max(1, std::min(o.n_rows / 16, (ctx->num_sms * 8 + comp_tiles - 1) / std::max(1, comp_tiles)));
+  }
+  const int rows_per_chunk = (o.n_rows + chunks - 1) / chunks;
+  int max_nnz = 0;
+  for (int q = 0; q < M->n_shape; ++q) max_nnz = std::max(max_nnz, M->s_off_host[q + 1] - M->s_off_host[q]);
+  const int sgrid = ctx->num_sms * 2;
+  const size_t chan_bytes = ((size_t)o.n_chan * sizeof(float4) + 255) & ~(size_t)255;
+  const size_t row_bytes = ((size_t)o.n_rows * sizeof(float4) + 255) & ~(size_t)255;
+  const size_t loss_bytes = ((size_t)loss_blocks * 8 + 255) & ~(size_t)255;
+  const size_t pg_bytes = ((size_t)chunks * n_pg * K4_NG * 8 + 255) & ~(size_t)255;
+  const size_t sh_bytes = M->n_shape ? (((size_t)sgrid * (K4S_NS + max_nnz) * 8 + 255) & ~(size_t)255) : 0;
+  const size_t need = chan_bytes + row_bytes + loss_bytes + pg_bytes + sh_bytes;
+  if (ctx->ws2_bytes < need) {
+    if (ctx->ws2) {
+      cudaStreamSynchronize(st);
+      cudaFree(ctx->ws2);
+      ctx->ws2 = nullptr;
+      ctx->ws2_bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&ctx->ws2, need);
+    if (e != cudaSuccess) return set_error(WN_ENOMEM, std::string("adjoint workspace: ") + cudaGetErrorString(e));
+    ctx->ws2_bytes = need;
+  }
+  char* ws = static_cast<char*>(ctx->ws2);
+  float4* chaninfo = reinterpret_cast<float4*>(ws);
+  float4* rowinfo = reinterpret_cast<float4*>(ws + chan_bytes);
+  double* lpart = reinterpret_cast<double*>(ws + chan_bytes + row_bytes);
+  double* pgpart = reinterpret_cast<double*>(ws + chan_bytes + row_bytes + loss_bytes);
+  double* shpart = reinterpret_cast<double*>(ws + chan_bytes + row_bytes + loss_bytes + pg_bytes);
+
+  // 2. loss
+  const size_t n_vis = (size_t)o.n_rows * o.n_chan;
+  if (loss) {
+    k4_loss_partial<<<loss_blocks, 256, 0, st>>>(resid, n_vis, lpart);
+    k4_loss_final<<<1, 32, 0, st>>>(lpart, loss_blocks, loss);
+    if (int r = cuda_err("loss kernels")) return r;
+  }
+  // 3. points and Gaussians, one pass per 512 channels
+  if (n_pg > 0) {
+    const int npass = (o.n_chan + 32 * K4_KMAX - 1) / (32 * K4_KMAX);
+    for (int p = 0; p < npass; ++p) {
+      K4Args a;
+      a.uvw = o.uvw;
+      a.freq = o.freq;
+      a.n_rows = o.n_rows;
+      a.n_chan = o.n_chan;
+      a.n_base = o.n_base;
+      a.f_lo = p * 32 * K4_KMAX;
+      a.f_cnt = std::min(32 * K4_KMAX, o.n_chan - a.f_lo);
+      a.nu0 = o.nu0;
+      a.comps = M->pg;
+      a.flux = M->r_flux();
+      a.nuref = M->r_nuref();
+      a.gmaj = M->r_gmaj();
+      a.gmin = M->r_gmin();
+      a.gpa = M->r_gpa();
+      a.n_point = M->n_point;
+      a.n_gauss = M->n_gauss;
+      a.resid = resid;
+      a.peel = pa;
+      a.rows_per_chunk = rows_per_chunk;
+      a.partials = pgpart;
+      a.err = ctx->d_err;
+      const dim3 grid(comp_tiles, chunks);
+      const int km = (a.f_cnt + 31) / 32;
+      if (km <= 2) k4_grad_pg<2><<<grid, K4_WARPS * 32, 0, st>>>(a);
+      else if (km <= 4) k4_grad_pg<4><<<grid, K4_WARPS * 32, 0, st>>>(a);
+      else if (km <= 8) k4_grad_pg<8><<<grid, K4_WARPS * 32, 0, st>>>(a);
+      else if (km <= 12) k4_grad_pg<12><<<grid, K4_WARPS * 32, 0, st>>>(a);
+      else k4_grad_pg<16><<<grid, K4_WARPS * 32, 0, st>>>(a);
+      k4_reduce_pg<<<(n_pg + 127) / 128, 128, 0, st>>>(pgpart, chunks, M->n_point, M->n_gauss, p == 0, g->flux,
+                                                       g->alpha, g->l, g->m, g->g_maj, g->g_min, g->g_pa);
+      if (int r = cuda_err("point/Gaussian adjoint")) return r;
+    }
+  }
+  // 4. shapelets
+  const double L0 = std::log2(o.nu0);
+  for (int q = 0; q < M->n_shape; ++q) {
+    if (int r = launch_shapelet_prep(ctx, o, M, q, chaninfo, rowinfo, q == 0, st)) return r;
+    const ShapeRec& h = M->sh_host[q];
+    const int j = n_pg + q;
+    K4SArgs a;
+    a.rowinfo = rowinfo;
+    a.chaninfo = chaninfo;
+    a.uvw = o.uvw;
+    a.n_rows = o.n_rows;
+    a.n_chan = o.n_chan;
+    a.n_base = o.n_base;
+    a.n_vis = (long long)n_vis;
+    a.nmax = h.nmax;
+    a.nnz = M->s_off_host[q + 1] - M->s_off_host[q];
+    a.n1 = M->m_n1() + M->s_off_host[q];
+    a.n2 = M->m_n2() + M->s_off_host[q];
+    a.coeff = M->s_coeff + M->s_off_host[q];
+    a.l = h.l;
+    a.m = h.m;
+    a.nm1 = h.nm1;
+    a.lnref_nu0 = (L0 - h.lref) * 0.6931471805599453;
+    a.c_amp = (float)((double)h.alpha * (L0 - h.lref));  // flux-free
+    a.alpha = h.alpha;
+    a.sgn = h.sgn;
+    double hostv[4];
+    cudaMemcpyAsync(hostv, M->r_flux() + j, sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(hostv + 1, M->r_sb1() + q, sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(hostv + 2, M->r_sb2() + q, sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(hostv + 3, M->r_spa() + q, sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    a.flux = hostv[0];
+    a.beta1 = hostv[1];
+    a.beta2 = hostv[2];
+    a.pa = hostv[3];
+    a.resid = resid;
+    a.peel = pa;
+    a.part_s = shpart;
+    a.part_c = shpart + (size_t)sgrid * K4S_NS;
+    a.err = ctx->d_err;
+    const int ld = h.nmax + 3;
+    const size_t smem = (size_t)(2 * K4S_T * ld + 2 * K4S_T + 2) * 4 + (size_t)a.nnz * 8 + 16;
+    if (smem > 227 * 1024) return set_error(WN_EINVAL, "adjoint: shapelet too large for the shared-memory reduction");
+    cudaFuncSetAttribute(k4_grad_shape, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k4_grad_shape<<<sgrid, K4S_T, smem, st>>>(a);
+    const int rt = std::max(a.nnz, K4S_NS);
+    k4_reduce_shape<<<(rt + 127) / 128, 128, 0, st>>>(shpart, shpart + (size_t)sgrid * K4S_NS, sgrid, a.nnz, j, q,
+                                                      g->flux, g->alpha, g->l, g->m, g->s_beta1, g->s_beta2, g->s_pa,
+                                                      g->s_coeff, M->s_off_host[q], 1);
+    if (int r = cuda_err("shapelet adjoint")) return r;
+  }
+  return WN_OK;
+}
+
+}  // namespace wn

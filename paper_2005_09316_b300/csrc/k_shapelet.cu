@@ -562,10 +562,7 @@ int launch_shapelets(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, 
 
 }  // namespace wn
 
-extern "C" int wn_predict_grad(wn_ctx*, const wn_obs*, int, const void*, int, int, const void*, void*,
-                               const wn_sky_grad*, double*, void*) {
-  return wn::set_error(WN_EINVAL, "adjoint not built yet");
-}
+
 
 // ------------------------------------------------------------------------------------------------
 // Allocation-free shapelet launches (wn_predict_static).  The per-channel and per-row constants
@@ -660,4 +657,17 @@ int launch_shapelets_static(wn_ctx* ctx, const ObsDev& o, const Model* M, float2
   return WN_OK;
 }
 
+}  // namespace wn
+
+namespace wn {
+// Per-channel and per-row tables of shapelet q for the adjoint (same definitions as the prediction).
+int launch_shapelet_prep(wn_ctx* ctx, const ObsDev& o, const Model* M, int q, float4* chaninfo, float4* rowinfo,
+                         bool chan, cudaStream_t st) {
+  (void)ctx;
+  if (chan) k2_chaninfo<<<(o.n_chan + 255) / 256, 256, 0, st>>>(o.freq, o.n_chan, o.nu0, chaninfo);
+  k2_rowinfo<<<(o.n_rows + 255) / 256, 256, 0, st>>>(o.uvw, o.n_rows, M->sh + q, o.dec0, rowinfo);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(WN_ECUDA, std::string("shapelet prep: ") + cudaGetErrorString(e));
+  return WN_OK;
+}
 }  // namespace wn

@@ -124,6 +124,10 @@ static int run_model(wn_ctx* ctx, const ObsDev& d, const Model* M, float2* out, 
   return r;
 }
 
+int run_model_peel(wn_ctx* ctx, const ObsDev& d, const Model* M, float2* out, const PeelArgs& pa, cudaStream_t st) {
+  return run_model(ctx, d, M, out, OUT_PEEL, pa, st);
+}
+
 }  // namespace wn
 
 using namespace wn;
@@ -171,6 +175,7 @@ void wn_destroy(wn_ctx* ctx) {
   for (auto& kv : ctx->models) free_model(kv.second);
   cudaFree(ctx->d_err);
   cudaFree(ctx->ws);
+  cudaFree(ctx->ws2);
   delete ctx;
 }
 
@@ -407,6 +412,24 @@ int wn_peel_model(wn_ctx* ctx, const wn_obs* obs, const void* gains_c64, int gai
   DeviceGuard g(ctx->device);
   int r = launch_peel_model(ctx, d, pa, static_cast<const float2*>(model_c64), static_cast<float2*>(resid_c64),
                             static_cast<cudaStream_t>(stream));
+  return r == WN_OK ? ok() : r;
+}
+
+int wn_predict_grad(wn_ctx* ctx, const wn_obs* obs, int model_id, const void* gains_c64, int gains_t, int gains_f,
+                    const void* data_c64, void* resid_c64, const wn_sky_grad* grad_out, double* loss_out,
+                    void* stream) {
+  if (!ctx || !resid_c64 || !grad_out) return set_error(WN_EINVAL, "NULL argument");
+  if (resid_c64 == data_c64) return set_error(WN_EINVAL, "wn_predict_grad: resid must not alias data");
+  ObsDev d;
+  if (int r = check_obs(obs, d)) return r;
+  Model* M = find_model(ctx, model_id);
+  if (!M) return set_error(WN_ENOTFOUND, "unknown model id");
+  PeelArgs pa;
+  if (int r = check_gains(d, gains_c64, gains_t, gains_f, data_c64, pa)) return r;
+  if (ctx->precision != WN_PREC_MIXED) return set_error(WN_EINVAL, "wn_predict_grad runs in the mixed precision only");
+  DeviceGuard g(ctx->device);
+  int r = launch_grad(ctx, d, M, pa, static_cast<float2*>(resid_c64), grad_out, loss_out,
+                      static_cast<cudaStream_t>(stream));
   return r == WN_OK ? ok() : r;
 }
 

@@ -90,9 +90,11 @@ struct wn_ctx {
   unsigned* d_err = nullptr;
   std::map<int, wn::Model*> models;
   int next_id = 1;
-  // growable workspace (adjoint partial sums)
+  // growable workspaces: shapelet prediction tables, and the adjoint's tables and partial sums
   void* ws = nullptr;
   size_t ws_bytes = 0;
+  void* ws2 = nullptr;
+  size_t ws2_bytes = 0;
 };
 
 namespace wn {
@@ -272,4 +274,6 @@ int launch_shapelets(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, 
 int launch_shapelets_static(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, int mode, const PeelArgs& pa,
                             cudaStream_t st);
 size_t static_scratch_entries();
+int launch_grad(wn_ctx* ctx, const ObsDev& o, const Model* M, const PeelArgs& pa, float2* resid,
+                const wn_sky_grad* g, double* loss, cudaStream_t st);
 }  // namespace wn
