@@ -183,6 +183,53 @@ WN_API int wn_predict_grad(wn_ctx* ctx, const wn_obs* obs, int model_id, const v
                     const void* data_c64, void* resid_c64, const wn_sky_grad* grad_out, double* loss_out,
                     void* stream);
 
+/* ---- continuous-batching server (requests of uneven size) ------------------------------------ */
+
+/* A scheduler thread admits predict / peel requests by memory, packs the tiles of every admitted
+ * request into one batch run by a persistent phasor kernel replayed from a CUDA graph (shapelets
+ * follow per request on the same stream), and keeps up to n_streams batches on the GPU, so requests
+ * that arrive while others run are admitted as slots and pool memory free up and their work overlaps.
+ * Results do not depend on the batch a request ran in (same tiles, same order). */
+typedef struct wn_server wn_server;
+
+/* Request states reported by wn_server_poll. */
+#define WN_REQ_PENDING 0
+#define WN_REQ_ADMITTED 1
+#define WN_REQ_RUNNING 2
+#define WN_REQ_DONE 3
+#define WN_REQ_CANCELLED 4
+#define WN_REQ_FAILED 5
+
+/* Create a server on ctx: n_streams batch slots (1..16), a device pool of pool_bytes for the requests'
+ * outputs, at most max_inflight admitted requests, observations of at most max_rows (T*B) rows and
+ * max_chan channels.  Allocates the pool, per-stream tables and pinned staging, and captures one
+ * graph per stream.  Resident models must not be freed while requests that use them are unreleased. */
+WN_API int wn_server_create(wn_ctx* ctx, int n_streams, size_t pool_bytes, int max_inflight, int max_rows,
+                            int max_chan, wn_server** out);
+/* Stop the scheduler and free everything the server owns (waits for batches on the GPU). */
+WN_API void wn_server_destroy(wn_server* srv);
+/* Queue a request: predict (peel = 0) or peel (peel = 1, with gains [gains_t][gains_f][n_ant] and data
+ * as for wn_peel) of resident model model_id on obs (device arrays that stay valid until the request is
+ * released; the struct itself is copied).  Channels must be uniformly spaced.  Non-blocking.
+ * WN_EBUSY: the output can never fit in the pool; WN_EINVAL: invalid request. */
+WN_API int wn_server_submit(wn_server* srv, const wn_obs* obs, int model_id, int peel, const void* gains_c64,
+                            int gains_t, int gains_f, const void* data_c64, uint64_t* ticket);
+/* State of a request (WN_REQ_*); when done, *vis_out (optional) is the DEVICE address of its
+ * [T][B][F] complex64 result in the pool, valid until wn_server_release.  info (optional, 5 doubles):
+ * submit, admit, launch and completion times in seconds on the server's clock, and the batch index. */
+WN_API int wn_server_poll(wn_server* srv, uint64_t ticket, int* state, void** vis_out, double* info);
+/* Block until the request is done, failed or cancelled, or timeout_s passes (WN_ETIMEOUT). */
+WN_API int wn_server_wait(wn_server* srv, uint64_t ticket, double timeout_s, void** vis_out, double* info);
+/* Copy a finished request's visibilities ([T][B][F] complex64) to dst (DEVICE) on stream. */
+WN_API int wn_server_copy(wn_server* srv, uint64_t ticket, void* dst, void* stream);
+/* Return a finished request's pool memory and forget it (WN_EBUSY while it is on the GPU). */
+WN_API int wn_server_release(wn_server* srv, uint64_t ticket);
+/* Cancel a request that has not been admitted yet (WN_EBUSY otherwise). */
+WN_API int wn_server_cancel(wn_server* srv, uint64_t ticket);
+/* stats (6 doubles): batches launched, most batches on the GPU at once, most requests in one batch,
+ * requests launched, requests admitted and unreleased, free pool bytes. */
+WN_API int wn_server_stats(wn_server* srv, double* stats);
+
 /* ---- allocation-free prediction ------------------------------------------------------------ */
 
 /* The paper has no counterpart to this call; it exists for callers that cannot allocate device memory

@@ -26,7 +26,9 @@ WN_DEVERR_ANTENNA, WN_DEVERR_TIMEOUT, WN_DEVERR_SKY = 0x1, 0x2, 0x4
 
 EXPORTED = ("wn_create", "wn_destroy", "wn_last_error", "wn_version", "wn_set_precision", "wn_device_errors",
             "wn_sky_upload", "wn_sky_free", "wn_sky_bytes", "wn_predict", "wn_peel", "wn_peel_model",
-            "wn_predict_grad", "wn_predict_static")
+            "wn_predict_grad", "wn_predict_static", "wn_server_create", "wn_server_destroy", "wn_server_submit",
+            "wn_server_poll", "wn_server_wait", "wn_server_copy", "wn_server_release", "wn_server_cancel",
+            "wn_server_stats")
 
 
 class WnError(RuntimeError):
@@ -86,8 +88,19 @@ def load(build_if_missing: bool = True):
         L.wn_peel_model.argtypes = [P, ctypes.POINTER(WnObs), P, i, i, P, P, P, P]
         L.wn_predict_grad.argtypes = [P, ctypes.POINTER(WnObs), i, P, i, i, P, P, ctypes.POINTER(WnSkyGrad),
                                       P, P]
+        u64, dbl = ctypes.c_uint64, ctypes.c_double
+        L.wn_server_create.argtypes = [P, i, ctypes.c_size_t, i, i, i, ctypes.POINTER(P)]
+        L.wn_server_destroy.argtypes = [P]
+        L.wn_server_destroy.restype = None
+        L.wn_server_submit.argtypes = [P, ctypes.POINTER(WnObs), i, i, P, i, i, P, ctypes.POINTER(u64)]
+        L.wn_server_poll.argtypes = [P, u64, ctypes.POINTER(i), ctypes.POINTER(P), ctypes.POINTER(dbl)]
+        L.wn_server_wait.argtypes = [P, u64, dbl, ctypes.POINTER(P), ctypes.POINTER(dbl)]
+        L.wn_server_copy.argtypes = [P, u64, P, P]
+        L.wn_server_release.argtypes = [P, u64]
+        L.wn_server_cancel.argtypes = [P, u64]
+        L.wn_server_stats.argtypes = [P, ctypes.POINTER(dbl)]
         for name in EXPORTED:
-            if name not in ("wn_destroy", "wn_last_error", "wn_version"):
+            if name not in ("wn_destroy", "wn_last_error", "wn_version", "wn_server_destroy"):
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L

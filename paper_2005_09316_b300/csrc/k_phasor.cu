@@ -27,21 +27,7 @@ constexpr int K1_THREADS = 32 * K1_WARPS;
 constexpr int K1_CT = 32;      // components per TMA stage
 constexpr int K1_NSTAGE = 4;   // stages in the ring
 
-struct K1Args {
-  const double* uvw;
-  const double* freq;
-  int n_rows, n_chan, n_base;
-  int log2L;          // lanes per row pair = 1 << log2L (4..32)
-  int chan_block;     // channels per CTA column = L * K
-  double nu0;         // log-frequency reference
-  float dnu_h, dnu_l; // channel spacing / c as a float pair (uniform channels)
-  const PGRec* comps;
-  int n_point, n_gauss;
-  float2* out;
-  int mode;
-  PeelArgs peel;
-  unsigned* err;
-};
+
 
 constexpr int K1_FLUSH = 4;     // tiles (128 components) per register partial sum
 
@@ -78,9 +64,10 @@ __device__ __forceinline__ bool bounded_wait(uint64_t* bar, uint32_t parity, uns
   return true;
 }
 
+// One (row tile, channel block) of one observation: the body of the single-launch kernel below and
+// of the batched serving kernel.  Re-entrant: it initialises and invalidates its own barriers.
 template <int K, bool UNIFORM>
-__global__ void __launch_bounds__(K1_THREADS, 2) k1_phasor(const K1Args a) {
-  extern __shared__ __align__(128) unsigned char smem[];
+__device__ __forceinline__ void k1_tile(const K1Args& a, const int bx, const int by, unsigned char* smem) {
   const K1Smem lay = k1_smem_layout(a.log2L, K);
   PGRec* stage = reinterpret_cast<PGRec*>(smem + lay.stage);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + lay.bars);
@@ -91,8 +78,8 @@ __global__ void __launch_bounds__(K1_THREADS, 2) k1_phasor(const K1Args a) {
   const int groups = 32 >> a.log2L;
   const int rpw = 2 * groups;
   const int g = lane >> a.log2L, sub = lane & (L - 1);
-  const int row_w0 = blockIdx.x * (K1_WARPS * rpw) + warp * rpw;
-  const int f0 = blockIdx.y * a.chan_block + sub * K;
+  const int row_w0 = bx * (K1_WARPS * rpw) + warp * rpw;
+  const int f0 = by * a.chan_block + sub * K;
 
   double* uvw_s = reinterpret_cast<double*>(smem + lay.uvw) + warp * rpw * 3;
   float4* rec = reinterpret_cast<float4*>(smem + lay.rec) + warp * K1_CT * rpw;
@@ -281,6 +268,20 @@ __global__ void __launch_bounds__(K1_THREADS, 2) k1_phasor(const K1Args a) {
       }
     }
   }
+  __syncthreads();  // every warp is past its last barrier wait and shared-memory read
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < K1_NSTAGE; ++s) {
+      asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&full[s])) : "memory");
+      asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&empty[s])) : "memory");
+    }
+  }
+  __syncthreads();
+}
+
+template <int K, bool UNIFORM>
+__global__ void __launch_bounds__(K1_THREADS, 2) k1_phasor(const K1Args a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  k1_tile<K, UNIFORM>(a, blockIdx.x, blockIdx.y, smem);
 }
 
 struct K1Choice {
@@ -356,6 +357,70 @@ int launch_phasor_mixed(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* ou
   }
   if (e != cudaSuccess) return set_error(WN_ECUDA, std::string("phasor kernel launch: ") + cudaGetErrorString(e));
   return WN_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Batched persistent form for the serving loop: one launch walks a work table of (request, row
+// tile, channel block) entries of many observations; CTA b takes entries b, b + gridDim.x, ...
+// Every entry runs the same k1_tile code as a single launch, so a request's visibilities are
+// bit-identical whether it is predicted alone or in a batch.
+// ------------------------------------------------------------------------------------------------
+constexpr int K1B_K = 12;  // channels per lane in the batched form
+constexpr int K1B_MIN_LOG2L = 3;
+
+__global__ void __launch_bounds__(K1_THREADS, 2) k1_batched(const K1Args* reqs, const K1Work* work,
+                                                            const int* n_work) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ K1Args args;
+  const int n = *n_work;
+  for (int e = blockIdx.x; e < n; e += gridDim.x) {
+    const K1Work w = work[e];
+    if (threadIdx.x == 0) args = reqs[w.req];
+    __syncthreads();
+    k1_tile<K1B_K, true>(args, w.bx, w.by, smem);
+  }
+}
+
+int k1_batched_smem() { return k1_smem_layout(K1B_MIN_LOG2L, K1B_K).total; }
+
+// Arguments and tile grid of one observation for the batched kernel (uniform channels only).
+int k1_batched_args(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, int mode, const PeelArgs& pa,
+                    K1Args* args, int* grid_x, int* grid_y) {
+  if (!o.uniform) return set_error(WN_EINVAL, "batched prediction needs uniformly spaced channels");
+  int log2L = K1B_MIN_LOG2L;
+  while (log2L < 5 && (K1B_K << log2L) < o.n_chan) ++log2L;
+  K1Args& a = *args;
+  a.uvw = o.uvw;
+  a.freq = o.freq;
+  a.n_rows = o.n_rows;
+  a.n_chan = o.n_chan;
+  a.n_base = o.n_base;
+  a.log2L = log2L;
+  a.chan_block = K1B_K << log2L;
+  a.nu0 = o.nu0;
+  const double dn = o.dnu / kC;
+  a.dnu_h = (float)dn;
+  a.dnu_l = (float)(dn - (double)a.dnu_h);
+  a.comps = M->pg;
+  a.n_point = M->n_point;
+  a.n_gauss = M->n_gauss;
+  a.out = out;
+  a.mode = mode;
+  a.peel = pa;
+  a.err = ctx->d_err;
+  const int rows_per_cta = K1_WARPS * 2 * (32 >> log2L);
+  *grid_x = (o.n_rows + rows_per_cta - 1) / rows_per_cta;
+  *grid_y = (o.n_chan + a.chan_block - 1) / a.chan_block;
+  return WN_OK;
+}
+
+cudaError_t k1_batched_setup() {
+  return cudaFuncSetAttribute(k1_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, k1_batched_smem());
+}
+
+cudaError_t k1_batched_launch(const K1Args* reqs, const K1Work* work, const int* n_work, int grid, cudaStream_t st) {
+  k1_batched<<<grid, K1_THREADS, k1_batched_smem(), st>>>(reqs, work, n_work);
+  return cudaGetLastError();
 }
 
 }  // namespace wn

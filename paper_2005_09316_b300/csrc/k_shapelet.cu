@@ -502,13 +502,10 @@ static int ws_reserve(wn_ctx* ctx, size_t bytes, cudaStream_t st) {
   return WN_OK;
 }
 
-int launch_shapelets(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, int mode, const PeelArgs& pa,
-                     cudaStream_t st) {
+// Shapelet launches with caller-supplied tables: per-channel (n_chan float4) and per-row (n_rows float4).
+int launch_shapelets_ws(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, int mode, const PeelArgs& pa,
+                        float4* chaninfo, float4* rowinfo, cudaStream_t st) {
   if (int r = k2_setup_constants(ctx->device, st)) return r;
-  const size_t chan_bytes = ((size_t)o.n_chan * sizeof(float4) + 255) & ~(size_t)255;
-  if (int r = ws_reserve(ctx, chan_bytes + (size_t)o.n_rows * sizeof(float4), st)) return r;
-  float4* chaninfo = static_cast<float4*>(ctx->ws);
-  float4* rowinfo = reinterpret_cast<float4*>(static_cast<char*>(ctx->ws) + chan_bytes);
   k2_chaninfo<<<(o.n_chan + 255) / 256, 256, 0, st>>>(o.freq, o.n_chan, o.nu0, chaninfo);
   const long long n_vis = (long long)o.n_rows * o.n_chan;
   const int n_tiles = (int)((n_vis + K2_M - 1) / K2_M);
@@ -560,6 +557,15 @@ int launch_shapelets(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, 
   return WN_OK;
 }
 
+int launch_shapelets(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, int mode, const PeelArgs& pa,
+                     cudaStream_t st) {
+  const size_t chan_bytes = ((size_t)o.n_chan * sizeof(float4) + 255) & ~(size_t)255;
+  if (int r = ws_reserve(ctx, chan_bytes + (size_t)o.n_rows * sizeof(float4), st)) return r;
+  float4* chaninfo = static_cast<float4*>(ctx->ws);
+  float4* rowinfo = reinterpret_cast<float4*>(static_cast<char*>(ctx->ws) + chan_bytes);
+  return launch_shapelets_ws(ctx, o, M, out, mode, pa, chaninfo, rowinfo, st);
+}
+
 }  // namespace wn
 
 
@@ -604,57 +610,7 @@ int launch_shapelets_static(wn_ctx* ctx, const ObsDev& o, const Model* M, float2
                                     std::to_string(kStaticScratchEntries) + " entries");
   float4* base = nullptr;
   if (int r = static_scratch_address(ctx->device, &base)) return r;
-  if (int r = k2_setup_constants(ctx->device, st)) return r;
-  float4* chaninfo = base;
-  float4* rowinfo = base + chan_entries;
-  k2_chaninfo<<<(o.n_chan + 255) / 256, 256, 0, st>>>(o.freq, o.n_chan, o.nu0, chaninfo);
-  const long long n_vis = (long long)o.n_rows * o.n_chan;
-  const int n_tiles = (int)((n_vis + K2_M - 1) / K2_M);
-  const int passes = ctx->shape_mode == WN_SHAPE_BF16X1 ? 1 : 3;
-  const double L0 = std::log2(o.nu0);
-  for (int q = 0; q < M->n_shape; ++q) {
-    const ShapeRec& h = M->sh_host[q];
-    k2_rowinfo<<<(o.n_rows + 255) / 256, 256, 0, st>>>(o.uvw, o.n_rows, M->sh + q, o.dec0, rowinfo);
-    K2Args a;
-    a.rowinfo = rowinfo;
-    a.chaninfo = chaninfo;
-    a.bop = M->bop + h.b_off;
-    a.n_pad = h.n_pad;
-    a.nmax = h.nmax;
-    a.passes = passes;
-    a.n_chan = o.n_chan;
-    a.n_base = o.n_base;
-    a.n_tiles = n_tiles;
-    a.n_vis = n_vis;
-    a.c_amp = (float)((double)h.lS + (double)h.alpha * (L0 - h.lref));
-    a.alpha = h.alpha;
-    a.sgn = h.sgn;
-    a.out = out;
-    a.peel = pa;
-    a.err = ctx->d_err;
-    a.mode = q == 0 ? mode : (mode == OUT_STORE ? OUT_ACCUM : (mode == OUT_PEEL ? OUT_SUBG : mode));
-    a.groups = K2_GROUPS;
-    K2Layout lay = k2_layout(h.k_pad, h.n_pad, passes, a.groups);
-    if (lay.total > 227 * 1024) {
-      a.groups = 1;
-      lay = k2_layout(h.k_pad, h.n_pad, passes, 1);
-    }
-    if (lay.total > 227 * 1024) return set_error(WN_EINVAL, "shapelet operand does not fit in shared memory");
-    const int grid = std::min(n_tiles, ctx->num_sms);
-    cudaError_t e;
-    switch (h.k_pad) {
-      case 16: e = k2_launch_t<16>(a, grid, lay.total, st); break;
-      case 32: e = k2_launch_t<32>(a, grid, lay.total, st); break;
-      case 48: e = k2_launch_t<48>(a, grid, lay.total, st); break;
-      case 64: e = k2_launch_t<64>(a, grid, lay.total, st); break;
-      case 80: e = k2_launch_t<80>(a, grid, lay.total, st); break;
-      case 96: e = k2_launch_t<96>(a, grid, lay.total, st); break;
-      case 112: e = k2_launch_t<112>(a, grid, lay.total, st); break;
-      default: e = k2_launch_t<128>(a, grid, lay.total, st); break;
-    }
-    if (e != cudaSuccess) return set_error(WN_ECUDA, std::string("shapelet kernel launch: ") + cudaGetErrorString(e));
-  }
-  return WN_OK;
+  return launch_shapelets_ws(ctx, o, M, out, mode, pa, base, base + chan_entries, st);
 }
 
 }  // namespace wn

@@ -114,6 +114,28 @@ struct PeelArgs {
 
 int set_error(int code, const std::string& msg);
 
+// Arguments of the point/Gaussian phasor kernel for one observation (K1).
+struct K1Args {
+  const double* uvw;
+  const double* freq;
+  int n_rows, n_chan, n_base;
+  int log2L;          // lanes per row pair = 1 << log2L (4..32)
+  int chan_block;     // channels per CTA column = L * K
+  double nu0;         // log-frequency reference
+  float dnu_h, dnu_l; // channel spacing / c as a float pair (uniform channels)
+  const PGRec* comps;
+  int n_point, n_gauss;
+  float2* out;
+  int mode;
+  PeelArgs peel;
+  unsigned* err;
+};
+
+// One work entry of the batched phasor kernel: request index, row tile, channel block.
+struct K1Work {
+  int req, bx, by;
+};
+
 // ---------------------------------------------------------------------------------------------
 // Device helpers
 // ---------------------------------------------------------------------------------------------
@@ -276,4 +298,11 @@ int launch_shapelets_static(wn_ctx* ctx, const ObsDev& o, const Model* M, float2
 size_t static_scratch_entries();
 int launch_grad(wn_ctx* ctx, const ObsDev& o, const Model* M, const PeelArgs& pa, float2* resid,
                 const wn_sky_grad* g, double* loss, cudaStream_t st);
+int k1_batched_smem();
+cudaError_t k1_batched_setup();
+int k1_batched_args(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, int mode, const PeelArgs& pa,
+                    K1Args* args, int* grid_x, int* grid_y);
+cudaError_t k1_batched_launch(const K1Args* reqs, const K1Work* work, const int* n_work, int grid, cudaStream_t st);
+int launch_shapelets_ws(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, int mode, const PeelArgs& pa,
+                        float4* chaninfo, float4* rowinfo, cudaStream_t st);
 }  // namespace wn
