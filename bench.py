@@ -159,6 +159,151 @@ def run_reference(args):
     }), flush=True)
 
 
+def bench_shapelets(wn, ctx, local, P, torch):
+    """Fornax-like peel: two n_max = 80 shapelets (1,500 coefficients each) over the 5 km observation,
+    beside the equivalent 40,000-component point/Gaussian model (the paper's shapelet vs MS CLEAN cost)."""
+    import oracle
+    obs, sky = synth.fornax()
+    d = wn.obs_to_device(obs, f"cuda:{local}")
+    m = ctx.upload(sky)
+    gains_np = synth.make_gains(7, obs.n_ant).astype(np.complex64)
+    gains = torch.as_tensor(gains_np).cuda()
+    shape = (obs.n_time, obs.n_base, obs.n_chan)
+    data = torch.randn(shape, dtype=torch.complex64, device=f"cuda:{local}",
+                       generator=torch.Generator(device=f"cuda:{local}").manual_seed(5))
+    out = torch.empty_like(data)
+
+    def timed(fn, n):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+        e0.record()
+        for _ in range(n):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    ms = timed(lambda: ctx.peel(d, m, gains, data, out=out), 10)
+    nnz = int(sky.s_off[-1])
+    kp, npad = 96, 176
+    flops = 2.0 * obs.n_vis * kp * npad * 3 * sky.n_shape
+    tf = flops / (ms * 1e-3) / 1e12
+    peak = float(P.get("bf16_tflops", 1800.0))
+    rows = np.sort(np.random.default_rng(5).choice(obs.n_rows, size=16, replace=False))
+    V = oracle.predict(synth.sub_obs(obs, rows), obs.freq, obs.dec0, sky)
+    rt, rb = rows // obs.n_base, rows % obs.n_base
+    idx = torch.as_tensor(rows).cuda()
+    dat = data.reshape(obs.n_rows, obs.n_chan)[idx].cpu().numpy()
+    ref = oracle.peel(rt, rb, obs.ant1, obs.ant2, obs.n_ant, gains_np, dat, V)
+    got = out.reshape(obs.n_rows, obs.n_chan)[idx].cpu().numpy()
+    err = float(np.abs(got - ref).max() / np.abs(V).max())
+    m.free()
+    # the equivalent multi-scale-CLEAN-like model on the same observation
+    _, clean = synth.fornax_clean()
+    mc = ctx.upload(clean)
+    ms_clean = timed(lambda: ctx.peel(d, mc, gains, data, out=out), 2)
+    mc.free()
+    return {"workload": "fornax_peel: 128 tiles (5 km) x 14 x 384 ch, 2 shapelets n_max 80, 1500 coeffs each",
+            "ms_per_step": round(ms, 4), "shapelet_vis_per_s": obs.n_vis * sky.n_shape / (ms * 1e-3),
+            "coeff_vis_per_s": nnz * obs.n_vis / (ms * 1e-3),
+            "roofline": {"bound": "tensor", "achieved": round(tf, 2), "peak": peak, "unit": "TFLOP/s",
+                         "frac": round(tf / peak, 4), "traffic": None,
+                         "note": "issued bf16 flops (2 k_pad n_pad x 3 products per visibility); useful 2 nnz"},
+            "error": {"e_norm": err, "tolerance": 1e-3, "sample": "16 rows x 384 ch vs oracle peel"},
+            "clean_model_40k_ms": round(ms_clean, 3), "clean_over_shapelet_time": round(ms_clean / ms, 2)}
+
+
+def bench_adjoint(wn, ctx, local, torch):
+    """Adjoint (loss and every gradient) on 64 tiles x 4 steps x 64 channels, 500 points + 1 shapelet."""
+    obs, sky = synth.adjoint()
+    d = wn.obs_to_device(obs, f"cuda:{local}")
+    m = ctx.upload(sky)
+    gains = torch.as_tensor(synth.make_gains(9, obs.n_ant).astype(np.complex64)).cuda()
+    data = torch.randn((obs.n_time, obs.n_base, obs.n_chan), dtype=torch.complex64, device=f"cuda:{local}",
+                       generator=torch.Generator(device=f"cuda:{local}").manual_seed(9))
+    resid = torch.empty_like(data)
+    for _ in range(3):
+        ctx.predict_grad(d, m, gains, data, resid=resid)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+    e0.record()
+    n = 5
+    for _ in range(n):
+        ctx.predict_grad(d, m, gains, data, resid=resid)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    m.free()
+    return {"workload": "adjoint: 64 tiles (2016 baselines) x 4 x 64 ch, 500 P + 1 S (n_max 40)",
+            "ms_per_step": round(ms, 4), "grad_evals_per_s": obs.n_vis * sky.n_comp / (ms * 1e-3)}
+
+
+def bench_serving(wn, ctx, local, torch, n_req=48, seed=17):
+    """Seeded Poisson stream of predict/peel requests of uneven size (16-128 tiles, 1-14 steps, 32-384
+    channels, 100-50,000 P/G, 0-3 shapelets with n_max 10-80), models resident; the arrival rate is set
+    for ~70% GPU busy from the measured one-at-a-time service time."""
+    from paper_2005_09316_b300.serve import Server, latency_summary, poisson_arrivals, run_stream
+    rng = np.random.default_rng(seed)
+    reqs, models = [], []
+    for i in range(n_req):
+        n_ant = int(round(np.exp(rng.uniform(np.log(16), np.log(128)))))
+        n_time = int(rng.integers(1, 15))
+        n_chan = int(rng.integers(32, 385))
+        n_pg = int(round(np.exp(rng.uniform(np.log(100), np.log(50000)))))
+        n_sh = int(rng.integers(0, 4))
+        obs = synth.make_obs(seed + i, n_ant, n_time, synth.uniform_channels(167e6, 80e3, n_chan), layout="mwa")
+        sky = synth.make_sky(seed + 1000 + i, n_pg * 4 // 5, n_pg - n_pg * 4 // 5, n_sh, fov=20 * synth.DEG,
+                             shape_nmax=rng.integers(10, 81, size=max(n_sh, 1))[:n_sh] if n_sh else 10,
+                             shape_beta=(3 * synth.ARCMIN, 15 * synth.ARCMIN))
+        d = wn.obs_to_device(obs, f"cuda:{local}")
+        m = ctx.upload(sky)
+        models.append(m)
+        gains = data = None
+        if i % 2:
+            gains = torch.as_tensor(synth.make_gains(seed + 2000 + i, n_ant).astype(np.complex64)).cuda()
+            data = torch.randn((n_time, obs.n_base, n_chan), dtype=torch.complex64, device=f"cuda:{local}",
+                               generator=torch.Generator(device=f"cuda:{local}").manual_seed(i))
+        reqs.append((d, m, gains, data))
+    # one-at-a-time service times (each request alone, synchronously)
+    svc = []
+    for d, m, gains, data in reqs:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        (ctx.predict(d, m) if data is None else ctx.peel(d, m, gains, data))
+        torch.cuda.synchronize()
+        svc.append(time.perf_counter() - t0)
+    svc = svc  # first call of each size includes no compilation (kernels are prebuilt)
+    mean_s = float(np.mean(svc))
+    rate = 0.7 / mean_s
+    arrivals = poisson_arrivals(np.random.default_rng(seed), rate, n_req)
+    # one-at-a-time launches at the same arrival times: a FIFO in front of single-request calls
+    lat_serial, t_free = [], 0.0
+    for a, s_ in zip(arrivals, svc):
+        start = max(a, t_free)
+        t_free = start + s_
+        lat_serial.append(t_free - a)
+    max_rows = max(r[0].n_rows for r in reqs)
+    srv = Server(ctx, n_streams=3, pool_bytes=6 << 30, max_inflight=32, max_rows=max_rows, max_chan=384)
+    results, wall = run_stream(srv, reqs, arrivals)
+    st = srv.stats()
+    srv.close()
+    for m in models:
+        m.free()
+    total_evals = sum(r[0].n_vis * r[1].n_comp for r in reqs)
+    lat = latency_summary(results)
+    return {"workload": f"serving: {n_req} Poisson requests, 16-128 tiles, 1-14 steps, 32-384 ch, "
+                        "100-50000 P/G + 0-3 shapelets (n_max 10-80)",
+            "rate_hz": round(rate, 2), "mean_service_ms": round(1e3 * mean_s, 3),
+            "p50_ms": round(lat["p50_ms"], 3), "p99_ms": round(lat["p99_ms"], 3),
+            "one_at_a_time_p50_ms": round(1e3 * float(np.percentile(lat_serial, 50)), 3),
+            "one_at_a_time_p99_ms": round(1e3 * float(np.percentile(lat_serial, 99)), 3),
+            "throughput_evals_per_s": total_evals / wall, "wall_s": round(wall, 3),
+            "batches": st["batches"], "max_batches_in_flight": st["max_batches_in_flight"],
+            "max_batch_requests": st["max_batch_requests"]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -167,6 +312,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-extras", action="store_true", help="skip the shapelet, adjoint and serving reports")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -320,6 +466,15 @@ def main():
         extra["e2e"] = {"value": evals / t_e2e, "unit": UNIT,
                         "h2d_bytes_per_step": int(data_h.numel() * 8 + uvw_h.numel() * 8),
                         "d2h_bytes_per_step": int(res_h.numel() * 8), "ms_per_step": round(t_e2e * 1e3, 3)}
+
+        if not args.no_extras:
+            for key, fn in (("shapelet", lambda: bench_shapelets(wn, ctx, local, P, torch)),
+                            ("adjoint", lambda: bench_adjoint(wn, ctx, local, torch)),
+                            ("serving", lambda: bench_serving(wn, ctx, local, torch))):
+                try:
+                    extra[key] = fn()
+                except Exception as exc:  # an extra report must not hide the headline number
+                    extra[key] = {"error": f"{type(exc).__name__}: {exc}"}
 
         if not args.no_cpu_baseline:
             rate, smp = oracle_rate(obs, sky, args.cpu_seconds)
