@@ -53,18 +53,19 @@ __global__ void __launch_bounds__(K4_WARPS * 32) k4_grad_pg(const K4Args a) {
   if (threadIdx.x < ncomp) comps[threadIdx.x] = a.comps[c0 + threadIdx.x];
   __syncthreads();
 
-  // per-lane channel constants
+  // per-lane channel constants: nu/c as a float pair (one FP64 multiply and split), the rest in FP32
   float ah[KM], al[KM], lam[KM], nuc[KM], wg[KM];
   int fch[KM];
+  const float inv_nu0 = (float)(1.0 / a.nu0);
 #pragma unroll
   for (int k = 0; k < KM; ++k) {
     const int fi = lane + 32 * k;
     fch[k] = fi < a.f_cnt ? a.f_lo + fi : -1;
     const double nu = a.freq[fch[k] >= 0 ? fch[k] : a.f_lo];
-    split_double(nu / kC, ah[k], al[k]);
-    lam[k] = (float)log2(nu / a.nu0);
-    nuc[k] = (float)(nu / kC);
-    wg[k] = (float)(kGaussE * kLog2e * (nu / kC) * (nu / kC));
+    split_double(nu * (1.0 / kC), ah[k], al[k]);
+    lam[k] = log2f((float)nu * inv_nu0);
+    nuc[k] = ah[k];
+    wg[k] = (float)(kGaussE * kLog2e) * nuc[k] * nuc[k];
   }
   const double L0 = log2(a.nu0);
 
@@ -74,6 +75,7 @@ __global__ void __launch_bounds__(K4_WARPS * 32) k4_grad_pg(const K4Args a) {
   const PGRec& me = comps[mine ? lane : 0];
   const bool my_gauss = mine && jc >= a.n_point;
   const double my_n = 1.0 + me.nm1;
+  const float my_ln = (float)(me.l / my_n), my_mn = (float)(me.m / my_n);  // l / n, m / n
   const float my_lnref = (float)((L0 - me.lref) * 0.6931471805599453);  // ln(nu0 / nu_ref)
   const float my_S = mine ? (float)a.flux[jc] : 0.f;
   float my_pa = 0.f, my_maj = 0.f, my_min = 0.f;
@@ -114,10 +116,10 @@ __global__ void __launch_bounds__(K4_WARPS * 32) k4_grad_pg(const K4Args a) {
     float th = 0.f, tl = 0.f, q = 0.f, fl = 0.f, fm = 0.f, fmaj = 0.f, fmin = 0.f, fpa = 0.f;
     if (mine) {
       split_double(fma(u, me.l, fma(v, me.m, w * me.nm1)), th, tl);
-      fl = (float)(-4.0 * kPi * (u - w * me.l / my_n));
-      fm = (float)(-4.0 * kPi * (v - w * me.m / my_n));
+      const float uf = (float)u, vf = (float)v, wf = (float)w;
+      fl = -4.0f * (float)kPi * (uf - wf * my_ln);
+      fm = -4.0f * (float)kPi * (vf - wf * my_mn);
       if (my_gauss) {
-        const float uf = (float)u, vf = (float)v;
         q = me.ga * uf * uf + me.gb * uf * vf + me.gc * vf * vf;
         const float kx = sp * uf + cp * vf, ky = cp * uf - sp * vf;
         fmaj = 4.0f * (float)kGaussE * my_maj * kx * kx;
@@ -214,8 +216,12 @@ __global__ void k4_reduce_pg(const double* partials, int chunks, int n_point, in
 // coefficient gradients sum_vis w phi_a(x) phi_b(y) for the tile (w = Re or Im of conj(W) S P by the
 // parity of a+b) into FP64 shared accumulators.
 // ---------------------------------------------------------------------------------------------
-constexpr int K4S_T = 64;
+constexpr int K4S_T = 128;
 constexpr int K4S_NS = 7;  // flux, alpha, l, m, beta1, beta2, pa
+
+// sqrt(n/2) and sqrt((n+1)/2) (derivative phi_n' = sqrt(n/2) phi_{n-1} - sqrt((n+1)/2) phi_{n+1}) and the
+// recurrence coefficients sqrt(2/(n+1)), sqrt(n/(n+1)), for n <= 128.
+__constant__ float c_dn_lo[kNmaxLimit + 2], c_dn_hi[kNmaxLimit + 2], c_ra[kNmaxLimit + 2], c_rb[kNmaxLimit + 2];
 
 struct K4SArgs {
   const float4* rowinfo;   // per row: (xs, ys, tau hi, tau lo)
@@ -227,6 +233,7 @@ struct K4SArgs {
   const int *n1, *n2;
   const double* coeff;
   double l, m, nm1, lnref_nu0;   // ln(nu0 / nu_ref)
+  float l_over_n, m_over_n, lnref_nu0_f;
   double flux, beta1, beta2, pa;
   float c_amp, alpha, sgn;
   const float2* resid;
@@ -244,7 +251,7 @@ __device__ void hermite_scaled_row(float x, int nmax1, float* out) {
   float scale = __int_as_float(max(0, 127 - E) << 23);
   for (int n = 0; n <= nmax1; ++n) {
     out[n] = p * scale;
-    const float pn = sqrtf(2.0f / (n + 1)) * x * p - sqrtf((float)n / (n + 1)) * p_prev;
+    const float pn = c_ra[n] * x * p - c_rb[n] * p_prev;
     p_prev = p;
     p = pn;
     if (fabsf(p) > 1.8446744e19f) {
@@ -266,6 +273,8 @@ __global__ void __launch_bounds__(K4S_T) k4_grad_shape(const K4SArgs a) {
   double* accc = reinterpret_cast<double*>(wim + K4S_T + (K4S_T & 1));
   for (int k = threadIdx.x; k < a.nnz; k += K4S_T) accc[k] = 0.0;
   double accs[K4S_NS] = {0, 0, 0, 0, 0, 0, 0};
+  float acc32[K4S_NS] = {0, 0, 0, 0, 0, 0, 0};
+  int nacc = 0;
   const int t = threadIdx.x;
   const long long n_tiles = (a.n_vis + K4S_T - 1) / K4S_T;
   for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
@@ -301,8 +310,8 @@ __global__ void __launch_bounds__(K4S_T) k4_grad_shape(const K4SArgs a) {
       const int na = __ldg(a.n1 + k), nb = __ldg(a.n2 + k);
       const float c = (float)__ldg(a.coeff + k);
       const float fa = px[na], fb = py[nb];
-      const float dxa = (na > 0 ? sqrtf(0.5f * na) * px[na - 1] : 0.f) - sqrtf(0.5f * (na + 1)) * px[na + 1];
-      const float dyb = (nb > 0 ? sqrtf(0.5f * nb) * py[nb - 1] : 0.f) - sqrtf(0.5f * (nb + 1)) * py[nb + 1];
+      const float dxa = (na > 0 ? c_dn_lo[na] * px[na - 1] : 0.f) - c_dn_hi[na] * px[na + 1];
+      const float dyb = (nb > 0 ? c_dn_lo[nb] * py[nb - 1] : 0.f) - c_dn_hi[nb] * py[nb + 1];
       const float e0 = c * fa * fb;
       const float e1 = c * dxa * fb;                       // times x / beta1 below
       const float e2 = c * fa * dyb;                       // times y / beta2 below
@@ -319,18 +328,26 @@ __global__ void __launch_bounds__(K4S_T) k4_grad_shape(const K4SArgs a) {
       d1r *= fx; d1i *= fx;
       d2r *= fy; d2i *= fy;
       // Re(Y * (pr + i pi)) = yr pr - yi pi
-      const float re_xi = yr * xr - yi * xi;          // Re(conj(W) V)
-      const float im_xi = yr * xi + yi * xr;          // Im(conj(W) V)
-      const double nu = ci.w;
-      const double u = a.uvw[3 * (size_t)row], v = a.uvw[3 * (size_t)row + 1], w = a.uvw[3 * (size_t)row + 2];
-      const double n = 1.0 + a.nm1;
-      accs[0] += -2.0 * re_xi;
-      accs[1] += -2.0 * a.flux * re_xi * ((double)ci.z * 0.6931471805599453 + a.lnref_nu0);
-      accs[2] += -4.0 * kPi * a.flux * (nu / kC) * (u - w * a.l / n) * im_xi;
-      accs[3] += -4.0 * kPi * a.flux * (nu / kC) * (v - w * a.m / n) * im_xi;
-      accs[4] += -2.0 * a.flux * (yr * d1r - yi * d1i);
-      accs[5] += -2.0 * a.flux * (yr * d2r - yi * d2i);
-      accs[6] += -2.0 * a.flux * (yr * dpr - yi * dpi);
+      const float re_xi = yr * xr - yi * xi;          // Re(conj(W) V) / S_ref
+      const float im_xi = yr * xi + yi * xr;          // Im(conj(W) V) / S_ref
+      const float nuc = ci.x;                          // nu / c
+      const float u = __ldg(a.uvw + 3 * (size_t)row), v = __ldg(a.uvw + 3 * (size_t)row + 1),
+                  w = __ldg(a.uvw + 3 * (size_t)row + 2);
+      acc32[0] += -2.0f * re_xi;
+      acc32[1] += -2.0f * re_xi * fmaf(ci.z, 0.6931471805599453f, a.lnref_nu0_f);
+      acc32[2] += -4.0f * (float)kPi * nuc * (u - w * a.l_over_n) * im_xi;
+      acc32[3] += -4.0f * (float)kPi * nuc * (v - w * a.m_over_n) * im_xi;
+      acc32[4] += -2.0f * (yr * d1r - yi * d1i);
+      acc32[5] += -2.0f * (yr * d2r - yi * d2i);
+      acc32[6] += -2.0f * (yr * dpr - yi * dpi);
+    }
+    if (++nacc == 16) {
+#pragma unroll
+      for (int i = 0; i < K4S_NS; ++i) {
+        accs[i] += (double)acc32[i];
+        acc32[i] = 0.f;
+      }
+      nacc = 0;
     }
     __syncthreads();
     // coefficient gradients for this tile
@@ -342,14 +359,14 @@ __global__ void __launch_bounds__(K4S_T) k4_grad_shape(const K4SArgs a) {
       float s = 0.f;
       for (int vv = 0; vv < nv; ++vv) s = fmaf(wsel[vv] * phx[vv * ld + na], phy[vv * ld + nb], s);
       // -2 Re(Y s_k) phi phi with s_k = 1, -i, -1, i: Re(Y) , Im(Y), -Re(Y), -Im(Y)
-      accc[k] += (ph >= 2 ? 2.0 : -2.0) * a.flux * (double)s;
+      accc[k] += (double)((ph >= 2 ? 2.0f : -2.0f) * s);
     }
     __syncthreads();
   }
-  // per-CTA partials
-  for (int k = t; k < a.nnz; k += K4S_T) a.part_c[(size_t)blockIdx.x * a.nnz + k] = accc[k];
+  // per-CTA partials (the flux factor of every group but the flux one is applied here, in FP64)
+  for (int k = t; k < a.nnz; k += K4S_T) a.part_c[(size_t)blockIdx.x * a.nnz + k] = accc[k] * a.flux;
   __shared__ double red[K4S_T][K4S_NS];
-  for (int i = 0; i < K4S_NS; ++i) red[t][i] = accs[i];
+  for (int i = 0; i < K4S_NS; ++i) red[t][i] = (accs[i] + (double)acc32[i]) * (i == 0 ? 1.0 : a.flux);
   __syncthreads();
   if (t < K4S_NS) {
     double s = 0.0;
@@ -428,8 +445,29 @@ static int cuda_err(const char* what) {
 
 int run_model_peel(wn_ctx* ctx, const ObsDev& d, const Model* M, float2* out, const PeelArgs& pa, cudaStream_t st);
 
+static int g_grad_consts[64] = {0};
+
+static int grad_constants(int device, cudaStream_t st) {
+  if (device >= 0 && device < 64 && g_grad_consts[device]) return WN_OK;
+  float lo[kNmaxLimit + 2], hi[kNmaxLimit + 2], ra[kNmaxLimit + 2], rb[kNmaxLimit + 2];
+  for (int n = 0; n <= kNmaxLimit + 1; ++n) {
+    lo[n] = (float)std::sqrt(0.5 * n);
+    hi[n] = (float)std::sqrt(0.5 * (n + 1));
+    ra[n] = (float)std::sqrt(2.0 / (n + 1));
+    rb[n] = (float)std::sqrt((double)n / (n + 1));
+  }
+  cudaError_t e = cudaMemcpyToSymbolAsync(c_dn_lo, lo, sizeof(lo), 0, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_dn_hi, hi, sizeof(hi), 0, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_ra, ra, sizeof(ra), 0, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_rb, rb, sizeof(rb), 0, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return set_error(WN_ECUDA, std::string("adjoint constants: ") + cudaGetErrorString(e));
+  if (device >= 0 && device < 64) g_grad_consts[device] = 1;
+  return WN_OK;
+}
+
 int launch_grad(wn_ctx* ctx, const ObsDev& o, const Model* M, const PeelArgs& pa, float2* resid,
                 const wn_sky_grad* g, double* loss, cudaStream_t st) {
+  if (int r = grad_constants(ctx->device, st)) return r;
   // 1. forward: resid = data - G V
   if (int r = run_model_peel(ctx, o, M, resid, pa, st)) return r;
   // workspace: loss partials, point/Gaussian partials, shapelet tables and partials
@@ -444,7 +482,7 @@ int launch_grad(wn_ctx* ctx, const ObsDev& o, const Model* M, const PeelArgs& pa
   const int rows_per_chunk = (o.n_rows + chunks - 1) / chunks;
   int max_nnz = 0;
   for (int q = 0; q < M->n_shape; ++q) max_nnz = std::max(max_nnz, M->s_off_host[q + 1] - M->s_off_host[q]);
-  const int sgrid = ctx->num_sms * 2;
+  const int sgrid = ctx->num_sms * 8;
   const size_t chan_bytes = ((size_t)o.n_chan * sizeof(float4) + 255) & ~(size_t)255;
   const size_t row_bytes = ((size_t)o.n_rows * sizeof(float4) + 255) & ~(size_t)255;
   const size_t loss_bytes = ((size_t)loss_blocks * 8 + 255) & ~(size_t)255;
@@ -537,6 +575,9 @@ int launch_grad(wn_ctx* ctx, const ObsDev& o, const Model* M, const PeelArgs& pa
     a.m = h.m;
     a.nm1 = h.nm1;
     a.lnref_nu0 = (L0 - h.lref) * 0.6931471805599453;
+    a.lnref_nu0_f = (float)a.lnref_nu0;
+    a.l_over_n = (float)(h.l / (1.0 + h.nm1));
+    a.m_over_n = (float)(h.m / (1.0 + h.nm1));
     a.c_amp = (float)((double)h.alpha * (L0 - h.lref));  // flux-free
     a.alpha = h.alpha;
     a.sgn = h.sgn;

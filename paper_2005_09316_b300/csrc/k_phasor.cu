@@ -117,20 +117,21 @@ __device__ __forceinline__ void k1_tile(const K1Args& a, const int bx, const int
     }
   }
 
-  // Per-lane channel constants.
+  // Per-lane channel constants: nu/c as float pairs (an FP64 multiply and split), the rest in FP32.
   float lam[K], wg[K];
   float ah[UNIFORM ? 1 : K], al[UNIFORM ? 1 : K];
+  const float inv_nu0 = (float)(1.0 / a.nu0);
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    int f = min(f0 + k, a.n_chan - 1);
-    double nu = a.freq[f];
-    lam[k] = (float)log2(nu / a.nu0);
-    double x = nu / kC;
-    wg[k] = (float)(kGaussE * kLog2e * x * x);
-    if (!UNIFORM) split_double(x, ah[k], al[k]);
+    const int f = min(f0 + k, a.n_chan - 1);
+    const double nu = a.freq[f];
+    lam[k] = log2f((float)nu * inv_nu0);
+    const float x = (float)(nu * (1.0 / kC));
+    wg[k] = (float)(kGaussE * kLog2e) * x * x;
+    if (!UNIFORM) split_double(nu * (1.0 / kC), ah[k], al[k]);
   }
   float a0h, a0l;
-  split_double(a.freq[min(f0, a.n_chan - 1)] / kC, a0h, a0l);
+  split_double(a.freq[min(f0, a.n_chan - 1)] * (1.0 / kC), a0h, a0l);
   const double L0 = log2(a.nu0);
 
   float2 V0[K], V1[K];
@@ -365,7 +366,7 @@ int launch_phasor_mixed(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* ou
 // Every entry runs the same k1_tile code as a single launch, so a request's visibilities are
 // bit-identical whether it is predicted alone or in a batch.
 // ------------------------------------------------------------------------------------------------
-constexpr int K1B_K = 12;  // channels per lane in the batched form
+constexpr int K1B_KMAX = 12;  // channels per lane in the batched form: 8 or 12, chosen per request
 constexpr int K1B_MIN_LOG2L = 3;
 
 __global__ void __launch_bounds__(K1_THREADS, 2) k1_batched(const K1Args* reqs, const K1Work* work,
@@ -377,18 +378,29 @@ __global__ void __launch_bounds__(K1_THREADS, 2) k1_batched(const K1Args* reqs, 
     const K1Work w = work[e];
     if (threadIdx.x == 0) args = reqs[w.req];
     __syncthreads();
-    k1_tile<K1B_K, true>(args, w.bx, w.by, smem);
+    if (args.chan_block == (12 << args.log2L)) k1_tile<12, true>(args, w.bx, w.by, smem);
+    else k1_tile<8, true>(args, w.bx, w.by, smem);
   }
 }
 
-int k1_batched_smem() { return k1_smem_layout(K1B_MIN_LOG2L, K1B_K).total; }
+int k1_batched_smem() { return k1_smem_layout(K1B_MIN_LOG2L, K1B_KMAX).total; }
 
 // Arguments and tile grid of one observation for the batched kernel (uniform channels only).
 int k1_batched_args(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, int mode, const PeelArgs& pa,
                     K1Args* args, int* grid_x, int* grid_y) {
   if (!o.uniform) return set_error(WN_EINVAL, "batched prediction needs uniformly spaced channels");
-  int log2L = K1B_MIN_LOG2L;
-  while (log2L < 5 && (K1B_K << log2L) < o.n_chan) ++log2L;
+  // fewest padded channel slots over K in {12, 8} and L in {8, 16, 32}; ties go to the wider block
+  int log2L = 5, K = 12;
+  long best = -1;
+  for (int li = K1B_MIN_LOG2L; li <= 5; ++li)
+    for (int kk : {12, 8}) {
+      const long cb = (long)kk << li, slots = ((o.n_chan + cb - 1) / cb) * cb;
+      if (best < 0 || slots < best || (slots == best && cb > ((long)K << log2L))) {
+        best = slots;
+        log2L = li;
+        K = kk;
+      }
+    }
   K1Args& a = *args;
   a.uvw = o.uvw;
   a.freq = o.freq;
@@ -396,7 +408,7 @@ int k1_batched_args(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, i
   a.n_chan = o.n_chan;
   a.n_base = o.n_base;
   a.log2L = log2L;
-  a.chan_block = K1B_K << log2L;
+  a.chan_block = K << log2L;
   a.nu0 = o.nu0;
   const double dn = o.dnu / kC;
   a.dnu_h = (float)dn;
