@@ -4,13 +4,16 @@
 //  * admission by memory: each request's output visibilities are carved from one device pool
 //    (first fit); a request waits until a slot (max_inflight) and pool space are free, and one that
 //    can never fit is refused at submit (WN_EBUSY);
-//  * batching: all admitted requests that are not yet running are packed into one work table of
+//  * batching: admitted requests that are not yet running are packed into one work table of
 //    (request, row tile, channel block) entries and run by the persistent batched phasor kernel,
 //    replayed from a CUDA graph captured once per stream; shapelet components follow per request on
 //    the same stream, with that stream's own tables;
 //  * overlap: there are n_streams batch slots; requests that arrive while batches are on the GPU are
 //    admitted as memory and slots free up and go out in the next batch on a free stream, so their
 //    work overlaps the batches in flight;
+//  * time slicing: a batch carries at most ~kBatchBudget of estimated GPU work; a request larger than
+//    that takes a low-priority stream of its own and is issued there chunk by chunk (its shapelets with
+//    the last chunk), so small requests keep flowing on the other streams between its chunks;
 //  * completion: an event per batch, polled without blocking; the caller reads the result in place
 //    and releases it, which returns its pool space.
 // Every tile is computed by the same code in the same order as a single-request launch, so a request's
@@ -28,8 +31,16 @@ namespace wn {
 
 enum ReqState { RQ_PENDING = 0, RQ_ADMITTED = 1, RQ_RUNNING = 2, RQ_DONE = 3, RQ_CANCELLED = 4, RQ_FAILED = 5 };
 
+constexpr double kBatchBudget = 0.02;   // seconds of estimated GPU work per batch / chunk
+constexpr double kEvalRate = 3.0e12;    // component-visibility evaluations per second (estimate)
+
 struct ServeReq {
   uint64_t ticket = 0;
+  K1Args k1;              // batched-kernel arguments (set at admission)
+  int gx = 0, gy = 0;     // tile grid of the phasor kernel
+  long tiles = 0, issued = 0;
+  double tile_cost = 0;   // estimated seconds per tile
+  int owner_slot = -1;    // slot that issues a large request's chunks
   ObsDev od;
   const Model* M = nullptr;
   int mode = OUT_STORE;
@@ -50,8 +61,11 @@ struct ServeSlot {
   char* h_table = nullptr;  // pinned copy written before each replay
   float4* chaninfo = nullptr;
   float4* rowinfo = nullptr;
-  std::vector<uint64_t> reqs;
+  std::vector<uint64_t> reqs;     // requests that complete with this slot's current launch
   bool busy = false;
+  int priority = 0;                // CUDA stream priority (lower number runs first)
+  uint64_t owner = 0;              // large request whose chunks this slot issues (0: none)
+  bool chunk_next = true;          // an owning slot's next launch: a chunk (else a small batch)
 };
 
 }  // namespace wn
@@ -117,52 +131,19 @@ static void pool_free(wn_server* s, size_t off, size_t bytes) {
 
 static size_t round_bytes(size_t b) { return (b + 255) & ~(size_t)255; }
 
-// Build one batch from admitted requests and launch it on slot `k`. Called with the lock held.
-static void launch_batch(wn_server* s, int k) {
+static bool has_pg(const ServeReq& r) { return r.M->n_point + r.M->n_gauss > 0 || r.M->n_shape == 0; }
+
+// Launch on slot k the work table in the slot's pinned staging (nwork entries), the shapelets of the
+// requests in `shapes`, and the completion event that completes the requests in `complete`.  Called
+// with the lock held.
+static void launch_slot(wn_server* s, int k, int nwork, const std::vector<uint64_t>& complete,
+                        const std::vector<uint64_t>& shapes) {
   ServeSlot& sl = s->slots[k];
-  int* n_work = reinterpret_cast<int*>(sl.h_table);
-  K1Args* args = reinterpret_cast<K1Args*>(sl.h_table + 16);
-  K1Work* work = reinterpret_cast<K1Work*>(sl.h_table + 16 + sizeof(K1Args) * s->max_reqs);
-  int nreq = 0, nwork = 0;
-  sl.reqs.clear();
-  std::vector<uint64_t> shapes;
-  for (auto& kv : s->reqs) {
-    ServeReq& r = kv.second;
-    if (r.state != RQ_ADMITTED) continue;
-    if (nreq == s->max_reqs) break;
-    float2* out = reinterpret_cast<float2*>(s->pool + r.off);
-    const bool pg = r.M->n_point + r.M->n_gauss > 0 || r.M->n_shape == 0;
-    if (pg) {
-      int gx = 0, gy = 0;
-      if (k1_batched_args(s->ctx, r.od, r.M, out, r.mode, r.pa, &args[nreq], &gx, &gy) != WN_OK) {
-        r.state = RQ_FAILED;
-        r.error = WN_EINVAL;
-        continue;
-      }
-      if (nwork + gx * gy > s->max_work) {
-        if (nwork == 0) {  // larger than any batch: refuse rather than stall the queue
-          r.state = RQ_FAILED;
-          r.error = WN_EBUSY;
-        }
-        continue;
-      }
-      for (int y = 0; y < gy; ++y)
-        for (int x = 0; x < gx; ++x) work[nwork++] = K1Work{nreq, x, y};
-      ++nreq;
-    }
-    r.state = RQ_RUNNING;
-    r.batch = s->batches;
-    r.t_launch = now_s(s);
-    sl.reqs.push_back(r.ticket);
-    if (r.M->n_shape > 0) shapes.push_back(r.ticket);
-  }
-  if (sl.reqs.empty()) return;
-  *n_work = nwork;
+  *reinterpret_cast<int*>(sl.h_table) = nwork;
   cudaError_t e = cudaGraphLaunch(sl.gexec, sl.st);  // copies the table, then the batched kernel
   for (uint64_t t : shapes) {
     ServeReq& r = s->reqs[t];
-    const bool pg = r.M->n_point + r.M->n_gauss > 0;
-    const int smode = pg ? (r.mode == OUT_PEEL ? OUT_SUBG : OUT_ACCUM) : r.mode;
+    const int smode = r.M->n_point + r.M->n_gauss > 0 ? (r.mode == OUT_PEEL ? OUT_SUBG : OUT_ACCUM) : r.mode;
     if (launch_shapelets_ws(s->ctx, r.od, r.M, reinterpret_cast<float2*>(s->pool + r.off), smode, r.pa, sl.chaninfo,
                             sl.rowinfo, sl.st) != WN_OK) {
       r.state = RQ_FAILED;
@@ -170,19 +151,135 @@ static void launch_batch(wn_server* s, int k) {
     }
   }
   if (e == cudaSuccess) e = cudaEventRecord(sl.done, sl.st);
-  if (e != cudaSuccess) {
+  sl.reqs = complete;
+  if (e != cudaSuccess)
     for (uint64_t t : sl.reqs) {
       s->reqs[t].state = RQ_FAILED;
       s->reqs[t].error = WN_ECUDA;
     }
-  }
   sl.busy = true;
   s->batches++;
-  s->launched += (int)sl.reqs.size();
-  s->max_batch_reqs = std::max(s->max_batch_reqs, (int)sl.reqs.size());
+  s->launched += (int)complete.size();
+  s->max_batch_reqs = std::max(s->max_batch_reqs, (int)complete.size());
   int running = 0;
   for (auto& x : s->slots) running += x.busy ? 1 : 0;
   s->max_running_batches = std::max(s->max_running_batches, running);
+}
+
+// Append tiles [from, to) of request r (table entry index `slot_req`) to the work list.
+static int add_tiles(ServeReq& r, int slot_req, long from, long to, K1Work* work, int nwork) {
+  for (long t = from; t < to; ++t) work[nwork++] = K1Work{slot_req, (int)(t % r.gx), (int)(t / r.gx)};
+  return nwork;
+}
+
+static bool is_large(const ServeReq& r) { return r.tiles > 0 && r.tile_cost * r.tiles > kBatchBudget; }
+
+// An admitted request that no launch has taken yet.
+static bool unstarted(const ServeReq& r) { return r.state == RQ_ADMITTED && r.issued == 0 && r.owner_slot < 0; }
+
+static bool small_waiting(wn_server* s) {
+  for (auto& kv : s->reqs)
+    if (unstarted(kv.second) && !is_large(kv.second)) return true;
+  return false;
+}
+
+static K1Args* slot_args(wn_server* s, ServeSlot& sl) { return reinterpret_cast<K1Args*>(sl.h_table + 16); }
+static K1Work* slot_work(wn_server* s, ServeSlot& sl) {
+  return reinterpret_cast<K1Work*>(sl.h_table + 16 + sizeof(K1Args) * s->max_reqs);
+}
+
+// Launch on slot k the next ~kBatchBudget of tiles of the large request the slot owns; the last chunk
+// carries the request's shapelets and completes it.  Called with the lock held.
+static void launch_chunk(wn_server* s, int k) {
+  ServeSlot& sl = s->slots[k];
+  ServeReq& r = s->reqs[sl.owner];
+  std::vector<uint64_t> complete, shapes;
+  const long per = std::max(1L, std::min((long)s->max_work, (long)(kBatchBudget / std::max(r.tile_cost, 1e-12))));
+  const long to = std::min(r.tiles, r.issued + per);
+  slot_args(s, sl)[0] = r.k1;
+  const int nwork = add_tiles(r, 0, r.issued, to, slot_work(s, sl), 0);
+  r.issued = to;
+  if (r.issued == r.tiles) {
+    r.state = RQ_RUNNING;
+    r.batch = s->batches;
+    r.owner_slot = -1;
+    sl.owner = 0;
+    complete.push_back(r.ticket);
+    if (r.M->n_shape > 0) shapes.push_back(r.ticket);
+  }
+  launch_slot(s, k, nwork, complete, shapes);
+}
+
+// Launch on slot k one batch of small unstarted requests, in ticket order, up to kBatchBudget of
+// estimated work (the first always goes).  Called with the lock held.
+static void launch_small(wn_server* s, int k) {
+  ServeSlot& sl = s->slots[k];
+  K1Args* args = slot_args(s, sl);
+  K1Work* work = slot_work(s, sl);
+  std::vector<uint64_t> complete, shapes;
+  int nreq = 0, nwork = 0;
+  double budget = kBatchBudget;
+  for (auto& kv : s->reqs) {
+    ServeReq& r = kv.second;
+    if (!unstarted(r) || is_large(r)) continue;
+    const double cost = r.tile_cost * r.tiles;
+    if (nreq == s->max_reqs || (!complete.empty() && (cost > budget || nwork + r.tiles > s->max_work))) continue;
+    if (r.tiles > 0) {
+      args[nreq] = r.k1;
+      nwork = add_tiles(r, nreq, 0, r.tiles, work, nwork);
+      ++nreq;
+    }
+    budget -= cost;
+    r.issued = std::max(1L, r.tiles);
+    r.state = RQ_RUNNING;
+    r.batch = s->batches;
+    r.t_launch = now_s(s);
+    complete.push_back(r.ticket);
+    if (r.M->n_shape > 0) shapes.push_back(r.ticket);
+  }
+  if (!complete.empty()) launch_slot(s, k, nwork, complete, shapes);
+}
+
+// Fill the free slots.  Large requests claim the lowest-priority free slots (all but one, so small
+// requests always have a stream); small batches take the highest-priority free ones; a slot that owns a
+// large request alternates between its chunks and small batches while small requests wait.
+static bool launch_ready(wn_server* s) {
+  bool progress = false;
+  const int ns = (int)s->slots.size();
+  int owners = 0;
+  for (auto& sl : s->slots) owners += sl.owner ? 1 : 0;
+  for (auto& kv : s->reqs) {
+    ServeReq& r = kv.second;
+    if (!unstarted(r) || !is_large(r)) continue;
+    if (owners >= std::max(1, ns - 1)) break;
+    int k = ns - 1;
+    while (k >= 0 && (s->slots[k].busy || s->slots[k].owner)) --k;
+    if (k < 0) break;
+    r.owner_slot = k;
+    r.t_launch = now_s(s);
+    s->slots[k].owner = r.ticket;
+    s->slots[k].chunk_next = true;
+    ++owners;
+  }
+  for (int k = 0; k < ns; ++k) {
+    ServeSlot& sl = s->slots[k];
+    if (sl.busy || sl.owner || !small_waiting(s)) continue;
+    launch_small(s, k);
+    progress = true;
+  }
+  for (int k = 0; k < ns; ++k) {
+    ServeSlot& sl = s->slots[k];
+    if (sl.busy || !sl.owner) continue;
+    if (!sl.chunk_next && small_waiting(s)) {
+      launch_small(s, k);
+      sl.chunk_next = true;
+    } else {
+      launch_chunk(s, k);
+      sl.chunk_next = false;
+    }
+    progress = true;
+  }
+  return progress;
 }
 
 static void scheduler(wn_server* s) {
@@ -221,6 +318,18 @@ static void scheduler(wn_server* s) {
         r.off = off;
         r.has_mem = true;
         r.state = RQ_ADMITTED;
+        r.tiles = 0;
+        if (has_pg(r)) {
+          if (k1_batched_args(s->ctx, r.od, r.M, reinterpret_cast<float2*>(s->pool + off), r.mode, r.pa, &r.k1, &r.gx,
+                              &r.gy) != WN_OK) {
+            r.state = RQ_FAILED;
+            r.error = WN_EINVAL;
+          } else {
+            r.tiles = (long)r.gx * r.gy;
+            const double rows_tile = (double)r.od.n_rows / r.gx, chans_tile = (double)r.od.n_chan / r.gy;
+            r.tile_cost = rows_tile * chans_tile * (r.M->n_point + r.M->n_gauss) / kEvalRate;
+          }
+        }
         r.t_admit = now_s(s);
         s->admitted++;
         it = s->queue.erase(it);
@@ -229,21 +338,7 @@ static void scheduler(wn_server* s) {
         ++it;
       }
     }
-    // launch admitted work on a free stream
-    bool have = false;
-    for (auto& kv : s->reqs)
-      if (kv.second.state == RQ_ADMITTED) {
-        have = true;
-        break;
-      }
-    if (have) {
-      for (int k = 0; k < (int)s->slots.size(); ++k)
-        if (!s->slots[k].busy) {
-          launch_batch(s, k);
-          progress = true;
-          break;
-        }
-    }
+    progress |= launch_ready(s);
     if (progress) s->cv.notify_all();
     s->cv.wait_for(lk, std::chrono::microseconds(progress ? 0 : 20));
   }
@@ -280,8 +375,13 @@ int wn_server_create(wn_ctx* ctx, int n_streams, size_t pool_bytes, int max_infl
   const size_t chan_bytes = round_bytes((size_t)max_chan * sizeof(float4));
   const int grid = ctx->num_sms * 2;
   s->slots.resize(n_streams);
-  for (auto& sl : s->slots) {
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking);
+  int prio_least = 0, prio_greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+  for (size_t k = 0; k < s->slots.size(); ++k) {
+    auto& sl = s->slots[k];
+    // slot 0 has the highest priority, later slots lower ones (clamped to the device's range)
+    sl.priority = std::min(prio_least, prio_greatest + (int)k);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&sl.st, cudaStreamNonBlocking, sl.priority);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc(&sl.d_table, s->table_bytes);
     if (e == cudaSuccess) e = cudaHostAlloc(&sl.h_table, s->table_bytes, cudaHostAllocDefault);

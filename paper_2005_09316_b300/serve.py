@@ -119,18 +119,38 @@ def latency_summary(results) -> dict:
 
 
 def run_stream(server: Server, requests, arrivals, release=True, timeout=120.0):
-    """Submit `requests` ((obs, model, gains, data) tuples) at the given arrival times (seconds from now),
-    collect every result; returns (results, wall seconds)."""
+    """Submit `requests` ((obs, model, gains, data) tuples) at the given arrival times (seconds from now)
+    while a consumer thread collects (and releases) each result as it completes; returns
+    (results in submission order, wall seconds)."""
+    import queue
+    import threading
+
     t0 = time.perf_counter()
-    tickets = []
-    for (obs, model, gains, data), ta in zip(requests, arrivals):
+    pending = queue.Queue()
+    results = {}
+    errors = []
+
+    def consume():
+        while True:
+            item = pending.get()
+            if item is None:
+                return
+            i, t = item
+            try:
+                results[i] = server.wait(t, timeout)
+                if release:
+                    server.release(t)
+            except Exception as exc:  # surfaced after the join
+                errors.append(exc)
+
+    th = threading.Thread(target=consume, daemon=True)
+    th.start()
+    for i, ((obs, model, gains, data), ta) in enumerate(zip(requests, arrivals)):
         while time.perf_counter() - t0 < ta:
             time.sleep(min(2e-4, max(0.0, ta - (time.perf_counter() - t0))))
-        tickets.append(server.submit(obs, model, gains, data))
-    results = []
-    for t in tickets:
-        r = server.wait(t, timeout)
-        results.append(r)
-        if release:
-            server.release(t)
-    return results, time.perf_counter() - t0
+        pending.put((i, server.submit(obs, model, gains, data)))
+    pending.put(None)
+    th.join()
+    if errors:
+        raise errors[0]
+    return [results[i] for i in range(len(requests))], time.perf_counter() - t0
