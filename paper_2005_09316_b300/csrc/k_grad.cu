@@ -74,8 +74,9 @@ __global__ void __launch_bounds__(K4_WARPS * 32) k4_grad_pg(const K4Args a) {
   const int jc = c0 + (mine ? lane : 0);
   const PGRec& me = comps[mine ? lane : 0];
   const bool my_gauss = mine && jc >= a.n_point;
-  const double my_n = 1.0 + me.nm1;
-  const float my_ln = (float)(me.l / my_n), my_mn = (float)(me.m / my_n);  // l / n, m / n
+  const double me_l = (double)me.lh + me.ll, me_m = (double)me.mh + me.ml, me_nm1 = (double)me.nh + me.nl;
+  const double my_n = 1.0 + me_nm1;
+  const float my_ln = (float)(me_l / my_n), my_mn = (float)(me_m / my_n);  // l / n, m / n
   const float my_lnref = (float)((L0 - me.lref) * 0.6931471805599453);  // ln(nu0 / nu_ref)
   const float my_S = mine ? (float)a.flux[jc] : 0.f;
   float my_pa = 0.f, my_maj = 0.f, my_min = 0.f;
@@ -115,7 +116,7 @@ __global__ void __launch_bounds__(K4_WARPS * 32) k4_grad_pg(const K4Args a) {
     // this lane's component: phase argument (FP64), Gaussian form and the per-row factors
     float th = 0.f, tl = 0.f, q = 0.f, fl = 0.f, fm = 0.f, fmaj = 0.f, fmin = 0.f, fpa = 0.f;
     if (mine) {
-      split_double(fma(u, me.l, fma(v, me.m, w * me.nm1)), th, tl);
+      split_double(fma(u, me_l, fma(v, me_m, w * me_nm1)), th, tl);
       const float uf = (float)u, vf = (float)v, wf = (float)w;
       fl = -4.0f * (float)kPi * (uf - wf * my_ln);
       fm = -4.0f * (float)kPi * (vf - wf * my_mn);

@@ -16,9 +16,9 @@ __global__ void k_pack_pg(wn_sky s, PGRec* out, unsigned* err) {
   double flux = s.flux[j], nuref = s.nu_ref[j];
   PGRec r;
   bool bad = !(r2 < 1.0) || !(nuref > 0.0) || !isfinite(flux) || !isfinite(s.alpha[j]);
-  r.l = l;
-  r.m = m;
-  r.nm1 = bad ? 0.0 : -r2 / (1.0 + sqrt(1.0 - r2));
+  split_double(l, r.lh, r.ll);
+  split_double(m, r.mh, r.ml);
+  split_double(bad ? 0.0 : -r2 / (1.0 + sqrt(1.0 - r2)), r.nh, r.nl);
   r.lref = bad ? 0.0 : log2(nuref);
   r.lS = flux == 0.0 ? 0.0f : (float)log2(fabs(flux));
   r.alpha = (float)s.alpha[j];

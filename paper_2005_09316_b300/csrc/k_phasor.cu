@@ -8,10 +8,11 @@
 //    the CTA streams the whole component table through shared memory (TMA bulk copies into a ring
 //    of stages, mbarrier-synchronised), then writes each visibility once (predict, accumulate or
 //    the fused peel R = D - g1 conj(g2) V of Sec. 5.1).
-//  * Within a warp, L lanes share a pair of rows; each lane owns K channels of both rows.
-//  * FP64 is used only for the phase argument: tau is formed in FP64 once per (component, row) and
-//    split into a float pair; per-channel phases are reduced to [-1/2, 1/2] turns in double-float
-//    FP32 arithmetic (no FP64 in the channel loop).
+//  * Within a warp, L lanes share a pair of rows; each lane owns K channels of both rows, and the two
+//    rows travel together in f32x2 register pairs (one packed FFMA2/FMUL2 does both rows).
+//  * No FP64 in the loops: tau is formed once per (component, row) in double-float FP32 from float-pair
+//    operands (error-free two-product and two-sum) and per-channel phases are reduced to [-1/2, 1/2]
+//    turns in double-float FP32 arithmetic.
 //  * Uniformly spaced channels: the phasor of channel f+1 is the phasor of channel f times
 //    Delta = exp(-2 pi i tau dnu / c) (one complex multiply), restarted from an exact phase at the
 //    first channel of every lane; Delta itself is formed from an exactly reduced phase with the
@@ -33,21 +34,24 @@ constexpr int K1_FLUSH = 4;     // tiles (128 components) per register partial s
 
 struct K1Smem {
   // offsets in bytes into dynamic shared memory
-  int stage, bars, uvw, rec, q, cs, acc, total;
+  int stage, bars, uvw, rec, cs, acc, total;
 };
 
-// acc holds the second-level sums: every K1_FLUSH tiles the register partial sums (at most 128
-// components) are added into it, which keeps the FP32 rounding of a 25,000-term sum near 1e-7.
+// Per warp: (u, v, w) of its rows as float pairs, and per (component, row pair) a 48-byte record of
+// three float4: {th0, tl0, th1, tl1} (tau pairs), {D0.x, D1.x, D0.y, D1.y} and {-D0.y, -D1.y, -q0, -q1}
+// (D the one-channel phasor step, q the Gaussian form), laid out so each pair of the two rows loads
+// straight into an f32x2 register pair.  acc holds the second-level sums: every K1_FLUSH tiles the
+// register partial sums (at most 128 components) are added into it, which keeps the FP32 rounding of a
+// 25,000-term sum near 1e-7.
 __host__ __device__ inline K1Smem k1_smem_layout(int log2L, int K) {
-  int groups = 32 >> log2L;
-  int rpw = 2 * groups;  // rows per warp
+  const int groups = 32 >> log2L;  // row pairs per warp
+  const int rpw = 2 * groups;      // rows per warp
   K1Smem s;
   s.stage = 0;
   s.bars = s.stage + K1_NSTAGE * K1_CT * (int)sizeof(PGRec);
   s.uvw = s.bars + 2 * K1_NSTAGE * 8;
-  s.rec = s.uvw + K1_WARPS * rpw * 3 * 8;
-  s.q = s.rec + K1_WARPS * K1_CT * rpw * 16;
-  s.cs = s.q + K1_WARPS * K1_CT * rpw * 4;
+  s.rec = s.uvw + K1_WARPS * rpw * 6 * 4;
+  s.cs = s.rec + K1_WARPS * K1_CT * groups * 48;
   s.acc = s.cs + K1_WARPS * K1_CT * 16;
   s.total = s.acc + K1_THREADS * 2 * K * 8;
   return s;
@@ -64,6 +68,65 @@ __device__ __forceinline__ bool bounded_wait(uint64_t* bar, uint32_t parity, uns
   return true;
 }
 
+// One component against the K channels of this lane's two rows, uniform channels.  The two rows
+// travel together in f32x2 pairs (x: row 0, y: row 1), so the phasor step P <- P D and the sum
+// V += A P each take one packed instruction per component of the complex value.  Start phasors
+// come from the exactly reduced phase at the lane's first channel; the amplitude of both rows is one
+// exp2 for points, one per row for Gaussians (the envelope depends on (u, v)).
+template <int K, bool GAUSS>
+__device__ __forceinline__ void k1_comp_uniform(const float4 c, const float4 Ra, const float4 Rb, const float4 Rc,
+                                                const float a0h, const float a0l, const float* lam, const float* wg,
+                                                float2* Vre, float2* Vim) {
+  const float2 P0 = phasor_fast(reduce_turns(Ra.x, Ra.y, a0h, a0l));
+  const float2 P1 = phasor_fast(reduce_turns(Ra.z, Ra.w, a0h, a0l));
+  const float2 sg = make_float2(c.z, c.w);
+  float2 Pre = __fmul2_rn(make_float2(P0.x, P1.x), sg);
+  float2 Pim = __fmul2_rn(make_float2(P0.y, P1.y), sg);
+  const float2 Dre = make_float2(Rb.x, Rb.y), Dim = make_float2(Rb.z, Rb.w), nDim = make_float2(Rc.x, Rc.y);
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const float e = fmaf(c.y, lam[k], c.x);
+    float2 A;
+    if (GAUSS) {
+      A.x = ex2_approx(fmaf(Rc.z, wg[k], e));
+      A.y = ex2_approx(fmaf(Rc.w, wg[k], e));
+    } else {
+      A.x = ex2_approx(e);
+      A.y = A.x;
+    }
+    Vre[k] = __ffma2_rn(A, Pre, Vre[k]);
+    Vim[k] = __ffma2_rn(A, Pim, Vim[k]);
+    if (k + 1 < K) {
+      const float2 nre = __ffma2_rn(Pre, Dre, __fmul2_rn(Pim, nDim));
+      Pim = __ffma2_rn(Pre, Dim, __fmul2_rn(Pim, Dre));
+      Pre = nre;
+    }
+  }
+}
+
+// The same for an arbitrary channel list: every channel's phase is reduced and evaluated.
+template <int K, bool GAUSS>
+__device__ __forceinline__ void k1_comp_list(const float4 c, const float4 Ra, const float4 Rc, const float* ah,
+                                             const float* al, const float* lam, const float* wg, float2* Vre,
+                                             float2* Vim) {
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const float2 P0 = phasor_fast(reduce_turns(Ra.x, Ra.y, ah[k], al[k]));
+    const float2 P1 = phasor_fast(reduce_turns(Ra.z, Ra.w, ah[k], al[k]));
+    const float e = fmaf(c.y, lam[k], c.x);
+    float2 A;
+    if (GAUSS) {
+      A.x = c.z * ex2_approx(fmaf(Rc.z, wg[k], e));
+      A.y = c.z * ex2_approx(fmaf(Rc.w, wg[k], e));
+    } else {
+      A.x = c.z * ex2_approx(e);
+      A.y = A.x;
+    }
+    Vre[k] = __ffma2_rn(A, make_float2(P0.x, P1.x), Vre[k]);
+    Vim[k] = __ffma2_rn(A, make_float2(P0.y, P1.y), Vim[k]);
+  }
+}
+
 // One (row tile, channel block) of one observation: the body of the single-launch kernel below and
 // of the batched serving kernel.  Re-entrant: it initialises and invalidates its own barriers.
 template <int K, bool UNIFORM>
@@ -75,17 +138,17 @@ __device__ __forceinline__ void k1_tile(const K1Args& a, const int bx, const int
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int L = 1 << a.log2L;
-  const int groups = 32 >> a.log2L;
+  const int gshift = 5 - a.log2L;
+  const int groups = 1 << gshift;  // row pairs per warp
   const int rpw = 2 * groups;
   const int g = lane >> a.log2L, sub = lane & (L - 1);
   const int row_w0 = bx * (K1_WARPS * rpw) + warp * rpw;
   const int f0 = by * a.chan_block + sub * K;
 
-  double* uvw_s = reinterpret_cast<double*>(smem + lay.uvw) + warp * rpw * 3;
-  float4* rec = reinterpret_cast<float4*>(smem + lay.rec) + warp * K1_CT * rpw;
-  float* qs = reinterpret_cast<float*>(smem + lay.q) + warp * K1_CT * rpw;
+  float* uvw_s = reinterpret_cast<float*>(smem + lay.uvw) + warp * rpw * 6;
+  float4* rec = reinterpret_cast<float4*>(smem + lay.rec) + warp * K1_CT * groups * 3;
   float4* cs = reinterpret_cast<float4*>(smem + lay.cs) + warp * K1_CT;
-  float2* acc = reinterpret_cast<float2*>(smem + lay.acc) + threadIdx.x;  // [2K][K1_THREADS]
+  float2* acc = reinterpret_cast<float2*>(smem + lay.acc) + threadIdx.x;  // [2K][K1_THREADS]: re, then im pairs
 #pragma unroll
   for (int i = 0; i < 2 * K; ++i) acc[i * K1_THREADS] = make_float2(0.f, 0.f);
 
@@ -103,10 +166,13 @@ __device__ __forceinline__ void k1_tile(const K1Args& a, const int bx, const int
     }
     fence_mbar_init();
   }
-  // rows of this warp: (u, v, w) in FP64
+  // rows of this warp: (u, v, w) split into float pairs
   for (int i = lane; i < rpw * 3; i += 32) {
-    int r = row_w0 + i / 3;
-    uvw_s[i] = r < a.n_rows ? a.uvw[(size_t)r * 3 + i % 3] : 0.0;
+    const int r = row_w0 + i / 3;
+    float h, l;
+    split_double(r < a.n_rows ? a.uvw[(size_t)r * 3 + i % 3] : 0.0, h, l);
+    uvw_s[2 * i] = h;
+    uvw_s[2 * i + 1] = l;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -134,9 +200,9 @@ __device__ __forceinline__ void k1_tile(const K1Args& a, const int bx, const int
   split_double(a.freq[min(f0, a.n_chan - 1)] * (1.0 / kC), a0h, a0l);
   const double L0 = log2(a.nu0);
 
-  float2 V0[K], V1[K];
+  float2 Vre[K], Vim[K];
 #pragma unroll
-  for (int k = 0; k < K; ++k) V0[k] = V1[k] = make_float2(0.f, 0.f);
+  for (int k = 0; k < K; ++k) Vre[k] = Vim[k] = make_float2(0.f, 0.f);
 
   bool ok = true;
   for (int t = 0; t < n_tiles && ok; ++t) {
@@ -158,91 +224,76 @@ __device__ __forceinline__ void k1_tile(const K1Args& a, const int bx, const int
     const bool gauss = t >= n_pt_tiles;
     const PGRec* st = stage + s * K1_CT;
 
-    // --- records: FP64 phase argument per (component, row), shared by the L lanes of a row pair
-    const int rshift = 6 - a.log2L;  // rpw == 1 << rshift
-    for (int idx = lane; idx < (cnt << rshift); idx += 32) {
-      const int j = idx >> rshift, rr = idx & (rpw - 1);
-      const double u = uvw_s[rr * 3 + 0], v = uvw_s[rr * 3 + 1], w = uvw_s[rr * 3 + 2];
-      const double tau = fma(u, st[j].l, fma(v, st[j].m, w * st[j].nm1));
-      float th, tl;
-      split_double(tau, th, tl);
-      float4 r;
-      r.x = th;
-      r.y = tl;
+    // --- records per (component, row pair), shared by the L lanes of the pair
+    for (int idx = lane; idx < (cnt << gshift); idx += 32) {
+      const int j = idx >> gshift, gg = idx & (groups - 1);
+      const PGRec& c = st[j];
+      const float* x0 = uvw_s + 12 * gg;
+      const float* x1 = x0 + 6;
+      float th0, tl0, th1, tl1;
+      tau_df(x0, c, th0, tl0);
+      tau_df(x1, c, th1, tl1);
+      float4 Rb = make_float4(0.f, 0.f, 0.f, 0.f), Rc = Rb;
       if (UNIFORM) {
-        float2 D = phasor_accurate(reduce_turns(th, tl, a.dnu_h, a.dnu_l));
-        r.z = D.x;
-        r.w = D.y;
-      } else {
-        r.z = r.w = 0.f;
+        const float2 D0 = phasor_accurate(reduce_turns(th0, tl0, a.dnu_h, a.dnu_l));
+        const float2 D1 = phasor_accurate(reduce_turns(th1, tl1, a.dnu_h, a.dnu_l));
+        Rb = make_float4(D0.x, D1.x, D0.y, D1.y);
+        Rc.x = -D0.y;
+        Rc.y = -D1.y;
       }
-      rec[j * rpw + rr] = r;
       if (gauss) {
-        const float uf = (float)u, vf = (float)v;
-        qs[j * rpw + rr] = st[j].ga * uf * uf + st[j].gb * uf * vf + st[j].gc * vf * vf;
+        const float u0 = x0[0], v0 = x0[2], u1 = x1[0], v1 = x1[2];
+        Rc.z = -(c.ga * u0 * u0 + c.gb * u0 * v0 + c.gc * v0 * v0);
+        Rc.w = -(c.ga * u1 * u1 + c.gb * u1 * v1 + c.gc * v1 * v1);
       }
+      float4* R = rec + 3 * (j * groups + gg);
+      R[0] = make_float4(th0, tl0, th1, tl1);
+      R[1] = Rb;
+      R[2] = Rc;
     }
     for (int j = lane; j < cnt; j += 32)
-      cs[j] = make_float4(st[j].lS + st[j].alpha * (float)(L0 - st[j].lref), st[j].alpha, st[j].sgn, 0.f);
+      cs[j] = make_float4(st[j].lS + st[j].alpha * (float)(L0 - st[j].lref), st[j].alpha, st[j].sgn, st[j].sgn);
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
 
     // --- channel loop: K channels of two rows per lane
-    for (int j = 0; j < cnt; ++j) {
-      const float4 c = cs[j];
-      const float4 R0 = rec[j * rpw + 2 * g], R1 = rec[j * rpw + 2 * g + 1];
-      const float q0 = gauss ? qs[j * rpw + 2 * g] : 0.f;
-      const float q1 = gauss ? qs[j * rpw + 2 * g + 1] : 0.f;
-      if (UNIFORM) {
-        float2 P0 = phasor_fast(reduce_turns(R0.x, R0.y, a0h, a0l));
-        float2 P1 = phasor_fast(reduce_turns(R1.x, R1.y, a0h, a0l));
-        P0.x *= c.z; P0.y *= c.z;
-        P1.x *= c.z; P1.y *= c.z;
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-          // amplitude: spectrum and (for Gaussians) envelope in one exp2
-          const float e = fmaf(c.y, lam[k], c.x);
-          const float A0 = ex2_approx(gauss ? fmaf(-q0, wg[k], e) : e);
-          const float A1 = gauss ? ex2_approx(fmaf(-q1, wg[k], e)) : A0;
-          V0[k].x = fmaf(A0, P0.x, V0[k].x);
-          V0[k].y = fmaf(A0, P0.y, V0[k].y);
-          V1[k].x = fmaf(A1, P1.x, V1[k].x);
-          V1[k].y = fmaf(A1, P1.y, V1[k].y);
-          if (k + 1 < K) {
-            const float x0 = P0.x * R0.z - P0.y * R0.w, y0 = P0.x * R0.w + P0.y * R0.z;
-            const float x1 = P1.x * R1.z - P1.y * R1.w, y1 = P1.x * R1.w + P1.y * R1.z;
-            P0 = make_float2(x0, y0);
-            P1 = make_float2(x1, y1);
-          }
-        }
+    const float4* Rg = rec + 3 * g;
+    if (UNIFORM) {
+      if (gauss) {
+        for (int j = 0; j < cnt; ++j)
+          k1_comp_uniform<K, true>(cs[j], Rg[3 * groups * j], Rg[3 * groups * j + 1], Rg[3 * groups * j + 2], a0h, a0l,
+                                   lam, wg, Vre, Vim);
       } else {
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-          const float2 P0 = phasor_fast(reduce_turns(R0.x, R0.y, ah[k], al[k]));
-          const float2 P1 = phasor_fast(reduce_turns(R1.x, R1.y, ah[k], al[k]));
-          const float e = fmaf(c.y, lam[k], c.x);
-          const float s0 = c.z * ex2_approx(gauss ? fmaf(-q0, wg[k], e) : e);
-          const float s1 = gauss ? c.z * ex2_approx(fmaf(-q1, wg[k], e)) : s0;
-          V0[k].x = fmaf(s0, P0.x, V0[k].x);
-          V0[k].y = fmaf(s0, P0.y, V0[k].y);
-          V1[k].x = fmaf(s1, P1.x, V1[k].x);
-          V1[k].y = fmaf(s1, P1.y, V1[k].y);
-        }
+        for (int j = 0; j < cnt; ++j)
+          k1_comp_uniform<K, false>(cs[j], Rg[3 * groups * j], Rg[3 * groups * j + 1], Rg[3 * groups * j + 2], a0h,
+                                    a0l, lam, wg, Vre, Vim);
+      }
+    } else {
+      if (gauss) {
+        for (int j = 0; j < cnt; ++j)
+          k1_comp_list<K, true>(cs[j], Rg[3 * groups * j], Rg[3 * groups * j + 2], ah, al, lam, wg, Vre, Vim);
+      } else {
+        for (int j = 0; j < cnt; ++j)
+          k1_comp_list<K, false>(cs[j], Rg[3 * groups * j], Rg[3 * groups * j + 2], ah, al, lam, wg, Vre, Vim);
       }
     }
     __syncwarp();
     if ((t + 1) % K1_FLUSH == 0) {
 #pragma unroll
       for (int k = 0; k < K; ++k) {
-        float2 x = acc[k * K1_THREADS], y = acc[(K + k) * K1_THREADS];
-        acc[k * K1_THREADS] = make_float2(x.x + V0[k].x, x.y + V0[k].y);
-        acc[(K + k) * K1_THREADS] = make_float2(y.x + V1[k].x, y.y + V1[k].y);
-        V0[k] = V1[k] = make_float2(0.f, 0.f);
+        acc[k * K1_THREADS] = __fadd2_rn(acc[k * K1_THREADS], Vre[k]);
+        acc[(K + k) * K1_THREADS] = __fadd2_rn(acc[(K + k) * K1_THREADS], Vim[k]);
+        Vre[k] = Vim[k] = make_float2(0.f, 0.f);
       }
     }
   }
 
   // --- epilogue: each visibility written once
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    Vre[k] = __fadd2_rn(acc[k * K1_THREADS], Vre[k]);
+    Vim[k] = __fadd2_rn(acc[(K + k) * K1_THREADS], Vim[k]);
+  }
 #pragma unroll
   for (int rr = 0; rr < 2; ++rr) {
     const int row = row_w0 + 2 * g + rr;
@@ -252,9 +303,7 @@ __device__ __forceinline__ void k1_tile(const K1Args& a, const int bx, const int
       const int f = f0 + k;
       if (f >= a.n_chan) continue;
       const size_t idx = (size_t)row * a.n_chan + f;
-      const float2 p = rr == 0 ? V0[k] : V1[k];
-      const float2 q = acc[(rr * K + k) * K1_THREADS];
-      float2 v = make_float2(q.x + p.x, q.y + p.y);
+      float2 v = rr == 0 ? make_float2(Vre[k].x, Vim[k].x) : make_float2(Vre[k].y, Vim[k].y);
       if (!ok) v = make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
       if (a.mode == OUT_STORE) {
         a.out[idx] = v;
@@ -289,25 +338,36 @@ struct K1Choice {
   int log2L, K;
 };
 
-// Pick lanes-per-row L and channels-per-lane K: fewest padded channel slots, then the widest channel
-// block (each FP64 phase record per (component, row) then serves the most channels), then larger K.
-static K1Choice k1_choose(int F) {
+// Estimated cost of a (lanes per row pair L = 2^log2L, channels per lane K) configuration, in units
+// of one component-visibility evaluation: every padded channel slot costs one evaluation plus the
+// lane's per-(component, row) start phasor spread over its K channels (about 1.5 evaluations), and
+// every (component, row, channel block) one record (about 12).  `waves` > 0 rounds the CTA count up
+// to whole waves of that many resident CTAs; configurations that fit only one CTA per SM pay 30%.
+static double k1_cost(long rows, int F, int log2L, int K, int waves) {
+  const long cb = (long)K << log2L, nblk = (F + cb - 1) / cb;
+  const long rpc = (long)K1_WARPS * 2 * (32 >> log2L);
+  const long ctas = ((rows + rpc - 1) / rpc) * nblk;
+  const double per_cta = (double)rpc * ((double)cb * (1.0 + 1.5 / K) + 12.0);
+  const bool two = k1_smem_layout(log2L, K).total <= 113 * 1024;
+  double c = per_cta * (waves > 0 ? (double)((ctas + (two ? 2 : 1) * waves - 1) / ((two ? 2 : 1) * waves)) *
+                                        (two ? 2 : 1) * waves
+                                  : (double)ctas);
+  return two ? c : 1.3 * c;
+}
+
+// Pick L in {8, 16, 32} and K in {4, 8, 12, 16} by the cost above (ties: the wider block).
+static K1Choice k1_choose(long rows, int F, int num_sms) {
   K1Choice best{5, 12};
-  long best_slots = -1, best_cb = 0;
-  const int Ks[4] = {12, 8, 16, 4};
-  for (int li = 2; li <= 5; ++li) {
+  double best_c = -1.0;
+  const int Ks[4] = {12, 16, 8, 4};
+  for (int li = 5; li >= 3; --li)
     for (int K : Ks) {
-      long cb = (long)K << li;
-      long slots = ((F + cb - 1) / cb) * cb;
-      bool better = best_slots < 0 || slots < best_slots || (slots == best_slots && cb > best_cb) ||
-                    (slots == best_slots && cb == best_cb && K > best.K && K <= 12);
-      if (better) {
-        best_slots = slots;
-        best_cb = cb;
+      const double c = k1_cost(rows, F, li, K, num_sms);
+      if (best_c < 0 || c < best_c * 0.999) {
+        best_c = c;
         best = {li, K};
       }
     }
-  }
   return best;
 }
 
@@ -322,7 +382,7 @@ static cudaError_t k1_launch(const K1Args& a, dim3 grid, int smem, cudaStream_t 
 
 int launch_phasor_mixed(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, int mode, const PeelArgs& pa,
                         cudaStream_t st) {
-  K1Choice ch = k1_choose(o.n_chan);
+  K1Choice ch = k1_choose(o.n_rows, o.n_chan, ctx->num_sms);
   K1Args a;
   a.uvw = o.uvw;
   a.freq = o.freq;
@@ -389,14 +449,15 @@ int k1_batched_smem() { return k1_smem_layout(K1B_MIN_LOG2L, K1B_KMAX).total; }
 int k1_batched_args(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, int mode, const PeelArgs& pa,
                     K1Args* args, int* grid_x, int* grid_y) {
   if (!o.uniform) return set_error(WN_EINVAL, "batched prediction needs uniformly spaced channels");
-  // fewest padded channel slots over K in {12, 8} and L in {8, 16, 32}; ties go to the wider block
+  // the cheapest of K in {12, 8} and L in {8, 16, 32} by the single-launch cost model, without waves
+  // (the batched kernel is persistent)
   int log2L = 5, K = 12;
-  long best = -1;
-  for (int li = K1B_MIN_LOG2L; li <= 5; ++li)
+  double best = -1.0;
+  for (int li = 5; li >= K1B_MIN_LOG2L; --li)
     for (int kk : {12, 8}) {
-      const long cb = (long)kk << li, slots = ((o.n_chan + cb - 1) / cb) * cb;
-      if (best < 0 || slots < best || (slots == best && cb > ((long)K << log2L))) {
-        best = slots;
+      const double c = k1_cost(o.n_rows, o.n_chan, li, kk, 0);
+      if (best < 0 || c < best * 0.999) {
+        best = c;
         log2L = li;
         K = kk;
       }
