@@ -38,6 +38,21 @@ OPS_PER_EVAL = 6
 FP32_LANES_PER_SM = 128
 
 
+def k1_traffic():
+    """DRAM bytes per launch of the phasor kernel from the committed ncu record, or None when the kernel
+    sources have changed since the counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k1_phasor_mwa_traffic.json")
+    try:
+        rec = json.load(open(path))
+        m = hashlib.sha256()
+        for p in rec["sources"]:
+            m.update(open(os.path.join(ROOT, p), "rb").read())
+        return rec["dram_bytes_per_launch"] if m.hexdigest() == rec["sources_sha256"] else None
+    except Exception:
+        return None
+
+
 def peaks():
     p = {}
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -304,6 +319,49 @@ def bench_serving(wn, ctx, local, torch, n_req=48, seed=17):
             "max_batch_requests": st["max_batch_requests"]}
 
 
+def run_case(case: str):
+    """Small fixed cases for ncu captures (three warm-up calls, then one timed call)."""
+    import torch
+    import paper_2005_09316_b300 as wn
+    ctx = wn.Context(0)
+    if case == "mwa_small":      # K1: 2 steps of the MWA array, 2,000 points + 500 Gaussians
+        obs, _ = synth.mwa(n_time=2)
+        sky = synth.make_sky(102, 2000, 500, 0)
+    elif case == "fornax_small":  # K2: 2 steps of the Fornax array, 2 shapelets at n_max 80
+        obs, sky = synth.fornax(n_time=2)
+    elif case == "adjoint":       # K4: the full adjoint workload
+        obs, sky = synth.adjoint()
+    else:                         # K3: standalone peel of the full MWA observation
+        obs, sky = synth.mwa()
+    d = wn.obs_to_device(obs)
+    shape = (obs.n_time, obs.n_base, obs.n_chan)
+    out = torch.empty(shape, dtype=torch.complex64, device="cuda")
+    gains = torch.as_tensor(synth.make_gains(5, obs.n_ant).astype(np.complex64)).cuda()
+    data = torch.randn(shape, dtype=torch.complex64, device="cuda")
+    if case == "peel":
+        model = torch.randn(shape, dtype=torch.complex64, device="cuda")
+        fn = lambda: ctx.peel_model(d, gains, data, model, out=out)  # noqa: E731
+        work = 24 * obs.n_vis
+    else:
+        m = ctx.upload(sky)
+        if case == "adjoint":
+            fn = lambda: ctx.predict_grad(d, m, gains, data, resid=out)  # noqa: E731
+        else:
+            fn = lambda: ctx.predict(d, m, out=out)  # noqa: E731
+        work = obs.n_vis * sky.n_comp
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+    e0.record()
+    fn()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    print(json.dumps({"case": case, "ms": ms, "work": work, "rate": work / (ms * 1e-3),
+                      "device_errors": ctx.device_errors()}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -313,7 +371,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-extras", action="store_true", help="skip the shapelet, adjoint and serving reports")
+    ap.add_argument("--case", choices=["mwa_small", "fornax_small", "adjoint", "peel"],
+                    help="run one small fixed case for profiling instead of the benchmark")
     args = ap.parse_args()
+    if args.case:
+        return run_case(args.case)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
@@ -385,7 +447,9 @@ def main():
         achieved = OPS_PER_EVAL * evals / (ms * 1e-3) / 1e12
         extra["roofline"] = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_ops, 3),
                              "unit": "Top/s (FP32-pipe lane ops)", "frac": round(achieved / peak_ops, 4),
-                             "traffic": None,
+                             "traffic": k1_traffic(),
+                             "traffic_unit": "bytes per launch (ncu dram__bytes_read + write, full size)",
+                             "algorithmic_bytes": 16 * obs.n_vis + 24 * obs.n_rows,
                              "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (derived, not measured)",
                              "ops_per_eval": OPS_PER_EVAL}
         if clocks.get("sm_mhz"):
@@ -486,7 +550,7 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64phase", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_vis": obs.n_vis, "n_comp": sky.n_comp, "evals_per_step": evals,
                        "l2": "inputs > L2 each step (350 MB data in, 350 MB residual out); the 1.6 MB "
                              "component table stays L2-resident by design", "parallelism": f"replicas x{ws}"},
