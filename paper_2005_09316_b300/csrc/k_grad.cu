@@ -22,10 +22,10 @@ constexpr int K4_CT = 32;     // components per CTA: lane j forms comp j's phase
 constexpr int K4_WARPS = 8;
 constexpr int K4_KMAX = 16;   // most channels per lane per pass (strided by 32): 512 channels per pass
 constexpr int K4_NG = 7;      // gradient components per point/Gaussian: flux, alpha, l, m, maj, min, pa
-constexpr int K4_FLUSH = 8;   // rows per FP32 partial before it is added to the FP64 sum
+constexpr int K4_FLUSH = 32;  // rows per FP32 partial before it is added to the FP64 sum
 
 struct K4Args {
-  const double* uvw;
+  const float* uvw_pairs;     // [n_rows][6]: (u, v, w) metres as float pairs hi, lo
   const double* freq;
   int n_rows, n_chan, n_base;
   int f_lo, f_cnt;            // channel pass
@@ -45,12 +45,17 @@ struct K4Args {
 template <int KM>
 __global__ void __launch_bounds__(K4_WARPS * 32) k4_grad_pg(const K4Args a) {
   __shared__ PGRec comps[K4_CT];
+  __shared__ float cjs[K4_CT];  // alpha log2(nu0 / nu_ref): the flux-free log2 amplitude at nu0
   __shared__ double gsum[K4_WARPS][K4_CT][K4_NG];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n_pg = a.n_point + a.n_gauss;
   const int c0 = blockIdx.x * K4_CT;
   const int ncomp = min(K4_CT, n_pg - c0);
-  if (threadIdx.x < ncomp) comps[threadIdx.x] = a.comps[c0 + threadIdx.x];
+  if (threadIdx.x < ncomp) {
+    const PGRec c = a.comps[c0 + threadIdx.x];
+    comps[threadIdx.x] = c;
+    cjs[threadIdx.x] = c.alpha * (float)(log2(a.nu0) - c.lref);
+  }
   __syncthreads();
 
   // per-lane channel constants: nu/c as a float pair (one FP64 multiply and split), the rest in FP32
@@ -100,7 +105,9 @@ __global__ void __launch_bounds__(K4_WARPS * 32) k4_grad_pg(const K4Args a) {
   const int r_hi = min(a.n_rows, r_lo + a.rows_per_chunk);
   int nrow = 0;
   for (int row = r_lo + warp; row < r_hi; row += K4_WARPS) {
-    const double u = a.uvw[3 * (size_t)row], v = a.uvw[3 * (size_t)row + 1], w = a.uvw[3 * (size_t)row + 2];
+    float xuvw[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) xuvw[i] = __ldg(a.uvw_pairs + 6 * (size_t)row + i);
     // W = conj(G) R for this lane's channels
     float2 W[KM];
 #pragma unroll
@@ -113,11 +120,11 @@ __global__ void __launch_bounds__(K4_WARPS * 32) k4_grad_pg(const K4Args a) {
         W[k] = make_float2(G.x * R.x + G.y * R.y, G.x * R.y - G.y * R.x);
       }
     }
-    // this lane's component: phase argument (FP64), Gaussian form and the per-row factors
+    // this lane's component: phase argument (double-float FP32), Gaussian form and the per-row factors
     float th = 0.f, tl = 0.f, q = 0.f, fl = 0.f, fm = 0.f, fmaj = 0.f, fmin = 0.f, fpa = 0.f;
     if (mine) {
-      split_double(fma(u, me_l, fma(v, me_m, w * me_nm1)), th, tl);
-      const float uf = (float)u, vf = (float)v, wf = (float)w;
+      tau_df(xuvw, me, th, tl);
+      const float uf = xuvw[0], vf = xuvw[2], wf = xuvw[4];
       fl = -4.0f * (float)kPi * (uf - wf * my_ln);
       fm = -4.0f * (float)kPi * (vf - wf * my_mn);
       if (my_gauss) {
@@ -133,7 +140,7 @@ __global__ void __launch_bounds__(K4_WARPS * 32) k4_grad_pg(const K4Args a) {
       const float qj = __shfl_sync(0xffffffffu, q, j);
       const PGRec& c = comps[j];
       // channel sums use the amplitude without the flux: dV/dS_ref = V / S_ref holds for S_ref = 0 too
-      const float cj = c.alpha * (float)(L0 - c.lref);
+      const float cj = cjs[j];
       float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
 #pragma unroll
       for (int k = 0; k < KM; ++k) {
@@ -211,11 +218,17 @@ __global__ void k4_reduce_pg(const double* partials, int chunks, int n_point, in
 }
 
 // ---------------------------------------------------------------------------------------------
-// Shapelets: one launch per shapelet; persistent CTAs of 64 threads, one visibility per thread per
-// tile.  Each thread forms phi_n(x), phi_n(y) (n <= nmax+1) into shared memory, its W, S and phasor,
-// and the envelope derivatives by a loop over the coefficient triples; then the CTA reduces the
-// coefficient gradients sum_vis w phi_a(x) phi_b(y) for the tile (w = Re or Im of conj(W) S P by the
-// parity of a+b) into FP64 shared accumulators.
+// Shapelets: one launch per shapelet; persistent CTAs of 128 threads, one visibility per thread per
+// tile.  With f_ab = C_ab times the sign of (-i)^(a+b) (real part for even a+b, imaginary for odd),
+//   xi      = sum_a phi_a(x)  T_a,   T_a  = sum_b f_ab phi_b(y),
+//   dxi/dx  = sum_a phi_a'(x) T_a,
+//   dxi/dy  = sum_a phi_a(x)  T'_a,  T'_a = sum_b g_ab phi_b(y),
+// where g_ab = sqrt((b+1)/2) f_a,b+1 - sqrt(b/2) f_a,b-1 is the y-derivative folded into the
+// coefficients (phi_b' = sqrt(b/2) phi_b-1 - sqrt((b+1)/2) phi_b+1), so both sums run over the same
+// phi_b(y) and T'_a takes the opposite real/imaginary part.  Each thread keeps its phi_n(x), phi_n(y)
+// rows in shared memory (odd row stride: conflict-free both per thread and across threads); the CTA
+// then reduces the coefficient gradients sum_vis w phi_a(x) phi_b(y) for the tile (w = Re or Im of
+// conj(W) S P by the parity of a+b) into FP64 shared accumulators.
 // ---------------------------------------------------------------------------------------------
 constexpr int K4S_T = 128;
 constexpr int K4S_NS = 7;  // flux, alpha, l, m, beta1, beta2, pa
@@ -227,16 +240,15 @@ __constant__ float c_dn_lo[kNmaxLimit + 2], c_dn_hi[kNmaxLimit + 2], c_ra[kNmaxL
 struct K4SArgs {
   const float4* rowinfo;   // per row: (xs, ys, tau hi, tau lo)
   const float4* chaninfo;  // per channel: (nu/c hi, nu/c lo, log2(nu/nu0), nu)
-  const double* uvw;
+  const float* uvw_pairs;  // [n_rows][6]
   int n_rows, n_chan, n_base;
   long long n_vis;
   int nmax, nnz;
   const int *n1, *n2;
   const double* coeff;
-  double l, m, nm1, lnref_nu0;   // ln(nu0 / nu_ref)
-  float l_over_n, m_over_n, lnref_nu0_f;
-  double flux, beta1, beta2, pa;
-  float c_amp, alpha, sgn;
+  float l_over_n, m_over_n, lnref_nu0_f;   // l / n, m / n, ln(nu0 / nu_ref)
+  const double *flux, *beta1, *beta2;      // device scalars of this shapelet (raw FP64 tables)
+  float c_amp, alpha;
   const float2* resid;
   PeelArgs peel;
   double* part_s;   // [grid][K4S_NS]
@@ -264,22 +276,73 @@ __device__ void hermite_scaled_row(float x, int nmax1, float* out) {
   }
 }
 
+// Shared-memory layout of k4_grad_shape (bytes): basis rows, folded coefficient pairs (f, g) per
+// triangle row a (b = 0..n-a+1), row offsets, tile weights, FP64 coefficient accumulators.
+struct K4SSmem {
+  int ld, phx, phy, fg, toff, wre, wim, accc, total;
+};
+__host__ __device__ inline K4SSmem k4s_layout(int nmax, int nnz, int T) {
+  K4SSmem s;
+  s.ld = (nmax + 3) | 1;
+  const int nfg = (nmax + 1) * (nmax + 4) / 2;  // sum over a of (n - a + 2)
+  s.phx = 0;
+  s.phy = s.phx + T * s.ld * 4;
+  s.fg = (s.phy + T * s.ld * 4 + 7) & ~7;
+  s.toff = s.fg + nfg * 8;
+  s.wre = s.toff + (nmax + 2) * 4;
+  s.wim = s.wre + T * 4;
+  s.accc = (s.wim + T * 4 + 7) & ~7;
+  s.total = s.accc + nnz * 8;
+  return s;
+}
+
 __global__ void __launch_bounds__(K4S_T) k4_grad_shape(const K4SArgs a) {
   extern __shared__ __align__(16) unsigned char sm[];
-  const int ld = a.nmax + 3;  // phi_0 .. phi_{nmax+1}, padded
-  float* phx = reinterpret_cast<float*>(sm);
-  float* phy = phx + K4S_T * ld;
-  float* wre = phy + K4S_T * ld;
-  float* wim = wre + K4S_T;
-  double* accc = reinterpret_cast<double*>(wim + K4S_T + (K4S_T & 1));
-  for (int k = threadIdx.x; k < a.nnz; k += K4S_T) accc[k] = 0.0;
+  const int n = a.nmax;
+  const int T = blockDim.x;  // 128, or 64 for the largest n_max
+  const K4SSmem lay = k4s_layout(n, a.nnz, T);
+  const int ld = lay.ld;
+  float* phx = reinterpret_cast<float*>(sm + lay.phx);
+  float* phy = reinterpret_cast<float*>(sm + lay.phy);
+  float2* fg = reinterpret_cast<float2*>(sm + lay.fg);
+  int* toff = reinterpret_cast<int*>(sm + lay.toff);
+  float* wre = reinterpret_cast<float*>(sm + lay.wre);
+  float* wim = reinterpret_cast<float*>(sm + lay.wim);
+  double* accc = reinterpret_cast<double*>(sm + lay.accc);
+  const int t = threadIdx.x;
+  const double flux = *a.flux, beta1 = *a.beta1, beta2 = *a.beta2;
+
+  // folded coefficients: row a holds (f_ab, g_ab) for b = 0..n-a+1 (f is zero past the triangle)
+  for (int aa = t; aa <= n + 1; aa += T) toff[aa] = aa * (n + 2) - aa * (aa - 1) / 2;
+  const int nfg = (n + 1) * (n + 4) / 2;
+  for (int i = t; i < nfg; i += T) fg[i] = make_float2(0.f, 0.f);
+  for (int k = t; k < a.nnz; k += T) accc[k] = 0.0;
+  __syncthreads();
+  for (int k = t; k < a.nnz; k += T) {
+    const int na = __ldg(a.n1 + k), nb = __ldg(a.n2 + k);
+    const int ph = (na + nb) & 3;  // (-i)^k = 1, -i, -1, i: signs +, -, -, + on the real / imaginary part
+    fg[toff[na] + nb].x = (ph == 1 || ph == 2 ? -1.0f : 1.0f) * (float)__ldg(a.coeff + k);
+  }
+  __syncthreads();
+  for (int aa = t; aa <= n; aa += T) {
+    float2* row = fg + toff[aa];
+    const int nb = n - aa;
+    for (int b = 0; b <= nb + 1; ++b) {
+      const float up = b + 1 <= nb ? row[b + 1].x : 0.f;   // f_a,b+1
+      const float dn = b >= 1 && b - 1 <= nb ? row[b - 1].x : 0.f;  // f_a,b-1
+      row[b].y = c_dn_hi[b] * up - c_dn_lo[b] * dn;
+    }
+  }
+  __syncthreads();
+
   double accs[K4S_NS] = {0, 0, 0, 0, 0, 0, 0};
   float acc32[K4S_NS] = {0, 0, 0, 0, 0, 0, 0};
   int nacc = 0;
-  const int t = threadIdx.x;
-  const long long n_tiles = (a.n_vis + K4S_T - 1) / K4S_T;
+  const float rb = (float)(beta1 / beta2), rb2 = (float)(beta2 / beta1);
+  const float ib1 = (float)(1.0 / beta1), ib2 = (float)(1.0 / beta2);
+  const long long n_tiles = (a.n_vis + T - 1) / T;
   for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    const long long vis = tile * K4S_T + t;
+    const long long vis = tile * T + t;
     const bool valid = vis < a.n_vis;
     const int row = valid ? (int)(vis / a.n_chan) : 0;
     const int f = valid ? (int)(vis - (long long)row * a.n_chan) : 0;
@@ -287,8 +350,10 @@ __global__ void __launch_bounds__(K4S_T) k4_grad_shape(const K4SArgs a) {
     const float x = ri.x * ci.w, y = ri.y * ci.w;
     float* px = phx + t * ld;
     float* py = phy + t * ld;
-    hermite_scaled_row(x, a.nmax + 1, px);
-    hermite_scaled_row(y, a.nmax + 1, py);
+    hermite_scaled_row(x, n + 1, px);
+    hermite_scaled_row(y, n + 1, py);
+    px[n + 2] = 0.f;
+    py[n + 2] = 0.f;
     // W = conj(G) R, amplitude and phasor
     float2 W = make_float2(0.f, 0.f);
     if (valid) {
@@ -304,43 +369,58 @@ __global__ void __launch_bounds__(K4S_T) k4_grad_shape(const K4SArgs a) {
     const float yr = S * (W.x * P.x + W.y * P.y), yi = S * (W.x * P.y - W.y * P.x);
     wre[t] = yr;
     wim[t] = yi;
-    // envelope and its derivatives by the coefficient triples; phase factor (-i)^(a+b)
-    float xr = 0.f, xi = 0.f, d1r = 0.f, d1i = 0.f, d2r = 0.f, d2i = 0.f, dpr = 0.f, dpi = 0.f;
-    const float rb = (float)(a.beta1 / a.beta2), rb2 = (float)(a.beta2 / a.beta1);
-    for (int k = 0; k < a.nnz; ++k) {
-      const int na = __ldg(a.n1 + k), nb = __ldg(a.n2 + k);
-      const float c = (float)__ldg(a.coeff + k);
-      const float fa = px[na], fb = py[nb];
-      const float dxa = (na > 0 ? c_dn_lo[na] * px[na - 1] : 0.f) - c_dn_hi[na] * px[na + 1];
-      const float dyb = (nb > 0 ? c_dn_lo[nb] * py[nb - 1] : 0.f) - c_dn_hi[nb] * py[nb + 1];
-      const float e0 = c * fa * fb;
-      const float e1 = c * dxa * fb;                       // times x / beta1 below
-      const float e2 = c * fa * dyb;                       // times y / beta2 below
-      const float e3 = c * (dxa * rb * y * fb - fa * dyb * rb2 * x);
-      switch ((na + nb) & 3) {
-        case 0: xr += e0; d1r += e1; d2r += e2; dpr += e3; break;
-        case 1: xi -= e0; d1i -= e1; d2i -= e2; dpi -= e3; break;
-        case 2: xr -= e0; d1r -= e1; d2r -= e2; dpr -= e3; break;
-        default: xi += e0; d1i += e1; d2i += e2; dpi += e3; break;
+    // xi, dxi/dx, dxi/dy by the factorised sums
+    float xr = 0.f, xi = 0.f, dxr = 0.f, dxi = 0.f, dyr = 0.f, dyi = 0.f;
+    float pa_prev = 0.f, pa_cur = px[0];
+    for (int aa = 0; aa <= n; ++aa) {
+      const float pa_next = px[aa + 1];
+      const float dpa = c_dn_lo[aa] * pa_prev - c_dn_hi[aa] * pa_next;  // phi_a'(x)
+      const float2* r = fg + toff[aa];
+      const int nb = n - aa + 1;  // b = 0..nb (g reaches one past the triangle)
+      float te = 0.f, to = 0.f, ge = 0.f, go = 0.f;  // f and g sums over even / odd b
+      int b = 0;
+      for (; b + 1 <= nb; b += 2) {
+        const float2 c0 = r[b], c1 = r[b + 1];
+        const float p0 = py[b], p1 = py[b + 1];
+        te = fmaf(c0.x, p0, te);
+        ge = fmaf(c0.y, p0, ge);
+        to = fmaf(c1.x, p1, to);
+        go = fmaf(c1.y, p1, go);
       }
+      if (b <= nb) {
+        const float2 c0 = r[b];
+        const float p0 = py[b];
+        te = fmaf(c0.x, p0, te);
+        ge = fmaf(c0.y, p0, ge);
+      }
+      // f terms with a+b even are real; g terms take the opposite part
+      const bool odd = aa & 1;
+      const float Tr = odd ? to : te, Ti = odd ? te : to;
+      const float Dr = odd ? ge : go, Di = odd ? go : ge;
+      xr = fmaf(pa_cur, Tr, xr);
+      xi = fmaf(pa_cur, Ti, xi);
+      dxr = fmaf(dpa, Tr, dxr);
+      dxi = fmaf(dpa, Ti, dxi);
+      dyr = fmaf(pa_cur, Dr, dyr);
+      dyi = fmaf(pa_cur, Di, dyi);
+      pa_prev = pa_cur;
+      pa_cur = pa_next;
     }
     if (valid) {
-      const float fx = x / (float)a.beta1, fy = y / (float)a.beta2;
-      d1r *= fx; d1i *= fx;
-      d2r *= fy; d2i *= fy;
       // Re(Y * (pr + i pi)) = yr pr - yi pi
-      const float re_xi = yr * xr - yi * xi;          // Re(conj(W) V) / S_ref
-      const float im_xi = yr * xi + yi * xr;          // Im(conj(W) V) / S_ref
-      const float nuc = ci.x;                          // nu / c
-      const float u = __ldg(a.uvw + 3 * (size_t)row), v = __ldg(a.uvw + 3 * (size_t)row + 1),
-                  w = __ldg(a.uvw + 3 * (size_t)row + 2);
+      const float re_xi = yr * xr - yi * xi;  // Re(conj(W) V) / S_ref
+      const float im_xi = yr * xi + yi * xr;  // Im(conj(W) V) / S_ref
+      const float re_dx = yr * dxr - yi * dxi, re_dy = yr * dyr - yi * dyi;
+      const float nuc = ci.x;                 // nu / c
+      const float* xu = a.uvw_pairs + 6 * (size_t)row;
+      const float u = __ldg(xu), v = __ldg(xu + 2), w = __ldg(xu + 4);
       acc32[0] += -2.0f * re_xi;
       acc32[1] += -2.0f * re_xi * fmaf(ci.z, 0.6931471805599453f, a.lnref_nu0_f);
       acc32[2] += -4.0f * (float)kPi * nuc * (u - w * a.l_over_n) * im_xi;
       acc32[3] += -4.0f * (float)kPi * nuc * (v - w * a.m_over_n) * im_xi;
-      acc32[4] += -2.0f * (yr * d1r - yi * d1i);
-      acc32[5] += -2.0f * (yr * d2r - yi * d2i);
-      acc32[6] += -2.0f * (yr * dpr - yi * dpi);
+      acc32[4] += -2.0f * re_dx * x * ib1;
+      acc32[5] += -2.0f * re_dy * y * ib2;
+      acc32[6] += -2.0f * (re_dx * rb * y - re_dy * rb2 * x);
     }
     if (++nacc == 16) {
 #pragma unroll
@@ -352,8 +432,8 @@ __global__ void __launch_bounds__(K4S_T) k4_grad_shape(const K4SArgs a) {
     }
     __syncthreads();
     // coefficient gradients for this tile
-    const int nv = (int)min((long long)K4S_T, a.n_vis - tile * K4S_T);
-    for (int k = t; k < a.nnz; k += K4S_T) {
+    const int nv = (int)min((long long)T, a.n_vis - tile * T);
+    for (int k = t; k < a.nnz; k += T) {
       const int na = __ldg(a.n1 + k), nb = __ldg(a.n2 + k);
       const int ph = (na + nb) & 3;
       const float* wsel = (ph & 1) ? wim : wre;
@@ -365,42 +445,59 @@ __global__ void __launch_bounds__(K4S_T) k4_grad_shape(const K4SArgs a) {
     __syncthreads();
   }
   // per-CTA partials (the flux factor of every group but the flux one is applied here, in FP64)
-  for (int k = t; k < a.nnz; k += K4S_T) a.part_c[(size_t)blockIdx.x * a.nnz + k] = accc[k] * a.flux;
+  for (int k = t; k < a.nnz; k += T) a.part_c[(size_t)blockIdx.x * a.nnz + k] = accc[k] * flux;
   __shared__ double red[K4S_T][K4S_NS];
-  for (int i = 0; i < K4S_NS; ++i) red[t][i] = (accs[i] + (double)acc32[i]) * (i == 0 ? 1.0 : a.flux);
+  for (int i = 0; i < K4S_NS; ++i) red[t][i] = (accs[i] + (double)acc32[i]) * (i == 0 ? 1.0 : flux);
   __syncthreads();
   if (t < K4S_NS) {
     double s = 0.0;
-    for (int q = 0; q < K4S_T; ++q) s += red[q][t];
+    for (int q = 0; q < T; ++q) s += red[q][t];
     a.part_s[(size_t)blockIdx.x * K4S_NS + t] = s;
   }
 }
 
+// One warp per output (coefficient or scalar group): lanes add strided per-CTA partials, then a fixed
+// butterfly; deterministic.
 __global__ void k4_reduce_shape(const double* part_s, const double* part_c, int grid, int nnz, int j, int q,
                                 double* gflux, double* galpha, double* gl, double* gm, double* gb1, double* gb2,
                                 double* gpa, double* gcoeff, int coeff_off, int first) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (t >= nnz + K4S_NS) return;
   auto put = [&](double* p, int idx, double v) {
     if (p) p[idx] = first ? v : p[idx] + v;
   };
+  double s = 0.0;
   if (t < nnz) {
-    double s = 0.0;
-    for (int c = 0; c < grid; ++c) s += part_c[(size_t)c * nnz + t];
+    for (int c = lane; c < grid; c += 32) s += part_c[(size_t)c * nnz + t];
+  } else {
+    for (int c = lane; c < grid; c += 32) s += part_s[(size_t)c * K4S_NS + (t - nnz)];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane != 0) return;
+  if (t < nnz) {
     put(gcoeff, coeff_off + t, s);
+    return;
   }
-  if (t < K4S_NS) {
-    double s = 0.0;
-    for (int c = 0; c < grid; ++c) s += part_s[(size_t)c * K4S_NS + t];
-    switch (t) {
-      case 0: put(gflux, j, s); break;
-      case 1: put(galpha, j, s); break;
-      case 2: put(gl, j, s); break;
-      case 3: put(gm, j, s); break;
-      case 4: put(gb1, q, s); break;
-      case 5: put(gb2, q, s); break;
-      default: put(gpa, q, s); break;
-    }
+  switch (t - nnz) {
+    case 0: put(gflux, j, s); break;
+    case 1: put(galpha, j, s); break;
+    case 2: put(gl, j, s); break;
+    case 3: put(gm, j, s); break;
+    case 4: put(gb1, q, s); break;
+    case 5: put(gb2, q, s); break;
+    default: put(gpa, q, s); break;
   }
+}
+
+// (u, v, w) of every row split into float pairs for the double-float phase arguments.
+__global__ void k4_split_uvw(const double* uvw, int n_rows, float* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 3 * n_rows) return;
+  float h, l;
+  split_double(uvw[i], h, l);
+  out[2 * i] = h;
+  out[2 * i + 1] = l;
 }
 
 // L = sum |R|^2: FP32 per thread over a grid-stride run, FP64 from there on, fixed order.
@@ -483,13 +580,14 @@ int launch_grad(wn_ctx* ctx, const ObsDev& o, const Model* M, const PeelArgs& pa
   const int rows_per_chunk = (o.n_rows + chunks - 1) / chunks;
   int max_nnz = 0;
   for (int q = 0; q < M->n_shape; ++q) max_nnz = std::max(max_nnz, M->s_off_host[q + 1] - M->s_off_host[q]);
-  const int sgrid = ctx->num_sms * 8;
+  const int sgrid = ctx->num_sms * 4;
   const size_t chan_bytes = ((size_t)o.n_chan * sizeof(float4) + 255) & ~(size_t)255;
   const size_t row_bytes = ((size_t)o.n_rows * sizeof(float4) + 255) & ~(size_t)255;
+  const size_t uvp_bytes = ((size_t)o.n_rows * 6 * sizeof(float) + 255) & ~(size_t)255;
   const size_t loss_bytes = ((size_t)loss_blocks * 8 + 255) & ~(size_t)255;
   const size_t pg_bytes = ((size_t)chunks * n_pg * K4_NG * 8 + 255) & ~(size_t)255;
   const size_t sh_bytes = M->n_shape ? (((size_t)sgrid * (K4S_NS + max_nnz) * 8 + 255) & ~(size_t)255) : 0;
-  const size_t need = chan_bytes + row_bytes + loss_bytes + pg_bytes + sh_bytes;
+  const size_t need = chan_bytes + row_bytes + uvp_bytes + loss_bytes + pg_bytes + sh_bytes;
   if (ctx->ws2_bytes < need) {
     if (ctx->ws2) {
       cudaStreamSynchronize(st);
@@ -504,9 +602,12 @@ int launch_grad(wn_ctx* ctx, const ObsDev& o, const Model* M, const PeelArgs& pa
   char* ws = static_cast<char*>(ctx->ws2);
   float4* chaninfo = reinterpret_cast<float4*>(ws);
   float4* rowinfo = reinterpret_cast<float4*>(ws + chan_bytes);
-  double* lpart = reinterpret_cast<double*>(ws + chan_bytes + row_bytes);
-  double* pgpart = reinterpret_cast<double*>(ws + chan_bytes + row_bytes + loss_bytes);
-  double* shpart = reinterpret_cast<double*>(ws + chan_bytes + row_bytes + loss_bytes + pg_bytes);
+  float* uvp = reinterpret_cast<float*>(ws + chan_bytes + row_bytes);
+  double* lpart = reinterpret_cast<double*>(ws + chan_bytes + row_bytes + uvp_bytes);
+  double* pgpart = reinterpret_cast<double*>(ws + chan_bytes + row_bytes + uvp_bytes + loss_bytes);
+  double* shpart = reinterpret_cast<double*>(ws + chan_bytes + row_bytes + uvp_bytes + loss_bytes + pg_bytes);
+  k4_split_uvw<<<(3 * o.n_rows + 255) / 256, 256, 0, st>>>(o.uvw, o.n_rows, uvp);
+  if (int r = cuda_err("uvw split")) return r;
 
   // 2. loss
   const size_t n_vis = (size_t)o.n_rows * o.n_chan;
@@ -520,7 +621,7 @@ int launch_grad(wn_ctx* ctx, const ObsDev& o, const Model* M, const PeelArgs& pa
     const int npass = (o.n_chan + 32 * K4_KMAX - 1) / (32 * K4_KMAX);
     for (int p = 0; p < npass; ++p) {
       K4Args a;
-      a.uvw = o.uvw;
+      a.uvw_pairs = uvp;
       a.freq = o.freq;
       a.n_rows = o.n_rows;
       a.n_chan = o.n_chan;
@@ -562,7 +663,7 @@ int launch_grad(wn_ctx* ctx, const ObsDev& o, const Model* M, const PeelArgs& pa
     K4SArgs a;
     a.rowinfo = rowinfo;
     a.chaninfo = chaninfo;
-    a.uvw = o.uvw;
+    a.uvw_pairs = uvp;
     a.n_rows = o.n_rows;
     a.n_chan = o.n_chan;
     a.n_base = o.n_base;
@@ -572,40 +673,34 @@ int launch_grad(wn_ctx* ctx, const ObsDev& o, const Model* M, const PeelArgs& pa
     a.n1 = M->m_n1() + M->s_off_host[q];
     a.n2 = M->m_n2() + M->s_off_host[q];
     a.coeff = M->s_coeff + M->s_off_host[q];
-    a.l = h.l;
-    a.m = h.m;
-    a.nm1 = h.nm1;
-    a.lnref_nu0 = (L0 - h.lref) * 0.6931471805599453;
-    a.lnref_nu0_f = (float)a.lnref_nu0;
+    a.lnref_nu0_f = (float)((L0 - h.lref) * 0.6931471805599453);
     a.l_over_n = (float)(h.l / (1.0 + h.nm1));
     a.m_over_n = (float)(h.m / (1.0 + h.nm1));
     a.c_amp = (float)((double)h.alpha * (L0 - h.lref));  // flux-free
     a.alpha = h.alpha;
-    a.sgn = h.sgn;
-    double hostv[4];
-    cudaMemcpyAsync(hostv, M->r_flux() + j, sizeof(double), cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(hostv + 1, M->r_sb1() + q, sizeof(double), cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(hostv + 2, M->r_sb2() + q, sizeof(double), cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(hostv + 3, M->r_spa() + q, sizeof(double), cudaMemcpyDeviceToHost, st);
-    cudaStreamSynchronize(st);
-    a.flux = hostv[0];
-    a.beta1 = hostv[1];
-    a.beta2 = hostv[2];
-    a.pa = hostv[3];
+    a.flux = M->r_flux() + j;
+    a.beta1 = M->r_sb1() + q;
+    a.beta2 = M->r_sb2() + q;
     a.resid = resid;
     a.peel = pa;
     a.part_s = shpart;
     a.part_c = shpart + (size_t)sgrid * K4S_NS;
     a.err = ctx->d_err;
-    const int ld = h.nmax + 3;
-    const size_t smem = (size_t)(2 * K4S_T * ld + 2 * K4S_T + 2) * 4 + (size_t)a.nnz * 8 + 16;
-    if (smem > 227 * 1024) return set_error(WN_EINVAL, "adjoint: shapelet too large for the shared-memory reduction");
+    // static shared memory: the 128 x 7 FP64 reduction array
+    const size_t smax = 227 * 1024 - sizeof(double) * K4S_T * K4S_NS;
+    int T = K4S_T;
+    size_t smem = (size_t)k4s_layout(h.nmax, a.nnz, T).total;
+    if (smem > smax) {
+      T = K4S_T / 2;
+      smem = (size_t)k4s_layout(h.nmax, a.nnz, T).total;
+    }
+    if (smem > smax) return set_error(WN_EINVAL, "adjoint: shapelet too large for the shared-memory reduction");
     cudaFuncSetAttribute(k4_grad_shape, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k4_grad_shape<<<sgrid, K4S_T, smem, st>>>(a);
-    const int rt = std::max(a.nnz, K4S_NS);
-    k4_reduce_shape<<<(rt + 127) / 128, 128, 0, st>>>(shpart, shpart + (size_t)sgrid * K4S_NS, sgrid, a.nnz, j, q,
-                                                      g->flux, g->alpha, g->l, g->m, g->s_beta1, g->s_beta2, g->s_pa,
-                                                      g->s_coeff, M->s_off_host[q], 1);
+    k4_grad_shape<<<sgrid, T, smem, st>>>(a);
+    const int nout = a.nnz + K4S_NS;
+    k4_reduce_shape<<<(nout * 32 + 255) / 256, 256, 0, st>>>(shpart, shpart + (size_t)sgrid * K4S_NS, sgrid, a.nnz, j,
+                                                            q, g->flux, g->alpha, g->l, g->m, g->s_beta1, g->s_beta2,
+                                                            g->s_pa, g->s_coeff, M->s_off_host[q], 1);
     if (int r = cuda_err("shapelet adjoint")) return r;
   }
   return WN_OK;
