@@ -255,14 +255,16 @@ def bench_adjoint(wn, ctx, local, torch):
             "ms_per_step": round(ms, 4), "grad_evals_per_s": obs.n_vis * sky.n_comp / (ms * 1e-3)}
 
 
-def bench_serving(wn, ctx, local, torch, n_req=48, seed=17):
+def bench_serving(wn, ctx, local, torch, n_req=1000, n_templates=48, seed=17):
     """Seeded Poisson stream of predict/peel requests of uneven size (16-128 tiles, 1-14 steps, 32-384
-    channels, 100-50,000 P/G, 0-3 shapelets with n_max 10-80), models resident; the arrival rate is set
-    for ~70% GPU busy from the measured one-at-a-time service time."""
+    channels, 100-50,000 P/G, 0-3 shapelets with n_max 10-80), models resident.  Requests are drawn
+    uniformly from n_templates distinct (observation, sky, data) sets; the arrival rate is set for ~70%
+    GPU busy from the measured one-at-a-time service times.  The one-at-a-time reference is a FIFO in
+    front of single-request calls, played with the measured service time of each request alone."""
     from paper_2005_09316_b300.serve import Server, latency_summary, poisson_arrivals, run_stream
     rng = np.random.default_rng(seed)
-    reqs, models = [], []
-    for i in range(n_req):
+    temps, models = [], []
+    for i in range(n_templates):
         n_ant = int(round(np.exp(rng.uniform(np.log(16), np.log(128)))))
         n_time = int(rng.integers(1, 15))
         n_chan = int(rng.integers(32, 385))
@@ -280,27 +282,31 @@ def bench_serving(wn, ctx, local, torch, n_req=48, seed=17):
             gains = torch.as_tensor(synth.make_gains(seed + 2000 + i, n_ant).astype(np.complex64)).cuda()
             data = torch.randn((n_time, obs.n_base, n_chan), dtype=torch.complex64, device=f"cuda:{local}",
                                generator=torch.Generator(device=f"cuda:{local}").manual_seed(i))
-        reqs.append((d, m, gains, data))
-    # one-at-a-time service times (each request alone, synchronously)
-    svc = []
-    for d, m, gains, data in reqs:
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        (ctx.predict(d, m) if data is None else ctx.peel(d, m, gains, data))
-        torch.cuda.synchronize()
-        svc.append(time.perf_counter() - t0)
-    svc = svc  # first call of each size includes no compilation (kernels are prebuilt)
+        temps.append((d, m, gains, data))
+    # one-at-a-time service time of each template (each alone, synchronously; median of 3)
+    svc_t = []
+    for d, m, gains, data in temps:
+        ts = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            (ctx.predict(d, m) if data is None else ctx.peel(d, m, gains, data))
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        svc_t.append(float(np.median(ts)))
+    pick = np.random.default_rng(seed + 1).integers(0, n_templates, size=n_req)
+    reqs = [temps[k] for k in pick]
+    svc = [svc_t[k] for k in pick]
     mean_s = float(np.mean(svc))
     rate = 0.7 / mean_s
     arrivals = poisson_arrivals(np.random.default_rng(seed), rate, n_req)
-    # one-at-a-time launches at the same arrival times: a FIFO in front of single-request calls
     lat_serial, t_free = [], 0.0
     for a, s_ in zip(arrivals, svc):
         start = max(a, t_free)
         t_free = start + s_
         lat_serial.append(t_free - a)
-    max_rows = max(r[0].n_rows for r in reqs)
-    srv = Server(ctx, n_streams=3, pool_bytes=6 << 30, max_inflight=32, max_rows=max_rows, max_chan=384)
+    max_rows = max(r[0].n_rows for r in temps)
+    srv = Server(ctx, n_streams=6, pool_bytes=6 << 30, max_inflight=32, max_rows=max_rows, max_chan=384)
     results, wall = run_stream(srv, reqs, arrivals)
     st = srv.stats()
     srv.close()
@@ -308,12 +314,14 @@ def bench_serving(wn, ctx, local, torch, n_req=48, seed=17):
         m.free()
     total_evals = sum(r[0].n_vis * r[1].n_comp for r in reqs)
     lat = latency_summary(results)
-    return {"workload": f"serving: {n_req} Poisson requests, 16-128 tiles, 1-14 steps, 32-384 ch, "
-                        "100-50000 P/G + 0-3 shapelets (n_max 10-80)",
+    return {"workload": f"serving: {n_req} Poisson requests drawn from {n_templates} uneven request sets "
+                        "(16-128 tiles, 1-14 steps, 32-384 ch, 100-50000 P/G + 0-3 shapelets n_max 10-80)",
             "rate_hz": round(rate, 2), "mean_service_ms": round(1e3 * mean_s, 3),
             "p50_ms": round(lat["p50_ms"], 3), "p99_ms": round(lat["p99_ms"], 3),
             "one_at_a_time_p50_ms": round(1e3 * float(np.percentile(lat_serial, 50)), 3),
             "one_at_a_time_p99_ms": round(1e3 * float(np.percentile(lat_serial, 99)), 3),
+            "service_alone_p50_ms": round(1e3 * float(np.percentile(svc, 50)), 3),
+            "service_alone_p99_ms": round(1e3 * float(np.percentile(svc, 99)), 3),
             "throughput_evals_per_s": total_evals / wall, "wall_s": round(wall, 3),
             "batches": st["batches"], "max_batches_in_flight": st["max_batches_in_flight"],
             "max_batch_requests": st["max_batch_requests"]}
@@ -452,6 +460,12 @@ def main():
                              "algorithmic_bytes": 16 * obs.n_vis + 24 * obs.n_rows,
                              "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (derived, not measured)",
                              "ops_per_eval": OPS_PER_EVAL}
+        try:  # measured pipe rates (microbenchmarks in the library), for context beside the derived peak
+            pr = ctx.pipe_rates()
+            extra["roofline"]["measured_pipes_Tops"] = {k: round(v / 1e12, 3) for k, v in pr.items()}
+            extra["roofline"]["frac_of_measured_ffma"] = round(achieved / (pr["ffma"] / 1e12), 4)
+        except Exception as exc:  # noqa: BLE001 - reported, not fatal
+            extra["roofline"]["measured_pipes_Tops"] = f"unavailable: {exc}"
         if clocks.get("sm_mhz"):
             extra["roofline"]["frac_at_sampled_clock"] = round(
                 achieved / (n_sm * FP32_LANES_PER_SM * clocks["sm_mhz"] * 1e6 / 1e12), 4)

@@ -248,6 +248,15 @@ WN_API int wn_server_stats(wn_server* srv, double* stats);
  * The model must already be resident (wn_sky_upload) and the context created beforehand. */
 WN_API int wn_predict_static(wn_ctx* ctx, const wn_obs* obs, int model_id, void* vis_c64, int accumulate, void* stream);
 
+/* ---- measurement ------------------------------------------------------------------------------ */
+
+/* Measured pipe throughputs of the context's GPU, for the roofline fractions of the phasor kernels (no
+ * paper counterpart).  rates (4 doubles, lane operations per second): FP32 FMA, FP32 FMA issued as
+ * packed f32x2 (each counting two), MUFU ex2, FP64 FMA.  Each is the best of three timed launches of a
+ * kernel running eight independent dependency chains per thread over 8 CTAs of 256 threads per SM;
+ * it allocates a small scratch buffer and synchronises its own stream.  Takes a few milliseconds. */
+WN_API int wn_pipe_rates(wn_ctx* ctx, double* rates);
+
 #ifdef __cplusplus
 }
 #endif

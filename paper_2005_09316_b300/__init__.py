@@ -28,7 +28,7 @@ EXPORTED = ("wn_create", "wn_destroy", "wn_last_error", "wn_version", "wn_set_pr
             "wn_sky_upload", "wn_sky_free", "wn_sky_bytes", "wn_predict", "wn_peel", "wn_peel_model",
             "wn_predict_grad", "wn_predict_static", "wn_server_create", "wn_server_destroy", "wn_server_submit",
             "wn_server_poll", "wn_server_wait", "wn_server_copy", "wn_server_release", "wn_server_cancel",
-            "wn_server_stats")
+            "wn_server_stats", "wn_pipe_rates")
 
 
 class WnError(RuntimeError):
@@ -252,6 +252,12 @@ class Context:
         v = ctypes.c_uint32()
         _check(load().wn_device_errors(self.h, ctypes.byref(v)))
         return int(v.value)
+
+    def pipe_rates(self) -> dict:
+        """Measured lane operations per second of the FP32 FMA, packed FFMA2, MUFU ex2 and FP64 FMA pipes."""
+        r = (ctypes.c_double * 4)()
+        _check(load().wn_pipe_rates(self.h, r))
+        return {"ffma": r[0], "ffma2": r[1], "mufu_ex2": r[2], "dfma": r[3]}
 
     def upload(self, sky, stream=None) -> Model:
         d = sky if isinstance(sky, dict) else sky_to_device(sky, f"cuda:{self.device}")

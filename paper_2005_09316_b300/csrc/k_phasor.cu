@@ -313,7 +313,7 @@ __device__ __forceinline__ void k1_tile(const K1Args& a, const int bx, const int
       } else {
         float2 G;
         if (!gain_product(a.peel, row, a.n_base, f, G)) atomicOr(a.err, WN_DEVERR_ANTENNA);
-        const float2 d = a.peel.data[idx];
+        const float2 d = a.mode == OUT_SUBG ? a.out[idx] : a.peel.data[idx];
         a.out[idx] = make_float2(d.x - (G.x * v.x - G.y * v.y), d.y - (G.x * v.y + G.y * v.x));
       }
     }

@@ -1,0 +1,111 @@
+// Pipe-throughput microbenchmarks: the rates the roofline fractions of the phasor kernels are read
+// against.  Each kernel runs eight independent dependency chains per thread (enough to hide the
+// pipe latency at 8 CTAs of 256 threads per SM) for a fixed iteration count; the host times the
+// launch with CUDA events (best of three) and converts to lane operations per second.
+#include "wn_internal.cuh"
+
+namespace wn {
+
+constexpr int KP_CHAINS = 8;
+
+__global__ void kp_ffma(float* out, int iters, float a, float b) {
+  float x[KP_CHAINS];
+#pragma unroll
+  for (int i = 0; i < KP_CHAINS; ++i) x[i] = threadIdx.x * 1e-3f + i;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < KP_CHAINS; ++i) x[i] = fmaf(x[i], a, b);
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int i = 0; i < KP_CHAINS; ++i) s += x[i];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+__global__ void kp_ffma2(float* out, int iters, float a, float b) {
+  float2 x[KP_CHAINS];
+#pragma unroll
+  for (int i = 0; i < KP_CHAINS; ++i) x[i] = make_float2(threadIdx.x * 1e-3f + i, 0.5f * i);
+  const float2 a2 = make_float2(a, a), b2 = make_float2(b, b);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < KP_CHAINS; ++i) x[i] = __ffma2_rn(x[i], a2, b2);
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int i = 0; i < KP_CHAINS; ++i) s += x[i].x + x[i].y;
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+__global__ void kp_ex2(float* out, int iters, float a) {
+  float x[KP_CHAINS];
+#pragma unroll
+  for (int i = 0; i < KP_CHAINS; ++i) x[i] = threadIdx.x * 1e-6f + i * 1e-3f;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < KP_CHAINS; ++i) x[i] = ex2_approx(x[i]) * a;
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int i = 0; i < KP_CHAINS; ++i) s += x[i];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+__global__ void kp_dfma(float* out, int iters, double a, double b) {
+  double x[KP_CHAINS];
+#pragma unroll
+  for (int i = 0; i < KP_CHAINS; ++i) x[i] = threadIdx.x * 1e-3 + i;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < KP_CHAINS; ++i) x[i] = fma(x[i], a, b);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < KP_CHAINS; ++i) s += x[i];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = (float)s;
+}
+
+}  // namespace wn
+
+using namespace wn;
+
+extern "C" int wn_pipe_rates(wn_ctx* ctx, double* rates) {
+  if (!ctx || !rates) return set_error(WN_EINVAL, "NULL argument");
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaError_t e = cudaSetDevice(ctx->device);
+  const int blocks = ctx->num_sms * 8, threads = 256;
+  float* out = nullptr;
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaMalloc(&out, sizeof(float) * blocks * threads);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  const int iters[4] = {1 << 14, 1 << 13, 1 << 12, 1 << 9};
+  const double per_iter[4] = {KP_CHAINS, 2.0 * KP_CHAINS, KP_CHAINS, KP_CHAINS};  // lane operations
+  for (int kind = 0; kind < 4 && e == cudaSuccess; ++kind) {
+    float best = 1e30f;
+    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+      e = cudaEventRecord(e0, st);
+      if (kind == 0) kp_ffma<<<blocks, threads, 0, st>>>(out, iters[0], 0.999f, 1e-3f);
+      else if (kind == 1) kp_ffma2<<<blocks, threads, 0, st>>>(out, iters[1], 0.999f, 1e-3f);
+      else if (kind == 2) kp_ex2<<<blocks, threads, 0, st>>>(out, iters[2], 0.999f);
+      else kp_dfma<<<blocks, threads, 0, st>>>(out, iters[3], 0.999, 1e-3);
+      if (e == cudaSuccess) e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess && ms < best) best = ms;
+    }
+    rates[kind] = (double)blocks * threads * iters[kind] * per_iter[kind] / (best * 1e-3);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st) cudaStreamDestroy(st);
+  cudaFree(out);
+  cudaSetDevice(prev);
+  if (e != cudaSuccess) return set_error(WN_ECUDA, std::string("pipe-rate probe: ") + cudaGetErrorString(e));
+  return WN_OK;
+}

@@ -13,7 +13,10 @@
 //    work overlaps the batches in flight;
 //  * time slicing: a batch carries at most ~kBatchBudget of estimated GPU work; a request larger than
 //    that takes a low-priority stream of its own and is issued there chunk by chunk (its shapelets with
-//    the last chunk), so small requests keep flowing on the other streams between its chunks;
+//    the last chunk), so small requests keep flowing on the other streams between its chunks.  Its
+//    point/Gaussian table is also cut into component ranges of at most ~kTileEvals evaluations per
+//    CTA tile (range 0 stores or peels, later ranges add or subtract on the same stream), so no CTA
+//    of a large request holds an SM for more than a few milliseconds;
 //  * completion: an event per batch, polled without blocking; the caller reads the result in place
 //    and releases it, which returns its pool space.
 // Every tile is computed by the same code in the same order as a single-request launch, so a request's
@@ -33,13 +36,15 @@ enum ReqState { RQ_PENDING = 0, RQ_ADMITTED = 1, RQ_RUNNING = 2, RQ_DONE = 3, RQ
 
 constexpr double kBatchBudget = 0.02;   // seconds of estimated GPU work per batch / chunk
 constexpr double kEvalRate = 3.0e12;    // component-visibility evaluations per second (estimate)
+constexpr double kTileEvals = 2.4e7;    // evaluations per CTA tile of a large request (~2 ms on one CTA)
 
 struct ServeReq {
   uint64_t ticket = 0;
   K1Args k1;              // batched-kernel arguments (set at admission)
   int gx = 0, gy = 0;     // tile grid of the phasor kernel
-  long tiles = 0, issued = 0;
-  double tile_cost = 0;   // estimated seconds per tile
+  long tiles = 0, issued = 0;  // tiles of one component range; work items issued (range-major)
+  int n_cc = 1, cc = 0;        // component ranges and components per range (large requests only)
+  double tile_cost = 0;        // estimated GPU seconds per tile of one component range
   int owner_slot = -1;    // slot that issues a large request's chunks
   ObsDev od;
   const Model* M = nullptr;
@@ -66,6 +71,7 @@ struct ServeSlot {
   int priority = 0;                // CUDA stream priority (lower number runs first)
   uint64_t owner = 0;              // large request whose chunks this slot issues (0: none)
   bool chunk_next = true;          // an owning slot's next launch: a chunk (else a small batch)
+  bool shapes = false;             // the launch in flight carries shapelet kernels
 };
 
 }  // namespace wn
@@ -152,6 +158,7 @@ static void launch_slot(wn_server* s, int k, int nwork, const std::vector<uint64
   }
   if (e == cudaSuccess) e = cudaEventRecord(sl.done, sl.st);
   sl.reqs = complete;
+  sl.shapes = !shapes.empty();
   if (e != cudaSuccess)
     for (uint64_t t : sl.reqs) {
       s->reqs[t].state = RQ_FAILED;
@@ -172,7 +179,21 @@ static int add_tiles(ServeReq& r, int slot_req, long from, long to, K1Work* work
   return nwork;
 }
 
-static bool is_large(const ServeReq& r) { return r.tiles > 0 && r.tile_cost * r.tiles > kBatchBudget; }
+static bool is_large(const ServeReq& r) { return r.tiles > 0 && r.tile_cost * r.tiles * r.n_cc > kBatchBudget; }
+
+// Kernel arguments of component range c of a request: the point/Gaussian table is points then
+// Gaussians, so a range is a contiguous slice with its own point / Gaussian counts.
+static K1Args range_args(const ServeReq& r, int c) {
+  K1Args a = r.k1;
+  if (r.n_cc <= 1) return a;
+  const int n_pg = r.k1.n_point + r.k1.n_gauss;
+  const int c0 = c * r.cc, c1 = std::min(n_pg, c0 + r.cc);
+  a.comps = r.k1.comps + c0;
+  a.n_point = std::max(0, std::min(r.k1.n_point, c1) - c0);
+  a.n_gauss = (c1 - c0) - a.n_point;
+  if (c > 0) a.mode = r.mode == OUT_PEEL ? OUT_SUBG : OUT_ACCUM;
+  return a;
+}
 
 // An admitted request that no launch has taken yet.
 static bool unstarted(const ServeReq& r) { return r.state == RQ_ADMITTED && r.issued == 0 && r.owner_slot < 0; }
@@ -195,11 +216,13 @@ static void launch_chunk(wn_server* s, int k) {
   ServeReq& r = s->reqs[sl.owner];
   std::vector<uint64_t> complete, shapes;
   const long per = std::max(1L, std::min((long)s->max_work, (long)(kBatchBudget / std::max(r.tile_cost, 1e-12))));
-  const long to = std::min(r.tiles, r.issued + per);
-  slot_args(s, sl)[0] = r.k1;
-  const int nwork = add_tiles(r, 0, r.issued, to, slot_work(s, sl), 0);
-  r.issued = to;
-  if (r.issued == r.tiles) {
+  // one component range per launch: two ranges of a tile must not run at once (they add to it in turn)
+  const int c = (int)(r.issued / r.tiles);
+  const long from = r.issued % r.tiles, to = std::min(r.tiles, from + per);
+  slot_args(s, sl)[0] = range_args(r, c);
+  const int nwork = add_tiles(r, 0, from, to, slot_work(s, sl), 0);
+  r.issued += to - from;
+  if (r.issued == r.tiles * r.n_cc) {
     r.state = RQ_RUNNING;
     r.batch = s->batches;
     r.owner_slot = -1;
@@ -242,7 +265,9 @@ static void launch_small(wn_server* s, int k) {
 
 // Fill the free slots.  Large requests claim the lowest-priority free slots (all but one, so small
 // requests always have a stream); small batches take the highest-priority free ones; a slot that owns a
-// large request alternates between its chunks and small batches while small requests wait.
+// large request alternates between its chunks and small batches while small requests wait.  While a
+// launch with shapelet kernels is on the GPU no new chunk starts: the shapelet kernel needs a whole SM,
+// which the phasor CTAs of back-to-back chunks would otherwise never leave free.
 static bool launch_ready(wn_server* s) {
   bool progress = false;
   const int ns = (int)s->slots.size();
@@ -267,9 +292,12 @@ static bool launch_ready(wn_server* s) {
     launch_small(s, k);
     progress = true;
   }
+  bool shapes_waiting = false;
+  for (auto& sl : s->slots) shapes_waiting |= sl.busy && sl.shapes;
   for (int k = 0; k < ns; ++k) {
     ServeSlot& sl = s->slots[k];
     if (sl.busy || !sl.owner) continue;
+    if (shapes_waiting && (sl.chunk_next || !small_waiting(s))) continue;
     if (!sl.chunk_next && small_waiting(s)) {
       launch_small(s, k);
       sl.chunk_next = true;
@@ -327,7 +355,18 @@ static void scheduler(wn_server* s) {
           } else {
             r.tiles = (long)r.gx * r.gy;
             const double rows_tile = (double)r.od.n_rows / r.gx, chans_tile = (double)r.od.n_chan / r.gy;
-            r.tile_cost = rows_tile * chans_tile * (r.M->n_point + r.M->n_gauss) / kEvalRate;
+            const int n_pg = r.M->n_point + r.M->n_gauss;
+            r.n_cc = 1;
+            r.cc = n_pg;
+            if (rows_tile * chans_tile * n_pg * r.tiles / kEvalRate > kBatchBudget) {
+              // large: component ranges of whole 32-component TMA stages, at most kTileEvals per tile
+              const int cc = std::max(1024, (int)(kTileEvals / (rows_tile * chans_tile)) & ~31);
+              if (cc < n_pg) {
+                r.cc = cc;
+                r.n_cc = (n_pg + cc - 1) / cc;
+              }
+            }
+            r.tile_cost = rows_tile * chans_tile * r.cc / kEvalRate;
           }
         }
         r.t_admit = now_s(s);

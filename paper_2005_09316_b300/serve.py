@@ -120,36 +120,58 @@ def latency_summary(results) -> dict:
 
 def run_stream(server: Server, requests, arrivals, release=True, timeout=120.0):
     """Submit `requests` ((obs, model, gains, data) tuples) at the given arrival times (seconds from now)
-    while a consumer thread collects (and releases) each result as it completes; returns
-    (results in submission order, wall seconds)."""
-    import queue
+    while a consumer thread collects (and releases) every result as soon as it completes, in any order;
+    returns (results in submission order, wall seconds)."""
     import threading
 
     t0 = time.perf_counter()
-    pending = queue.Queue()
+    lock = threading.Lock()
+    outstanding = {}          # ticket -> submission index
     results = {}
     errors = []
+    submitted_all = threading.Event()
 
     def consume():
+        deadline = None
         while True:
-            item = pending.get()
-            if item is None:
+            with lock:
+                items = list(outstanding.items())
+            if not items and submitted_all.is_set():
                 return
-            i, t = item
-            try:
-                results[i] = server.wait(t, timeout)
-                if release:
-                    server.release(t)
-            except Exception as exc:  # surfaced after the join
-                errors.append(exc)
+            progressed = False
+            for t, i in items:
+                try:
+                    r = server.poll(t)
+                except Exception as exc:  # surfaced after the join
+                    errors.append(exc)
+                    r = None
+                if r is None or r.state in (REQ_DONE, REQ_FAILED, REQ_CANCELLED):
+                    if r is not None:
+                        results[i] = r
+                        if release:
+                            server.release(t)
+                    with lock:
+                        outstanding.pop(t, None)
+                    progressed = True
+            if not progressed:
+                if items and deadline is None:
+                    deadline = time.perf_counter() + timeout
+                if deadline is not None and time.perf_counter() > deadline:
+                    errors.append(TimeoutError("requests still outstanding"))
+                    return
+                time.sleep(2e-4)
+            else:
+                deadline = None
 
     th = threading.Thread(target=consume, daemon=True)
     th.start()
     for i, ((obs, model, gains, data), ta) in enumerate(zip(requests, arrivals)):
         while time.perf_counter() - t0 < ta:
             time.sleep(min(2e-4, max(0.0, ta - (time.perf_counter() - t0))))
-        pending.put((i, server.submit(obs, model, gains, data)))
-    pending.put(None)
+        t = server.submit(obs, model, gains, data)
+        with lock:
+            outstanding[t] = i
+    submitted_all.set()
     th.join()
     if errors:
         raise errors[0]

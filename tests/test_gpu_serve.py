@@ -146,3 +146,31 @@ def test_cancel_and_bounded_wait(wn, ctx):
     srv.close()
     for r in reqs:
         r[1].free()
+
+
+@pytest.mark.parametrize("peel", [False, True])
+def test_large_request_in_component_ranges(wn, ctx, peel):
+    """A request above the batch work budget is served in time slices over row tiles and component
+    ranges (range 0 stores or peels, later ranges add or subtract); its result matches the single call."""
+    from paper_2005_09316_b300.serve import Server
+    obs = synth.make_obs(71, 128, 3, synth.uniform_channels(167e6, 80e3, 384), layout="mwa")
+    sky = synth.make_sky(72, 16000, 4000, 1, fov=15 * synth.DEG, shape_nmax=20)
+    d = wn.obs_to_device(obs)
+    m = ctx.upload(sky)
+    gains = data = None
+    if peel:
+        gains = torch.as_tensor(synth.make_gains(73, obs.n_ant).astype(np.complex64)).cuda()
+        data = torch.randn(obs.n_time, obs.n_base, obs.n_chan, dtype=torch.complex64, device="cuda",
+                           generator=torch.Generator(device="cuda").manual_seed(74))
+    srv = Server(ctx, n_streams=2, pool_bytes=1 << 30, max_inflight=4, max_rows=obs.n_rows, max_chan=384)
+    t = srv.submit(d, m, gains, data)
+    assert srv.wait(t, 120).state == 3
+    got = srv.result_tensor(t, d).cpu().numpy()
+    srv.release(t)
+    st = srv.stats()
+    srv.close()
+    assert st["batches"] >= 4, st            # several launches: tile chunks of several component ranges
+    ref = solo(ctx, (d, m, gains, data))
+    assert e_norm(got, ref) <= 1e-5
+    assert ctx.device_errors() == 0
+    m.free()
