@@ -112,3 +112,28 @@ def test_adjoint_full_size_sampled_components(wn, ctx):
         assert rel(got[name][idx], ref[name]) <= 2e-3, name
     for name in ("s_beta1", "s_beta2", "s_pa", "s_coeff"):
         assert rel(got[name], ref[name]) <= 2e-3, name
+
+
+def test_time_slices_add_up_to_the_whole_observation(wn, ctx):
+    """The sharded adjoint's exchange step rests on additivity over rows: the gradients and losses of
+    time slices (views of one device observation, as shard.time_slice makes them, with time-dependent
+    gains sliced alongside) add up to those of the whole observation."""
+    from paper_2005_09316_b300 import shard
+    obs, sky, gains, data, G, V = problem(61, n_time=3)
+    d = wn.obs_to_device(obs)
+    m = ctx.upload(sky)
+    gd = torch.as_tensor(gains.astype(np.complex64)).cuda()
+    dd = torch.as_tensor(data.astype(np.complex64).reshape(obs.n_time, obs.n_base, obs.n_chan)).cuda()
+    full = ctx.predict_grad(d, m, gd, dd)
+    parts = []
+    for r in range(2):
+        t0, t1 = shard.time_partition(obs.n_time, 2, r)
+        parts.append(ctx.predict_grad(shard.time_slice(d, t0, t1), m, gd[t0:t1], dd[t0:t1]))
+    torch.cuda.synchronize()
+    for k in shard.GRAD_KEYS:
+        if full[k] is None or not full[k].numel():
+            continue
+        s = (parts[0][k] + parts[1][k]).cpu().numpy()
+        assert rel(s, full[k].cpu().numpy()) <= 1e-5, k
+    m.free()
+    assert ctx.device_errors() == 0
