@@ -1,10 +1,12 @@
-"""FP64 CPU oracle for direct measurement-equation prediction, peeling and its gradient.
+"""FP64 CPU oracle for direct measurement-equation prediction, peeling, its gradient and the gain
+calibration loop.
 
 TEST INFRASTRUCTURE ONLY: imported by tests/, by ``__graft_entry__.smoke()`` and by the
 ``cpu_baseline`` / ``--impl reference`` legs of bench.py, never by the library itself.
 
 The arithmetic lives in ``wn_oracle.c`` (plain C, FP64, loops in the paper's order); this module
-builds it with gcc, loads it with ctypes and marshals numpy arrays.  It also holds the oracle's own
+builds it with gcc, loads it with ctypes and marshals numpy arrays.  The calibration loop is numpy
+(design matrix written out, numpy's solve for the normal equations).  It also holds the oracle's own
 packers (triangular coefficient index, parity split of the (-i)^(n1+n2) phase, bf16 hi/lo split),
 written from the same definitions the CUDA packer follows, so the two can be compared bit for bit.
 
@@ -246,3 +248,72 @@ def pack_coeff_bf16(nmax: int, n1, n2, c, k_pad: int, n_pad: int):
         dense[2 * b, :nmax + 1] = re[:, b]
         dense[2 * b + 1, :nmax + 1] = im[:, b]
     return bf16_hi_lo(dense)
+
+
+# ------------------------------------------------------------------------------------------------
+# Gain calibration (Sec. 5.1, eq:peeling-iter): per (time, channel), the linearised least squares for
+# additive per-antenna gain errors e, iterated.  Model M_ij = g_i conj(g_j) I_ij; residual
+# R_ij = V_ij - M_ij ~ e_i conj(g_j) I_ij + conj(e_j) g_i I_ij with the e e* term dropped.  Free
+# parameters Re(e_i), Im(e_i); the conjugation shows up as sign flips on Im(e_j).  The overall phase
+# of the gains is not determined by the data (g -> g e^{i phi} leaves M unchanged), so A^T A is
+# singular as printed; the oracle fixes the gauge by holding Im(e_0) = 0 (antenna 0's column dropped),
+# the same rule as the CUDA path.  numpy's solve is the library step for [A^T A]^{-1} A^T b.
+# ------------------------------------------------------------------------------------------------
+
+def calib_columns(n_ant: int):
+    """Column of Re(e_i) and of Im(e_i) in the parameter vector x (Im(e_0) has none: -1)."""
+    re = np.array([0] + [2 * i - 1 for i in range(1, n_ant)], dtype=np.int64)
+    im = np.array([-1] + [2 * i for i in range(1, n_ant)], dtype=np.int64)
+    return re, im
+
+
+def calib_design(ant1, ant2, n_ant: int, I, V, g):
+    """Design matrix A [2B, 2A-1] and residual vector b [2B] of one (time, channel) at gains g [A]:
+    rows 2k, 2k+1 are Re and Im of R for baseline k = (i, j)."""
+    ant1, ant2 = np.asarray(ant1), np.asarray(ant2)
+    I, V, g = np.asarray(I, complex), np.asarray(V, complex), np.asarray(g, complex)
+    B = ant1.size
+    re, im = calib_columns(n_ant)
+    gi, gj = g[ant1], g[ant2]
+    R = V - gi * np.conj(gj) * I
+    a = np.conj(gj) * I        # coefficient of e_i
+    c = gi * I                 # coefficient of conj(e_j)
+    A = np.zeros((2 * B, 2 * n_ant - 1))
+    rows_re, rows_im = 2 * np.arange(B), 2 * np.arange(B) + 1
+    # e_i a:  Re -> x_i Re a - y_i Im a ;  Im -> x_i Im a + y_i Re a
+    A[rows_re, re[ant1]] += a.real
+    A[rows_im, re[ant1]] += a.imag
+    ok = im[ant1] >= 0
+    A[rows_re[ok], im[ant1][ok]] += -a.imag[ok]
+    A[rows_im[ok], im[ant1][ok]] += a.real[ok]
+    # conj(e_j) c:  Re -> x_j Re c + y_j Im c ;  Im -> x_j Im c - y_j Re c
+    A[rows_re, re[ant2]] += c.real
+    A[rows_im, re[ant2]] += c.imag
+    ok = im[ant2] >= 0
+    A[rows_re[ok], im[ant2][ok]] += c.imag[ok]
+    A[rows_im[ok], im[ant2][ok]] += -c.real[ok]
+    b = np.empty(2 * B)
+    b[0::2], b[1::2] = R.real, R.imag
+    return A, b
+
+
+def calib_step(ant1, ant2, n_ant: int, I, V, g):
+    """One iteration: x = [A^T A]^{-1} A^T b, then g <- g + e.  Returns the new gains [A]."""
+    A, b = calib_design(ant1, ant2, n_ant, I, V, g)
+    x = np.linalg.solve(A.T @ A, A.T @ b)
+    re, im = calib_columns(n_ant)
+    e = x[re] + 1j * np.where(im >= 0, x[np.maximum(im, 0)], 0.0)
+    return np.asarray(g, complex) + e
+
+
+def calibrate(ant1, ant2, n_ant: int, I, V, g0, n_iter: int = 10):
+    """Gains [T, F, A] fitted per (time, channel) by n_iter iterations from g0 [T, F, A];
+    I (model) and V (data) are [T, B, F]."""
+    I, V = np.asarray(I, complex), np.asarray(V, complex)
+    g = np.array(g0, dtype=complex, copy=True)
+    T, _, F = I.shape
+    for t in range(T):
+        for f in range(F):
+            for _ in range(n_iter):
+                g[t, f] = calib_step(ant1, ant2, n_ant, I[t, :, f], V[t, :, f], g[t, f])
+    return g
