@@ -74,6 +74,7 @@ typedef enum {
 #define WN_DEVERR_ANTENNA 0x1u  /* an ant1/ant2 entry outside [0, n_ant) met by a peel */
 #define WN_DEVERR_TIMEOUT 0x2u  /* a bounded mbarrier / queue wait gave up */
 #define WN_DEVERR_SKY     0x4u  /* a sky entry rejected during upload */
+#define WN_DEVERR_CALIB   0x8u  /* a calibration solve met a non-positive pivot (its gains were kept) */
 
 /* An observation: baselines, time steps and channels (Sec. 3.2, last paragraph: uvw once per time
  * step, scaled per channel). */
@@ -247,6 +248,25 @@ WN_API int wn_server_stats(wn_server* srv, double* stats);
  * overlaps on the GPU (concurrent streams, devices sharing the process) race on it, so order them.
  * The model must already be resident (wn_sky_upload) and the context created beforehand. */
 WN_API int wn_predict_static(wn_ctx* ctx, const wn_obs* obs, int model_id, void* vis_c64, int accumulate, void* stream);
+
+/* ---- gain calibration ------------------------------------------------------------------------- */
+
+/* Fit one complex gain per antenna for every (time, channel): the linearised least squares of Sec. 5.1
+ * (eq:peeling-iter), iterated n_iter times (the paper uses 10).  With the model M = g_i conj(g_j) I
+ * and residual R = V - M, each iteration solves [A^T A] x = A^T b for the real and imaginary parts of
+ * additive gain errors e (the e e* term dropped) and sets g <- g + e.  The overall phase of the gains
+ * is not determined by the data, so the gauge is fixed by holding Im(e_0) = 0: antenna 0's imaginary
+ * part keeps its starting value.
+ *   model_c64  I, device [n_time][n_base][n_chan] complex64: the ideal model (e.g. from wn_predict);
+ *   data_c64   V, device [n_time][n_base][n_chan] complex64: the measured visibilities;
+ *   gains_c64  device [n_time][n_chan][n_ant] complex64: starting gains in, fitted gains out.
+ * Each antenna pair may appear at most once among the baselines (ant1 < ant2).  Requires
+ * n_ant <= 128 (the normal matrix of one (time, channel), 2 n_ant - 1 parameters, stays in shared
+ * memory) and 1 <= n_iter <= 1000; otherwise WN_EINVAL.  Solves run in FP32.  A problem whose normal
+ * matrix is not positive definite (for example an all-zero model) keeps its last gains and sets
+ * WN_DEVERR_CALIB.  Asynchronous on `stream`; uses the context's workspace. */
+WN_API int wn_calibrate(wn_ctx* ctx, const wn_obs* obs, const void* model_c64, const void* data_c64, void* gains_c64,
+                        int n_iter, void* stream);
 
 /* ---- measurement ------------------------------------------------------------------------------ */
 

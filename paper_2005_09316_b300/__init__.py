@@ -22,13 +22,13 @@ _lock = threading.Lock()
 WN_OK, WN_EINVAL, WN_ENOMEM, WN_ECUDA, WN_ETIMEOUT, WN_EBUSY, WN_ENOTFOUND = range(7)
 WN_PREC_MIXED, WN_PREC_FP64 = 0, 1
 WN_SHAPE_BF16X3, WN_SHAPE_BF16X1 = 0, 1
-WN_DEVERR_ANTENNA, WN_DEVERR_TIMEOUT, WN_DEVERR_SKY = 0x1, 0x2, 0x4
+WN_DEVERR_ANTENNA, WN_DEVERR_TIMEOUT, WN_DEVERR_SKY, WN_DEVERR_CALIB = 0x1, 0x2, 0x4, 0x8
 
 EXPORTED = ("wn_create", "wn_destroy", "wn_last_error", "wn_version", "wn_set_precision", "wn_device_errors",
             "wn_sky_upload", "wn_sky_free", "wn_sky_bytes", "wn_predict", "wn_peel", "wn_peel_model",
             "wn_predict_grad", "wn_predict_static", "wn_server_create", "wn_server_destroy", "wn_server_submit",
             "wn_server_poll", "wn_server_wait", "wn_server_copy", "wn_server_release", "wn_server_cancel",
-            "wn_server_stats", "wn_pipe_rates")
+            "wn_server_stats", "wn_calibrate", "wn_pipe_rates")
 
 
 class WnError(RuntimeError):
@@ -99,6 +99,8 @@ def load(build_if_missing: bool = True):
         L.wn_server_release.argtypes = [P, u64]
         L.wn_server_cancel.argtypes = [P, u64]
         L.wn_server_stats.argtypes = [P, ctypes.POINTER(dbl)]
+        L.wn_calibrate.argtypes = [P, ctypes.POINTER(WnObs), P, P, P, i, P]
+        L.wn_pipe_rates.argtypes = [P, ctypes.POINTER(dbl)]
         for name in EXPORTED:
             if name not in ("wn_destroy", "wn_last_error", "wn_version", "wn_server_destroy"):
                 getattr(L, name).restype = ctypes.c_int
@@ -252,6 +254,22 @@ class Context:
         v = ctypes.c_uint32()
         _check(load().wn_device_errors(self.h, ctypes.byref(v)))
         return int(v.value)
+
+    def calibrate(self, obs: DeviceObs, model_vis, data, gains=None, n_iter: int = 10, stream=None):
+        """Per-(time, channel) antenna gains fitted by n_iter iterations of the linearised least squares
+        (Sec. 5.1); gains [T][F][A] complex64 are updated in place (ones if not given) and returned."""
+        torch = _torch()
+        if gains is None:
+            gains = torch.ones((obs.n_time, obs.n_chan, obs.n_ant), dtype=torch.complex64,
+                               device=f"cuda:{self.device}")
+        for t, shape in ((model_vis, (obs.n_time, obs.n_base, obs.n_chan)), (data, (obs.n_time, obs.n_base, obs.n_chan)),
+                         (gains, (obs.n_time, obs.n_chan, obs.n_ant))):
+            if t.dtype != torch.complex64 or tuple(t.shape) != shape or not t.is_contiguous():
+                raise ValueError(f"expected a contiguous complex64 tensor of shape {shape}")
+        o = obs.struct()
+        _check(load().wn_calibrate(self.h, ctypes.byref(o), model_vis.data_ptr(), data.data_ptr(), gains.data_ptr(),
+                                   int(n_iter), _stream_handle(stream)))
+        return gains
 
     def pipe_rates(self) -> dict:
         """Measured lane operations per second of the FP32 FMA, packed FFMA2, MUFU ex2 and FP64 FMA pipes."""

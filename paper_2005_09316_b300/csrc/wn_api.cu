@@ -433,6 +433,21 @@ int wn_predict_grad(wn_ctx* ctx, const wn_obs* obs, int model_id, const void* ga
   return r == WN_OK ? ok() : r;
 }
 
+int wn_calibrate(wn_ctx* ctx, const wn_obs* obs, const void* model_c64, const void* data_c64, void* gains_c64,
+                 int n_iter, void* stream) {
+  if (!ctx || !model_c64 || !data_c64 || !gains_c64) return set_error(WN_EINVAL, "NULL argument");
+  ObsDev d;
+  if (int r = check_obs(obs, d)) return r;
+  if (n_iter < 1 || n_iter > 1000) return set_error(WN_EINVAL, "wn_calibrate: n_iter must be in [1, 1000]");
+  if (d.n_ant > 128) return set_error(WN_EINVAL, "wn_calibrate: at most 128 antennas");
+  if (((uintptr_t)model_c64 | (uintptr_t)data_c64 | (uintptr_t)gains_c64) & 7)
+    return set_error(WN_EINVAL, "wn_calibrate: complex64 arrays must be 8-byte aligned");
+  DeviceGuard g(ctx->device);
+  int r = launch_calibrate(ctx, d, static_cast<const float2*>(model_c64), static_cast<const float2*>(data_c64),
+                           static_cast<float2*>(gains_c64), n_iter, static_cast<cudaStream_t>(stream));
+  return r == WN_OK ? ok() : r;
+}
+
 // Allocation-free prediction: like wn_predict, but the shapelet launches take their per-row and
 // per-channel tables from a fixed device array instead of the context's workspace, so the call
 // makes no device allocation.  Points and Gaussians, and the FP64 form, need no scratch at all.

@@ -31,6 +31,16 @@ def test_library_exports_every_declared_symbol():
     assert set(wn.EXPORTED) == set(declared())
 
 
+def test_binding_declares_argument_types_for_every_entry_point():
+    # without argtypes ctypes passes Python ints as C int, which would truncate device pointers
+    import paper_2005_09316_b300 as wn
+    lib = wn.load()
+    for name in wn.EXPORTED:
+        if name in ("wn_last_error", "wn_version"):
+            continue  # take no arguments
+        assert getattr(lib, name).argtypes, name
+
+
 def test_version_string_without_a_device():
     import paper_2005_09316_b300 as wn
     assert "sm_103a" in wn.version()
