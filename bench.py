@@ -339,6 +339,9 @@ def run_case(case: str):
         obs, sky = synth.fornax(n_time=2)
     elif case == "adjoint":       # K4: the full adjoint workload
         obs, sky = synth.adjoint()
+    elif case == "calib":         # K7: gain calibration, 128 tiles x 2 steps x 384 ch, 10 iterations
+        obs, _ = synth.mwa(n_time=2)
+        sky = synth.make_sky(102, 2000, 500, 0)
     else:                         # K3: standalone peel of the full MWA observation
         obs, sky = synth.mwa()
     d = wn.obs_to_device(obs)
@@ -350,6 +353,13 @@ def run_case(case: str):
         model = torch.randn(shape, dtype=torch.complex64, device="cuda")
         fn = lambda: ctx.peel_model(d, gains, data, model, out=out)  # noqa: E731
         work = 24 * obs.n_vis
+    elif case == "calib":
+        m = ctx.upload(sky)
+        model = ctx.predict(d, m)
+        data = model * 1.01
+        g0 = torch.ones((obs.n_time, obs.n_chan, obs.n_ant), dtype=torch.complex64, device="cuda")
+        fn = lambda: ctx.calibrate(d, model, data, g0.clone(), n_iter=10)  # noqa: E731
+        work = obs.n_time * obs.n_chan * 10   # solves
     else:
         m = ctx.upload(sky)
         if case == "adjoint":
@@ -379,7 +389,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-extras", action="store_true", help="skip the shapelet, adjoint and serving reports")
-    ap.add_argument("--case", choices=["mwa_small", "fornax_small", "adjoint", "peel"],
+    ap.add_argument("--case", choices=["mwa_small", "fornax_small", "adjoint", "peel", "calib"],
                     help="run one small fixed case for profiling instead of the benchmark")
     args = ap.parse_args()
     if args.case:
