@@ -15,9 +15,11 @@
 //
 // One CTA per (time, channel) owns its problem through every iteration: gains and the packed lower
 // triangle of [A^T A | A^T b] (the right-hand side as an extra row, so the Cholesky factorisation also
-// does the forward substitution) stay in shared memory.  Warp w accumulates antennas w, w + 16, ...
-// over their incident baselines in a fixed order (no atomics on the sums), the factorisation is a
-// right-looking Cholesky in FP32 over all warps, and warp 0 back-substitutes.  A non-positive pivot
+// does the forward substitution) stay in shared memory as 32 x 32 tiles.  Warp w accumulates antennas
+// w, w + 16, ... over their incident baselines in a fixed order (no atomics on the sums).  The
+// factorisation is a tiled right-looking Cholesky in FP32: one warp factors the diagonal tile, a lane
+// per row solves the panel below it, and every warp updates trailing tiles with an 8 x 4 register
+// block per lane.  Warp 0 back-substitutes.  A non-positive pivot
 // stops the problem's iterations with the last gains kept and WN_DEVERR_CALIB set.
 #include "wn_internal.cuh"
 
@@ -87,58 +89,112 @@ __global__ void k7_incidence(const int* ant1, const int* ant2, int n_base, int n
   }
 }
 
+// Storage of the augmented lower triangle [A^T A | A^T b] in 32 x 32 tiles: tile (I, J), J <= I, at
+// index I (I + 1) / 2 + J, rows padded to 33 floats so a column of a tile is conflict-free.
+constexpr int K7_TS = 33;               // row stride of a tile
+constexpr int K7_TILE = 32 * K7_TS;     // floats per tile
+__device__ __forceinline__ float* k7_elem(float* T, int r, int c) {
+  return T + ((r >> 5) * ((r >> 5) + 1) / 2 + (c >> 5)) * K7_TILE + (r & 31) * K7_TS + (c & 31);
+}
+__device__ __forceinline__ float* k7_tile(float* T, int I, int J) { return T + (I * (I + 1) / 2 + J) * K7_TILE; }
+
+// Column C of the unblocked factorisation of a 32 x 32 diagonal tile held one row per lane; recursion
+// keeps every register index a compile-time constant.  n_here = rows of this tile that are part of the
+// system (pivots at or past it belong to the right-hand side row or the padding and are kept positive).
+template <int C>
+__device__ __forceinline__ void k7_diag_col(float (&row)[32], float* dinv, int lane, int n_here, int* s_bad) {
+  float piv = __shfl_sync(0xffffffffu, row[C], C);
+  if (!(piv > 0.f) || !isfinite(piv)) {
+    if (C < n_here && lane == 0) *s_bad = 1;
+    piv = 1.f;
+  }
+  const float rinv = rsqrtf(piv), l = piv * rinv;
+  if (lane == C) {
+    row[C] = l;
+    dinv[C] = rinv;
+  } else if (lane > C) {
+    row[C] *= rinv;
+  }
+  const float lc = row[C];
+#pragma unroll
+  for (int j = C + 1; j < 32; ++j) {
+    const float ljc = __shfl_sync(0xffffffffu, lc, j);  // L[j][C], held by lane j
+    if (lane >= j) row[j] -= lc * ljc;
+  }
+  if constexpr (C + 1 < 32) k7_diag_col<C + 1>(row, dinv, lane, n_here, s_bad);
+}
+
 __global__ void __launch_bounds__(K7_THREADS, 1) k7_calib(const K7Args a) {
   extern __shared__ __align__(16) unsigned char sm[];
   const int A = a.n_ant, n = 2 * A - 1;
-  float* N = reinterpret_cast<float*>(sm);                            // packed lower, (n+1)(n+2)/2
-  float* col = N + (n + 1) * (n + 2) / 2;                             // [n + 1]
-  float* x = col + n + 1;                                             // [n]
-  float2* g = reinterpret_cast<float2*>((reinterpret_cast<uintptr_t>(x + n + 1) + 7) & ~(uintptr_t)7);  // [A]
-  __shared__ float s_rinv;
+  const int NT = (n + 1 + 31) / 32;                                   // tile rows (row n is A^T b)
+  float* T = reinterpret_cast<float*>(sm);                            // NT (NT + 1) / 2 tiles
+  float* x = T + NT * (NT + 1) / 2 * K7_TILE;                         // [n]
+  float* dinv = x + NT * 32;                                          // [NT * 32]: 1 / L_kk
+  float2* g = reinterpret_cast<float2*>(dinv + NT * 32);              // [A]
   __shared__ int s_bad;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int t = blockIdx.x / a.n_chan, f = blockIdx.x % a.n_chan;
   float2* gout = a.gains + ((size_t)t * a.n_chan + f) * A;
   for (int i = tid; i < A; i += K7_THREADS) g[i] = gout[i];
   if (tid == 0) s_bad = 0;
-  const int packed = (n + 1) * (n + 2) / 2;
+  const int nfl = NT * (NT + 1) / 2 * K7_TILE;
   const size_t plane = (size_t)a.n_base * a.n_chan;
 
   for (int it = 0; it < a.n_iter; ++it) {
     __syncthreads();
-    for (int k = tid; k < packed; k += K7_THREADS) N[k] = 0.f;
+    for (int k = tid; k < nfl; k += K7_THREADS) T[k] = 0.f;
     __syncthreads();
+    // rows past the right-hand side row pad the last tile row: unit pivots
+    for (int r = n + 1 + tid; r < NT * 32; r += K7_THREADS) *k7_elem(T, r, r) = 1.f;
     // --- [A^T A | A^T b] at the current gains
     for (int i = warp; i < A; i += K7_WARPS) {
       float d = 0.f, br = 0.f, bi = 0.f;
-      for (int k = a.inc_off[i] + lane; k < a.inc_off[i + 1]; k += 32) {
-        const int e = a.inc_list[k], b = e >> 1;
-        const size_t idx = (size_t)t * plane + (size_t)b * a.n_chan + f;
-        const float2 I = a.model[idx], V = a.data[idx];
-        const int p = a.ant1[b], q = a.ant2[b];
-        const float2 gp = g[p], gq = g[q];
-        const float2 M = cmul(cmul(gp, cconj(gq)), I);
-        const float2 R = make_float2(V.x - M.x, V.y - M.y);
-        if ((e & 1) == 0) {
-          const float2 av = cmul(cconj(gq), I), cv = cmul(gp, I);
-          d += av.x * av.x + av.y * av.y;
-          const float2 aR = cmul(cconj(av), R);
-          br += aR.x;
-          bi += aR.y;
-          // the block of this baseline, rows of q (> p) and columns of p
-          const float2 ac = cmul(cconj(av), cv);
-          atomicAdd(&N[tri(col_re(q), col_re(p))], ac.x);
-          atomicAdd(&N[tri(col_im(q), col_re(p))], ac.y);
-          if (p > 0) {
-            atomicAdd(&N[tri(col_re(q), col_im(p))], ac.y);
-            atomicAdd(&N[tri(col_im(q), col_im(p))], -ac.x);
+      const int k0 = a.inc_off[i], k1 = a.inc_off[i + 1];
+      for (int kb = k0 + lane; kb < k1; kb += 4 * 32) {
+        // four gathers in flight per lane; the sums still run over k in increasing order
+        int ev[4];
+        float2 Iv[4], Vv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int k = kb + 32 * u;
+          ev[u] = k < k1 ? a.inc_list[k] : -1;
+          if (ev[u] >= 0) {
+            const size_t idx = (size_t)t * plane + (size_t)(ev[u] >> 1) * a.n_chan + f;
+            Iv[u] = a.model[idx];
+            Vv[u] = a.data[idx];
           }
-        } else {
-          const float2 cv = cmul(gp, I);
-          d += cv.x * cv.x + cv.y * cv.y;
-          const float2 cR = cmul(cconj(cv), R);
-          br += cR.x;
-          bi -= cR.y;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (ev[u] < 0) continue;
+          const int e = ev[u], b = e >> 1;
+          const float2 I = Iv[u], V = Vv[u];
+          const int p = a.ant1[b], q = a.ant2[b];
+          const float2 gp = g[p], gq = g[q];
+          const float2 M = cmul(cmul(gp, cconj(gq)), I);
+          const float2 R = make_float2(V.x - M.x, V.y - M.y);
+          if ((e & 1) == 0) {
+            const float2 av = cmul(cconj(gq), I), cv = cmul(gp, I);
+            d += av.x * av.x + av.y * av.y;
+            const float2 aR = cmul(cconj(av), R);
+            br += aR.x;
+            bi += aR.y;
+            // the block of this baseline, rows of q (> p) and columns of p
+            const float2 ac = cmul(cconj(av), cv);
+            atomicAdd(k7_elem(T, col_re(q), col_re(p)), ac.x);
+            atomicAdd(k7_elem(T, col_im(q), col_re(p)), ac.y);
+            if (p > 0) {
+              atomicAdd(k7_elem(T, col_re(q), col_im(p)), ac.y);
+              atomicAdd(k7_elem(T, col_im(q), col_im(p)), -ac.x);
+            }
+          } else {
+            const float2 cv = cmul(gp, I);
+            d += cv.x * cv.x + cv.y * cv.y;
+            const float2 cR = cmul(cconj(cv), R);
+            br += cR.x;
+            bi -= cR.y;
+          }
         }
       }
 #pragma unroll
@@ -148,52 +204,109 @@ __global__ void __launch_bounds__(K7_THREADS, 1) k7_calib(const K7Args a) {
         bi += __shfl_xor_sync(0xffffffffu, bi, o);
       }
       if (lane == 0) {
-        N[tri(col_re(i), col_re(i))] = d;
-        N[tri(n, col_re(i))] = br;  // right-hand side: row n
+        *k7_elem(T, col_re(i), col_re(i)) = d;
+        *k7_elem(T, n, col_re(i)) = br;  // right-hand side: row n
         if (i > 0) {
-          N[tri(col_im(i), col_im(i))] = d;
-          N[tri(n, col_im(i))] = bi;
+          *k7_elem(T, col_im(i), col_im(i)) = d;
+          *k7_elem(T, n, col_im(i)) = bi;
         }
       }
     }
-    // --- Cholesky of the leading n x n block; row n becomes L^{-1} (A^T b)
-    for (int k = 0; k < n; ++k) {
+    // --- tiled right-looking Cholesky of the augmented matrix; row n becomes L^{-1} (A^T b).  Pivots of
+    // row n and of the padding rows are not part of the system and are only kept positive.
+    for (int K = 0; K < NT; ++K) {
       __syncthreads();
-      if (tid == 0) {
-        float piv = N[tri(k, k)];
-        if (!(piv > 0.f) || !isfinite(piv)) {
-          s_bad = 1;
-          piv = 1.f;
+      if (warp == 0) {  // diagonal tile, unblocked, in registers: lane r holds row r, columns by shuffle
+        float* D = k7_tile(T, K, K);
+        float row[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) row[c] = D[lane * K7_TS + c];
+        k7_diag_col<0>(row, dinv + K * 32, lane, n - K * 32, &s_bad);
+#pragma unroll
+        for (int c = 0; c < 32; ++c) D[lane * K7_TS + c] = row[c];
+      }
+      __syncthreads();
+      // panel: X L_KK^T = A_IK for the tiles below; lane r solves row r of one tile, column by column
+      for (int I = K + 1 + warp; I < NT; I += K7_WARPS) {
+        float* P = k7_tile(T, I, K);
+        const float* D = k7_tile(T, K, K);
+        float xr[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) xr[c] = P[lane * K7_TS + c];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          xr[c] *= dinv[K * 32 + c];
+#pragma unroll
+          for (int j = c + 1; j < 32; ++j) xr[j] -= xr[c] * D[j * K7_TS + c];
         }
-        const float l = sqrtf(piv);
-        N[tri(k, k)] = l;
-        s_rinv = 1.0f / l;
+#pragma unroll
+        for (int c = 0; c < 32; ++c) P[lane * K7_TS + c] = xr[c];
       }
       __syncthreads();
-      const float rinv = s_rinv;
-      for (int j = k + 1 + tid; j <= n; j += K7_THREADS) {
-        const float v = N[tri(j, k)] * rinv;
-        N[tri(j, k)] = v;
-        col[j] = v;
-      }
-      __syncthreads();
-      for (int i = k + 1 + warp; i <= n; i += K7_WARPS) {
-        const float ci = col[i];
-        float* row = N + tri(i, 0);
-        const int jmax = min(i, n - 1);
-        for (int j = k + 1 + lane; j <= jmax; j += 32) row[j] -= ci * col[j];
+      // trailing update A_IJ -= L_IK L_JK^T, K < J <= I; a warp per tile, lane = 8 rows x 4 columns
+      const int m = NT - K - 1;
+      const int rg = lane >> 3, cg = lane & 7;
+      for (int q = warp; q < m * (m + 1) / 2; q += K7_WARPS) {
+        int I = 0;
+        while ((I + 1) * (I + 2) / 2 <= q) ++I;
+        const int J = q - I * (I + 1) / 2;
+        const float* PI = k7_tile(T, K + 1 + I, K);
+        const float* PJ = k7_tile(T, K + 1 + J, K);
+        float* C = k7_tile(T, K + 1 + I, K + 1 + J);
+        float acc[8][4];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+#pragma unroll 4
+        for (int k = 0; k < 32; ++k) {
+          float av[8], bv[4];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) av[i] = PI[(rg * 8 + i) * K7_TS + k];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) bv[j] = PJ[(cg * 4 + j) * K7_TS + k];
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) C[(rg * 8 + i) * K7_TS + cg * 4 + j] -= acc[i][j];
       }
     }
     __syncthreads();
-    // --- back substitution L^T x = y (warp 0)
+    // --- back substitution L^T x = y (warp 0), column by column: x_k = y_k / L_kk, then y_j -= L_kj x_k
+    // for j < k along row k of L (contiguous in its tiles).  Lane l keeps y_j, j = 32 m + l, in register
+    // xs[m]; tile rows are unrolled so every register index is a constant.
     if (warp == 0) {
-      for (int k = n - 1; k >= 0; --k) {
-        float s = 0.f;
-        for (int j = k + 1 + lane; j < n; j += 32) s += N[tri(j, k)] * x[j];
+      float xs[8];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) x[k] = (N[tri(n, k)] - s) / N[tri(k, k)];
-        __syncwarp();
+      for (int m = 0; m < 8; ++m) {
+        const int j = 32 * m + lane;
+        xs[m] = (m < NT && j < n) ? *k7_elem(T, n, j) : 0.f;
+      }
+#pragma unroll
+      for (int R = 7; R >= 0; --R) {
+        if (R >= NT) continue;
+        for (int c = 31; c >= 0; --c) {
+          const int k = 32 * R + c;
+          if (k >= n) continue;
+          const float xk = __shfl_sync(0xffffffffu, xs[R], c) * dinv[k];
+          const float* rowk = T + (R * (R + 1) / 2) * K7_TILE + c * K7_TS;  // tile (R, 0), row c
+#pragma unroll
+          for (int m = 0; m < 8; ++m) {
+            if (m > R) continue;
+            if (32 * m + lane < k) xs[m] -= rowk[m * K7_TILE + lane] * xk;
+          }
+          if (lane == c) xs[R] = xk;
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const int j = 32 * m + lane;
+        if (m < NT && j < n) x[j] = xs[m];
       }
     }
     __syncthreads();
@@ -210,8 +323,8 @@ __global__ void __launch_bounds__(K7_THREADS, 1) k7_calib(const K7Args a) {
 }
 
 size_t k7_smem_bytes(int n_ant) {
-  const int n = 2 * n_ant - 1;
-  return sizeof(float) * ((size_t)(n + 1) * (n + 2) / 2 + (n + 1) + ((n + 1) & ~1) + 1) + sizeof(float2) * n_ant + 16;
+  const int n = 2 * n_ant - 1, NT = (n + 1 + 31) / 32;
+  return sizeof(float) * ((size_t)NT * (NT + 1) / 2 * K7_TILE + 2 * NT * 32) + sizeof(float2) * n_ant;
 }
 
 int launch_calibrate(wn_ctx* ctx, const ObsDev& o, const float2* model, const float2* data, float2* gains, int n_iter,
