@@ -230,6 +230,68 @@ def bench_shapelets(wn, ctx, local, P, torch):
             "clean_model_40k_ms": round(ms_clean, 3), "clean_over_shapelet_time": round(ms_clean / ms, 2)}
 
 
+def bench_calibration(wn, ctx, local, torch, n_iter=10):
+    """Gain calibration (Sec. 5.1, eq:peeling-iter) of the MWA case: 14 x 384 (time, channel) problems of
+    128 antennas (255 real parameters each), n_iter iterations, model from the library's prediction of
+    2,000 points + 500 Gaussians, data from known per-(t, f) gains 1 + N(0, 0.05) plus noise."""
+    import oracle
+    obs, _ = synth.mwa()
+    sky = synth.make_sky(102, 2000, 500, 0)
+    d = wn.obs_to_device(obs, f"cuda:{local}")
+    m = ctx.upload(sky)
+    I = ctx.predict(d, m)
+    m.free()
+    rng = np.random.default_rng(23)
+    T, B, F, A = obs.n_time, obs.n_base, obs.n_chan, obs.n_ant
+    g_true = (1 + 0.05 * (rng.normal(size=(T, F, A)) + 1j * rng.normal(size=(T, F, A)))).astype(np.complex64)
+    gt = torch.as_tensor(g_true).cuda()
+    a1 = torch.as_tensor(obs.ant1.astype(np.int64)).cuda()
+    a2 = torch.as_tensor(obs.ant2.astype(np.int64)).cuda()
+    G = (gt[:, :, a1] * torch.conj(gt[:, :, a2])).permute(0, 2, 1)          # [T, B, F]
+    sigma = 0.01 * float(I.abs().mean())
+    gen = torch.Generator(device=f"cuda:{local}").manual_seed(24)
+    noise = torch.complex(torch.randn(I.shape, generator=gen, device=I.device),
+                          torch.randn(I.shape, generator=gen, device=I.device)) * sigma
+    V = (G * I + noise).contiguous()
+    g0 = torch.ones((T, F, A), dtype=torch.complex64, device=I.device)
+    ctx.calibrate(d, I, V, g0.clone(), n_iter=n_iter)                        # warm-up
+    ev = [torch.cuda.Event(True) for _ in range(2)]
+    times = []
+    for _ in range(3):
+        g = g0.clone()
+        torch.cuda.synchronize()
+        ev[0].record()
+        ctx.calibrate(d, I, V, g, n_iter=n_iter)
+        ev[1].record()
+        torch.cuda.synchronize()
+        times.append(ev[0].elapsed_time(ev[1]))
+    flags = ctx.device_errors()
+    ms = float(np.median(times))
+    gg = g.cpu().numpy().astype(np.complex128)
+    want = g_true.astype(np.complex128) * np.exp(-1j * np.angle(g_true[:, :, :1].astype(np.complex128)))
+    resid = ctx.peel_model(d, g, V, I)
+    rms = float(resid.abs().pow(2).mean().sqrt())
+    # oracle on two (t, f) problems, same start and iteration count
+    Ih, Vh = I.cpu().numpy().astype(np.complex128), V.cpu().numpy().astype(np.complex128)
+    t0 = time.perf_counter()
+    par = 0.0
+    for (t, f) in ((0, 0), (T - 1, F // 2)):
+        ref = oracle.calibrate(obs.ant1, obs.ant2, A, Ih[t:t + 1, :, f:f + 1], Vh[t:t + 1, :, f:f + 1],
+                               np.ones((1, 1, A)), n_iter)
+        par = max(par, float(np.abs(gg[t, f] - ref[0, 0]).max()))
+    cpu_s = (time.perf_counter() - t0) / 2
+    n = 2 * A - 1
+    flops = T * F * n_iter * (n ** 3 / 3 + 2 * n * n + 60 * B)
+    return {"workload": f"calibration: {T} x {F} (time, channel) problems, {A} antennas ({n} parameters), "
+                        f"{n_iter} iterations, model 2000 P + 500 G, gains 1+N(0,0.05), noise 1% of |model|",
+            "ms": round(ms, 3), "solves_per_s": T * F * n_iter / (ms * 1e-3),
+            "achieved_tflops": round(flops / (ms * 1e-3) / 1e12, 3),
+            "note": "FP32 normal equations (Cholesky n^3/3 + solves + accumulation) per solve; one problem per SM",
+            "gain_error_max": float(np.abs(gg - want).max()), "parity_vs_oracle_max": par,
+            "resid_rms_over_noise": round(rms / (sigma * np.sqrt(2)), 4), "device_errors": flags,
+            "oracle_cpu_s_per_problem": round(cpu_s, 3)}
+
+
 def bench_adjoint(wn, ctx, local, torch):
     """Adjoint (loss and every gradient) on 64 tiles x 4 steps x 64 channels, 500 points + 1 shapelet."""
     obs, sky = synth.adjoint()
@@ -388,7 +450,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--no-extras", action="store_true", help="skip the shapelet, adjoint and serving reports")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the shapelet, adjoint, calibration and serving reports")
     ap.add_argument("--case", choices=["mwa_small", "fornax_small", "adjoint", "peel", "calib"],
                     help="run one small fixed case for profiling instead of the benchmark")
     args = ap.parse_args()
@@ -558,6 +621,7 @@ def main():
         if not args.no_extras:
             for key, fn in (("shapelet", lambda: bench_shapelets(wn, ctx, local, P, torch)),
                             ("adjoint", lambda: bench_adjoint(wn, ctx, local, torch)),
+                            ("calibration", lambda: bench_calibration(wn, ctx, local, torch)),
                             ("serving", lambda: bench_serving(wn, ctx, local, torch))):
                 try:
                     extra[key] = fn()
