@@ -202,8 +202,10 @@ def bench_shapelets(wn, ctx, local, P, torch):
 
     ms = timed(lambda: ctx.peel(d, m, gains, data, out=out), 10)
     nnz = int(sky.s_off[-1])
-    kp, npad = 96, 176
-    flops = 2.0 * obs.n_vis * kp * npad * 3 * sky.n_shape
+    # the dense operands are sized by the highest order each shapelet's coefficients reach
+    n_eff = [int(np.max(sky.s_n1[a:b] + sky.s_n2[a:b])) for a, b in zip(sky.s_off[:-1], sky.s_off[1:])]
+    pads = [((n + 1 + 15) // 16 * 16, (2 * (n + 1) + 15) // 16 * 16) for n in n_eff]
+    flops = sum(2.0 * obs.n_vis * kp * npad * 3 for kp, npad in pads)
     tf = flops / (ms * 1e-3) / 1e12
     peak = float(P.get("bf16_tflops", 1800.0))
     rows = np.sort(np.random.default_rng(5).choice(obs.n_rows, size=16, replace=False))
@@ -221,6 +223,7 @@ def bench_shapelets(wn, ctx, local, P, torch):
     ms_clean = timed(lambda: ctx.peel(d, mc, gains, data, out=out), 2)
     mc.free()
     return {"workload": "fornax_peel: 128 tiles (5 km) x 14 x 384 ch, 2 shapelets n_max 80, 1500 coeffs each",
+            "orders_present": n_eff, "k_pad_n_pad": pads,
             "ms_per_step": round(ms, 4), "shapelet_vis_per_s": obs.n_vis * sky.n_shape / (ms * 1e-3),
             "coeff_vis_per_s": nnz * obs.n_vis / (ms * 1e-3),
             "roofline": {"bound": "tensor", "achieved": round(tf, 2), "peak": peak, "unit": "TFLOP/s",
@@ -290,6 +293,44 @@ def bench_calibration(wn, ctx, local, torch, n_iter=10):
             "gain_error_max": float(np.abs(gg - want).max()), "parity_vs_oracle_max": par,
             "resid_rms_over_noise": round(rms / (sigma * np.sqrt(2)), 4), "device_errors": flags,
             "oracle_cpu_s_per_problem": round(cpu_s, 3)}
+
+
+def bench_truncation(wn, ctx, local, torch, fractions=(1.0, 0.999, 0.99, 0.95, 0.9, 0.8)):
+    """Model truncation (Sec. 6.2) on the Fornax observation: GPU prediction time and model error against
+    the full model as f_comp falls, for the 40,000-component point/Gaussian model and for the two
+    n_max 80 shapelets.  Model error = max |V_f - V_full| / max |V_full| over every visibility."""
+    from paper_2005_09316_b300 import truncate as tr
+    obs, sky_s = synth.fornax()
+    _, sky_c = synth.fornax_clean()
+    d = wn.obs_to_device(obs, f"cuda:{local}")
+    ev = [torch.cuda.Event(True) for _ in range(2)]
+    out = {"workload": "fornax observation (128 tiles, 5 km, 14 x 384 ch): 40000 P/G model and 2 shapelets n_max 80"}
+    for name, sky, reps in (("clean_40k", sky_c, 1), ("shapelets", sky_s, 3)):
+        rows = []
+        full = None
+        for f in fractions:
+            t, info = tr.truncate(sky, f)
+            m = ctx.upload(t)
+            v = ctx.predict(d, m)                      # warm-up, and the visibilities for the error
+            torch.cuda.synchronize()
+            ev[0].record()
+            for _ in range(reps):
+                ctx.predict(d, m, out=v)
+            ev[1].record()
+            torch.cuda.synchronize()
+            ms = ev[0].elapsed_time(ev[1]) / reps
+            m.free()
+            if full is None:
+                full, vmax = v, float(v.abs().max())
+                err = 0.0
+            else:
+                err = float((v - full).abs().max()) / vmax
+            rows.append({"f_comp": f, "n_comp": info["n_comp"], "flux_fraction_kept": round(info["flux_fraction_kept"], 6),
+                         "n_max": [int(x) for x in t.s_nmax] if t.n_shape else None,
+                         "ms": round(ms, 3), "model_error": err})
+        out[name] = rows
+        del full
+    return out
 
 
 def bench_adjoint(wn, ctx, local, torch):
@@ -451,7 +492,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the shapelet, adjoint, calibration and serving reports")
+                    help="skip the shapelet, adjoint, calibration, truncation and serving reports")
     ap.add_argument("--case", choices=["mwa_small", "fornax_small", "adjoint", "peel", "calib"],
                     help="run one small fixed case for profiling instead of the benchmark")
     args = ap.parse_args()
@@ -622,6 +663,7 @@ def main():
             for key, fn in (("shapelet", lambda: bench_shapelets(wn, ctx, local, P, torch)),
                             ("adjoint", lambda: bench_adjoint(wn, ctx, local, torch)),
                             ("calibration", lambda: bench_calibration(wn, ctx, local, torch)),
+                            ("truncation", lambda: bench_truncation(wn, ctx, local, torch)),
                             ("serving", lambda: bench_serving(wn, ctx, local, torch))):
                 try:
                     extra[key] = fn()

@@ -108,7 +108,7 @@ typedef struct {
     const double* s_beta1;    /* [n_shape] beta_1 (rad), pairs with the major (PA) axis */
     const double* s_beta2;    /* [n_shape] beta_2 (rad) */
     const double* s_pa;       /* [n_shape] position angle (rad) */
-    const int32_t* s_nmax;    /* [n_shape] n_max in [0, 127] */
+    const int32_t* s_nmax;    /* [n_shape] n_max in [0, 127]; each shapelet is evaluated up to the highest n1 + n2 its triples reach */
     const int32_t* s_off;     /* [n_shape + 1] offsets into the coefficient triples, s_off[0] == 0 */
     const int32_t* s_n1;      /* [nnz] basis order along x (beta_1) */
     const int32_t* s_n2;      /* [nnz] basis order along y (beta_2); n1 + n2 <= n_max */

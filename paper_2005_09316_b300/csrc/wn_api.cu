@@ -269,6 +269,14 @@ int wn_sky_upload(wn_ctx* ctx, const wn_sky* s, int* model_id, void* stream) {
         c = 1;
       }
     }
+    // Each shapelet is sized by the highest order its coefficients reach (n1 + n2), not the declared
+    // n_max: the basis functions above it have zero coefficients and contribute nothing, so the
+    // envelope is the same and the dense contraction carries no empty orders.
+    for (int q = 0; q < s->n_shape; ++q) {
+      int hi = 0;
+      for (int k = off[q]; k < off[q + 1]; ++k) hi = std::max(hi, n1[k] + n2[k]);
+      nmax[q] = hi;
+    }
     M->sh_host.resize(s->n_shape);
     size_t b = 0;
     for (int q = 0; q < s->n_shape; ++q) {
@@ -324,7 +332,10 @@ int wn_sky_upload(wn_ctx* ctx, const wn_sky* s, int* model_id, void* stream) {
   }
   unsigned zero = 0;
   cudaMemcpyAsync(ctx->d_err, &zero, sizeof(unsigned), cudaMemcpyHostToDevice, st);
-  int r = launch_pack(ctx, s, M, st);
+  // the packers read each shapelet's order from the model's own (effective) n_max table
+  wn_sky sp = *s;
+  if (s->n_shape > 0) sp.s_nmax = M->s_meta;
+  int r = launch_pack(ctx, &sp, M, st);
   if (r != WN_OK) {
     free_model(M);
     return r;
