@@ -9,16 +9,21 @@
 // per-row dot product xi = sum_n2 T[., n2] phi_n2(y).  The contribution S(nu) xi exp(-2 pi i tau nu/c)
 // is then stored, accumulated, or subtracted as G times it for the peel.
 //
-// Kernel organisation (persistent, one CTA per SM; tiles of 128 visibilities, two in flight):
+// Kernel organisation (persistent, one CTA per SM; tiles of 128 R visibilities, two in flight):
 //  * producer warpgroups P0, P1 (warps 0-3, 4-7) take the even / odd tiles: thread i computes
-//    phi_n(x) of row i by the normalised Hermite recurrence (FP32, rescaled to stay in range) and
-//    writes them as bf16 hi/lo into that parity's A buffer in the canonical K-major shared-memory
-//    layout (8x8 core matrices, no swizzle);
+//    phi_n(x) of rows i, i + 128, ... (R of them, interleaved so the serial recurrences overlap) by the
+//    normalised Hermite recurrence (FP32, rescaled to stay in range) and writes them as bf16 hi/lo into
+//    that parity's A buffer (one 128-row block per r) in the canonical K-major shared-memory layout
+//    (8x8 core matrices, no swizzle);
 //  * warp 16 allocates TMEM, loads the packed coefficient operand with one TMA bulk copy, and one of
 //    its threads issues tcgen05.mma (kind::f16, bf16 x bf16 -> f32; three products hi*hi + hi*lo + lo*hi
-//    in the split mode) into the parity's TMEM accumulator and commits to an mbarrier;
+//    in the split mode; one M = 128 block per r) into the parity's TMEM accumulators and commits to an
+//    mbarrier;
 //  * epilogue warpgroups E0, E1 (warps 8-11, 12-15) read their accumulator rows from TMEM (warp w
-//    reaches lanes 32 (w % 4) ..), stream phi_n(y) against them, release TMEM, and write the output.
+//    reaches lanes 32 (w % 4) ..), stream phi_n(y) against them (R rows per thread, interleaved),
+//    release TMEM, and write the output.
+//  R = 2 when two parities of the doubled A buffers and 4 n_pad TMEM columns fit (n_pad <= 128),
+//  else R = 1.
 //  Per parity: P(k+2) waits for MMA(k) to finish reading A, MMA(k+2) for E(k) to release TMEM.
 // Every wait is bounded; on a timeout the kernel raises WN_DEVERR_TIMEOUT, drains its own commits and
 // frees TMEM before returning.
@@ -121,11 +126,11 @@ struct K2Layout {
   int b_bytes, a_bytes, a0, coef, bars, total;
 };
 
-__host__ __device__ inline K2Layout k2_layout(int kp, int n_pad, int passes, int groups) {
+__host__ __device__ inline K2Layout k2_layout(int kp, int n_pad, int passes, int groups, int R) {
   K2Layout L;
   const int parts = passes > 1 ? 2 : 1;
   L.b_bytes = parts * kp * n_pad * 2;
-  L.a_bytes = parts * kp * K2_M * 2;  // one group's A (hi [+ lo])
+  L.a_bytes = R * parts * kp * K2_M * 2;  // one group's A: R blocks of 128 rows (hi [+ lo])
   L.a0 = (L.b_bytes + 1023) & ~1023;
   L.coef = L.a0 + groups * L.a_bytes;  // recurrence coefficients a_n, b_n: 2 x 128 floats
   L.bars = L.coef + 2 * (kNmaxLimit + 1) * 4;
@@ -152,57 +157,71 @@ __device__ __forceinline__ void store_bf16_split(float (&v)[8], unsigned char* a
   if (a_lo) *reinterpret_cast<uint4*>(a_lo + off) = *reinterpret_cast<uint4*>(l);
 }
 
-template <int KP>
-__device__ __forceinline__ void produce_row(float x, int nmax, bool valid, unsigned char* a_hi, unsigned char* a_lo,
-                                            int row, const float4* ca, const float4* cb) {
-  const float ax = fabsf(x);
-  const float xcut = sqrtf(2.0f * nmax + 1.0f) + 10.0f;
-  const bool zero = !valid || !(ax <= xcut);
-  const float hx = 0.5f * x * x * 1.4426950408889634f;  // log2 of 1/phi_0
-  float p_prev = 0.f;
-  if (zero || ax <= 12.5f) {
-    float p = zero ? 0.f : exp2f(-hx);
+template <int KP, int R, bool SCALED>
+__device__ __forceinline__ void produce_rows_run(const float (&x)[R], float (&p)[R], float (&p_prev)[R], float (&scale)[R],
+                                                 int (&E)[R], unsigned char* a_base, int blk, bool split, int row,
+                                                 const float4* ca, const float4* cb) {
 #pragma unroll 1
-    for (int k0 = 0; k0 < KP; k0 += 8) {
-      const float4 A0 = ca[k0 >> 2], A1 = ca[(k0 >> 2) + 1], B0 = cb[k0 >> 2], B1 = cb[(k0 >> 2) + 1];
-      const float av[8] = {A0.x, A0.y, A0.z, A0.w, A1.x, A1.y, A1.z, A1.w};
-      const float bv[8] = {B0.x, B0.y, B0.z, B0.w, B1.x, B1.y, B1.z, B1.w};
-      float v[8];
+  for (int k0 = 0; k0 < KP; k0 += 8) {
+    const float4 A0 = ca[k0 >> 2], A1 = ca[(k0 >> 2) + 1], B0 = cb[k0 >> 2], B1 = cb[(k0 >> 2) + 1];
+    const float av[8] = {A0.x, A0.y, A0.z, A0.w, A1.x, A1.y, A1.z, A1.w};
+    const float bv[8] = {B0.x, B0.y, B0.z, B0.w, B1.x, B1.y, B1.z, B1.w};
+    float v[R][8];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        v[i] = p;
-        const float pn = fmaf(av[i] * x, p, -bv[i] * p_prev);
-        p_prev = p;
-        p = pn;
+    for (int i = 0; i < 8; ++i) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {  // R independent recurrences, interleaved
+        v[r][i] = SCALED ? p[r] * scale[r] : p[r];
+        const float pn = fmaf(av[i] * x[r], p[r], -bv[i] * p_prev[r]);
+        p_prev[r] = p[r];
+        p[r] = pn;
       }
-      store_bf16_split(v, a_hi, a_lo, kmaj_off(row, k0, K2_M));
     }
-  } else {
-    int E = max(0, (int)ceilf(hx) - 100);  // stored value = phi * 2^E
-    float p = exp2f((float)E - hx);
-    float scale = __int_as_float(max(0, 127 - E) << 23);  // 2^-E (0 below 2^-126)
-#pragma unroll 1
-    for (int k0 = 0; k0 < KP; k0 += 8) {
-      const float4 A0 = ca[k0 >> 2], A1 = ca[(k0 >> 2) + 1], B0 = cb[k0 >> 2], B1 = cb[(k0 >> 2) + 1];
-      const float av[8] = {A0.x, A0.y, A0.z, A0.w, A1.x, A1.y, A1.z, A1.w};
-      const float bv[8] = {B0.x, B0.y, B0.z, B0.w, B1.x, B1.y, B1.z, B1.w};
-      float v[8];
+    if (SCALED) {
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        v[i] = p * scale;
-        const float pn = fmaf(av[i] * x, p, -bv[i] * p_prev);
-        p_prev = p;
-        p = pn;
+      for (int r = 0; r < R; ++r) {
+        if (fabsf(p[r]) > 1.8446744e19f) {  // 2^64: rescale (8 steps grow by at most 2^43)
+          p[r] *= 5.421011e-20f;
+          p_prev[r] *= 5.421011e-20f;
+          E[r] -= 64;
+          scale[r] = __int_as_float(max(0, 127 - E[r]) << 23);
+        }
       }
-      if (fabsf(p) > 1.8446744e19f) {  // 2^64: rescale (8 steps grow by at most 2^43)
-        p *= 5.421011e-20f;
-        p_prev *= 5.421011e-20f;
-        E -= 64;
-        scale = __int_as_float(max(0, 127 - E) << 23);
-      }
-      store_bf16_split(v, a_hi, a_lo, kmaj_off(row, k0, K2_M));
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      unsigned char* hi = a_base + r * blk;
+      store_bf16_split(v[r], hi, split ? hi + KP * K2_M * 2 : nullptr, kmaj_off(row, k0, K2_M));
     }
   }
+}
+
+// Rows r of this thread go to row `row` of block r (a_base + r * blk).  The scaled form is taken for
+// all R rows when any of them needs it (it is exact for every x).
+template <int KP, int R>
+__device__ __forceinline__ void produce_rows(const float (&x)[R], int nmax, const bool (&valid)[R], unsigned char* a_base,
+                                             int blk, bool split, int row, const float4* ca, const float4* cb) {
+  const float xcut = sqrtf(2.0f * nmax + 1.0f) + 10.0f;
+  bool zero[R], fast = true;
+  float hx[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const float ax = fabsf(x[r]);
+    zero[r] = !valid[r] || !(ax <= xcut);
+    hx[r] = 0.5f * x[r] * x[r] * 1.4426950408889634f;  // log2 of 1/phi_0
+    fast = fast && (zero[r] || ax <= 12.5f);
+  }
+  float p[R], p_prev[R], scale[R];
+  int E[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    p_prev[r] = 0.f;
+    E[r] = fast ? 0 : max(0, (int)ceilf(hx[r]) - 100);  // stored value = phi * 2^E
+    p[r] = zero[r] ? 0.f : exp2f((float)E[r] - hx[r]);
+    scale[r] = __int_as_float(max(0, 127 - E[r]) << 23);  // 2^-E (0 below 2^-126)
+  }
+  if (fast) produce_rows_run<KP, R, false>(x, p, p_prev, scale, E, a_base, blk, split, row, ca, cb);
+  else produce_rows_run<KP, R, true>(x, p, p_prev, scale, E, a_base, blk, split, row, ca, cb);
 }
 
 // Epilogue dot product of one accumulator chunk (16 n2 values: columns 2 n2, 2 n2 + 1 = Re, Im) with
@@ -234,18 +253,19 @@ __device__ __forceinline__ void epi_chunk(const uint32_t* t, const float4* ca, c
   }
 }
 
-template <int KP>
+template <int KP, int R>
 __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int ng = a.groups;  // tile parities in flight (2, or 1 when two A buffers do not fit)
-  const K2Layout lay = k2_layout(KP, a.n_pad, a.passes, ng);
+  const K2Layout lay = k2_layout(KP, a.n_pad, a.passes, ng, R);
+  const int blk = lay.a_bytes / R;  // one 128-row block of A (hi [+ lo])
   uint64_t* bfull = reinterpret_cast<uint64_t*>(smem + lay.bars);
   uint64_t* afull = bfull + 1;                // [parity] producer -> MMA: A written
   uint64_t* mdone = afull + K2_GROUPS;        // [parity] MMA -> producer/epilogue: MMA complete
   uint64_t* tfree = mdone + K2_GROUPS;        // [parity] epilogue -> MMA: TMEM read
   uint32_t* tslot = reinterpret_cast<uint32_t*>(tfree + K2_GROUPS);
   const int warp = threadIdx.x >> 5;
-  const int acc_cols = a.n_pad * ng;
+  const int acc_cols = a.n_pad * ng * R;
   const uint32_t ncols = acc_cols <= 32 ? 32 : (acc_cols <= 64 ? 64 : (acc_cols <= 128 ? 128 : (acc_cols <= 256 ? 256 : 512)));
 
   if (threadIdx.x == 0) {
@@ -292,18 +312,21 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
         if (!k2_wait(&afull[sp], j & 1, a.err)) break;
         if (j > 0 && !k2_wait(&tfree[sp], (j - 1) & 1, a.err)) break;
         tc_fence_after();
-        const uint32_t a_hi = smem_u32(smem + lay.a0 + sp * lay.a_bytes);
-        const uint32_t a_lo = a_hi + (uint32_t)(KP * K2_M * 2);
-        const uint32_t d = tmem + (uint32_t)(sp * a.n_pad);
-#pragma unroll 1
-        for (int p = 0; p < a.passes; ++p) {
-          const uint32_t aa = (p == 2) ? a_lo : a_hi;  // hi*hi, hi*lo, lo*hi
-          const uint32_t bb = (p == 1) ? b_lo : b_hi;
 #pragma unroll
-          for (int kk = 0; kk < KP / 16; ++kk) {
-            const uint64_t da = umma_desc(aa + (uint32_t)(2 * kk) * lbo_a, lbo_a, 128);
-            const uint64_t db = umma_desc(bb + (uint32_t)(2 * kk) * lbo_b, lbo_b, 128);
-            umma_bf16(d, da, db, idesc, (p > 0 || kk > 0) ? 1u : 0u);
+        for (int r = 0; r < R; ++r) {  // block r of the tile into accumulator sp * R + r
+          const uint32_t a_hi = smem_u32(smem + lay.a0 + sp * lay.a_bytes + r * blk);
+          const uint32_t a_lo = a_hi + (uint32_t)(KP * K2_M * 2);
+          const uint32_t d = tmem + (uint32_t)((sp * R + r) * a.n_pad);
+#pragma unroll 1
+          for (int p = 0; p < a.passes; ++p) {
+            const uint32_t aa = (p == 2) ? a_lo : a_hi;  // hi*hi, hi*lo, lo*hi
+            const uint32_t bb = (p == 1) ? b_lo : b_hi;
+#pragma unroll
+            for (int kk = 0; kk < KP / 16; ++kk) {
+              const uint64_t da = umma_desc(aa + (uint32_t)(2 * kk) * lbo_a, lbo_a, 128);
+              const uint64_t db = umma_desc(bb + (uint32_t)(2 * kk) * lbo_b, lbo_b, 128);
+              umma_bf16(d, da, db, idesc, (p > 0 || kk > 0) ? 1u : 0u);
+            }
           }
         }
         umma_commit(&mdone[sp]);
@@ -321,30 +344,37 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
     const int sp = warp >> 2;
     if (sp >= ng) goto done;
     const int m = threadIdx.x & 127;
-    unsigned char* a_hi = smem + lay.a0 + sp * lay.a_bytes;
-    unsigned char* a_lo = a.passes > 1 ? a_hi + KP * K2_M * 2 : nullptr;
+    unsigned char* a_base = smem + lay.a0 + sp * lay.a_bytes;
     // the next tile's (xs, nu) are loaded one tile ahead and multiplied only when used
-    auto load_x = [&](int it, bool& valid, float& xs, float& nu) {
-      const long long vis = (long long)(blockIdx.x + it * gridDim.x) * K2_M + m;
-      valid = it < n_it && vis < a.n_vis;
-      xs = 0.f;
-      nu = 0.f;
-      if (valid) {
-        const int row = (int)(vis / a.n_chan);
-        const int f = (int)(vis - (long long)row * a.n_chan);
-        xs = __ldg(&a.rowinfo[row].x);
-        nu = __ldg(&a.chaninfo[f].w);
+    auto load_x = [&](int it, bool (&valid)[R], float (&xs)[R], float (&nu)[R]) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const long long vis = (long long)(blockIdx.x + it * gridDim.x) * (K2_M * R) + r * K2_M + m;
+        valid[r] = it < n_it && vis < a.n_vis;
+        xs[r] = 0.f;
+        nu[r] = 0.f;
+        if (valid[r]) {
+          const int row = (int)(vis / a.n_chan);
+          const int f = (int)(vis - (long long)row * a.n_chan);
+          xs[r] = __ldg(&a.rowinfo[row].x);
+          nu[r] = __ldg(&a.chaninfo[f].w);
+        }
       }
     };
-    bool valid;
-    float xs, nu;
+    bool valid[R];
+    float xs[R], nu[R];
     load_x(sp, valid, xs, nu);
     for (int it = sp, j = 0; it < n_it; it += ng, ++j) {
-      const float x = xs * nu;
-      const bool v0 = valid;
+      float x[R];
+      bool v0[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        x[r] = xs[r] * nu[r];
+        v0[r] = valid[r];
+      }
       load_x(it + ng, valid, xs, nu);
       if (j > 0 && !k2_wait(&mdone[sp], (j - 1) & 1, a.err)) break;  // MMA(j-1) has read A
-      produce_row<KP>(x, a.nmax, v0, a_hi, a_lo, m, ca, cb);
+      produce_rows<KP, R>(x, a.nmax, v0, a_base, blk, a.passes > 1, m, ca, cb);
       fence_async_smem();
       mbar_arrive(&afull[sp]);
     }
@@ -353,76 +383,109 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
     const int sp = (warp - 4 * K2_GROUPS) >> 2;
     if (sp >= ng) goto done;
     const int m = threadIdx.x & 127;
-    const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(sp * a.n_pad);
+    const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(sp * R * a.n_pad);
     const float ycut = sqrtf(2.0f * a.nmax + 1.0f) + 10.0f;
     struct EpiIn {
       float4 ri, ci;
       float2 base;
       long long vis;
-      int row, f;
       bool valid;
     };
-    auto load_epi = [&](int it) {
+    auto load_epi = [&](int it, int r) {
       EpiIn e;
-      e.vis = (long long)(blockIdx.x + it * gridDim.x) * K2_M + m;
+      e.vis = (long long)(blockIdx.x + it * gridDim.x) * (K2_M * R) + r * K2_M + m;
       e.valid = it < n_it && e.vis < a.n_vis;
-      e.row = e.valid ? (int)(e.vis / a.n_chan) : 0;
-      e.f = e.valid ? (int)(e.vis - (long long)e.row * a.n_chan) : 0;
-      e.ri = e.valid ? __ldg(a.rowinfo + e.row) : make_float4(0.f, 0.f, 0.f, 0.f);
-      e.ci = e.valid ? __ldg(a.chaninfo + e.f) : make_float4(0.f, 0.f, 0.f, 1.f);
+      const int row = e.valid ? (int)(e.vis / a.n_chan) : 0;
+      const int f = e.valid ? (int)(e.vis - (long long)row * a.n_chan) : 0;
+      e.ri = e.valid ? __ldg(a.rowinfo + row) : make_float4(0.f, 0.f, 0.f, 0.f);
+      e.ci = e.valid ? __ldg(a.chaninfo + f) : make_float4(0.f, 0.f, 0.f, 1.f);
       e.base = make_float2(0.f, 0.f);
       if (e.valid && a.mode != OUT_STORE) e.base = a.mode == OUT_PEEL ? a.peel.data[e.vis] : a.out[e.vis];
       return e;
     };
-    EpiIn nxt = load_epi(sp);
+    EpiIn nxt[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) nxt[r] = load_epi(sp, r);
     for (int it = sp, j = 0; it < n_it; it += ng, ++j) {
-      const EpiIn cur = nxt;
+      EpiIn cur[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) cur[r] = nxt[r];
       if (!k2_wait(&mdone[sp], j & 1, a.err)) break;
-      nxt = load_epi(it + ng);  // next tile's inputs in flight while this one is formed
+#pragma unroll
+      for (int r = 0; r < R; ++r) nxt[r] = load_epi(it + ng, r);  // next tile's inputs in flight
       tc_fence_after();
-      const bool valid = cur.valid;
-      const int row = cur.row, f = cur.f;
-      const size_t idx = (size_t)(valid ? cur.vis : 0);
-      const float2 base = cur.base;
-      const float4 ri = cur.ri, ci = cur.ci;
-      const float y = ri.y * ci.w;
-      const float2 P = phasor_fast(reduce_turns(ri.z, ri.w, ci.x, ci.y));
-      const float amp = valid ? a.sgn * ex2_approx(fmaf(a.alpha, ci.z, a.c_amp)) : 0.f;
-      const bool yzero = !valid || !(fabsf(y) <= ycut);
-      const bool yfast = yzero || fabsf(y) <= 12.5f;
-      const float hy = 0.5f * y * y * 1.4426950408889634f;
-      int E = yfast ? 0 : max(0, (int)ceilf(hy) - 100);
-      float q_prev = 0.f, q = yzero ? 0.f : exp2f((float)E - hy);
-      float scale = __int_as_float(max(0, 127 - E) << 23);
-      float xr = 0.f, xi = 0.f;
-      // accumulator row in chunks of 16 columns (8 n2), the next chunk's load in flight while one is used
+      float y[R], q[R], q_prev[R], scale[R], xr[R], xi[R];
+      int E[R];
+      bool yfast = true;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        y[r] = cur[r].ri.y * cur[r].ci.w;
+        const bool yzero = !cur[r].valid || !(fabsf(y[r]) <= ycut);
+        yfast = yfast && (yzero || fabsf(y[r]) <= 12.5f);
+        q[r] = yzero ? 0.f : 1.f;  // marks zero rows until the seed below
+        xr[r] = xi[r] = 0.f;
+        q_prev[r] = 0.f;
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const float hy = 0.5f * y[r] * y[r] * 1.4426950408889634f;
+        E[r] = yfast ? 0 : max(0, (int)ceilf(hy) - 100);
+        q[r] = q[r] == 0.f ? 0.f : exp2f((float)E[r] - hy);
+        scale[r] = __int_as_float(max(0, 127 - E[r]) << 23);
+      }
+      // accumulator rows in chunks of 16 columns (8 n2)
       const int nch = a.n_pad >> 4;
-      uint32_t tb0[16], tb1[16];
-      tmem_issue16x(trow, tb0);
-      tmem_wait16(tb0);
+      if (R == 1) {  // one row: the next chunk's load in flight while one is used
+        uint32_t tb0[16], tb1[16];
+        tmem_issue16x(trow, tb0);
+        tmem_wait16(tb0);
 #pragma unroll 1
-      for (int c = 0; c < nch; c += 2) {
-        if (c + 1 < nch) tmem_issue16x(trow + (uint32_t)((c + 1) << 4), tb1);
-        if (yfast) epi_chunk<false>(tb0, ca, cb, c << 3, y, q, q_prev, xr, xi, E, scale);
-        else epi_chunk<true>(tb0, ca, cb, c << 3, y, q, q_prev, xr, xi, E, scale);
-        tmem_wait16(tb1);
-        if (c + 1 < nch) {
-          if (c + 2 < nch) tmem_issue16x(trow + (uint32_t)((c + 2) << 4), tb0);
-          if (yfast) epi_chunk<false>(tb1, ca, cb, (c + 1) << 3, y, q, q_prev, xr, xi, E, scale);
-          else epi_chunk<true>(tb1, ca, cb, (c + 1) << 3, y, q, q_prev, xr, xi, E, scale);
-          tmem_wait16(tb0);
+        for (int c = 0; c < nch; c += 2) {
+          if (c + 1 < nch) tmem_issue16x(trow + (uint32_t)((c + 1) << 4), tb1);
+          if (yfast) epi_chunk<false>(tb0, ca, cb, c << 3, y[0], q[0], q_prev[0], xr[0], xi[0], E[0], scale[0]);
+          else epi_chunk<true>(tb0, ca, cb, c << 3, y[0], q[0], q_prev[0], xr[0], xi[0], E[0], scale[0]);
+          tmem_wait16(tb1);
+          if (c + 1 < nch) {
+            if (c + 2 < nch) tmem_issue16x(trow + (uint32_t)((c + 2) << 4), tb0);
+            if (yfast) epi_chunk<false>(tb1, ca, cb, (c + 1) << 3, y[0], q[0], q_prev[0], xr[0], xi[0], E[0], scale[0]);
+            else epi_chunk<true>(tb1, ca, cb, (c + 1) << 3, y[0], q[0], q_prev[0], xr[0], xi[0], E[0], scale[0]);
+            tmem_wait16(tb0);
+          }
+        }
+      } else {  // R rows: one chunk of every row in flight, their recurrences interleaved
+        uint32_t tb[R][16];
+#pragma unroll 1
+        for (int c = 0; c < nch; ++c) {
+#pragma unroll
+          for (int r = 0; r < R; ++r) tmem_issue16x(trow + (uint32_t)(r * a.n_pad + (c << 4)), tb[r]);
+#pragma unroll
+          for (int r = 0; r < R; ++r) tmem_wait16(tb[r]);
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            if (yfast) epi_chunk<false>(tb[r], ca, cb, c << 3, y[r], q[r], q_prev[r], xr[r], xi[r], E[r], scale[r]);
+            else epi_chunk<true>(tb[r], ca, cb, c << 3, y[r], q[r], q_prev[r], xr[r], xi[r], E[r], scale[r]);
+          }
         }
       }
       tc_fence_before();
       mbar_arrive(&tfree[sp]);
-      if (valid) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        if (!cur[r].valid) continue;
+        const float4 ri = cur[r].ri, ci = cur[r].ci;
+        const float2 P = phasor_fast(reduce_turns(ri.z, ri.w, ci.x, ci.y));
+        const float amp = a.sgn * ex2_approx(fmaf(a.alpha, ci.z, a.c_amp));
         // Z = amp (xr + i xi) P
-        const float zr = amp * (xr * P.x - xi * P.y), zi = amp * (xr * P.y + xi * P.x);
+        const float zr = amp * (xr[r] * P.x - xi[r] * P.y), zi = amp * (xr[r] * P.y + xi[r] * P.x);
+        const size_t idx = (size_t)cur[r].vis;
+        const float2 base = cur[r].base;
         if (a.mode == OUT_STORE) {
           a.out[idx] = make_float2(zr, zi);
         } else if (a.mode == OUT_ACCUM) {
           a.out[idx] = make_float2(base.x + zr, base.y + zi);
         } else {
+          const int row = (int)(cur[r].vis / a.n_chan);
+          const int f = (int)(cur[r].vis - (long long)row * a.n_chan);
           float2 G;
           if (!gain_product(a.peel, row, a.n_base, f, G)) atomicOr(a.err, WN_DEVERR_ANTENNA);
           a.out[idx] = make_float2(base.x - (G.x * zr - G.y * zi), base.y - (G.x * zi + G.y * zr));
@@ -478,9 +541,9 @@ static int k2_setup_constants(int device, cudaStream_t st) {
   return WN_OK;
 }
 
-template <int KP>
+template <int KP, int R>
 static cudaError_t k2_launch_t(const K2Args& a, int grid, int smem, cudaStream_t st) {
-  auto fn = k2_shapelet<KP>;
+  auto fn = k2_shapelet<KP, R>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   fn<<<grid, K2_THREADS, smem, st>>>(a);
@@ -508,7 +571,6 @@ int launch_shapelets_ws(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* ou
   if (int r = k2_setup_constants(ctx->device, st)) return r;
   k2_chaninfo<<<(o.n_chan + 255) / 256, 256, 0, st>>>(o.freq, o.n_chan, o.nu0, chaninfo);
   const long long n_vis = (long long)o.n_rows * o.n_chan;
-  const int n_tiles = (int)((n_vis + K2_M - 1) / K2_M);
   const int passes = ctx->shape_mode == WN_SHAPE_BF16X1 ? 1 : 3;
   const double L0 = std::log2(o.nu0);
   for (int q = 0; q < M->n_shape; ++q) {
@@ -523,7 +585,6 @@ int launch_shapelets_ws(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* ou
     a.passes = passes;
     a.n_chan = o.n_chan;
     a.n_base = o.n_base;
-    a.n_tiles = n_tiles;
     a.n_vis = n_vis;
     a.c_amp = (float)((double)h.lS + (double)h.alpha * (L0 - h.lref));
     a.alpha = h.alpha;
@@ -533,24 +594,42 @@ int launch_shapelets_ws(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* ou
     a.err = ctx->d_err;
     // the first shapelet applies the caller's mode, the rest add (or subtract G times) their part
     a.mode = q == 0 ? mode : (mode == OUT_STORE ? OUT_ACCUM : (mode == OUT_PEEL ? OUT_SUBG : mode));
+    // two rows per producer / epilogue thread when both parities' doubled A buffers and 4 n_pad TMEM
+    // columns fit; else one
     a.groups = K2_GROUPS;
-    K2Layout lay = k2_layout(h.k_pad, h.n_pad, passes, a.groups);
+    int R = 2;
+    K2Layout lay = k2_layout(h.k_pad, h.n_pad, passes, a.groups, R);
+    if (h.n_pad > 128 || lay.total > 227 * 1024) {
+      R = 1;
+      lay = k2_layout(h.k_pad, h.n_pad, passes, a.groups, R);
+    }
     if (lay.total > 227 * 1024) {  // large n_max in the split mode: one tile in flight
       a.groups = 1;
-      lay = k2_layout(h.k_pad, h.n_pad, passes, 1);
+      lay = k2_layout(h.k_pad, h.n_pad, passes, 1, R);
     }
     if (lay.total > 227 * 1024) return set_error(WN_EINVAL, "shapelet operand does not fit in shared memory");
+    const int n_tiles = (int)((n_vis + K2_M * R - 1) / (K2_M * R));
+    a.n_tiles = n_tiles;
     const int grid = std::min(n_tiles, ctx->num_sms);
     cudaError_t e;
-    switch (h.k_pad) {
-      case 16: e = k2_launch_t<16>(a, grid, lay.total, st); break;
-      case 32: e = k2_launch_t<32>(a, grid, lay.total, st); break;
-      case 48: e = k2_launch_t<48>(a, grid, lay.total, st); break;
-      case 64: e = k2_launch_t<64>(a, grid, lay.total, st); break;
-      case 80: e = k2_launch_t<80>(a, grid, lay.total, st); break;
-      case 96: e = k2_launch_t<96>(a, grid, lay.total, st); break;
-      case 112: e = k2_launch_t<112>(a, grid, lay.total, st); break;
-      default: e = k2_launch_t<128>(a, grid, lay.total, st); break;
+    if (R == 2) {
+      switch (h.k_pad) {
+        case 16: e = k2_launch_t<16, 2>(a, grid, lay.total, st); break;
+        case 32: e = k2_launch_t<32, 2>(a, grid, lay.total, st); break;
+        case 48: e = k2_launch_t<48, 2>(a, grid, lay.total, st); break;
+        default: e = k2_launch_t<64, 2>(a, grid, lay.total, st); break;
+      }
+    } else {
+      switch (h.k_pad) {
+        case 16: e = k2_launch_t<16, 1>(a, grid, lay.total, st); break;
+        case 32: e = k2_launch_t<32, 1>(a, grid, lay.total, st); break;
+        case 48: e = k2_launch_t<48, 1>(a, grid, lay.total, st); break;
+        case 64: e = k2_launch_t<64, 1>(a, grid, lay.total, st); break;
+        case 80: e = k2_launch_t<80, 1>(a, grid, lay.total, st); break;
+        case 96: e = k2_launch_t<96, 1>(a, grid, lay.total, st); break;
+        case 112: e = k2_launch_t<112, 1>(a, grid, lay.total, st); break;
+        default: e = k2_launch_t<128, 1>(a, grid, lay.total, st); break;
+      }
     }
     if (e != cudaSuccess) return set_error(WN_ECUDA, std::string("shapelet kernel launch: ") + cudaGetErrorString(e));
   }
