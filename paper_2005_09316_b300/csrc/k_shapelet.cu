@@ -97,6 +97,19 @@ __device__ __forceinline__ void tmem_issue16x(uint32_t taddr, uint32_t* r) {
       : "r"(taddr));
 }
 
+__device__ __forceinline__ void tmem_issue8x(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait8(uint32_t* r) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7])
+               :
+               : "memory");
+}
+
 __device__ __forceinline__ void tmem_wait16(uint32_t* r) {
   asm volatile("tcgen05.wait::ld.sync.aligned;"
                : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
@@ -226,11 +239,11 @@ __device__ __forceinline__ void produce_rows(const float (&x)[R], int nmax, cons
 
 // Epilogue dot product of one accumulator chunk (16 n2 values: columns 2 n2, 2 n2 + 1 = Re, Im) with
 // phi_n2(y), advancing the y recurrence.  SCALED: values carry 2^E as in produce_row.
-template <bool SCALED>
+template <bool SCALED, int G4 = 2>
 __device__ __forceinline__ void epi_chunk(const uint32_t* t, const float4* ca, const float4* cb, int n0, float y,
                                           float& q, float& q_prev, float& xr, float& xi, int& E, float& scale) {
 #pragma unroll
-  for (int g4 = 0; g4 < 2; ++g4) {
+  for (int g4 = 0; g4 < G4; ++g4) {
     const float4 A = ca[(n0 >> 2) + g4], B = cb[(n0 >> 2) + g4];
     const float av[4] = {A.x, A.y, A.z, A.w};
     const float bv[4] = {B.x, B.y, B.z, B.w};
@@ -244,7 +257,7 @@ __device__ __forceinline__ void epi_chunk(const uint32_t* t, const float4* ca, c
       q_prev = q;
       q = qn;
     }
-    if (SCALED && g4 == 1 && fabsf(q) > 1.8446744e19f) {
+    if (SCALED && g4 == G4 - 1 && fabsf(q) > 1.8446744e19f) {
       q *= 5.421011e-20f;
       q_prev *= 5.421011e-20f;
       E -= 64;
@@ -387,20 +400,17 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
     const float ycut = sqrtf(2.0f * a.nmax + 1.0f) + 10.0f;
     struct EpiIn {
       float4 ri, ci;
-      float2 base;
-      long long vis;
-      bool valid;
     };
+    auto vis_of = [&](int it, int r) { return (long long)(blockIdx.x + it * gridDim.x) * (K2_M * R) + r * K2_M + m; };
+    auto valid_of = [&](int it, long long vis) { return it < n_it && vis < a.n_vis; };
     auto load_epi = [&](int it, int r) {
       EpiIn e;
-      e.vis = (long long)(blockIdx.x + it * gridDim.x) * (K2_M * R) + r * K2_M + m;
-      e.valid = it < n_it && e.vis < a.n_vis;
-      const int row = e.valid ? (int)(e.vis / a.n_chan) : 0;
-      const int f = e.valid ? (int)(e.vis - (long long)row * a.n_chan) : 0;
-      e.ri = e.valid ? __ldg(a.rowinfo + row) : make_float4(0.f, 0.f, 0.f, 0.f);
-      e.ci = e.valid ? __ldg(a.chaninfo + f) : make_float4(0.f, 0.f, 0.f, 1.f);
-      e.base = make_float2(0.f, 0.f);
-      if (e.valid && a.mode != OUT_STORE) e.base = a.mode == OUT_PEEL ? a.peel.data[e.vis] : a.out[e.vis];
+      const long long vis = vis_of(it, r);
+      const bool valid = valid_of(it, vis);
+      const int row = valid ? (int)(vis / a.n_chan) : 0;
+      const int f = valid ? (int)(vis - (long long)row * a.n_chan) : 0;
+      e.ri = valid ? __ldg(a.rowinfo + row) : make_float4(0.f, 0.f, 0.f, 0.f);
+      e.ci = valid ? __ldg(a.chaninfo + f) : make_float4(0.f, 0.f, 0.f, 1.f);
       return e;
     };
     EpiIn nxt[R];
@@ -411,8 +421,18 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
 #pragma unroll
       for (int r = 0; r < R; ++r) cur[r] = nxt[r];
       if (!k2_wait(&mdone[sp], j & 1, a.err)) break;
+      long long vis[R];
+      bool valid[R];
+      float2 base[R];  // the value the output is formed from, in flight while the accumulator is read
 #pragma unroll
-      for (int r = 0; r < R; ++r) nxt[r] = load_epi(it + ng, r);  // next tile's inputs in flight
+      for (int r = 0; r < R; ++r) {
+        vis[r] = vis_of(it, r);
+        valid[r] = valid_of(it, vis[r]);
+        base[r] = make_float2(0.f, 0.f);
+        if (valid[r] && a.mode != OUT_STORE) base[r] = a.mode == OUT_PEEL ? a.peel.data[vis[r]] : a.out[vis[r]];
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) nxt[r] = load_epi(it + ng, r);  // next tile's constants in flight
       tc_fence_after();
       float y[R], q[R], q_prev[R], scale[R], xr[R], xi[R];
       int E[R];
@@ -420,7 +440,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         y[r] = cur[r].ri.y * cur[r].ci.w;
-        const bool yzero = !cur[r].valid || !(fabsf(y[r]) <= ycut);
+        const bool yzero = !valid[r] || !(fabsf(y[r]) <= ycut);
         yfast = yfast && (yzero || fabsf(y[r]) <= 12.5f);
         q[r] = yzero ? 0.f : 1.f;  // marks zero rows until the seed below
         xr[r] = xi[r] = 0.f;
@@ -452,7 +472,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
             tmem_wait16(tb0);
           }
         }
-      } else {  // R rows: one chunk of every row in flight, their recurrences interleaved
+      } else {  // R rows: a 16-column chunk of every row in flight, their recurrences interleaved
         uint32_t tb[R][16];
 #pragma unroll 1
         for (int c = 0; c < nch; ++c) {
@@ -471,24 +491,23 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
       mbar_arrive(&tfree[sp]);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        if (!cur[r].valid) continue;
+        if (!valid[r]) continue;
         const float4 ri = cur[r].ri, ci = cur[r].ci;
         const float2 P = phasor_fast(reduce_turns(ri.z, ri.w, ci.x, ci.y));
         const float amp = a.sgn * ex2_approx(fmaf(a.alpha, ci.z, a.c_amp));
         // Z = amp (xr + i xi) P
         const float zr = amp * (xr[r] * P.x - xi[r] * P.y), zi = amp * (xr[r] * P.y + xi[r] * P.x);
-        const size_t idx = (size_t)cur[r].vis;
-        const float2 base = cur[r].base;
+        const size_t idx = (size_t)vis[r];
         if (a.mode == OUT_STORE) {
           a.out[idx] = make_float2(zr, zi);
         } else if (a.mode == OUT_ACCUM) {
-          a.out[idx] = make_float2(base.x + zr, base.y + zi);
+          a.out[idx] = make_float2(base[r].x + zr, base[r].y + zi);
         } else {
-          const int row = (int)(cur[r].vis / a.n_chan);
-          const int f = (int)(cur[r].vis - (long long)row * a.n_chan);
+          const int row = (int)(vis[r] / a.n_chan);
+          const int f = (int)(vis[r] - (long long)row * a.n_chan);
           float2 G;
           if (!gain_product(a.peel, row, a.n_base, f, G)) atomicOr(a.err, WN_DEVERR_ANTENNA);
-          a.out[idx] = make_float2(base.x - (G.x * zr - G.y * zi), base.y - (G.x * zi + G.y * zr));
+          a.out[idx] = make_float2(base[r].x - (G.x * zr - G.y * zi), base[r].y - (G.x * zi + G.y * zr));
         }
       }
     }
