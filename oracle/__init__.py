@@ -317,3 +317,43 @@ def calibrate(ant1, ant2, n_ant: int, I, V, g0, n_iter: int = 10):
             for _ in range(n_iter):
                 g[t, f] = calib_step(ant1, ant2, n_ant, I[t, :, f], V[t, :, f], g[t, f])
     return g
+
+
+# ------------------------------------------------------------------------------------------------
+# Visibility-space least-squares fit of shapelet coefficients (the counterpart of the image-space fit
+# of Sec. 2.2): V is linear in the coefficients, so column k of the design matrix is the (gain-applied)
+# visibility of coefficient k alone at unit value; the model's points and Gaussians are a fixed part.
+# numpy's lstsq is the library step for the real least-squares problem on stacked Re / Im parts.
+# ------------------------------------------------------------------------------------------------
+
+def _shapelet_only(sky, coeff):
+    import copy
+    s = copy.deepcopy(sky)
+    n_pg = sky.n_point + sky.n_gauss
+    s.flux = np.array(sky.flux, dtype=np.float64).copy()
+    s.flux[:n_pg] = 0.0
+    s.s_coeff = np.asarray(coeff, dtype=np.float64).copy()
+    return s
+
+
+def fit_design(uvw_rows, freq, dec0, sky, G):
+    """Complex design matrix [R*F, nnz]: column k = G * V(shapelets with only coefficient k = 1)."""
+    nnz = int(sky.s_off[-1])
+    cols = []
+    for k in range(nnz):
+        e = np.zeros(nnz)
+        e[k] = 1.0
+        cols.append((G * predict(uvw_rows, freq, dec0, _shapelet_only(sky, e))).ravel())
+    return np.stack(cols, axis=1)
+
+
+def fit_shapelet_coeffs(uvw_rows, freq, dec0, sky, G, data):
+    """Least-squares coefficients of |D - G (V_fixed + A C)|^2 over the given rows (G and D [R, F])."""
+    import copy
+    pg = copy.deepcopy(sky)
+    pg.s_coeff = np.zeros(int(sky.s_off[-1]))          # the fixed part: points and Gaussians only
+    b = (np.asarray(data) - G * predict(uvw_rows, freq, dec0, pg)).ravel()
+    A = fit_design(uvw_rows, freq, dec0, sky, G)
+    Ar = np.concatenate([A.real, A.imag], axis=0)
+    br = np.concatenate([b.real, b.imag])
+    return np.linalg.lstsq(Ar, br, rcond=None)[0]
