@@ -249,6 +249,29 @@ WN_API int wn_server_stats(wn_server* srv, double* stats);
  * The model must already be resident (wn_sky_upload) and the context created beforehand. */
 WN_API int wn_predict_static(wn_ctx* ctx, const wn_obs* obs, int model_id, void* vis_c64, int accumulate, void* stream);
 
+/* ---- visibility-space shapelet fitting ------------------------------------------------------- */
+
+/* Fit the shapelet coefficients of a resident model to data by linear least squares in visibility
+ * space.  The model's positions, scales and position angles, and its points and Gaussians, stay
+ * fixed.  The visibilities are linear in the coefficients C (eq:shape-env), so the C minimising
+ * sum |D - G (V_fixed + V_shapelets(C))|^2 solves the normal equations.  The paper fits in image space
+ * (Sec. 2.2); this is the visibility-space counterpart.  Solved by CGLS from the starting
+ * coefficients, without forming the normal matrix.  Each iteration is one shapelet contraction and one
+ * coefficient adjoint.  It stops after n_iter iterations, or when the normal-equation residual
+ * |A^T r| has fallen below tol times its starting value.
+ *   gains_c64    device [gains_t][gains_f][n_ant] complex64 (1 or n_time, 1 or n_chan);
+ *   data_c64     D, device [n_time][n_base][n_chan] complex64;
+ *   coeff_inout  device double [nnz]: every shapelet coefficient of the model, in upload order;
+ *                starting values in, fitted values out;
+ *   info         host double[4] or NULL: iterations run, final |A^T r| / starting |A^T r|, final and
+ *                starting sum |r|^2.
+ * On return the model holds the fitted coefficients (later predictions and peels use them).
+ * Synchronises `stream` once per iteration and allocates its scratch per call.  WN_EINVAL if the
+ * model has no shapelet coefficients or the context is not in the mixed precision. */
+WN_API int wn_fit_shapelets(wn_ctx* ctx, const wn_obs* obs, int model_id, const void* gains_c64, int gains_t,
+                            int gains_f, const void* data_c64, int n_iter, double tol, double* coeff_inout,
+                            double* info, void* stream);
+
 /* ---- gain calibration ------------------------------------------------------------------------- */
 
 /* Fit one complex gain per antenna for every (time, channel): the linearised least squares of Sec. 5.1

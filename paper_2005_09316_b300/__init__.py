@@ -28,7 +28,7 @@ EXPORTED = ("wn_create", "wn_destroy", "wn_last_error", "wn_version", "wn_set_pr
             "wn_sky_upload", "wn_sky_free", "wn_sky_bytes", "wn_predict", "wn_peel", "wn_peel_model",
             "wn_predict_grad", "wn_predict_static", "wn_server_create", "wn_server_destroy", "wn_server_submit",
             "wn_server_poll", "wn_server_wait", "wn_server_copy", "wn_server_release", "wn_server_cancel",
-            "wn_server_stats", "wn_calibrate", "wn_pipe_rates")
+            "wn_server_stats", "wn_calibrate", "wn_fit_shapelets", "wn_pipe_rates")
 
 
 class WnError(RuntimeError):
@@ -100,6 +100,7 @@ def load(build_if_missing: bool = True):
         L.wn_server_cancel.argtypes = [P, u64]
         L.wn_server_stats.argtypes = [P, ctypes.POINTER(dbl)]
         L.wn_calibrate.argtypes = [P, ctypes.POINTER(WnObs), P, P, P, i, P]
+        L.wn_fit_shapelets.argtypes = [P, ctypes.POINTER(WnObs), i, P, i, i, P, i, dbl, P, ctypes.POINTER(dbl), P]
         L.wn_pipe_rates.argtypes = [P, ctypes.POINTER(dbl)]
         for name in EXPORTED:
             if name not in ("wn_destroy", "wn_last_error", "wn_version", "wn_server_destroy"):
@@ -270,6 +271,22 @@ class Context:
         _check(load().wn_calibrate(self.h, ctypes.byref(o), model_vis.data_ptr(), data.data_ptr(), gains.data_ptr(),
                                    int(n_iter), _stream_handle(stream)))
         return gains
+
+    def fit_shapelets(self, obs: DeviceObs, model: Model, gains, data, coeff=None, n_iter: int = 200,
+                      tol: float = 1e-6, stream=None):
+        """Least-squares shapelet coefficients of `model` for `data` (visibility space, CGLS); returns
+        (coefficients as a float64 device tensor in upload order, info dict).  The model keeps them."""
+        torch = _torch()
+        if coeff is None:
+            coeff = torch.zeros(model.nnz, dtype=torch.float64, device=f"cuda:{self.device}")
+        if coeff.dtype != torch.float64 or coeff.numel() != model.nnz or not coeff.is_contiguous():
+            raise ValueError("coeff must be a contiguous float64 tensor of the model's nnz")
+        info = (ctypes.c_double * 4)()
+        o = obs.struct()
+        _check(load().wn_fit_shapelets(self.h, ctypes.byref(o), model.id, gains.data_ptr(), int(gains.shape[0]),
+                                       int(gains.shape[1]), data.data_ptr(), int(n_iter), float(tol),
+                                       coeff.data_ptr(), info, _stream_handle(stream)))
+        return coeff, {"iterations": int(info[0]), "rel_grad": info[1], "resid2": info[2], "resid2_start": info[3]}
 
     def pipe_rates(self) -> dict:
         """Measured lane operations per second of the FP32 FMA, packed FFMA2, MUFU ex2 and FP64 FMA pipes."""

@@ -1,0 +1,186 @@
+// K8: visibility-space fitting of shapelet coefficients.  The visibilities are linear in the shapelet
+// coefficients C (eq:shape-env): V = V_fixed + A C, where (A C)(vis) = G sum_k C_k S(nu) (-i)^(n1+n2)
+// phi_n1(x) phi_n2(y) e^{-2 pi i tau nu / c} and V_fixed holds the model's points and Gaussians.  The
+// least-squares C of |D - V|^2 over all visibilities solves A^T A C = A^T (D - V_fixed); this is the
+// visibility-space counterpart of the image-space fit of Sec. 2.2.  It is solved by CGLS (conjugate
+// gradients on the normal equations) without forming A^T A.
+//  - A p is one shapelet contraction (K2) of the model re-packed with coefficients p, subtracted as G V
+//    from a zero buffer.
+//  - A^T r is the coefficient part of the adjoint (K4) for residual r, times -1/2.
+//  - Vector updates and norms are small kernels here; norms are reduced in FP64 in a fixed order.
+// Positions, scales and position angles stay fixed.
+#include <cmath>
+#include <vector>
+
+#include "wn_internal.cuh"
+
+namespace wn {
+
+int launch_grad_shape_coeff(wn_ctx* ctx, const ObsDev& o, const Model* M, const PeelArgs& pa, const float2* resid,
+                            double* gcoeff, cudaStream_t st);
+int launch_pack_coeff(wn_ctx* ctx, Model* M, const double* coeff, const int* dmeta, cudaStream_t st);
+int run_model_peel(wn_ctx* ctx, const ObsDev& d, const Model* M, float2* out, const PeelArgs& pa, cudaStream_t st);
+
+constexpr int K8_T = 256;
+
+__global__ void k8_norm2_c64(const float2* v, size_t n, double* part) {
+  __shared__ double red[K8_T];
+  double s = 0.0;
+  for (size_t i = (size_t)blockIdx.x * K8_T + threadIdx.x; i < n; i += (size_t)gridDim.x * K8_T) {
+    const float2 x = v[i];
+    s += (double)x.x * x.x + (double)x.y * x.y;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = K8_T / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void k8_norm2_f64(const double* v, int n, double* part) {
+  __shared__ double red[K8_T];
+  double s = 0.0;
+  for (int i = blockIdx.x * K8_T + threadIdx.x; i < n; i += gridDim.x * K8_T) s += v[i] * v[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = K8_T / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void k8_sum(const double* part, int n, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += part[i];
+    *out = s;
+  }
+}
+
+__global__ void k8_axpy_c64(float2* y, const float2* x, size_t n, float a) {  // y += a x
+  for (size_t i = (size_t)blockIdx.x * K8_T + threadIdx.x; i < n; i += (size_t)gridDim.x * K8_T) {
+    const float2 u = y[i], v = x[i];
+    y[i] = make_float2(fmaf(a, v.x, u.x), fmaf(a, v.y, u.y));
+  }
+}
+
+__global__ void k8_vec_f64(double* y, const double* x, int n, double a, double b) {  // y = a x + b y
+  for (int i = blockIdx.x * K8_T + threadIdx.x; i < n; i += gridDim.x * K8_T) y[i] = a * x[i] + b * y[i];
+}
+
+int launch_fit_shapelets(wn_ctx* ctx, const ObsDev& o, Model* M, const PeelArgs& pa, int n_iter, double tol,
+                         double* coeff, double* info, cudaStream_t st) {
+  const size_t n_vis = (size_t)o.n_rows * o.n_chan;
+  const int nnz = M->nnz, S = M->n_shape;
+  const int vgrid = ctx->num_sms * 2, cgrid = std::max(1, std::min(ctx->num_sms, (nnz + K8_T - 1) / K8_T));
+  // scratch: r, q (visibilities), s, p, g (coefficients), meta (b_off, k_pad, n_pad), partials, scalar
+  float2 *r = nullptr, *q = nullptr;
+  double *sv = nullptr, *pv = nullptr, *gv = nullptr, *part = nullptr, *scal = nullptr;
+  int* meta = nullptr;
+  cudaError_t e = cudaMalloc(&r, n_vis * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMalloc(&q, n_vis * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMalloc(&sv, 3 * (size_t)nnz * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&part, (vgrid + 8) * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&meta, 3 * (size_t)S * sizeof(int));
+  auto release = [&]() {
+    cudaStreamSynchronize(st);
+    cudaFree(r);
+    cudaFree(q);
+    cudaFree(sv);
+    cudaFree(part);
+    cudaFree(meta);
+  };
+  if (e != cudaSuccess) {
+    release();
+    return set_error(WN_ENOMEM, std::string("fit workspace: ") + cudaGetErrorString(e));
+  }
+  pv = sv + nnz;
+  gv = pv + nnz;
+  scal = part + vgrid;
+  cudaMemsetAsync(sv, 0, 3 * (size_t)nnz * sizeof(double), st);
+  {
+    std::vector<int> h(3 * S);
+    for (int k = 0; k < S; ++k) {
+      h[k] = M->sh_host[k].b_off;
+      h[S + k] = M->sh_host[k].k_pad;
+      h[2 * S + k] = M->sh_host[k].n_pad;
+    }
+    cudaMemcpyAsync(meta, h.data(), sizeof(int) * 3 * S, cudaMemcpyHostToDevice, st);
+    cudaStreamSynchronize(st);
+  }
+  auto norm2_vis = [&](const float2* v, double* out_host) {
+    k8_norm2_c64<<<vgrid, K8_T, 0, st>>>(v, n_vis, part);
+    k8_sum<<<1, 32, 0, st>>>(part, vgrid, scal);
+    cudaMemcpyAsync(out_host, scal, sizeof(double), cudaMemcpyDeviceToHost, st);
+  };
+  auto norm2_coef = [&](const double* v, double* out_host) {
+    k8_norm2_f64<<<cgrid, K8_T, 0, st>>>(v, nnz, part);
+    k8_sum<<<1, 32, 0, st>>>(part, cgrid, scal);
+    cudaMemcpyAsync(out_host, scal, sizeof(double), cudaMemcpyDeviceToHost, st);
+  };
+  // s = A^T r = -1/2 dL/dC
+  auto atr = [&](const float2* res) -> int {
+    if (int rc = launch_grad_shape_coeff(ctx, o, M, pa, res, gv, st)) return rc;
+    k8_vec_f64<<<cgrid, K8_T, 0, st>>>(sv, gv, nnz, -0.5, 0.0);
+    return WN_OK;
+  };
+  int rc = WN_OK;
+  double rr0 = 0, rr = 0, gam0 = 0, gam = 0;
+  int it = 0;
+  // r0 = D - G (V_fixed + A x0)
+  if (!rc) rc = launch_pack_coeff(ctx, M, coeff, meta, st);
+  if (!rc) rc = run_model_peel(ctx, o, M, r, pa, st);
+  if (!rc) norm2_vis(r, &rr0);
+  if (!rc) rc = atr(r);
+  if (!rc) {
+    cudaMemcpyAsync(pv, sv, (size_t)nnz * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    norm2_coef(sv, &gam0);
+    cudaStreamSynchronize(st);
+    gam = gam0;
+    rr = rr0;
+  }
+  for (; !rc && it < n_iter && gam > tol * tol * gam0 && gam > 0.0; ++it) {
+    // q = -A p
+    rc = launch_pack_coeff(ctx, M, pv, meta, st);
+    if (rc) break;
+    cudaMemsetAsync(q, 0, n_vis * sizeof(float2), st);
+    rc = launch_shapelets(ctx, o, M, q, OUT_SUBG, pa, st);
+    if (rc) break;
+    double qq = 0;
+    norm2_vis(q, &qq);
+    cudaStreamSynchronize(st);
+    if (!(qq > 0.0)) break;
+    const double alpha = gam / qq;
+    k8_vec_f64<<<cgrid, K8_T, 0, st>>>(coeff, pv, nnz, alpha, 1.0);   // x += alpha p
+    k8_axpy_c64<<<vgrid, K8_T, 0, st>>>(r, q, n_vis, (float)alpha);  // r -= alpha A p
+    rc = atr(r);
+    if (rc) break;
+    double gnew = 0;
+    norm2_coef(sv, &gnew);
+    cudaStreamSynchronize(st);
+    k8_vec_f64<<<cgrid, K8_T, 0, st>>>(pv, sv, nnz, 1.0, gnew / gam);  // p = s + beta p
+    gam = gnew;
+  }
+  // the model keeps the fitted coefficients: dense operand and the FP64 copy
+  if (!rc) rc = launch_pack_coeff(ctx, M, coeff, meta, st);
+  if (!rc) {
+    cudaMemcpyAsync(M->s_coeff, coeff, (size_t)nnz * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    norm2_vis(r, &rr);
+    cudaStreamSynchronize(st);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) rc = set_error(WN_ECUDA, std::string("fit: ") + cudaGetErrorString(e));
+  }
+  if (info) {
+    info[0] = it;
+    info[1] = gam0 > 0 ? std::sqrt(gam / gam0) : 0.0;
+    info[2] = rr;
+    info[3] = rr0;
+  }
+  release();
+  return rc;
+}
+
+}  // namespace wn

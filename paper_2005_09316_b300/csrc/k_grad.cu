@@ -706,4 +706,89 @@ int launch_grad(wn_ctx* ctx, const ObsDev& o, const Model* M, const PeelArgs& pa
   return WN_OK;
 }
 
+// Coefficient gradients only, for a residual the caller provides: gcoeff[k] = dL/dC_k of
+// L = sum |R - G V|^2 with respect to every shapelet coefficient of M (triple order), evaluated as
+// -2 Re sum conj(conj(G) R) dV/dC_k.  It is linear in R and does not depend on the coefficients, so
+// -gcoeff / 2 is the adjoint of the linear map C -> G V_shapelets(C) applied to R.
+int launch_grad_shape_coeff(wn_ctx* ctx, const ObsDev& o, const Model* M, const PeelArgs& pa, const float2* resid,
+                            double* gcoeff, cudaStream_t st) {
+  if (int r = grad_constants(ctx->device, st)) return r;
+  int max_nnz = 0;
+  for (int q = 0; q < M->n_shape; ++q) max_nnz = std::max(max_nnz, M->s_off_host[q + 1] - M->s_off_host[q]);
+  const int sgrid = ctx->num_sms * 4;
+  const size_t chan_bytes = ((size_t)o.n_chan * sizeof(float4) + 255) & ~(size_t)255;
+  const size_t row_bytes = ((size_t)o.n_rows * sizeof(float4) + 255) & ~(size_t)255;
+  const size_t uvp_bytes = ((size_t)o.n_rows * 6 * sizeof(float) + 255) & ~(size_t)255;
+  const size_t sh_bytes = (((size_t)sgrid * (K4S_NS + max_nnz) * 8 + 255) & ~(size_t)255);
+  const size_t need = chan_bytes + row_bytes + uvp_bytes + sh_bytes;
+  if (ctx->ws2_bytes < need) {
+    if (ctx->ws2) {
+      cudaStreamSynchronize(st);
+      cudaFree(ctx->ws2);
+      ctx->ws2 = nullptr;
+      ctx->ws2_bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&ctx->ws2, need);
+    if (e != cudaSuccess) return set_error(WN_ENOMEM, std::string("adjoint workspace: ") + cudaGetErrorString(e));
+    ctx->ws2_bytes = need;
+  }
+  char* ws = static_cast<char*>(ctx->ws2);
+  float4* chaninfo = reinterpret_cast<float4*>(ws);
+  float4* rowinfo = reinterpret_cast<float4*>(ws + chan_bytes);
+  float* uvp = reinterpret_cast<float*>(ws + chan_bytes + row_bytes);
+  double* shpart = reinterpret_cast<double*>(ws + chan_bytes + row_bytes + uvp_bytes);
+  k4_split_uvw<<<(3 * o.n_rows + 255) / 256, 256, 0, st>>>(o.uvw, o.n_rows, uvp);
+  if (int r = cuda_err("uvw split")) return r;
+  const double L0 = std::log2(o.nu0);
+  const int n_pg = M->n_point + M->n_gauss;
+  const size_t n_vis = (size_t)o.n_rows * o.n_chan;
+  for (int q = 0; q < M->n_shape; ++q) {
+    if (int r = launch_shapelet_prep(ctx, o, M, q, chaninfo, rowinfo, q == 0, st)) return r;
+    const ShapeRec& h = M->sh_host[q];
+    const int j = n_pg + q;
+    K4SArgs a;
+    a.rowinfo = rowinfo;
+    a.chaninfo = chaninfo;
+    a.uvw_pairs = uvp;
+    a.n_rows = o.n_rows;
+    a.n_chan = o.n_chan;
+    a.n_base = o.n_base;
+    a.n_vis = (long long)n_vis;
+    a.nmax = h.nmax;
+    a.nnz = M->s_off_host[q + 1] - M->s_off_host[q];
+    a.n1 = M->m_n1() + M->s_off_host[q];
+    a.n2 = M->m_n2() + M->s_off_host[q];
+    a.coeff = M->s_coeff + M->s_off_host[q];
+    a.lnref_nu0_f = (float)((L0 - h.lref) * 0.6931471805599453);
+    a.l_over_n = (float)(h.l / (1.0 + h.nm1));
+    a.m_over_n = (float)(h.m / (1.0 + h.nm1));
+    a.c_amp = (float)((double)h.alpha * (L0 - h.lref));
+    a.alpha = h.alpha;
+    a.flux = M->r_flux() + j;
+    a.beta1 = M->r_sb1() + q;
+    a.beta2 = M->r_sb2() + q;
+    a.resid = resid;
+    a.peel = pa;
+    a.part_s = shpart;
+    a.part_c = shpart + (size_t)sgrid * K4S_NS;
+    a.err = ctx->d_err;
+    const size_t smax = 227 * 1024 - sizeof(double) * K4S_T * K4S_NS;
+    int T = K4S_T;
+    size_t smem = (size_t)k4s_layout(h.nmax, a.nnz, T).total;
+    if (smem > smax) {
+      T = K4S_T / 2;
+      smem = (size_t)k4s_layout(h.nmax, a.nnz, T).total;
+    }
+    if (smem > smax) return set_error(WN_EINVAL, "adjoint: shapelet too large for the shared-memory reduction");
+    cudaFuncSetAttribute(k4_grad_shape, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k4_grad_shape<<<sgrid, T, smem, st>>>(a);
+    const int nout = a.nnz + K4S_NS;
+    k4_reduce_shape<<<(nout * 32 + 255) / 256, 256, 0, st>>>(shpart, shpart + (size_t)sgrid * K4S_NS, sgrid, a.nnz, j,
+                                                            q, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                            nullptr, gcoeff, M->s_off_host[q], 1);
+    if (int r = cuda_err("shapelet coefficient adjoint")) return r;
+  }
+  return WN_OK;
+}
+
 }  // namespace wn

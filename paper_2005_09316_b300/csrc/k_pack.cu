@@ -139,3 +139,18 @@ int launch_pack(wn_ctx* ctx, const wn_sky* s, Model* M, cudaStream_t st) {
 }
 
 }  // namespace wn
+
+namespace wn {
+
+// Re-pack the dense coefficient operand of a resident model from a new coefficient vector (device,
+// FP64, the model's triple order); dmeta holds the per-shapelet b_off, k_pad, n_pad (device ints).
+int launch_pack_coeff(wn_ctx* ctx, Model* M, const double* coeff, const int* dmeta, cudaStream_t st) {
+  if (M->n_shape == 0 || M->nnz == 0) return WN_OK;
+  cudaMemsetAsync(M->bop, 0, M->bop_elems * sizeof(__nv_bfloat16), st);
+  k_pack_coeff<<<(M->nnz + 255) / 256, 256, 0, st>>>(M->nnz, M->m_n1(), M->m_n2(), coeff, M->m_off(), M->m_nmax(),
+                                                     M->n_shape, dmeta, dmeta + M->n_shape, dmeta + 2 * M->n_shape,
+                                                     M->bop, ctx->d_err);
+  return cuda_check(cudaGetLastError(), "pack coefficients");
+}
+
+}  // namespace wn

@@ -444,6 +444,23 @@ int wn_predict_grad(wn_ctx* ctx, const wn_obs* obs, int model_id, const void* ga
   return r == WN_OK ? ok() : r;
 }
 
+int wn_fit_shapelets(wn_ctx* ctx, const wn_obs* obs, int model_id, const void* gains_c64, int gains_t, int gains_f,
+                     const void* data_c64, int n_iter, double tol, double* coeff_inout, double* info, void* stream) {
+  if (!ctx || !coeff_inout) return set_error(WN_EINVAL, "NULL argument");
+  ObsDev d;
+  if (int r = check_obs(obs, d)) return r;
+  Model* M = find_model(ctx, model_id);
+  if (!M) return set_error(WN_ENOTFOUND, "unknown model id");
+  if (M->n_shape < 1 || M->nnz < 1) return set_error(WN_EINVAL, "wn_fit_shapelets: the model has no shapelet coefficients");
+  PeelArgs pa;
+  if (int r = check_gains(d, gains_c64, gains_t, gains_f, data_c64, pa)) return r;
+  if (n_iter < 0 || n_iter > 100000 || !(tol >= 0.0)) return set_error(WN_EINVAL, "wn_fit_shapelets: bad n_iter or tol");
+  if (ctx->precision != WN_PREC_MIXED) return set_error(WN_EINVAL, "wn_fit_shapelets runs in the mixed precision only");
+  DeviceGuard g(ctx->device);
+  int r = launch_fit_shapelets(ctx, d, M, pa, n_iter, tol, coeff_inout, info, static_cast<cudaStream_t>(stream));
+  return r == WN_OK ? ok() : r;
+}
+
 int wn_calibrate(wn_ctx* ctx, const wn_obs* obs, const void* model_c64, const void* data_c64, void* gains_c64,
                  int n_iter, void* stream) {
   if (!ctx || !model_c64 || !data_c64 || !gains_c64) return set_error(WN_EINVAL, "NULL argument");

@@ -330,6 +330,8 @@ size_t static_scratch_entries();
 int launch_grad(wn_ctx* ctx, const ObsDev& o, const Model* M, const PeelArgs& pa, float2* resid,
                 const wn_sky_grad* g, double* loss, cudaStream_t st);
 int k1_batched_smem();
+int launch_fit_shapelets(wn_ctx* ctx, const ObsDev& o, Model* M, const PeelArgs& pa, int n_iter, double tol,
+                         double* coeff, double* info, cudaStream_t st);
 int launch_calibrate(wn_ctx* ctx, const ObsDev& o, const float2* model, const float2* data, float2* gains, int n_iter,
                      cudaStream_t st);
 cudaError_t k1_batched_setup();
