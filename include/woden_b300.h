@@ -60,14 +60,17 @@ typedef enum {
 
 /* Precision of the point/Gaussian phasor sum. */
 typedef enum {
-    WN_PREC_MIXED = 0,   /* FP64 phase argument, FP32 phasors and sums (default) */
+    WN_PREC_MIXED = 0,   /* double-float phase argument, FP32 phasors and sums (default) */
     WN_PREC_FP64 = 1     /* every step in FP64: the plain reference form */
 } wn_precision;
 
 /* Precision of the tensor-core shapelet contraction (xi = A C B^T, Sec. 3.2 eq:shape-env). */
 typedef enum {
     WN_SHAPE_BF16X3 = 0, /* bf16 hi+lo split of both operands, three products, FP32 accumulate (default) */
-    WN_SHAPE_BF16X1 = 1  /* plain bf16 operands, one product, FP32 accumulate */
+    WN_SHAPE_BF16X1 = 1, /* plain bf16 operands, one product, FP32 accumulate */
+    WN_SHAPE_LUT_BF16X3 = 2 /* as BF16X3, but the Hermite functions are interpolated linearly from a 1-D table
+                               (spacing 1/256, orders 0..127; the look-up tables of Sec. 3.2) instead of the
+                               recurrence; the table (6.8 MB) is built once per context */
 } wn_shape_mode;
 
 /* Device-side error flags (bit mask) reported by wn_device_errors. */

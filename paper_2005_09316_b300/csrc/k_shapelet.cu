@@ -43,10 +43,18 @@ constexpr int K2_MMA_WARP = 8 * K2_GROUPS;
 __constant__ float c_herm_a[kNmaxLimit + 1];
 __constant__ float c_herm_b[kNmaxLimit + 1];
 
+// Lookup-table form of the basis (the 1-D tables of Sec. 3.2): phi_0..phi_127 at x_i = -K2_LUT_X + i / K2_LUT_D,
+// row i of 128 floats, interpolated linearly.  |x| beyond sqrt(2 * 127 + 1) + 10 < K2_LUT_X is zero.
+constexpr float K2_LUT_X = 26.0f;
+constexpr int K2_LUT_D = 256;                                   // samples per unit of x
+constexpr int K2_LUT_N = 2 * 26 * K2_LUT_D + 2;                 // samples
+constexpr int K2_LUT_W = 128;                                   // orders per sample
+
 struct K2Args {
   const float4* rowinfo;     // [n_rows] (xs, ys, tau_hi, tau_lo): x = xs nu, y = ys nu, tau in metres
   const float4* chaninfo;    // [n_chan] (nu/c hi, nu/c lo, log2(nu/nu0), nu)
   const __nv_bfloat16* bop;  // this shapelet's packed B operand: hi [n_pad][kp], then lo
+  const float* lut;          // basis table (lookup-table mode only)
   int n_pad, nmax, passes, n_chan, n_base, n_tiles, mode, groups;
   long long n_vis;
   float c_amp, alpha, sgn;
@@ -211,6 +219,49 @@ __device__ __forceinline__ void produce_rows_run(const float (&x)[R], float (&p)
 
 // Rows r of this thread go to row `row` of block r (a_base + r * blk).  The scaled form is taken for
 // all R rows when any of them needs it (it is exact for every x).
+// Table position of x: sample index i (rows i, i + 1 interpolated with weight t), or -1 for a zero row.
+__device__ __forceinline__ int lut_pos(float x, bool valid, float xcut, float& t) {
+  if (!valid || !(fabsf(x) <= xcut)) {
+    t = 0.f;
+    return -1;
+  }
+  const float u = (x + K2_LUT_X) * (float)K2_LUT_D;
+  const int i = min(max((int)floorf(u), 0), K2_LUT_N - 2);
+  t = u - (float)i;
+  return i;
+}
+
+template <int KP, int R>
+__device__ __forceinline__ void produce_rows_lut(const float (&x)[R], int nmax, const bool (&valid)[R],
+                                                 unsigned char* a_base, int blk, bool split, int row, const float* lut) {
+  const float xcut = sqrtf(2.0f * nmax + 1.0f) + 10.0f;
+  int ip[R];
+  float tw[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) ip[r] = lut_pos(x[r], valid[r], xcut, tw[r]);
+#pragma unroll 1
+  for (int k0 = 0; k0 < KP; k0 += 8) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      float v[8];
+      if (ip[r] < 0) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = 0.f;
+      } else {
+        const float4* a = reinterpret_cast<const float4*>(lut + (size_t)ip[r] * K2_LUT_W + k0);
+        const float4* b = reinterpret_cast<const float4*>(lut + (size_t)(ip[r] + 1) * K2_LUT_W + k0);
+        const float4 a0 = __ldg(a), a1 = __ldg(a + 1), b0 = __ldg(b), b1 = __ldg(b + 1);
+        const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = fmaf(tw[r], bv[i] - av[i], av[i]);
+      }
+      unsigned char* hi = a_base + r * blk;
+      store_bf16_split(v, hi, split ? hi + KP * K2_M * 2 : nullptr, kmaj_off(row, k0, K2_M));
+    }
+  }
+}
+
 template <int KP, int R>
 __device__ __forceinline__ void produce_rows(const float (&x)[R], int nmax, const bool (&valid)[R], unsigned char* a_base,
                                              int blk, bool split, int row, const float4* ca, const float4* cb) {
@@ -266,7 +317,24 @@ __device__ __forceinline__ void epi_chunk(const uint32_t* t, const float4* ca, c
   }
 }
 
-template <int KP, int R>
+// Epilogue dot product of one 16-column chunk with table-interpolated phi_n2(y), n2 = n0 .. n0 + 7.
+__device__ __forceinline__ void epi_chunk_lut(const uint32_t* t, const float* lut, int iy, float ty, int n0, float& xr,
+                                              float& xi) {
+  if (iy < 0) return;
+  const float4* a = reinterpret_cast<const float4*>(lut + (size_t)iy * K2_LUT_W + n0);
+  const float4* b = reinterpret_cast<const float4*>(lut + (size_t)(iy + 1) * K2_LUT_W + n0);
+  const float4 a0 = __ldg(a), a1 = __ldg(a + 1), b0 = __ldg(b), b1 = __ldg(b + 1);
+  const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+  const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const float ph = fmaf(ty, bv[i] - av[i], av[i]);
+    xr = fmaf(__uint_as_float(t[2 * i]), ph, xr);
+    xi = fmaf(__uint_as_float(t[2 * i + 1]), ph, xi);
+  }
+}
+
+template <int KP, int R, bool LUT>
 __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int ng = a.groups;  // tile parities in flight (2, or 1 when two A buffers do not fit)
@@ -387,7 +455,8 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
       }
       load_x(it + ng, valid, xs, nu);
       if (j > 0 && !k2_wait(&mdone[sp], (j - 1) & 1, a.err)) break;  // MMA(j-1) has read A
-      produce_rows<KP, R>(x, a.nmax, v0, a_base, blk, a.passes > 1, m, ca, cb);
+      if (LUT) produce_rows_lut<KP, R>(x, a.nmax, v0, a_base, blk, a.passes > 1, m, a.lut);
+      else produce_rows<KP, R>(x, a.nmax, v0, a_base, blk, a.passes > 1, m, ca, cb);
       fence_async_smem();
       mbar_arrive(&afull[sp]);
     }
@@ -455,7 +524,22 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
       }
       // accumulator rows in chunks of 16 columns (8 n2)
       const int nch = a.n_pad >> 4;
-      if (R == 1) {  // one row: the next chunk's load in flight while one is used
+      if (LUT) {  // table-interpolated phi_n2(y): one chunk of every row at a time
+        int iy[R];
+        float ty[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) iy[r] = lut_pos(y[r], valid[r], ycut, ty[r]);
+        uint32_t tb[R][16];
+#pragma unroll 1
+        for (int c = 0; c < nch; ++c) {
+#pragma unroll
+          for (int r = 0; r < R; ++r) tmem_issue16x(trow + (uint32_t)(r * a.n_pad + (c << 4)), tb[r]);
+#pragma unroll
+          for (int r = 0; r < R; ++r) tmem_wait16(tb[r]);
+#pragma unroll
+          for (int r = 0; r < R; ++r) epi_chunk_lut(tb[r], a.lut, iy[r], ty[r], c << 3, xr[r], xi[r]);
+        }
+      } else if (R == 1) {  // one row: the next chunk's load in flight while one is used
         uint32_t tb0[16], tb1[16];
         tmem_issue16x(trow, tb0);
         tmem_wait16(tb0);
@@ -560,13 +644,66 @@ static int k2_setup_constants(int device, cudaStream_t st) {
   return WN_OK;
 }
 
-template <int KP, int R>
+template <int KP, int R, bool LUT>
 static cudaError_t k2_launch_t(const K2Args& a, int grid, int smem, cudaStream_t st) {
-  auto fn = k2_shapelet<KP, R>;
+  auto fn = k2_shapelet<KP, R, LUT>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   fn<<<grid, K2_THREADS, smem, st>>>(a);
   return cudaGetLastError();
+}
+
+template <bool LUT>
+static cudaError_t k2_dispatch_t(const K2Args& a, int k_pad, int R, int grid, int smem, cudaStream_t st) {
+  if (R == 2) {
+    switch (k_pad) {
+      case 16: return k2_launch_t<16, 2, LUT>(a, grid, smem, st);
+      case 32: return k2_launch_t<32, 2, LUT>(a, grid, smem, st);
+      case 48: return k2_launch_t<48, 2, LUT>(a, grid, smem, st);
+      default: return k2_launch_t<64, 2, LUT>(a, grid, smem, st);
+    }
+  }
+  switch (k_pad) {
+    case 16: return k2_launch_t<16, 1, LUT>(a, grid, smem, st);
+    case 32: return k2_launch_t<32, 1, LUT>(a, grid, smem, st);
+    case 48: return k2_launch_t<48, 1, LUT>(a, grid, smem, st);
+    case 64: return k2_launch_t<64, 1, LUT>(a, grid, smem, st);
+    case 80: return k2_launch_t<80, 1, LUT>(a, grid, smem, st);
+    case 96: return k2_launch_t<96, 1, LUT>(a, grid, smem, st);
+    case 112: return k2_launch_t<112, 1, LUT>(a, grid, smem, st);
+    default: return k2_launch_t<128, 1, LUT>(a, grid, smem, st);
+  }
+}
+
+static cudaError_t k2_dispatch(const K2Args& a, int k_pad, int R, bool lut, int grid, int smem, cudaStream_t st) {
+  return lut ? k2_dispatch_t<true>(a, k_pad, R, grid, smem, st) : k2_dispatch_t<false>(a, k_pad, R, grid, smem, st);
+}
+
+// The basis table of the lookup-table mode: phi_0..phi_127 in FP64 by the normalised recurrence at every
+// sample, stored in FP32.  Built once per context.
+__global__ void k2_lut_build(float* lut) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= K2_LUT_N) return;
+  const double x = -(double)K2_LUT_X + (double)i / K2_LUT_D;
+  double p_prev = 0.0, p = exp(-0.5 * x * x);
+  for (int n = 0; n < K2_LUT_W; ++n) {
+    lut[(size_t)i * K2_LUT_W + n] = (float)p;
+    const double pn = sqrt(2.0 / (n + 1)) * x * p - sqrt((double)n / (n + 1)) * p_prev;
+    p_prev = p;
+    p = pn;
+  }
+}
+
+static int k2_lut(wn_ctx* ctx, cudaStream_t st, const float** out) {
+  if (!ctx->lut) {
+    cudaError_t e = cudaMalloc(&ctx->lut, sizeof(float) * (size_t)K2_LUT_N * K2_LUT_W);
+    if (e != cudaSuccess) return set_error(WN_ENOMEM, std::string("basis table: ") + cudaGetErrorString(e));
+    k2_lut_build<<<(K2_LUT_N + 127) / 128, 128, 0, st>>>(ctx->lut);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(WN_ECUDA, std::string("basis table: ") + cudaGetErrorString(e));
+  }
+  *out = ctx->lut;
+  return WN_OK;
 }
 
 // Workspace: grow-only device buffer owned by the context.
@@ -591,6 +728,9 @@ int launch_shapelets_ws(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* ou
   k2_chaninfo<<<(o.n_chan + 255) / 256, 256, 0, st>>>(o.freq, o.n_chan, o.nu0, chaninfo);
   const long long n_vis = (long long)o.n_rows * o.n_chan;
   const int passes = ctx->shape_mode == WN_SHAPE_BF16X1 ? 1 : 3;
+  const float* lut = nullptr;
+  if (ctx->shape_mode == WN_SHAPE_LUT_BF16X3)
+    if (int r = k2_lut(ctx, st, &lut)) return r;
   const double L0 = std::log2(o.nu0);
   for (int q = 0; q < M->n_shape; ++q) {
     const ShapeRec& h = M->sh_host[q];
@@ -599,6 +739,7 @@ int launch_shapelets_ws(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* ou
     a.rowinfo = rowinfo;
     a.chaninfo = chaninfo;
     a.bop = M->bop + h.b_off;
+    a.lut = lut;
     a.n_pad = h.n_pad;
     a.nmax = h.nmax;
     a.passes = passes;
@@ -630,26 +771,7 @@ int launch_shapelets_ws(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* ou
     const int n_tiles = (int)((n_vis + K2_M * R - 1) / (K2_M * R));
     a.n_tiles = n_tiles;
     const int grid = std::min(n_tiles, ctx->num_sms);
-    cudaError_t e;
-    if (R == 2) {
-      switch (h.k_pad) {
-        case 16: e = k2_launch_t<16, 2>(a, grid, lay.total, st); break;
-        case 32: e = k2_launch_t<32, 2>(a, grid, lay.total, st); break;
-        case 48: e = k2_launch_t<48, 2>(a, grid, lay.total, st); break;
-        default: e = k2_launch_t<64, 2>(a, grid, lay.total, st); break;
-      }
-    } else {
-      switch (h.k_pad) {
-        case 16: e = k2_launch_t<16, 1>(a, grid, lay.total, st); break;
-        case 32: e = k2_launch_t<32, 1>(a, grid, lay.total, st); break;
-        case 48: e = k2_launch_t<48, 1>(a, grid, lay.total, st); break;
-        case 64: e = k2_launch_t<64, 1>(a, grid, lay.total, st); break;
-        case 80: e = k2_launch_t<80, 1>(a, grid, lay.total, st); break;
-        case 96: e = k2_launch_t<96, 1>(a, grid, lay.total, st); break;
-        case 112: e = k2_launch_t<112, 1>(a, grid, lay.total, st); break;
-        default: e = k2_launch_t<128, 1>(a, grid, lay.total, st); break;
-      }
-    }
+    cudaError_t e = k2_dispatch(a, h.k_pad, R, lut != nullptr, grid, lay.total, st);
     if (e != cudaSuccess) return set_error(WN_ECUDA, std::string("shapelet kernel launch: ") + cudaGetErrorString(e));
   }
   return WN_OK;

@@ -176,13 +176,15 @@ void wn_destroy(wn_ctx* ctx) {
   cudaFree(ctx->d_err);
   cudaFree(ctx->ws);
   cudaFree(ctx->ws2);
+  cudaFree(ctx->lut);
   delete ctx;
 }
 
 int wn_set_precision(wn_ctx* ctx, int precision, int shape_mode) {
   if (!ctx) return set_error(WN_EINVAL, "ctx is NULL");
   if (precision != WN_PREC_MIXED && precision != WN_PREC_FP64) return set_error(WN_EINVAL, "unknown precision");
-  if (shape_mode != WN_SHAPE_BF16X3 && shape_mode != WN_SHAPE_BF16X1) return set_error(WN_EINVAL, "unknown shape mode");
+  if (shape_mode != WN_SHAPE_BF16X3 && shape_mode != WN_SHAPE_BF16X1 && shape_mode != WN_SHAPE_LUT_BF16X3)
+    return set_error(WN_EINVAL, "unknown shape mode");
   ctx->precision = precision;
   ctx->shape_mode = shape_mode;
   return ok();
@@ -486,6 +488,9 @@ int wn_predict_static(wn_ctx* ctx, const wn_obs* obs, int model_id, void* vis_c6
   Model* M = find_model(ctx, model_id);
   if (!M) return set_error(WN_ENOTFOUND, "unknown model id");
   if (accumulate != 0 && accumulate != 1) return set_error(WN_EINVAL, "accumulate must be 0 or 1");
+  if (M->n_shape > 0 && ctx->shape_mode == WN_SHAPE_LUT_BF16X3 && !ctx->lut)
+    return set_error(WN_EINVAL, "wn_predict_static: the lookup-table shapelet mode needs its table, built by a first "
+                                "wn_predict in that mode");
   DeviceGuard g(ctx->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int mode = accumulate ? OUT_ACCUM : OUT_STORE;

@@ -97,6 +97,7 @@ struct wn_ctx {
   size_t ws_bytes = 0;
   void* ws2 = nullptr;
   size_t ws2_bytes = 0;
+  float* lut = nullptr;  // basis table of the lookup-table shapelet mode (built on first use)
 };
 
 namespace wn {

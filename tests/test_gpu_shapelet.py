@@ -56,6 +56,18 @@ def test_single_shapelet_orders(wn, ctx, nmax):
     assert e_norm(got, ref) <= 2e-4, e_norm(got, ref)
 
 
+@pytest.mark.parametrize("nmax", [5, 40, 80, 127])
+def test_lookup_table_basis_mode(wn, ctx, nmax):
+    """Hermite functions interpolated from the 1-D table (spacing 1/256) instead of the recurrence: the
+    interpolation error grows like (2n + 1) / (8 * 256^2) of the basis values, inside the 1e-3 target."""
+    obs = synth.make_obs(nmax + 7, 12, 2, synth.uniform_channels(160e6, 1.5e6, 40), layout="mwa",
+                         max_baseline=3000.0, dec0=-30 * synth.DEG)
+    sky = shapelet_sky(nmax + 60, [nmax], lm=[(0.01, -0.02)])
+    ref = oracle_rows(obs, sky, np.arange(obs.n_rows))
+    got = predict(wn, ctx, obs, sky, shape_mode=wn.WN_SHAPE_LUT_BF16X3)
+    assert e_norm(got, ref) <= 1e-3, e_norm(got, ref)
+
+
 def test_plain_bf16_mode(wn, ctx):
     obs = synth.make_obs(3, 12, 2, synth.uniform_channels(160e6, 1.5e6, 40), layout="mwa", max_baseline=3000.0)
     sky = shapelet_sky(4, [30])
