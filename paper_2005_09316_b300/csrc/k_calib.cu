@@ -361,7 +361,7 @@ int launch_calibrate(wn_ctx* ctx, const ObsDev& o, const float2* model, const fl
   a.n_iter = n_iter;
   a.err = ctx->d_err;
   const size_t smem = k7_smem_bytes(o.n_ant);
-  cudaError_t e = cudaFuncSetAttribute(k7_calib, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(k7_calib));
   if (e == cudaSuccess) {
     k7_calib<<<o.n_time * o.n_chan, K7_THREADS, smem, st>>>(a);
     e = cudaGetLastError();

@@ -695,7 +695,8 @@ int launch_grad(wn_ctx* ctx, const ObsDev& o, const Model* M, const PeelArgs& pa
       smem = (size_t)k4s_layout(h.nmax, a.nnz, T).total;
     }
     if (smem > smax) return set_error(WN_EINVAL, "adjoint: shapelet too large for the shared-memory reduction");
-    cudaFuncSetAttribute(k4_grad_shape, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaError_t ea = allow_max_dynamic_smem(reinterpret_cast<const void*>(k4_grad_shape)))
+      return set_error(WN_ECUDA, std::string("adjoint attribute: ") + cudaGetErrorString(ea));
     k4_grad_shape<<<sgrid, T, smem, st>>>(a);
     const int nout = a.nnz + K4S_NS;
     k4_reduce_shape<<<(nout * 32 + 255) / 256, 256, 0, st>>>(shpart, shpart + (size_t)sgrid * K4S_NS, sgrid, a.nnz, j,
@@ -780,7 +781,8 @@ int launch_grad_shape_coeff(wn_ctx* ctx, const ObsDev& o, const Model* M, const 
       smem = (size_t)k4s_layout(h.nmax, a.nnz, T).total;
     }
     if (smem > smax) return set_error(WN_EINVAL, "adjoint: shapelet too large for the shared-memory reduction");
-    cudaFuncSetAttribute(k4_grad_shape, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaError_t ea = allow_max_dynamic_smem(reinterpret_cast<const void*>(k4_grad_shape)))
+      return set_error(WN_ECUDA, std::string("adjoint attribute: ") + cudaGetErrorString(ea));
     k4_grad_shape<<<sgrid, T, smem, st>>>(a);
     const int nout = a.nnz + K4S_NS;
     k4_reduce_shape<<<(nout * 32 + 255) / 256, 256, 0, st>>>(shpart, shpart + (size_t)sgrid * K4S_NS, sgrid, a.nnz, j,

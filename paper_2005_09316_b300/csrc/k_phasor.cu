@@ -374,7 +374,7 @@ static K1Choice k1_choose(long rows, int F, int num_sms) {
 template <int K, bool U>
 static cudaError_t k1_launch(const K1Args& a, dim3 grid, int smem, cudaStream_t st) {
   auto fn = k1_phasor<K, U>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(fn));
   if (e != cudaSuccess) return e;
   fn<<<grid, K1_THREADS, smem, st>>>(a);
   return cudaGetLastError();
@@ -488,7 +488,7 @@ int k1_batched_args(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, i
 }
 
 cudaError_t k1_batched_setup() {
-  return cudaFuncSetAttribute(k1_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, k1_batched_smem());
+  return allow_max_dynamic_smem(reinterpret_cast<const void*>(k1_batched));
 }
 
 cudaError_t k1_batched_launch(const K1Args* reqs, const K1Work* work, const int* n_work, int grid, cudaStream_t st) {

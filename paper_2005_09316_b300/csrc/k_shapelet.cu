@@ -153,8 +153,9 @@ __host__ __device__ inline K2Layout k2_layout(int kp, int n_pad, int passes, int
   L.b_bytes = parts * kp * n_pad * 2;
   L.a_bytes = R * parts * kp * K2_M * 2;  // one group's A: R blocks of 128 rows (hi [+ lo])
   L.a0 = (L.b_bytes + 1023) & ~1023;
-  L.coef = L.a0 + groups * L.a_bytes;  // recurrence coefficients a_n, b_n: 2 x 128 floats
-  L.bars = L.coef + 2 * (kNmaxLimit + 1) * 4;
+  L.coef = L.a0 + groups * L.a_bytes;  // recurrence coefficients a_n, b_n: 2 x 128 floats, then the
+                                       // pairs {a_n, a_n}, {-b_n, -b_n} for two rows at once: 2 x 128 float2
+  L.bars = L.coef + 2 * (kNmaxLimit + 1) * 4 + 2 * (kNmaxLimit + 1) * 8;
   L.total = L.bars + 128;  // barriers (1 + 3 per parity) and the TMEM address slot
   return L;
 }
@@ -181,7 +182,31 @@ __device__ __forceinline__ void store_bf16_split(float (&v)[8], unsigned char* a
 template <int KP, int R, bool SCALED>
 __device__ __forceinline__ void produce_rows_run(const float (&x)[R], float (&p)[R], float (&p_prev)[R], float (&scale)[R],
                                                  int (&E)[R], unsigned char* a_base, int blk, bool split, int row,
-                                                 const float4* ca, const float4* cb) {
+                                                 const float4* ca, const float4* cb, const float2* ca2,
+                                                 const float2* cb2) {
+  if constexpr (R == 2 && !SCALED) {
+    // two rows as one f32x2 recurrence: {p_r0, p_r1}' = {a,a} {x0,x1} {p_r0,p_r1} + {-b,-b} {p'_r0,p'_r1}
+    float2 P = make_float2(p[0], p[1]), Pp = make_float2(p_prev[0], p_prev[1]);
+    const float2 X = make_float2(x[0], x[1]);
+#pragma unroll 1
+    for (int k0 = 0; k0 < KP; k0 += 8) {
+      float v[2][8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        v[0][i] = P.x;
+        v[1][i] = P.y;
+        const float2 Pn = __ffma2_rn(__fmul2_rn(ca2[k0 + i], X), P, __fmul2_rn(cb2[k0 + i], Pp));
+        Pp = P;
+        P = Pn;
+      }
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        unsigned char* hi = a_base + r * blk;
+        store_bf16_split(v[r], hi, split ? hi + KP * K2_M * 2 : nullptr, kmaj_off(row, k0, K2_M));
+      }
+    }
+    return;
+  }
 #pragma unroll 1
   for (int k0 = 0; k0 < KP; k0 += 8) {
     const float4 A0 = ca[k0 >> 2], A1 = ca[(k0 >> 2) + 1], B0 = cb[k0 >> 2], B1 = cb[(k0 >> 2) + 1];
@@ -264,7 +289,8 @@ __device__ __forceinline__ void produce_rows_lut(const float (&x)[R], int nmax, 
 
 template <int KP, int R>
 __device__ __forceinline__ void produce_rows(const float (&x)[R], int nmax, const bool (&valid)[R], unsigned char* a_base,
-                                             int blk, bool split, int row, const float4* ca, const float4* cb) {
+                                             int blk, bool split, int row, const float4* ca, const float4* cb,
+                                             const float2* ca2, const float2* cb2) {
   const float xcut = sqrtf(2.0f * nmax + 1.0f) + 10.0f;
   bool zero[R], fast = true;
   float hx[R];
@@ -284,8 +310,8 @@ __device__ __forceinline__ void produce_rows(const float (&x)[R], int nmax, cons
     p[r] = zero[r] ? 0.f : exp2f((float)E[r] - hx[r]);
     scale[r] = __int_as_float(max(0, 127 - E[r]) << 23);  // 2^-E (0 below 2^-126)
   }
-  if (fast) produce_rows_run<KP, R, false>(x, p, p_prev, scale, E, a_base, blk, split, row, ca, cb);
-  else produce_rows_run<KP, R, true>(x, p, p_prev, scale, E, a_base, blk, split, row, ca, cb);
+  if (fast) produce_rows_run<KP, R, false>(x, p, p_prev, scale, E, a_base, blk, split, row, ca, cb, ca2, cb2);
+  else produce_rows_run<KP, R, true>(x, p, p_prev, scale, E, a_base, blk, split, row, ca, cb, ca2, cb2);
 }
 
 // Epilogue dot product of one accumulator chunk (16 n2 values: columns 2 n2, 2 n2 + 1 = Re, Im) with
@@ -314,6 +340,22 @@ __device__ __forceinline__ void epi_chunk(const uint32_t* t, const float4* ca, c
       E -= 64;
       scale = __int_as_float(max(0, 127 - E) << 23);
     }
+  }
+}
+
+// Epilogue of two rows at once (no scaling): their y recurrences as one f32x2 recurrence, each row's
+// accumulator chunk (16 columns, 8 n2) against its half of the pair.
+__device__ __forceinline__ void epi_chunk2(const uint32_t* t0, const uint32_t* t1, const float2* ca2, const float2* cb2,
+                                           int n0, float2 Y, float2& Q, float2& Qp, float (&xr)[2], float (&xi)[2]) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    xr[0] = fmaf(__uint_as_float(t0[2 * i]), Q.x, xr[0]);
+    xi[0] = fmaf(__uint_as_float(t0[2 * i + 1]), Q.x, xi[0]);
+    xr[1] = fmaf(__uint_as_float(t1[2 * i]), Q.y, xr[1]);
+    xi[1] = fmaf(__uint_as_float(t1[2 * i + 1]), Q.y, xi[1]);
+    const float2 Qn = __ffma2_rn(__fmul2_rn(ca2[n0 + i], Y), Q, __fmul2_rn(cb2[n0 + i], Qp));
+    Qp = Q;
+    Q = Qn;
   }
 }
 
@@ -362,6 +404,9 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
     float* cf = reinterpret_cast<float*>(smem + lay.coef);
     cf[threadIdx.x] = c_herm_a[threadIdx.x];
     cf[kNmaxLimit + 1 + threadIdx.x] = c_herm_b[threadIdx.x];
+    float2* cp = reinterpret_cast<float2*>(cf + 2 * (kNmaxLimit + 1));
+    cp[threadIdx.x] = make_float2(c_herm_a[threadIdx.x], c_herm_a[threadIdx.x]);
+    cp[kNmaxLimit + 1 + threadIdx.x] = make_float2(-c_herm_b[threadIdx.x], -c_herm_b[threadIdx.x]);
   }
   if (warp == K2_MMA_WARP) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
@@ -375,6 +420,8 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
   const uint32_t tmem = *tslot;
   const float4* ca = reinterpret_cast<const float4*>(smem + lay.coef);
   const float4* cb = ca + (kNmaxLimit + 1) / 4;
+  const float2* ca2 = reinterpret_cast<const float2*>(cb + (kNmaxLimit + 1) / 4);  // {a_n, a_n}
+  const float2* cb2 = ca2 + (kNmaxLimit + 1);                                      // {-b_n, -b_n}
   // tiles of this CTA: it = 0, 1, 2, ... -> tile blockIdx.x + it * gridDim.x; parity s = it % ng, j = it / ng
   const int n_it = a.n_tiles > (int)blockIdx.x ? (a.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
@@ -456,7 +503,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
       load_x(it + ng, valid, xs, nu);
       if (j > 0 && !k2_wait(&mdone[sp], (j - 1) & 1, a.err)) break;  // MMA(j-1) has read A
       if (LUT) produce_rows_lut<KP, R>(x, a.nmax, v0, a_base, blk, a.passes > 1, m, a.lut);
-      else produce_rows<KP, R>(x, a.nmax, v0, a_base, blk, a.passes > 1, m, ca, cb);
+      else produce_rows<KP, R>(x, a.nmax, v0, a_base, blk, a.passes > 1, m, ca, cb, ca2, cb2);
       fence_async_smem();
       mbar_arrive(&afull[sp]);
     }
@@ -558,16 +605,24 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
         }
       } else {  // R rows: a 16-column chunk of every row in flight, their recurrences interleaved
         uint32_t tb[R][16];
+        if constexpr (R == 2) {
+          // The TMEM loads are warp-collective (.sync.aligned): every thread issues them in the same
+          // order whatever its rows need; only the arithmetic below depends on the thread.
+          float2 Q = make_float2(q[0], q[1]), Qp = make_float2(q_prev[0], q_prev[1]);
+          const float2 Y = make_float2(y[0], y[1]);
 #pragma unroll 1
-        for (int c = 0; c < nch; ++c) {
+          for (int c = 0; c < nch; ++c) {
+            tmem_issue16x(trow + (uint32_t)(c << 4), tb[0]);
+            tmem_issue16x(trow + (uint32_t)(a.n_pad + (c << 4)), tb[1]);
+            tmem_wait16(tb[0]);
+            tmem_wait16(tb[1]);
+            if (yfast) {  // both rows unscaled: one f32x2 recurrence
+              epi_chunk2(tb[0], tb[1], ca2, cb2, c << 3, Y, Q, Qp, xr, xi);
+            } else {
 #pragma unroll
-          for (int r = 0; r < R; ++r) tmem_issue16x(trow + (uint32_t)(r * a.n_pad + (c << 4)), tb[r]);
-#pragma unroll
-          for (int r = 0; r < R; ++r) tmem_wait16(tb[r]);
-#pragma unroll
-          for (int r = 0; r < R; ++r) {
-            if (yfast) epi_chunk<false>(tb[r], ca, cb, c << 3, y[r], q[r], q_prev[r], xr[r], xi[r], E[r], scale[r]);
-            else epi_chunk<true>(tb[r], ca, cb, c << 3, y[r], q[r], q_prev[r], xr[r], xi[r], E[r], scale[r]);
+              for (int r = 0; r < R; ++r)
+                epi_chunk<true>(tb[r], ca, cb, c << 3, y[r], q[r], q_prev[r], xr[r], xi[r], E[r], scale[r]);
+            }
           }
         }
       }
@@ -647,7 +702,7 @@ static int k2_setup_constants(int device, cudaStream_t st) {
 template <int KP, int R, bool LUT>
 static cudaError_t k2_launch_t(const K2Args& a, int grid, int smem, cudaStream_t st) {
   auto fn = k2_shapelet<KP, R, LUT>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(fn));
   if (e != cudaSuccess) return e;
   fn<<<grid, K2_THREADS, smem, st>>>(a);
   return cudaGetLastError();

@@ -6,6 +6,9 @@
 #include <cstring>
 #include <mutex>
 
+#include <mutex>
+#include <set>
+
 #include "wn_internal.cuh"
 
 namespace wn {
@@ -15,6 +18,25 @@ static thread_local std::string g_last_error;
 int set_error(int code, const std::string& msg) {
   g_last_error = msg;
   return code;
+}
+
+cudaError_t allow_max_dynamic_smem(const void* kernel) {
+  static std::mutex mu;
+  static std::set<std::pair<const void*, int>> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count({kernel, dev})) return cudaSuccess;
+  int mx = 0;
+  cudaFuncAttributes fa;
+  e = cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
+  // the limit excludes the kernel's own static shared memory
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx - (int)fa.sharedSizeBytes);
+  if (e == cudaSuccess) done.insert({kernel, dev});
+  return e;
 }
 
 static int ok() {

@@ -117,6 +117,11 @@ struct PeelArgs {
 
 int set_error(int code, const std::string& msg);
 
+// Raise a kernel's dynamic shared-memory limit to the device maximum, once per (kernel, device).
+// Setting it to each launch's own size instead would race between host threads that launch the same
+// kernel with different sizes (one thread lowering the limit between another's setting and launch).
+cudaError_t allow_max_dynamic_smem(const void* kernel);
+
 // Arguments of the point/Gaussian phasor kernel for one observation (K1).
 struct K1Args {
   const double* uvw;
