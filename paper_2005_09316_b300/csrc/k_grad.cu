@@ -30,6 +30,7 @@ struct K4Args {
   int n_rows, n_chan, n_base;
   int f_lo, f_cnt;            // channel pass
   double nu0;
+  float dnu_h, dnu_l;         // channel spacing / c as a float pair (uniform channels)
   const PGRec* comps;
   const double *flux, *nuref, *gmaj, *gmin, *gpa;  // raw FP64 tables (all components / Gaussians)
   int n_point, n_gauss;
@@ -190,6 +191,164 @@ __global__ void __launch_bounds__(K4_WARPS * 32) k4_grad_pg(const K4Args a) {
     double s = 0.0;
     for (int ww = 0; ww < K4_WARPS; ++ww) s += gsum[ww][j][i];
     a.partials[((size_t)blockIdx.y * n_pg + c0 + j) * K4_NG + i] = s;
+  }
+}
+
+// Point / Gaussian gradients for uniformly spaced channels.  grid = (component tiles of 32, row
+// chunks); warp w takes rows r0 + w, r0 + w + 8, ...; lane j owns component j of the tile and runs over
+// every channel of the pass itself, so its sums need no cross-lane reduction.  Per row, the warp first
+// writes W = conj(G) R of every channel to shared memory (read back by broadcast); the phasor advances
+// by the one-channel step D (accurate) and restarts from an exactly reduced phase every K4U_RS channels.
+constexpr int K4U_RS = 16;
+
+struct K4USmem {
+  int comps, cjs, cc, nh, wb, total;
+};
+__host__ __device__ inline K4USmem k4u_layout(int f_cnt) {
+  K4USmem L;
+  L.comps = 0;
+  L.cjs = L.comps + K4_CT * (int)sizeof(PGRec);
+  L.cc = L.cjs + K4_CT * 4;
+  L.nh = L.cc + f_cnt * 16;
+  L.wb = L.nh + f_cnt * 8;
+  const int wbytes = K4_WARPS * f_cnt * 8, gbytes = K4_WARPS * K4_CT * K4_NG * 8;
+  L.total = L.wb + (wbytes > gbytes ? wbytes : gbytes);
+  return L;
+}
+
+__global__ void __launch_bounds__(K4_WARPS * 32) k4_grad_pg_u(const K4Args a) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int F = a.f_cnt;
+  const K4USmem L = k4u_layout(F);
+  PGRec* comps = reinterpret_cast<PGRec*>(sm + L.comps);
+  float* cjs = reinterpret_cast<float*>(sm + L.cjs);
+  float4* cc = reinterpret_cast<float4*>(sm + L.cc);   // per channel: log2(nu/nu0), Gaussian weight, nu/c, (nu/c)^2
+  float2* nh = reinterpret_cast<float2*>(sm + L.nh);   // per channel: nu/c as a float pair
+  float2* wb = reinterpret_cast<float2*>(sm + L.wb);   // [warp][F] W of the current row
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_pg = a.n_point + a.n_gauss;
+  const int c0 = blockIdx.x * K4_CT;
+  const int ncomp = min(K4_CT, n_pg - c0);
+  const double L0 = log2(a.nu0);
+  if (threadIdx.x < ncomp) {
+    const PGRec c = a.comps[c0 + threadIdx.x];
+    comps[threadIdx.x] = c;
+    cjs[threadIdx.x] = c.alpha * (float)(L0 - c.lref);
+  }
+  const float inv_nu0 = (float)(1.0 / a.nu0);
+  for (int f = threadIdx.x; f < F; f += blockDim.x) {
+    const double nu = a.freq[a.f_lo + f];
+    float h, l;
+    split_double(nu * (1.0 / kC), h, l);
+    cc[f] = make_float4(log2f((float)nu * inv_nu0), (float)(kGaussE * kLog2e) * h * h, h, h * h);
+    nh[f] = make_float2(h, l);
+  }
+  __syncthreads();
+
+  // this lane's component
+  const bool mine = lane < ncomp;
+  const int jc = c0 + (mine ? lane : 0);
+  const PGRec& me = comps[mine ? lane : 0];
+  const bool my_gauss = mine && jc >= a.n_point;
+  const double me_l = (double)me.lh + me.ll, me_m = (double)me.mh + me.ml, me_nm1 = (double)me.nh + me.nl;
+  const double my_n = 1.0 + me_nm1;
+  const float my_ln = (float)(me_l / my_n), my_mn = (float)(me_m / my_n);
+  const float my_lnref = (float)((L0 - me.lref) * 0.6931471805599453);
+  const float my_S = mine ? (float)a.flux[jc] : 0.f;
+  const float my_alpha = me.alpha, my_cj = cjs[mine ? lane : 0];
+  float my_pa = 0.f, my_maj = 0.f, my_min = 0.f;
+  if (my_gauss) {
+    const int g = jc - a.n_point;
+    my_maj = (float)a.gmaj[g];
+    my_min = (float)a.gmin[g];
+    my_pa = (float)a.gpa[g];
+  }
+  const float sp = sinf(my_pa), cp = cosf(my_pa);
+
+  float acc32[K4_NG];
+  double acc64[K4_NG];
+#pragma unroll
+  for (int i = 0; i < K4_NG; ++i) {
+    acc32[i] = 0.f;
+    acc64[i] = 0.0;
+  }
+  float2* myw = wb + warp * F;
+  const int r_lo = blockIdx.y * a.rows_per_chunk;
+  const int r_hi = min(a.n_rows, r_lo + a.rows_per_chunk);
+  int nrow = 0;
+  for (int row = r_lo + warp; row < r_hi; row += K4_WARPS) {
+    __syncwarp();  // the previous row's W is no longer read
+    for (int f = lane; f < F; f += 32) {
+      float2 G;
+      if (!gain_product(a.peel, row, a.n_base, a.f_lo + f, G)) atomicOr(a.err, WN_DEVERR_ANTENNA);
+      const float2 R = a.resid[(size_t)row * a.n_chan + a.f_lo + f];
+      myw[f] = make_float2(G.x * R.x + G.y * R.y, G.x * R.y - G.y * R.x);
+    }
+    __syncwarp();
+    if (mine) {
+      float xuvw[6];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) xuvw[i] = __ldg(a.uvw_pairs + 6 * (size_t)row + i);
+      float th, tl;
+      tau_df(xuvw, me, th, tl);
+      const float uf = xuvw[0], vf = xuvw[2], wf = xuvw[4];
+      const float fl = -4.0f * (float)kPi * (uf - wf * my_ln);
+      const float fm = -4.0f * (float)kPi * (vf - wf * my_mn);
+      float q = 0.f, fmaj = 0.f, fmin = 0.f, fpa = 0.f;
+      if (my_gauss) {
+        q = me.ga * uf * uf + me.gb * uf * vf + me.gc * vf * vf;
+        const float kx = sp * uf + cp * vf, ky = cp * uf - sp * vf;
+        fmaj = 4.0f * (float)kGaussE * my_maj * kx * kx;
+        fmin = 4.0f * (float)kGaussE * my_min * ky * ky;
+        fpa = 4.0f * (float)kGaussE * (my_maj * my_maj - my_min * my_min) * kx * ky;
+      }
+      const float2 D = phasor_accurate(reduce_turns(th, tl, a.dnu_h, a.dnu_l));
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+      for (int fb = 0; fb < F; fb += K4U_RS) {
+        float2 P = phasor_fast(reduce_turns(th, tl, nh[fb].x, nh[fb].y));
+        const int fe = min(fb + K4U_RS, F);
+        for (int f = fb; f < fe; ++f) {
+          const float4 c = cc[f];
+          const float2 W = myw[f];
+          // channel sums use the amplitude without the flux: dV/dS_ref = V / S_ref holds for S_ref = 0 too
+          const float A = ex2_approx(fmaf(-q, c.y, fmaf(my_alpha, c.x, my_cj)));
+          const float vr = A * P.x, vi = A * P.y;
+          const float zr = W.x * vr + W.y * vi, zi = W.x * vi - W.y * vr;  // z = conj(W) V
+          s0 += zr;
+          s1 = fmaf(c.x, zr, s1);
+          s2 = fmaf(c.z, zi, s2);
+          s3 = fmaf(c.w, zr, s3);
+          P = make_float2(P.x * D.x - P.y * D.y, P.x * D.y + P.y * D.x);
+        }
+      }
+      // s1 holds sum log2(nu/nu0) Re z: ln(nu/nu_ref) = ln2 log2(nu/nu0) + ln(nu0/nu_ref)
+      acc32[0] += -2.0f * s0;
+      acc32[1] += -2.0f * my_S * (0.6931471805599453f * s1 + my_lnref * s0);
+      acc32[2] += my_S * fl * s2;
+      acc32[3] += my_S * fm * s2;
+      acc32[4] += my_S * fmaj * s3;
+      acc32[5] += my_S * fmin * s3;
+      acc32[6] += my_S * fpa * s3;
+    }
+    if (++nrow == K4_FLUSH) {
+#pragma unroll
+      for (int i = 0; i < K4_NG; ++i) {
+        acc64[i] += (double)acc32[i];
+        acc32[i] = 0.f;
+      }
+      nrow = 0;
+    }
+  }
+  __syncthreads();  // every warp is done with its W buffer: the area now holds the per-warp sums
+  double* gsum = reinterpret_cast<double*>(wb);  // [warp][K4_CT][K4_NG]
+#pragma unroll
+  for (int i = 0; i < K4_NG; ++i) gsum[(warp * K4_CT + lane) * K4_NG + i] = acc64[i] + (double)acc32[i];
+  __syncthreads();
+  for (int t = threadIdx.x; t < ncomp * K4_NG; t += blockDim.x) {
+    const int j = t / K4_NG, i = t % K4_NG;
+    double sum = 0.0;
+    for (int ww = 0; ww < K4_WARPS; ++ww) sum += gsum[(ww * K4_CT + j) * K4_NG + i];
+    a.partials[((size_t)blockIdx.y * n_pg + c0 + j) * K4_NG + i] = sum;
   }
 }
 
@@ -629,6 +788,11 @@ int launch_grad(wn_ctx* ctx, const ObsDev& o, const Model* M, const PeelArgs& pa
       a.f_lo = p * 32 * K4_KMAX;
       a.f_cnt = std::min(32 * K4_KMAX, o.n_chan - a.f_lo);
       a.nu0 = o.nu0;
+      {
+        const double dn = o.dnu / kC;
+        a.dnu_h = (float)dn;
+        a.dnu_l = (float)(dn - (double)a.dnu_h);
+      }
       a.comps = M->pg;
       a.flux = M->r_flux();
       a.nuref = M->r_nuref();
@@ -644,7 +808,11 @@ int launch_grad(wn_ctx* ctx, const ObsDev& o, const Model* M, const PeelArgs& pa
       a.err = ctx->d_err;
       const dim3 grid(comp_tiles, chunks);
       const int km = (a.f_cnt + 31) / 32;
-      if (km <= 2) k4_grad_pg<2><<<grid, K4_WARPS * 32, 0, st>>>(a);
+      if (o.uniform) {
+        if (cudaError_t ea = allow_max_dynamic_smem(reinterpret_cast<const void*>(k4_grad_pg_u)))
+          return set_error(WN_ECUDA, std::string("adjoint attribute: ") + cudaGetErrorString(ea));
+        k4_grad_pg_u<<<grid, K4_WARPS * 32, k4u_layout(a.f_cnt).total, st>>>(a);
+      } else if (km <= 2) k4_grad_pg<2><<<grid, K4_WARPS * 32, 0, st>>>(a);
       else if (km <= 4) k4_grad_pg<4><<<grid, K4_WARPS * 32, 0, st>>>(a);
       else if (km <= 8) k4_grad_pg<8><<<grid, K4_WARPS * 32, 0, st>>>(a);
       else if (km <= 12) k4_grad_pg<12><<<grid, K4_WARPS * 32, 0, st>>>(a);

@@ -32,9 +32,9 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-def problem(seed, n_ant=12, n_time=2, n_chan=24, n_point=40, n_gauss=10, nmaxs=(8,)):
-    obs = synth.make_obs(seed, n_ant, n_time, synth.uniform_channels(167e6, 0.5e6, n_chan), layout="mwa",
-                         max_baseline=2500.0, dec0=-30 * synth.DEG)
+def problem(seed, n_ant=12, n_time=2, n_chan=24, n_point=40, n_gauss=10, nmaxs=(8,), freq=None):
+    freq = synth.uniform_channels(167e6, 0.5e6, n_chan) if freq is None else freq
+    obs = synth.make_obs(seed, n_ant, n_time, freq, layout="mwa", max_baseline=2500.0, dec0=-30 * synth.DEG)
     sky = synth.make_sky(seed + 1, n_point, n_gauss, len(nmaxs), fov=8 * synth.DEG, shape_nmax=np.array(nmaxs),
                          shape_beta=(4 * synth.ARCMIN, 9 * synth.ARCMIN))
     sky.flux[n_point + n_gauss:] = 5.0 + np.arange(len(nmaxs))
@@ -58,9 +58,13 @@ def gpu_grad(wn, ctx, obs, sky, gains, data):
     return {k: (v.cpu().numpy() if v is not None else None) for k, v in out.items()}
 
 
-@pytest.mark.parametrize("seed,n_chan", [(41, 24), (42, 7), (43, 40)])
-def test_gradients_match_oracle(wn, ctx, seed, n_chan):
-    obs, sky, gains, data, G, V = problem(seed, n_chan=n_chan)
+@pytest.mark.parametrize("seed,n_chan,uniform", [(41, 24, True), (42, 7, True), (43, 40, True), (45, 600, True),
+                                                 (46, 30, False), (47, 70, False)])
+def test_gradients_match_oracle(wn, ctx, seed, n_chan, uniform):
+    """Uniform channels take the component-per-lane kernel (600 channels: two channel passes); arbitrary
+    channel lists the channel-per-lane one."""
+    freq = None if uniform else np.sort(np.random.default_rng(seed).uniform(150e6, 190e6, n_chan))
+    obs, sky, gains, data, G, V = problem(seed, n_chan=n_chan, freq=freq)
     W = np.conj(G) * (data - G * V)
     ref = oracle.grad(obs.uvw.reshape(-1, 3), obs.freq, obs.dec0, sky, W)
     got = gpu_grad(wn, ctx, obs, sky, gains, data)
