@@ -180,13 +180,14 @@ __global__ void __launch_bounds__(K7_THREADS, 1) k7_calib(const K7Args a) {
             const float2 aR = cmul(cconj(av), R);
             br += aR.x;
             bi += aR.y;
-            // the block of this baseline, rows of q (> p) and columns of p
+            // the block of this baseline, rows of q (> p) and columns of p: written once, since each
+            // antenna pair appears at most once among the baselines
             const float2 ac = cmul(cconj(av), cv);
-            atomicAdd(k7_elem(T, col_re(q), col_re(p)), ac.x);
-            atomicAdd(k7_elem(T, col_im(q), col_re(p)), ac.y);
+            *k7_elem(T, col_re(q), col_re(p)) = ac.x;
+            *k7_elem(T, col_im(q), col_re(p)) = ac.y;
             if (p > 0) {
-              atomicAdd(k7_elem(T, col_re(q), col_im(p)), ac.y);
-              atomicAdd(k7_elem(T, col_im(q), col_im(p)), -ac.x);
+              *k7_elem(T, col_re(q), col_im(p)) = ac.y;
+              *k7_elem(T, col_im(q), col_im(p)) = -ac.x;
             }
           } else {
             const float2 cv = cmul(gp, I);
