@@ -53,6 +53,29 @@ def k1_traffic():
         return None
 
 
+def count_launches(step, torch):
+    """The library's kernels that one step launches, counted from the CUDA activity trace of one extra
+    untimed step (torch.profiler); returns (count, {kernel: launches}) or (None, reason)."""
+    try:
+        import warnings
+
+        from torch.profiler import ProfilerActivity, profile
+        torch.cuda.synchronize()
+        with warnings.catch_warnings():
+            warnings.simplefilter("ignore")
+            with profile(activities=[ProfilerActivity.CUDA]) as prof:
+                step()
+                torch.cuda.synchronize()
+        names = {}
+        for e in prof.key_averages():
+            if "wn::" in e.key and e.count:
+                short = e.key.split("wn::", 1)[1].split("(", 1)[0]
+                names[short] = names.get(short, 0) + int(e.count)
+        return (sum(names.values()) or None), names
+    except Exception as exc:  # noqa: BLE001 - reported in the line, not fatal
+        return None, f"unavailable: {type(exc).__name__}: {exc}"
+
+
 def peaks():
     p = {}
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -597,6 +620,7 @@ def main():
     torch.cuda.synchronize()
     per = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
     ms = ev[0].elapsed_time(ev[-1]) / args.steps
+    launches_per_step, launch_names = count_launches(step, torch)
     clocks = clk.summary()
     flags = ctx.device_errors()
     if flags:
@@ -733,7 +757,8 @@ def main():
             "config": {"workload": WORKLOAD, "n_vis": obs.n_vis, "n_comp": sky.n_comp, "evals_per_step": evals,
                        "l2": "inputs > L2 each step (350 MB data in, 350 MB residual out); the 1.6 MB "
                              "component table stays L2-resident by design", "parallelism": f"replicas x{ws}"},
-            "clocks": clocks, "gpu_launches": args.steps * 1,
+            "clocks": clocks, "gpu_launches": (args.steps * launches_per_step if launches_per_step else None),
+            "gpu_launches_per_step": launch_names,
             "step_ms": {"min": min(per), "max": max(per)},
         }
         line.update(extra)

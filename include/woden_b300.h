@@ -25,6 +25,10 @@
  *    unless documented as synchronous.  A call that returns an error launches nothing.
  *  - Return value: WN_OK (0) or a wn_status code; wn_last_error() gives a message for the last
  *    failing call on the calling thread.
+ *  - A context's device workspaces (the phasor launch's partial sums of split tail tiles, the
+ *    shapelet and adjoint tables) are shared by its calls, so calls on one context that are issued to
+ *    different streams must not overlap on the GPU: order them (events), or use one context per
+ *    stream.  The serving API (wn_server_*) gives each of its slots its own workspace.
  *  - Device-side faults of the inputs that host checks cannot see (an antenna index outside
  *    [0, n_ant)) are not dereferenced: the kernels skip the access, write NaN for that output and
  *    raise a flag that wn_device_errors() reports.

@@ -21,6 +21,9 @@
 //    - q (nu/c)^2 E log2 e), q the Gaussian quadratic form in (u, v) metres.
 #include "wn_internal.cuh"
 
+#include <algorithm>
+#include <climits>
+
 namespace wn {
 
 constexpr int K1_WARPS = 8;
@@ -73,15 +76,25 @@ __device__ __forceinline__ bool bounded_wait(uint64_t* bar, uint32_t parity, uns
 // V += A P each take one packed instruction per component of the complex value.  Start phasors
 // come from the exactly reduced phase at the lane's first channel; the amplitude of both rows is one
 // exp2 for points, one per row for Gaussians (the envelope depends on (u, v)).
+// exp(-2 pi i r), negated when hpi = pi: a negative flux enters as a half turn added to the MUFU
+// argument (one FFMA in place of the FMUL by 2 pi), so the start phasor needs no sign multiply.  The
+// argument stays within [-pi, 2 pi].
+__device__ __forceinline__ float2 phasor_fast_turned(float r, float hpi) {
+  float s, c;
+  const float x = fmaf(r, 6.283185307179586f, hpi);
+  asm("sin.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(x));
+  asm("cos.approx.ftz.f32 %0, %1;" : "=f"(c) : "f"(x));
+  return make_float2(c, -s);
+}
+
 template <int K, bool GAUSS>
 __device__ __forceinline__ void k1_comp_uniform(const float4 c, const float4 Ra, const float4 Rb, const float4 Rc,
                                                 const float a0h, const float a0l, const float* lam, const float* wg,
                                                 float2* Vre, float2* Vim) {
-  const float2 P0 = phasor_fast(reduce_turns(Ra.x, Ra.y, a0h, a0l));
-  const float2 P1 = phasor_fast(reduce_turns(Ra.z, Ra.w, a0h, a0l));
-  const float2 sg = make_float2(c.z, c.w);
-  float2 Pre = __fmul2_rn(make_float2(P0.x, P1.x), sg);
-  float2 Pim = __fmul2_rn(make_float2(P0.y, P1.y), sg);
+  const float2 P0 = phasor_fast_turned(reduce_turns(Ra.x, Ra.y, a0h, a0l), c.z);
+  const float2 P1 = phasor_fast_turned(reduce_turns(Ra.z, Ra.w, a0h, a0l), c.z);
+  float2 Pre = make_float2(P0.x, P1.x);
+  float2 Pim = make_float2(P0.y, P1.y);
   const float2 Dre = make_float2(Rb.x, Rb.y), Dim = make_float2(Rb.z, Rb.w), nDim = make_float2(Rc.x, Rc.y);
 #pragma unroll
   for (int k = 0; k < K; ++k) {
@@ -116,10 +129,10 @@ __device__ __forceinline__ void k1_comp_list(const float4 c, const float4 Ra, co
     const float e = fmaf(c.y, lam[k], c.x);
     float2 A;
     if (GAUSS) {
-      A.x = c.z * ex2_approx(fmaf(Rc.z, wg[k], e));
-      A.y = c.z * ex2_approx(fmaf(Rc.w, wg[k], e));
+      A.x = c.w * ex2_approx(fmaf(Rc.z, wg[k], e));
+      A.y = c.w * ex2_approx(fmaf(Rc.w, wg[k], e));
     } else {
-      A.x = c.z * ex2_approx(e);
+      A.x = c.w * ex2_approx(e);
       A.y = A.x;
     }
     Vre[k] = __ffma2_rn(A, make_float2(P0.x, P1.x), Vre[k]);
@@ -127,10 +140,45 @@ __device__ __forceinline__ void k1_comp_list(const float4 c, const float4 Ra, co
   }
 }
 
-// One (row tile, channel block) of one observation: the body of the single-launch kernel below and
-// of the batched serving kernel.  Re-entrant: it initialises and invalidates its own barriers.
+// Write a lane's K channels of its two rows (rows row0, row0 + 1; channels f0 ..) in the output mode:
+// store, accumulate, the peel residual D - G V, or subtract G V from the output.
+template <int K>
+__device__ __forceinline__ void k1_store(const K1Args& a, const int row0, const int f0, const float2* Vre,
+                                         const float2* Vim, const bool ok) {
+#pragma unroll
+  for (int rr = 0; rr < 2; ++rr) {
+    const int row = row0 + rr;
+    if (row >= a.n_rows) continue;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int f = f0 + k;
+      if (f >= a.n_chan) continue;
+      const size_t idx = (size_t)row * a.n_chan + f;
+      float2 v = rr == 0 ? make_float2(Vre[k].x, Vim[k].x) : make_float2(Vre[k].y, Vim[k].y);
+      if (!ok) v = make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
+      if (a.mode == OUT_STORE) {
+        a.out[idx] = v;
+      } else if (a.mode == OUT_ACCUM) {
+        float2 o = a.out[idx];
+        a.out[idx] = make_float2(o.x + v.x, o.y + v.y);
+      } else {
+        float2 G;
+        if (!gain_product(a.peel, row, a.n_base, f, G)) atomicOr(a.err, WN_DEVERR_ANTENNA);
+        const float2 d = a.mode == OUT_SUBG ? a.out[idx] : a.peel.data[idx];
+        a.out[idx] = make_float2(d.x - (G.x * v.x - G.y * v.y), d.y - (G.x * v.y + G.y * v.x));
+      }
+    }
+  }
+}
+
+// One (row tile, channel block) of one observation over the component tiles t_beg .. t_end-1 (32
+// components each, points first): the body of the single-launch kernel below and of the batched
+// serving kernel.  With part == nullptr the visibilities are written in the output mode; otherwise the
+// raw partial sums go to part (2K x 256 float2, thread fastest) for k1_tail_sum.  Re-entrant: it
+// initialises and invalidates its own barriers.
 template <int K, bool UNIFORM>
-__device__ __forceinline__ void k1_tile(const K1Args& a, const int bx, const int by, unsigned char* smem) {
+__device__ __forceinline__ void k1_tile(const K1Args& a, const int bx, const int by, int t_beg, int t_end,
+                                        float2* part, unsigned char* smem) {
   const K1Smem lay = k1_smem_layout(a.log2L, K);
   PGRec* stage = reinterpret_cast<PGRec*>(smem + lay.stage);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + lay.bars);
@@ -153,9 +201,14 @@ __device__ __forceinline__ void k1_tile(const K1Args& a, const int bx, const int
   for (int i = 0; i < 2 * K; ++i) acc[i * K1_THREADS] = make_float2(0.f, 0.f);
 
   const int n_pt_tiles = (a.n_point + K1_CT - 1) / K1_CT;
-  const int n_tiles = n_pt_tiles + (a.n_gauss + K1_CT - 1) / K1_CT;
-  auto tile_start = [&](int t) { return t < n_pt_tiles ? t * K1_CT : a.n_point + (t - n_pt_tiles) * K1_CT; };
-  auto tile_count = [&](int t) {
+  t_end = min(t_end, n_pt_tiles + (a.n_gauss + K1_CT - 1) / K1_CT);
+  const int n_tiles = max(t_end - t_beg, 0);  // component tiles t_beg .. t_end-1 of this CTA, local index u
+  auto tile_start = [&](int u) {
+    const int t = t_beg + u;
+    return t < n_pt_tiles ? t * K1_CT : a.n_point + (t - n_pt_tiles) * K1_CT;
+  };
+  auto tile_count = [&](int u) {
+    const int t = t_beg + u;
     return t < n_pt_tiles ? min(K1_CT, a.n_point - t * K1_CT) : min(K1_CT, a.n_gauss - (t - n_pt_tiles) * K1_CT);
   };
 
@@ -221,7 +274,7 @@ __device__ __forceinline__ void k1_tile(const K1Args& a, const int bx, const int
       break;
     }
     const int cnt = tile_count(t);
-    const bool gauss = t >= n_pt_tiles;
+    const bool gauss = t_beg + t >= n_pt_tiles;
     const PGRec* st = stage + s * K1_CT;
 
     // --- records per (component, row pair), shared by the L lanes of the pair
@@ -251,8 +304,13 @@ __device__ __forceinline__ void k1_tile(const K1Args& a, const int bx, const int
       R[1] = Rb;
       R[2] = Rc;
     }
-    for (int j = lane; j < cnt; j += 32)
-      cs[j] = make_float4(st[j].lS + st[j].alpha * (float)(L0 - st[j].lref), st[j].alpha, st[j].sgn, st[j].sgn);
+    // per component: log2 of |flux| at the log-frequency reference (-inf for a zero or rejected
+    // component, whose amplitude is then exactly 0), alpha, the sign as a half turn, and the sign
+    for (int j = lane; j < cnt; j += 32) {
+      const float sg = st[j].sgn;
+      cs[j] = make_float4(sg == 0.f ? __int_as_float(0xff800000) : st[j].lS + st[j].alpha * (float)(L0 - st[j].lref), st[j].alpha,
+                          sg < 0.f ? 3.14159265358979f : 0.f, sg);
+    }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
 
@@ -288,35 +346,22 @@ __device__ __forceinline__ void k1_tile(const K1Args& a, const int bx, const int
     }
   }
 
-  // --- epilogue: each visibility written once
+  // --- epilogue: each visibility written once (or, for a component-range part of a split tile, the
+  // raw partial sums in thread order for k1_tail_sum)
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     Vre[k] = __fadd2_rn(acc[k * K1_THREADS], Vre[k]);
     Vim[k] = __fadd2_rn(acc[(K + k) * K1_THREADS], Vim[k]);
   }
-#pragma unroll
-  for (int rr = 0; rr < 2; ++rr) {
-    const int row = row_w0 + 2 * g + rr;
-    if (row >= a.n_rows) continue;
+  if (part) {
+    const float2 nan2 = make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      const int f = f0 + k;
-      if (f >= a.n_chan) continue;
-      const size_t idx = (size_t)row * a.n_chan + f;
-      float2 v = rr == 0 ? make_float2(Vre[k].x, Vim[k].x) : make_float2(Vre[k].y, Vim[k].y);
-      if (!ok) v = make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
-      if (a.mode == OUT_STORE) {
-        a.out[idx] = v;
-      } else if (a.mode == OUT_ACCUM) {
-        float2 o = a.out[idx];
-        a.out[idx] = make_float2(o.x + v.x, o.y + v.y);
-      } else {
-        float2 G;
-        if (!gain_product(a.peel, row, a.n_base, f, G)) atomicOr(a.err, WN_DEVERR_ANTENNA);
-        const float2 d = a.mode == OUT_SUBG ? a.out[idx] : a.peel.data[idx];
-        a.out[idx] = make_float2(d.x - (G.x * v.x - G.y * v.y), d.y - (G.x * v.y + G.y * v.x));
-      }
+      part[(2 * k) * K1_THREADS + threadIdx.x] = ok ? Vre[k] : nan2;
+      part[(2 * k + 1) * K1_THREADS + threadIdx.x] = ok ? Vim[k] : nan2;
     }
+  } else {
+    k1_store<K>(a, row_w0 + 2 * g, f0, Vre, Vim, ok);
   }
   __syncthreads();  // every warp is past its last barrier wait and shared-memory read
   if (threadIdx.x == 0) {
@@ -328,10 +373,47 @@ __device__ __forceinline__ void k1_tile(const K1Args& a, const int bx, const int
   __syncthreads();
 }
 
+// Single launch over a 1-D grid.  CTAs 0 .. n_main-1 are whole tiles in (row tile fastest, channel
+// block) order.  When the tile count leaves the last wave of resident CTAs mostly empty, each of the
+// remaining tiles is split into tail_parts CTAs over consecutive ranges of tail_ct component tiles,
+// so the tail fills that wave; k1_tail_sum then adds their partial sums in part order and writes them.
 template <int K, bool UNIFORM>
 __global__ void __launch_bounds__(K1_THREADS, 2) k1_phasor(const K1Args a) {
   extern __shared__ __align__(128) unsigned char smem[];
-  k1_tile<K, UNIFORM>(a, blockIdx.x, blockIdx.y, smem);
+  int lin = blockIdx.x, t_beg = 0, t_end = INT_MAX;
+  float2* part = nullptr;
+  if (lin >= a.n_main) {
+    const int j = lin - a.n_main, p = j % a.tail_parts;
+    lin = a.n_main + j / a.tail_parts;
+    t_beg = p * a.tail_ct;
+    t_end = t_beg + a.tail_ct;
+    part = a.part + (size_t)j * (2 * K * K1_THREADS);
+  }
+  k1_tile<K, UNIFORM>(a, lin % a.grid_x, lin / a.grid_x, t_beg, t_end, part, smem);
+}
+
+// The split tail tiles: CTA i sums the tail_parts partial sums of tile n_main + i in part order (a
+// fixed order, so the result does not depend on scheduling) and writes them in the output mode.  Each
+// thread owns the same (rows, channels) as the k1_tile thread of the same index.
+template <int K>
+__global__ void __launch_bounds__(K1_THREADS) k1_tail_sum(const K1Args a) {
+  const int lin = a.n_main + blockIdx.x;
+  const int bx = lin % a.grid_x, by = lin / a.grid_x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rpw = 2 << (5 - a.log2L);
+  const int g = lane >> a.log2L, sub = lane & ((1 << a.log2L) - 1);
+  float2 Vre[K], Vim[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) Vre[k] = Vim[k] = make_float2(0.f, 0.f);
+  const float2* src = a.part + (size_t)blockIdx.x * a.tail_parts * (2 * K * K1_THREADS) + threadIdx.x;
+  for (int p = 0; p < a.tail_parts; ++p, src += 2 * K * K1_THREADS) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      Vre[k] = __fadd2_rn(Vre[k], src[(2 * k) * K1_THREADS]);
+      Vim[k] = __fadd2_rn(Vim[k], src[(2 * k + 1) * K1_THREADS]);
+    }
+  }
+  k1_store<K>(a, bx * (K1_WARPS * rpw) + warp * rpw + 2 * g, by * a.chan_block + sub * K, Vre, Vim, true);
 }
 
 struct K1Choice {
@@ -372,13 +454,18 @@ static K1Choice k1_choose(long rows, int F, int num_sms) {
 }
 
 template <int K, bool U>
-static cudaError_t k1_launch(const K1Args& a, dim3 grid, int smem, cudaStream_t st) {
+static cudaError_t k1_launch(const K1Args& a, int n_tail, int smem, cudaStream_t st) {
   auto fn = k1_phasor<K, U>;
   cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(fn));
   if (e != cudaSuccess) return e;
-  fn<<<grid, K1_THREADS, smem, st>>>(a);
+  fn<<<a.n_main + n_tail * a.tail_parts, K1_THREADS, smem, st>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || n_tail == 0) return e;
+  k1_tail_sum<K><<<n_tail, K1_THREADS, 0, st>>>(a);
   return cudaGetLastError();
 }
+
+size_t k1_part_bytes(int num_sms) { return (size_t)2 * num_sms * 2 * 16 * K1_THREADS * sizeof(float2); }
 
 int launch_phasor_mixed(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, int mode, const PeelArgs& pa,
                         cudaStream_t st) {
@@ -403,18 +490,39 @@ int launch_phasor_mixed(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* ou
   a.peel = pa;
   a.err = ctx->d_err;
   const int rows_per_cta = K1_WARPS * 2 * (32 >> ch.log2L);
-  dim3 grid((o.n_rows + rows_per_cta - 1) / rows_per_cta, (o.n_chan + a.chan_block - 1) / a.chan_block);
+  a.grid_x = (o.n_rows + rows_per_cta - 1) / rows_per_cta;
+  const long n_cta = (long)a.grid_x * ((o.n_chan + a.chan_block - 1) / a.chan_block);
+  if (n_cta > INT_MAX / 2) return set_error(WN_EINVAL, "observation too large for one phasor launch");
   const int smem = k1_smem_layout(ch.log2L, ch.K).total;
+  // Tail split: the last n_cta mod slots tiles (slots = resident CTAs) would run as a mostly empty
+  // wave; split each into parts over component ranges so that they fill it.
+  const int slots = ctx->num_sms * (smem <= 113 * 1024 ? 2 : 1);
+  const int n_ct = (M->n_point + K1_CT - 1) / K1_CT + (M->n_gauss + K1_CT - 1) / K1_CT;
+  const int rem = (int)(n_cta % slots);
+  a.n_main = (int)n_cta;
+  a.tail_parts = 1;
+  a.tail_ct = n_ct;
+  a.part = ctx->k1_part;
+  int n_tail = 0;
+  if (rem > 0 && n_ct >= 2 && ctx->k1_part) {
+    int parts = std::min(slots / rem, n_ct);
+    if (parts >= 2) {
+      a.tail_ct = (n_ct + parts - 1) / parts;
+      a.tail_parts = (n_ct + a.tail_ct - 1) / a.tail_ct;  // no empty part
+      a.n_main = (int)n_cta - rem;
+      n_tail = rem;
+    }
+  }
   cudaError_t e;
   switch (ch.K * 2 + (o.uniform ? 1 : 0)) {
-    case 4 * 2 + 1: e = k1_launch<4, true>(a, grid, smem, st); break;
-    case 4 * 2: e = k1_launch<4, false>(a, grid, smem, st); break;
-    case 8 * 2 + 1: e = k1_launch<8, true>(a, grid, smem, st); break;
-    case 8 * 2: e = k1_launch<8, false>(a, grid, smem, st); break;
-    case 12 * 2 + 1: e = k1_launch<12, true>(a, grid, smem, st); break;
-    case 12 * 2: e = k1_launch<12, false>(a, grid, smem, st); break;
-    case 16 * 2 + 1: e = k1_launch<16, true>(a, grid, smem, st); break;
-    default: e = k1_launch<16, false>(a, grid, smem, st); break;
+    case 4 * 2 + 1: e = k1_launch<4, true>(a, n_tail, smem, st); break;
+    case 4 * 2: e = k1_launch<4, false>(a, n_tail, smem, st); break;
+    case 8 * 2 + 1: e = k1_launch<8, true>(a, n_tail, smem, st); break;
+    case 8 * 2: e = k1_launch<8, false>(a, n_tail, smem, st); break;
+    case 12 * 2 + 1: e = k1_launch<12, true>(a, n_tail, smem, st); break;
+    case 12 * 2: e = k1_launch<12, false>(a, n_tail, smem, st); break;
+    case 16 * 2 + 1: e = k1_launch<16, true>(a, n_tail, smem, st); break;
+    default: e = k1_launch<16, false>(a, n_tail, smem, st); break;
   }
   if (e != cudaSuccess) return set_error(WN_ECUDA, std::string("phasor kernel launch: ") + cudaGetErrorString(e));
   return WN_OK;
@@ -438,8 +546,8 @@ __global__ void __launch_bounds__(K1_THREADS, 2) k1_batched(const K1Args* reqs, 
     const K1Work w = work[e];
     if (threadIdx.x == 0) args = reqs[w.req];
     __syncthreads();
-    if (args.chan_block == (12 << args.log2L)) k1_tile<12, true>(args, w.bx, w.by, smem);
-    else k1_tile<8, true>(args, w.bx, w.by, smem);
+    if (args.chan_block == (12 << args.log2L)) k1_tile<12, true>(args, w.bx, w.by, 0, INT_MAX, nullptr, smem);
+    else k1_tile<8, true>(args, w.bx, w.by, 0, INT_MAX, nullptr, smem);
   }
 }
 

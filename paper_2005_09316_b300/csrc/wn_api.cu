@@ -185,6 +185,12 @@ int wn_create(wn_ctx** out, int device) {
     return cuda_fail(e, "cudaMalloc(error word)");
   }
   cudaMemset(c->d_err, 0, sizeof(unsigned));
+  e = cudaMalloc(&c->k1_part, k1_part_bytes(c->num_sms));
+  if (e != cudaSuccess) {
+    cudaFree(c->d_err);
+    delete c;
+    return cuda_fail(e, "cudaMalloc(phasor tail partial sums)");
+  }
   cudaDeviceSynchronize();
   *out = c;
   return ok();
@@ -196,6 +202,7 @@ void wn_destroy(wn_ctx* ctx) {
   cudaDeviceSynchronize();
   for (auto& kv : ctx->models) free_model(kv.second);
   cudaFree(ctx->d_err);
+  cudaFree(ctx->k1_part);
   cudaFree(ctx->ws);
   cudaFree(ctx->ws2);
   cudaFree(ctx->lut);

@@ -98,6 +98,7 @@ struct wn_ctx {
   void* ws2 = nullptr;
   size_t ws2_bytes = 0;
   float* lut = nullptr;  // basis table of the lookup-table shapelet mode (built on first use)
+  float2* k1_part = nullptr;  // partial sums of the split tail tiles of the phasor launch (fixed size)
 };
 
 namespace wn {
@@ -137,6 +138,10 @@ struct K1Args {
   int mode;
   PeelArgs peel;
   unsigned* err;
+  // single launch only: CTAs 0 .. n_main-1 are whole tiles (grid_x row tiles per channel block); the
+  // tiles after them are split into tail_parts component ranges of tail_ct tiles with partial sums in part
+  int grid_x = 1, n_main = 0, tail_parts = 1, tail_ct = 0;
+  float2* part = nullptr;
 };
 
 // One work entry of the batched phasor kernel: request index, row tile, channel block.
@@ -336,6 +341,7 @@ size_t static_scratch_entries();
 int launch_grad(wn_ctx* ctx, const ObsDev& o, const Model* M, const PeelArgs& pa, float2* resid,
                 const wn_sky_grad* g, double* loss, cudaStream_t st);
 int k1_batched_smem();
+size_t k1_part_bytes(int num_sms);
 int launch_fit_shapelets(wn_ctx* ctx, const ObsDev& o, Model* M, const PeelArgs& pa, int n_iter, double tol,
                          double* coeff, double* info, cudaStream_t st);
 int launch_calibrate(wn_ctx* ctx, const ObsDev& o, const float2* model, const float2* data, float2* gains, int n_iter,
