@@ -652,6 +652,13 @@ def main():
             extra["roofline"]["frac_of_measured_ffma"] = round(achieved / (pr["ffma"] / 1e12), 4)
         except Exception as exc:  # noqa: BLE001 - reported, not fatal
             extra["roofline"]["measured_pipes_Tops"] = f"unavailable: {exc}"
+        try:  # the kernel's own channel loop run alone: the bound its instruction mix sets
+            lr = ctx.phasor_loop_rate()
+            extra["roofline"]["loop_bound"] = {"value": lr, "unit": UNIT, "frac": round(value / ws / lr, 4),
+                                               "what": "the kernel's channel loop alone (shared-memory components, "
+                                                       "4 point tiles per Gaussian tile, no records/I/O/barriers)"}
+        except Exception as exc:  # noqa: BLE001 - reported, not fatal
+            extra["roofline"]["loop_bound"] = f"unavailable: {exc}"
         if clocks.get("sm_mhz"):
             extra["roofline"]["frac_at_sampled_clock"] = round(
                 achieved / (n_sm * FP32_LANES_PER_SM * clocks["sm_mhz"] * 1e6 / 1e12), 4)

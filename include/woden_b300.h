@@ -307,6 +307,14 @@ WN_API int wn_calibrate(wn_ctx* ctx, const wn_obs* obs, const void* model_c64, c
  * it allocates a small scratch buffer and synchronises its own stream.  Takes a few milliseconds. */
 WN_API int wn_pipe_rates(wn_ctx* ctx, double* rates);
 
+/* Component-visibility evaluations per second that the point/Gaussian kernel's channel loop sustains
+ * by itself (no paper counterpart): the kernel's own loop code over components held in shared memory,
+ * four tiles of 32 points per tile of 32 Gaussians, 12 channels of two rows per lane, 2 CTAs of 256
+ * threads per SM, with no records, global memory or barriers inside the loop.  The rate the full
+ * prediction approaches; its instruction mix, not the FP32 peak, sets it.  Best of three timed launches
+ * after one warm-up; allocates a small scratch buffer and synchronises its own stream. */
+WN_API int wn_phasor_loop_rate(wn_ctx* ctx, double* evals_per_s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,7 +28,8 @@ EXPORTED = ("wn_create", "wn_destroy", "wn_last_error", "wn_version", "wn_set_pr
             "wn_sky_upload", "wn_sky_free", "wn_sky_bytes", "wn_predict", "wn_peel", "wn_peel_model",
             "wn_predict_grad", "wn_predict_static", "wn_server_create", "wn_server_destroy", "wn_server_submit",
             "wn_server_poll", "wn_server_wait", "wn_server_copy", "wn_server_release", "wn_server_cancel",
-            "wn_server_stats", "wn_calibrate", "wn_fit_shapelets", "wn_pipe_rates")
+            "wn_server_stats", "wn_calibrate", "wn_fit_shapelets", "wn_pipe_rates",
+            "wn_phasor_loop_rate")
 
 
 class WnError(RuntimeError):
@@ -102,6 +103,7 @@ def load(build_if_missing: bool = True):
         L.wn_calibrate.argtypes = [P, ctypes.POINTER(WnObs), P, P, P, i, P]
         L.wn_fit_shapelets.argtypes = [P, ctypes.POINTER(WnObs), i, P, i, i, P, i, dbl, P, ctypes.POINTER(dbl), P]
         L.wn_pipe_rates.argtypes = [P, ctypes.POINTER(dbl)]
+        L.wn_phasor_loop_rate.argtypes = [P, ctypes.POINTER(dbl)]
         for name in EXPORTED:
             if name not in ("wn_destroy", "wn_last_error", "wn_version", "wn_server_destroy"):
                 getattr(L, name).restype = ctypes.c_int
@@ -293,6 +295,12 @@ class Context:
         r = (ctypes.c_double * 4)()
         _check(load().wn_pipe_rates(self.h, r))
         return {"ffma": r[0], "ffma2": r[1], "mufu_ex2": r[2], "dfma": r[3]}
+
+    def phasor_loop_rate(self) -> float:
+        """Evaluations per second the point/Gaussian kernel's channel loop sustains by itself."""
+        r = ctypes.c_double()
+        _check(load().wn_phasor_loop_rate(self.h, ctypes.byref(r)))
+        return r.value
 
     def upload(self, sky, stream=None) -> Model:
         d = sky if isinstance(sky, dict) else sky_to_device(sky, f"cuda:{self.device}")

@@ -21,3 +21,37 @@ def test_pipe_rates():
     assert 0.7 < r["ffma2"] / r["ffma"] < 1.4, r
     assert r["mufu_ex2"] < 0.5 * r["ffma"], r
     assert r["dfma"] < 0.25 * r["ffma"], r
+
+
+def test_phasor_loop_rate_bounds_the_kernel():
+    """The channel loop alone is at least as fast as the whole prediction (which adds records, barriers
+    and I/O) and below the evaluations per second the FP32 pipe allows at 6 lane operations each."""
+    import numpy as np
+
+    import paper_2005_09316_b300 as wn
+    import synth
+    ctx = wn.Context(0)
+    loop = ctx.phasor_loop_rate()
+    ffma = ctx.pipe_rates()["ffma"]
+    obs, sky = synth.mwa(n_time=2)
+    d = wn.obs_to_device(obs)
+    m = ctx.upload(sky)
+    out = torch.empty(obs.n_time, obs.n_base, obs.n_chan, dtype=torch.complex64, device="cuda")
+    for _ in range(2):
+        ctx.predict(d, m, out=out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+    ts = []
+    for _ in range(3):
+        e0.record()
+        ctx.predict(d, m, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) * 1e-3)
+    kernel = obs.n_vis * sky.n_comp / min(ts)
+    m.free()
+    ctx.close()
+    assert math.isfinite(loop) and loop > 0
+    assert kernel <= 1.05 * loop, (kernel, loop)
+    assert loop < ffma / 6.0, (loop, ffma)
+    assert np.isfinite(kernel)
