@@ -37,6 +37,8 @@ constexpr int K2_M = 128;
 constexpr int K2_GROUPS = 2;                     // tile parities in flight
 constexpr int K2_THREADS = 32 * (8 * K2_GROUPS + 1);
 constexpr int K2_MMA_WARP = 8 * K2_GROUPS;
+// Rows per thread whose output the epilogue forms itself (the rest go to the producers): half of them.
+#define K2_RE(R) ((R) / 2)
 
 // sqrt(2/(n+1)) and sqrt(n/(n+1)) of the normalised Hermite recurrence
 //   phi_{n+1} = sqrt(2/(n+1)) x phi_n - sqrt(n/(n+1)) phi_{n-1}.
@@ -60,6 +62,8 @@ struct K2Args {
   float c_amp, alpha, sgn;
   float2* out;
   PeelArgs peel;
+  const float2* rowg;  // [n_rows] gain product g[ant1] conj(g[ant2]) of a peel whose gains do not depend on
+                       // frequency (else nullptr: the epilogue forms it from the gains)
   unsigned* err;
 };
 
@@ -144,7 +148,7 @@ __host__ __device__ __forceinline__ uint32_t kmaj_off(int row, int k, int rows) 
 }
 
 struct K2Layout {
-  int b_bytes, a_bytes, a0, coef, bars, total;
+  int b_bytes, a_bytes, a0, coef, bars, xfer, total;
 };
 
 __host__ __device__ inline K2Layout k2_layout(int kp, int n_pad, int passes, int groups, int R) {
@@ -156,7 +160,9 @@ __host__ __device__ inline K2Layout k2_layout(int kp, int n_pad, int passes, int
   L.coef = L.a0 + groups * L.a_bytes;  // recurrence coefficients a_n, b_n: 2 x 128 floats, then the
                                        // pairs {a_n, a_n}, {-b_n, -b_n} for two rows at once: 2 x 128 float2
   L.bars = L.coef + 2 * (kNmaxLimit + 1) * 4 + 2 * (kNmaxLimit + 1) * 8;
-  L.total = L.bars + 128;  // barriers (1 + 3 per parity) and the TMEM address slot
+  L.xfer = L.bars + 128;  // barriers (1 + 5 per parity) and the TMEM address slot
+  // the epilogue's dot products (xr, xi) per visibility of a tile, handed to the producers for the output
+  L.total = L.xfer + groups * R * K2_M * 8;
   return L;
 }
 
@@ -376,6 +382,41 @@ __device__ __forceinline__ void epi_chunk_lut(const uint32_t* t, const float* lu
   }
 }
 
+// The output of one visibility of a shapelet launch: S(nu) xi e^{-2 pi i tau nu / c} (eq:shape-env,
+// eq:measure_eq_discrete) from the dot product xi = xr + i xi_i, stored, added to the output, or
+// subtracted as G times it from the data or the output (Sec. 5.1).  k2_out_load issues the loads of
+// its inputs; k2_out_store forms and writes it once xi is known.
+struct K2OutIn {
+  float4 ri, ci;  // (., ., tau hi, tau lo), (nu/c hi, nu/c lo, log2(nu/nu0), .)
+  float2 base, G;
+};
+
+__device__ __forceinline__ void k2_out_load(const K2Args& a, long long vis, K2OutIn& o) {
+  const bool ok = vis < a.n_vis;
+  const int row = ok ? (int)(vis / a.n_chan) : 0;
+  const int f = ok ? (int)(vis - (long long)row * a.n_chan) : 0;
+  o.ri = ok ? __ldg(a.rowinfo + row) : make_float4(0.f, 0.f, 0.f, 0.f);
+  o.ci = ok ? __ldg(a.chaninfo + f) : make_float4(0.f, 0.f, 0.f, 1.f);
+  o.base = make_float2(0.f, 0.f);
+  o.G = make_float2(0.f, 0.f);
+  if (ok && a.mode != OUT_STORE) o.base = a.mode == OUT_PEEL ? a.peel.data[vis] : a.out[vis];
+  if (ok && a.mode >= OUT_PEEL) {
+    if (a.rowg) o.G = __ldg(a.rowg + row);
+    else if (!gain_product(a.peel, row, a.n_base, f, o.G)) atomicOr(a.err, WN_DEVERR_ANTENNA);
+  }
+}
+
+__device__ __forceinline__ void k2_out_store(const K2Args& a, long long vis, const K2OutIn& o, float xr, float xi) {
+  if (vis >= a.n_vis) return;
+  const float2 P = phasor_fast(reduce_turns(o.ri.z, o.ri.w, o.ci.x, o.ci.y));
+  const float amp = a.sgn * ex2_approx(fmaf(a.alpha, o.ci.z, a.c_amp));
+  const float zr = amp * (xr * P.x - xi * P.y), zi = amp * (xr * P.y + xi * P.x);  // amp (xr + i xi) P
+  const size_t idx = (size_t)vis;
+  if (a.mode == OUT_STORE) a.out[idx] = make_float2(zr, zi);
+  else if (a.mode == OUT_ACCUM) a.out[idx] = make_float2(o.base.x + zr, o.base.y + zi);
+  else a.out[idx] = make_float2(o.base.x - (o.G.x * zr - o.G.y * zi), o.base.y - (o.G.x * zi + o.G.y * zr));
+}
+
 template <int KP, int R, bool LUT>
 __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -386,7 +427,9 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
   uint64_t* afull = bfull + 1;                // [parity] producer -> MMA: A written
   uint64_t* mdone = afull + K2_GROUPS;        // [parity] MMA -> producer/epilogue: MMA complete
   uint64_t* tfree = mdone + K2_GROUPS;        // [parity] epilogue -> MMA: TMEM read
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(tfree + K2_GROUPS);
+  uint64_t* xfull = tfree + K2_GROUPS;        // [parity] epilogue -> producers: dot products written
+  uint64_t* xempty = xfull + K2_GROUPS;       // [parity] producers -> epilogue: dot products read
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(xempty + K2_GROUPS);
   const int warp = threadIdx.x >> 5;
   const int acc_cols = a.n_pad * ng * R;
   const uint32_t ncols = acc_cols <= 32 ? 32 : (acc_cols <= 64 ? 64 : (acc_cols <= 128 ? 128 : (acc_cols <= 256 ? 256 : 512)));
@@ -397,6 +440,8 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
       mbar_init(&afull[g], 128);
       mbar_init(&mdone[g], 1);
       mbar_init(&tfree[g], 128);
+      mbar_init(&xfull[g], 128);
+      mbar_init(&xempty[g], 128);
     }
     fence_mbar_init();
   }
@@ -492,6 +537,24 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
     bool valid[R];
     float xs[R], nu[R];
     load_x(sp, valid, xs, nu);
+    const float2* xfer = reinterpret_cast<const float2*>(smem + lay.xfer) + sp * R * K2_M + m;
+    // The output of rows RE .. R-1 of this parity's tile jo (tile index ito); the epilogue forms rows
+    // 0 .. RE-1 itself.  The inputs' loads are issued first and arrive while the epilogue finishes.
+    auto out_tile = [&](int ito, int jo) -> bool {
+      K2OutIn o[R];
+#pragma unroll
+      for (int r = K2_RE(R); r < R; ++r)
+        k2_out_load(a, (long long)(blockIdx.x + ito * gridDim.x) * (K2_M * R) + r * K2_M + m, o[r]);
+      if (!k2_wait(&xfull[sp], jo & 1, a.err)) return false;
+#pragma unroll
+      for (int r = K2_RE(R); r < R; ++r) {
+        const float2 d = xfer[r * K2_M];
+        k2_out_store(a, (long long)(blockIdx.x + ito * gridDim.x) * (K2_M * R) + r * K2_M + m, o[r], d.x, d.y);
+      }
+      mbar_arrive(&xempty[sp]);
+      return true;
+    };
+    int last = -1;  // this parity's last tile produced whose output is still to be formed
     for (int it = sp, j = 0; it < n_it; it += ng, ++j) {
       float x[R];
       bool v0[R];
@@ -506,16 +569,24 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
       else produce_rows<KP, R>(x, a.nmax, v0, a_base, blk, a.passes > 1, m, ca, cb, ca2, cb2);
       fence_async_smem();
       mbar_arrive(&afull[sp]);
+      // the previous tile's output, while the MMA of this one runs
+      if (j > 0 && !out_tile(it - ng, j - 1)) {
+        last = -1;
+        break;
+      }
+      last = j;
     }
+    if (last >= 0) out_tile(sp + last * ng, last);
   } else {
-    // ---------------- epilogues: xi = sum_n2 T[., n2] phi_n2(y), then S xi P into the output ----------------
+    // ---------------- epilogues: xi = sum_n2 T[., n2] phi_n2(y), handed to the producers ----------------
     const int sp = (warp - 4 * K2_GROUPS) >> 2;
     if (sp >= ng) goto done;
     const int m = threadIdx.x & 127;
     const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(sp * R * a.n_pad);
     const float ycut = sqrtf(2.0f * a.nmax + 1.0f) + 10.0f;
+    float2* xfer = reinterpret_cast<float2*>(smem + lay.xfer) + sp * R * K2_M + m;
     struct EpiIn {
-      float4 ri, ci;
+      float ys, nu;  // y = ys nu
     };
     auto vis_of = [&](int it, int r) { return (long long)(blockIdx.x + it * gridDim.x) * (K2_M * R) + r * K2_M + m; };
     auto valid_of = [&](int it, long long vis) { return it < n_it && vis < a.n_vis; };
@@ -525,8 +596,8 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
       const bool valid = valid_of(it, vis);
       const int row = valid ? (int)(vis / a.n_chan) : 0;
       const int f = valid ? (int)(vis - (long long)row * a.n_chan) : 0;
-      e.ri = valid ? __ldg(a.rowinfo + row) : make_float4(0.f, 0.f, 0.f, 0.f);
-      e.ci = valid ? __ldg(a.chaninfo + f) : make_float4(0.f, 0.f, 0.f, 1.f);
+      e.ys = valid ? __ldg(&a.rowinfo[row].y) : 0.f;
+      e.nu = valid ? __ldg(&a.chaninfo[f].w) : 1.f;
       return e;
     };
     EpiIn nxt[R];
@@ -536,17 +607,17 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
       EpiIn cur[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) cur[r] = nxt[r];
-      if (!k2_wait(&mdone[sp], j & 1, a.err)) break;
       long long vis[R];
       bool valid[R];
-      float2 base[R];  // the value the output is formed from, in flight while the accumulator is read
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         vis[r] = vis_of(it, r);
         valid[r] = valid_of(it, vis[r]);
-        base[r] = make_float2(0.f, 0.f);
-        if (valid[r] && a.mode != OUT_STORE) base[r] = a.mode == OUT_PEEL ? a.peel.data[vis[r]] : a.out[vis[r]];
       }
+      K2OutIn eo[R];  // the inputs of this thread's own outputs, in flight during the wait
+#pragma unroll
+      for (int r = 0; r < K2_RE(R); ++r) k2_out_load(a, valid[r] ? vis[r] : a.n_vis, eo[r]);
+      if (!k2_wait(&mdone[sp], j & 1, a.err)) break;
 #pragma unroll
       for (int r = 0; r < R; ++r) nxt[r] = load_epi(it + ng, r);  // next tile's constants in flight
       tc_fence_after();
@@ -555,7 +626,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
       bool yfast = true;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        y[r] = cur[r].ri.y * cur[r].ci.w;
+        y[r] = cur[r].ys * cur[r].nu;
         const bool yzero = !valid[r] || !(fabsf(y[r]) <= ycut);
         yfast = yfast && (yzero || fabsf(y[r]) <= 12.5f);
         q[r] = yzero ? 0.f : 1.f;  // marks zero rows until the seed below
@@ -628,27 +699,12 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
       }
       tc_fence_before();
       mbar_arrive(&tfree[sp]);
+      if (j > 0 && !k2_wait(&xempty[sp], (j - 1) & 1, a.err)) break;  // the producers have read tile j-1's
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        if (!valid[r]) continue;
-        const float4 ri = cur[r].ri, ci = cur[r].ci;
-        const float2 P = phasor_fast(reduce_turns(ri.z, ri.w, ci.x, ci.y));
-        const float amp = a.sgn * ex2_approx(fmaf(a.alpha, ci.z, a.c_amp));
-        // Z = amp (xr + i xi) P
-        const float zr = amp * (xr[r] * P.x - xi[r] * P.y), zi = amp * (xr[r] * P.y + xi[r] * P.x);
-        const size_t idx = (size_t)vis[r];
-        if (a.mode == OUT_STORE) {
-          a.out[idx] = make_float2(zr, zi);
-        } else if (a.mode == OUT_ACCUM) {
-          a.out[idx] = make_float2(base[r].x + zr, base[r].y + zi);
-        } else {
-          const int row = (int)(vis[r] / a.n_chan);
-          const int f = (int)(vis[r] - (long long)row * a.n_chan);
-          float2 G;
-          if (!gain_product(a.peel, row, a.n_base, f, G)) atomicOr(a.err, WN_DEVERR_ANTENNA);
-          a.out[idx] = make_float2(base[r].x - (G.x * zr - G.y * zi), base[r].y - (G.x * zi + G.y * zr));
-        }
-      }
+      for (int r = K2_RE(R); r < R; ++r) xfer[r * K2_M] = valid[r] ? make_float2(xr[r], xi[r]) : make_float2(0.f, 0.f);
+      mbar_arrive(&xfull[sp]);
+#pragma unroll
+      for (int r = 0; r < K2_RE(R); ++r) k2_out_store(a, valid[r] ? vis[r] : a.n_vis, eo[r], xr[r], xi[r]);
     }
   }
 done:
@@ -681,6 +737,16 @@ __global__ void k2_rowinfo(const double* uvw, int n_rows, const ShapeRec* sh, do
   const double tau = u * sh->l + v * sh->m + w * sh->nm1;
   const float th = __double2float_rn(tau);
   out[r] = make_float4((float)xs, (float)ys, th, __double2float_rn(tau - (double)th));
+}
+
+// Per-row gain product of a peel with frequency-independent gains: G[row] = g[tg][0][ant1] conj(g[tg][0][ant2]),
+// NaN (and the antenna flag) for an antenna index out of range, as the epilogue would form it.
+__global__ void k2_rowgain(PeelArgs p, int n_rows, int n_base, float2* out, unsigned* err) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_rows) return;
+  float2 G;
+  if (!gain_product(p, r, n_base, 0, G)) atomicOr(err, WN_DEVERR_ANTENNA);
+  out[r] = G;
 }
 
 static int g_consts_ready[64] = {0};
@@ -778,7 +844,7 @@ static int ws_reserve(wn_ctx* ctx, size_t bytes, cudaStream_t st) {
 
 // Shapelet launches with caller-supplied tables: per-channel (n_chan float4) and per-row (n_rows float4).
 int launch_shapelets_ws(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, int mode, const PeelArgs& pa,
-                        float4* chaninfo, float4* rowinfo, cudaStream_t st) {
+                        float4* chaninfo, float4* rowinfo, cudaStream_t st, float2* rowg) {
   if (int r = k2_setup_constants(ctx->device, st)) return r;
   k2_chaninfo<<<(o.n_chan + 255) / 256, 256, 0, st>>>(o.freq, o.n_chan, o.nu0, chaninfo);
   const long long n_vis = (long long)o.n_rows * o.n_chan;
@@ -787,6 +853,9 @@ int launch_shapelets_ws(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* ou
   if (ctx->shape_mode == WN_SHAPE_LUT_BF16X3)
     if (int r = k2_lut(ctx, st, &lut)) return r;
   const double L0 = std::log2(o.nu0);
+  const bool peeling = mode == OUT_PEEL || mode == OUT_SUBG;
+  if (rowg && (!peeling || pa.gf != 1)) rowg = nullptr;
+  if (rowg) k2_rowgain<<<(o.n_rows + 255) / 256, 256, 0, st>>>(pa, o.n_rows, o.n_base, rowg, ctx->d_err);
   for (int q = 0; q < M->n_shape; ++q) {
     const ShapeRec& h = M->sh_host[q];
     k2_rowinfo<<<(o.n_rows + 255) / 256, 256, 0, st>>>(o.uvw, o.n_rows, M->sh + q, o.dec0, rowinfo);
@@ -806,6 +875,7 @@ int launch_shapelets_ws(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* ou
     a.sgn = h.sgn;
     a.out = out;
     a.peel = pa;
+    a.rowg = rowg;
     a.err = ctx->d_err;
     // the first shapelet applies the caller's mode, the rest add (or subtract G times) their part
     a.mode = q == 0 ? mode : (mode == OUT_STORE ? OUT_ACCUM : (mode == OUT_PEEL ? OUT_SUBG : mode));
@@ -835,10 +905,12 @@ int launch_shapelets_ws(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* ou
 int launch_shapelets(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, int mode, const PeelArgs& pa,
                      cudaStream_t st) {
   const size_t chan_bytes = ((size_t)o.n_chan * sizeof(float4) + 255) & ~(size_t)255;
-  if (int r = ws_reserve(ctx, chan_bytes + (size_t)o.n_rows * sizeof(float4), st)) return r;
+  const size_t row_bytes = ((size_t)o.n_rows * sizeof(float4) + 255) & ~(size_t)255;
+  if (int r = ws_reserve(ctx, chan_bytes + row_bytes + (size_t)o.n_rows * sizeof(float2), st)) return r;
   float4* chaninfo = static_cast<float4*>(ctx->ws);
   float4* rowinfo = reinterpret_cast<float4*>(static_cast<char*>(ctx->ws) + chan_bytes);
-  return launch_shapelets_ws(ctx, o, M, out, mode, pa, chaninfo, rowinfo, st);
+  float2* rowg = reinterpret_cast<float2*>(static_cast<char*>(ctx->ws) + chan_bytes + row_bytes);
+  return launch_shapelets_ws(ctx, o, M, out, mode, pa, chaninfo, rowinfo, st, rowg);
 }
 
 }  // namespace wn
@@ -885,7 +957,7 @@ int launch_shapelets_static(wn_ctx* ctx, const ObsDev& o, const Model* M, float2
                                     std::to_string(kStaticScratchEntries) + " entries");
   float4* base = nullptr;
   if (int r = static_scratch_address(ctx->device, &base)) return r;
-  return launch_shapelets_ws(ctx, o, M, out, mode, pa, base, base + chan_entries, st);
+  return launch_shapelets_ws(ctx, o, M, out, mode, pa, base, base + chan_entries, st, nullptr);
 }
 
 }  // namespace wn

@@ -351,5 +351,5 @@ int k1_batched_args(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, i
                     K1Args* args, int* grid_x, int* grid_y);
 cudaError_t k1_batched_launch(const K1Args* reqs, const K1Work* work, const int* n_work, int grid, cudaStream_t st);
 int launch_shapelets_ws(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, int mode, const PeelArgs& pa,
-                        float4* chaninfo, float4* rowinfo, cudaStream_t st);
+                        float4* chaninfo, float4* rowinfo, cudaStream_t st, float2* rowg = nullptr);
 }  // namespace wn
