@@ -435,14 +435,26 @@ __device__ void hermite_scaled_row(float x, int nmax1, float* out) {
   }
 }
 
-// Shared-memory layout of k4_grad_shape (bytes): basis rows, folded coefficient pairs (f, g) per
-// triangle row a (b = 0..n-a+1), row offsets, tile weights, FP64 coefficient accumulators.
+// The coefficient gradients are summed in blocks of 2 n1 x 4 n2 (n1 from 2I, n2 from 4J) covering the
+// triangle n1 + n2 <= n; the number of such blocks.
+__host__ __device__ inline int k4s_nblocks(int nmax) {
+  int c = 0;
+  for (int J = 0; 4 * J <= nmax; ++J) c += (nmax - 4 * J) / 2 + 1;
+  return c;
+}
+
+// Shared-memory layout of k4_grad_shape (bytes): basis rows (a multiple of 4 floats with an odd count of
+// 16-byte quarters, so per-thread rows read as float4 without bank conflicts), folded coefficient pairs
+// (f, g) per triangle row a (b = 0..n-a+1), row offsets, tile weights, the FP64 coefficient-gradient
+// sums over the same folded triangle, and the list of (n1, n2) blocks.
 struct K4SSmem {
-  int ld, phx, phy, fg, toff, wre, wim, accc, total;
+  int ld, phx, phy, fg, toff, wre, wim, accd, blocks, total;
 };
 __host__ __device__ inline K4SSmem k4s_layout(int nmax, int nnz, int T) {
+  (void)nnz;
   K4SSmem s;
-  s.ld = (nmax + 3) | 1;
+  s.ld = (nmax + 4 + 3) & ~3;  // entries 0 .. n + 3 (the blocks read up to n2 = 4J + 3)
+  if (((s.ld >> 2) & 1) == 0) s.ld += 4;
   const int nfg = (nmax + 1) * (nmax + 4) / 2;  // sum over a of (n - a + 2)
   s.phx = 0;
   s.phy = s.phx + T * s.ld * 4;
@@ -450,8 +462,9 @@ __host__ __device__ inline K4SSmem k4s_layout(int nmax, int nnz, int T) {
   s.toff = s.fg + nfg * 8;
   s.wre = s.toff + (nmax + 2) * 4;
   s.wim = s.wre + T * 4;
-  s.accc = (s.wim + T * 4 + 7) & ~7;
-  s.total = s.accc + nnz * 8;
+  s.accd = (s.wim + T * 4 + 7) & ~7;
+  s.blocks = s.accd + nfg * 8;
+  s.total = s.blocks + k4s_nblocks(nmax) * 4;
   return s;
 }
 
@@ -467,15 +480,24 @@ __global__ void __launch_bounds__(K4S_T) k4_grad_shape(const K4SArgs a) {
   int* toff = reinterpret_cast<int*>(sm + lay.toff);
   float* wre = reinterpret_cast<float*>(sm + lay.wre);
   float* wim = reinterpret_cast<float*>(sm + lay.wim);
-  double* accc = reinterpret_cast<double*>(sm + lay.accc);
+  double* accd = reinterpret_cast<double*>(sm + lay.accd);  // [folded triangle] coefficient-gradient sums
+  ushort2* blocks = reinterpret_cast<ushort2*>(sm + lay.blocks);
+  const int nblk = k4s_nblocks(n);
   const int t = threadIdx.x;
   const double flux = *a.flux, beta1 = *a.beta1, beta2 = *a.beta2;
 
   // folded coefficients: row a holds (f_ab, g_ab) for b = 0..n-a+1 (f is zero past the triangle)
   for (int aa = t; aa <= n + 1; aa += T) toff[aa] = aa * (n + 2) - aa * (aa - 1) / 2;
   const int nfg = (n + 1) * (n + 4) / 2;
-  for (int i = t; i < nfg; i += T) fg[i] = make_float2(0.f, 0.f);
-  for (int k = t; k < a.nnz; k += T) accc[k] = 0.0;
+  for (int i = t; i < nfg; i += T) {
+    fg[i] = make_float2(0.f, 0.f);
+    accd[i] = 0.0;
+  }
+  if (t == 0) {  // (2I, 4J) blocks of the triangle, J outer
+    int c = 0;
+    for (int J = 0; 4 * J <= n; ++J)
+      for (int I = 0; 2 * I <= n - 4 * J; ++I) blocks[c++] = make_ushort2((unsigned short)(2 * I), (unsigned short)(4 * J));
+  }
   __syncthreads();
   for (int k = t; k < a.nnz; k += T) {
     const int na = __ldg(a.n1 + k), nb = __ldg(a.n2 + k);
@@ -511,8 +533,8 @@ __global__ void __launch_bounds__(K4S_T) k4_grad_shape(const K4SArgs a) {
     float* py = phy + t * ld;
     hermite_scaled_row(x, n + 1, px);
     hermite_scaled_row(y, n + 1, py);
-    px[n + 2] = 0.f;
-    py[n + 2] = 0.f;
+    px[n + 2] = px[n + 3] = 0.f;
+    py[n + 2] = py[n + 3] = 0.f;
     // W = conj(G) R, amplitude and phasor
     float2 W = make_float2(0.f, 0.f);
     if (valid) {
@@ -538,6 +560,18 @@ __global__ void __launch_bounds__(K4S_T) k4_grad_shape(const K4SArgs a) {
       const int nb = n - aa + 1;  // b = 0..nb (g reaches one past the triangle)
       float te = 0.f, to = 0.f, ge = 0.f, go = 0.f;  // f and g sums over even / odd b
       int b = 0;
+      for (; b + 3 <= nb; b += 4) {
+        const float4 p = *reinterpret_cast<const float4*>(py + b);
+        const float2 c0 = r[b], c1 = r[b + 1], c2 = r[b + 2], c3 = r[b + 3];
+        te = fmaf(c0.x, p.x, te);
+        ge = fmaf(c0.y, p.x, ge);
+        to = fmaf(c1.x, p.y, to);
+        go = fmaf(c1.y, p.y, go);
+        te = fmaf(c2.x, p.z, te);
+        ge = fmaf(c2.y, p.z, ge);
+        to = fmaf(c3.x, p.w, to);
+        go = fmaf(c3.y, p.w, go);
+      }
       for (; b + 1 <= nb; b += 2) {
         const float2 c0 = r[b], c1 = r[b + 1];
         const float p0 = py[b], p1 = py[b + 1];
@@ -590,21 +624,46 @@ __global__ void __launch_bounds__(K4S_T) k4_grad_shape(const K4SArgs a) {
       nacc = 0;
     }
     __syncthreads();
-    // coefficient gradients for this tile
+    // coefficient gradients for this tile, for every (n1, n2) of the triangle in blocks of 2 x 4: one
+    // thread per block sums sum_v Re or Im (Y_v) phi_n1(x_v) phi_n2(y_v) over the tile's visibilities.
+    // -2 Re(Y s) phi phi with s = (-i)^(n1+n2) = 1, -i, -1, i takes Re(Y), Im(Y), -Re(Y), -Im(Y): the
+    // parity of n1 + n2 selects Re or Im (fixed within a block, since n1 starts even and n2 at 4J), the
+    // sign follows when the block is added to the FP64 sums.
     const int nv = (int)min((long long)T, a.n_vis - tile * T);
-    for (int k = t; k < a.nnz; k += T) {
-      const int na = __ldg(a.n1 + k), nb = __ldg(a.n2 + k);
-      const int ph = (na + nb) & 3;
-      const float* wsel = (ph & 1) ? wim : wre;
-      float s = 0.f;
-      for (int vv = 0; vv < nv; ++vv) s = fmaf(wsel[vv] * phx[vv * ld + na], phy[vv * ld + nb], s);
-      // -2 Re(Y s_k) phi phi with s_k = 1, -i, -1, i: Re(Y) , Im(Y), -Re(Y), -Im(Y)
-      accc[k] += (double)((ph >= 2 ? 2.0f : -2.0f) * s);
+    for (int bk = t; bk < nblk; bk += T) {
+      const int na0 = blocks[bk].x, nb0 = blocks[bk].y;
+      float s[2][4];
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) s[i][jj] = 0.f;
+      for (int vv = 0; vv < nv; ++vv) {
+        const float wr = wre[vv], wi = wim[vv];
+        const float2 px = *reinterpret_cast<const float2*>(phx + vv * ld + na0);
+        const float4 py4 = *reinterpret_cast<const float4*>(phy + vv * ld + nb0);
+        const float xr0 = wr * px.x, xi0 = wi * px.x, xr1 = wr * px.y, xi1 = wi * px.y;
+        s[0][0] = fmaf(xr0, py4.x, s[0][0]);
+        s[0][1] = fmaf(xi0, py4.y, s[0][1]);
+        s[0][2] = fmaf(xr0, py4.z, s[0][2]);
+        s[0][3] = fmaf(xi0, py4.w, s[0][3]);
+        s[1][0] = fmaf(xi1, py4.x, s[1][0]);
+        s[1][1] = fmaf(xr1, py4.y, s[1][1]);
+        s[1][2] = fmaf(xi1, py4.z, s[1][2]);
+        s[1][3] = fmaf(xr1, py4.w, s[1][3]);
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+          const int na = na0 + i, nb = nb0 + jj;
+          if (na + nb <= n) accd[toff[na] + nb] += (double)((((na + nb) & 3) >= 2 ? 2.0f : -2.0f) * s[i][jj]);
+        }
     }
     __syncthreads();
   }
   // per-CTA partials (the flux factor of every group but the flux one is applied here, in FP64)
-  for (int k = t; k < a.nnz; k += T) a.part_c[(size_t)blockIdx.x * a.nnz + k] = accc[k] * flux;
+  for (int k = t; k < a.nnz; k += T)
+    a.part_c[(size_t)blockIdx.x * a.nnz + k] = accd[toff[__ldg(a.n1 + k)] + __ldg(a.n2 + k)] * flux;
   __shared__ double red[K4S_T][K4S_NS];
   for (int i = 0; i < K4S_NS; ++i) red[t][i] = (accs[i] + (double)acc32[i]) * (i == 0 ? 1.0 : flux);
   __syncthreads();
