@@ -354,14 +354,20 @@ __global__ void __launch_bounds__(K4_WARPS * 32) k4_grad_pg_u(const K4Args a) {
 
 // Sum the per-chunk partials in fixed order and scatter them into the gradient arrays.  Channel
 // passes accumulate (first pass writes).
+// One warp per component: lane l adds chunks l, l + 32, ..., then a fixed butterfly (deterministic).
 __global__ void k4_reduce_pg(const double* partials, int chunks, int n_point, int n_gauss, int first, double* gflux,
                              double* galpha, double* gl, double* gm, double* gmaj, double* gmin, double* gpa) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   const int n_pg = n_point + n_gauss;
-  if (j >= n_pg) return;
+  if (j >= n_pg) return;  // uniform per warp
   double s[K4_NG] = {0, 0, 0, 0, 0, 0, 0};
-  for (int c = 0; c < chunks; ++c)
+  for (int c = lane; c < chunks; c += 32)
     for (int i = 0; i < K4_NG; ++i) s[i] += partials[((size_t)c * n_pg + j) * K4_NG + i];
+#pragma unroll
+  for (int i = 0; i < K4_NG; ++i)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s[i] += __shfl_xor_sync(0xffffffffu, s[i], o);
+  if (lane != 0) return;
   auto put = [&](double* p, int idx, double v) {
     if (p) p[idx] = first ? v : p[idx] + v;
   };
@@ -742,12 +748,14 @@ __global__ void k4_loss_partial(const float2* r, size_t n, double* part) {
   if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
 
+// One warp: lane l adds partials l, l + 32, ..., then a fixed butterfly (deterministic).
 __global__ void k4_loss_final(const double* part, int n, double* out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double s = 0.0;
-    for (int i = 0; i < n; ++i) s += part[i];
-    *out = s;
-  }
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int i = lane; i < n; i += 32) s += part[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0 && blockIdx.x == 0) *out = s;
 }
 
 int launch_shapelet_prep(wn_ctx* ctx, const ObsDev& o, const Model* M, int q, float4* chaninfo, float4* rowinfo,
@@ -876,7 +884,7 @@ int launch_grad(wn_ctx* ctx, const ObsDev& o, const Model* M, const PeelArgs& pa
       else if (km <= 8) k4_grad_pg<8><<<grid, K4_WARPS * 32, 0, st>>>(a);
       else if (km <= 12) k4_grad_pg<12><<<grid, K4_WARPS * 32, 0, st>>>(a);
       else k4_grad_pg<16><<<grid, K4_WARPS * 32, 0, st>>>(a);
-      k4_reduce_pg<<<(n_pg + 127) / 128, 128, 0, st>>>(pgpart, chunks, M->n_point, M->n_gauss, p == 0, g->flux,
+      k4_reduce_pg<<<(n_pg * 32 + 255) / 256, 256, 0, st>>>(pgpart, chunks, M->n_point, M->n_gauss, p == 0, g->flux,
                                                        g->alpha, g->l, g->m, g->g_maj, g->g_min, g->g_pa);
       if (int r = cuda_err("point/Gaussian adjoint")) return r;
     }
