@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(128) k5_fp64(const K5Args a, int shape_lo, int
   const int ns = shape_hi - shape_lo;
   if (threadIdx.x < ns) {
     const int j = a.n_point + a.n_gauss + shape_lo + threadIdx.x;
-    shapelet_frame(a.l[j], a.m[j], a.dec0, frames + 9 * threadIdx.x);
+    shapelet_frame(a.l[j], a.m[j], sin(a.dec0), cos(a.dec0), frames + 9 * threadIdx.x);
   }
   __syncthreads();
   const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;

@@ -27,6 +27,7 @@
 //  Per parity: P(k+2) waits for MMA(k) to finish reading A, MMA(k+2) for E(k) to release TMEM.
 // Every wait is bounded; on a timeout the kernel raises WN_DEVERR_TIMEOUT, drains its own commits and
 // frees TMEM before returning.
+#include <cmath>
 #include <mutex>
 
 #include "wn_internal.cuh"
@@ -724,9 +725,9 @@ __global__ void k2_chaninfo(const double* freq, int n_chan, double nu0, float4* 
   out[f] = make_float4(ah, __double2float_rn(a - (double)ah), (float)log2(nu / nu0), (float)nu);
 }
 
-__global__ void k2_rowinfo(const double* uvw, int n_rows, const ShapeRec* sh, double dec0, float4* out) {
+__global__ void k2_rowinfo(const double* uvw, int n_rows, const ShapeRec* sh, double sd0, double cd0, float4* out) {
   __shared__ double F[9];
-  if (threadIdx.x == 0) shapelet_frame(sh->l, sh->m, dec0, F);
+  if (threadIdx.x == 0) shapelet_frame(sh->l, sh->m, sd0, cd0, F);
   __syncthreads();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n_rows) return;
@@ -858,7 +859,7 @@ int launch_shapelets_ws(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* ou
   if (rowg) k2_rowgain<<<(o.n_rows + 255) / 256, 256, 0, st>>>(pa, o.n_rows, o.n_base, rowg, ctx->d_err);
   for (int q = 0; q < M->n_shape; ++q) {
     const ShapeRec& h = M->sh_host[q];
-    k2_rowinfo<<<(o.n_rows + 255) / 256, 256, 0, st>>>(o.uvw, o.n_rows, M->sh + q, o.dec0, rowinfo);
+    k2_rowinfo<<<(o.n_rows + 255) / 256, 256, 0, st>>>(o.uvw, o.n_rows, M->sh + q, std::sin(o.dec0), std::cos(o.dec0), rowinfo);
     K2Args a;
     a.rowinfo = rowinfo;
     a.chaninfo = chaninfo;
@@ -968,7 +969,7 @@ int launch_shapelet_prep(wn_ctx* ctx, const ObsDev& o, const Model* M, int q, fl
                          bool chan, cudaStream_t st) {
   (void)ctx;
   if (chan) k2_chaninfo<<<(o.n_chan + 255) / 256, 256, 0, st>>>(o.freq, o.n_chan, o.nu0, chaninfo);
-  k2_rowinfo<<<(o.n_rows + 255) / 256, 256, 0, st>>>(o.uvw, o.n_rows, M->sh + q, o.dec0, rowinfo);
+  k2_rowinfo<<<(o.n_rows + 255) / 256, 256, 0, st>>>(o.uvw, o.n_rows, M->sh + q, std::sin(o.dec0), std::cos(o.dec0), rowinfo);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(WN_ECUDA, std::string("shapelet prep: ") + cudaGetErrorString(e));
   return WN_OK;

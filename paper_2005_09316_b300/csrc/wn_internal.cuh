@@ -248,12 +248,14 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // the shapelet's own RA_j, dec_j).  F = R(H_j, dec_j) R(H0, dec0)^T with R the XYZ -> uvw rotation,
 // sin dec_j = m cos dec0 + n sin dec0 and H_j - H0 = -atan2(l, n cos dec0 - m sin dec0); F does not
 // depend on H0, so H0 = 0.
-__device__ inline void shapelet_frame(double l, double m, double dec0, double F[9]) {
-  double n = sqrt(1.0 - l * l - m * m);
-  double decj = asin(m * cos(dec0) + n * sin(dec0));
-  double hj = -atan2(l, n * cos(dec0) - m * sin(dec0));
-  double shj = sin(hj), chj = cos(hj), sdj = sin(decj), cdj = cos(decj);
-  double sd0 = sin(dec0), cd0 = cos(dec0);
+// Formed without transcendentals: with y = n cos dec0 - m sin dec0, (l, y, sin dec_j) is the unit
+// direction of the component, so cos dec_j = sqrt(l^2 + y^2) = r and H_j - H0 = -atan2(l, y) has
+// sin = -l / r, cos = y / r (H = 0 at the pole, r = 0).  sd0, cd0 = sin dec0, cos dec0.
+__device__ inline void shapelet_frame(double l, double m, double sd0, double cd0, double F[9]) {
+  const double n = sqrt(1.0 - l * l - m * m);
+  const double sdj = m * cd0 + n * sd0, y = n * cd0 - m * sd0;
+  const double cdj = sqrt(l * l + y * y);
+  const double shj = cdj > 0.0 ? -l / cdj : 0.0, chj = cdj > 0.0 ? y / cdj : 1.0;
   double rj[9] = {shj, chj, 0.0, -sdj * chj, sdj * shj, cdj, cdj * chj, -cdj * shj, sdj};
   double r0[9] = {0.0, 1.0, 0.0, -sd0, 0.0, cd0, cd0, 0.0, sd0};
   for (int a = 0; a < 3; ++a)
