@@ -216,7 +216,34 @@ __host__ __device__ inline K4USmem k4u_layout(int f_cnt) {
   return L;
 }
 
-__global__ void __launch_bounds__(K4_WARPS * 32) k4_grad_pg_u(const K4Args a) {
+// The channel sums of one (component, row): s0 = sum Re z, s1 = sum log2(nu/nu0) Re z,
+// s2 = sum (nu/c) Im z, s3 = sum (nu/c)^2 Re z with z = conj(W) V / S_ref.  GAUSS = false (a tile of
+// points only) leaves out the Gaussian envelope's exponent term and s3, which only Gaussians use.
+template <bool GAUSS>
+__device__ __forceinline__ void k4u_channels(int F, float th, float tl, float q, float alpha, float cj, float2 D,
+                                             const float2* nh, const float4* cc, const float2* myw, float& s0,
+                                             float& s1, float& s2, float& s3) {
+  for (int fb = 0; fb < F; fb += K4U_RS) {
+    float2 P = phasor_fast(reduce_turns(th, tl, nh[fb].x, nh[fb].y));
+    const int fe = min(fb + K4U_RS, F);
+    for (int f = fb; f < fe; ++f) {
+      const float4 c = cc[f];
+      const float2 W = myw[f];
+      // channel sums use the amplitude without the flux: dV/dS_ref = V / S_ref holds for S_ref = 0 too
+      const float e = fmaf(alpha, c.x, cj);
+      const float A = ex2_approx(GAUSS ? fmaf(-q, c.y, e) : e);
+      const float vr = A * P.x, vi = A * P.y;
+      const float zr = W.x * vr + W.y * vi, zi = W.x * vi - W.y * vr;  // z = conj(W) V
+      s0 += zr;
+      s1 = fmaf(c.x, zr, s1);
+      s2 = fmaf(c.z, zi, s2);
+      if (GAUSS) s3 = fmaf(c.w, zr, s3);
+      P = make_float2(P.x * D.x - P.y * D.y, P.x * D.y + P.y * D.x);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(K4_WARPS * 32, 3) k4_grad_pg_u(const K4Args a) {
   extern __shared__ __align__(16) unsigned char sm[];
   const int F = a.f_cnt;
   const K4USmem L = k4u_layout(F);
@@ -250,6 +277,7 @@ __global__ void __launch_bounds__(K4_WARPS * 32) k4_grad_pg_u(const K4Args a) {
   const int jc = c0 + (mine ? lane : 0);
   const PGRec& me = comps[mine ? lane : 0];
   const bool my_gauss = mine && jc >= a.n_point;
+  const bool tile_gauss = c0 + ncomp > a.n_point;  // the tile holds a Gaussian (uniform over the CTA)
   const double me_l = (double)me.lh + me.ll, me_m = (double)me.mh + me.ml, me_nm1 = (double)me.nh + me.nl;
   const double my_n = 1.0 + me_nm1;
   const float my_ln = (float)(me_l / my_n), my_mn = (float)(me_m / my_n);
@@ -304,22 +332,10 @@ __global__ void __launch_bounds__(K4_WARPS * 32) k4_grad_pg_u(const K4Args a) {
       }
       const float2 D = phasor_accurate(reduce_turns(th, tl, a.dnu_h, a.dnu_l));
       float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-      for (int fb = 0; fb < F; fb += K4U_RS) {
-        float2 P = phasor_fast(reduce_turns(th, tl, nh[fb].x, nh[fb].y));
-        const int fe = min(fb + K4U_RS, F);
-        for (int f = fb; f < fe; ++f) {
-          const float4 c = cc[f];
-          const float2 W = myw[f];
-          // channel sums use the amplitude without the flux: dV/dS_ref = V / S_ref holds for S_ref = 0 too
-          const float A = ex2_approx(fmaf(-q, c.y, fmaf(my_alpha, c.x, my_cj)));
-          const float vr = A * P.x, vi = A * P.y;
-          const float zr = W.x * vr + W.y * vi, zi = W.x * vi - W.y * vr;  // z = conj(W) V
-          s0 += zr;
-          s1 = fmaf(c.x, zr, s1);
-          s2 = fmaf(c.z, zi, s2);
-          s3 = fmaf(c.w, zr, s3);
-          P = make_float2(P.x * D.x - P.y * D.y, P.x * D.y + P.y * D.x);
-        }
+      if (tile_gauss) {
+        k4u_channels<true>(F, th, tl, q, my_alpha, my_cj, D, nh, cc, myw, s0, s1, s2, s3);
+      } else {
+        k4u_channels<false>(F, th, tl, q, my_alpha, my_cj, D, nh, cc, myw, s0, s1, s2, s3);
       }
       // s1 holds sum log2(nu/nu0) Re z: ln(nu/nu_ref) = ln2 log2(nu/nu0) + ln(nu0/nu_ref)
       acc32[0] += -2.0f * s0;

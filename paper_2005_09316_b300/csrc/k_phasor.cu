@@ -392,14 +392,16 @@ static double k1_cost(long rows, int F, int log2L, int K, int waves) {
   return two ? c : 1.3 * c;
 }
 
-// Pick L in {8, 16, 32} and K in {4, 8, 12, 16} by the cost above (ties: the wider block).
-static K1Choice k1_choose(long rows, int F, int num_sms) {
+// Pick L in {8, 16, 32} and K in {4, 8, 12, 16} by the cost above (ties: the wider block).  The single
+// launch splits a partial last wave over component ranges (k1_phasor), so whole waves are not counted
+// (waves = 0) unless the model has a single component tile, which cannot be split.
+static K1Choice k1_choose(long rows, int F, int num_sms, bool splittable) {
   K1Choice best{5, 12};
   double best_c = -1.0;
   const int Ks[4] = {12, 16, 8, 4};
   for (int li = 5; li >= 3; --li)
     for (int K : Ks) {
-      const double c = k1_cost(rows, F, li, K, num_sms);
+      const double c = k1_cost(rows, F, li, K, splittable ? 0 : num_sms);
       if (best_c < 0 || c < best_c * 0.999) {
         best_c = c;
         best = {li, K};
@@ -424,7 +426,8 @@ size_t k1_part_bytes(int num_sms) { return (size_t)2 * num_sms * 2 * 16 * K1_THR
 
 int launch_phasor_mixed(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, int mode, const PeelArgs& pa,
                         cudaStream_t st) {
-  K1Choice ch = k1_choose(o.n_rows, o.n_chan, ctx->num_sms);
+  const int n_ct_all = (M->n_point + K1_CT - 1) / K1_CT + (M->n_gauss + K1_CT - 1) / K1_CT;
+  K1Choice ch = k1_choose(o.n_rows, o.n_chan, ctx->num_sms, n_ct_all >= 2);
   K1Args a;
   a.uvw = o.uvw;
   a.freq = o.freq;
