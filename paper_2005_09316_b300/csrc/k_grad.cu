@@ -465,6 +465,15 @@ __host__ __device__ inline int k4s_nblocks(int nmax) {
   return c;
 }
 
+// Folded triangle: row a (b = 0 .. n - a + 1) padded to an even length, so every row starts on a
+// 16-byte boundary and two (f, g) pairs load as one float4.  Row offset and total entries.
+__host__ __device__ inline int k4s_row_off(int nmax, int a) {
+  int o = 0;
+  for (int i = 0; i < a; ++i) o += (nmax - i + 2 + 1) & ~1;
+  return o;
+}
+__host__ __device__ inline int k4s_nfg(int nmax) { return k4s_row_off(nmax, nmax + 1); }
+
 // Shared-memory layout of k4_grad_shape (bytes): basis rows (a multiple of 4 floats with an odd count of
 // 16-byte quarters, so per-thread rows read as float4 without bank conflicts), folded coefficient pairs
 // (f, g) per triangle row a (b = 0..n-a+1), row offsets, tile weights, the FP64 coefficient-gradient
@@ -477,10 +486,10 @@ __host__ __device__ inline K4SSmem k4s_layout(int nmax, int nnz, int T) {
   K4SSmem s;
   s.ld = (nmax + 4 + 3) & ~3;  // entries 0 .. n + 3 (the blocks read up to n2 = 4J + 3)
   if (((s.ld >> 2) & 1) == 0) s.ld += 4;
-  const int nfg = (nmax + 1) * (nmax + 4) / 2;  // sum over a of (n - a + 2)
+  const int nfg = k4s_nfg(nmax);
   s.phx = 0;
   s.phy = s.phx + T * s.ld * 4;
-  s.fg = (s.phy + T * s.ld * 4 + 7) & ~7;
+  s.fg = (s.phy + T * s.ld * 4 + 15) & ~15;
   s.toff = s.fg + nfg * 8;
   s.wre = s.toff + (nmax + 2) * 4;
   s.wim = s.wre + T * 4;
@@ -509,8 +518,8 @@ __global__ void __launch_bounds__(K4S_T) k4_grad_shape(const K4SArgs a) {
   const double flux = *a.flux, beta1 = *a.beta1, beta2 = *a.beta2;
 
   // folded coefficients: row a holds (f_ab, g_ab) for b = 0..n-a+1 (f is zero past the triangle)
-  for (int aa = t; aa <= n + 1; aa += T) toff[aa] = aa * (n + 2) - aa * (aa - 1) / 2;
-  const int nfg = (n + 1) * (n + 4) / 2;
+  for (int aa = t; aa <= n + 1; aa += T) toff[aa] = k4s_row_off(n, aa);
+  const int nfg = k4s_nfg(n);
   for (int i = t; i < nfg; i += T) {
     fg[i] = make_float2(0.f, 0.f);
     accd[i] = 0.0;
@@ -584,15 +593,16 @@ __global__ void __launch_bounds__(K4S_T) k4_grad_shape(const K4SArgs a) {
       int b = 0;
       for (; b + 3 <= nb; b += 4) {
         const float4 p = *reinterpret_cast<const float4*>(py + b);
-        const float2 c0 = r[b], c1 = r[b + 1], c2 = r[b + 2], c3 = r[b + 3];
-        te = fmaf(c0.x, p.x, te);
-        ge = fmaf(c0.y, p.x, ge);
-        to = fmaf(c1.x, p.y, to);
-        go = fmaf(c1.y, p.y, go);
-        te = fmaf(c2.x, p.z, te);
-        ge = fmaf(c2.y, p.z, ge);
-        to = fmaf(c3.x, p.w, to);
-        go = fmaf(c3.y, p.w, go);
+        const float4 c01 = *reinterpret_cast<const float4*>(r + b);  // f_b, g_b, f_b+1, g_b+1
+        const float4 c23 = *reinterpret_cast<const float4*>(r + b + 2);
+        te = fmaf(c01.x, p.x, te);
+        ge = fmaf(c01.y, p.x, ge);
+        to = fmaf(c01.z, p.y, to);
+        go = fmaf(c01.w, p.y, go);
+        te = fmaf(c23.x, p.z, te);
+        ge = fmaf(c23.y, p.z, ge);
+        to = fmaf(c23.z, p.w, to);
+        go = fmaf(c23.w, p.w, go);
       }
       for (; b + 1 <= nb; b += 2) {
         const float2 c0 = r[b], c1 = r[b + 1];
