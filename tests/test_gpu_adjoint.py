@@ -78,6 +78,22 @@ def test_gradients_match_oracle(wn, ctx, seed, n_chan, uniform):
         assert rel(got[name], ref[name]) <= 2e-3, name
 
 
+@pytest.mark.parametrize("seed,nmaxs", [(51, (127,)), (52, (3, 80))])
+def test_gradients_match_oracle_high_orders(wn, ctx, seed, nmaxs):
+    """Shapelets up to n_max 127: the shapelet adjoint's largest shared-memory layout (64 threads per
+    CTA), coefficient-gradient blocks over the whole triangle, and two shapelets of very different
+    order in one model."""
+    obs, sky, gains, data, G, V = problem(seed, n_point=8, n_gauss=2, nmaxs=nmaxs)
+    W = np.conj(G) * (data - G * V)
+    ref = oracle.grad(obs.uvw.reshape(-1, 3), obs.freq, obs.dec0, sky, W)
+    got = gpu_grad(wn, ctx, obs, sky, gains, data)
+    npg = sky.n_point + sky.n_gauss
+    for name in ("flux", "alpha", "l", "m"):
+        assert rel(got[name][npg:], ref[name][npg:]) <= 2e-3, name + " (shapelet)"
+    for name in ("s_beta1", "s_beta2", "s_pa", "s_coeff"):
+        assert rel(got[name], ref[name]) <= 2e-3, name
+
+
 def test_autograd_function_matches_predict_grad(wn, ctx):
     from paper_2005_09316_b300.autograd import peel_loss
     obs, sky, gains, data, G, V = problem(44)
