@@ -165,6 +165,16 @@ WN_API int wn_sky_upload(wn_ctx* ctx, const wn_sky* sky, int* model_id, void* st
 WN_API int wn_sky_free(wn_ctx* ctx, int model_id);
 /* Bytes of device memory a resident model holds (admission accounting). */
 WN_API int wn_sky_bytes(wn_ctx* ctx, int model_id, size_t* bytes_out);
+/* The packed coefficient operand of shapelet q of a resident model, copied to HOST memory (no paper
+ * counterpart; for checking the packer).  It holds bf16 hi then lo, k_pad x n_pad each, in the tcgen05
+ * canonical K-major layout without swizzle: element (n, k) (n = 2 n2 + {0: Re, 1: Im} of
+ * C[n1, n2] (-i)^(n1+n2), k = n1) at ((k/8) (n_pad/8) + n/8) 64 + (n%8) 8 + k%8; hi = RN(float(value)),
+ * lo = RN(float(value) - hi).  k_pad and n_pad follow the highest order n1 + n2 the coefficients reach.
+ * host_out may be NULL to query k_pad and n_pad; otherwise it must hold bytes >= 4 k_pad n_pad.
+ * Synchronous.  WN_ENOTFOUND for an unknown model, WN_EINVAL for q outside [0, n_shape) or a short
+ * buffer. */
+WN_API int wn_sky_shapelet_operand(wn_ctx* ctx, int model_id, int q, void* host_out, size_t bytes, int* k_pad,
+                                   int* n_pad);
 
 /* ---- hot path ------------------------------------------------------------------------------ */
 

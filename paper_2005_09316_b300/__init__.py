@@ -29,7 +29,7 @@ EXPORTED = ("wn_create", "wn_destroy", "wn_last_error", "wn_version", "wn_set_pr
             "wn_predict_grad", "wn_predict_static", "wn_server_create", "wn_server_destroy", "wn_server_submit",
             "wn_server_poll", "wn_server_wait", "wn_server_copy", "wn_server_release", "wn_server_cancel",
             "wn_server_stats", "wn_calibrate", "wn_fit_shapelets", "wn_pipe_rates",
-            "wn_phasor_loop_rate")
+            "wn_phasor_loop_rate", "wn_sky_shapelet_operand")
 
 
 class WnError(RuntimeError):
@@ -83,6 +83,7 @@ def load(build_if_missing: bool = True):
         L.wn_sky_upload.argtypes = [P, ctypes.POINTER(WnSky), ctypes.POINTER(i), P]
         L.wn_sky_free.argtypes = [P, i]
         L.wn_sky_bytes.argtypes = [P, i, ctypes.POINTER(ctypes.c_size_t)]
+        L.wn_sky_shapelet_operand.argtypes = [P, i, i, P, ctypes.c_size_t, ctypes.POINTER(i), ctypes.POINTER(i)]
         L.wn_predict.argtypes = [P, ctypes.POINTER(WnObs), i, P, i, P]
         L.wn_predict_static.argtypes = [P, ctypes.POINTER(WnObs), i, P, i, P]
         L.wn_peel.argtypes = [P, ctypes.POINTER(WnObs), i, P, i, i, P, P, P]
@@ -223,6 +224,17 @@ class Model:
         v = ctypes.c_size_t()
         _check(load().wn_sky_bytes(self.ctx.h, self.id, ctypes.byref(v)))
         return int(v.value)
+
+    def shapelet_operand(self, q: int):
+        """Shapelet q's packed coefficient operand as raw bf16 bit patterns (uint16 hi, lo, each k_pad x n_pad
+        in the canonical K-major core-matrix order) with k_pad and n_pad."""
+        kp, npd = ctypes.c_int(), ctypes.c_int()
+        _check(load().wn_sky_shapelet_operand(self.ctx.h, self.id, q, None, 0, ctypes.byref(kp), ctypes.byref(npd)))
+        buf = np.empty(2 * kp.value * npd.value, dtype=np.uint16)
+        _check(load().wn_sky_shapelet_operand(self.ctx.h, self.id, q, buf.ctypes.data, buf.nbytes, ctypes.byref(kp),
+                                              ctypes.byref(npd)))
+        half = kp.value * npd.value
+        return buf[:half], buf[half:], kp.value, npd.value
 
     def free(self):
         if self.id:

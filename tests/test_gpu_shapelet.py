@@ -56,6 +56,28 @@ def test_single_shapelet_orders(wn, ctx, nmax):
     assert e_norm(got, ref) <= 2e-4, e_norm(got, ref)
 
 
+@pytest.mark.parametrize("seed,nmaxs,keep", [(5, (10,), None), (6, (80,), 1500), (7, (33, 3), 200), (8, (127,), None)])
+def test_packed_operand_bit_exact_with_the_oracle_packer(wn, ctx, seed, nmaxs, keep):
+    """The coefficient operand the device packs on upload equals the oracle's restatement of it
+    (parity split of C (-i)^(n1+n2), bf16 hi = RN(x), lo = RN(x - hi), zero padding), bit for bit, in the
+    documented core-matrix layout, sized by the highest order the coefficients reach."""
+    sky = shapelet_sky(seed, nmaxs, keep=keep)
+    m = ctx.upload(sky)
+    for q in range(sky.n_shape):
+        hi, lo, kp, npd = m.shapelet_operand(q)
+        o0, o1 = sky.s_off[q], sky.s_off[q + 1]
+        n1, n2, c = sky.s_n1[o0:o1], sky.s_n2[o0:o1], sky.s_coeff[o0:o1]
+        ne = int((n1 + n2).max())
+        assert kp >= ne + 1 and npd >= 2 * (ne + 1)
+        rh, rl = oracle.pack_coeff_bf16(ne, n1, n2, c, kp, npd)  # [n_pad][k_pad]
+        n = np.arange(npd)[:, None]
+        k = np.arange(kp)[None, :]
+        at = ((k >> 3) * (npd >> 3) + (n >> 3)) * 64 + (n & 7) * 8 + (k & 7)
+        assert np.array_equal(hi[at], rh), f"hi, shapelet {q}"
+        assert np.array_equal(lo[at], rl), f"lo, shapelet {q}"
+    m.free()
+
+
 @pytest.mark.parametrize("nmax", [5, 40, 80, 127])
 def test_lookup_table_basis_mode(wn, ctx, nmax):
     """Hermite functions interpolated from the 1-D table (spacing 1/256) instead of the recurrence: the
