@@ -143,6 +143,39 @@ def test_several_shapelets_with_points_fused_peel(wn, ctx):
     assert ctx.device_errors() == 0
 
 
+def _conj_pair(wn, ctx, obs, sky):
+    """V(uvw) and V(-uvw) on the GPU for one observation."""
+    d = wn.obs_to_device(obs)
+    dn = wn.obs_to_device(obs)
+    dn.uvw.neg_()
+    m = ctx.upload(sky)
+    v, vn = ctx.predict(d, m), ctx.predict(dn, m)
+    torch.cuda.synchronize()
+    m.free()
+    assert ctx.device_errors() == 0
+    return v, vn
+
+
+def test_hermitian_symmetry_all_component_types(wn, ctx):
+    """V(-u,-v,-w) = conj V(u,v,w) for points, Gaussians and shapelets (phi_n(-x) = (-1)^n phi_n(x), real
+    coefficients), negative fluxes included: a property the GPU path must keep at any size."""
+    obs = synth.make_obs(71, 12, 2, synth.uniform_channels(160e6, 250e3, 48), layout="mwa", max_baseline=3000.0)
+    sky = shapelet_sky(72, (20, 7), n_point=60, n_gauss=20)
+    sky.flux[::4] *= -1.0
+    v, vn = _conj_pair(wn, ctx, obs, sky)
+    scale = v.abs().max().item()
+    assert (vn - v.conj()).abs().max().item() <= 1e-5 * scale
+
+
+def test_hermitian_symmetry_fornax_full_size(wn, ctx):
+    """The same property over all 43.7 M visibilities of the 5 km observation with the two n_max 80
+    shapelets (tensor-core path), compared on the device, to 1e-4 of the peak (the path's tolerance is 1e-3)."""
+    obs, sky = synth.fornax()
+    v, vn = _conj_pair(wn, ctx, obs, sky)
+    scale = v.abs().max().item()
+    assert (vn - v.conj()).abs().max().item() <= 1e-4 * scale
+
+
 def test_fornax_full_size_sampled_rows(wn, ctx):
     """Two n_max = 80 shapelets (1,500 coefficients each) on the 5 km, 43.7 M-visibility observation."""
     obs, sky = synth.fornax()
