@@ -244,6 +244,46 @@ def test_split_tail_tiles_every_mode(wn, ctx, n_time, n_chan, uniform):
     m.free()
 
 
+def _sky_part(sky, idx_p, idx_g):
+    """The points idx_p and Gaussians idx_g (indices within their groups) of a point/Gaussian sky."""
+    P, G = sky.n_point, sky.n_gauss
+    sel = np.concatenate([np.asarray(idx_p, int), P + np.asarray(idx_g, int)])
+    z = np.zeros(0)
+    return synth.Sky(len(idx_p), len(idx_g), 0, sky.l[sel], sky.m[sel], sky.flux[sel], sky.alpha[sel], sky.nu_ref[sel],
+                     sky.g_maj[idx_g], sky.g_min[idx_g], sky.g_pa[idx_g], z, z, z, np.zeros(0, np.int32),
+                     np.zeros(1, np.int32), np.zeros(0, np.int32), np.zeros(0, np.int32), z)
+
+
+def test_mwa_full_size_properties(wn, ctx):
+    """Properties that hold at any size, over all 43.7 M visibilities and 25,000 components of the
+    bench's workload: V(-uvw) = conj V(uvw), and V of the whole sky = the sum of V of two disjoint halves
+    (every component tile, the split tail and the fixed-order sums included)."""
+    obs, sky = synth.mwa()
+    d = wn.obs_to_device(obs)
+    dn = wn.obs_to_device(obs)
+    dn.uvw.neg_()
+    m = ctx.upload(sky)
+    v = ctx.predict(d, m)
+    vn = ctx.predict(dn, m)
+    torch.cuda.synchronize()
+    scale = v.abs().max().item()
+    assert (vn - v.conj()).abs().max().item() <= 2e-6 * scale
+    del vn
+    m.free()
+    rng = np.random.default_rng(8)
+    pp, pg = rng.permutation(sky.n_point), rng.permutation(sky.n_gauss)
+    a = _sky_part(sky, np.sort(pp[:12000]), np.sort(pg[:2000]))
+    b = _sky_part(sky, np.sort(pp[12000:]), np.sort(pg[2000:]))
+    ma, mb = ctx.upload(a), ctx.upload(b)
+    va = ctx.predict(d, ma)
+    ctx.predict(d, mb, out=va, accumulate=True)
+    torch.cuda.synchronize()
+    assert (va - v).abs().max().item() <= 2e-6 * scale
+    assert ctx.device_errors() == 0
+    ma.free()
+    mb.free()
+
+
 def test_mwa_full_size_sampled_rows(wn, ctx):
     """The 43.7 M-visibility, 25,000-component workload in the bench's launch configuration, checked
     on sampled rows (all channels, all components) against the oracle."""
