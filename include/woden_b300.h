@@ -325,6 +325,13 @@ WN_API int wn_pipe_rates(wn_ctx* ctx, double* rates);
  * after one warm-up; allocates a small scratch buffer and synchronises its own stream. */
 WN_API int wn_phasor_loop_rate(wn_ctx* ctx, double* evals_per_s);
 
+/* The failure path of the kernels' bounded waits, without a fault (no paper counterpart).  A one-thread
+ * kernel waits on an mbarrier that nothing ever arrives at, through the same bounded-wait helper as the
+ * prediction kernels but with a limit of `seconds` (0 < seconds <= 5) instead of ~2 s; it gives up,
+ * raises WN_DEVERR_TIMEOUT in the context's device flags (wn_device_errors) and returns.  The context
+ * stays usable.  Synchronous (device-wide); WN_OK once the kernel has returned. */
+WN_API int wn_selftest_timeout(wn_ctx* ctx, double seconds);
+
 #ifdef __cplusplus
 }
 #endif

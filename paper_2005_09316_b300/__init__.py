@@ -29,7 +29,7 @@ EXPORTED = ("wn_create", "wn_destroy", "wn_last_error", "wn_version", "wn_set_pr
             "wn_predict_grad", "wn_predict_static", "wn_server_create", "wn_server_destroy", "wn_server_submit",
             "wn_server_poll", "wn_server_wait", "wn_server_copy", "wn_server_release", "wn_server_cancel",
             "wn_server_stats", "wn_calibrate", "wn_fit_shapelets", "wn_pipe_rates",
-            "wn_phasor_loop_rate", "wn_sky_shapelet_operand")
+            "wn_phasor_loop_rate", "wn_sky_shapelet_operand", "wn_selftest_timeout")
 
 
 class WnError(RuntimeError):
@@ -105,6 +105,7 @@ def load(build_if_missing: bool = True):
         L.wn_fit_shapelets.argtypes = [P, ctypes.POINTER(WnObs), i, P, i, i, P, i, dbl, P, ctypes.POINTER(dbl), P]
         L.wn_pipe_rates.argtypes = [P, ctypes.POINTER(dbl)]
         L.wn_phasor_loop_rate.argtypes = [P, ctypes.POINTER(dbl)]
+        L.wn_selftest_timeout.argtypes = [P, dbl]
         for name in EXPORTED:
             if name not in ("wn_destroy", "wn_last_error", "wn_version", "wn_server_destroy"):
                 getattr(L, name).restype = ctypes.c_int
@@ -307,6 +308,10 @@ class Context:
         r = (ctypes.c_double * 4)()
         _check(load().wn_pipe_rates(self.h, r))
         return {"ffma": r[0], "ffma2": r[1], "mufu_ex2": r[2], "dfma": r[3]}
+
+    def selftest_timeout(self, seconds: float = 0.5):
+        """Run a kernel whose bounded wait cannot complete; it must give up after `seconds` and flag it."""
+        _check(load().wn_selftest_timeout(self.h, float(seconds)))
 
     def phasor_loop_rate(self) -> float:
         """Evaluations per second the point/Gaussian kernel's channel loop sustains by itself."""

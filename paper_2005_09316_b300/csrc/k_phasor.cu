@@ -62,14 +62,7 @@ __host__ __device__ inline K1Smem k1_smem_layout(int log2L, int K) {
 }
 
 __device__ __forceinline__ bool bounded_wait(uint64_t* bar, uint32_t parity, unsigned* err) {
-  long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > (1ll << 32)) {  // ~2 s at the B300 clock: something is wrong
-      atomicOr(err, WN_DEVERR_TIMEOUT);
-      return false;
-    }
-  }
-  return true;
+  return mbar_wait_bounded(bar, parity, err);
 }
 
 // As k1_comp_uniform, for an arbitrary channel list: every channel's phase is reduced and evaluated.

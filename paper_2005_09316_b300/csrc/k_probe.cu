@@ -108,9 +108,41 @@ __global__ void __launch_bounds__(256, 2) kp_loop(float* out, int passes) {
   out[blockIdx.x * blockDim.x + tid] = s;
 }
 
+// The failure path of the kernels' bounded waits: one thread waits on an mbarrier that nothing ever
+// arrives at, with the given limit, using the same helper as the kernels.  It must give up, raise
+// WN_DEVERR_TIMEOUT and return; nothing faults and the context stays usable.
+__global__ void kp_wait_timeout(unsigned* err, long long limit) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    (void)mbar_wait_bounded(&bar, 0, err, limit);
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&bar)) : "memory");
+  }
+}
+
 }  // namespace wn
 
 using namespace wn;
+
+extern "C" int wn_selftest_timeout(wn_ctx* ctx, double seconds) {
+  if (!ctx) return set_error(WN_EINVAL, "NULL argument");
+  if (!(seconds > 0.0 && seconds <= 5.0)) return set_error(WN_EINVAL, "wn_selftest_timeout: seconds must be in (0, 5]");
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaError_t e = cudaSetDevice(ctx->device);
+  int khz = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, ctx->device);
+  const long long limit = (long long)(seconds * 1e3 * (double)(khz > 0 ? khz : 2032000));
+  if (e == cudaSuccess) {
+    kp_wait_timeout<<<1, 32>>>(ctx->d_err, limit);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaSetDevice(prev);
+  if (e != cudaSuccess) return set_error(WN_ECUDA, std::string("wait self-test: ") + cudaGetErrorString(e));
+  return WN_OK;
+}
 
 extern "C" int wn_phasor_loop_rate(wn_ctx* ctx, double* evals_per_s) {
   if (!ctx || !evals_per_s) return set_error(WN_EINVAL, "NULL argument");

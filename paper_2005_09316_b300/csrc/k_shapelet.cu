@@ -132,15 +132,7 @@ __device__ __forceinline__ void tmem_wait16(uint32_t* r) {
 }
 
 __device__ __forceinline__ bool k2_wait(uint64_t* bar, uint32_t parity, unsigned* err) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const long long t0 = clock64();
-  for (uint32_t i = 1;; ++i) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 63) == 0 && clock64() - t0 > (1ll << 32)) {  // ~2 s: something is wrong
-      atomicOr(err, WN_DEVERR_TIMEOUT);
-      return false;
-    }
-  }
+  return mbar_wait_bounded(bar, parity, err);
 }
 
 // Offset in bytes of element (row, k) in a canonical K-major no-swizzle tile with `rows` rows.

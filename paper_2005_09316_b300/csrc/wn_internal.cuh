@@ -297,13 +297,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait: gives up after ~2^26 polls (each try_wait itself blocks for a hardware-defined
-// interval), raises WN_DEVERR_TIMEOUT and returns false so the kernel can wind down.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned* err) {
-  for (uint32_t it = 0; it < (1u << 26); ++it)
+// Bounded wait on an mbarrier phase: gives up after `limit` SM clocks (the kernels use kWaitLimit,
+// ~2 s at the B300 clock, far beyond any legitimate wait), raises WN_DEVERR_TIMEOUT and returns false
+// so the caller can wind down (drain its own copies and commits, free what it holds, return).
+constexpr long long kWaitLimit = 1ll << 32;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, unsigned* err,
+                                                  long long limit = kWaitLimit) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  for (uint32_t i = 1;; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
-  if (err) atomicOr(err, WN_DEVERR_TIMEOUT);
-  return false;
+    if ((i & 63) == 0 && clock64() - t0 > limit) {
+      if (err) atomicOr(err, WN_DEVERR_TIMEOUT);
+      return false;
+    }
+  }
 }
 
 // One-dimensional TMA bulk copy global -> shared, completing on an mbarrier (bytes multiple of 16,

@@ -55,3 +55,33 @@ def test_phasor_loop_rate_bounds_the_kernel():
     assert kernel <= 1.05 * loop, (kernel, loop)
     assert loop < ffma / 6.0, (loop, ffma)
     assert np.isfinite(kernel)
+
+
+def test_bounded_wait_gives_up_flags_and_leaves_the_context_usable():
+    """The kernels' bounded-wait helper on an mbarrier nothing arrives at, with a 0.3 s limit: the kernel
+    returns after about that long, the context reports WN_DEVERR_TIMEOUT (and clears it on reading), and a
+    prediction afterwards still matches the oracle."""
+    import time
+
+    import numpy as np
+
+    import oracle
+    import paper_2005_09316_b300 as wn
+    import synth
+    ctx = wn.Context(0)
+    assert ctx.device_errors() == 0
+    t0 = time.perf_counter()
+    ctx.selftest_timeout(0.3)
+    dt = time.perf_counter() - t0
+    assert ctx.device_errors() & wn.WN_DEVERR_TIMEOUT
+    assert ctx.device_errors() == 0
+    assert 0.2 < dt < 5.0, dt
+    obs, sky = synth.tiny(3)
+    d = wn.obs_to_device(obs)
+    m = ctx.upload(sky)
+    v = ctx.predict(d, m).cpu().numpy().reshape(obs.n_rows, obs.n_chan)
+    ref = oracle.predict(obs.uvw.reshape(-1, 3), obs.freq, obs.dec0, sky)
+    assert np.abs(v - ref).max() <= 2e-4 * np.abs(ref).max()
+    assert ctx.device_errors() == 0
+    m.free()
+    ctx.close()
