@@ -124,6 +124,47 @@ __device__ __forceinline__ void k7_diag_col(float (&row)[32], float* dinv, int l
   if constexpr (C + 1 < 32) k7_diag_col<C + 1>(row, dinv, lane, n_here, s_bad);
 }
 
+// Factor diagonal tile K in place (warp-wide): lane r holds row r, columns by shuffle; 1 / L_kk to dinv.
+__device__ __forceinline__ void k7_factor_diag(float* T, int K, float* dinv, int lane, int n, int* s_bad) {
+  float* D = k7_tile(T, K, K);
+  float row[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) row[c] = D[lane * K7_TS + c];
+  k7_diag_col<0>(row, dinv + K * 32, lane, n - K * 32, s_bad);
+#pragma unroll
+  for (int c = 0; c < 32; ++c) D[lane * K7_TS + c] = row[c];
+}
+
+// Trailing update of tile (K + 1 + I, K + 1 + J) by step K's panel: A -= L_IK L_JK^T.  A warp per tile,
+// each lane 8 rows x 4 columns.
+__device__ __forceinline__ void k7_trail_tile(float* T, int K, int I, int J, int lane) {
+  const int rg = lane >> 3, cg = lane & 7;
+  const float* PI = k7_tile(T, K + 1 + I, K);
+  const float* PJ = k7_tile(T, K + 1 + J, K);
+  float* C = k7_tile(T, K + 1 + I, K + 1 + J);
+  float acc[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+#pragma unroll 4
+  for (int k = 0; k < 32; ++k) {
+    float av[8], bv[4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) av[i] = PI[(rg * 8 + i) * K7_TS + k];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) bv[j] = PJ[(cg * 4 + j) * K7_TS + k];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) C[(rg * 8 + i) * K7_TS + cg * 4 + j] -= acc[i][j];
+}
+
 __global__ void __launch_bounds__(K7_THREADS, 1) k7_calib(const K7Args a) {
   extern __shared__ __align__(16) unsigned char sm[];
   const int A = a.n_ant, n = 2 * A - 1;
@@ -214,18 +255,12 @@ __global__ void __launch_bounds__(K7_THREADS, 1) k7_calib(const K7Args a) {
       }
     }
     // --- tiled right-looking Cholesky of the augmented matrix; row n becomes L^{-1} (A^T b).  Pivots of
-    // row n and of the padding rows are not part of the system and are only kept positive.
+    // row n and of the padding rows are not part of the system and are only kept positive.  Look-ahead:
+    // while warps 1.. apply step K's trailing update, warp 0 updates the next diagonal tile first and
+    // factors it, so no phase runs the diagonal factorisation alone.
+    __syncthreads();
+    if (warp == 0) k7_factor_diag(T, 0, dinv, lane, n, &s_bad);
     for (int K = 0; K < NT; ++K) {
-      __syncthreads();
-      if (warp == 0) {  // diagonal tile, unblocked, in registers: lane r holds row r, columns by shuffle
-        float* D = k7_tile(T, K, K);
-        float row[32];
-#pragma unroll
-        for (int c = 0; c < 32; ++c) row[c] = D[lane * K7_TS + c];
-        k7_diag_col<0>(row, dinv + K * 32, lane, n - K * 32, &s_bad);
-#pragma unroll
-        for (int c = 0; c < 32; ++c) D[lane * K7_TS + c] = row[c];
-      }
       __syncthreads();
       // panel: X L_KK^T = A_IK for the tiles below; lane r solves row r of one tile, column by column
       for (int I = K + 1 + warp; I < NT; I += K7_WARPS) {
@@ -244,70 +279,48 @@ __global__ void __launch_bounds__(K7_THREADS, 1) k7_calib(const K7Args a) {
         for (int c = 0; c < 32; ++c) P[lane * K7_TS + c] = xr[c];
       }
       __syncthreads();
-      // trailing update A_IJ -= L_IK L_JK^T, K < J <= I; a warp per tile, lane = 8 rows x 4 columns
+      // trailing update A_IJ -= L_IK L_JK^T, K < J <= I: tile q = 0 is the next diagonal tile (warp 0,
+      // which then factors it); the others go to warps 1.. in turn
       const int m = NT - K - 1;
-      const int rg = lane >> 3, cg = lane & 7;
-      for (int q = warp; q < m * (m + 1) / 2; q += K7_WARPS) {
-        int I = 0;
-        while ((I + 1) * (I + 2) / 2 <= q) ++I;
-        const int J = q - I * (I + 1) / 2;
-        const float* PI = k7_tile(T, K + 1 + I, K);
-        const float* PJ = k7_tile(T, K + 1 + J, K);
-        float* C = k7_tile(T, K + 1 + I, K + 1 + J);
-        float acc[8][4];
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-#pragma unroll 4
-        for (int k = 0; k < 32; ++k) {
-          float av[8], bv[4];
-#pragma unroll
-          for (int i = 0; i < 8; ++i) av[i] = PI[(rg * 8 + i) * K7_TS + k];
-#pragma unroll
-          for (int j = 0; j < 4; ++j) bv[j] = PJ[(cg * 4 + j) * K7_TS + k];
-#pragma unroll
-          for (int i = 0; i < 8; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+      if (warp == 0) {
+        if (m > 0) {
+          k7_trail_tile(T, K, 0, 0, lane);
+          __syncwarp();
+          k7_factor_diag(T, K + 1, dinv, lane, n, &s_bad);
         }
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) C[(rg * 8 + i) * K7_TS + cg * 4 + j] -= acc[i][j];
+      } else {
+        for (int q = warp; q < m * (m + 1) / 2; q += K7_WARPS - 1) {
+          int I = 0;
+          while ((I + 1) * (I + 2) / 2 <= q) ++I;
+          k7_trail_tile(T, K, I, q - I * (I + 1) / 2, lane);
+        }
       }
     }
     __syncthreads();
-    // --- back substitution L^T x = y (warp 0), column by column: x_k = y_k / L_kk, then y_j -= L_kj x_k
-    // for j < k along row k of L (contiguous in its tiles).  Lane l keeps y_j, j = 32 m + l, in register
-    // xs[m]; tile rows are unrolled so every register index is a constant.
-    if (warp == 0) {
-      float xs[8];
-#pragma unroll
-      for (int m = 0; m < 8; ++m) {
-        const int j = 32 * m + lane;
-        xs[m] = (m < NT && j < n) ? *k7_elem(T, n, j) : 0.f;
-      }
-#pragma unroll
-      for (int R = 7; R >= 0; --R) {
-        if (R >= NT) continue;
+    // --- back substitution L^T x = y, by tile rows R = NT-1 .. 0: warp 0 solves the diagonal block
+    // (x_k = y_k / L_kk, then y_j -= L_kj x_k for j < k in the block), then warp J subtracts L_RJ^T x_R
+    // from y_J for every J < R.  x holds y, and becomes x block by block.
+    for (int j = tid; j < NT * 32; j += K7_THREADS) x[j] = j < n ? *k7_elem(T, n, j) : 0.f;
+    for (int R = NT - 1; R >= 0; --R) {
+      __syncthreads();
+      if (warp == 0) {
+        const float* D = k7_tile(T, R, R);
+        float yv = x[32 * R + lane];
         for (int c = 31; c >= 0; --c) {
           const int k = 32 * R + c;
-          if (k >= n) continue;
-          const float xk = __shfl_sync(0xffffffffu, xs[R], c) * dinv[k];
-          const float* rowk = T + (R * (R + 1) / 2) * K7_TILE + c * K7_TS;  // tile (R, 0), row c
-#pragma unroll
-          for (int m = 0; m < 8; ++m) {
-            if (m > R) continue;
-            if (32 * m + lane < k) xs[m] -= rowk[m * K7_TILE + lane] * xk;
-          }
-          if (lane == c) xs[R] = xk;
+          const float xk = k < n ? __shfl_sync(0xffffffffu, yv, c) * dinv[k] : 0.f;
+          if (lane == c) yv = xk;
+          else if (lane < c) yv -= D[c * K7_TS + lane] * xk;  // L_{k, 32R + lane}
         }
+        x[32 * R + lane] = yv;
       }
-#pragma unroll
-      for (int m = 0; m < 8; ++m) {
-        const int j = 32 * m + lane;
-        if (m < NT && j < n) x[j] = xs[m];
+      __syncthreads();
+      for (int J = warp; J < R; J += K7_WARPS) {
+        const float* P = k7_tile(T, R, J);
+        float sum = 0.f;
+#pragma unroll 8
+        for (int c = 0; c < 32; ++c) sum = fmaf(P[c * K7_TS + lane], x[32 * R + c], sum);  // L_{32R+c, 32J+lane}
+        x[32 * J + lane] -= sum;
       }
     }
     __syncthreads();
