@@ -31,10 +31,10 @@ import synth  # noqa: E402
 METRIC = "comp-vis evals/s (mixed vs FP64 GPU) at stated error; % roofline; p50/p99"
 UNIT = "comp-vis evals/s"
 WORKLOAD = "mwa_phase1_predict_peel: 128 tiles (8128 baselines) x 14 steps x 384 ch, 20000 P + 5000 G"
-# Algorithmic FP32-pipe operations per component-visibility evaluation of the phasor sum:
-# one complex rotation of the phasor to the next channel (2 FMUL + 2 FFMA) and one complex
-# accumulate of amplitude x phasor (2 FFMA).
-OPS_PER_EVAL = 6
+# Algorithmic FP32-pipe operations per component-visibility evaluation of the phasor sum: one step
+# of the three-term phasor recurrence across channels (1 FFMA for each of the real and imaginary
+# parts) and one complex accumulate of amplitude x phasor (2 FFMA).
+OPS_PER_EVAL = 4
 FP32_LANES_PER_SM = 128
 
 

@@ -197,8 +197,11 @@ __device__ __forceinline__ void k1_tile(const K1Args& a, const int bx, const int
     wg[k] = (float)(kGaussE * kLog2e) * x * x;
     if (!UNIFORM) split_double(nu * (1.0 / kC), ah[k], al[k]);
   }
+  // nu / c of the start channel: the lane's first (channel lists) or middle (uniform, k1_mid) channel
   float a0h, a0l;
-  split_double(a.freq[min(f0, a.n_chan - 1)] * (1.0 / kC), a0h, a0l);
+  split_double(a.freq[min(f0, a.n_chan - 1)] * (1.0 / kC) +
+                   (UNIFORM ? k1_mid(K) * ((double)a.dnu_h + (double)a.dnu_l) : 0.0),
+               a0h, a0l);
   const double L0 = log2(a.nu0);
 
   float2 Vre[K], Vim[K];
@@ -300,6 +303,10 @@ __device__ __forceinline__ void k1_tile(const K1Args& a, const int bx, const int
   for (int k = 0; k < K; ++k) {
     Vre[k] = __fadd2_rn(acc[k * K1_THREADS], Vre[k]);
     Vim[k] = __fadd2_rn(acc[(K + k) * K1_THREADS], Vim[k]);
+    if (UNIFORM && k1_neg(K, k)) {  // the uniform loop's signed sums (k1_comp_uniform)
+      Vre[k] = make_float2(-Vre[k].x, -Vre[k].y);
+      Vim[k] = make_float2(-Vim[k].x, -Vim[k].y);
+    }
   }
   if (part) {
     const float2 nan2 = make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));

@@ -3,7 +3,8 @@
 Tolerances: the mixed-precision path (FP64 phase argument, FP32 phasors and sums) must reach
 e_norm <= 1e-5 (normwise, relative to max |V|); the all-FP64 form is limited by the final
 complex64 rounding of its output, e_norm <= 1e-6.  Element-wise errors (e_elem, over visibilities
-above 1e-3 of the peak) are held to 1e-4 and 1e-6 respectively.
+above 1e-3 of the peak) are held to 1e-4 and 1e-6 respectively on the tiny sky, and to 3e-4 for the
+mixed path where lanes run 16 channels.
 """
 import numpy as np
 import pytest
@@ -83,9 +84,11 @@ def test_tiles_and_ragged_tails(wn, ctx, n_chan, uniform):
     got = run_predict(wn, ctx, obs, sky, 0)
     ref = oracle_rows(obs, sky, np.arange(obs.n_rows))
     assert e_norm(got, ref) <= 1e-5
-    # e_elem is reported beside the e_norm target; lanes of 16 channels (chosen for 512) advance the
-    # phasor 15 steps, which shows on the smallest elements (1e-3 of the maximum)
-    assert e_elem(got, ref) <= 2e-4
+    # e_elem is reported beside the e_norm target.  Lanes of 16 channels (chosen for 400 and 512) run the
+    # three-term phasor recurrence up to 8 steps from their start channel; its rounding error grows like
+    # steps^2 / 2 ulp where the phasor barely turns, which shows on the smallest elements (1e-3 of the
+    # maximum) as a few 1e-4 of their size
+    assert e_elem(got, ref) <= 3e-4
 
 
 def test_negative_and_zero_flux_and_edge_positions(wn, ctx):
