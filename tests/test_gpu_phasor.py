@@ -91,6 +91,35 @@ def test_tiles_and_ragged_tails(wn, ctx, n_chan, uniform):
     assert e_elem(got, ref) <= 3e-4
 
 
+@pytest.mark.parametrize("n_chan", [384, 512])
+def test_phase_step_near_zero_and_half_turn(wn, ctx, n_chan):
+    """The phasor recurrence across uniform channels is least accurate where the per-channel phase step
+    delta is near 0 or a half turn (2 cos delta near +-2): its rounding then adds up coherently over the
+    steps from a lane's start channel.  Rows are placed so that every component sees such a step (tau
+    dnu / c within 1e-4 turn of 0, 1/2 or 1), and a sky of co-located components makes the errors of
+    all terms add up in the same direction.  Lanes run 12 channels (384) and 16 (512)."""
+    dnu, c = 100e3, 299792458.0
+    freq = synth.uniform_channels(150e6, dnu, n_chan)
+    rng = np.random.default_rng(n_chan)
+    turns = np.array([0.0, 0.5, 1.0, 0.5, 0.0, 1.0, 0.5, 0.0])
+    l0 = 0.3
+    n_rows = 28
+    targets = np.resize(turns, n_rows) + rng.uniform(-1e-4, 1e-4, n_rows)
+    uvw = np.zeros((1, n_rows, 3))
+    uvw[0, :, 0] = targets * c / dnu / l0           # tau = u l0 on these rows (m = 0, w = 0)
+    uvw[0, :, 1] = rng.uniform(-0.5, 0.5, n_rows)   # a small v: components spread in m by < 1e-3
+    ant1, ant2 = synth.baselines(8)
+    obs = synth.Obs(n_ant=8, n_time=1, n_chan=n_chan, uvw=uvw, freq=freq, ant1=ant1, ant2=ant2, dec0=-0.47)
+    sky = synth.make_sky(n_chan + 3, 60, 20, 0)
+    sky.l[:] = l0 + rng.uniform(-1e-7, 1e-7, sky.l.size)
+    sky.m[:] = rng.uniform(-1e-3, 1e-3, sky.m.size)
+    sky.flux[:] = np.abs(sky.flux)
+    got = run_predict(wn, ctx, obs, sky, 0)
+    ref = oracle_rows(obs, sky, np.arange(obs.n_rows))
+    assert e_norm(got, ref) <= 1e-5, e_norm(got, ref)
+    assert e_elem(got, ref) <= 3e-4, e_elem(got, ref)
+
+
 def test_negative_and_zero_flux_and_edge_positions(wn, ctx):
     obs = small_obs(5, 10, 2, synth.uniform_channels(160e6, 1e6, 24), layout="disc", diameter=2000.0)
     sky = synth.make_sky(6, 40, 20, 0, fov=60 * synth.DEG)
