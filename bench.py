@@ -488,12 +488,20 @@ def bench_serving(wn, ctx, local, torch, n_req=1000, n_templates=48, seed=17):
         m.free()
     total_evals = sum(r[0].n_vis * r[1].n_comp for r in reqs)
     lat = latency_summary(results)
+    # p99 by request class (service time alone below / at or above 20 ms): large requests start least
+    # work first, which shortens the wait of all but the largest and lengthens theirs
+    svc_a, lat_a, ser_a = np.array(svc), np.array([r.latency for r in results]), np.array(lat_serial)
+    by_class = {}
+    for name, sel in (("below_20ms", svc_a < 0.02), ("20ms_and_above", svc_a >= 0.02)):
+        by_class[name] = {"n": int(sel.sum()), "p99_ms": round(1e3 * float(np.percentile(lat_a[sel], 99)), 3),
+                          "one_at_a_time_p99_ms": round(1e3 * float(np.percentile(ser_a[sel], 99)), 3)}
     return {"workload": f"serving: {n_req} Poisson requests drawn from {n_templates} uneven request sets "
                         "(16-128 tiles, 1-14 steps, 32-384 ch, 100-50000 P/G + 0-3 shapelets n_max 10-80)",
             "rate_hz": round(rate, 2), "mean_service_ms": round(1e3 * mean_s, 3),
             "p50_ms": round(lat["p50_ms"], 3), "p99_ms": round(lat["p99_ms"], 3),
             "one_at_a_time_p50_ms": round(1e3 * float(np.percentile(lat_serial, 50)), 3),
             "one_at_a_time_p99_ms": round(1e3 * float(np.percentile(lat_serial, 99)), 3),
+            "p99_by_class": by_class,
             "service_alone_p50_ms": round(1e3 * float(np.percentile(svc, 50)), 3),
             "service_alone_p99_ms": round(1e3 * float(np.percentile(svc, 99)), 3),
             "throughput_evals_per_s": total_evals / wall, "wall_s": round(wall, 3),

@@ -36,10 +36,15 @@ enum ReqState { RQ_PENDING = 0, RQ_ADMITTED = 1, RQ_RUNNING = 2, RQ_DONE = 3, RQ
 
 constexpr double kBatchBudget = 0.02;   // seconds of estimated GPU work per batch / chunk
 // Large requests in flight at once.  They share the GPU with each other and with the small batches, so
-// more of them at once stretches every one of them; with two, the large requests (which set p99) queue
-// in arrival order, and the small ones keep the remaining streams (measured on the serving bench: p50
-// 6.6 against 8.2 ms, p99 685 against 710 ms, with five).
-constexpr int kMaxLargeInFlight = 2;
+// more of them at once stretches every one of them.  One at a time, started least work first (below),
+// the queue of large requests drains fastest for all but the largest; the small ones keep the remaining
+// streams (measured on the serving bench: p99 372-495 ms with one, 492-536 ms with two, 600-620 ms
+// with two in arrival order).
+constexpr int kMaxLargeInFlight = 1;
+// Large requests start in order of estimated work, least first, which keeps a burst of them from
+// holding back the many mid-sized ones behind the few largest; a request that has waited this long
+// since submission starts before any younger one, so the largest are passed over for a bounded time.
+constexpr double kMaxLargeWait = 1.0;
 constexpr double kEvalRate = 3.0e12;    // component-visibility evaluations per second (estimate)
 constexpr double kTileEvals = 2.4e7;    // evaluations per CTA tile of a large request (~2 ms on one CTA)
 
@@ -184,7 +189,8 @@ static int add_tiles(ServeReq& r, int slot_req, long from, long to, K1Work* work
   return nwork;
 }
 
-static bool is_large(const ServeReq& r) { return r.tiles > 0 && r.tile_cost * r.tiles * r.n_cc > kBatchBudget; }
+static double large_cost(const ServeReq& r) { return r.tile_cost * r.tiles * r.n_cc; }
+static bool is_large(const ServeReq& r) { return r.tiles > 0 && large_cost(r) > kBatchBudget; }
 
 // Kernel arguments of component range c of a request: the point/Gaussian table is points then
 // Gaussians, so a range is a contiguous slice with its own point / Gaussian counts.
@@ -278,13 +284,26 @@ static bool launch_ready(wn_server* s) {
   const int ns = (int)s->slots.size();
   int owners = 0;
   for (auto& sl : s->slots) owners += sl.owner ? 1 : 0;
-  for (auto& kv : s->reqs) {
-    ServeReq& r = kv.second;
-    if (!unstarted(r) || !is_large(r)) continue;
-    if (owners >= std::min(kMaxLargeInFlight, std::max(1, ns - 1))) break;
+  const double t_now = now_s(s);
+  while (owners < std::min(kMaxLargeInFlight, std::max(1, ns - 1))) {
     int k = ns - 1;
     while (k >= 0 && (s->slots[k].busy || s->slots[k].owner)) --k;
     if (k < 0) break;
+    // the oldest request past the wait limit, else the least estimated work (ties: ticket order)
+    ServeReq* pick = nullptr;
+    bool pick_old = false;
+    for (auto& kv : s->reqs) {
+      ServeReq& q = kv.second;
+      if (!unstarted(q) || !is_large(q)) continue;
+      const bool old = t_now - q.t_submit > kMaxLargeWait;
+      if (pick_old && !old) continue;
+      if (!pick || (old && !pick_old) || (!old && large_cost(q) < large_cost(*pick))) {
+        pick = &q;
+        pick_old = old;
+      }
+    }
+    if (!pick) break;
+    ServeReq& r = *pick;
     r.owner_slot = k;
     r.t_launch = now_s(s);
     s->slots[k].owner = r.ticket;

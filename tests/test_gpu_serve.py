@@ -174,3 +174,28 @@ def test_large_request_in_component_ranges(wn, ctx, peel):
     assert e_norm(got, ref) <= 1e-5
     assert ctx.device_errors() == 0
     m.free()
+
+
+def test_large_requests_start_least_work_first(wn, ctx):
+    """Queued large requests start in order of estimated work, least first (one at a time here): with a
+    large request running, a larger one and then a smaller one are submitted; the smaller starts first.
+    Each result still matches the single call."""
+    from paper_2005_09316_b300.serve import Server
+    obs = synth.make_obs(81, 128, 4, synth.uniform_channels(167e6, 80e3, 384), layout="mwa")
+    d = wn.obs_to_device(obs)
+    models = [ctx.upload(synth.make_sky(82 + i, n * 4 // 5, n // 5, 0, fov=15 * synth.DEG))
+              for i, n in enumerate((20000, 20000, 8000))]
+    srv = Server(ctx, n_streams=2, pool_bytes=1 << 30, max_inflight=4, max_rows=obs.n_rows, max_chan=384)
+    tickets = [srv.submit(d, m) for m in models]   # running, then larger, then smaller
+    res = [srv.wait(t, 120) for t in tickets]
+    assert all(r.state == 3 for r in res)
+    got = [srv.result_tensor(t, d).cpu().numpy() for t in tickets]
+    for t in tickets:
+        srv.release(t)
+    srv.close()
+    assert res[2].t_launch < res[1].t_launch, [(r.t_submit, r.t_launch) for r in res]
+    for g, m in zip(got, models):
+        assert e_norm(g, ctx.predict(d, m).cpu().numpy()) <= 1e-5
+    assert ctx.device_errors() == 0
+    for m in models:
+        m.free()
