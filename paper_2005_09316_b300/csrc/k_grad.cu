@@ -476,25 +476,29 @@ __host__ __device__ inline int k4s_nfg(int nmax) { return k4s_row_off(nmax, nmax
 
 // Shared-memory layout of k4_grad_shape (bytes): basis rows (a multiple of 4 floats with an odd count of
 // 16-byte quarters, so per-thread rows read as float4 without bank conflicts), folded coefficient pairs
-// (f, g) per triangle row a (b = 0..n-a+1), row offsets, tile weights, the FP64 coefficient-gradient
-// sums over the same folded triangle, and the list of (n1, n2) blocks.
+// (f, g) per triangle row a (b = 0..n-a+1), row offsets, tile weights (Re, Im) Y, the FP64
+// coefficient-gradient sums over the same folded triangle, and the list of (n1, n2) blocks.  When every
+// thread owns at most one block (k4s_nblocks(n) <= T) the sums stay in its registers and accd is empty;
+// at the end the basis rows' area holds them and the scalar reduction.
 struct K4SSmem {
-  int ld, phx, phy, fg, toff, wre, wim, accd, blocks, total;
+  int ld, phx, phy, fg, toff, w, accd, blocks, total;
 };
+__host__ __device__ inline bool k4s_reg_acc(int nmax, int T) { return k4s_nblocks(nmax) <= T; }
 __host__ __device__ inline K4SSmem k4s_layout(int nmax, int nnz, int T) {
   (void)nnz;
   K4SSmem s;
-  s.ld = (nmax + 4 + 3) & ~3;  // entries 0 .. n + 3 (the blocks read up to n2 = 4J + 3)
+  // entries 0 .. n + 3 (the blocks read up to n2 = 4J + 3); at least 20, so that one thread's row of the
+  // second area holds its K4S_NS doubles of the final reduction
+  s.ld = max((nmax + 4 + 3) & ~3, 20);
   if (((s.ld >> 2) & 1) == 0) s.ld += 4;
   const int nfg = k4s_nfg(nmax);
   s.phx = 0;
   s.phy = s.phx + T * s.ld * 4;
   s.fg = (s.phy + T * s.ld * 4 + 15) & ~15;
   s.toff = s.fg + nfg * 8;
-  s.wre = s.toff + (nmax + 2) * 4;
-  s.wim = s.wre + T * 4;
-  s.accd = (s.wim + T * 4 + 7) & ~7;
-  s.blocks = s.accd + nfg * 8;
+  s.w = (s.toff + (nmax + 2) * 4 + 7) & ~7;
+  s.accd = s.w + T * 8;
+  s.blocks = s.accd + (k4s_reg_acc(nmax, T) ? 0 : nfg * 8);
   s.total = s.blocks + k4s_nblocks(nmax) * 4;
   return s;
 }
@@ -509,11 +513,13 @@ __global__ void __launch_bounds__(K4S_T) k4_grad_shape(const K4SArgs a) {
   float* phy = reinterpret_cast<float*>(sm + lay.phy);
   float2* fg = reinterpret_cast<float2*>(sm + lay.fg);
   int* toff = reinterpret_cast<int*>(sm + lay.toff);
-  float* wre = reinterpret_cast<float*>(sm + lay.wre);
-  float* wim = reinterpret_cast<float*>(sm + lay.wim);
-  double* accd = reinterpret_cast<double*>(sm + lay.accd);  // [folded triangle] coefficient-gradient sums
+  float2* wy = reinterpret_cast<float2*>(sm + lay.w);
+  const bool reg_acc = k4s_reg_acc(n, T);
+  // [folded triangle] coefficient-gradient sums: in shared memory, or (reg_acc) in registers until the end
+  double* accd = reinterpret_cast<double*>(sm + (reg_acc ? lay.phx : lay.accd));
   ushort2* blocks = reinterpret_cast<ushort2*>(sm + lay.blocks);
   const int nblk = k4s_nblocks(n);
+  double accr[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};  // reg_acc: this thread's block
   const int t = threadIdx.x;
   const double flux = *a.flux, beta1 = *a.beta1, beta2 = *a.beta2;
 
@@ -522,7 +528,7 @@ __global__ void __launch_bounds__(K4S_T) k4_grad_shape(const K4SArgs a) {
   const int nfg = k4s_nfg(n);
   for (int i = t; i < nfg; i += T) {
     fg[i] = make_float2(0.f, 0.f);
-    accd[i] = 0.0;
+    if (!reg_acc) accd[i] = 0.0;
   }
   if (t == 0) {  // (2I, 4J) blocks of the triangle, J outer
     int c = 0;
@@ -579,8 +585,7 @@ __global__ void __launch_bounds__(K4S_T) k4_grad_shape(const K4SArgs a) {
     // flux derivative); contributions are -2 S_ref Re(Y * dxi)
     const float S = valid ? ex2_approx(fmaf(a.alpha, ci.z, a.c_amp)) : 0.f;
     const float yr = S * (W.x * P.x + W.y * P.y), yi = S * (W.x * P.y - W.y * P.x);
-    wre[t] = yr;
-    wim[t] = yi;
+    wy[t] = make_float2(yr, yi);
     // xi, dxi/dx, dxi/dy by the factorised sums
     float xr = 0.f, xi = 0.f, dxr = 0.f, dxi = 0.f, dyr = 0.f, dyi = 0.f;
     float pa_prev = 0.f, pa_cur = px[0];
@@ -670,7 +675,8 @@ __global__ void __launch_bounds__(K4S_T) k4_grad_shape(const K4SArgs a) {
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj) s[i][jj] = 0.f;
       for (int vv = 0; vv < nv; ++vv) {
-        const float wr = wre[vv], wi = wim[vv];
+        const float2 w2 = wy[vv];
+        const float wr = w2.x, wi = w2.y;
         const float2 px = *reinterpret_cast<const float2*>(phx + vv * ld + na0);
         const float4 py4 = *reinterpret_cast<const float4*>(phy + vv * ld + nb0);
         const float xr0 = wr * px.x, xi0 = wi * px.x, xr1 = wr * px.y, xi1 = wi * px.y;
@@ -688,20 +694,33 @@ __global__ void __launch_bounds__(K4S_T) k4_grad_shape(const K4SArgs a) {
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj) {
           const int na = na0 + i, nb = nb0 + jj;
-          if (na + nb <= n) accd[toff[na] + nb] += (double)((((na + nb) & 3) >= 2 ? 2.0f : -2.0f) * s[i][jj]);
+          const double d = (double)((((na + nb) & 3) >= 2 ? 2.0f : -2.0f) * s[i][jj]);
+          if (reg_acc) accr[i][jj] += d;
+          else if (na + nb <= n) accd[toff[na] + nb] += d;
         }
+    }
+    __syncthreads();
+  }
+  if (reg_acc) {  // the basis rows are free now: the sums go to the folded triangle there
+    if (t < nblk) {
+      const int na0 = blocks[t].x, nb0 = blocks[t].y;
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj)
+          if (na0 + i + nb0 + jj <= n) accd[toff[na0 + i] + nb0 + jj] = accr[i][jj];
     }
     __syncthreads();
   }
   // per-CTA partials (the flux factor of every group but the flux one is applied here, in FP64)
   for (int k = t; k < a.nnz; k += T)
     a.part_c[(size_t)blockIdx.x * a.nnz + k] = accd[toff[__ldg(a.n1 + k)] + __ldg(a.n2 + k)] * flux;
-  __shared__ double red[K4S_T][K4S_NS];
-  for (int i = 0; i < K4S_NS; ++i) red[t][i] = (accs[i] + (double)acc32[i]) * (i == 0 ? 1.0 : flux);
+  double* red = reinterpret_cast<double*>(sm + lay.phy);  // [T][K4S_NS], in the second basis-row area
+  for (int i = 0; i < K4S_NS; ++i) red[t * K4S_NS + i] = (accs[i] + (double)acc32[i]) * (i == 0 ? 1.0 : flux);
   __syncthreads();
   if (t < K4S_NS) {
     double s = 0.0;
-    for (int q = 0; q < T; ++q) s += red[q][t];
+    for (int q = 0; q < T; ++q) s += red[q * K4S_NS + t];
     a.part_s[(size_t)blockIdx.x * K4S_NS + t] = s;
   }
 }
@@ -947,8 +966,7 @@ int launch_grad(wn_ctx* ctx, const ObsDev& o, const Model* M, const PeelArgs& pa
     a.part_s = shpart;
     a.part_c = shpart + (size_t)sgrid * K4S_NS;
     a.err = ctx->d_err;
-    // static shared memory: the 128 x 7 FP64 reduction array
-    const size_t smax = 227 * 1024 - sizeof(double) * K4S_T * K4S_NS;
+    const size_t smax = 227 * 1024;
     int T = K4S_T;
     size_t smem = (size_t)k4s_layout(h.nmax, a.nnz, T).total;
     if (smem > smax) {
@@ -1034,7 +1052,7 @@ int launch_grad_shape_coeff(wn_ctx* ctx, const ObsDev& o, const Model* M, const 
     a.part_s = shpart;
     a.part_c = shpart + (size_t)sgrid * K4S_NS;
     a.err = ctx->d_err;
-    const size_t smax = 227 * 1024 - sizeof(double) * K4S_T * K4S_NS;
+    const size_t smax = 227 * 1024;
     int T = K4S_T;
     size_t smem = (size_t)k4s_layout(h.nmax, a.nnz, T).total;
     if (smem > smax) {
