@@ -465,14 +465,21 @@ __host__ __device__ inline int k4s_nblocks(int nmax) {
   return c;
 }
 
-// Folded triangle: row a (b = 0 .. n - a + 1) padded to an even length, so every row starts on a
-// 16-byte boundary and two (f, g) pairs load as one float4.  Row offset and total entries.
+// The factorised sums run over K4S_RA rows a of the folded triangle at once, so each thread's phi(y)
+// entries are read once per group of rows instead of once per row.
+constexpr int K4S_RA = 4;
+// Rows of the folded triangle with the zero rows that complete the last group.
+__host__ __device__ inline int k4s_rows(int nmax) { return (nmax + K4S_RA) / K4S_RA * K4S_RA; }
+// Folded triangle: row a holds b = 0 .. n - a + 1 and is padded to an even length at least that of the
+// first row of its group (b = 0 .. n - a0 + 1, zeros past its own end), so every row starts on a 16-byte
+// boundary, two (f, g) pairs load as one float4, and the rows of a group share one b range.  Row offset
+// and total entries (rows 0 .. k4s_rows(n) - 1).
 __host__ __device__ inline int k4s_row_off(int nmax, int a) {
   int o = 0;
-  for (int i = 0; i < a; ++i) o += (nmax - i + 2 + 1) & ~1;
+  for (int i = 0; i < a; ++i) o += (nmax - (i - i % K4S_RA) + 2 + 1) & ~1;
   return o;
 }
-__host__ __device__ inline int k4s_nfg(int nmax) { return k4s_row_off(nmax, nmax + 1); }
+__host__ __device__ inline int k4s_nfg(int nmax) { return k4s_row_off(nmax, k4s_rows(nmax)); }
 
 // Shared-memory layout of k4_grad_shape (bytes): basis rows (a multiple of 4 floats with an odd count of
 // 16-byte quarters, so per-thread rows read as float4 without bank conflicts), folded coefficient pairs
@@ -496,7 +503,7 @@ __host__ __device__ inline K4SSmem k4s_layout(int nmax, int nnz, int T) {
   s.phy = s.phx + T * s.ld * 4;
   s.fg = (s.phy + T * s.ld * 4 + 15) & ~15;
   s.toff = s.fg + nfg * 8;
-  s.w = (s.toff + (nmax + 2) * 4 + 7) & ~7;
+  s.w = (s.toff + (k4s_rows(nmax) + 1) * 4 + 7) & ~7;
   s.accd = s.w + T * 8;
   s.blocks = s.accd + (k4s_reg_acc(nmax, T) ? 0 : nfg * 8);
   s.total = s.blocks + k4s_nblocks(nmax) * 4;
@@ -524,7 +531,8 @@ __global__ void __launch_bounds__(K4S_T) k4_grad_shape(const K4SArgs a) {
   const double flux = *a.flux, beta1 = *a.beta1, beta2 = *a.beta2;
 
   // folded coefficients: row a holds (f_ab, g_ab) for b = 0..n-a+1 (f is zero past the triangle)
-  for (int aa = t; aa <= n + 1; aa += T) toff[aa] = k4s_row_off(n, aa);
+  const int n_rows_fg = k4s_rows(n);
+  for (int aa = t; aa <= n_rows_fg; aa += T) toff[aa] = k4s_row_off(n, aa);
   const int nfg = k4s_nfg(n);
   for (int i = t; i < nfg; i += T) {
     fg[i] = make_float2(0.f, 0.f);
@@ -588,53 +596,75 @@ __global__ void __launch_bounds__(K4S_T) k4_grad_shape(const K4SArgs a) {
     wy[t] = make_float2(yr, yi);
     // xi, dxi/dx, dxi/dy by the factorised sums
     float xr = 0.f, xi = 0.f, dxr = 0.f, dxi = 0.f, dyr = 0.f, dyi = 0.f;
+    // phi_a(x) for a = 0 .. n + 1 (entries n + 2, n + 3 are zero; rows past n + 1 read entry n + 3)
+    auto phx_at = [&](int aa) { return px[min(aa, n + 3)]; };
     float pa_prev = 0.f, pa_cur = px[0];
-    for (int aa = 0; aa <= n; ++aa) {
-      const float pa_next = px[aa + 1];
-      const float dpa = c_dn_lo[aa] * pa_prev - c_dn_hi[aa] * pa_next;  // phi_a'(x)
-      const float2* r = fg + toff[aa];
-      const int nb = n - aa + 1;  // b = 0..nb (g reaches one past the triangle)
-      float te = 0.f, to = 0.f, ge = 0.f, go = 0.f;  // f and g sums over even / odd b
+    for (int a0 = 0; a0 <= n; a0 += K4S_RA) {
+      const int nb = n - a0 + 1;  // b = 0..nb for every row of the group (g reaches one past the triangle)
+      const float2* r[K4S_RA];
+      float te[K4S_RA], to[K4S_RA], ge[K4S_RA], go[K4S_RA];  // f and g sums over even / odd b
+#pragma unroll
+      for (int i = 0; i < K4S_RA; ++i) {
+        r[i] = fg + toff[a0 + i];
+        te[i] = to[i] = ge[i] = go[i] = 0.f;
+      }
       int b = 0;
       for (; b + 3 <= nb; b += 4) {
         const float4 p = *reinterpret_cast<const float4*>(py + b);
-        const float4 c01 = *reinterpret_cast<const float4*>(r + b);  // f_b, g_b, f_b+1, g_b+1
-        const float4 c23 = *reinterpret_cast<const float4*>(r + b + 2);
-        te = fmaf(c01.x, p.x, te);
-        ge = fmaf(c01.y, p.x, ge);
-        to = fmaf(c01.z, p.y, to);
-        go = fmaf(c01.w, p.y, go);
-        te = fmaf(c23.x, p.z, te);
-        ge = fmaf(c23.y, p.z, ge);
-        to = fmaf(c23.z, p.w, to);
-        go = fmaf(c23.w, p.w, go);
+#pragma unroll
+        for (int i = 0; i < K4S_RA; ++i) {
+          const float4 c01 = *reinterpret_cast<const float4*>(r[i] + b);  // f_b, g_b, f_b+1, g_b+1
+          const float4 c23 = *reinterpret_cast<const float4*>(r[i] + b + 2);
+          te[i] = fmaf(c01.x, p.x, te[i]);
+          ge[i] = fmaf(c01.y, p.x, ge[i]);
+          to[i] = fmaf(c01.z, p.y, to[i]);
+          go[i] = fmaf(c01.w, p.y, go[i]);
+          te[i] = fmaf(c23.x, p.z, te[i]);
+          ge[i] = fmaf(c23.y, p.z, ge[i]);
+          to[i] = fmaf(c23.z, p.w, to[i]);
+          go[i] = fmaf(c23.w, p.w, go[i]);
+        }
       }
       for (; b + 1 <= nb; b += 2) {
-        const float2 c0 = r[b], c1 = r[b + 1];
         const float p0 = py[b], p1 = py[b + 1];
-        te = fmaf(c0.x, p0, te);
-        ge = fmaf(c0.y, p0, ge);
-        to = fmaf(c1.x, p1, to);
-        go = fmaf(c1.y, p1, go);
+#pragma unroll
+        for (int i = 0; i < K4S_RA; ++i) {
+          const float4 c = *reinterpret_cast<const float4*>(r[i] + b);
+          te[i] = fmaf(c.x, p0, te[i]);
+          ge[i] = fmaf(c.y, p0, ge[i]);
+          to[i] = fmaf(c.z, p1, to[i]);
+          go[i] = fmaf(c.w, p1, go[i]);
+        }
       }
       if (b <= nb) {
-        const float2 c0 = r[b];
         const float p0 = py[b];
-        te = fmaf(c0.x, p0, te);
-        ge = fmaf(c0.y, p0, ge);
+#pragma unroll
+        for (int i = 0; i < K4S_RA; ++i) {
+          const float2 c0 = r[i][b];
+          te[i] = fmaf(c0.x, p0, te[i]);
+          ge[i] = fmaf(c0.y, p0, ge[i]);
+        }
       }
-      // f terms with a+b even are real; g terms take the opposite part
-      const bool odd = aa & 1;
-      const float Tr = odd ? to : te, Ti = odd ? te : to;
-      const float Dr = odd ? ge : go, Di = odd ? go : ge;
-      xr = fmaf(pa_cur, Tr, xr);
-      xi = fmaf(pa_cur, Ti, xi);
-      dxr = fmaf(dpa, Tr, dxr);
-      dxi = fmaf(dpa, Ti, dxi);
-      dyr = fmaf(pa_cur, Dr, dyr);
-      dyi = fmaf(pa_cur, Di, dyi);
-      pa_prev = pa_cur;
-      pa_cur = pa_next;
+#pragma unroll
+      for (int i = 0; i < K4S_RA; ++i) {
+        const int aa = a0 + i;  // rows past n hold zeros: their terms vanish
+        const float pa_next = phx_at(aa + 1);
+        const int ac = min(aa, n + 1);
+        const float dpa = c_dn_lo[ac] * pa_prev - c_dn_hi[ac] * pa_next;  // phi_a'(x)
+        // f terms with a+b even are real; g terms take the opposite part (a0 is a multiple of K4S_RA,
+        // so the parity of a is that of i)
+        const bool odd = i & 1;
+        const float Tr = odd ? to[i] : te[i], Ti = odd ? te[i] : to[i];
+        const float Dr = odd ? ge[i] : go[i], Di = odd ? go[i] : ge[i];
+        xr = fmaf(pa_cur, Tr, xr);
+        xi = fmaf(pa_cur, Ti, xi);
+        dxr = fmaf(dpa, Tr, dxr);
+        dxi = fmaf(dpa, Ti, dxi);
+        dyr = fmaf(pa_cur, Dr, dyr);
+        dyi = fmaf(pa_cur, Di, dyi);
+        pa_prev = pa_cur;
+        pa_cur = pa_next;
+      }
     }
     if (valid) {
       // Re(Y * (pr + i pi)) = yr pr - yi pi
