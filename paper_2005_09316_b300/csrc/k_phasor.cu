@@ -13,10 +13,11 @@
 //  * No FP64 in the loops: tau is formed once per (component, row) in double-float FP32 from float-pair
 //    operands (error-free two-product and two-sum) and per-channel phases are reduced to [-1/2, 1/2]
 //    turns in double-float FP32 arithmetic.
-//  * Uniformly spaced channels: the phasor of channel f+1 is the phasor of channel f times
-//    Delta = exp(-2 pi i tau dnu / c) (one complex multiply), restarted from an exact phase at the
-//    first channel of every lane; Delta itself is formed from an exactly reduced phase with the
-//    accurate sincospif.  Arbitrary channel lists reduce and evaluate every channel.
+//  * Uniformly spaced channels: the phasors follow the three-term recurrence P(f+1) = 2 cos(delta) P(f)
+//    - P(f-1), delta = 2 pi tau dnu / c (one packed FMA per component of the complex value), run up and
+//    down from an exact phase at the middle channel of every lane (k1_loop.cuh); the one-channel step
+//    exp(-i delta) is formed from an exactly reduced phase with the accurate sincospif.  Arbitrary
+//    channel lists reduce and evaluate every channel.
 //  * Spectrum and Gaussian envelope share one exp2: amplitude = sgn * 2^(log2|S| + alpha log2(nu/nu_ref)
 //    - q (nu/c)^2 E log2 e), q the Gaussian quadratic form in (u, v) metres.
 #include "wn_internal.cuh"
