@@ -325,6 +325,15 @@ WN_API int wn_pipe_rates(wn_ctx* ctx, double* rates);
  * after one warm-up; allocates a small scratch buffer and synchronises its own stream. */
 WN_API int wn_phasor_loop_rate(wn_ctx* ctx, double* evals_per_s);
 
+/* Tensor-core and TMEM timings as the shapelet kernel uses them (no paper counterpart).  One CTA per SM
+ * issues 2,048 tcgen05 kind::f16 MMAs (M = 128, K = 16, bf16 operands, FP32 accumulator in TMEM) back to
+ * back from one thread, with zero operands K-major in shared memory in the shapelet kernel's
+ * no-swizzle layout.  out (4 doubles): SM clocks per MMA instruction at N = 128 and at N = 64
+ * (issue to completion, averaged over the CTAs), then SM clocks of one 16-column TMEM load and its wait
+ * (one warp, alone), and of eight such loads under one wait.  Allocates a small buffer and synchronises
+ * its own stream; flags WN_DEVERR_TIMEOUT if a bounded wait gave up. */
+WN_API int wn_mma_rate(wn_ctx* ctx, double* out);
+
 /* The failure path of the kernels' bounded waits, without a fault (no paper counterpart).  A one-thread
  * kernel waits on an mbarrier that nothing ever arrives at, through the same bounded-wait helper as the
  * prediction kernels but with a limit of `seconds` (0 < seconds <= 5) instead of ~2 s; it gives up,

@@ -5,6 +5,8 @@
 #include "wn_internal.cuh"
 #include "k1_loop.cuh"
 
+#include <vector>
+
 namespace wn {
 
 constexpr int KP_CHAINS = 8;
@@ -106,6 +108,99 @@ __global__ void __launch_bounds__(256, 2) kp_loop(float* out, int passes) {
 #pragma unroll
   for (int k = 0; k < KP_LOOP_K; ++k) s += Vre[k].x + Vre[k].y + Vim[k].x + Vim[k].y;
   out[blockIdx.x * blockDim.x + tid] = s;
+}
+
+// tcgen05 throughput as the shapelet kernel uses it: kind::f16 MMAs (M = 128, K = 16, bf16 operands,
+// FP32 accumulator in TMEM) with both operands K-major in shared memory in the same no-swizzle
+// core-matrix layout, issued back to back by one thread per CTA, one CTA per SM.  The operands are zero
+// (the timing does not depend on them).  Block 0, warp 0 then times 16-column TMEM loads: one load and
+// its wait at a time, and eight loads under one wait.  clk = {MMA issue-to-completion clocks of each
+// CTA, then the two load timings}.
+constexpr int KP_MMA_REP = 512;  // K = 64 passes (4 MMAs each)
+
+__global__ void __launch_bounds__(128, 1) kp_mma(int n, long long* clk, unsigned* err) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  unsigned char* a_t = smem + ((1024u - (smem_u32(smem) & 1023u)) & 1023u);  // 128 x 64 bf16
+  unsigned char* b_t = a_t + 16384;                                            // n x 64 bf16
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tslot;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  for (int i = tid; i < (16384 + n * 128) / 16; i += 128) reinterpret_cast<uint4*>(a_t)[i] = make_uint4(0, 0, 0, 0);
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(smem_u32(&tslot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tslot;
+  if (tid == 0) {
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    const uint32_t a0 = smem_u32(a_t), b0 = smem_u32(b_t);
+    const uint32_t lbo_a = (128u >> 3) << 7, lbo_b = ((uint32_t)n >> 3) << 7;
+    auto desc = [](uint32_t addr, uint32_t lbo) {
+      return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) | ((uint64_t)(128u >> 4) << 32) |
+             (1ull << 46);
+    };
+    const long long t0 = clock64();
+    for (int r = 0; r < KP_MMA_REP; ++r) {
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const uint64_t da = desc(a0 + 2u * kk * lbo_a, lbo_a), db = desc(b0 + 2u * kk * lbo_b, lbo_b);
+        const uint32_t acc = (r > 0 || kk > 0) ? 1u : 0u;
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                     "l"(da), "l"(db), "r"(idesc), "r"(acc)
+                     : "memory");
+      }
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&bar))
+                 : "memory");
+    const bool ok = mbar_wait_bounded(&bar, 0, err);
+    clk[blockIdx.x] = ok ? (clock64() - t0) : -1;
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (blockIdx.x == 0 && warp == 0) {
+    uint32_t v[8][16];
+    float acc = 0.f;
+    const long long t0 = clock64();
+    for (int rep = 0; rep < 16; ++rep) {
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                   : "=r"(v[0][0]), "=r"(v[0][1]), "=r"(v[0][2]), "=r"(v[0][3]), "=r"(v[0][4]), "=r"(v[0][5]), "=r"(v[0][6]),
+                     "=r"(v[0][7]), "=r"(v[0][8]), "=r"(v[0][9]), "=r"(v[0][10]), "=r"(v[0][11]), "=r"(v[0][12]),
+                     "=r"(v[0][13]), "=r"(v[0][14]), "=r"(v[0][15])
+                   : "r"(tmem + (uint32_t)((rep & 7) * 16)));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(v[0][0]), "+r"(v[0][15])::"memory");
+      acc += __uint_as_float(v[0][0]) + __uint_as_float(v[0][15]);
+    }
+    const long long t1 = clock64();
+    for (int rep = 0; rep < 2; ++rep) {
+#pragma unroll
+      for (int c = 0; c < 8; ++c)
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                     : "=r"(v[c][0]), "=r"(v[c][1]), "=r"(v[c][2]), "=r"(v[c][3]), "=r"(v[c][4]), "=r"(v[c][5]),
+                       "=r"(v[c][6]), "=r"(v[c][7]), "=r"(v[c][8]), "=r"(v[c][9]), "=r"(v[c][10]), "=r"(v[c][11]),
+                       "=r"(v[c][12]), "=r"(v[c][13]), "=r"(v[c][14]), "=r"(v[c][15])
+                     : "r"(tmem + (uint32_t)(c * 16)));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int c = 0; c < 8; ++c) acc += __uint_as_float(v[c][rep]) + __uint_as_float(v[c][15 - rep]);
+    }
+    const long long t2 = clock64();
+    if (tid == 0) {
+      clk[gridDim.x] = (t1 - t0) / 16;
+      clk[gridDim.x + 1] = (t2 - t1) / 2;
+    }
+    if (acc != 0.f) atomicOr(err, WN_DEVERR_TIMEOUT);  // zero operands give a zero accumulator
+  }
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
 }
 
 // The failure path of the kernels' bounded waits: one thread waits on an mbarrier that nothing ever
@@ -216,5 +311,47 @@ extern "C" int wn_pipe_rates(wn_ctx* ctx, double* rates) {
   cudaFree(out);
   cudaSetDevice(prev);
   if (e != cudaSuccess) return set_error(WN_ECUDA, std::string("pipe-rate probe: ") + cudaGetErrorString(e));
+  return WN_OK;
+}
+
+extern "C" int wn_mma_rate(wn_ctx* ctx, double* out) {
+  if (!ctx || !out) return set_error(WN_EINVAL, "NULL argument");
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaError_t e = cudaSetDevice(ctx->device);
+  const int grid = ctx->num_sms;
+  long long* clk = nullptr;
+  cudaStream_t st = nullptr;
+  if (e == cudaSuccess) e = cudaMalloc(&clk, sizeof(long long) * (grid + 2));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  std::vector<long long> h(grid + 2);
+  const int ns[2] = {128, 64};
+  // 64 KB of shared memory per CTA: at most 3 CTAs (384 TMEM columns) share an SM, so no allocation waits
+  const int smem = 64 * 1024;
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kp_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // the first launch is a warm-up
+      kp_mma<<<grid, 128, smem, st>>>(ns[i], clk, ctx->d_err);
+      e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(h.data(), clk, sizeof(long long) * (grid + 2), cudaMemcpyDeviceToHost);
+    double sum = 0.0;
+    int cnt = 0;
+    for (int b = 0; b < grid; ++b)
+      if (h[b] > 0) {
+        sum += (double)h[b];
+        ++cnt;
+      }
+    out[i] = cnt ? sum / cnt / (4.0 * KP_MMA_REP) : -1.0;
+    if (i == 0) {
+      out[2] = (double)h[grid];
+      out[3] = (double)h[grid + 1];
+    }
+  }
+  if (st) cudaStreamDestroy(st);
+  cudaFree(clk);
+  cudaSetDevice(prev);
+  if (e != cudaSuccess) return set_error(WN_ECUDA, std::string("MMA rate probe: ") + cudaGetErrorString(e));
   return WN_OK;
 }

@@ -633,8 +633,15 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
         q[r] = q[r] == 0.f ? 0.f : exp2f((float)E[r] - hy);
         scale[r] = __int_as_float(max(0, 127 - E[r]) << 23);
       }
-      // accumulator rows in chunks of 16 columns (8 n2)
+      // accumulator rows in chunks of 16 columns (8 n2).  Once the last chunk's loads have completed the
+      // accumulator is released to the MMA warp (tfree), before that chunk is used.
       const int nch = a.n_pad >> 4;
+      bool released = false;
+      auto release = [&]() {
+        tc_fence_before();
+        mbar_arrive(&tfree[sp]);
+        released = true;
+      };
       if (LUT) {  // table-interpolated phi_n2(y): one chunk of every row at a time
         int iy[R];
         float ty[R];
@@ -647,6 +654,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
           for (int r = 0; r < R; ++r) tmem_issue16x(trow + (uint32_t)(r * a.n_pad + (c << 4)), tb[r]);
 #pragma unroll
           for (int r = 0; r < R; ++r) tmem_wait16(tb[r]);
+          if (c == nch - 1) release();
 #pragma unroll
           for (int r = 0; r < R; ++r) epi_chunk_lut(tb[r], a.lut, iy[r], ty[r], c << 3, xr[r], xi[r]);
         }
@@ -680,6 +688,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
             tmem_issue16x(trow + (uint32_t)(a.n_pad + (c << 4)), tb[1]);
             tmem_wait16(tb[0]);
             tmem_wait16(tb[1]);
+            if (c == nch - 1) release();
             if (yfast) {  // both rows unscaled: one f32x2 recurrence
               epi_chunk2(tb[0], tb[1], ca2, cb2, c << 3, Y, Q, Qp, xr, xi);
             } else {
@@ -690,8 +699,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
           }
         }
       }
-      tc_fence_before();
-      mbar_arrive(&tfree[sp]);
+      if (!released) release();
       if (j > 0 && !k2_wait(&xempty[sp], (j - 1) & 1, a.err)) break;  // the producers have read tile j-1's
 #pragma unroll
       for (int r = K2_RE(R); r < R; ++r) xfer[r * K2_M] = valid[r] ? make_float2(xr[r], xi[r]) : make_float2(0.f, 0.f);
