@@ -407,9 +407,11 @@ __global__ void k4_reduce_pg(const double* partials, int chunks, int n_point, in
 // where g_ab = sqrt((b+1)/2) f_a,b+1 - sqrt(b/2) f_a,b-1 is the y-derivative folded into the
 // coefficients (phi_b' = sqrt(b/2) phi_b-1 - sqrt((b+1)/2) phi_b+1), so both sums run over the same
 // phi_b(y) and T'_a takes the opposite real/imaginary part.  Each thread keeps its phi_n(x), phi_n(y)
-// rows in shared memory (odd row stride: conflict-free both per thread and across threads); the CTA
-// then reduces the coefficient gradients sum_vis w phi_a(x) phi_b(y) for the tile (w = Re or Im of
-// conj(W) S P by the parity of a+b) into FP64 shared accumulators.
+// rows in shared memory (rows of an odd count of 16-byte quarters: float4 reads conflict-free) and runs
+// the sums over K4S_RA rows a at once.  The CTA then sums the coefficient gradients
+// sum_vis w phi_a(x) phi_b(y) over the tile (w = Re or Im of conj(W) S P by the parity of a+b) in 2 x 4
+// blocks, one per thread, into FP64 sums (in the thread's registers when it owns one block, else in
+// shared memory).
 // ---------------------------------------------------------------------------------------------
 constexpr int K4S_T = 128;
 constexpr int K4S_NS = 7;  // flux, alpha, l, m, beta1, beta2, pa
