@@ -514,6 +514,11 @@ def run_case(case: str):
     import torch
     import paper_2005_09316_b300 as wn
     ctx = wn.Context(0)
+    if case == "serve":          # K6: a reduced serving stream (200 requests drawn from 12 request sets)
+        r = bench_serving(wn, ctx, 0, torch, n_req=200, n_templates=12)
+        print(json.dumps({"case": case, "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"], "batches": r["batches"],
+                          "wall_s": r["wall_s"], "device_errors": ctx.device_errors()}))
+        return
     if case == "mwa_small":      # K1: 2 steps of the MWA array, 2,000 points + 500 Gaussians
         obs, _ = synth.mwa(n_time=2)
         sky = synth.make_sky(102, 2000, 500, 0)
@@ -572,7 +577,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the shapelet, adjoint, calibration, truncation, fit and serving reports")
-    ap.add_argument("--case", choices=["mwa_small", "fornax_small", "adjoint", "peel", "calib"],
+    ap.add_argument("--case", choices=["mwa_small", "fornax_small", "adjoint", "peel", "calib", "serve"],
                     help="run one small fixed case for profiling instead of the benchmark")
     args = ap.parse_args()
     if args.case:
