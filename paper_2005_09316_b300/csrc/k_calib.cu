@@ -91,12 +91,29 @@ __global__ void k7_incidence(const int* ant1, const int* ant2, int n_base, int n
 
 // Storage of the augmented lower triangle [A^T A | A^T b] in 32 x 32 tiles: tile (I, J), J <= I, at
 // index I (I + 1) / 2 + J, rows padded to 33 floats so a column of a tile is conflict-free.
-constexpr int K7_TS = 33;               // row stride of a tile
+constexpr int K7_TS = 36;               // row stride of a tile: 9 float4 (odd), so rows read as float4 without conflicts
 constexpr int K7_TILE = 32 * K7_TS;     // floats per tile
 __device__ __forceinline__ float* k7_elem(float* T, int r, int c) {
   return T + ((r >> 5) * ((r >> 5) + 1) / 2 + (c >> 5)) * K7_TILE + (r & 31) * K7_TS + (c & 31);
 }
 __device__ __forceinline__ float* k7_tile(float* T, int I, int J) { return T + (I * (I + 1) / 2 + J) * K7_TILE; }
+
+// One tile row (32 floats, 16-byte aligned) to registers and back, as float4: with the row stride of 9
+// float4 the 8 lanes of each quarter-warp hit distinct banks.
+__device__ __forceinline__ void k7_row_load(const float* r, float (&v)[32]) {
+#pragma unroll
+  for (int c = 0; c < 32; c += 4) {
+    const float4 q = *reinterpret_cast<const float4*>(r + c);
+    v[c] = q.x;
+    v[c + 1] = q.y;
+    v[c + 2] = q.z;
+    v[c + 3] = q.w;
+  }
+}
+__device__ __forceinline__ void k7_row_store(float* r, const float (&v)[32]) {
+#pragma unroll
+  for (int c = 0; c < 32; c += 4) *reinterpret_cast<float4*>(r + c) = make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]);
+}
 
 // Column C of the unblocked factorisation of a 32 x 32 diagonal tile held one row per lane; recursion
 // keeps every register index a compile-time constant.  n_here = rows of this tile that are part of the
@@ -128,15 +145,15 @@ __device__ __forceinline__ void k7_diag_col(float (&row)[32], float* dinv, int l
 __device__ __forceinline__ void k7_factor_diag(float* T, int K, float* dinv, int lane, int n, int* s_bad) {
   float* D = k7_tile(T, K, K);
   float row[32];
-#pragma unroll
-  for (int c = 0; c < 32; ++c) row[c] = D[lane * K7_TS + c];
+  k7_row_load(D + lane * K7_TS, row);
   k7_diag_col<0>(row, dinv + K * 32, lane, n - K * 32, s_bad);
-#pragma unroll
-  for (int c = 0; c < 32; ++c) D[lane * K7_TS + c] = row[c];
+  k7_row_store(D + lane * K7_TS, row);
 }
 
-// Trailing update of tile (K + 1 + I, K + 1 + J) by step K's panel: A -= L_IK L_JK^T.  A warp per tile,
-// each lane 8 rows x 4 columns.
+// Trailing update of tile (K + 1 + I, K + 1 + J) by step K's panel: A -= L_IK L_JK^T.  A warp per tile;
+// lane (rg, cg) = (lane / 8, lane % 8) holds rows rg + 4i (i < 8) and columns cg + 8j (j < 4), and reads
+// both panels four k at a time as float4: the 4 (or 8) distinct rows a load touches are adjacent, at
+// distinct banks.
 __device__ __forceinline__ void k7_trail_tile(float* T, int K, int I, int J, int lane) {
   const int rg = lane >> 3, cg = lane & 7;
   const float* PI = k7_tile(T, K + 1 + I, K);
@@ -147,22 +164,27 @@ __device__ __forceinline__ void k7_trail_tile(float* T, int K, int I, int J, int
   for (int i = 0; i < 8; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-#pragma unroll 4
-  for (int k = 0; k < 32; ++k) {
-    float av[8], bv[4];
+#pragma unroll 2
+  for (int k = 0; k < 32; k += 4) {
+    float4 av[8], bv[4];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) av[i] = PI[(rg * 8 + i) * K7_TS + k];
+    for (int i = 0; i < 8; ++i) av[i] = *reinterpret_cast<const float4*>(PI + (rg + 4 * i) * K7_TS + k);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) bv[j] = PJ[(cg * 4 + j) * K7_TS + k];
+    for (int j = 0; j < 4; ++j) bv[j] = *reinterpret_cast<const float4*>(PJ + (cg + 8 * j) * K7_TS + k);
 #pragma unroll
     for (int i = 0; i < 8; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+      for (int j = 0; j < 4; ++j) {
+        acc[i][j] = fmaf(av[i].x, bv[j].x, acc[i][j]);
+        acc[i][j] = fmaf(av[i].y, bv[j].y, acc[i][j]);
+        acc[i][j] = fmaf(av[i].z, bv[j].z, acc[i][j]);
+        acc[i][j] = fmaf(av[i].w, bv[j].w, acc[i][j]);
+      }
   }
 #pragma unroll
   for (int i = 0; i < 8; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) C[(rg * 8 + i) * K7_TS + cg * 4 + j] -= acc[i][j];
+    for (int j = 0; j < 4; ++j) C[(rg + 4 * i) * K7_TS + cg + 8 * j] -= acc[i][j];
 }
 
 __global__ void __launch_bounds__(K7_THREADS, 1) k7_calib(const K7Args a) {
@@ -267,16 +289,14 @@ __global__ void __launch_bounds__(K7_THREADS, 1) k7_calib(const K7Args a) {
         float* P = k7_tile(T, I, K);
         const float* D = k7_tile(T, K, K);
         float xr[32];
-#pragma unroll
-        for (int c = 0; c < 32; ++c) xr[c] = P[lane * K7_TS + c];
+        k7_row_load(P + lane * K7_TS, xr);
 #pragma unroll
         for (int c = 0; c < 32; ++c) {
           xr[c] *= dinv[K * 32 + c];
 #pragma unroll
           for (int j = c + 1; j < 32; ++j) xr[j] -= xr[c] * D[j * K7_TS + c];
         }
-#pragma unroll
-        for (int c = 0; c < 32; ++c) P[lane * K7_TS + c] = xr[c];
+        k7_row_store(P + lane * K7_TS, xr);
       }
       __syncthreads();
       // trailing update A_IJ -= L_IK L_JK^T, K < J <= I: tile q = 0 is the next diagonal tile (warp 0,
