@@ -149,6 +149,11 @@ WN_API const char* wn_last_error(void);
 WN_API const char* wn_version(void);
 /* Select the point/Gaussian precision (wn_precision) and the shapelet mode (wn_shape_mode). */
 WN_API int wn_set_precision(wn_ctx* ctx, int precision, int shape_mode);
+/* Tracing (no paper counterpart): with on != 0, every compute entry point of the context (wn_sky_upload,
+ * wn_predict, wn_predict_static, wn_peel, wn_peel_model, wn_predict_grad, wn_fit_shapelets, wn_calibrate,
+ * wn_server_submit) opens an NVTX range named after itself for the duration of the call, for profilers
+ * that record NVTX (ncu --nvtx).  Off by default.  Host-side only: results are unchanged. */
+WN_API int wn_set_trace(wn_ctx* ctx, int on);
 /* Read and clear the device error flags (WN_DEVERR_*).  Synchronizes the device. */
 WN_API int wn_device_errors(wn_ctx* ctx, uint32_t* flags_out);
 

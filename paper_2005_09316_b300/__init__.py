@@ -29,7 +29,7 @@ EXPORTED = ("wn_create", "wn_destroy", "wn_last_error", "wn_version", "wn_set_pr
             "wn_predict_grad", "wn_predict_static", "wn_server_create", "wn_server_destroy", "wn_server_submit",
             "wn_server_poll", "wn_server_wait", "wn_server_copy", "wn_server_release", "wn_server_cancel",
             "wn_server_stats", "wn_calibrate", "wn_fit_shapelets", "wn_pipe_rates",
-            "wn_phasor_loop_rate", "wn_sky_shapelet_operand", "wn_selftest_timeout", "wn_mma_rate")
+            "wn_phasor_loop_rate", "wn_sky_shapelet_operand", "wn_selftest_timeout", "wn_mma_rate", "wn_set_trace")
 
 
 class WnError(RuntimeError):
@@ -107,6 +107,7 @@ def load(build_if_missing: bool = True):
         L.wn_phasor_loop_rate.argtypes = [P, ctypes.POINTER(dbl)]
         L.wn_selftest_timeout.argtypes = [P, dbl]
         L.wn_mma_rate.argtypes = [P, ctypes.POINTER(dbl)]
+        L.wn_set_trace.argtypes = [P, ctypes.c_int]
         for name in EXPORTED:
             if name not in ("wn_destroy", "wn_last_error", "wn_version", "wn_server_destroy"):
                 getattr(L, name).restype = ctypes.c_int
@@ -313,6 +314,10 @@ class Context:
     def selftest_timeout(self, seconds: float = 0.5):
         """Run a kernel whose bounded wait cannot complete; it must give up after `seconds` and flag it."""
         _check(load().wn_selftest_timeout(self.h, float(seconds)))
+
+    def set_trace(self, on: bool = True):
+        """NVTX ranges around the context's compute calls (for profilers that record NVTX)."""
+        _check(load().wn_set_trace(self.h, 1 if on else 0))
 
     def mma_rate(self) -> dict:
         """SM clocks per tcgen05 MMA (M = 128, K = 16, bf16) at N = 128 and 64, and of TMEM loads."""

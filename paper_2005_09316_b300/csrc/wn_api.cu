@@ -219,6 +219,12 @@ int wn_set_precision(wn_ctx* ctx, int precision, int shape_mode) {
   return ok();
 }
 
+int wn_set_trace(wn_ctx* ctx, int on) {
+  if (!ctx) return set_error(WN_EINVAL, "ctx is NULL");
+  ctx->trace = on ? 1 : 0;
+  return ok();
+}
+
 int wn_device_errors(wn_ctx* ctx, uint32_t* flags_out) {
   if (!ctx || !flags_out) return set_error(WN_EINVAL, "NULL argument");
   DeviceGuard g(ctx->device);
@@ -233,6 +239,7 @@ int wn_device_errors(wn_ctx* ctx, uint32_t* flags_out) {
 }
 
 int wn_sky_upload(wn_ctx* ctx, const wn_sky* s, int* model_id, void* stream) {
+  TraceRange trace_range(ctx, "wn_sky_upload");
   if (!ctx || !s || !model_id) return set_error(WN_EINVAL, "NULL argument");
   *model_id = 0;
   if (s->n_point < 0 || s->n_gauss < 0 || s->n_shape < 0) return set_error(WN_EINVAL, "negative component count");
@@ -434,6 +441,7 @@ int wn_sky_shapelet_operand(wn_ctx* ctx, int model_id, int q, void* host_out, si
 }
 
 int wn_predict(wn_ctx* ctx, const wn_obs* obs, int model_id, void* vis_c64, int accumulate, void* stream) {
+  TraceRange trace_range(ctx, "wn_predict");
   if (!ctx || !vis_c64) return set_error(WN_EINVAL, "NULL argument");
   ObsDev d;
   if (int r = check_obs(obs, d)) return r;
@@ -449,6 +457,7 @@ int wn_predict(wn_ctx* ctx, const wn_obs* obs, int model_id, void* vis_c64, int 
 
 int wn_peel(wn_ctx* ctx, const wn_obs* obs, int model_id, const void* gains_c64, int gains_t, int gains_f,
             const void* data_c64, void* resid_c64, void* stream) {
+  TraceRange trace_range(ctx, "wn_peel");
   if (!ctx || !resid_c64) return set_error(WN_EINVAL, "NULL argument");
   ObsDev d;
   if (int r = check_obs(obs, d)) return r;
@@ -463,6 +472,7 @@ int wn_peel(wn_ctx* ctx, const wn_obs* obs, int model_id, const void* gains_c64,
 
 int wn_peel_model(wn_ctx* ctx, const wn_obs* obs, const void* gains_c64, int gains_t, int gains_f,
                   const void* data_c64, const void* model_c64, void* resid_c64, void* stream) {
+  TraceRange trace_range(ctx, "wn_peel_model");
   if (!ctx || !model_c64 || !resid_c64) return set_error(WN_EINVAL, "NULL argument");
   ObsDev d;
   if (int r = check_obs(obs, d)) return r;
@@ -477,6 +487,7 @@ int wn_peel_model(wn_ctx* ctx, const wn_obs* obs, const void* gains_c64, int gai
 int wn_predict_grad(wn_ctx* ctx, const wn_obs* obs, int model_id, const void* gains_c64, int gains_t, int gains_f,
                     const void* data_c64, void* resid_c64, const wn_sky_grad* grad_out, double* loss_out,
                     void* stream) {
+  TraceRange trace_range(ctx, "wn_predict_grad");
   if (!ctx || !resid_c64 || !grad_out) return set_error(WN_EINVAL, "NULL argument");
   if (resid_c64 == data_c64) return set_error(WN_EINVAL, "wn_predict_grad: resid must not alias data");
   ObsDev d;
@@ -494,6 +505,7 @@ int wn_predict_grad(wn_ctx* ctx, const wn_obs* obs, int model_id, const void* ga
 
 int wn_fit_shapelets(wn_ctx* ctx, const wn_obs* obs, int model_id, const void* gains_c64, int gains_t, int gains_f,
                      const void* data_c64, int n_iter, double tol, double* coeff_inout, double* info, void* stream) {
+  TraceRange trace_range(ctx, "wn_fit_shapelets");
   if (!ctx || !coeff_inout) return set_error(WN_EINVAL, "NULL argument");
   ObsDev d;
   if (int r = check_obs(obs, d)) return r;
@@ -511,6 +523,7 @@ int wn_fit_shapelets(wn_ctx* ctx, const wn_obs* obs, int model_id, const void* g
 
 int wn_calibrate(wn_ctx* ctx, const wn_obs* obs, const void* model_c64, const void* data_c64, void* gains_c64,
                  int n_iter, void* stream) {
+  TraceRange trace_range(ctx, "wn_calibrate");
   if (!ctx || !model_c64 || !data_c64 || !gains_c64) return set_error(WN_EINVAL, "NULL argument");
   ObsDev d;
   if (int r = check_obs(obs, d)) return r;
@@ -528,6 +541,7 @@ int wn_calibrate(wn_ctx* ctx, const wn_obs* obs, const void* model_c64, const vo
 // per-channel tables from a fixed device array instead of the context's workspace, so the call
 // makes no device allocation.  Points and Gaussians, and the FP64 form, need no scratch at all.
 int wn_predict_static(wn_ctx* ctx, const wn_obs* obs, int model_id, void* vis_c64, int accumulate, void* stream) {
+  TraceRange trace_range(ctx, "wn_predict_static");
   if (!ctx || !vis_c64) return set_error(WN_EINVAL, "NULL argument");
   ObsDev d;
   if (int r = check_obs(obs, d)) return r;

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "woden_b300.h"
+#include <nvtx3/nvToolsExt.h>
 
 namespace wn {
 
@@ -89,6 +90,7 @@ struct wn_ctx {
   int num_sms = 148;
   int precision = WN_PREC_MIXED;
   int shape_mode = WN_SHAPE_BF16X3;
+  int trace = 0;  // NVTX ranges around the entry points (wn_set_trace)
   unsigned* d_err = nullptr;
   std::map<int, wn::Model*> models;
   int next_id = 1;
@@ -100,6 +102,20 @@ struct wn_ctx {
   float* lut = nullptr;  // basis table of the lookup-table shapelet mode (built on first use)
   float2* k1_part = nullptr;  // partial sums of the split tail tiles of the phasor launch (fixed size)
 };
+// An NVTX range named after the entry point, for the duration of the call, when the context traces.
+// NVTX is header-only: without a tool attached a range costs a few nanoseconds.
+struct TraceRange {
+  bool on;
+  TraceRange(const wn_ctx* ctx, const char* name) : on(ctx && ctx->trace) {
+    if (on) nvtxRangePushA(name);
+  }
+  ~TraceRange() {
+    if (on) nvtxRangePop();
+  }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
+
 
 namespace wn {
 

@@ -508,6 +508,7 @@ void wn_server_destroy(wn_server* s) {
 
 int wn_server_submit(wn_server* s, const wn_obs* obs, int model_id, int peel, const void* gains_c64, int gains_t,
                      int gains_f, const void* data_c64, uint64_t* ticket) {
+  TraceRange trace_range(s ? s->ctx : nullptr, "wn_server_submit");
   if (!s || !ticket) return set_error(WN_EINVAL, "NULL argument");
   *ticket = 0;
   ServeReq r;

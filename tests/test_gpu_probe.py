@@ -102,3 +102,26 @@ def test_mma_rate_probe():
     assert 62.0 <= r["clk_per_mma_n128"] <= 400.0, r
     assert 0.0 < r["clk_per_mma_n64"] <= r["clk_per_mma_n128"] + 1.0, r
     assert 0.0 < r["clk_tmem_ld16"] < 200.0 and 0.0 < r["clk_tmem_ld16_x8"] < 8 * 200.0, r
+
+
+def test_tracing_leaves_results_unchanged():
+    """With NVTX ranges on, the entry points give bit-identical results (the ranges are host-side only)."""
+    import numpy as np
+
+    import paper_2005_09316_b300 as wn
+    import synth
+    ctx = wn.Context(0)
+    obs, sky = synth.tiny(5)
+    d = wn.obs_to_device(obs)
+    m = ctx.upload(sky)
+    v0 = ctx.predict(d, m).cpu().numpy()
+    ctx.set_trace(True)
+    v1 = ctx.predict(d, m).cpu().numpy()
+    m2 = ctx.upload(sky)
+    v2 = ctx.predict(d, m2).cpu().numpy()
+    ctx.set_trace(False)
+    assert np.array_equal(v0, v1) and np.array_equal(v0, v2)
+    assert ctx.device_errors() == 0
+    m.free()
+    m2.free()
+    ctx.close()
