@@ -154,6 +154,11 @@ WN_API int wn_set_precision(wn_ctx* ctx, int precision, int shape_mode);
  * wn_server_submit) opens an NVTX range named after itself for the duration of the call, for profilers
  * that record NVTX (ncu --nvtx).  Off by default.  Host-side only: results are unchanged. */
 WN_API int wn_set_trace(wn_ctx* ctx, int on);
+/* Host-side fault injection for tests (no paper counterpart): the next n device allocations the library
+ * makes, in any context or server of the process, fail as an out-of-memory cudaMalloc would, without
+ * calling CUDA; the calls that need them return WN_ENOMEM and leave their context usable.  n = 0
+ * cancels.  WN_EINVAL for n < 0. */
+WN_API int wn_debug_fail_allocs(int n);
 /* Read and clear the device error flags (WN_DEVERR_*).  Synchronizes the device. */
 WN_API int wn_device_errors(wn_ctx* ctx, uint32_t* flags_out);
 

@@ -29,7 +29,7 @@ EXPORTED = ("wn_create", "wn_destroy", "wn_last_error", "wn_version", "wn_set_pr
             "wn_predict_grad", "wn_predict_static", "wn_server_create", "wn_server_destroy", "wn_server_submit",
             "wn_server_poll", "wn_server_wait", "wn_server_copy", "wn_server_release", "wn_server_cancel",
             "wn_server_stats", "wn_calibrate", "wn_fit_shapelets", "wn_pipe_rates",
-            "wn_phasor_loop_rate", "wn_sky_shapelet_operand", "wn_selftest_timeout", "wn_mma_rate", "wn_set_trace")
+            "wn_phasor_loop_rate", "wn_sky_shapelet_operand", "wn_selftest_timeout", "wn_mma_rate", "wn_set_trace", "wn_debug_fail_allocs")
 
 
 class WnError(RuntimeError):
@@ -108,6 +108,7 @@ def load(build_if_missing: bool = True):
         L.wn_selftest_timeout.argtypes = [P, dbl]
         L.wn_mma_rate.argtypes = [P, ctypes.POINTER(dbl)]
         L.wn_set_trace.argtypes = [P, ctypes.c_int]
+        L.wn_debug_fail_allocs.argtypes = [ctypes.c_int]
         for name in EXPORTED:
             if name not in ("wn_destroy", "wn_last_error", "wn_version", "wn_server_destroy"):
                 getattr(L, name).restype = ctypes.c_int
@@ -397,3 +398,8 @@ class Context:
 
 def version() -> str:
     return load().wn_version().decode()
+
+
+def debug_fail_allocs(n: int):
+    """Make the library's next n device allocations fail as out-of-memory (host-side fault injection)."""
+    _check(load().wn_debug_fail_allocs(int(n)))

@@ -373,7 +373,7 @@ int launch_calibrate(wn_ctx* ctx, const ObsDev& o, const float2* model, const fl
       ctx->ws2 = nullptr;
       ctx->ws2_bytes = 0;
     }
-    cudaError_t e = cudaMalloc(&ctx->ws2, need);
+    cudaError_t e = dev_malloc(&ctx->ws2, need);
     if (e != cudaSuccess) return set_error(WN_ENOMEM, std::string("calibration workspace: ") + cudaGetErrorString(e));
     ctx->ws2_bytes = need;
   }

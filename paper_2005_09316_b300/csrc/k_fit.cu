@@ -80,11 +80,11 @@ int launch_fit_shapelets(wn_ctx* ctx, const ObsDev& o, Model* M, const PeelArgs&
   float2 *r = nullptr, *q = nullptr;
   double *sv = nullptr, *pv = nullptr, *gv = nullptr, *part = nullptr, *scal = nullptr;
   int* meta = nullptr;
-  cudaError_t e = cudaMalloc(&r, n_vis * sizeof(float2));
-  if (e == cudaSuccess) e = cudaMalloc(&q, n_vis * sizeof(float2));
-  if (e == cudaSuccess) e = cudaMalloc(&sv, 3 * (size_t)nnz * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&part, (vgrid + 8) * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&meta, 3 * (size_t)S * sizeof(int));
+  cudaError_t e = dev_malloc(&r, n_vis * sizeof(float2));
+  if (e == cudaSuccess) e = dev_malloc(&q, n_vis * sizeof(float2));
+  if (e == cudaSuccess) e = dev_malloc(&sv, 3 * (size_t)nnz * sizeof(double));
+  if (e == cudaSuccess) e = dev_malloc(&part, (vgrid + 8) * sizeof(double));
+  if (e == cudaSuccess) e = dev_malloc(&meta, 3 * (size_t)S * sizeof(int));
   auto release = [&]() {
     cudaStreamSynchronize(st);
     cudaFree(r);

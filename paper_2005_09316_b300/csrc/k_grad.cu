@@ -898,7 +898,7 @@ int launch_grad(wn_ctx* ctx, const ObsDev& o, const Model* M, const PeelArgs& pa
       ctx->ws2 = nullptr;
       ctx->ws2_bytes = 0;
     }
-    cudaError_t e = cudaMalloc(&ctx->ws2, need);
+    cudaError_t e = dev_malloc(&ctx->ws2, need);
     if (e != cudaSuccess) return set_error(WN_ENOMEM, std::string("adjoint workspace: ") + cudaGetErrorString(e));
     ctx->ws2_bytes = need;
   }
@@ -1040,7 +1040,7 @@ int launch_grad_shape_coeff(wn_ctx* ctx, const ObsDev& o, const Model* M, const 
       ctx->ws2 = nullptr;
       ctx->ws2_bytes = 0;
     }
-    cudaError_t e = cudaMalloc(&ctx->ws2, need);
+    cudaError_t e = dev_malloc(&ctx->ws2, need);
     if (e != cudaSuccess) return set_error(WN_ENOMEM, std::string("adjoint workspace: ") + cudaGetErrorString(e));
     ctx->ws2_bytes = need;
   }

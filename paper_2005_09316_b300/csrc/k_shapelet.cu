@@ -818,7 +818,7 @@ __global__ void k2_lut_build(float* lut) {
 
 static int k2_lut(wn_ctx* ctx, cudaStream_t st, const float** out) {
   if (!ctx->lut) {
-    cudaError_t e = cudaMalloc(&ctx->lut, sizeof(float) * (size_t)K2_LUT_N * K2_LUT_W);
+    cudaError_t e = dev_malloc(&ctx->lut, sizeof(float) * (size_t)K2_LUT_N * K2_LUT_W);
     if (e != cudaSuccess) return set_error(WN_ENOMEM, std::string("basis table: ") + cudaGetErrorString(e));
     k2_lut_build<<<(K2_LUT_N + 127) / 128, 128, 0, st>>>(ctx->lut);
     e = cudaGetLastError();
@@ -837,7 +837,7 @@ static int ws_reserve(wn_ctx* ctx, size_t bytes, cudaStream_t st) {
     ctx->ws = nullptr;
     ctx->ws_bytes = 0;
   }
-  cudaError_t e = cudaMalloc(&ctx->ws, bytes);
+  cudaError_t e = dev_malloc(&ctx->ws, bytes);
   if (e != cudaSuccess) return set_error(WN_ENOMEM, std::string("workspace: ") + cudaGetErrorString(e));
   ctx->ws_bytes = bytes;
   return WN_OK;

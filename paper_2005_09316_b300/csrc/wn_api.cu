@@ -126,7 +126,7 @@ static cudaError_t dalloc(T** p, size_t n, size_t& total) {
   *p = nullptr;
   if (n == 0) return cudaSuccess;
   total += n * sizeof(T);
-  return cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(T));
+  return dev_malloc(p, n * sizeof(T));
 }
 
 // Predict (mode STORE / ACCUM) or peel of one resident model on one observation.
@@ -154,6 +154,10 @@ int run_model_peel(wn_ctx* ctx, const ObsDev& d, const Model* M, float2* out, co
 
 using namespace wn;
 
+namespace wn {
+std::atomic<int> g_fail_allocs{0};
+}
+
 extern "C" {
 
 const char* wn_last_error(void) { return g_last_error.c_str(); }
@@ -179,13 +183,13 @@ int wn_create(wn_ctx** out, int device) {
     return set_error(WN_EINVAL, "woden_b300 is built for sm_103a (B300); device reports sm_" + std::to_string(major) +
                                     std::to_string(minor));
   }
-  e = cudaMalloc(&c->d_err, sizeof(unsigned));
+  e = dev_malloc(&c->d_err, sizeof(unsigned));
   if (e != cudaSuccess) {
     delete c;
     return cuda_fail(e, "cudaMalloc(error word)");
   }
   cudaMemset(c->d_err, 0, sizeof(unsigned));
-  e = cudaMalloc(&c->k1_part, k1_part_bytes(c->num_sms));
+  e = dev_malloc(&c->k1_part, k1_part_bytes(c->num_sms));
   if (e != cudaSuccess) {
     cudaFree(c->d_err);
     delete c;
@@ -216,6 +220,12 @@ int wn_set_precision(wn_ctx* ctx, int precision, int shape_mode) {
     return set_error(WN_EINVAL, "unknown shape mode");
   ctx->precision = precision;
   ctx->shape_mode = shape_mode;
+  return ok();
+}
+
+int wn_debug_fail_allocs(int n) {
+  if (n < 0) return set_error(WN_EINVAL, "wn_debug_fail_allocs: n must be >= 0");
+  wn::g_fail_allocs.store(n);
   return ok();
 }
 

@@ -7,6 +7,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <map>
 #include <string>
 #include <vector>
@@ -15,6 +16,21 @@
 #include <nvtx3/nvToolsExt.h>
 
 namespace wn {
+
+// Device allocations of the library go through dev_malloc.  g_fail_allocs > 0 (wn_debug_fail_allocs)
+// makes that many of the next ones fail as an out-of-memory cudaMalloc would, without calling CUDA:
+// host-side fault injection for the allocation-failure paths.
+extern std::atomic<int> g_fail_allocs;
+template <class T>
+inline cudaError_t dev_malloc(T** p, size_t bytes) {
+  int n = g_fail_allocs.load();
+  while (n > 0)
+    if (g_fail_allocs.compare_exchange_weak(n, n - 1)) {
+      *p = nullptr;
+      return cudaErrorMemoryAllocation;
+    }
+  return cudaMalloc(reinterpret_cast<void**>(p), bytes);
+}
 
 constexpr double kC = 299792458.0;
 constexpr double kPi = 3.14159265358979323846;

@@ -429,7 +429,7 @@ int wn_server_create(wn_ctx* ctx, int n_streams, size_t pool_bytes, int max_infl
   s->table_bytes = 16 + sizeof(K1Args) * s->max_reqs + sizeof(K1Work) * s->max_work;
   s->pool_bytes = pool_bytes & ~(size_t)255;
   s->t0 = std::chrono::steady_clock::now();
-  cudaError_t e = cudaMalloc(&s->pool, s->pool_bytes);
+  cudaError_t e = dev_malloc(&s->pool, s->pool_bytes);
   if (e != cudaSuccess) {
     delete s;
     return set_error(WN_ENOMEM, std::string("server pool: ") + cudaGetErrorString(e));
@@ -446,9 +446,9 @@ int wn_server_create(wn_ctx* ctx, int n_streams, size_t pool_bytes, int max_infl
     sl.priority = std::min(prio_least, prio_greatest + (int)k);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&sl.st, cudaStreamNonBlocking, sl.priority);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaMalloc(&sl.d_table, s->table_bytes);
+    if (e == cudaSuccess) e = dev_malloc(&sl.d_table, s->table_bytes);
     if (e == cudaSuccess) e = cudaHostAlloc(&sl.h_table, s->table_bytes, cudaHostAllocDefault);
-    if (e == cudaSuccess) e = cudaMalloc(&sl.chaninfo, chan_bytes + (size_t)max_rows * sizeof(float4));
+    if (e == cudaSuccess) e = dev_malloc(&sl.chaninfo, chan_bytes + (size_t)max_rows * sizeof(float4));
     if (e == cudaSuccess) sl.rowinfo = reinterpret_cast<float4*>(reinterpret_cast<char*>(sl.chaninfo) + chan_bytes);
     if (e == cudaSuccess) {
       // graph per stream: copy of the work table from pinned memory, then the batched kernel
