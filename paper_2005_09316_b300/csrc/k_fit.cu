@@ -71,6 +71,44 @@ __global__ void k8_vec_f64(double* y, const double* x, int n, double a, double b
   for (int i = blockIdx.x * K8_T + threadIdx.x; i < n; i += gridDim.x * K8_T) y[i] = a * x[i] + b * y[i];
 }
 
+// The CGLS scalars stay on the device (no host round trip per iteration): sc = {gam0, gam, qq, gnew,
+// stop, iterations done}.  Once stop is set every update below leaves the state as it is, so the
+// iterations the host launches before it sees the flag change nothing.
+enum { SC_GAM0 = 0, SC_GAM = 1, SC_QQ = 2, SC_GNEW = 3, SC_STOP = 4, SC_IT = 5 };
+
+__global__ void k8_cg_qq(double* sc) {  // breakdown: |A p|^2 not positive
+  if (threadIdx.x == 0 && sc[SC_STOP] == 0.0 && !(sc[SC_QQ] > 0.0)) sc[SC_STOP] = 1.0;
+}
+
+// x += alpha p and r += alpha q (q = -A p), alpha = gam / qq
+__global__ void k8_cg_step(double* x, const double* p, int nnz, float2* r, const float2* q, size_t n_vis,
+                           const double* sc) {
+  if (sc[SC_STOP] != 0.0) return;
+  const double alpha = sc[SC_GAM] / sc[SC_QQ];
+  const float af = (float)alpha;
+  const size_t stride = (size_t)gridDim.x * K8_T;
+  for (size_t i = (size_t)blockIdx.x * K8_T + threadIdx.x; i < (size_t)nnz; i += stride) x[i] = alpha * p[i] + x[i];
+  for (size_t i = (size_t)blockIdx.x * K8_T + threadIdx.x; i < n_vis; i += stride) {
+    const float2 u = r[i], v = q[i];
+    r[i] = make_float2(fmaf(af, v.x, u.x), fmaf(af, v.y, u.y));
+  }
+}
+
+// p = s + beta p, beta = gnew / gam
+__global__ void k8_cg_dir(double* p, const double* s, int nnz, const double* sc) {
+  if (sc[SC_STOP] != 0.0) return;
+  const double beta = sc[SC_GNEW] / sc[SC_GAM];
+  for (int i = blockIdx.x * K8_T + threadIdx.x; i < nnz; i += gridDim.x * K8_T) p[i] = 1.0 * s[i] + beta * p[i];
+}
+
+// gam = gnew, one more iteration done; stop once gam <= tol^2 gam0 (or is not positive)
+__global__ void k8_cg_finish(double* sc, double tol2) {
+  if (threadIdx.x != 0 || sc[SC_STOP] != 0.0) return;
+  sc[SC_GAM] = sc[SC_GNEW];
+  sc[SC_IT] += 1.0;
+  if (!(sc[SC_GAM] > tol2 * sc[SC_GAM0] && sc[SC_GAM] > 0.0)) sc[SC_STOP] = 1.0;
+}
+
 int launch_fit_shapelets(wn_ctx* ctx, const ObsDev& o, Model* M, const PeelArgs& pa, int n_iter, double tol,
                          double* coeff, double* info, cudaStream_t st) {
   const size_t n_vis = (size_t)o.n_rows * o.n_chan;
@@ -130,6 +168,7 @@ int launch_fit_shapelets(wn_ctx* ctx, const ObsDev& o, Model* M, const PeelArgs&
   int rc = WN_OK;
   double rr0 = 0, rr = 0, gam0 = 0, gam = 0;
   int it = 0;
+  double* sc = scal;  // device CGLS scalars (SC_*)
   // r0 = D - G (V_fixed + A x0)
   if (!rc) rc = launch_pack_coeff(ctx, M, coeff, meta, st);
   if (!rc) rc = run_model_peel(ctx, o, M, r, pa, st);
@@ -141,28 +180,42 @@ int launch_fit_shapelets(wn_ctx* ctx, const ObsDev& o, Model* M, const PeelArgs&
     cudaStreamSynchronize(st);
     gam = gam0;
     rr = rr0;
+    const double h[6] = {gam0, gam0, 0.0, 0.0, (n_iter > 0 && gam0 > 0.0 && tol < 1.0) ? 0.0 : 1.0, 0.0};
+    cudaMemcpyAsync(sc, h, sizeof(h), cudaMemcpyHostToDevice, st);
   }
-  for (; !rc && it < n_iter && gam > tol * tol * gam0 && gam > 0.0; ++it) {
+  const double tol2 = tol * tol;
+  const int kCheck = 8;  // iterations between looks at the device's stop flag
+  bool stopped = rc != WN_OK || !(n_iter > 0 && gam0 > 0.0 && tol < 1.0);
+  for (int launched = 0; !rc && !stopped && launched < n_iter; ++launched) {
     // q = -A p
     rc = launch_pack_coeff(ctx, M, pv, meta, st);
     if (rc) break;
     cudaMemsetAsync(q, 0, n_vis * sizeof(float2), st);
     rc = launch_shapelets(ctx, o, M, q, OUT_SUBG, pa, st);
     if (rc) break;
-    double qq = 0;
-    norm2_vis(q, &qq);
-    cudaStreamSynchronize(st);
-    if (!(qq > 0.0)) break;
-    const double alpha = gam / qq;
-    k8_vec_f64<<<cgrid, K8_T, 0, st>>>(coeff, pv, nnz, alpha, 1.0);   // x += alpha p
-    k8_axpy_c64<<<vgrid, K8_T, 0, st>>>(r, q, n_vis, (float)alpha);  // r -= alpha A p
+    k8_norm2_c64<<<vgrid, K8_T, 0, st>>>(q, n_vis, part);
+    k8_sum<<<1, 32, 0, st>>>(part, vgrid, sc + SC_QQ);
+    k8_cg_qq<<<1, 32, 0, st>>>(sc);
+    k8_cg_step<<<vgrid, K8_T, 0, st>>>(coeff, pv, nnz, r, q, n_vis, sc);  // x += alpha p, r -= alpha A p
     rc = atr(r);
     if (rc) break;
-    double gnew = 0;
-    norm2_coef(sv, &gnew);
+    k8_norm2_f64<<<cgrid, K8_T, 0, st>>>(sv, nnz, part);
+    k8_sum<<<1, 32, 0, st>>>(part, cgrid, sc + SC_GNEW);
+    k8_cg_dir<<<cgrid, K8_T, 0, st>>>(pv, sv, nnz, sc);  // p = s + beta p
+    k8_cg_finish<<<1, 32, 0, st>>>(sc, tol2);
+    if ((launched + 1) % kCheck == 0 || launched + 1 == n_iter) {
+      double h[6];
+      cudaMemcpyAsync(h, sc, sizeof(h), cudaMemcpyDeviceToHost, st);
+      cudaStreamSynchronize(st);
+      stopped = h[SC_STOP] != 0.0;
+    }
+  }
+  if (!rc) {
+    double h[6];
+    cudaMemcpyAsync(h, sc, sizeof(h), cudaMemcpyDeviceToHost, st);
     cudaStreamSynchronize(st);
-    k8_vec_f64<<<cgrid, K8_T, 0, st>>>(pv, sv, nnz, 1.0, gnew / gam);  // p = s + beta p
-    gam = gnew;
+    gam = h[SC_GAM];
+    it = (int)h[SC_IT];
   }
   // the model keeps the fitted coefficients: dense operand and the FP64 copy
   if (!rc) rc = launch_pack_coeff(ctx, M, coeff, meta, st);

@@ -437,6 +437,7 @@ struct K4SArgs {
   double* part_s;   // [grid][K4S_NS]
   double* part_c;   // [grid][nnz]
   unsigned* err;
+  int coef_only = 0;  // only the coefficient gradients (the fit's A^T r): no factorised sums, part_s zero
 };
 
 __device__ void hermite_scaled_row(float x, int nmax1, float* out) {
@@ -596,79 +597,81 @@ __global__ void __launch_bounds__(K4S_T) k4_grad_shape(const K4SArgs a) {
     const float S = valid ? ex2_approx(fmaf(a.alpha, ci.z, a.c_amp)) : 0.f;
     const float yr = S * (W.x * P.x + W.y * P.y), yi = S * (W.x * P.y - W.y * P.x);
     wy[t] = make_float2(yr, yi);
-    // xi, dxi/dx, dxi/dy by the factorised sums
+    // xi, dxi/dx, dxi/dy by the factorised sums (not needed for the coefficient gradients alone)
     float xr = 0.f, xi = 0.f, dxr = 0.f, dxi = 0.f, dyr = 0.f, dyi = 0.f;
-    // phi_a(x) for a = 0 .. n + 1 (entries n + 2, n + 3 are zero; rows past n + 1 read entry n + 3)
-    auto phx_at = [&](int aa) { return px[min(aa, n + 3)]; };
-    float pa_prev = 0.f, pa_cur = px[0];
-    for (int a0 = 0; a0 <= n; a0 += K4S_RA) {
-      const int nb = n - a0 + 1;  // b = 0..nb for every row of the group (g reaches one past the triangle)
-      const float2* r[K4S_RA];
-      float te[K4S_RA], to[K4S_RA], ge[K4S_RA], go[K4S_RA];  // f and g sums over even / odd b
-#pragma unroll
-      for (int i = 0; i < K4S_RA; ++i) {
-        r[i] = fg + toff[a0 + i];
-        te[i] = to[i] = ge[i] = go[i] = 0.f;
-      }
-      int b = 0;
-      for (; b + 3 <= nb; b += 4) {
-        const float4 p = *reinterpret_cast<const float4*>(py + b);
-#pragma unroll
+    if (!a.coef_only) {
+      // phi_a(x) for a = 0 .. n + 1 (entries n + 2, n + 3 are zero; rows past n + 1 read entry n + 3)
+      auto phx_at = [&](int aa) { return px[min(aa, n + 3)]; };
+      float pa_prev = 0.f, pa_cur = px[0];
+      for (int a0 = 0; a0 <= n; a0 += K4S_RA) {
+        const int nb = n - a0 + 1;  // b = 0..nb for every row of the group (g reaches one past the triangle)
+        const float2* r[K4S_RA];
+        float te[K4S_RA], to[K4S_RA], ge[K4S_RA], go[K4S_RA];  // f and g sums over even / odd b
+  #pragma unroll
         for (int i = 0; i < K4S_RA; ++i) {
-          const float4 c01 = *reinterpret_cast<const float4*>(r[i] + b);  // f_b, g_b, f_b+1, g_b+1
-          const float4 c23 = *reinterpret_cast<const float4*>(r[i] + b + 2);
-          te[i] = fmaf(c01.x, p.x, te[i]);
-          ge[i] = fmaf(c01.y, p.x, ge[i]);
-          to[i] = fmaf(c01.z, p.y, to[i]);
-          go[i] = fmaf(c01.w, p.y, go[i]);
-          te[i] = fmaf(c23.x, p.z, te[i]);
-          ge[i] = fmaf(c23.y, p.z, ge[i]);
-          to[i] = fmaf(c23.z, p.w, to[i]);
-          go[i] = fmaf(c23.w, p.w, go[i]);
+          r[i] = fg + toff[a0 + i];
+          te[i] = to[i] = ge[i] = go[i] = 0.f;
         }
-      }
-      for (; b + 1 <= nb; b += 2) {
-        const float p0 = py[b], p1 = py[b + 1];
-#pragma unroll
+        int b = 0;
+        for (; b + 3 <= nb; b += 4) {
+          const float4 p = *reinterpret_cast<const float4*>(py + b);
+  #pragma unroll
+          for (int i = 0; i < K4S_RA; ++i) {
+            const float4 c01 = *reinterpret_cast<const float4*>(r[i] + b);  // f_b, g_b, f_b+1, g_b+1
+            const float4 c23 = *reinterpret_cast<const float4*>(r[i] + b + 2);
+            te[i] = fmaf(c01.x, p.x, te[i]);
+            ge[i] = fmaf(c01.y, p.x, ge[i]);
+            to[i] = fmaf(c01.z, p.y, to[i]);
+            go[i] = fmaf(c01.w, p.y, go[i]);
+            te[i] = fmaf(c23.x, p.z, te[i]);
+            ge[i] = fmaf(c23.y, p.z, ge[i]);
+            to[i] = fmaf(c23.z, p.w, to[i]);
+            go[i] = fmaf(c23.w, p.w, go[i]);
+          }
+        }
+        for (; b + 1 <= nb; b += 2) {
+          const float p0 = py[b], p1 = py[b + 1];
+  #pragma unroll
+          for (int i = 0; i < K4S_RA; ++i) {
+            const float4 c = *reinterpret_cast<const float4*>(r[i] + b);
+            te[i] = fmaf(c.x, p0, te[i]);
+            ge[i] = fmaf(c.y, p0, ge[i]);
+            to[i] = fmaf(c.z, p1, to[i]);
+            go[i] = fmaf(c.w, p1, go[i]);
+          }
+        }
+        if (b <= nb) {
+          const float p0 = py[b];
+  #pragma unroll
+          for (int i = 0; i < K4S_RA; ++i) {
+            const float2 c0 = r[i][b];
+            te[i] = fmaf(c0.x, p0, te[i]);
+            ge[i] = fmaf(c0.y, p0, ge[i]);
+          }
+        }
+  #pragma unroll
         for (int i = 0; i < K4S_RA; ++i) {
-          const float4 c = *reinterpret_cast<const float4*>(r[i] + b);
-          te[i] = fmaf(c.x, p0, te[i]);
-          ge[i] = fmaf(c.y, p0, ge[i]);
-          to[i] = fmaf(c.z, p1, to[i]);
-          go[i] = fmaf(c.w, p1, go[i]);
+          const int aa = a0 + i;  // rows past n hold zeros: their terms vanish
+          const float pa_next = phx_at(aa + 1);
+          const int ac = min(aa, n + 1);
+          const float dpa = c_dn_lo[ac] * pa_prev - c_dn_hi[ac] * pa_next;  // phi_a'(x)
+          // f terms with a+b even are real; g terms take the opposite part (a0 is a multiple of K4S_RA,
+          // so the parity of a is that of i)
+          const bool odd = i & 1;
+          const float Tr = odd ? to[i] : te[i], Ti = odd ? te[i] : to[i];
+          const float Dr = odd ? ge[i] : go[i], Di = odd ? go[i] : ge[i];
+          xr = fmaf(pa_cur, Tr, xr);
+          xi = fmaf(pa_cur, Ti, xi);
+          dxr = fmaf(dpa, Tr, dxr);
+          dxi = fmaf(dpa, Ti, dxi);
+          dyr = fmaf(pa_cur, Dr, dyr);
+          dyi = fmaf(pa_cur, Di, dyi);
+          pa_prev = pa_cur;
+          pa_cur = pa_next;
         }
-      }
-      if (b <= nb) {
-        const float p0 = py[b];
-#pragma unroll
-        for (int i = 0; i < K4S_RA; ++i) {
-          const float2 c0 = r[i][b];
-          te[i] = fmaf(c0.x, p0, te[i]);
-          ge[i] = fmaf(c0.y, p0, ge[i]);
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < K4S_RA; ++i) {
-        const int aa = a0 + i;  // rows past n hold zeros: their terms vanish
-        const float pa_next = phx_at(aa + 1);
-        const int ac = min(aa, n + 1);
-        const float dpa = c_dn_lo[ac] * pa_prev - c_dn_hi[ac] * pa_next;  // phi_a'(x)
-        // f terms with a+b even are real; g terms take the opposite part (a0 is a multiple of K4S_RA,
-        // so the parity of a is that of i)
-        const bool odd = i & 1;
-        const float Tr = odd ? to[i] : te[i], Ti = odd ? te[i] : to[i];
-        const float Dr = odd ? ge[i] : go[i], Di = odd ? go[i] : ge[i];
-        xr = fmaf(pa_cur, Tr, xr);
-        xi = fmaf(pa_cur, Ti, xi);
-        dxr = fmaf(dpa, Tr, dxr);
-        dxi = fmaf(dpa, Ti, dxi);
-        dyr = fmaf(pa_cur, Dr, dyr);
-        dyi = fmaf(pa_cur, Di, dyi);
-        pa_prev = pa_cur;
-        pa_cur = pa_next;
       }
     }
-    if (valid) {
+    if (valid && !a.coef_only) {
       // Re(Y * (pr + i pi)) = yr pr - yi pi
       const float re_xi = yr * xr - yi * xi;  // Re(conj(W) V) / S_ref
       const float im_xi = yr * xi + yi * xr;  // Im(conj(W) V) / S_ref
@@ -1084,6 +1087,7 @@ int launch_grad_shape_coeff(wn_ctx* ctx, const ObsDev& o, const Model* M, const 
     a.part_s = shpart;
     a.part_c = shpart + (size_t)sgrid * K4S_NS;
     a.err = ctx->d_err;
+    a.coef_only = 1;
     const size_t smax = 227 * 1024;
     int T = K4S_T;
     size_t smem = (size_t)k4s_layout(h.nmax, a.nnz, T).total;
