@@ -38,11 +38,11 @@ OPS_PER_EVAL = 4
 FP32_LANES_PER_SM = 128
 
 
-def k1_traffic():
-    """DRAM bytes per launch of the phasor kernel from the committed ncu record, or None when the kernel
+def traffic_record(name: str):
+    """DRAM bytes per launch of a kernel from a committed ncu record in profiles/, or None when the kernel
     sources have changed since the counters were taken."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "k1_phasor_mwa_traffic.json")
+    path = os.path.join(ROOT, "profiles", name)
     try:
         rec = json.load(open(path))
         m = hashlib.sha256()
@@ -51,6 +51,10 @@ def k1_traffic():
         return rec["dram_bytes_per_launch"] if m.hexdigest() == rec["sources_sha256"] else None
     except Exception:
         return None
+
+
+def k1_traffic():
+    return traffic_record("k1_phasor_mwa_traffic.json")
 
 
 def count_launches(step, torch):
@@ -256,7 +260,9 @@ def bench_shapelets(wn, ctx, local, P, torch):
             "ms_per_step": round(ms, 4), "shapelet_vis_per_s": obs.n_vis * sky.n_shape / (ms * 1e-3),
             "coeff_vis_per_s": nnz * obs.n_vis / (ms * 1e-3),
             "roofline": {"bound": "tensor", "achieved": round(tf, 2), "peak": peak, "unit": "TFLOP/s",
-                         "frac": round(tf / peak, 4), "traffic": None,
+                         "frac": round(tf / peak, 4),
+                         "traffic": traffic_record("k2_shapelet_fornax_traffic.json"),
+                         "traffic_unit": "bytes per launch (one shapelet; ncu dram__bytes_read + write, full size)",
                          "note": "issued bf16 flops (2 k_pad n_pad x 3 products per visibility); useful 2 nnz"},
             "error": {"e_norm": err, "tolerance": 1e-3, "sample": "16 rows x 384 ch vs oracle peel"},
             "lookup_table_basis": {"ms_per_step": round(ms_lut, 4), "e_norm": err_lut,
@@ -524,6 +530,8 @@ def run_case(case: str):
         sky = synth.make_sky(102, 2000, 500, 0)
     elif case == "fornax_small":  # K2: 2 steps of the Fornax array, 2 shapelets at n_max 80
         obs, sky = synth.fornax(n_time=2)
+    elif case == "fornax":        # K2: the full Fornax peel (14 steps), for the one-pass traffic record
+        obs, sky = synth.fornax()
     elif case == "adjoint":       # K4: the full adjoint workload
         obs, sky = synth.adjoint()
     elif case == "calib":         # K7: gain calibration, 128 tiles x 2 steps x 384 ch, 10 iterations
@@ -551,6 +559,8 @@ def run_case(case: str):
         m = ctx.upload(sky)
         if case == "adjoint":
             fn = lambda: ctx.predict_grad(d, m, gains, data, resid=out)  # noqa: E731
+        elif case == "fornax":    # the peel the bench's shapelet report times
+            fn = lambda: ctx.peel(d, m, gains, data, out=out)  # noqa: E731
         else:
             fn = lambda: ctx.predict(d, m, out=out)  # noqa: E731
         work = obs.n_vis * sky.n_comp
@@ -577,7 +587,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the shapelet, adjoint, calibration, truncation, fit and serving reports")
-    ap.add_argument("--case", choices=["mwa_small", "fornax_small", "adjoint", "peel", "calib", "serve"],
+    ap.add_argument("--case", choices=["mwa_small", "fornax_small", "fornax", "adjoint", "peel", "calib", "serve"],
                     help="run one small fixed case for profiling instead of the benchmark")
     args = ap.parse_args()
     if args.case:
