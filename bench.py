@@ -248,7 +248,14 @@ def bench_shapelets(wn, ctx, local, P, torch):
     ms_lut = timed(lambda: ctx.peel(d, m, gains, data, out=out), 10)
     got_lut = out.reshape(obs.n_rows, obs.n_chan)[idx].cpu().numpy()
     err_lut = float(np.abs(got_lut - ref).max() / np.abs(V).max())
+    # the same peel with tf32 operands and one product (kind::tf32)
+    ctx.set_precision(0, wn.WN_SHAPE_TF32)
+    ms_tf32 = timed(lambda: ctx.peel(d, m, gains, data, out=out), 10)
+    got_tf32 = out.reshape(obs.n_rows, obs.n_chan)[idx].cpu().numpy()
+    err_tf32 = float(np.abs(got_tf32 - ref).max() / np.abs(V).max())
     ctx.set_precision(0, wn.WN_SHAPE_BF16X3)
+    tf_tf32 = sum(2.0 * obs.n_vis * kp * npad for kp, npad in pads) / (ms_tf32 * 1e-3) / 1e12  # one product
+    peak_tf32 = peak / 2.0  # tf32 tensor rate: half the bf16 one (nominal ratio)
     m.free()
     # the equivalent multi-scale-CLEAN-like model on the same observation
     _, clean = synth.fornax_clean()
@@ -265,6 +272,11 @@ def bench_shapelets(wn, ctx, local, P, torch):
                          "traffic_unit": "bytes per launch (one shapelet; ncu dram__bytes_read + write, full size)",
                          "note": "issued bf16 flops (2 k_pad n_pad x 3 products per visibility); useful 2 nnz"},
             "error": {"e_norm": err, "tolerance": 1e-3, "sample": "16 rows x 384 ch vs oracle peel"},
+            "tf32": {"ms_per_step": round(ms_tf32, 4), "e_norm": err_tf32,
+                     "roofline": {"bound": "tensor", "achieved": round(tf_tf32, 2), "peak": peak_tf32, "unit": "TFLOP/s",
+                                  "frac": round(tf_tf32 / peak_tf32, 4),
+                                  "peak_basis": "measured bf16 peak x the nominal tf32/bf16 ratio 1/2"},
+                     "note": "tf32 operands rounded to nearest, one product per visibility"},
             "lookup_table_basis": {"ms_per_step": round(ms_lut, 4), "e_norm": err_lut,
                                    "note": "phi_n interpolated from a 1/256-spaced table in L2 instead of the recurrence"},
             "clean_model_40k_ms": round(ms_clean, 3), "clean_over_shapelet_time": round(ms_clean / ms, 2)}

@@ -72,9 +72,13 @@ typedef enum {
 typedef enum {
     WN_SHAPE_BF16X3 = 0, /* bf16 hi+lo split of both operands, three products, FP32 accumulate (default) */
     WN_SHAPE_BF16X1 = 1, /* plain bf16 operands, one product, FP32 accumulate */
-    WN_SHAPE_LUT_BF16X3 = 2 /* as BF16X3, but the Hermite functions are interpolated linearly from a 1-D table
-                               (spacing 1/256, orders 0..127; the look-up tables of Sec. 3.2) instead of the
-                               recurrence; the table (6.8 MB) is built once per context */
+    WN_SHAPE_LUT_BF16X3 = 2, /* as BF16X3, but the Hermite functions are interpolated linearly from a 1-D table
+                                (spacing 1/256, orders 0..127; the look-up tables of Sec. 3.2) instead of the
+                                recurrence; the table (6.8 MB) is built once per context */
+    WN_SHAPE_TF32 = 3        /* tf32 operands (both rounded to nearest from FP32, 10 explicit mantissa bits), one
+                                product, FP32 accumulate.  A tf32 hi+lo split (three products) is not offered:
+                                its two A tiles per block do not fit the kernel's shared memory beside the
+                                coefficient operand. */
 } wn_shape_mode;
 
 /* Device-side error flags (bit mask) reported by wn_device_errors. */

@@ -21,7 +21,7 @@ _lock = threading.Lock()
 
 WN_OK, WN_EINVAL, WN_ENOMEM, WN_ECUDA, WN_ETIMEOUT, WN_EBUSY, WN_ENOTFOUND = range(7)
 WN_PREC_MIXED, WN_PREC_FP64 = 0, 1
-WN_SHAPE_BF16X3, WN_SHAPE_BF16X1, WN_SHAPE_LUT_BF16X3 = 0, 1, 2
+WN_SHAPE_BF16X3, WN_SHAPE_BF16X1, WN_SHAPE_LUT_BF16X3, WN_SHAPE_TF32 = 0, 1, 2, 3
 WN_DEVERR_ANTENNA, WN_DEVERR_TIMEOUT, WN_DEVERR_SKY, WN_DEVERR_CALIB = 0x1, 0x2, 0x4, 0x8
 
 EXPORTED = ("wn_create", "wn_destroy", "wn_last_error", "wn_version", "wn_set_precision", "wn_device_errors",

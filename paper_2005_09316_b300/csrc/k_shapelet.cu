@@ -59,6 +59,7 @@ struct K2Args {
   const __nv_bfloat16* bop;  // this shapelet's packed B operand: hi [n_pad][kp], then lo
   const float* lut;          // basis table (lookup-table mode only)
   int n_pad, nmax, passes, n_chan, n_base, n_tiles, mode, groups;
+  int tf32 = 0;              // operands as tf32 (one product, kind::tf32); else bf16 (passes products)
   long long n_vis;
   float c_amp, alpha, sgn;
   float2* out;
@@ -82,10 +83,23 @@ __host__ __device__ constexpr uint32_t umma_idesc_bf16(int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(K2_M >> 4) << 24);
 }
 
+// Instruction descriptor for kind::tf32: D f32, A and B tf32 (format 2), both K-major, M = 128, N = n.
+__host__ __device__ constexpr uint32_t umma_idesc_tf32(int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(K2_M >> 4) << 24);
+}
+
 __device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
       "l"(a), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
 }
@@ -140,13 +154,18 @@ __host__ __device__ __forceinline__ uint32_t kmaj_off(int row, int k, int rows) 
   return (uint32_t)((((k >> 3) * (rows >> 3) + (row >> 3)) << 7) + ((row & 7) << 4) + ((k & 7) << 1));
 }
 
+// The same for 4-byte (tf32) elements: core matrices of 8 rows x 4 elements.
+__host__ __device__ __forceinline__ uint32_t kmaj_off32(int row, int k, int rows) {
+  return (uint32_t)((((k >> 2) * (rows >> 3) + (row >> 3)) << 7) + ((row & 7) << 4) + ((k & 3) << 2));
+}
+
 struct K2Layout {
   int b_bytes, a_bytes, a0, coef, bars, xfer, total;
 };
 
-__host__ __device__ inline K2Layout k2_layout(int kp, int n_pad, int passes, int groups, int R) {
+__host__ __device__ inline K2Layout k2_layout(int kp, int n_pad, int passes, int groups, int R, bool tf32 = false) {
   K2Layout L;
-  const int parts = passes > 1 ? 2 : 1;
+  const int parts = passes > 1 || tf32 ? 2 : 1;  // bf16 hi + lo, or one 4-byte tf32 element
   L.b_bytes = parts * kp * n_pad * 2;
   L.a_bytes = R * parts * kp * K2_M * 2;  // one group's A: R blocks of 128 rows (hi [+ lo])
   L.a0 = (L.b_bytes + 1023) & ~1023;
@@ -178,10 +197,19 @@ __device__ __forceinline__ void store_bf16_split(float (&v)[8], unsigned char* a
   if (a_lo) *reinterpret_cast<uint4*>(a_lo + off) = *reinterpret_cast<uint4*>(l);
 }
 
+// Columns k0 .. k0 + 7 of one row as tf32 (rounded to nearest) into a K-major tile of 4-byte elements:
+// two core matrices, 16 row groups x 128 B apart.
+__device__ __forceinline__ void store_tf32(const float (&v)[8], unsigned char* a, int row, int k0) {
+  const uint32_t off = kmaj_off32(row, k0, K2_M);
+  *reinterpret_cast<float4*>(a + off) = make_float4(to_tf32(v[0]), to_tf32(v[1]), to_tf32(v[2]), to_tf32(v[3]));
+  *reinterpret_cast<float4*>(a + off + (K2_M >> 3) * 128) =
+      make_float4(to_tf32(v[4]), to_tf32(v[5]), to_tf32(v[6]), to_tf32(v[7]));
+}
+
 template <int KP, int R, bool SCALED>
 __device__ __forceinline__ void produce_rows_run(const float (&x)[R], float (&p)[R], float (&p_prev)[R], float (&scale)[R],
-                                                 int (&E)[R], unsigned char* a_base, int blk, bool split, int row,
-                                                 const float4* ca, const float4* cb, const float2* ca2,
+                                                 int (&E)[R], unsigned char* a_base, int blk, bool split, bool tf32,
+                                                 int row, const float4* ca, const float4* cb, const float2* ca2,
                                                  const float2* cb2) {
   if constexpr (R == 2 && !SCALED) {
     // two rows as one f32x2 recurrence: {p_r0, p_r1}' = {a,a} {x0,x1} {p_r0,p_r1} + {-b,-b} {p'_r0,p'_r1}
@@ -201,7 +229,8 @@ __device__ __forceinline__ void produce_rows_run(const float (&x)[R], float (&p)
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
         unsigned char* hi = a_base + r * blk;
-        store_bf16_split(v[r], hi, split ? hi + KP * K2_M * 2 : nullptr, kmaj_off(row, k0, K2_M));
+        if (tf32) store_tf32(v[r], hi, row, k0);
+        else store_bf16_split(v[r], hi, split ? hi + KP * K2_M * 2 : nullptr, kmaj_off(row, k0, K2_M));
       }
     }
     return;
@@ -236,7 +265,8 @@ __device__ __forceinline__ void produce_rows_run(const float (&x)[R], float (&p)
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       unsigned char* hi = a_base + r * blk;
-      store_bf16_split(v[r], hi, split ? hi + KP * K2_M * 2 : nullptr, kmaj_off(row, k0, K2_M));
+      if (tf32) store_tf32(v[r], hi, row, k0);
+      else store_bf16_split(v[r], hi, split ? hi + KP * K2_M * 2 : nullptr, kmaj_off(row, k0, K2_M));
     }
   }
 }
@@ -288,7 +318,7 @@ __device__ __forceinline__ void produce_rows_lut(const float (&x)[R], int nmax, 
 
 template <int KP, int R>
 __device__ __forceinline__ void produce_rows(const float (&x)[R], int nmax, const bool (&valid)[R], unsigned char* a_base,
-                                             int blk, bool split, int row, const float4* ca, const float4* cb,
+                                             int blk, bool split, bool tf32, int row, const float4* ca, const float4* cb,
                                              const float2* ca2, const float2* cb2) {
   const float xcut = sqrtf(2.0f * nmax + 1.0f) + 10.0f;
   bool zero[R], fast = true;
@@ -309,8 +339,8 @@ __device__ __forceinline__ void produce_rows(const float (&x)[R], int nmax, cons
     p[r] = zero[r] ? 0.f : exp2f((float)E[r] - hx[r]);
     scale[r] = __int_as_float(max(0, 127 - E[r]) << 23);  // 2^-E (0 below 2^-126)
   }
-  if (fast) produce_rows_run<KP, R, false>(x, p, p_prev, scale, E, a_base, blk, split, row, ca, cb, ca2, cb2);
-  else produce_rows_run<KP, R, true>(x, p, p_prev, scale, E, a_base, blk, split, row, ca, cb, ca2, cb2);
+  if (fast) produce_rows_run<KP, R, false>(x, p, p_prev, scale, E, a_base, blk, split, tf32, row, ca, cb, ca2, cb2);
+  else produce_rows_run<KP, R, true>(x, p, p_prev, scale, E, a_base, blk, split, tf32, row, ca, cb, ca2, cb2);
 }
 
 // Epilogue dot product of one accumulator chunk (16 n2 values: columns 2 n2, 2 n2 + 1 = Re, Im) with
@@ -414,7 +444,7 @@ template <int KP, int R, bool LUT>
 __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int ng = a.groups;  // tile parities in flight (2, or 1 when two A buffers do not fit)
-  const K2Layout lay = k2_layout(KP, a.n_pad, a.passes, ng, R);
+  const K2Layout lay = k2_layout(KP, a.n_pad, a.passes, ng, R, a.tf32 != 0);
   const int blk = lay.a_bytes / R;  // one 128-row block of A (hi [+ lo])
   uint64_t* bfull = reinterpret_cast<uint64_t*>(smem + lay.bars);
   uint64_t* afull = bfull + 1;                // [parity] producer -> MMA: A written
@@ -468,7 +498,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
     if ((threadIdx.x & 31) == 0) {
       mbar_arrive_expect_tx(bfull, (uint32_t)lay.b_bytes);
       tma_bulk_g2s(smem, a.bop, (uint32_t)lay.b_bytes, bfull);
-      const uint32_t idesc = umma_idesc_bf16(a.n_pad);
+      const uint32_t idesc = umma_idesc_bf16(a.n_pad), idesc32 = umma_idesc_tf32(a.n_pad);
       const uint32_t b_hi = smem_u32(smem), b_lo = b_hi + (uint32_t)(KP * a.n_pad * 2);
       const uint32_t lbo_b = (uint32_t)(a.n_pad >> 3) << 7, lbo_a = (uint32_t)(K2_M >> 3) << 7;
       bool ok = k2_wait(bfull, 0, a.err);
@@ -483,6 +513,15 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
           const uint32_t a_hi = smem_u32(smem + lay.a0 + sp * lay.a_bytes + r * blk);
           const uint32_t a_lo = a_hi + (uint32_t)(KP * K2_M * 2);
           const uint32_t d = tmem + (uint32_t)((sp * R + r) * a.n_pad);
+          if (a.tf32) {  // K = 8 per instruction: two core matrices of 4-byte elements
+#pragma unroll
+            for (int kk = 0; kk < KP / 8; ++kk) {
+              const uint64_t da = umma_desc(a_hi + (uint32_t)(2 * kk) * lbo_a, lbo_a, 128);
+              const uint64_t db = umma_desc(b_hi + (uint32_t)(2 * kk) * lbo_b, lbo_b, 128);
+              umma_tf32(d, da, db, idesc32, kk > 0 ? 1u : 0u);
+            }
+            continue;
+          }
 #pragma unroll 1
           for (int p = 0; p < a.passes; ++p) {
             const uint32_t aa = (p == 2) ? a_lo : a_hi;  // hi*hi, hi*lo, lo*hi
@@ -559,7 +598,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
       load_x(it + ng, valid, xs, nu);
       if (j > 0 && !k2_wait(&mdone[sp], (j - 1) & 1, a.err)) break;  // MMA(j-1) has read A
       if (LUT) produce_rows_lut<KP, R>(x, a.nmax, v0, a_base, blk, a.passes > 1, m, a.lut);
-      else produce_rows<KP, R>(x, a.nmax, v0, a_base, blk, a.passes > 1, m, ca, cb, ca2, cb2);
+      else produce_rows<KP, R>(x, a.nmax, v0, a_base, blk, a.passes > 1, a.tf32 != 0, m, ca, cb, ca2, cb2);
       fence_async_smem();
       mbar_arrive(&afull[sp]);
       // the previous tile's output, while the MMA of this one runs
@@ -849,7 +888,8 @@ int launch_shapelets_ws(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* ou
   if (int r = k2_setup_constants(ctx->device, st)) return r;
   k2_chaninfo<<<(o.n_chan + 255) / 256, 256, 0, st>>>(o.freq, o.n_chan, o.nu0, chaninfo);
   const long long n_vis = (long long)o.n_rows * o.n_chan;
-  const int passes = ctx->shape_mode == WN_SHAPE_BF16X1 ? 1 : 3;
+  const bool tf32 = ctx->shape_mode == WN_SHAPE_TF32;
+  const int passes = ctx->shape_mode == WN_SHAPE_BF16X1 || tf32 ? 1 : 3;
   const float* lut = nullptr;
   if (ctx->shape_mode == WN_SHAPE_LUT_BF16X3)
     if (int r = k2_lut(ctx, st, &lut)) return r;
@@ -863,7 +903,8 @@ int launch_shapelets_ws(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* ou
     K2Args a;
     a.rowinfo = rowinfo;
     a.chaninfo = chaninfo;
-    a.bop = M->bop + h.b_off;
+    a.bop = tf32 ? reinterpret_cast<const __nv_bfloat16*>(M->bop32 + h.b_off / 2) : M->bop + h.b_off;
+    a.tf32 = tf32 ? 1 : 0;
     a.lut = lut;
     a.n_pad = h.n_pad;
     a.nmax = h.nmax;
@@ -884,14 +925,14 @@ int launch_shapelets_ws(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* ou
     // columns fit; else one
     a.groups = K2_GROUPS;
     int R = 2;
-    K2Layout lay = k2_layout(h.k_pad, h.n_pad, passes, a.groups, R);
+    K2Layout lay = k2_layout(h.k_pad, h.n_pad, passes, a.groups, R, tf32);
     if (h.n_pad > 128 || lay.total > 227 * 1024) {
       R = 1;
-      lay = k2_layout(h.k_pad, h.n_pad, passes, a.groups, R);
+      lay = k2_layout(h.k_pad, h.n_pad, passes, a.groups, R, tf32);
     }
     if (lay.total > 227 * 1024) {  // large n_max in the split mode: one tile in flight
       a.groups = 1;
-      lay = k2_layout(h.k_pad, h.n_pad, passes, 1, R);
+      lay = k2_layout(h.k_pad, h.n_pad, passes, 1, R, tf32);
     }
     if (lay.total > 227 * 1024) return set_error(WN_EINVAL, "shapelet operand does not fit in shared memory");
     const int n_tiles = (int)((n_vis + K2_M * R - 1) / (K2_M * R));

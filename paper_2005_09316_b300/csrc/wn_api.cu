@@ -115,6 +115,7 @@ static void free_model(Model* M) {
   cudaFree(M->pg);
   cudaFree(M->sh);
   cudaFree(M->bop);
+  cudaFree(M->bop32);
   cudaFree(M->raw);
   cudaFree(M->s_meta);
   cudaFree(M->s_coeff);
@@ -216,7 +217,8 @@ void wn_destroy(wn_ctx* ctx) {
 int wn_set_precision(wn_ctx* ctx, int precision, int shape_mode) {
   if (!ctx) return set_error(WN_EINVAL, "ctx is NULL");
   if (precision != WN_PREC_MIXED && precision != WN_PREC_FP64) return set_error(WN_EINVAL, "unknown precision");
-  if (shape_mode != WN_SHAPE_BF16X3 && shape_mode != WN_SHAPE_BF16X1 && shape_mode != WN_SHAPE_LUT_BF16X3)
+  if (shape_mode != WN_SHAPE_BF16X3 && shape_mode != WN_SHAPE_BF16X1 && shape_mode != WN_SHAPE_LUT_BF16X3 &&
+      shape_mode != WN_SHAPE_TF32)
     return set_error(WN_EINVAL, "unknown shape mode");
   ctx->precision = precision;
   ctx->shape_mode = shape_mode;
@@ -345,6 +347,7 @@ int wn_sky_upload(wn_ctx* ctx, const wn_sky* s, int* model_id, void* stream) {
   cudaError_t e = dalloc(&M->pg, (size_t)s->n_point + s->n_gauss, total);
   if (e == cudaSuccess) e = dalloc(&M->sh, (size_t)s->n_shape, total);
   if (e == cudaSuccess) e = dalloc(&M->bop, M->bop_elems, total);
+  if (e == cudaSuccess) e = dalloc(&M->bop32, M->bop_elems / 2, total);
   if (e == cudaSuccess) e = dalloc(&M->raw, std::max<size_t>(n_raw, 1), total);
   if (e == cudaSuccess) e = dalloc(&M->s_meta, 2 * (size_t)s->n_shape + 1 + 2 * (size_t)M->nnz, total);
   if (e == cudaSuccess) e = dalloc(&M->s_coeff, (size_t)M->nnz, total);

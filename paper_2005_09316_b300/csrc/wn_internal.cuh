@@ -74,6 +74,7 @@ struct Model {
   ShapeRec* sh = nullptr;          // [n_shape]
   std::vector<ShapeRec> sh_host;   // host copy of the headers (sizes, offsets)
   __nv_bfloat16* bop = nullptr;    // dense shapelet B operands (hi then lo per shapelet), UMMA layout
+  float* bop32 = nullptr;          // the same operands as tf32 (K-major, 4-byte elements): shapelet q at b_off / 2
   size_t bop_elems = 0;
   // raw FP64 copies for the FP64 form and the adjoint
   double* raw = nullptr;           // l, m, flux, alpha, nu_ref [n_comp] each; g_maj,g_min,g_pa; s_b1,s_b2,s_pa
@@ -216,6 +217,14 @@ __device__ __forceinline__ float reduce_turns(float th, float tl, float ah, floa
   const float kShift = 12582912.0f;
   float n = __fsub_rn(__fadd_rn(p, kShift), kShift);
   return __fadd_rn(__fsub_rn(p, n), e);
+}
+
+// x rounded to the nearest tf32 (10 explicit mantissa bits, ties away from zero), as an FP32 value with
+// the 13 low mantissa bits zero: what a tf32 tensor-core operand reads.
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
 }
 
 // Split a double into an unevaluated float pair hi + lo.

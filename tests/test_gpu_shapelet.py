@@ -90,6 +90,20 @@ def test_lookup_table_basis_mode(wn, ctx, nmax):
     assert e_norm(got, ref) <= 1e-3, e_norm(got, ref)
 
 
+@pytest.mark.parametrize("nmaxs,keep", [([30], None), ([80, 80], 1500), ([10, 41, 3], None)])
+def test_tf32_mode(wn, ctx, nmaxs, keep):
+    """tf32 operands, one product (kind::tf32): each operand carries a relative rounding error of at most
+    2^-11, so the contraction stays inside the 1e-3 target of the tensor-core path; the same sky in the
+    default bf16 hi+lo mode is an order of magnitude closer."""
+    obs = synth.make_obs(31, 14, 2, synth.uniform_channels(167e6, 80e3, 48), layout="mwa", max_baseline=5000.0,
+                         dec0=-37.2 * synth.DEG)
+    sky = shapelet_sky(32, nmaxs, keep=keep)
+    ref = oracle_rows(obs, sky, np.arange(obs.n_rows))
+    got = predict(wn, ctx, obs, sky, 0, wn.WN_SHAPE_TF32)
+    assert e_norm(got, ref) <= 1e-3, e_norm(got, ref)
+    assert e_norm(predict(wn, ctx, obs, sky, 0, wn.WN_SHAPE_BF16X3), ref) <= 1e-4
+
+
 def test_plain_bf16_mode(wn, ctx):
     obs = synth.make_obs(3, 12, 2, synth.uniform_channels(160e6, 1.5e6, 40), layout="mwa", max_baseline=3000.0)
     sky = shapelet_sky(4, [30])
