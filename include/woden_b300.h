@@ -187,6 +187,12 @@ WN_API int wn_sky_bytes(wn_ctx* ctx, int model_id, size_t* bytes_out);
  * host_out may be NULL to query k_pad and n_pad; otherwise it must hold bytes >= 4 k_pad n_pad.
  * Synchronous.  WN_ENOTFOUND for an unknown model, WN_EINVAL for q outside [0, n_shape) or a short
  * buffer. */
+/* The tf32 copy of the same operand (WN_SHAPE_TF32), copied to HOST memory: k_pad x n_pad FP32 values,
+ * each RN_tf32 (ties away from zero) of float(value), in the K-major layout with 8 x 4 core matrices:
+ * element (n, k) at ((k/4) (n_pad/8) + n/8) 32 + (n%8) 4 + k%4.  Same arguments, sizes and errors as
+ * wn_sky_shapelet_operand (bytes >= 4 k_pad n_pad). */
+WN_API int wn_sky_shapelet_operand_tf32(wn_ctx* ctx, int model_id, int q, void* host_out, size_t bytes, int* k_pad,
+                                        int* n_pad);
 WN_API int wn_sky_shapelet_operand(wn_ctx* ctx, int model_id, int q, void* host_out, size_t bytes, int* k_pad,
                                    int* n_pad);
 

@@ -7,7 +7,8 @@ TEST INFRASTRUCTURE ONLY: imported by tests/, by ``__graft_entry__.smoke()`` and
 The arithmetic lives in ``wn_oracle.c`` (plain C, FP64, loops in the paper's order); this module
 builds it with gcc, loads it with ctypes and marshals numpy arrays.  The calibration loop is numpy
 (design matrix written out, numpy's solve for the normal equations).  It also holds the oracle's own
-packers (triangular coefficient index, parity split of the (-i)^(n1+n2) phase, bf16 hi/lo split),
+packers (triangular coefficient index, parity split of the (-i)^(n1+n2) phase, bf16 hi/lo split, tf32
+rounding),
 written from the same definitions the CUDA packer follows, so the two can be compared bit for bit.
 
 Parity pins (tests/test_oracle_pins.py) tie every function here to closed forms, library
@@ -237,6 +238,25 @@ def bf16_hi_lo(x) -> tuple[np.ndarray, np.ndarray]:
     hi = f32_to_bf16_bits(x32)
     lo = f32_to_bf16_bits((x32 - bf16_bits_to_f32(hi)).astype(np.float32))
     return hi, lo
+
+
+def f32_to_tf32_bits(x32) -> np.ndarray:
+    """float32 values rounded to the nearest tf32 (10 explicit mantissa bits, ties away from zero), as
+    float32 bit patterns: half the range of the 13 dropped bits is added to the magnitude, then they are
+    cleared."""
+    b = np.asarray(x32, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    return ((b + 0x1000) & 0xFFFFE000).astype(np.uint32)
+
+
+def pack_coeff_tf32(nmax: int, n1, n2, c, k_pad: int, n_pad: int) -> np.ndarray:
+    """The dense B operand of pack_coeff_bf16 as tf32 bit patterns [n_pad][k_pad] (one element per entry,
+    RN_tf32(float32(value))), for the tensor-core tf32 mode."""
+    re, im = parity_split(nmax, n1, n2, c)
+    dense = np.zeros((n_pad, k_pad))
+    for b in range(nmax + 1):
+        dense[2 * b, :nmax + 1] = re[:, b]
+        dense[2 * b + 1, :nmax + 1] = im[:, b]
+    return f32_to_tf32_bits(dense.astype(np.float32))
 
 
 def pack_coeff_bf16(nmax: int, n1, n2, c, k_pad: int, n_pad: int):

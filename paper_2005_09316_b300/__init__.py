@@ -29,7 +29,8 @@ EXPORTED = ("wn_create", "wn_destroy", "wn_last_error", "wn_version", "wn_set_pr
             "wn_predict_grad", "wn_predict_static", "wn_server_create", "wn_server_destroy", "wn_server_submit",
             "wn_server_poll", "wn_server_wait", "wn_server_copy", "wn_server_release", "wn_server_cancel",
             "wn_server_stats", "wn_calibrate", "wn_fit_shapelets", "wn_pipe_rates",
-            "wn_phasor_loop_rate", "wn_sky_shapelet_operand", "wn_selftest_timeout", "wn_mma_rate", "wn_set_trace", "wn_debug_fail_allocs")
+            "wn_phasor_loop_rate", "wn_sky_shapelet_operand", "wn_selftest_timeout", "wn_mma_rate", "wn_set_trace", "wn_debug_fail_allocs",
+            "wn_sky_shapelet_operand_tf32")
 
 
 class WnError(RuntimeError):
@@ -109,6 +110,7 @@ def load(build_if_missing: bool = True):
         L.wn_mma_rate.argtypes = [P, ctypes.POINTER(dbl)]
         L.wn_set_trace.argtypes = [P, ctypes.c_int]
         L.wn_debug_fail_allocs.argtypes = [ctypes.c_int]
+        L.wn_sky_shapelet_operand_tf32.argtypes = L.wn_sky_shapelet_operand.argtypes
         for name in EXPORTED:
             if name not in ("wn_destroy", "wn_last_error", "wn_version", "wn_server_destroy"):
                 getattr(L, name).restype = ctypes.c_int
@@ -239,6 +241,16 @@ class Model:
                                               ctypes.byref(npd)))
         half = kp.value * npd.value
         return buf[:half], buf[half:], kp.value, npd.value
+
+    def shapelet_operand_tf32(self, q: int):
+        """Shapelet q's tf32 operand as raw FP32 bit patterns (uint32, k_pad x n_pad in the K-major order of
+        8 x 4 core matrices) with k_pad and n_pad."""
+        kp, npd = ctypes.c_int(), ctypes.c_int()
+        f = load().wn_sky_shapelet_operand_tf32
+        _check(f(self.ctx.h, self.id, q, None, 0, ctypes.byref(kp), ctypes.byref(npd)))
+        buf = np.empty(kp.value * npd.value, dtype=np.uint32)
+        _check(f(self.ctx.h, self.id, q, buf.ctypes.data, buf.nbytes, ctypes.byref(kp), ctypes.byref(npd)))
+        return buf, kp.value, npd.value
 
     def free(self):
         if self.id:

@@ -453,6 +453,23 @@ int wn_sky_shapelet_operand(wn_ctx* ctx, int model_id, int q, void* host_out, si
   return ok();
 }
 
+int wn_sky_shapelet_operand_tf32(wn_ctx* ctx, int model_id, int q, void* host_out, size_t bytes, int* k_pad, int* n_pad) {
+  if (!ctx || !k_pad || !n_pad) return set_error(WN_EINVAL, "NULL argument");
+  Model* M = find_model(ctx, model_id);
+  if (!M) return set_error(WN_ENOTFOUND, "unknown model id");
+  if (q < 0 || q >= M->n_shape) return set_error(WN_EINVAL, "shapelet index out of range");
+  const ShapeRec& h = M->sh_host[q];
+  *k_pad = h.k_pad;
+  *n_pad = h.n_pad;
+  if (!host_out) return ok();
+  const size_t need = (size_t)4 * h.k_pad * h.n_pad;
+  if (bytes < need) return set_error(WN_EINVAL, "wn_sky_shapelet_operand_tf32: buffer shorter than 4 k_pad n_pad bytes");
+  DeviceGuard g(ctx->device);
+  cudaError_t e = cudaMemcpy(host_out, M->bop32 + h.b_off / 2, need, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "wn_sky_shapelet_operand_tf32 copy");
+  return ok();
+}
+
 int wn_predict(wn_ctx* ctx, const wn_obs* obs, int model_id, void* vis_c64, int accumulate, void* stream) {
   TraceRange trace_range(ctx, "wn_predict");
   if (!ctx || !vis_c64) return set_error(WN_EINVAL, "NULL argument");

@@ -78,6 +78,26 @@ def test_packed_operand_bit_exact_with_the_oracle_packer(wn, ctx, seed, nmaxs, k
     m.free()
 
 
+@pytest.mark.parametrize("seed,nmaxs,keep", [(41, [10], None), (42, [80, 80], 1500), (43, [3, 60, 127], None)])
+def test_tf32_operand_bit_exact_with_the_oracle_packer(wn, ctx, seed, nmaxs, keep):
+    """The tf32 copy of the coefficient operand (WN_SHAPE_TF32) equals the oracle's restatement of it
+    (RN_tf32 of float(value), ties away from zero, zero padding), bit for bit, in the K-major order of
+    8 x 4 core matrices."""
+    sky = shapelet_sky(seed, nmaxs, keep=keep)
+    m = ctx.upload(sky)
+    for q in range(sky.n_shape):
+        got, kp, npd = m.shapelet_operand_tf32(q)
+        o0, o1 = sky.s_off[q], sky.s_off[q + 1]
+        n1, n2, c = sky.s_n1[o0:o1], sky.s_n2[o0:o1], sky.s_coeff[o0:o1]
+        ne = int((n1 + n2).max())
+        ref = oracle.pack_coeff_tf32(ne, n1, n2, c, kp, npd)  # [n_pad][k_pad]
+        n = np.arange(npd)[:, None]
+        k = np.arange(kp)[None, :]
+        at = ((k >> 2) * (npd >> 3) + (n >> 3)) * 32 + (n & 7) * 4 + (k & 3)
+        assert np.array_equal(got[at], ref), f"shapelet {q}"
+    m.free()
+
+
 @pytest.mark.parametrize("nmax", [5, 40, 80, 127])
 def test_lookup_table_basis_mode(wn, ctx, nmax):
     """Hermite functions interpolated from the 1-D table (spacing 1/256) instead of the recurrence: the

@@ -398,3 +398,25 @@ def test_oracle_threads_do_not_change_results():
     a = oracle.predict(uvw, obs.freq, obs.dec0, sky, n_threads=1)
     b = oracle.predict(uvw, obs.freq, obs.dec0, sky, n_threads=4)
     assert np.array_equal(a, b)
+
+
+def test_tf32_rounding_is_nearest_with_ties_away_from_zero():
+    """oracle.f32_to_tf32_bits against its definition, without its formula: the result keeps 10 explicit
+    mantissa bits (the 13 low bits clear); it is the tf32 value nearest the input, found here by
+    comparing the two tf32 neighbours that bracket it; ties go away from zero."""
+    rng = np.random.default_rng(11)
+    x = np.concatenate([rng.standard_normal(20000) * 10.0 ** rng.integers(-20, 20, 20000),
+                        np.array([1.0, -1.0, 0.0, 3.0e-39, -2.5e-38])]).astype(np.float32)
+    # exact ties: a tf32 value plus half its last-place unit
+    base = (rng.standard_normal(200).astype(np.float32).view(np.uint32) & np.uint32(0xFFFFE000))
+    ties = (base | np.uint32(0x1000)).view(np.float32)
+    xs = np.concatenate([x, ties])
+    got = oracle.f32_to_tf32_bits(xs)
+    assert np.all(got & np.uint32(0x1FFF) == 0)
+    b = xs.view(np.uint32)
+    lo = (b & np.uint32(0xFFFFE000)).view(np.float32).astype(np.float64)          # toward zero
+    hi = ((b & np.uint32(0xFFFFE000)) + np.uint32(0x2000)).view(np.float32).astype(np.float64)  # away
+    x64 = xs.astype(np.float64)
+    d_lo, d_hi = np.abs(x64 - lo), np.abs(hi - x64)
+    want = np.where(d_hi <= d_lo, hi, lo)   # nearest; at a tie (equal distance) the one away from zero
+    assert np.array_equal(got.view(np.float32).astype(np.float64), want)
