@@ -59,7 +59,6 @@ struct K2Args {
   const __nv_bfloat16* bop;  // this shapelet's packed B operand: hi [n_pad][kp], then lo
   const float* lut;          // basis table (lookup-table mode only)
   int n_pad, nmax, passes, n_chan, n_base, n_tiles, mode, groups;
-  int tf32 = 0;              // operands as tf32 (one product, kind::tf32); else bf16 (passes products)
   long long n_vis;
   float c_amp, alpha, sgn;
   float2* out;
@@ -206,10 +205,10 @@ __device__ __forceinline__ void store_tf32(const float (&v)[8], unsigned char* a
       make_float4(to_tf32(v[4]), to_tf32(v[5]), to_tf32(v[6]), to_tf32(v[7]));
 }
 
-template <int KP, int R, bool SCALED>
+template <int KP, int R, bool SCALED, bool TF32>
 __device__ __forceinline__ void produce_rows_run(const float (&x)[R], float (&p)[R], float (&p_prev)[R], float (&scale)[R],
-                                                 int (&E)[R], unsigned char* a_base, int blk, bool split, bool tf32,
-                                                 int row, const float4* ca, const float4* cb, const float2* ca2,
+                                                 int (&E)[R], unsigned char* a_base, int blk, bool split, int row,
+                                                 const float4* ca, const float4* cb, const float2* ca2,
                                                  const float2* cb2) {
   if constexpr (R == 2 && !SCALED) {
     // two rows as one f32x2 recurrence: {p_r0, p_r1}' = {a,a} {x0,x1} {p_r0,p_r1} + {-b,-b} {p'_r0,p'_r1}
@@ -229,7 +228,7 @@ __device__ __forceinline__ void produce_rows_run(const float (&x)[R], float (&p)
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
         unsigned char* hi = a_base + r * blk;
-        if (tf32) store_tf32(v[r], hi, row, k0);
+        if constexpr (TF32) store_tf32(v[r], hi, row, k0);
         else store_bf16_split(v[r], hi, split ? hi + KP * K2_M * 2 : nullptr, kmaj_off(row, k0, K2_M));
       }
     }
@@ -265,7 +264,7 @@ __device__ __forceinline__ void produce_rows_run(const float (&x)[R], float (&p)
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       unsigned char* hi = a_base + r * blk;
-      if (tf32) store_tf32(v[r], hi, row, k0);
+      if constexpr (TF32) store_tf32(v[r], hi, row, k0);
       else store_bf16_split(v[r], hi, split ? hi + KP * K2_M * 2 : nullptr, kmaj_off(row, k0, K2_M));
     }
   }
@@ -316,9 +315,9 @@ __device__ __forceinline__ void produce_rows_lut(const float (&x)[R], int nmax, 
   }
 }
 
-template <int KP, int R>
+template <int KP, int R, bool TF32>
 __device__ __forceinline__ void produce_rows(const float (&x)[R], int nmax, const bool (&valid)[R], unsigned char* a_base,
-                                             int blk, bool split, bool tf32, int row, const float4* ca, const float4* cb,
+                                             int blk, bool split, int row, const float4* ca, const float4* cb,
                                              const float2* ca2, const float2* cb2) {
   const float xcut = sqrtf(2.0f * nmax + 1.0f) + 10.0f;
   bool zero[R], fast = true;
@@ -339,8 +338,8 @@ __device__ __forceinline__ void produce_rows(const float (&x)[R], int nmax, cons
     p[r] = zero[r] ? 0.f : exp2f((float)E[r] - hx[r]);
     scale[r] = __int_as_float(max(0, 127 - E[r]) << 23);  // 2^-E (0 below 2^-126)
   }
-  if (fast) produce_rows_run<KP, R, false>(x, p, p_prev, scale, E, a_base, blk, split, tf32, row, ca, cb, ca2, cb2);
-  else produce_rows_run<KP, R, true>(x, p, p_prev, scale, E, a_base, blk, split, tf32, row, ca, cb, ca2, cb2);
+  if (fast) produce_rows_run<KP, R, false, TF32>(x, p, p_prev, scale, E, a_base, blk, split, row, ca, cb, ca2, cb2);
+  else produce_rows_run<KP, R, true, TF32>(x, p, p_prev, scale, E, a_base, blk, split, row, ca, cb, ca2, cb2);
 }
 
 // Epilogue dot product of one accumulator chunk (16 n2 values: columns 2 n2, 2 n2 + 1 = Re, Im) with
@@ -440,11 +439,13 @@ __device__ __forceinline__ void k2_out_store(const K2Args& a, long long vis, con
   else a.out[idx] = make_float2(o.base.x - (o.G.x * zr - o.G.y * zi), o.base.y - (o.G.x * zi + o.G.y * zr));
 }
 
-template <int KP, int R, bool LUT>
+// FORM: 0 = bf16 operands, basis by the recurrence; 1 = bf16, basis from the lookup table; 2 = tf32.
+template <int KP, int R, int FORM>
 __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
+  constexpr bool LUT = FORM == 1, TF32 = FORM == 2;
   extern __shared__ __align__(1024) unsigned char smem[];
   const int ng = a.groups;  // tile parities in flight (2, or 1 when two A buffers do not fit)
-  const K2Layout lay = k2_layout(KP, a.n_pad, a.passes, ng, R, a.tf32 != 0);
+  const K2Layout lay = k2_layout(KP, a.n_pad, a.passes, ng, R, TF32);
   const int blk = lay.a_bytes / R;  // one 128-row block of A (hi [+ lo])
   uint64_t* bfull = reinterpret_cast<uint64_t*>(smem + lay.bars);
   uint64_t* afull = bfull + 1;                // [parity] producer -> MMA: A written
@@ -513,7 +514,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
           const uint32_t a_hi = smem_u32(smem + lay.a0 + sp * lay.a_bytes + r * blk);
           const uint32_t a_lo = a_hi + (uint32_t)(KP * K2_M * 2);
           const uint32_t d = tmem + (uint32_t)((sp * R + r) * a.n_pad);
-          if (a.tf32) {  // K = 8 per instruction: two core matrices of 4-byte elements
+          if constexpr (TF32) {  // K = 8 per instruction: two core matrices of 4-byte elements
 #pragma unroll
             for (int kk = 0; kk < KP / 8; ++kk) {
               const uint64_t da = umma_desc(a_hi + (uint32_t)(2 * kk) * lbo_a, lbo_a, 128);
@@ -598,7 +599,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
       load_x(it + ng, valid, xs, nu);
       if (j > 0 && !k2_wait(&mdone[sp], (j - 1) & 1, a.err)) break;  // MMA(j-1) has read A
       if (LUT) produce_rows_lut<KP, R>(x, a.nmax, v0, a_base, blk, a.passes > 1, m, a.lut);
-      else produce_rows<KP, R>(x, a.nmax, v0, a_base, blk, a.passes > 1, a.tf32 != 0, m, ca, cb, ca2, cb2);
+      else produce_rows<KP, R, TF32>(x, a.nmax, v0, a_base, blk, a.passes > 1, m, ca, cb, ca2, cb2);
       fence_async_smem();
       mbar_arrive(&afull[sp]);
       // the previous tile's output, while the MMA of this one runs
@@ -805,39 +806,41 @@ static int k2_setup_constants(int device, cudaStream_t st) {
   return WN_OK;
 }
 
-template <int KP, int R, bool LUT>
+template <int KP, int R, int FORM>
 static cudaError_t k2_launch_t(const K2Args& a, int grid, int smem, cudaStream_t st) {
-  auto fn = k2_shapelet<KP, R, LUT>;
+  auto fn = k2_shapelet<KP, R, FORM>;
   cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(fn));
   if (e != cudaSuccess) return e;
   fn<<<grid, K2_THREADS, smem, st>>>(a);
   return cudaGetLastError();
 }
 
-template <bool LUT>
+template <int FORM>
 static cudaError_t k2_dispatch_t(const K2Args& a, int k_pad, int R, int grid, int smem, cudaStream_t st) {
   if (R == 2) {
     switch (k_pad) {
-      case 16: return k2_launch_t<16, 2, LUT>(a, grid, smem, st);
-      case 32: return k2_launch_t<32, 2, LUT>(a, grid, smem, st);
-      case 48: return k2_launch_t<48, 2, LUT>(a, grid, smem, st);
-      default: return k2_launch_t<64, 2, LUT>(a, grid, smem, st);
+      case 16: return k2_launch_t<16, 2, FORM>(a, grid, smem, st);
+      case 32: return k2_launch_t<32, 2, FORM>(a, grid, smem, st);
+      case 48: return k2_launch_t<48, 2, FORM>(a, grid, smem, st);
+      default: return k2_launch_t<64, 2, FORM>(a, grid, smem, st);
     }
   }
   switch (k_pad) {
-    case 16: return k2_launch_t<16, 1, LUT>(a, grid, smem, st);
-    case 32: return k2_launch_t<32, 1, LUT>(a, grid, smem, st);
-    case 48: return k2_launch_t<48, 1, LUT>(a, grid, smem, st);
-    case 64: return k2_launch_t<64, 1, LUT>(a, grid, smem, st);
-    case 80: return k2_launch_t<80, 1, LUT>(a, grid, smem, st);
-    case 96: return k2_launch_t<96, 1, LUT>(a, grid, smem, st);
-    case 112: return k2_launch_t<112, 1, LUT>(a, grid, smem, st);
-    default: return k2_launch_t<128, 1, LUT>(a, grid, smem, st);
+    case 16: return k2_launch_t<16, 1, FORM>(a, grid, smem, st);
+    case 32: return k2_launch_t<32, 1, FORM>(a, grid, smem, st);
+    case 48: return k2_launch_t<48, 1, FORM>(a, grid, smem, st);
+    case 64: return k2_launch_t<64, 1, FORM>(a, grid, smem, st);
+    case 80: return k2_launch_t<80, 1, FORM>(a, grid, smem, st);
+    case 96: return k2_launch_t<96, 1, FORM>(a, grid, smem, st);
+    case 112: return k2_launch_t<112, 1, FORM>(a, grid, smem, st);
+    default: return k2_launch_t<128, 1, FORM>(a, grid, smem, st);
   }
 }
 
-static cudaError_t k2_dispatch(const K2Args& a, int k_pad, int R, bool lut, int grid, int smem, cudaStream_t st) {
-  return lut ? k2_dispatch_t<true>(a, k_pad, R, grid, smem, st) : k2_dispatch_t<false>(a, k_pad, R, grid, smem, st);
+static cudaError_t k2_dispatch(const K2Args& a, int k_pad, int R, int form, int grid, int smem, cudaStream_t st) {
+  if (form == 1) return k2_dispatch_t<1>(a, k_pad, R, grid, smem, st);
+  if (form == 2) return k2_dispatch_t<2>(a, k_pad, R, grid, smem, st);
+  return k2_dispatch_t<0>(a, k_pad, R, grid, smem, st);
 }
 
 // The basis table of the lookup-table mode: phi_0..phi_127 in FP64 by the normalised recurrence at every
@@ -904,7 +907,6 @@ int launch_shapelets_ws(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* ou
     a.rowinfo = rowinfo;
     a.chaninfo = chaninfo;
     a.bop = tf32 ? reinterpret_cast<const __nv_bfloat16*>(M->bop32 + h.b_off / 2) : M->bop + h.b_off;
-    a.tf32 = tf32 ? 1 : 0;
     a.lut = lut;
     a.n_pad = h.n_pad;
     a.nmax = h.nmax;
@@ -938,7 +940,7 @@ int launch_shapelets_ws(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* ou
     const int n_tiles = (int)((n_vis + K2_M * R - 1) / (K2_M * R));
     a.n_tiles = n_tiles;
     const int grid = std::min(n_tiles, ctx->num_sms);
-    cudaError_t e = k2_dispatch(a, h.k_pad, R, lut != nullptr, grid, lay.total, st);
+    cudaError_t e = k2_dispatch(a, h.k_pad, R, lut != nullptr ? 1 : (tf32 ? 2 : 0), grid, lay.total, st);
     if (e != cudaSuccess) return set_error(WN_ECUDA, std::string("shapelet kernel launch: ") + cudaGetErrorString(e));
   }
   return WN_OK;
