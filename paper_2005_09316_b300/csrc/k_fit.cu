@@ -186,29 +186,69 @@ int launch_fit_shapelets(wn_ctx* ctx, const ObsDev& o, Model* M, const PeelArgs&
   const double tol2 = tol * tol;
   const int kCheck = 8;  // iterations between looks at the device's stop flag
   bool stopped = rc != WN_OK || !(n_iter > 0 && gam0 > 0.0 && tol < 1.0);
-  for (int launched = 0; !rc && !stopped && launched < n_iter; ++launched) {
+  // One CGLS iteration's launches on stream s, with no host synchronisation.
+  auto iteration = [&](cudaStream_t s) -> int {
     // q = -A p
-    rc = launch_pack_coeff(ctx, M, pv, meta, st);
+    if (int r2 = launch_pack_coeff(ctx, M, pv, meta, s)) return r2;
+    cudaMemsetAsync(q, 0, n_vis * sizeof(float2), s);
+    if (int r2 = launch_shapelets(ctx, o, M, q, OUT_SUBG, pa, s)) return r2;
+    k8_norm2_c64<<<vgrid, K8_T, 0, s>>>(q, n_vis, part);
+    k8_sum<<<1, 32, 0, s>>>(part, vgrid, sc + SC_QQ);
+    k8_cg_qq<<<1, 32, 0, s>>>(sc);
+    k8_cg_step<<<vgrid, K8_T, 0, s>>>(coeff, pv, nnz, r, q, n_vis, sc);  // x += alpha p, r -= alpha A p
+    // s = A^T r = -1/2 dL/dC
+    if (int r2 = launch_grad_shape_coeff(ctx, o, M, pa, r, gv, s)) return r2;
+    k8_vec_f64<<<cgrid, K8_T, 0, s>>>(sv, gv, nnz, -0.5, 0.0);
+    k8_norm2_f64<<<cgrid, K8_T, 0, s>>>(sv, nnz, part);
+    k8_sum<<<1, 32, 0, s>>>(part, cgrid, sc + SC_GNEW);
+    k8_cg_dir<<<cgrid, K8_T, 0, s>>>(pv, sv, nnz, sc);  // p = s + beta p
+    k8_cg_finish<<<1, 32, 0, s>>>(sc, tol2);
+    return WN_OK;
+  };
+  // The iterations run on a private stream (a graph cannot be captured on the legacy stream): the first
+  // as plain launches, which also sizes the workspaces, the rest as replays of a CUDA graph of one
+  // iteration, which removes the per-launch gaps.  If the capture fails they stay plain launches.
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ev = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  if (!stopped) {
+    cudaError_t es = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (es == cudaSuccess) es = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (es == cudaSuccess) es = cudaEventRecord(ev, st);
+    if (es == cudaSuccess) es = cudaStreamWaitEvent(cs, ev, 0);
+    if (es != cudaSuccess) rc = set_error(WN_ECUDA, std::string("fit stream: ") + cudaGetErrorString(es));
+  }
+  for (int launched = 0; !rc && !stopped && launched < n_iter; ++launched) {
+    if (gexec) {
+      const cudaError_t eg = cudaGraphLaunch(gexec, cs);
+      if (eg != cudaSuccess) rc = set_error(WN_ECUDA, std::string("fit graph launch: ") + cudaGetErrorString(eg));
+    } else {
+      rc = iteration(cs);
+    }
     if (rc) break;
-    cudaMemsetAsync(q, 0, n_vis * sizeof(float2), st);
-    rc = launch_shapelets(ctx, o, M, q, OUT_SUBG, pa, st);
-    if (rc) break;
-    k8_norm2_c64<<<vgrid, K8_T, 0, st>>>(q, n_vis, part);
-    k8_sum<<<1, 32, 0, st>>>(part, vgrid, sc + SC_QQ);
-    k8_cg_qq<<<1, 32, 0, st>>>(sc);
-    k8_cg_step<<<vgrid, K8_T, 0, st>>>(coeff, pv, nnz, r, q, n_vis, sc);  // x += alpha p, r -= alpha A p
-    rc = atr(r);
-    if (rc) break;
-    k8_norm2_f64<<<cgrid, K8_T, 0, st>>>(sv, nnz, part);
-    k8_sum<<<1, 32, 0, st>>>(part, cgrid, sc + SC_GNEW);
-    k8_cg_dir<<<cgrid, K8_T, 0, st>>>(pv, sv, nnz, sc);  // p = s + beta p
-    k8_cg_finish<<<1, 32, 0, st>>>(sc, tol2);
+    if (launched == 0 && n_iter > 1 &&
+        cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      const int rcap = iteration(cs);  // recorded, not run
+      const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
+      if (rcap != WN_OK || ec != cudaSuccess || cudaGraphInstantiate(&gexec, graph, 0) != cudaSuccess) gexec = nullptr;
+      cudaGetLastError();  // a failed capture leaves plain launches, not an error
+    }
     if ((launched + 1) % kCheck == 0 || launched + 1 == n_iter) {
       double h[6];
-      cudaMemcpyAsync(h, sc, sizeof(h), cudaMemcpyDeviceToHost, st);
-      cudaStreamSynchronize(st);
+      cudaMemcpyAsync(h, sc, sizeof(h), cudaMemcpyDeviceToHost, cs);
+      cudaStreamSynchronize(cs);
       stopped = h[SC_STOP] != 0.0;
     }
+  }
+  if (cs) {
+    cudaEventRecord(ev, cs);
+    cudaStreamWaitEvent(st, ev, 0);
+    cudaStreamSynchronize(cs);
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    cudaEventDestroy(ev);
   }
   if (!rc) {
     double h[6];
