@@ -447,12 +447,13 @@ def bench_adjoint(wn, ctx, local, torch):
             "ms_per_step": round(ms, 4), "grad_evals_per_s": obs.n_vis * sky.n_comp / (ms * 1e-3)}
 
 
-def bench_serving(wn, ctx, local, torch, n_req=1000, n_templates=48, seed=17):
+def bench_serving(wn, ctx, local, torch, n_req=1000, n_templates=48, seed=17, policy=None):
     """Seeded Poisson stream of predict/peel requests of uneven size (16-128 tiles, 1-14 steps, 32-384
     channels, 100-50,000 P/G, 0-3 shapelets with n_max 10-80), models resident.  Requests are drawn
     uniformly from n_templates distinct (observation, sky, data) sets; the arrival rate is set for ~70%
     GPU busy from the measured one-at-a-time service times.  The one-at-a-time reference is a FIFO in
-    front of single-request calls, played with the measured service time of each request alone."""
+    front of single-request calls, played with the measured service time of each request alone.
+    policy: (large requests in flight, wait limit in s) for Server.set_policy; None keeps the defaults."""
     from paper_2005_09316_b300.serve import Server, latency_summary, poisson_arrivals, run_stream
     rng = np.random.default_rng(seed)
     temps, models = [], []
@@ -499,6 +500,8 @@ def bench_serving(wn, ctx, local, torch, n_req=1000, n_templates=48, seed=17):
         lat_serial.append(t_free - a)
     max_rows = max(r[0].n_rows for r in temps)
     srv = Server(ctx, n_streams=6, pool_bytes=6 << 30, max_inflight=32, max_rows=max_rows, max_chan=384)
+    if policy is not None:
+        srv.set_policy(*policy)
     results, wall = run_stream(srv, reqs, arrivals)
     st = srv.stats()
     srv.close()

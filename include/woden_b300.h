@@ -264,6 +264,13 @@ WN_API int wn_server_copy(wn_server* srv, uint64_t ticket, void* dst, void* stre
 WN_API int wn_server_release(wn_server* srv, uint64_t ticket);
 /* Cancel a request that has not been admitted yet (WN_EBUSY otherwise). */
 WN_API int wn_server_cancel(wn_server* srv, uint64_t ticket);
+/* Admission policy for large requests (those whose estimated work exceeds one batch's budget, about
+ * 20 ms; they run in chunks).  At most max_large_inflight of them (1..16; never more than the slots
+ * less one) own a slot at a time; among the waiting ones the least estimated work starts first, except
+ * that one waiting longer than max_large_wait_s seconds since submission starts before any younger one
+ * (0 gives submission order).  Defaults: 1 and 1.0 s.  Takes effect at the next admission; requests
+ * already started keep their slot.  WN_EINVAL for a NULL server or values outside those ranges. */
+WN_API int wn_server_set_policy(wn_server* srv, int max_large_inflight, double max_large_wait_s);
 /* stats (6 doubles): batches launched, most batches on the GPU at once, most requests in one batch,
  * requests launched, requests admitted and unreleased, free pool bytes. */
 WN_API int wn_server_stats(wn_server* srv, double* stats);

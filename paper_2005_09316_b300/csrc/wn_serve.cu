@@ -40,11 +40,11 @@ constexpr double kBatchBudget = 0.02;   // seconds of estimated GPU work per bat
 // the queue of large requests drains fastest for all but the largest; the small ones keep the remaining
 // streams (measured on the serving bench: p99 372-495 ms with one, 492-536 ms with two, 600-620 ms
 // with two in arrival order).
-constexpr int kMaxLargeInFlight = 1;
+constexpr int kMaxLargeInFlight = 1;  // default; wn_server_set_policy changes it per server
 // Large requests start in order of estimated work, least first, which keeps a burst of them from
 // holding back the many mid-sized ones behind the few largest; a request that has waited this long
 // since submission starts before any younger one, so the largest are passed over for a bounded time.
-constexpr double kMaxLargeWait = 1.0;
+constexpr double kMaxLargeWait = 1.0;  // seconds; default, as above
 constexpr double kEvalRate = 3.0e12;    // component-visibility evaluations per second (estimate)
 constexpr double kTileEvals = 2.4e7;    // evaluations per CTA tile of a large request (~2 ms on one CTA)
 
@@ -93,6 +93,8 @@ struct wn_server {
   int max_work = 1 << 14;
   size_t table_bytes = 0;
   int max_rows = 0, max_chan = 0;
+  int max_large_inflight = wn::kMaxLargeInFlight;  // admission policy (wn_server_set_policy)
+  double max_large_wait = wn::kMaxLargeWait;
   char* pool = nullptr;
   size_t pool_bytes = 0;
   std::map<size_t, size_t> free_list;  // offset -> size
@@ -285,7 +287,7 @@ static bool launch_ready(wn_server* s) {
   int owners = 0;
   for (auto& sl : s->slots) owners += sl.owner ? 1 : 0;
   const double t_now = now_s(s);
-  while (owners < std::min(kMaxLargeInFlight, std::max(1, ns - 1))) {
+  while (owners < std::min(s->max_large_inflight, std::max(1, ns - 1))) {
     int k = ns - 1;
     while (k >= 0 && (s->slots[k].busy || s->slots[k].owner)) --k;
     if (k < 0) break;
@@ -295,7 +297,7 @@ static bool launch_ready(wn_server* s) {
     for (auto& kv : s->reqs) {
       ServeReq& q = kv.second;
       if (!unstarted(q) || !is_large(q)) continue;
-      const bool old = t_now - q.t_submit > kMaxLargeWait;
+      const bool old = t_now - q.t_submit > s->max_large_wait;
       if (pick_old && !old) continue;
       if (!pick || (old && !pick_old) || (!old && large_cost(q) < large_cost(*pick))) {
         pick = &q;
@@ -636,6 +638,19 @@ int wn_server_cancel(wn_server* s, uint64_t ticket) {
   if (it == s->reqs.end()) return set_error(WN_ENOTFOUND, "unknown ticket");
   if (it->second.state != RQ_PENDING) return set_error(WN_EBUSY, "request already admitted");
   it->second.state = RQ_CANCELLED;
+  return WN_OK;
+}
+
+int wn_server_set_policy(wn_server* s, int max_large_inflight, double max_large_wait_s) {
+  if (!s) return set_error(WN_EINVAL, "NULL argument");
+  if (max_large_inflight < 1 || max_large_inflight > 16) return set_error(WN_EINVAL, "max_large_inflight outside 1..16");
+  if (!(max_large_wait_s >= 0.0)) return set_error(WN_EINVAL, "max_large_wait_s must be >= 0");
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->max_large_inflight = max_large_inflight;
+    s->max_large_wait = max_large_wait_s;
+  }
+  s->cv.notify_all();
   return WN_OK;
 }
 

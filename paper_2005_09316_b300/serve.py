@@ -96,6 +96,12 @@ class Server:
     def cancel(self, ticket: int):
         _check(load().wn_server_cancel(self.h, ticket))
 
+    def set_policy(self, max_large_inflight: int = 1, max_large_wait_s: float = 1.0):
+        """Admission of large (chunked) requests: how many own a slot at once, and after how many
+        seconds of waiting one starts ahead of any younger one (least estimated work first otherwise;
+        0 gives submission order)."""
+        _check(load().wn_server_set_policy(self.h, int(max_large_inflight), float(max_large_wait_s)))
+
     def stats(self) -> dict:
         v = (ctypes.c_double * 6)()
         _check(load().wn_server_stats(self.h, v))

@@ -199,3 +199,32 @@ def test_large_requests_start_least_work_first(wn, ctx):
     assert ctx.device_errors() == 0
     for m in models:
         m.free()
+
+
+def test_policy_with_no_age_limit_starts_large_requests_in_submission_order(wn, ctx):
+    """With the wait limit at 0 every queued large request counts as overdue, so they start in
+    submission order: the same submissions as above, and now the larger (earlier) one starts first.
+    Values outside the documented ranges are refused."""
+    from paper_2005_09316_b300.serve import Server
+    obs = synth.make_obs(81, 128, 4, synth.uniform_channels(167e6, 80e3, 384), layout="mwa")
+    d = wn.obs_to_device(obs)
+    models = [ctx.upload(synth.make_sky(82 + i, n * 4 // 5, n // 5, 0, fov=15 * synth.DEG))
+              for i, n in enumerate((20000, 20000, 8000))]
+    srv = Server(ctx, n_streams=2, pool_bytes=1 << 30, max_inflight=4, max_rows=obs.n_rows, max_chan=384)
+    for bad in ((0, 1.0), (17, 1.0), (1, -1.0), (1, float("nan"))):
+        with pytest.raises(wn.WnError):
+            srv.set_policy(*bad)
+    srv.set_policy(1, 0.0)
+    tickets = [srv.submit(d, m) for m in models]
+    res = [srv.wait(t, 120) for t in tickets]
+    assert all(r.state == 3 for r in res)
+    got = [srv.result_tensor(t, d).cpu().numpy() for t in tickets]
+    for t in tickets:
+        srv.release(t)
+    srv.close()
+    assert res[1].t_launch < res[2].t_launch, [(r.t_submit, r.t_launch) for r in res]
+    for g, m in zip(got, models):
+        assert e_norm(g, ctx.predict(d, m).cpu().numpy()) <= 1e-5
+    assert ctx.device_errors() == 0
+    for m in models:
+        m.free()
