@@ -518,6 +518,7 @@ def bench_serving(wn, ctx, local, torch, n_req=1000, n_templates=48, seed=17, po
                           "one_at_a_time_p99_ms": round(1e3 * float(np.percentile(ser_a[sel], 99)), 3)}
     return {"workload": f"serving: {n_req} Poisson requests drawn from {n_templates} uneven request sets "
                         "(16-128 tiles, 1-14 steps, 32-384 ch, 100-50000 P/G + 0-3 shapelets n_max 10-80)",
+            "policy": {"max_large_inflight": (policy or (1, 1.0))[0], "max_large_wait_s": (policy or (1, 1.0))[1]},
             "rate_hz": round(rate, 2), "mean_service_ms": round(1e3 * mean_s, 3),
             "p50_ms": round(lat["p50_ms"], 3), "p99_ms": round(lat["p99_ms"], 3),
             "one_at_a_time_p50_ms": round(1e3 * float(np.percentile(lat_serial, 50)), 3),
