@@ -65,7 +65,11 @@ typedef enum {
 /* Precision of the point/Gaussian phasor sum. */
 typedef enum {
     WN_PREC_MIXED = 0,   /* double-float phase argument, FP32 phasors and sums (default) */
-    WN_PREC_FP64 = 1     /* every step in FP64: the plain reference form */
+    WN_PREC_FP64 = 1,    /* every step in FP64: the plain reference form, with the per-component constants
+                            (log-flux and spectral index, Gaussian quadratic form, shapelet frame and scales)
+                            formed once per component per thread block, as the mixed path forms them once */
+    WN_PREC_FP64_UNTUNED = 2 /* every step in FP64, the formulas evaluated per visibility as printed (pow for
+                                the spectrum, the position angle's cos and sin per evaluation) */
 } wn_precision;
 
 /* Precision of the tensor-core shapelet contraction (xi = A C B^T, Sec. 3.2 eq:shape-env). */
@@ -286,10 +290,11 @@ WN_API int wn_server_stats(wn_server* srv, double* stats);
  * context's growable workspace, and nothing in the call allocates.
  * Limits: n_chan rounded up to a multiple of 16, plus n_time * n_base, must not exceed 262144;
  * larger observations are rejected with WN_EINVAL.
- * The first call on a device looks up the array's device address (and uploads the Hermite recurrence
- * constants) for that device; make that first call before any stream capture on the device.
- * Every call in the process shares the array and it keeps the last call's contents; calls whose work
- * overlaps on the GPU (concurrent streams, devices sharing the process) race on it, so order them.
+ * The array's device address is looked up once, when the context is created (wn_create, with the
+ * context's device current), and kept in the context; the call itself only launches kernels.
+ * Each device has its own copy of the array.  Every call on one device shares that copy, which keeps
+ * the last call's contents: calls whose work overlaps on the same device (concurrent streams, or
+ * several contexts on one device) race on it, so order them; calls on different devices do not.
  * The model must already be resident (wn_sky_upload) and the context created beforehand. */
 WN_API int wn_predict_static(wn_ctx* ctx, const wn_obs* obs, int model_id, void* vis_c64, int accumulate, void* stream);
 

@@ -1,12 +1,13 @@
-"""FP64 CPU oracle for direct measurement-equation prediction, peeling, its gradient and the gain
-calibration loop.
+"""FP64 CPU oracle for direct measurement-equation prediction, peeling, its gradient, the gain
+calibration loop and the model-truncation rule.
 
 TEST INFRASTRUCTURE ONLY: imported by tests/, by ``__graft_entry__.smoke()`` and by the
 ``cpu_baseline`` / ``--impl reference`` legs of bench.py, never by the library itself.
 
 The arithmetic lives in ``wn_oracle.c`` (plain C, FP64, loops in the paper's order); this module
 builds it with gcc, loads it with ctypes and marshals numpy arrays.  The calibration loop is numpy
-(design matrix written out, numpy's solve for the normal equations).  It also holds the oracle's own
+(design matrix written out, numpy's solve for the normal equations).  The truncation rule of
+Sec. 6.2 is plain Python over weights from a Gauss-Legendre quadrature of the Hermite functions.  It also holds the oracle's own
 packers (triangular coefficient index, parity split of the (-i)^(n1+n2) phase, bf16 hi/lo split, tf32
 rounding),
 written from the same definitions the CUDA packer follows, so the two can be compared bit for bit.
@@ -377,3 +378,94 @@ def fit_shapelet_coeffs(uvw_rows, freq, dec0, sky, G, data):
     Ar = np.concatenate([A.real, A.imag], axis=0)
     br = np.concatenate([b.real, b.imag])
     return np.linalg.lstsq(Ar, br, rcond=None)[0]
+
+
+# ------------------------------------------------------------------------------------------------
+# Model truncation (Sec. 6.2, "Model truncation").  Each point/Gaussian component, and each shapelet
+# basis function, carries an absolute flux |I_j|; after sorting them so that |I_j| > |I_{j+1}|, the
+# truncated model keeps the first N_comp, N_comp being the largest count whose summed |I_j| does not
+# exceed f_comp times the sum over the whole model.  With no restoring beam and no image here (the
+# paper sums the beam-convolved basis image over the fitted pixels), the weight of basis function
+# (n1, n2) of a shapelet of flux S is |S C_n1n2| times the l1 norms of its two image-space 1-D factors,
+# each normalised so that the (0, 0) function has unit flux: (1 / sqrt(2 pi)) * integral |phi_n(t)| dt,
+# with phi_n(t) = H_n(t) exp(-t^2 / 2) / sqrt(2^n n!) the peak-normalised Hermite function of the uv
+# envelope (its image-space partner psi_n(x) = phi_n(x / b) / (sqrt(2 pi) b) transforms to
+# (-i)^n phi_n(2 pi u b), so the norm does not depend on b).
+#
+# The integral is computed here independently of the library's recurrence: phi_n keeps one sign between
+# consecutive zeros of H_n, so integral |phi_n|^p is a sum of Gauss-Legendre quadratures over those
+# intervals (the zeros from numpy's Gauss-Hermite nodes, H_n from scipy's eval_hermite), plus the tail
+# beyond the last zero in unit steps out to 40 past it.
+# ------------------------------------------------------------------------------------------------
+
+def hermite_abs_moment(n: int, p: float, order: int = 48) -> float:
+    """integral over the real line of |phi_n(t)|^p dt (phi_n peak-normalised; even in t)."""
+    import math
+
+    import scipy.special as sp
+    from numpy.polynomial.hermite import hermgauss
+    from numpy.polynomial.legendre import leggauss
+    x, w = leggauss(order)
+    zeros = np.sort(hermgauss(n)[0]) if n > 0 else np.zeros(0)
+    edges = [0.0] + [float(z) for z in zeros if z > 0.0]
+    top = edges[-1] + 40.0
+    edges += [float(v) for v in np.arange(edges[-1] + 1.0, top, 1.0)] + [top]
+    lognorm = 0.5 * (n * math.log(2.0) + math.lgamma(n + 1.0))
+    total = 0.0
+    for a, b in zip(edges[:-1], edges[1:]):
+        t = 0.5 * (b - a) * x + 0.5 * (a + b)
+        f = sp.eval_hermite(n, t) * np.exp(-0.5 * t * t - lognorm)
+        total += 0.5 * (b - a) * float(np.sum(w * np.abs(f) ** p))
+    return 2.0 * total          # |phi_n| is even
+
+
+def basis_l1(nmax: int) -> np.ndarray:
+    """Flux-normalised l1 norm of the 1-D image-space shapelet factor of order n = 0..nmax:
+    (1 / sqrt(2 pi)) * integral |phi_n(t)| dt (1 for n = 0)."""
+    return np.array([hermite_abs_moment(n, 1.0) for n in range(nmax + 1)]) / np.sqrt(2.0 * np.pi)
+
+
+def truncation_weights(sky) -> np.ndarray:
+    """|I_j| of every point/Gaussian component (|S_ref|), then of every shapelet basis function in
+    coefficient-triple order (|S C_n1n2| l1(n1) l1(n2))."""
+    n_pg = sky.n_point + sky.n_gauss
+    w = [abs(float(sky.flux[j])) for j in range(n_pg)]
+    if sky.n_shape:
+        l1 = basis_l1(int(np.max(sky.s_nmax)))
+        for q in range(sky.n_shape):
+            S = float(sky.flux[n_pg + q])
+            for k in range(int(sky.s_off[q]), int(sky.s_off[q + 1])):
+                w.append(abs(S * float(sky.s_coeff[k])) * l1[int(sky.s_n1[k])] * l1[int(sky.s_n2[k])])
+    return np.array(w, dtype=np.float64)
+
+
+def truncation_keep(sky, f_comp: float) -> np.ndarray:
+    """Boolean mask over truncation_weights(sky): True for the N_comp entries of largest |I_j| (ties
+    keep the earlier entry), N_comp the largest count with cumulative |I| <= f_comp * total."""
+    w = truncation_weights(sky)
+    order = sorted(range(len(w)), key=lambda j: (-w[j], j))
+    total = 0.0
+    for j in order:             # summed in the same order as the running sum, so f_comp = 1 keeps all
+        total += w[j]
+    limit = f_comp * total
+    keep = np.zeros(len(w), dtype=bool)
+    running = 0.0
+    for j in order:
+        if running + w[j] > limit:
+            break
+        running += w[j]
+        keep[j] = True
+    return keep
+
+
+def truncation_zeroed(sky, keep):
+    """The full model with every dropped component's flux and every dropped basis function's
+    coefficient set to zero: it predicts exactly what the truncated model predicts."""
+    import copy
+    z = copy.deepcopy(sky)
+    n_pg = sky.n_point + sky.n_gauss
+    z.flux = np.array(sky.flux, dtype=np.float64).copy()
+    z.s_coeff = np.array(sky.s_coeff, dtype=np.float64).copy()
+    z.flux[:n_pg][~keep[:n_pg]] = 0.0
+    z.s_coeff[~keep[n_pg:]] = 0.0
+    return z

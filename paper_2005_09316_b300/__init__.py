@@ -20,7 +20,7 @@ _lib = None
 _lock = threading.Lock()
 
 WN_OK, WN_EINVAL, WN_ENOMEM, WN_ECUDA, WN_ETIMEOUT, WN_EBUSY, WN_ENOTFOUND = range(7)
-WN_PREC_MIXED, WN_PREC_FP64 = 0, 1
+WN_PREC_MIXED, WN_PREC_FP64, WN_PREC_FP64_UNTUNED = 0, 1, 2
 WN_SHAPE_BF16X3, WN_SHAPE_BF16X1, WN_SHAPE_LUT_BF16X3, WN_SHAPE_TF32 = 0, 1, 2, 3
 WN_DEVERR_ANTENNA, WN_DEVERR_TIMEOUT, WN_DEVERR_SKY, WN_DEVERR_CALIB = 0x1, 0x2, 0x4, 0x8
 

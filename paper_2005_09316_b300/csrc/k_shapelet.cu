@@ -43,8 +43,6 @@ constexpr int K2_MMA_WARP = 8 * K2_GROUPS;
 
 // sqrt(2/(n+1)) and sqrt(n/(n+1)) of the normalised Hermite recurrence
 //   phi_{n+1} = sqrt(2/(n+1)) x phi_n - sqrt(n/(n+1)) phi_{n-1}.
-__constant__ float c_herm_a[kNmaxLimit + 1];
-__constant__ float c_herm_b[kNmaxLimit + 1];
 
 // Lookup-table form of the basis (the 1-D tables of Sec. 3.2): phi_0..phi_127 at x_i = -K2_LUT_X + i / K2_LUT_D,
 // row i of 128 floats, interpolated linearly.  |x| beyond sqrt(2 * 127 + 1) + 10 < K2_LUT_X is zero.
@@ -470,12 +468,17 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
     fence_mbar_init();
   }
   if (threadIdx.x <= kNmaxLimit) {
+    // the normalised recurrence's constants sqrt(2 / (n + 1)) and sqrt(n / (n + 1)), correctly rounded in
+    // FP64 and then to FP32 (the device's FP64 division and square root round to nearest), formed here in
+    // every CTA so that no upload has to be ordered with the launches of other streams
+    const double np1 = (double)(threadIdx.x + 1);
+    const float ha = (float)sqrt(2.0 / np1), hb = (float)sqrt((double)threadIdx.x / np1);
     float* cf = reinterpret_cast<float*>(smem + lay.coef);
-    cf[threadIdx.x] = c_herm_a[threadIdx.x];
-    cf[kNmaxLimit + 1 + threadIdx.x] = c_herm_b[threadIdx.x];
+    cf[threadIdx.x] = ha;
+    cf[kNmaxLimit + 1 + threadIdx.x] = hb;
     float2* cp = reinterpret_cast<float2*>(cf + 2 * (kNmaxLimit + 1));
-    cp[threadIdx.x] = make_float2(c_herm_a[threadIdx.x], c_herm_a[threadIdx.x]);
-    cp[kNmaxLimit + 1 + threadIdx.x] = make_float2(-c_herm_b[threadIdx.x], -c_herm_b[threadIdx.x]);
+    cp[threadIdx.x] = make_float2(ha, ha);
+    cp[kNmaxLimit + 1 + threadIdx.x] = make_float2(-hb, -hb);
   }
   if (warp == K2_MMA_WARP) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
@@ -790,22 +793,6 @@ __global__ void k2_rowgain(PeelArgs p, int n_rows, int n_base, float2* out, unsi
   out[r] = G;
 }
 
-static int g_consts_ready[64] = {0};
-
-static int k2_setup_constants(int device, cudaStream_t st) {
-  if (device >= 0 && device < 64 && g_consts_ready[device]) return WN_OK;
-  float ha[kNmaxLimit + 1], hb[kNmaxLimit + 1];
-  for (int n = 0; n <= kNmaxLimit; ++n) {
-    ha[n] = (float)std::sqrt(2.0 / (n + 1));
-    hb[n] = (float)std::sqrt((double)n / (n + 1));
-  }
-  cudaError_t e = cudaMemcpyToSymbolAsync(c_herm_a, ha, sizeof(ha), 0, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_herm_b, hb, sizeof(hb), 0, cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return set_error(WN_ECUDA, std::string("shapelet constants: ") + cudaGetErrorString(e));
-  if (device >= 0 && device < 64) g_consts_ready[device] = 1;
-  return WN_OK;
-}
-
 template <int KP, int R, int FORM>
 static cudaError_t k2_launch_t(const K2Args& a, int grid, int smem, cudaStream_t st) {
   auto fn = k2_shapelet<KP, R, FORM>;
@@ -888,7 +875,6 @@ static int ws_reserve(wn_ctx* ctx, size_t bytes, cudaStream_t st) {
 // Shapelet launches with caller-supplied tables: per-channel (n_chan float4) and per-row (n_rows float4).
 int launch_shapelets_ws(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, int mode, const PeelArgs& pa,
                         float4* chaninfo, float4* rowinfo, cudaStream_t st, float2* rowg) {
-  if (int r = k2_setup_constants(ctx->device, st)) return r;
   k2_chaninfo<<<(o.n_chan + 255) / 256, 256, 0, st>>>(o.freq, o.n_chan, o.nu0, chaninfo);
   const long long n_vis = (long long)o.n_rows * o.n_chan;
   const bool tf32 = ctx->shape_mode == WN_SHAPE_TF32;
@@ -964,29 +950,24 @@ int launch_shapelets(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, 
 // ------------------------------------------------------------------------------------------------
 // Allocation-free shapelet launches (wn_predict_static).  The per-channel and per-row constants
 // that launch_shapelets keeps in the context's growable workspace live here in a fixed device array
-// instead, so the call never allocates.  The array is shared by every call in the process and keeps
-// the last call's contents; both tables are fully rewritten by the prep kernels before the main
-// kernel reads them, so nothing needs clearing, but calls whose work overlaps on the GPU race on it.
+// instead, so the call never allocates.  Every GPU that loads the library holds its own copy of the
+// array until the process exits.  The copy is shared by every call on that device and keeps the last
+// call's contents; both tables are fully rewritten by the prep kernels before the main kernel reads
+// them, so nothing needs clearing, but calls whose work overlaps on the same device race on it.
 // ------------------------------------------------------------------------------------------------
 namespace wn {
 
 constexpr size_t kStaticScratchEntries = size_t(1) << 18;  // float4 entries (4 MiB): n_chan (padded to 16) + n_rows
 static __device__ __align__(256) float4 g_static_scratch[kStaticScratchEntries];
-static float4* g_static_scratch_addr[64] = {nullptr};
-static std::mutex g_static_scratch_mu;
 
-// Device address of the array for `device` (which must be current).  In host code the symbol is only
-// a host-side stand-in, so the address is looked up once per device and cached.
-static int static_scratch_address(int device, float4** out) {
-  std::lock_guard<std::mutex> lock(g_static_scratch_mu);
-  if (device < 0 || device >= 64) return set_error(WN_EINVAL, "device index out of range for the static scratch");
-  if (!g_static_scratch_addr[device]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess) return set_error(WN_ECUDA, std::string("cudaGetSymbolAddress(static scratch): ") + cudaGetErrorString(e));
-    g_static_scratch_addr[device] = static_cast<float4*>(p);
-  }
-  *out = g_static_scratch_addr[device];
+// Set-up at context creation (wn_create), with the context's device current: in host code the array's
+// name is only a host-side stand-in, so its device address is looked up here and kept in the context.
+// A context created after a device reset looks it up again.
+int static_scratch_setup(wn_ctx* ctx) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+  if (e != cudaSuccess) return set_error(WN_ECUDA, std::string("cudaGetSymbolAddress(static scratch): ") + cudaGetErrorString(e));
+  ctx->static_scratch = static_cast<float4*>(p);
   return WN_OK;
 }
 
@@ -999,8 +980,8 @@ int launch_shapelets_static(wn_ctx* ctx, const ObsDev& o, const Model* M, float2
     return set_error(WN_EINVAL, "wn_predict_static: n_chan (rounded up to 16) + n_time * n_base = " +
                                     std::to_string(chan_entries + (size_t)o.n_rows) + " exceeds the static scratch of " +
                                     std::to_string(kStaticScratchEntries) + " entries");
-  float4* base = nullptr;
-  if (int r = static_scratch_address(ctx->device, &base)) return r;
+  float4* base = ctx->static_scratch;
+  if (!base) return set_error(WN_ECUDA, "wn_predict_static: the static scratch address was not found at set-up");
   return launch_shapelets_ws(ctx, o, M, out, mode, pa, base, base + chan_entries, st, nullptr);
 }
 

@@ -133,7 +133,7 @@ static cudaError_t dalloc(T** p, size_t n, size_t& total) {
 // Predict (mode STORE / ACCUM) or peel of one resident model on one observation.
 static int run_model(wn_ctx* ctx, const ObsDev& d, const Model* M, float2* out, int mode, const PeelArgs& pa,
                      cudaStream_t st) {
-  if (ctx->precision == WN_PREC_FP64) return launch_phasor_fp64(ctx, d, M, out, mode, pa, true, st);
+  if (ctx->precision != WN_PREC_MIXED) return launch_phasor_fp64(ctx, d, M, out, mode, pa, true, st);
   int r = WN_OK;
   const bool have_pg = M->n_point + M->n_gauss > 0;
   if (have_pg || M->n_shape == 0) r = launch_phasor_mixed(ctx, d, M, out, mode, pa, st);
@@ -196,6 +196,12 @@ int wn_create(wn_ctx** out, int device) {
     delete c;
     return cuda_fail(e, "cudaMalloc(phasor tail partial sums)");
   }
+  if (int r = static_scratch_setup(c)) {  // device address of wn_predict_static's array, this device current
+    cudaFree(c->k1_part);
+    cudaFree(c->d_err);
+    delete c;
+    return r;
+  }
   cudaDeviceSynchronize();
   *out = c;
   return ok();
@@ -216,7 +222,8 @@ void wn_destroy(wn_ctx* ctx) {
 
 int wn_set_precision(wn_ctx* ctx, int precision, int shape_mode) {
   if (!ctx) return set_error(WN_EINVAL, "ctx is NULL");
-  if (precision != WN_PREC_MIXED && precision != WN_PREC_FP64) return set_error(WN_EINVAL, "unknown precision");
+  if (precision != WN_PREC_MIXED && precision != WN_PREC_FP64 && precision != WN_PREC_FP64_UNTUNED)
+    return set_error(WN_EINVAL, "unknown precision");
   if (shape_mode != WN_SHAPE_BF16X3 && shape_mode != WN_SHAPE_BF16X1 && shape_mode != WN_SHAPE_LUT_BF16X3 &&
       shape_mode != WN_SHAPE_TF32)
     return set_error(WN_EINVAL, "unknown shape mode");
@@ -586,7 +593,7 @@ int wn_predict_static(wn_ctx* ctx, const wn_obs* obs, int model_id, void* vis_c6
   const int mode = accumulate ? OUT_ACCUM : OUT_STORE;
   PeelArgs pa;
   int r = WN_OK;
-  if (ctx->precision == WN_PREC_FP64) {
+  if (ctx->precision != WN_PREC_MIXED) {
     r = launch_phasor_fp64(ctx, d, M, static_cast<float2*>(vis_c64), mode, pa, true, st);
   } else {
     const bool have_pg = M->n_point + M->n_gauss > 0;

@@ -118,6 +118,7 @@ struct wn_ctx {
   size_t ws2_bytes = 0;
   float* lut = nullptr;  // basis table of the lookup-table shapelet mode (built on first use)
   float2* k1_part = nullptr;  // partial sums of the split tail tiles of the phasor launch (fixed size)
+  float4* static_scratch = nullptr;  // device address of wn_predict_static's file-scope array (set-up)
 };
 // An NVTX range named after the entry point, for the duration of the call, when the context traces.
 // NVTX is header-only: without a tool attached a range costs a few nanoseconds.
@@ -389,6 +390,7 @@ int launch_shapelets(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, 
 int launch_shapelets_static(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, int mode, const PeelArgs& pa,
                             cudaStream_t st);
 size_t static_scratch_entries();
+int static_scratch_setup(wn_ctx* ctx);
 int launch_grad(wn_ctx* ctx, const ObsDev& o, const Model* M, const PeelArgs& pa, float2* resid,
                 const wn_sky_grad* g, double* loss, cudaStream_t st);
 int k1_batched_smem();

@@ -1,8 +1,9 @@
 """GPU adjoint (wn_predict_grad and the autograd Function) against the oracle's analytic gradient,
 which the CPU tests pin to central finite differences.
 
-Tolerance: relative L2 error per parameter group <= 2e-3 (FP32 sums with an FP64 phase argument over
-tens of thousands of terms with cancellation), and the loss within 1e-5 relative.
+Tolerance, element by element within each parameter group: max_k |g_k - g_oracle,k| <= 2e-3 max_k
+|g_oracle,k| (FP32 sums with a double-float phase argument over tens of thousands of terms with
+cancellation; measured up to 2.2e-4, on a single shapelet's beta_2), and the loss within 1e-5 relative.
 """
 import numpy as np
 import pytest
@@ -28,8 +29,9 @@ def ctx(wn):
 
 
 def rel(a, b):
+    """max_k |a_k - b_k| / max_k |b_k|: every element held to the group's scale."""
     a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
 
 
 def problem(seed, n_ant=12, n_time=2, n_chan=24, n_point=40, n_gauss=10, nmaxs=(8,), freq=None):

@@ -228,3 +228,106 @@ def test_policy_with_no_age_limit_starts_large_requests_in_submission_order(wn, 
     assert ctx.device_errors() == 0
     for m in models:
         m.free()
+
+
+# ---------------------------------------------------------------------------------------------------
+# Served results against the FP64 oracle (Sec. 5.1 peel, eq:env_visi_def), element by element on
+# sampled rows.  Bound per result: max|G| (1e-5 max|V_pg| + 2e-4 max|V_sh|) + 1e-6 max|D|, i.e. the
+# FP32 phasor path's and the bf16 hi+lo tensor path's tolerances on their parts of the model (each
+# max over the oracle's visibilities of that part alone on the sampled rows), scaled by the gains for
+# a peel, plus the complex64 rounding of the residual.
+# ---------------------------------------------------------------------------------------------------
+
+def _split(sky):
+    import copy
+    n_pg = sky.n_point + sky.n_gauss
+    pg, sh = copy.deepcopy(sky), copy.deepcopy(sky)
+    pg.flux = np.array(sky.flux, float).copy()
+    sh.flux = np.array(sky.flux, float).copy()
+    pg.flux[n_pg:] = 0.0
+    sh.flux[:n_pg] = 0.0
+    return pg, sh
+
+
+def _host_request(wn, ctx, seed, n_ant, n_time, n_chan, n_pg, nmaxs, peel):
+    obs = synth.make_obs(seed, n_ant, n_time, synth.uniform_channels(167e6, 80e3, n_chan), layout="mwa")
+    sky = synth.make_sky(seed + 1, n_pg * 4 // 5, n_pg - n_pg * 4 // 5, len(nmaxs), fov=15 * synth.DEG,
+                         shape_nmax=np.array(nmaxs) if nmaxs else 10)
+    gains = data = None
+    if peel:
+        gains = synth.make_gains(seed + 2, n_ant).astype(np.complex64)
+        data = synth.complex_noise(seed + 3, (obs.n_rows, n_chan), 1.0).astype(np.complex64)
+    return {"obs": obs, "sky": sky, "gains": gains, "data": data, "d": wn.obs_to_device(obs), "m": ctx.upload(sky),
+            "gd": None if gains is None else torch.as_tensor(gains).cuda(),
+            "dd": None if data is None else torch.as_tensor(data.reshape(n_time, obs.n_base, n_chan)).cuda()}
+
+
+def _check_against_oracle(srv, ticket, req, n_rows=8, seed=0):
+    from helpers import oracle_peel_rows, oracle_rows, sample_rows
+    obs = req["obs"]
+    got = srv.result_tensor(ticket, req["d"]).cpu().numpy().reshape(obs.n_rows, obs.n_chan)
+    rows = sample_rows(obs, n_rows, seed)
+    pg, sh = _split(req["sky"])
+    Vpg, Vsh = oracle_rows(obs, pg, rows), oracle_rows(obs, sh, rows)
+    V = Vpg + Vsh
+    bound = 1e-5 * np.abs(Vpg).max() + (2e-4 * np.abs(Vsh).max() if req["sky"].n_shape else 0.0)
+    if req["data"] is None:
+        ref = V
+    else:
+        ref = oracle_peel_rows(obs, rows, req["gains"], req["data"][rows], V)
+        bound = bound * np.abs(req["gains"]).max() ** 2 + 1e-6 * np.abs(req["data"][rows]).max()
+    err = np.abs(got[rows] - ref).max()
+    assert err <= bound, (ticket, err, bound)
+    return err
+
+
+def test_mixed_stream_matches_oracle(wn, ctx):
+    """Ten uneven requests (predict and peel, 0-2 shapelets) submitted at once: at least two share one
+    batched persistent launch, and every served result equals the oracle's on sampled rows."""
+    from paper_2005_09316_b300.serve import Server
+    rng = np.random.default_rng(91)
+    reqs = []
+    for i in range(10):
+        nm = [int(x) for x in rng.integers(5, 25, size=int(rng.integers(0, 3)))]
+        reqs.append(_host_request(wn, ctx, 900 + 10 * i, int(rng.integers(16, 41)), int(rng.integers(1, 4)),
+                                  int(rng.integers(32, 129)), int(rng.integers(100, 1500)), nm, peel=bool(i % 2)))
+    srv = Server(ctx, n_streams=2, pool_bytes=1 << 30, max_inflight=16, max_rows=3 * 780, max_chan=128)
+    tickets = [srv.submit(r["d"], r["m"], r["gd"], r["dd"]) for r in reqs]
+    for t in tickets:
+        assert srv.wait(t, 60).state == 3
+    batches = [srv.poll(t).batch for t in tickets]
+    assert max(batches.count(b) for b in set(batches)) >= 2, batches   # a launch ran two requests or more
+    assert srv.stats()["max_batch_requests"] >= 2
+    for i, (t, r) in enumerate(zip(tickets, reqs)):
+        _check_against_oracle(srv, t, r, seed=i)
+        srv.release(t)
+    srv.close()
+    assert ctx.device_errors() == 0
+    for r in reqs:
+        r["m"].free()
+
+
+@pytest.mark.parametrize("peel", [False, True])
+def test_large_request_in_component_ranges_matches_oracle(wn, ctx, peel):
+    """A request above the batch work budget (128 tiles x 3 steps x 384 ch, 16,000 P + 4,000 G + one
+    n_max 20 shapelet), served in slices over row tiles and component ranges, with five small requests
+    submitted behind it: every result equals the oracle's on sampled rows."""
+    from paper_2005_09316_b300.serve import Server
+    big = _host_request(wn, ctx, 71, 128, 3, 384, 20000, [20], peel)
+    small = [_host_request(wn, ctx, 700 + 10 * i, 24, 2, 64, 400, [8] if i == 2 else [], peel=bool(i % 2))
+             for i in range(5)]
+    srv = Server(ctx, n_streams=3, pool_bytes=1 << 30, max_inflight=8, max_rows=big["obs"].n_rows, max_chan=384)
+    tickets = [srv.submit(r["d"], r["m"], r["gd"], r["dd"]) for r in [big] + small]
+    for t in tickets:
+        assert srv.wait(t, 120).state == 3
+    st = srv.stats()
+    assert st["batches"] >= 4, st            # the large request ran in several launches
+    _check_against_oracle(srv, tickets[0], big, n_rows=10, seed=1)
+    for i, (t, r) in enumerate(zip(tickets[1:], small)):
+        _check_against_oracle(srv, t, r, seed=2 + i)
+    for t in tickets:
+        srv.release(t)
+    srv.close()
+    assert ctx.device_errors() == 0
+    for r in [big] + small:
+        r["m"].free()
