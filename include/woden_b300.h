@@ -350,11 +350,12 @@ WN_API int wn_calibrate(wn_ctx* ctx, const wn_obs* obs, const void* model_c64, c
 WN_API int wn_pipe_rates(wn_ctx* ctx, double* rates);
 
 /* Component-visibility evaluations per second that the point/Gaussian kernel's channel loop sustains
- * by itself (no paper counterpart): the kernel's own loop code over components held in shared memory,
- * four tiles of 32 points per tile of 32 Gaussians, 12 channels of two rows per lane, 2 CTAs of 256
- * threads per SM, with no records, global memory or barriers inside the loop.  The rate the full
- * prediction approaches; its instruction mix, not the FP32 peak, sets it.  Best of three timed launches
- * after one warm-up; allocates a small scratch buffer and synchronises its own stream. */
+ * by itself (no paper counterpart): the single-launch kernel's own loop code over component records and
+ * spectrum values held in shared memory, four groups of 16 points per group of 16 Gaussians, 12 channels
+ * of two rows per lane, one CTA of 512 threads per SM, with no record building, global memory or
+ * barriers inside the loop.  The rate the full prediction approaches; its instruction mix, not the FP32
+ * peak, sets it.  Best of three timed launches after one warm-up; allocates a small scratch buffer and
+ * synchronises its own stream. */
 WN_API int wn_phasor_loop_rate(wn_ctx* ctx, double* evals_per_s);
 
 /* Tensor-core and TMEM timings as the shapelet kernel uses them (no paper counterpart).  One CTA per SM

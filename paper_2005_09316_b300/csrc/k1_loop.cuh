@@ -1,5 +1,7 @@
 // The channel loop of the point/Gaussian phasor kernel (K1), shared by the kernel and by the
-// microbenchmark that measures the rate this loop sustains on its own (wn_phasor_loop_rate).
+// microbenchmark that measures the rate the loop sustains on its own (wn_phasor_loop_rate): the per-warp
+// form's loop (k_phasor.cu), the spectrum-table form's loop (k_phasor_tab.cu), and the output store that
+// both forms use.
 #pragma once
 #include "wn_internal.cuh"
 
@@ -91,6 +93,134 @@ __device__ __forceinline__ void k1_comp_uniform(const float4 c, const float4 Ra,
     Qre = nre;
     Qim = nim;
     add(k - 1, Qre, Qim);
+  }
+}
+
+// ---- the loop of the single-launch form (k_phasor_tab.cu): amplitudes from the spectrum table, a
+// 48-byte record per (component, row pair), packed start reduction
+
+// Both rows' start phases theta = tau nu / c reduced to [-1/2, 1/2] turns at once (th, tl: the rows'
+// tau pairs), each step as reduce_turns does it for one row.
+__device__ __forceinline__ float2 reduce_turns_pair(float2 th, float2 tl, float ah, float al) {
+  const float2 A = make_float2(ah, ah), Al = make_float2(al, al);
+  const float2 p = __fmul2_rn(th, A);
+  float2 e = __ffma2_rn(th, A, make_float2(-p.x, -p.y));
+  e = __ffma2_rn(th, Al, e);
+  e = __ffma2_rn(tl, A, e);
+  const float2 S = make_float2(12582912.0f, 12582912.0f);
+  const float2 q = __fadd2_rn(p, S);
+  const float2 n = __fadd2_rn(q, make_float2(-S.x, -S.y));
+  return __fadd2_rn(__fadd2_rn(p, make_float2(-n.x, -n.y)), e);
+}
+
+// exp(-2 pi i r) of both rows, each turned by the sign's half turn hpi.
+__device__ __forceinline__ void phasor_pair(const float2 r, const float hpi, float2& re, float2& im) {
+  const float2 x = __ffma2_rn(r, make_float2(6.283185307179586f, 6.283185307179586f), make_float2(hpi, hpi));
+  float s0, c0, s1, c1;
+  asm("sin.approx.ftz.f32 %0, %1;" : "=f"(s0) : "f"(x.x));
+  asm("cos.approx.ftz.f32 %0, %1;" : "=f"(c0) : "f"(x.x));
+  asm("sin.approx.ftz.f32 %0, %1;" : "=f"(s1) : "f"(x.y));
+  asm("cos.approx.ftz.f32 %0, %1;" : "=f"(c1) : "f"(x.y));
+  re = make_float2(c0, c1);
+  im = make_float2(-s0, -s1);
+}
+
+// Amplitude of both rows at channel k: the table value for points; exp2(table + envelope exponent)
+// for Gaussians (nq: the rows' -q; wg: E log2(e) (nu_k / c)^2).
+template <bool GAUSS>
+__device__ __forceinline__ float2 ks_amp(const float t, const float2 nq, const float wgk) {
+  if (GAUSS) return make_float2(ex2_approx(fmaf(nq.x, wgk, t)), ex2_approx(fmaf(nq.y, wgk, t)));
+  return make_float2(t, t);
+}
+
+// One component against the K uniform channels of this lane's two rows (the recurrence of
+// k1_comp_uniform: from the middle channel m up and down, signed form X_k = e_k P_k).  The 48-byte
+// record: R0 = both rows' tau pairs {th0, th1, tl0, tl1}, R1 = the one-channel step D = exp(-2 pi i delta)
+// of both rows {D0.x, D1.x, D0.y, D1.y}, R2 = {-q0, -q1, the sign's half turn, 0} with q the rows'
+// Gaussian forms; tab: the lane's K spectrum values of this component.
+template <int K, bool GAUSS>
+__device__ __forceinline__ void ks_comp_uniform(const float4 R0, const float4 R1, const float4 R2, const float* tab,
+                                                const float a0h, const float a0l, const float* wg, float2* Vre,
+                                                float2* Vim) {
+  constexpr int M = k1_mid(K);
+  float t[K];
+#pragma unroll
+  for (int q = 0; q < K / 4; ++q) {
+    const float4 v = reinterpret_cast<const float4*>(tab)[q];
+    t[4 * q] = v.x;
+    t[4 * q + 1] = v.y;
+    t[4 * q + 2] = v.z;
+    t[4 * q + 3] = v.w;
+  }
+  float2 Xre, Xim;
+  phasor_pair(reduce_turns_pair(make_float2(R0.x, R0.y), make_float2(R0.z, R0.w), a0h, a0l), R2.z, Xre, Xim);
+  const float2 Dre = make_float2(R1.x, R1.y), Dim = make_float2(R1.z, R1.w), nDim = make_float2(-R1.z, -R1.w);
+  const float2 nq = make_float2(R2.x, R2.y);
+  const float2 Yre = __ffma2_rn(Xre, Dre, __fmul2_rn(Xim, nDim));  // X_(m+1) = P_m D
+  const float2 Yim = __ffma2_rn(Xre, Dim, __fmul2_rn(Xim, Dre));
+  const float2 Cp = __fadd2_rn(Dre, Dre), Cn = make_float2(-Cp.x, -Cp.y);  // +-2 cos(delta)
+  auto add = [&](int k, float2 re, float2 im) {
+    const float2 A = ks_amp<GAUSS>(t[k], nq, GAUSS ? wg[k] : 0.f);
+    Vre[k] = __ffma2_rn(re, A, Vre[k]);
+    Vim[k] = __ffma2_rn(im, A, Vim[k]);
+  };
+  add(M, Xre, Xim);
+  add(M + 1, Yre, Yim);
+  float2 Pre = Xre, Pim = Xim, Qre = Yre, Qim = Yim;
+#pragma unroll
+  for (int k = M + 1; k + 1 < K; ++k) {
+    const float2 A = ((k - M) & 1) ? Cn : Cp;
+    const float2 nre = __ffma2_rn(A, Qre, Pre), nim = __ffma2_rn(A, Qim, Pim);
+    Pre = Qre;
+    Pim = Qim;
+    Qre = nre;
+    Qim = nim;
+    add(k + 1, Qre, Qim);
+  }
+  Pre = Yre;
+  Pim = Yim;
+  Qre = Xre;
+  Qim = Xim;
+#pragma unroll
+  for (int k = M; k > 0; --k) {
+    const float2 A = ((M - k) & 1) ? Cp : Cn;
+    const float2 nre = __ffma2_rn(A, Qre, Pre), nim = __ffma2_rn(A, Qim, Pim);
+    Pre = Qre;
+    Pim = Qim;
+    Qre = nre;
+    Qim = nim;
+    add(k - 1, Qre, Qim);
+  }
+}
+
+// Write a lane's K channels of its two rows (rows row0, row0 + 1; channels f0 ..) in the output mode:
+// store, accumulate, the peel residual D - G V, or subtract G V from the output.
+template <int K>
+__device__ __forceinline__ void k1_store(const K1Args& a, const int row0, const int f0, const float2* Vre,
+                                         const float2* Vim, const bool ok) {
+#pragma unroll
+  for (int rr = 0; rr < 2; ++rr) {
+    const int row = row0 + rr;
+    if (row >= a.n_rows) continue;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int f = f0 + k;
+      if (f >= a.n_chan) continue;
+      const size_t idx = (size_t)row * a.n_chan + f;
+      float2 v = rr == 0 ? make_float2(Vre[k].x, Vim[k].x) : make_float2(Vre[k].y, Vim[k].y);
+      if (!ok) v = make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
+      if (a.mode == OUT_STORE) {
+        a.out[idx] = v;
+      } else if (a.mode == OUT_ACCUM) {
+        float2 o = a.out[idx];
+        a.out[idx] = make_float2(o.x + v.x, o.y + v.y);
+      } else {
+        float2 G;
+        if (!gain_product(a.peel, row, a.n_base, f, G)) atomicOr(a.err, WN_DEVERR_ANTENNA);
+        const float2 d = a.mode == OUT_SUBG ? a.out[idx] : a.peel.data[idx];
+        a.out[idx] = make_float2(d.x - (G.x * v.x - G.y * v.y), d.y - (G.x * v.y + G.y * v.x));
+      }
+    }
   }
 }
 

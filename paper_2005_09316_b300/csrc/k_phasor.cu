@@ -89,37 +89,6 @@ __device__ __forceinline__ void k1_comp_list(const float4 c, const float4 Ra, co
   }
 }
 
-// Write a lane's K channels of its two rows (rows row0, row0 + 1; channels f0 ..) in the output mode:
-// store, accumulate, the peel residual D - G V, or subtract G V from the output.
-template <int K>
-__device__ __forceinline__ void k1_store(const K1Args& a, const int row0, const int f0, const float2* Vre,
-                                         const float2* Vim, const bool ok) {
-#pragma unroll
-  for (int rr = 0; rr < 2; ++rr) {
-    const int row = row0 + rr;
-    if (row >= a.n_rows) continue;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const int f = f0 + k;
-      if (f >= a.n_chan) continue;
-      const size_t idx = (size_t)row * a.n_chan + f;
-      float2 v = rr == 0 ? make_float2(Vre[k].x, Vim[k].x) : make_float2(Vre[k].y, Vim[k].y);
-      if (!ok) v = make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
-      if (a.mode == OUT_STORE) {
-        a.out[idx] = v;
-      } else if (a.mode == OUT_ACCUM) {
-        float2 o = a.out[idx];
-        a.out[idx] = make_float2(o.x + v.x, o.y + v.y);
-      } else {
-        float2 G;
-        if (!gain_product(a.peel, row, a.n_base, f, G)) atomicOr(a.err, WN_DEVERR_ANTENNA);
-        const float2 d = a.mode == OUT_SUBG ? a.out[idx] : a.peel.data[idx];
-        a.out[idx] = make_float2(d.x - (G.x * v.x - G.y * v.y), d.y - (G.x * v.y + G.y * v.x));
-      }
-    }
-  }
-}
-
 // One (row tile, channel block) of one observation over the component tiles t_beg .. t_end-1 (32
 // components each, points first): the body of the single-launch kernel below and of the batched
 // serving kernel.  With part == nullptr the visibilities are written in the output mode; otherwise the

@@ -68,46 +68,53 @@ __global__ void kp_dfma(float* out, int iters, double a, double b) {
   out[blockIdx.x * blockDim.x + threadIdx.x] = (float)s;
 }
 
-// The point/Gaussian kernel's channel loop by itself (k1_comp_uniform, K = 12): per pass, four tiles of
-// 32 points and one of 32 Gaussians (the 4:1 mix of the MWA-like workload) read from shared memory
-// against two rows x 12 channels per lane, at the kernel's occupancy of 2 CTAs of 256 threads per SM.
-// No records, no global memory and no barriers inside the loop: the rate the full kernel approaches.
+// The point/Gaussian kernel's channel loop by itself (ks_comp_uniform, K = 12, the single-launch
+// form): per pass, four groups of 16 points and one of 16 Gaussians (the 4:1 mix of the MWA-like
+// workload), their 48-byte records and spectrum values held in shared memory, against two rows x 12
+// channels per lane, at the kernel's occupancy of one CTA of 512 threads per SM.  No record building,
+// no global memory and no barriers inside the loop: the rate the full kernel approaches.
 constexpr int KP_LOOP_K = 12;
+constexpr int KP_LOOP_GROUPS = 5;    // groups of 16 components per pass
+constexpr int KP_LOOP_THREADS = 512;
 
-__global__ void __launch_bounds__(256, 2) kp_loop(float* out, int passes) {
-  __shared__ float4 rec[32 * 3];
-  __shared__ float4 cs[32];
-  const int tid = threadIdx.x;
-  if (tid < 32) {
+__global__ void __launch_bounds__(KP_LOOP_THREADS, 1) kp_loop(float* out, int passes) {
+  extern __shared__ __align__(16) unsigned char kp_smem[];
+  float4* rec = reinterpret_cast<float4*>(kp_smem);          // [16][3]
+  float* tab = reinterpret_cast<float*>(rec + 48);             // [16][384]
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (tid < 16) {
     const float ph = 1e-3f * tid;
-    rec[3 * tid] = make_float4(1234.5f + tid, 1e-5f, 2345.25f + tid, -1e-5f);
+    rec[3 * tid] = make_float4(1234.5f + tid, 2345.25f + tid, 1e-5f, -1e-5f);
     rec[3 * tid + 1] = make_float4(cosf(ph), cosf(2.f * ph), -sinf(ph), -sinf(2.f * ph));
-    rec[3 * tid + 2] = make_float4(sinf(ph), sinf(2.f * ph), -1e-3f * tid, -2e-3f * tid);
-    cs[tid] = make_float4(-0.01f * tid, -0.8f, (tid & 1) ? 3.14159265f : 0.f, (tid & 1) ? -1.f : 1.f);
+    rec[3 * tid + 2] = make_float4(-1e-3f * tid, -2e-3f * tid, (tid & 1) ? 3.14159265f : 0.f, 0.f);
   }
+  for (int i = tid; i < 16 * 384; i += KP_LOOP_THREADS) tab[i] = 1.0f + 1e-4f * (i & 511);
   __syncthreads();
-  float lam[KP_LOOP_K], wg[KP_LOOP_K];
-  const float a0h = 0.557f + 1e-4f * (tid & 31), a0l = 1e-9f;
+  float wg[KP_LOOP_K];
+  const float a0h = 0.557f + 1e-4f * lane, a0l = 1e-9f;
 #pragma unroll
-  for (int k = 0; k < KP_LOOP_K; ++k) {
-    lam[k] = 0.01f * k + 1e-4f * tid;
-    wg[k] = 1e-3f * (k + 1);
-  }
+  for (int k = 0; k < KP_LOOP_K; ++k) wg[k] = 1e-3f * (k + 1);
   float2 Vre[KP_LOOP_K], Vim[KP_LOOP_K];
 #pragma unroll
   for (int k = 0; k < KP_LOOP_K; ++k) Vre[k] = Vim[k] = make_float2(0.f, 0.f);
+  const float* tb = tab + lane * KP_LOOP_K;
   for (int it = 0; it < passes; ++it) {
-    for (int t = 0; t < 4; ++t)
-      for (int j = 0; j < 32; ++j)
-        k1_comp_uniform<KP_LOOP_K, false>(cs[j], rec[3 * j], rec[3 * j + 1], rec[3 * j + 2], a0h, a0l, lam, wg, Vre,
-                                          Vim);
-    for (int j = 0; j < 32; ++j)
-      k1_comp_uniform<KP_LOOP_K, true>(cs[j], rec[3 * j], rec[3 * j + 1], rec[3 * j + 2], a0h, a0l, lam, wg, Vre, Vim);
+    for (int t = 0; t < KP_LOOP_GROUPS; ++t) {
+      if (t == KP_LOOP_GROUPS - 1) {
+        for (int j = 0; j < 16; ++j)
+          ks_comp_uniform<KP_LOOP_K, true>(rec[3 * j], rec[3 * j + 1], rec[3 * j + 2], tb + j * 384, a0h, a0l, wg,
+                                           Vre, Vim);
+      } else {
+        for (int j = 0; j < 16; ++j)
+          ks_comp_uniform<KP_LOOP_K, false>(rec[3 * j], rec[3 * j + 1], rec[3 * j + 2], tb + j * 384, a0h, a0l, wg,
+                                            Vre, Vim);
+      }
+    }
   }
-  float s = 0.f;
+  float sum = 0.f;
 #pragma unroll
-  for (int k = 0; k < KP_LOOP_K; ++k) s += Vre[k].x + Vre[k].y + Vim[k].x + Vim[k].y;
-  out[blockIdx.x * blockDim.x + tid] = s;
+  for (int k = 0; k < KP_LOOP_K; ++k) sum += Vre[k].x + Vre[k].y + Vim[k].x + Vim[k].y;
+  out[blockIdx.x * blockDim.x + tid] = sum;
 }
 
 // tcgen05 throughput as the shapelet kernel uses it: kind::f16 MMAs (M = 128, K = 16, bf16 operands,
@@ -244,7 +251,8 @@ extern "C" int wn_phasor_loop_rate(wn_ctx* ctx, double* evals_per_s) {
   int prev = 0;
   cudaGetDevice(&prev);
   cudaError_t e = cudaSetDevice(ctx->device);
-  const int blocks = ctx->num_sms * 2, threads = 256, passes = 40;
+  const int blocks = ctx->num_sms, threads = KP_LOOP_THREADS, passes = 40;
+  const int smem = 48 * 16 + 16 * 384 * 4;
   float* out = nullptr;
   cudaStream_t st = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -255,7 +263,7 @@ extern "C" int wn_phasor_loop_rate(wn_ctx* ctx, double* evals_per_s) {
   float best = 1e30f;
   for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {  // the first launch is a warm-up
     e = cudaEventRecord(e0, st);
-    kp_loop<<<blocks, threads, 0, st>>>(out, passes);
+    kp_loop<<<blocks, threads, smem, st>>>(out, passes);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaEventRecord(e1, st);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -263,7 +271,7 @@ extern "C" int wn_phasor_loop_rate(wn_ctx* ctx, double* evals_per_s) {
     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
     if (e == cudaSuccess && rep > 0 && ms < best) best = ms;
   }
-  *evals_per_s = (double)blocks * threads * passes * 5 * 32 * 2 * KP_LOOP_K / (best * 1e-3);
+  *evals_per_s = (double)blocks * threads * passes * KP_LOOP_GROUPS * 16 * 2 * KP_LOOP_K / (best * 1e-3);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   if (st) cudaStreamDestroy(st);

@@ -136,7 +136,7 @@ static int run_model(wn_ctx* ctx, const ObsDev& d, const Model* M, float2* out, 
   if (ctx->precision != WN_PREC_MIXED) return launch_phasor_fp64(ctx, d, M, out, mode, pa, true, st);
   int r = WN_OK;
   const bool have_pg = M->n_point + M->n_gauss > 0;
-  if (have_pg || M->n_shape == 0) r = launch_phasor_mixed(ctx, d, M, out, mode, pa, st);
+  if (have_pg || M->n_shape == 0) r = launch_phasor_table(ctx, d, M, out, mode, pa, st);
   if (r != WN_OK) return r;
   if (M->n_shape > 0) {
     // with points/Gaussians already written the shapelet pass adds (or subtracts G times) its part;
@@ -217,6 +217,7 @@ void wn_destroy(wn_ctx* ctx) {
   cudaFree(ctx->ws);
   cudaFree(ctx->ws2);
   cudaFree(ctx->lut);
+  cudaFree(ctx->ws_spec);
   delete ctx;
 }
 

@@ -119,6 +119,8 @@ struct wn_ctx {
   float* lut = nullptr;  // basis table of the lookup-table shapelet mode (built on first use)
   float2* k1_part = nullptr;  // partial sums of the split tail tiles of the phasor launch (fixed size)
   float4* static_scratch = nullptr;  // device address of wn_predict_static's file-scope array (set-up)
+  float* ws_spec = nullptr;  // spectrum table of the point/Gaussian phasor launch (grow-only)
+  size_t ws_spec_bytes = 0;
 };
 // An NVTX range named after the entry point, for the duration of the call, when the context traces.
 // NVTX is header-only: without a tool attached a range costs a few nanoseconds.
@@ -380,6 +382,8 @@ struct ObsDev {
 };
 int launch_pack(wn_ctx* ctx, const wn_sky* sky, Model* M, cudaStream_t st);
 int launch_phasor_mixed(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, int mode, const PeelArgs& pa,
+                        cudaStream_t st);
+int launch_phasor_table(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, int mode, const PeelArgs& pa,
                         cudaStream_t st);
 int launch_phasor_fp64(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, int mode, const PeelArgs& pa,
                        bool include_shapelets, cudaStream_t st);
