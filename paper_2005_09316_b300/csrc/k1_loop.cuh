@@ -209,16 +209,17 @@ __device__ __forceinline__ void k1_store(const K1Args& a, const int row0, const 
       const size_t idx = (size_t)row * a.n_chan + f;
       float2 v = rr == 0 ? make_float2(Vre[k].x, Vim[k].x) : make_float2(Vre[k].y, Vim[k].y);
       if (!ok) v = make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
+      // data and output stream past L2 (evict first): each element is touched once
       if (a.mode == OUT_STORE) {
-        a.out[idx] = v;
+        __stcs(a.out + idx, v);
       } else if (a.mode == OUT_ACCUM) {
-        float2 o = a.out[idx];
-        a.out[idx] = make_float2(o.x + v.x, o.y + v.y);
+        const float2 o = __ldcs(a.out + idx);
+        __stcs(a.out + idx, make_float2(o.x + v.x, o.y + v.y));
       } else {
         float2 G;
         if (!gain_product(a.peel, row, a.n_base, f, G)) atomicOr(a.err, WN_DEVERR_ANTENNA);
-        const float2 d = a.mode == OUT_SUBG ? a.out[idx] : a.peel.data[idx];
-        a.out[idx] = make_float2(d.x - (G.x * v.x - G.y * v.y), d.y - (G.x * v.y + G.y * v.x));
+        const float2 d = a.mode == OUT_SUBG ? __ldcs(a.out + idx) : __ldcs(a.peel.data + idx);
+        __stcs(a.out + idx, make_float2(d.x - (G.x * v.x - G.y * v.y), d.y - (G.x * v.y + G.y * v.x)));
       }
     }
   }

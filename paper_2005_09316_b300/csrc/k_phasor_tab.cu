@@ -114,6 +114,45 @@ __global__ void ks_spectrum(const PGRec* comps, int n_point, int n_gauss, int n_
   spec[idx] = gauss ? e : ex2_approx(e);
 }
 
+// One output element in the output mode: store, accumulate, the peel residual D - G V, or subtract
+// G V from the output; data and output are streamed past L2 (evict first) so that the spectrum table
+// stays resident.
+__device__ __forceinline__ float2 ks_out_value(const K1Args& a, int row, int f, float2 v, const float2* out) {
+  if (a.mode == OUT_STORE) return v;
+  if (a.mode == OUT_ACCUM) {
+    const float2 o = __ldcs(out);
+    return make_float2(o.x + v.x, o.y + v.y);
+  }
+  float2 G;
+  if (!gain_product(a.peel, row, a.n_base, f, G)) atomicOr(a.err, WN_DEVERR_ANTENNA);
+  const float2 d = a.mode == OUT_SUBG ? __ldcs(out) : __ldcs(a.peel.data + (out - a.out));
+  return make_float2(d.x - (G.x * v.x - G.y * v.y), d.y - (G.x * v.y + G.y * v.x));
+}
+
+// A warp writes its rpw rows (row0 ..) of one channel block (channels fbase .. fbase + cb - 1) from
+// the staged values stg[row][channel]: consecutive lanes take consecutive channel pairs as 16-byte
+// vectors, or single channels when a pair could start on an 8-byte boundary (an odd n_chan, or an
+// output array that is 8- but not 16-byte aligned).
+__device__ __forceinline__ void ks_store_rows(const K1Args& a, int row0, int rpw, int fbase, int cb, const float2* stg,
+                                              int lane) {
+  const int nf = min(cb, a.n_chan - fbase);
+  for (int rr = 0; rr < rpw; ++rr) {
+    const int row = row0 + rr;
+    if (row >= a.n_rows) break;
+    const float2* src = stg + rr * cb;
+    float2* dst = a.out + (size_t)row * a.n_chan + fbase;
+    if ((a.n_chan & 1) == 0 && (reinterpret_cast<uintptr_t>(a.out) & 15) == 0) {  // nf is even
+      for (int i = lane; 2 * i < nf; i += 32) {
+        const float2 v0 = ks_out_value(a, row, fbase + 2 * i, src[2 * i], dst + 2 * i);
+        const float2 v1 = ks_out_value(a, row, fbase + 2 * i + 1, src[2 * i + 1], dst + 2 * i + 1);
+        __stcs(reinterpret_cast<float4*>(dst + 2 * i), make_float4(v0.x, v0.y, v1.x, v1.y));
+      }
+    } else {
+      for (int i = lane; i < nf; i += 32) __stcs(dst + i, ks_out_value(a, row, fbase + i, src[i], dst + i));
+    }
+  }
+}
+
 // One (row tile, channel block) over component groups g_beg .. g_end-1.  With part == nullptr the
 // visibilities are written in the output mode; otherwise the raw partial sums go to part (2K x 512
 // float2, thread fastest) for ks_tail_sum.
@@ -311,7 +350,18 @@ __device__ __forceinline__ void ks_tile(const KSArgs& A, const int bx, const int
       part[(2 * k + 1) * KS_THREADS + threadIdx.x] = ok ? Vim[k] : nan2;
     }
   } else {
-    k1_store<K>(a, row_w0 + 2 * g, f0, Vre, Vim, ok);
+    // stage the warp's rows in the freed second-level-sum area as [row][channel], then write them with
+    // warp-coalesced 16-byte accesses
+    __syncthreads();  // every thread has read its second-level sums
+    float2* stg = reinterpret_cast<float2*>(smem + lay.acc) + (size_t)warp * rpw * cb;
+    const float2 nan2 = make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      stg[(2 * g) * cb + sub * K + k] = ok ? make_float2(Vre[k].x, Vim[k].x) : nan2;
+      stg[(2 * g + 1) * cb + sub * K + k] = ok ? make_float2(Vre[k].y, Vim[k].y) : nan2;
+    }
+    __syncwarp();
+    ks_store_rows(a, row_w0, rpw, by * cb, cb, stg, lane);
   }
   __syncthreads();  // every warp is past its last barrier wait and shared-memory read
   if (threadIdx.x == 0) {

@@ -337,3 +337,32 @@ def test_mwa_full_size_sampled_rows(wn, ctx):
     assert np.max(np.abs(got - ref)) <= 1e-5 * np.max(np.abs(V))
     assert ctx.device_errors() == 0
     m.free()
+
+
+@pytest.mark.parametrize("n_chan", [64, 37])
+def test_output_arrays_only_8_byte_aligned(wn, ctx, n_chan):
+    """An output (and data) array that starts 8 bytes past a 16-byte boundary, as a complex64 view may:
+    the coalesced epilogue then writes single channels instead of 16-byte pairs; predict and peel
+    results equal those of aligned arrays bit for bit."""
+    obs = small_obs(31, 24, 2, synth.uniform_channels(167e6, 80e3, n_chan), layout="mwa")
+    sky = synth.make_sky(32, 300, 70, 0, fov=10 * synth.DEG)
+    d = wn.obs_to_device(obs)
+    m = ctx.upload(sky)
+    shape = (obs.n_time, obs.n_base, obs.n_chan)
+    n = obs.n_vis
+    ref = ctx.predict(d, m)
+    buf = torch.zeros(n + 1, dtype=torch.complex64, device="cuda")
+    view = buf[1:].view(shape)
+    assert view.data_ptr() % 16 == 8
+    ctx.predict(d, m, out=view)
+    assert torch.equal(view, ref)
+    gains = torch.as_tensor(synth.make_gains(33, obs.n_ant).astype(np.complex64)).cuda()
+    data = torch.randn(shape, dtype=torch.complex64, device="cuda", generator=torch.Generator(device="cuda").manual_seed(3))
+    rref = ctx.peel(d, m, gains, data)
+    dbuf = torch.zeros(n + 1, dtype=torch.complex64, device="cuda")
+    dview = dbuf[1:].view(shape)
+    dview.copy_(data)
+    ctx.peel(d, m, gains, dview, out=view)
+    assert torch.equal(view, rref)
+    m.free()
+    assert ctx.device_errors() == 0
