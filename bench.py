@@ -254,9 +254,23 @@ def bench_shapelets(wn, ctx, local, P, torch):
     ms_tf32 = timed(lambda: ctx.peel(d, m, gains, data, out=out), 10)
     got_tf32 = out.reshape(obs.n_rows, obs.n_chan)[idx].cpu().numpy()
     err_tf32 = float(np.abs(got_tf32 - ref).max() / np.abs(V).max())
+    # tf32 hi + lo operands, three products
+    ctx.set_precision(0, wn.WN_SHAPE_TF32X3)
+    ms_tf32x3 = timed(lambda: ctx.peel(d, m, gains, data, out=out), 10)
+    got_x3 = out.reshape(obs.n_rows, obs.n_chan)[idx].cpu().numpy()
+    err_x3 = float(np.abs(got_x3 - ref).max() / np.abs(V).max())
     ctx.set_precision(0, wn.WN_SHAPE_BF16X3)
     tf_tf32 = sum(2.0 * obs.n_vis * kp * npad for kp, npad in pads) / (ms_tf32 * 1e-3) / 1e12  # one product
-    peak_tf32 = peak / 2.0  # tf32 tensor rate: half the bf16 one (nominal ratio)
+    tf_x3 = 3.0 * sum(2.0 * obs.n_vis * kp * npad for kp, npad in pads) / (ms_tf32x3 * 1e-3) / 1e12
+    peak_tf32, tf32_basis = measured_tf32_peak(torch)
+    if peak_tf32 is None:
+        peak_tf32, tf32_basis = peak / 2.0, "measured bf16 peak x the nominal tf32/bf16 ratio 1/2"
+    try:  # the kernel's own instruction, timed alone: clocks per MMA of each kind at N = 128
+        c16, c32 = ctx.mma_rate()["clk_per_mma_n128"], ctx.mma_rate_tf32()["clk_per_mma_n128"]
+        mma_ratio = {"clk_bf16_k16": round(c16, 2), "clk_tf32_k8": round(c32, 2),
+                     "tf32_over_bf16_flops": round(c16 / (2.0 * c32), 4)}
+    except Exception as exc:  # noqa: BLE001 - reported, not fatal
+        mma_ratio = f"unavailable: {exc}"
     m.free()
     # the equivalent multi-scale-CLEAN-like model on the same observation
     _, clean = synth.fornax_clean()
@@ -276,13 +290,44 @@ def bench_shapelets(wn, ctx, local, P, torch):
                                  "2 nnz per visibility"},
             "error": {"e_norm": err, "tolerance": 1e-3, "sample": "16 rows x 384 ch vs oracle peel"},
             "tf32": {"ms_per_step": round(ms_tf32, 4), "e_norm": err_tf32,
-                     "roofline": {"bound": "tensor", "achieved": round(tf_tf32, 2), "peak": peak_tf32, "unit": "TFLOP/s",
-                                  "frac": round(tf_tf32 / peak_tf32, 4),
-                                  "peak_basis": "measured bf16 peak x the nominal tf32/bf16 ratio 1/2"},
+                     "roofline": {"bound": "tensor", "achieved": round(tf_tf32, 2), "peak": round(peak_tf32, 1),
+                                  "unit": "TFLOP/s", "frac": round(tf_tf32 / peak_tf32, 4), "peak_basis": tf32_basis,
+                                  "tcgen05_clocks": mma_ratio},
                      "note": "tf32 operands rounded to nearest, one product per visibility"},
+            "tf32x3": {"ms_per_step": round(ms_tf32x3, 4), "e_norm": err_x3,
+                       "roofline": {"bound": "tensor", "achieved": round(tf_x3, 2), "peak": round(peak_tf32, 1),
+                                    "unit": "TFLOP/s", "frac": round(tf_x3 / peak_tf32, 4), "peak_basis": tf32_basis},
+                       "note": "tf32 hi+lo operands, three products (hi*hi + hi*lo + lo*hi) per visibility"},
             "lookup_table_basis": {"ms_per_step": round(ms_lut, 4), "e_norm": err_lut,
                                    "note": "phi_n interpolated from a 1/256-spaced table in L2 instead of the recurrence"},
             "clean_model_40k_ms": round(ms_clean, 3), "clean_over_shapelet_time": round(ms_clean / ms, 2)}
+
+
+def measured_tf32_peak(torch):
+    """Dense tf32 tensor throughput of this GPU, measured as the bf16 peak is: cuBLAS through torch, an
+    8192^3 float32 matmul with tf32 allowed (2 N^3 flops), best of 10 after warm-up."""
+    try:
+        prev = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = True
+        n = 8192
+        a = torch.randn(n, n, device="cuda", dtype=torch.float32)
+        b = torch.randn(n, n, device="cuda", dtype=torch.float32)
+        for _ in range(3):
+            a @ b
+        torch.cuda.synchronize()
+        best = float("inf")
+        e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+        for _ in range(10):
+            e0.record()
+            a @ b
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        torch.backends.cuda.matmul.allow_tf32 = prev
+        del a, b
+        return 2.0 * n ** 3 / (best * 1e-3) / 1e12, "measured: cuBLAS tf32 GEMM 8192^3 (torch, tf32 allowed), best of 10, this run"
+    except Exception:  # noqa: BLE001 - fall back to the nominal ratio
+        return None, None
 
 
 def nnz_all(sky) -> int:
@@ -303,7 +348,8 @@ def summary_block(line: dict) -> dict:
                "loop_bound_frac": g("roofline", "loop_bound", "frac")},
         "k2_fornax": {"ms": g("shapelet", "ms_per_step"), "issued_frac": g("shapelet", "roofline", "frac"),
                       "useful_frac": g("shapelet", "roofline", "useful_frac"), "e_norm": g("shapelet", "error", "e_norm"),
-                      "tf32_ms": g("shapelet", "tf32", "ms_per_step")},
+                      "tf32_ms": g("shapelet", "tf32", "ms_per_step"), "tf32x3_ms": g("shapelet", "tf32x3", "ms_per_step"),
+                      "tf32x3_e_norm": g("shapelet", "tf32x3", "e_norm")},
         "k3_peel": {"gbs": g("standalone_peel", "achieved_gbs"), "frac": g("standalone_peel", "frac")},
         "k4_adjoint_ms": g("adjoint", "ms_per_step"),
         "k5_fp64": {"evals_per_s": g("fp64_gpu", "value"), "speedup": g("fp64_gpu", "speedup_mixed_over_fp64"),

@@ -79,10 +79,13 @@ typedef enum {
     WN_SHAPE_LUT_BF16X3 = 2, /* as BF16X3, but the Hermite functions are interpolated linearly from a 1-D table
                                 (spacing 1/256, orders 0..127; the look-up tables of Sec. 3.2) instead of the
                                 recurrence; the table (6.8 MB) is built once per context */
-    WN_SHAPE_TF32 = 3        /* tf32 operands (both rounded to nearest from FP32, 10 explicit mantissa bits), one
-                                product, FP32 accumulate.  A tf32 hi+lo split (three products) is not offered:
-                                its two A tiles per block do not fit the kernel's shared memory beside the
-                                coefficient operand. */
+    WN_SHAPE_TF32 = 3,       /* tf32 operands (both rounded to nearest from FP32, 10 explicit mantissa bits), one
+                                product, FP32 accumulate */
+    WN_SHAPE_TF32X3 = 4      /* tf32 hi+lo split of both operands (hi = RN_tf32(x), lo = RN_tf32(x - hi)), three
+                                products hi*hi + hi*lo + lo*hi, FP32 accumulate: about FP32 accuracy.  The split
+                                operands take 8 bytes per element; they fit the kernel's shared memory when the
+                                coefficients reach orders n1 + n2 up to 63 (k_pad 64, n_pad 128); a call on a
+                                model with a higher order returns WN_EINVAL. */
 } wn_shape_mode;
 
 /* Device-side error flags (bit mask) reported by wn_device_errors. */
@@ -191,10 +194,11 @@ WN_API int wn_sky_bytes(wn_ctx* ctx, int model_id, size_t* bytes_out);
  * host_out may be NULL to query k_pad and n_pad; otherwise it must hold bytes >= 4 k_pad n_pad.
  * Synchronous.  WN_ENOTFOUND for an unknown model, WN_EINVAL for q outside [0, n_shape) or a short
  * buffer. */
-/* The tf32 copy of the same operand (WN_SHAPE_TF32), copied to HOST memory: k_pad x n_pad FP32 values,
- * each RN_tf32 (ties away from zero) of float(value), in the K-major layout with 8 x 4 core matrices:
- * element (n, k) at ((k/4) (n_pad/8) + n/8) 32 + (n%8) 4 + k%4.  Same arguments, sizes and errors as
- * wn_sky_shapelet_operand (bytes >= 4 k_pad n_pad). */
+/* The tf32 copy of the same operand (WN_SHAPE_TF32, WN_SHAPE_TF32X3), copied to HOST memory: k_pad x n_pad
+ * FP32 values, each hi = RN_tf32 (ties away from zero) of float(value), in the K-major layout with 8 x 4
+ * core matrices: element (n, k) at ((k/4) (n_pad/8) + n/8) 32 + (n%8) 4 + k%4.  When bytes >= 8 k_pad n_pad
+ * the remainder operand lo = RN_tf32(float(value) - hi) follows in the same layout.  Same arguments and
+ * errors as wn_sky_shapelet_operand (bytes >= 4 k_pad n_pad). */
 WN_API int wn_sky_shapelet_operand_tf32(wn_ctx* ctx, int model_id, int q, void* host_out, size_t bytes, int* k_pad,
                                         int* n_pad);
 WN_API int wn_sky_shapelet_operand(wn_ctx* ctx, int model_id, int q, void* host_out, size_t bytes, int* k_pad,
@@ -366,6 +370,13 @@ WN_API int wn_phasor_loop_rate(wn_ctx* ctx, double* evals_per_s);
  * (one warp, alone), and of eight such loads under one wait.  Allocates a small buffer and synchronises
  * its own stream; flags WN_DEVERR_TIMEOUT if a bounded wait gave up. */
 WN_API int wn_mma_rate(wn_ctx* ctx, double* out);
+
+/* The same timing for the shapelet kernel's tf32 mode (no paper counterpart): 2,048 tcgen05 kind::tf32 MMAs
+ * (M = 128, K = 8, tf32 operands: the same 32 bytes of each operand row as one K = 16 bf16 MMA, FP32
+ * accumulator) per CTA, one CTA per SM, zero operands K-major in the kernel's no-swizzle layout.  out
+ * (2 doubles): SM clocks per MMA instruction at N = 128 and at N = 64.  Allocates a small buffer and
+ * synchronises its own stream. */
+WN_API int wn_mma_rate_tf32(wn_ctx* ctx, double* out);
 
 /* The failure path of the kernels' bounded waits, without a fault (no paper counterpart).  A one-thread
  * kernel waits on an mbarrier that nothing ever arrives at, through the same bounded-wait helper as the

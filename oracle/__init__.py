@@ -260,6 +260,24 @@ def pack_coeff_tf32(nmax: int, n1, n2, c, k_pad: int, n_pad: int) -> np.ndarray:
     return f32_to_tf32_bits(dense.astype(np.float32))
 
 
+def tf32_bits_to_f32(b) -> np.ndarray:
+    return np.asarray(b, dtype=np.uint32).view(np.float32)
+
+
+def pack_coeff_tf32x3(nmax: int, n1, n2, c, k_pad: int, n_pad: int):
+    """The split tf32 operand pair [n_pad][k_pad] as bit patterns: hi = RN_tf32(float32(value)) and
+    lo = RN_tf32(float32(value) - hi), the difference taken in float32 (where it is exact)."""
+    hi = pack_coeff_tf32(nmax, n1, n2, c, k_pad, n_pad)
+    re, im = parity_split(nmax, n1, n2, c)
+    dense = np.zeros((n_pad, k_pad))
+    for b in range(nmax + 1):
+        dense[2 * b, :nmax + 1] = re[:, b]
+        dense[2 * b + 1, :nmax + 1] = im[:, b]
+    d32 = dense.astype(np.float32)
+    lo = f32_to_tf32_bits((d32 - tf32_bits_to_f32(hi)).astype(np.float32))
+    return hi, lo
+
+
 def pack_coeff_bf16(nmax: int, n1, n2, c, k_pad: int, n_pad: int):
     """Dense B operand of the shapelet contraction, as bf16 hi/lo bit patterns [n_pad][k_pad]:
     row 2*n2 holds Re(C (-i)^(n1+n2))[n1, n2] over n1 (the K index), row 2*n2+1 the imaginary part."""

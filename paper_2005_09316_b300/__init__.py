@@ -21,7 +21,7 @@ _lock = threading.Lock()
 
 WN_OK, WN_EINVAL, WN_ENOMEM, WN_ECUDA, WN_ETIMEOUT, WN_EBUSY, WN_ENOTFOUND = range(7)
 WN_PREC_MIXED, WN_PREC_FP64, WN_PREC_FP64_UNTUNED = 0, 1, 2
-WN_SHAPE_BF16X3, WN_SHAPE_BF16X1, WN_SHAPE_LUT_BF16X3, WN_SHAPE_TF32 = 0, 1, 2, 3
+WN_SHAPE_BF16X3, WN_SHAPE_BF16X1, WN_SHAPE_LUT_BF16X3, WN_SHAPE_TF32, WN_SHAPE_TF32X3 = 0, 1, 2, 3, 4
 WN_DEVERR_ANTENNA, WN_DEVERR_TIMEOUT, WN_DEVERR_SKY, WN_DEVERR_CALIB = 0x1, 0x2, 0x4, 0x8
 
 EXPORTED = ("wn_create", "wn_destroy", "wn_last_error", "wn_version", "wn_set_precision", "wn_device_errors",
@@ -29,7 +29,7 @@ EXPORTED = ("wn_create", "wn_destroy", "wn_last_error", "wn_version", "wn_set_pr
             "wn_predict_grad", "wn_predict_static", "wn_server_create", "wn_server_destroy", "wn_server_submit",
             "wn_server_poll", "wn_server_wait", "wn_server_copy", "wn_server_release", "wn_server_cancel",
             "wn_server_stats", "wn_server_set_policy", "wn_calibrate", "wn_fit_shapelets", "wn_pipe_rates",
-            "wn_phasor_loop_rate", "wn_sky_shapelet_operand", "wn_selftest_timeout", "wn_mma_rate", "wn_set_trace", "wn_debug_fail_allocs",
+            "wn_phasor_loop_rate", "wn_sky_shapelet_operand", "wn_selftest_timeout", "wn_mma_rate", "wn_mma_rate_tf32", "wn_set_trace", "wn_debug_fail_allocs",
             "wn_sky_shapelet_operand_tf32")
 
 
@@ -109,6 +109,7 @@ def load(build_if_missing: bool = True):
         L.wn_phasor_loop_rate.argtypes = [P, ctypes.POINTER(dbl)]
         L.wn_selftest_timeout.argtypes = [P, dbl]
         L.wn_mma_rate.argtypes = [P, ctypes.POINTER(dbl)]
+        L.wn_mma_rate_tf32.argtypes = [P, ctypes.POINTER(dbl)]
         L.wn_set_trace.argtypes = [P, ctypes.c_int]
         L.wn_debug_fail_allocs.argtypes = [ctypes.c_int]
         L.wn_sky_shapelet_operand_tf32.argtypes = L.wn_sky_shapelet_operand.argtypes
@@ -243,14 +244,18 @@ class Model:
         half = kp.value * npd.value
         return buf[:half], buf[half:], kp.value, npd.value
 
-    def shapelet_operand_tf32(self, q: int):
+    def shapelet_operand_tf32(self, q: int, with_lo: bool = False):
         """Shapelet q's tf32 operand as raw FP32 bit patterns (uint32, k_pad x n_pad in the K-major order of
-        8 x 4 core matrices) with k_pad and n_pad."""
+        8 x 4 core matrices) with k_pad and n_pad; with_lo: (hi, lo, k_pad, n_pad), lo being the tf32
+        remainder operand of WN_SHAPE_TF32X3."""
         kp, npd = ctypes.c_int(), ctypes.c_int()
         f = load().wn_sky_shapelet_operand_tf32
         _check(f(self.ctx.h, self.id, q, None, 0, ctypes.byref(kp), ctypes.byref(npd)))
-        buf = np.empty(kp.value * npd.value, dtype=np.uint32)
+        n = kp.value * npd.value
+        buf = np.empty(2 * n if with_lo else n, dtype=np.uint32)
         _check(f(self.ctx.h, self.id, q, buf.ctypes.data, buf.nbytes, ctypes.byref(kp), ctypes.byref(npd)))
+        if with_lo:
+            return buf[:n], buf[n:], kp.value, npd.value
         return buf, kp.value, npd.value
 
     def free(self):
@@ -338,6 +343,12 @@ class Context:
         r = (ctypes.c_double * 4)()
         _check(load().wn_mma_rate(self.h, r))
         return {"clk_per_mma_n128": r[0], "clk_per_mma_n64": r[1], "clk_tmem_ld16": r[2], "clk_tmem_ld16_x8": r[3]}
+
+    def mma_rate_tf32(self) -> dict:
+        """SM clocks per tcgen05 MMA (M = 128, K = 8, tf32) at N = 128 and 64."""
+        r = (ctypes.c_double * 2)()
+        _check(load().wn_mma_rate_tf32(self.h, r))
+        return {"clk_per_mma_n128": r[0], "clk_per_mma_n64": r[1]}
 
     def phasor_loop_rate(self) -> float:
         """Evaluations per second the point/Gaussian kernel's channel loop sustains by itself."""

@@ -73,9 +73,10 @@ __global__ void k_pack_shape(wn_sky s, const int* b_off, const int* k_pad, const
 // Dense B operand of the shapelet contraction: column n = 2*n2 + {0: real, 1: imaginary} of
 // C[n1,n2] (-i)^(n1+n2) (eq:shape-env with the phase of eq:basis_FT), row k = n1, stored as bf16
 // hi = RN(float(C)), lo = RN(float(C) - hi) in the tcgen05 canonical K-major layout without swizzle:
-// 8x8 core matrices, element (n, k) at ((k/8) * (n_pad/8) + n/8) * 64 + (n%8) * 8 + k%8.  A tf32 copy
-// (RN(float(C)) to tf32) goes to bop32 in the same layout with 8x4 core matrices of 4-byte elements,
-// element (n, k) at ((k/4) * (n_pad/8) + n/8) * 32 + (n%8) * 4 + k%4.
+// 8x8 core matrices, element (n, k) at ((k/8) * (n_pad/8) + n/8) * 64 + (n%8) * 8 + k%8.  A tf32 copy goes
+// to bop32 in the same layout with 8x4 core matrices of 4-byte elements, element (n, k) at
+// ((k/4) * (n_pad/8) + n/8) * 32 + (n%8) * 4 + k%4: hi = RN_tf32(float(C)) at the shapelet's b_off, then
+// lo = RN_tf32(float(C) - hi) (the difference is exact in FP32) k_pad * n_pad elements further.
 __global__ void k_pack_coeff(int nnz_total, const int* n1, const int* n2, const double* c, const int* s_off,
                              const int* s_nmax, int n_shape, const int* b_off, const int* k_pad, const int* n_pad,
                              __nv_bfloat16* bop, float* bop32, unsigned* err) {
@@ -102,11 +103,16 @@ __global__ void k_pack_coeff(int nnz_total, const int* n1, const int* n2, const 
   lo[at(2 * b, a)] = __float2bfloat16_rn(re - __bfloat162float(rh));
   hi[at(2 * b + 1, a)] = ih;
   lo[at(2 * b + 1, a)] = __float2bfloat16_rn(im - __bfloat162float(ih));
-  // tf32 copy: core matrices of 8 rows x 4 elements (16 B), same order; values rounded to nearest tf32
-  float* f = bop32 + b_off[q] / 2;
+  // tf32 copy: core matrices of 8 rows x 4 elements (16 B), same order; values rounded to nearest tf32,
+  // hi then lo
+  float* f = bop32 + b_off[q];
+  float* fl = f + (size_t)np * kp;
   auto at32 = [&](int n, int k) { return ((k >> 2) * (np >> 3) + (n >> 3)) * 32 + (n & 7) * 4 + (k & 3); };
-  f[at32(2 * b, a)] = to_tf32(re);
-  f[at32(2 * b + 1, a)] = to_tf32(im);
+  const float rt = to_tf32(re), it = to_tf32(im);
+  f[at32(2 * b, a)] = rt;
+  fl[at32(2 * b, a)] = to_tf32(re - rt);
+  f[at32(2 * b + 1, a)] = it;
+  fl[at32(2 * b + 1, a)] = to_tf32(im - it);
 }
 
 static int cuda_check(cudaError_t e, const char* what) {
@@ -135,7 +141,7 @@ int launch_pack(wn_ctx* ctx, const wn_sky* s, Model* M, cudaStream_t st) {
     k_pack_shape<<<(s->n_shape + 63) / 64, 64, 0, st>>>(*s, dtmp, dtmp + s->n_shape, dtmp + 2 * s->n_shape,
                                                         M->sh, ctx->d_err);
     cudaMemsetAsync(M->bop, 0, M->bop_elems * sizeof(__nv_bfloat16), st);
-    cudaMemsetAsync(M->bop32, 0, M->bop_elems / 2 * sizeof(float), st);
+    cudaMemsetAsync(M->bop32, 0, M->bop_elems * sizeof(float), st);
     if (M->nnz > 0)
       k_pack_coeff<<<(M->nnz + 255) / 256, 256, 0, st>>>(M->nnz, s->s_n1, s->s_n2, s->s_coeff, s->s_off, s->s_nmax,
                                                          s->n_shape, dtmp, dtmp + s->n_shape, dtmp + 2 * s->n_shape,
@@ -155,7 +161,7 @@ namespace wn {
 int launch_pack_coeff(wn_ctx* ctx, Model* M, const double* coeff, const int* dmeta, cudaStream_t st) {
   if (M->n_shape == 0 || M->nnz == 0) return WN_OK;
   cudaMemsetAsync(M->bop, 0, M->bop_elems * sizeof(__nv_bfloat16), st);
-  cudaMemsetAsync(M->bop32, 0, M->bop_elems / 2 * sizeof(float), st);
+  cudaMemsetAsync(M->bop32, 0, M->bop_elems * sizeof(float), st);
   k_pack_coeff<<<(M->nnz + 255) / 256, 256, 0, st>>>(M->nnz, M->m_n1(), M->m_n2(), coeff, M->m_off(), M->m_nmax(),
                                                      M->n_shape, dmeta, dmeta + M->n_shape, dmeta + 2 * M->n_shape,
                                                      M->bop, M->bop32, ctx->d_err);

@@ -125,6 +125,7 @@ __global__ void __launch_bounds__(KP_LOOP_THREADS, 1) kp_loop(float* out, int pa
 // CTA, then the two load timings}.
 constexpr int KP_MMA_REP = 512;  // K = 64 passes (4 MMAs each)
 
+template <bool TF32>
 __global__ void __launch_bounds__(128, 1) kp_mma(int n, long long* clk, unsigned* err) {
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned char* a_t = smem + ((1024u - (smem_u32(smem) & 1023u)) & 1023u);  // 128 x 64 bf16
@@ -147,7 +148,9 @@ __global__ void __launch_bounds__(128, 1) kp_mma(int n, long long* clk, unsigned
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tslot;
   if (tid == 0) {
-    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    // kind::f16 with bf16 A and B (formats 1), or kind::tf32 (formats 2); D f32; M = 128, N = n
+    const uint32_t fmt = TF32 ? 2u : 1u;
+    const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
     const uint32_t a0 = smem_u32(a_t), b0 = smem_u32(b_t);
     const uint32_t lbo_a = (128u >> 3) << 7, lbo_b = ((uint32_t)n >> 3) << 7;
     auto desc = [](uint32_t addr, uint32_t lbo) {
@@ -160,10 +163,16 @@ __global__ void __launch_bounds__(128, 1) kp_mma(int n, long long* clk, unsigned
       for (int kk = 0; kk < 4; ++kk) {
         const uint64_t da = desc(a0 + 2u * kk * lbo_a, lbo_a), db = desc(b0 + 2u * kk * lbo_b, lbo_b);
         const uint32_t acc = (r > 0 || kk > 0) ? 1u : 0u;
-        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-                     "l"(da), "l"(db), "r"(idesc), "r"(acc)
-                     : "memory");
+        if (TF32)  // K = 8 four-byte elements: the same 32 bytes of each row as K = 16 bf16
+          asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                       "l"(da), "l"(db), "r"(idesc), "r"(acc)
+                       : "memory");
+        else
+          asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                       "l"(da), "l"(db), "r"(idesc), "r"(acc)
+                       : "memory");
       }
     }
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&bar))
@@ -322,7 +331,9 @@ extern "C" int wn_pipe_rates(wn_ctx* ctx, double* rates) {
   return WN_OK;
 }
 
-extern "C" int wn_mma_rate(wn_ctx* ctx, double* out) {
+// Clocks per MMA at N = 128 and N = 64 (out[0], out[1]) and the two TMEM load timings (out[2], out[3]).
+template <bool TF32>
+static int mma_rate(wn_ctx* ctx, double* out) {
   if (!ctx || !out) return set_error(WN_EINVAL, "NULL argument");
   int prev = 0;
   cudaGetDevice(&prev);
@@ -336,10 +347,10 @@ extern "C" int wn_mma_rate(wn_ctx* ctx, double* out) {
   const int ns[2] = {128, 64};
   // 64 KB of shared memory per CTA: at most 3 CTAs (384 TMEM columns) share an SM, so no allocation waits
   const int smem = 64 * 1024;
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(kp_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kp_mma<TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
     for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // the first launch is a warm-up
-      kp_mma<<<grid, 128, smem, st>>>(ns[i], clk, ctx->d_err);
+      kp_mma<TF32><<<grid, 128, smem, st>>>(ns[i], clk, ctx->d_err);
       e = cudaGetLastError();
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     }
@@ -362,4 +373,17 @@ extern "C" int wn_mma_rate(wn_ctx* ctx, double* out) {
   cudaSetDevice(prev);
   if (e != cudaSuccess) return set_error(WN_ECUDA, std::string("MMA rate probe: ") + cudaGetErrorString(e));
   return WN_OK;
+}
+
+extern "C" int wn_mma_rate(wn_ctx* ctx, double* out) { return mma_rate<false>(ctx, out); }
+
+extern "C" int wn_mma_rate_tf32(wn_ctx* ctx, double* out) {
+  if (!out) return set_error(WN_EINVAL, "NULL argument");
+  double full[4];
+  const int r = mma_rate<true>(ctx, full);
+  if (r == WN_OK) {
+    out[0] = full[0];
+    out[1] = full[1];
+  }
+  return r;
 }

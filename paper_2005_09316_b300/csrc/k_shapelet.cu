@@ -162,7 +162,8 @@ struct K2Layout {
 
 __host__ __device__ inline K2Layout k2_layout(int kp, int n_pad, int passes, int groups, int R, bool tf32 = false) {
   K2Layout L;
-  const int parts = passes > 1 || tf32 ? 2 : 1;  // bf16 hi + lo, or one 4-byte tf32 element
+  // 2-byte units per element: bf16 (1), bf16 hi + lo or one tf32 (2), tf32 hi + lo (4)
+  const int parts = tf32 ? (passes > 1 ? 4 : 2) : (passes > 1 ? 2 : 1);
   L.b_bytes = parts * kp * n_pad * 2;
   L.a_bytes = R * parts * kp * K2_M * 2;  // one group's A: R blocks of 128 rows (hi [+ lo])
   L.a0 = (L.b_bytes + 1023) & ~1023;
@@ -195,12 +196,22 @@ __device__ __forceinline__ void store_bf16_split(float (&v)[8], unsigned char* a
 }
 
 // Columns k0 .. k0 + 7 of one row as tf32 (rounded to nearest) into a K-major tile of 4-byte elements:
-// two core matrices, 16 row groups x 128 B apart.
-__device__ __forceinline__ void store_tf32(const float (&v)[8], unsigned char* a, int row, int k0) {
+// two core matrices, 16 row groups x 128 B apart.  With a_lo, the remainders v - hi (exact in FP32),
+// rounded to tf32, go to the same place in a second tile (the split operand of WN_SHAPE_TF32X3).
+__device__ __forceinline__ void store_tf32(const float (&v)[8], unsigned char* a, unsigned char* a_lo, int row, int k0) {
   const uint32_t off = kmaj_off32(row, k0, K2_M);
-  *reinterpret_cast<float4*>(a + off) = make_float4(to_tf32(v[0]), to_tf32(v[1]), to_tf32(v[2]), to_tf32(v[3]));
-  *reinterpret_cast<float4*>(a + off + (K2_M >> 3) * 128) =
-      make_float4(to_tf32(v[4]), to_tf32(v[5]), to_tf32(v[6]), to_tf32(v[7]));
+  float h[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) h[i] = to_tf32(v[i]);
+  *reinterpret_cast<float4*>(a + off) = make_float4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<float4*>(a + off + (K2_M >> 3) * 128) = make_float4(h[4], h[5], h[6], h[7]);
+  if (a_lo) {
+    float l[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) l[i] = to_tf32(v[i] - h[i]);
+    *reinterpret_cast<float4*>(a_lo + off) = make_float4(l[0], l[1], l[2], l[3]);
+    *reinterpret_cast<float4*>(a_lo + off + (K2_M >> 3) * 128) = make_float4(l[4], l[5], l[6], l[7]);
+  }
 }
 
 template <int KP, int R, bool SCALED, bool TF32>
@@ -226,7 +237,7 @@ __device__ __forceinline__ void produce_rows_run(const float (&x)[R], float (&p)
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
         unsigned char* hi = a_base + r * blk;
-        if constexpr (TF32) store_tf32(v[r], hi, row, k0);
+        if constexpr (TF32) store_tf32(v[r], hi, split ? hi + KP * K2_M * 4 : nullptr, row, k0);
         else store_bf16_split(v[r], hi, split ? hi + KP * K2_M * 2 : nullptr, kmaj_off(row, k0, K2_M));
       }
     }
@@ -262,7 +273,7 @@ __device__ __forceinline__ void produce_rows_run(const float (&x)[R], float (&p)
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       unsigned char* hi = a_base + r * blk;
-      if constexpr (TF32) store_tf32(v[r], hi, row, k0);
+      if constexpr (TF32) store_tf32(v[r], hi, split ? hi + KP * K2_M * 4 : nullptr, row, k0);
       else store_bf16_split(v[r], hi, split ? hi + KP * K2_M * 2 : nullptr, kmaj_off(row, k0, K2_M));
     }
   }
@@ -503,7 +514,8 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
       mbar_arrive_expect_tx(bfull, (uint32_t)lay.b_bytes);
       tma_bulk_g2s(smem, a.bop, (uint32_t)lay.b_bytes, bfull);
       const uint32_t idesc = umma_idesc_bf16(a.n_pad), idesc32 = umma_idesc_tf32(a.n_pad);
-      const uint32_t b_hi = smem_u32(smem), b_lo = b_hi + (uint32_t)(KP * a.n_pad * 2);
+      // the lo halves follow the hi ones: 2-byte bf16 or 4-byte tf32 elements
+      const uint32_t b_hi = smem_u32(smem), b_lo = b_hi + (uint32_t)(KP * a.n_pad * (TF32 ? 4 : 2));
       const uint32_t lbo_b = (uint32_t)(a.n_pad >> 3) << 7, lbo_a = (uint32_t)(K2_M >> 3) << 7;
       bool ok = k2_wait(bfull, 0, a.err);
       int done = 0;
@@ -515,14 +527,19 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
 #pragma unroll
         for (int r = 0; r < R; ++r) {  // block r of the tile into accumulator sp * R + r
           const uint32_t a_hi = smem_u32(smem + lay.a0 + sp * lay.a_bytes + r * blk);
-          const uint32_t a_lo = a_hi + (uint32_t)(KP * K2_M * 2);
+          const uint32_t a_lo = a_hi + (uint32_t)(KP * K2_M * (TF32 ? 4 : 2));
           const uint32_t d = tmem + (uint32_t)((sp * R + r) * a.n_pad);
           if constexpr (TF32) {  // K = 8 per instruction: two core matrices of 4-byte elements
+#pragma unroll 1
+            for (int p = 0; p < a.passes; ++p) {  // one product, or hi*hi, hi*lo, lo*hi
+              const uint32_t aa = (p == 2) ? a_lo : a_hi;
+              const uint32_t bb = (p == 1) ? b_lo : b_hi;
 #pragma unroll
-            for (int kk = 0; kk < KP / 8; ++kk) {
-              const uint64_t da = umma_desc(a_hi + (uint32_t)(2 * kk) * lbo_a, lbo_a, 128);
-              const uint64_t db = umma_desc(b_hi + (uint32_t)(2 * kk) * lbo_b, lbo_b, 128);
-              umma_tf32(d, da, db, idesc32, kk > 0 ? 1u : 0u);
+              for (int kk = 0; kk < KP / 8; ++kk) {
+                const uint64_t da = umma_desc(aa + (uint32_t)(2 * kk) * lbo_a, lbo_a, 128);
+                const uint64_t db = umma_desc(bb + (uint32_t)(2 * kk) * lbo_b, lbo_b, 128);
+                umma_tf32(d, da, db, idesc32, (p > 0 || kk > 0) ? 1u : 0u);
+              }
             }
             continue;
           }
@@ -877,8 +894,8 @@ int launch_shapelets_ws(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* ou
                         float4* chaninfo, float4* rowinfo, cudaStream_t st, float2* rowg) {
   k2_chaninfo<<<(o.n_chan + 255) / 256, 256, 0, st>>>(o.freq, o.n_chan, o.nu0, chaninfo);
   const long long n_vis = (long long)o.n_rows * o.n_chan;
-  const bool tf32 = ctx->shape_mode == WN_SHAPE_TF32;
-  const int passes = ctx->shape_mode == WN_SHAPE_BF16X1 || tf32 ? 1 : 3;
+  const bool tf32 = ctx->shape_mode == WN_SHAPE_TF32 || ctx->shape_mode == WN_SHAPE_TF32X3;
+  const int passes = ctx->shape_mode == WN_SHAPE_BF16X1 || ctx->shape_mode == WN_SHAPE_TF32 ? 1 : 3;
   const float* lut = nullptr;
   if (ctx->shape_mode == WN_SHAPE_LUT_BF16X3)
     if (int r = k2_lut(ctx, st, &lut)) return r;
@@ -892,7 +909,7 @@ int launch_shapelets_ws(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* ou
     K2Args a;
     a.rowinfo = rowinfo;
     a.chaninfo = chaninfo;
-    a.bop = tf32 ? reinterpret_cast<const __nv_bfloat16*>(M->bop32 + h.b_off / 2) : M->bop + h.b_off;
+    a.bop = tf32 ? reinterpret_cast<const __nv_bfloat16*>(M->bop32 + h.b_off) : M->bop + h.b_off;
     a.lut = lut;
     a.n_pad = h.n_pad;
     a.nmax = h.nmax;
@@ -922,7 +939,10 @@ int launch_shapelets_ws(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* ou
       a.groups = 1;
       lay = k2_layout(h.k_pad, h.n_pad, passes, 1, R, tf32);
     }
-    if (lay.total > 227 * 1024) return set_error(WN_EINVAL, "shapelet operand does not fit in shared memory");
+    if (lay.total > 227 * 1024)
+      return set_error(WN_EINVAL, "shapelet operand of orders up to " + std::to_string(h.nmax) + " (k_pad " +
+                                      std::to_string(h.k_pad) + ", n_pad " + std::to_string(h.n_pad) +
+                                      ") does not fit in shared memory in this shapelet mode");
     const int n_tiles = (int)((n_vis + K2_M * R - 1) / (K2_M * R));
     a.n_tiles = n_tiles;
     const int grid = std::min(n_tiles, ctx->num_sms);

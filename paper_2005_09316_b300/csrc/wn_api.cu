@@ -226,7 +226,7 @@ int wn_set_precision(wn_ctx* ctx, int precision, int shape_mode) {
   if (precision != WN_PREC_MIXED && precision != WN_PREC_FP64 && precision != WN_PREC_FP64_UNTUNED)
     return set_error(WN_EINVAL, "unknown precision");
   if (shape_mode != WN_SHAPE_BF16X3 && shape_mode != WN_SHAPE_BF16X1 && shape_mode != WN_SHAPE_LUT_BF16X3 &&
-      shape_mode != WN_SHAPE_TF32)
+      shape_mode != WN_SHAPE_TF32 && shape_mode != WN_SHAPE_TF32X3)
     return set_error(WN_EINVAL, "unknown shape mode");
   ctx->precision = precision;
   ctx->shape_mode = shape_mode;
@@ -355,7 +355,7 @@ int wn_sky_upload(wn_ctx* ctx, const wn_sky* s, int* model_id, void* stream) {
   cudaError_t e = dalloc(&M->pg, (size_t)s->n_point + s->n_gauss, total);
   if (e == cudaSuccess) e = dalloc(&M->sh, (size_t)s->n_shape, total);
   if (e == cudaSuccess) e = dalloc(&M->bop, M->bop_elems, total);
-  if (e == cudaSuccess) e = dalloc(&M->bop32, M->bop_elems / 2, total);
+  if (e == cudaSuccess) e = dalloc(&M->bop32, M->bop_elems, total);  // tf32 hi and lo per shapelet
   if (e == cudaSuccess) e = dalloc(&M->raw, std::max<size_t>(n_raw, 1), total);
   if (e == cudaSuccess) e = dalloc(&M->s_meta, 2 * (size_t)s->n_shape + 1 + 2 * (size_t)M->nnz, total);
   if (e == cudaSuccess) e = dalloc(&M->s_coeff, (size_t)M->nnz, total);
@@ -470,10 +470,11 @@ int wn_sky_shapelet_operand_tf32(wn_ctx* ctx, int model_id, int q, void* host_ou
   *k_pad = h.k_pad;
   *n_pad = h.n_pad;
   if (!host_out) return ok();
-  const size_t need = (size_t)4 * h.k_pad * h.n_pad;
-  if (bytes < need) return set_error(WN_EINVAL, "wn_sky_shapelet_operand_tf32: buffer shorter than 4 k_pad n_pad bytes");
+  const size_t one = (size_t)4 * h.k_pad * h.n_pad;
+  if (bytes < one) return set_error(WN_EINVAL, "wn_sky_shapelet_operand_tf32: buffer shorter than 4 k_pad n_pad bytes");
+  const size_t need = bytes >= 2 * one ? 2 * one : one;  // hi, and lo when the buffer holds both
   DeviceGuard g(ctx->device);
-  cudaError_t e = cudaMemcpy(host_out, M->bop32 + h.b_off / 2, need, cudaMemcpyDeviceToHost);
+  cudaError_t e = cudaMemcpy(host_out, M->bop32 + h.b_off, need, cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "wn_sky_shapelet_operand_tf32 copy");
   return ok();
 }

@@ -74,7 +74,7 @@ struct Model {
   ShapeRec* sh = nullptr;          // [n_shape]
   std::vector<ShapeRec> sh_host;   // host copy of the headers (sizes, offsets)
   __nv_bfloat16* bop = nullptr;    // dense shapelet B operands (hi then lo per shapelet), UMMA layout
-  float* bop32 = nullptr;          // the same operands as tf32 (K-major, 4-byte elements): shapelet q at b_off / 2
+  float* bop32 = nullptr;          // the same operands as tf32 hi then lo (K-major, 4-byte elements), shapelet q at b_off
   size_t bop_elems = 0;
   // raw FP64 copies for the FP64 form and the adjoint
   double* raw = nullptr;           // l, m, flux, alpha, nu_ref [n_comp] each; g_maj,g_min,g_pa; s_b1,s_b2,s_pa

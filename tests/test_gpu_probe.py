@@ -1,7 +1,7 @@
-"""Pipe-rate microbenchmarks (wn_pipe_rates, wn_phasor_loop_rate, wn_mma_rate): positive, finite, and in
-the relations the roofline discussion relies on (packed f32x2 FMA does the same lane work per second as
-scalar FMA; MUFU ex2 and FP64 FMA are much slower pipes on this part; a tcgen05 MMA is not faster than
-the nominal tensor rate allows)."""
+"""Pipe-rate microbenchmarks (wn_pipe_rates, wn_phasor_loop_rate, wn_mma_rate, wn_mma_rate_tf32): positive,
+finite, and in the relations the roofline discussion relies on (packed f32x2 FMA does the same lane work
+per second as scalar FMA; MUFU ex2 and FP64 FMA are much slower pipes on this part; a tcgen05 MMA is not
+faster than the nominal tensor rate allows)."""
 import math
 
 import pytest
@@ -102,6 +102,19 @@ def test_mma_rate_probe():
     assert 62.0 <= r["clk_per_mma_n128"] <= 400.0, r
     assert 0.0 < r["clk_per_mma_n64"] <= r["clk_per_mma_n128"] + 1.0, r
     assert 0.0 < r["clk_tmem_ld16"] < 200.0 and 0.0 < r["clk_tmem_ld16_x8"] < 8 * 200.0, r
+
+
+def test_mma_rate_probe_tf32():
+    """The tf32 form of the same instruction (M = 128, N = 128, K = 8: the same operand bytes as the bf16
+    one, half its flops): the nominal dense tf32 rate is half the bf16 rate per clock, so an instruction
+    cannot take fewer clocks than the bf16 one's nominal 64; N = 64 is no slower than N = 128."""
+    import paper_2005_09316_b300 as wn
+    ctx = wn.Context(0)
+    r = ctx.mma_rate_tf32()
+    assert ctx.device_errors() == 0
+    ctx.close()
+    assert 62.0 <= r["clk_per_mma_n128"] <= 400.0, r
+    assert 0.0 < r["clk_per_mma_n64"] <= r["clk_per_mma_n128"] + 1.0, r
 
 
 def test_tracing_leaves_results_unchanged():

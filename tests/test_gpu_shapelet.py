@@ -260,3 +260,82 @@ def test_fp64_forms_match_oracle(wn, ctx, prec):
     rref = oracle_peel_rows(obs, rows, gains, data, ref)
     assert np.abs(r - rref).max() <= 1e-6 * np.abs(ref).max() * np.abs(gains).max() ** 2 + 1e-6 * np.abs(data).max()
     assert ctx.device_errors() == 0
+
+
+@pytest.mark.parametrize("seed,nmaxs,keep", [(61, [10], None), (62, [80, 80], 1500), (63, [3, 40], None)])
+def test_tf32_split_operand_bit_exact_with_the_oracle_packer(wn, ctx, seed, nmaxs, keep):
+    """Both halves of the split tf32 coefficient operand (WN_SHAPE_TF32X3) equal the oracle's packer bit
+    for bit: hi = RN_tf32(float(value)), lo = RN_tf32(float(value) - hi), zero padding, K-major 8 x 4 core
+    matrices."""
+    sky = shapelet_sky(seed, nmaxs, keep=keep)
+    m = ctx.upload(sky)
+    for q in range(sky.n_shape):
+        hi, lo, kp, npd = m.shapelet_operand_tf32(q, with_lo=True)
+        o0, o1 = sky.s_off[q], sky.s_off[q + 1]
+        n1, n2, c = sky.s_n1[o0:o1], sky.s_n2[o0:o1], sky.s_coeff[o0:o1]
+        ne = int((n1 + n2).max())
+        rh, rl = oracle.pack_coeff_tf32x3(ne, n1, n2, c, kp, npd)
+        n = np.arange(npd)[:, None]
+        k = np.arange(kp)[None, :]
+        at = ((k >> 2) * (npd >> 3) + (n >> 3)) * 32 + (n & 7) * 4 + (k & 3)
+        assert np.array_equal(hi[at], rh), f"hi, shapelet {q}"
+        assert np.array_equal(lo[at], rl), f"lo, shapelet {q}"
+    m.free()
+
+
+@pytest.mark.parametrize("nmaxs,keep", [([30], None), ([80, 80], 1500), ([10, 41, 3], None), ([63], None)])
+def test_tf32_split_mode(wn, ctx, nmaxs, keep):
+    """tf32 hi+lo operands, three products (WN_SHAPE_TF32X3): each product carries about 2^-21 of relative
+    rounding, so the contraction is far inside the tensor path's 1e-3 target; held to the bf16 hi+lo
+    mode's 2e-4 and required to be no worse than the one-product tf32 mode."""
+    obs = synth.make_obs(35, 14, 2, synth.uniform_channels(167e6, 80e3, 48), layout="mwa", max_baseline=5000.0,
+                         dec0=-37.2 * synth.DEG)
+    sky = shapelet_sky(36, nmaxs, keep=keep)
+    ref = oracle_rows(obs, sky, np.arange(obs.n_rows))
+    got = predict(wn, ctx, obs, sky, 0, wn.WN_SHAPE_TF32X3)
+    e3 = e_norm(got, ref)
+    assert e3 <= 2e-4, e3
+    assert e3 <= e_norm(predict(wn, ctx, obs, sky, 0, wn.WN_SHAPE_TF32), ref)
+
+
+def test_tf32_split_mode_refuses_an_operand_that_does_not_fit(wn, ctx):
+    """Orders beyond 63 make the split tf32 operands too large for shared memory: the call returns
+    WN_EINVAL with a message and launches nothing; the default mode still predicts the same sky."""
+    obs = synth.make_obs(37, 8, 1, synth.uniform_channels(167e6, 80e3, 16), layout="mwa")
+    sky = shapelet_sky(38, [80])
+    d = wn.obs_to_device(obs)
+    m = ctx.upload(sky)
+    ctx.set_precision(0, wn.WN_SHAPE_TF32X3)
+    with pytest.raises(wn.WnError) as e:
+        ctx.predict(d, m)
+    assert e.value.code == wn.WN_EINVAL and "shared memory" in str(e.value)
+    ctx.set_precision(0, 0)
+    ref = oracle_rows(obs, sky, np.arange(obs.n_rows))
+    assert e_norm(ctx.predict(d, m).cpu().numpy().reshape(obs.n_rows, obs.n_chan), ref) <= 2e-4
+    m.free()
+    assert ctx.device_errors() == 0
+
+
+def test_fornax_full_size_tf32_split_mode(wn, ctx):
+    """The Fornax peel (two shapelets reaching orders 61 and 60 of n_max 80, 43.7 M visibilities) in the
+    split tf32 mode, on sampled rows against the oracle."""
+    obs, sky = synth.fornax()
+    d = wn.obs_to_device(obs)
+    m = ctx.upload(sky)
+    gains = synth.make_gains(7, obs.n_ant)
+    gd = torch.as_tensor(gains.astype(np.complex64)).cuda()
+    data = torch.randn(obs.n_time, obs.n_base, obs.n_chan, dtype=torch.complex64, device="cuda",
+                       generator=torch.Generator(device="cuda").manual_seed(3))
+    ctx.set_precision(0, wn.WN_SHAPE_TF32X3)
+    r = ctx.peel(d, m, gd, data)
+    torch.cuda.synchronize()
+    ctx.set_precision(0, 0)
+    rows = sample_rows(obs, 24, seed=6)
+    V = oracle_rows(obs, sky, rows)
+    idx = torch.as_tensor(rows).cuda()
+    dat = data.reshape(obs.n_rows, obs.n_chan)[idx].cpu().numpy()
+    ref = oracle_peel_rows(obs, rows, gains.astype(np.complex64), dat, V)
+    got = r.reshape(obs.n_rows, obs.n_chan)[idx].cpu().numpy()
+    assert np.max(np.abs(got - ref)) <= 2e-4 * np.max(np.abs(V))
+    assert ctx.device_errors() == 0
+    m.free()

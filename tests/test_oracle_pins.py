@@ -420,3 +420,26 @@ def test_tf32_rounding_is_nearest_with_ties_away_from_zero():
     d_lo, d_hi = np.abs(x64 - lo), np.abs(hi - x64)
     want = np.where(d_hi <= d_lo, hi, lo)   # nearest; at a tie (equal distance) the one away from zero
     assert np.array_equal(got.view(np.float32).astype(np.float64), want)
+
+
+def test_tf32_split_operand_pair():
+    """oracle.pack_coeff_tf32x3, from what the split must satisfy rather than its formula: hi is the one-
+    product tf32 operand itself; both halves are tf32 values (13 low bits clear); and hi + lo reproduces the
+    float32 coefficient to within the rounding of a 13-bit remainder to 11 bits (2^-21 of the value),
+    i.e. about 21 significant bits, where hi alone keeps 11."""
+    sky = synth.make_sky(21, 0, 0, 1, shape_nmax=30)
+    n1, n2, c = sky.s_n1, sky.s_n2, sky.s_coeff * 1e3
+    ne = int((n1 + n2).max())
+    kp, npd = (ne + 1 + 15) // 16 * 16, (2 * (ne + 1) + 15) // 16 * 16
+    hi, lo = oracle.pack_coeff_tf32x3(ne, n1, n2, c, kp, npd)
+    assert np.array_equal(hi, oracle.pack_coeff_tf32(ne, n1, n2, c, kp, npd))
+    assert np.all(hi & np.uint32(0x1FFF) == 0) and np.all(lo & np.uint32(0x1FFF) == 0)
+    re, im = oracle.parity_split(ne, n1, n2, c)
+    dense = np.zeros((npd, kp))
+    for b in range(ne + 1):
+        dense[2 * b, :ne + 1], dense[2 * b + 1, :ne + 1] = re[:, b], im[:, b]
+    f = dense.astype(np.float32).astype(np.float64)
+    both = hi.view(np.float32).astype(np.float64) + lo.view(np.float32).astype(np.float64)
+    assert np.all(np.abs(both - f) <= 2.0 ** -21 * np.abs(f))
+    only_hi = np.abs(hi.view(np.float32).astype(np.float64) - f)
+    assert np.max(only_hi / np.maximum(np.abs(f), 1e-300)) > 2.0 ** -14    # hi alone is much coarser
