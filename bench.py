@@ -351,7 +351,7 @@ def summary_block(line: dict) -> dict:
                       "tf32_ms": g("shapelet", "tf32", "ms_per_step"), "tf32x3_ms": g("shapelet", "tf32x3", "ms_per_step"),
                       "tf32x3_e_norm": g("shapelet", "tf32x3", "e_norm")},
         "k3_peel": {"gbs": g("standalone_peel", "achieved_gbs"), "frac": g("standalone_peel", "frac")},
-        "k4_adjoint_ms": g("adjoint", "ms_per_step"),
+        "k4_adjoint_ms": g("adjoint", "ms_per_step"), "fit_step_ms": g("adjoint", "autograd_fit_step_ms"),
         "k5_fp64": {"evals_per_s": g("fp64_gpu", "value"), "speedup": g("fp64_gpu", "speedup_mixed_over_fp64"),
                     "untuned_speedup": g("fp64_gpu_untuned", "speedup_mixed_over_untuned")},
         "k7_calib_ms": g("calibration", "ms"), "k8_fit_ms_per_iter": g("fit", "ms_per_iteration"),
@@ -524,8 +524,29 @@ def bench_adjoint(wn, ctx, local, torch):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / n
     m.free()
+    # one gradient step of a fit through the autograd loss (forward + backward + optimiser update), with the
+    # model re-packed in place (wn_sky_update) and with a model uploaded and freed per call; wall clock
+    from paper_2005_09316_b300.autograd import peel_loss
+    skyd = wn.sky_to_device(sky, f"cuda:{local}")
+    params = {k: skyd[k].clone().requires_grad_(True) for k in ("flux", "s_coeff")}
+    skyd.update(params)
+    opt = torch.optim.SGD(params.values(), lr=0.0)
+    resident = ctx.upload(sky)
+    step_ms = {}
+    for name, mdl in (("resident_model", resident), ("upload_per_call", None)):
+        for i in range(13):
+            if i == 3:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+            opt.zero_grad()
+            peel_loss(ctx, d, skyd, gains, data, model=mdl).backward()
+            opt.step()
+        torch.cuda.synchronize()
+        step_ms[name] = round(1e3 * (time.perf_counter() - t0) / 10, 3)
+    resident.free()
     return {"workload": "adjoint: 64 tiles (2016 baselines) x 4 x 64 ch, 500 P + 1 S (n_max 40)",
-            "ms_per_step": round(ms, 4), "grad_evals_per_s": obs.n_vis * sky.n_comp / (ms * 1e-3)}
+            "ms_per_step": round(ms, 4), "grad_evals_per_s": obs.n_vis * sky.n_comp / (ms * 1e-3),
+            "autograd_fit_step_ms": step_ms}
 
 
 def bench_serving(wn, ctx, local, torch, n_req=1000, n_templates=48, seed=17, policy=None):

@@ -182,6 +182,18 @@ WN_API int wn_device_errors(wn_ctx* ctx, uint32_t* flags_out);
  * Errors: WN_EINVAL for negative counts, NULL arrays that are needed, l^2+m^2 >= 1, nu_ref <= 0,
  * n_max outside [0,127], a triple outside the triangle n1+n2 <= n_max, non-monotone s_off. */
 WN_API int wn_sky_upload(wn_ctx* ctx, const wn_sky* sky, int* model_id, void* stream);
+/* Re-pack a resident model from new parameter values, in place and without allocating (no paper
+ * counterpart; for fitting loops that change a model every step).  sky must have the model's component
+ * counts; its l, m, flux, alpha, nu_ref, Gaussian axes and position angles, shapelet beta1, beta2,
+ * position angles and coefficients (in the model's triple order) are read; its shapelet structure
+ * (s_nmax, s_off, s_n1, s_n2) is not: the model keeps the one it was uploaded with.  The packing runs in
+ * kernels on `stream`, so later calls on that stream see the new values.  Asynchronous for models of
+ * points and Gaussians; with shapelets it ends by reading the packed shapelet headers back to the host
+ * (the launches are planned from them), which synchronises `stream`.  Values that wn_sky_upload would
+ * reject (l^2 + m^2 >= 1, nu_ref <= 0, a negative width, a non-finite value) are not detected on the
+ * host: they raise WN_DEVERR_SKY (wn_device_errors) and the component contributes nothing.
+ * WN_ENOTFOUND for an unknown model, WN_EINVAL for different counts or a NULL array that is needed. */
+WN_API int wn_sky_update(wn_ctx* ctx, int model_id, const wn_sky* sky, void* stream);
 /* Release a resident model.  Synchronous. */
 WN_API int wn_sky_free(wn_ctx* ctx, int model_id);
 /* Bytes of device memory a resident model holds (admission accounting). */

@@ -30,7 +30,7 @@ EXPORTED = ("wn_create", "wn_destroy", "wn_last_error", "wn_version", "wn_set_pr
             "wn_server_poll", "wn_server_wait", "wn_server_copy", "wn_server_release", "wn_server_cancel",
             "wn_server_stats", "wn_server_set_policy", "wn_calibrate", "wn_fit_shapelets", "wn_pipe_rates",
             "wn_phasor_loop_rate", "wn_sky_shapelet_operand", "wn_selftest_timeout", "wn_mma_rate", "wn_mma_rate_tf32", "wn_set_trace", "wn_debug_fail_allocs",
-            "wn_sky_shapelet_operand_tf32")
+            "wn_sky_shapelet_operand_tf32", "wn_sky_update")
 
 
 class WnError(RuntimeError):
@@ -83,6 +83,7 @@ def load(build_if_missing: bool = True):
         L.wn_device_errors.argtypes = [P, ctypes.POINTER(ctypes.c_uint32)]
         L.wn_sky_upload.argtypes = [P, ctypes.POINTER(WnSky), ctypes.POINTER(i), P]
         L.wn_sky_free.argtypes = [P, i]
+        L.wn_sky_update.argtypes = [P, i, ctypes.POINTER(WnSky), P]
         L.wn_sky_bytes.argtypes = [P, i, ctypes.POINTER(ctypes.c_size_t)]
         L.wn_sky_shapelet_operand.argtypes = [P, i, i, P, ctypes.c_size_t, ctypes.POINTER(i), ctypes.POINTER(i)]
         L.wn_predict.argtypes = [P, ctypes.POINTER(WnObs), i, P, i, P]
@@ -227,6 +228,15 @@ class Model:
     @property
     def n_comp(self) -> int:
         return self.n_point + self.n_gauss + self.n_shape
+
+    def update(self, sky, stream=None):
+        """Re-pack this resident model in place from new parameter values (a device sky dict or a host sky
+        table with this model's counts and shapelet structure); nothing is allocated on the device."""
+        d = sky if isinstance(sky, dict) else sky_to_device(sky, f"cuda:{self.ctx.device}")
+        if (d["n_point"], d["n_gauss"], d["n_shape"]) != (self.n_point, self.n_gauss, self.n_shape):
+            raise ValueError("component counts differ from the resident model's")
+        s = _sky_struct(d)
+        _check(load().wn_sky_update(self.ctx.h, self.id, ctypes.byref(s), _stream_handle(stream)))
 
     def nbytes(self) -> int:
         v = ctypes.c_size_t()

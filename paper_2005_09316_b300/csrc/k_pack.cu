@@ -2,6 +2,8 @@
 // prediction kernels read.  Runs once per model (wn_sky_upload).
 #include "wn_internal.cuh"
 
+#include <vector>
+
 namespace wn {
 
 // Point / Gaussian records (one thread per component).  n - 1 is formed without cancellation as
@@ -120,33 +122,41 @@ static int cuda_check(cudaError_t e, const char* what) {
   return set_error(WN_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// Pack a new model: its records, shapelet headers and dense coefficient operands.  M->dmeta (device) and
+// M->sh_host (sizes) are set up by the caller; the per-shapelet offsets and sizes are copied into dmeta.
 int launch_pack(wn_ctx* ctx, const wn_sky* s, Model* M, cudaStream_t st) {
-  int npg = s->n_point + s->n_gauss;
+  if (s->n_shape > 0) {
+    std::vector<int> meta(3 * (size_t)s->n_shape);
+    for (int q = 0; q < s->n_shape; ++q) {
+      meta[q] = M->sh_host[q].b_off;
+      meta[s->n_shape + q] = M->sh_host[q].k_pad;
+      meta[2 * s->n_shape + q] = M->sh_host[q].n_pad;
+    }
+    if (int r = cuda_check(cudaMemcpyAsync(M->dmeta, meta.data(), sizeof(int) * meta.size(), cudaMemcpyHostToDevice, st),
+                           "pack metadata"))
+      return r;
+  }
+  return launch_repack(ctx, s, M, st);
+}
+
+// Re-pack from the parameter values in s (device arrays; the shapelet structure, s_nmax and the triples,
+// is read from the model): records, shapelet headers and dense operands.  Kernels and device-to-device
+// copies only, asynchronous on st, no allocation.
+int launch_repack(wn_ctx* ctx, const wn_sky* s, Model* M, cudaStream_t st) {
+  const int npg = s->n_point + s->n_gauss;
   if (npg > 0) {
     k_pack_pg<<<(npg + 127) / 128, 128, 0, st>>>(*s, M->pg, ctx->d_err);
     if (int r = cuda_check(cudaGetLastError(), "pack points")) return r;
   }
   if (s->n_shape > 0) {
-    std::vector<int> boff(s->n_shape), kp(s->n_shape), np(s->n_shape);
-    for (int q = 0; q < s->n_shape; ++q) {
-      boff[q] = M->sh_host[q].b_off;
-      kp[q] = M->sh_host[q].k_pad;
-      np[q] = M->sh_host[q].n_pad;
-    }
-    int* dtmp = nullptr;
-    if (int r = cuda_check(cudaMallocAsync(&dtmp, sizeof(int) * 3 * s->n_shape, st), "pack alloc")) return r;
-    cudaMemcpyAsync(dtmp, boff.data(), sizeof(int) * s->n_shape, cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(dtmp + s->n_shape, kp.data(), sizeof(int) * s->n_shape, cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(dtmp + 2 * s->n_shape, np.data(), sizeof(int) * s->n_shape, cudaMemcpyHostToDevice, st);
-    k_pack_shape<<<(s->n_shape + 63) / 64, 64, 0, st>>>(*s, dtmp, dtmp + s->n_shape, dtmp + 2 * s->n_shape,
-                                                        M->sh, ctx->d_err);
+    const int* dm = M->dmeta;
+    k_pack_shape<<<(s->n_shape + 63) / 64, 64, 0, st>>>(*s, dm, dm + s->n_shape, dm + 2 * s->n_shape, M->sh, ctx->d_err);
     cudaMemsetAsync(M->bop, 0, M->bop_elems * sizeof(__nv_bfloat16), st);
     cudaMemsetAsync(M->bop32, 0, M->bop_elems * sizeof(float), st);
     if (M->nnz > 0)
       k_pack_coeff<<<(M->nnz + 255) / 256, 256, 0, st>>>(M->nnz, s->s_n1, s->s_n2, s->s_coeff, s->s_off, s->s_nmax,
-                                                         s->n_shape, dtmp, dtmp + s->n_shape, dtmp + 2 * s->n_shape,
-                                                         M->bop, M->bop32, ctx->d_err);
-    cudaFreeAsync(dtmp, st);
+                                                         s->n_shape, dm, dm + s->n_shape, dm + 2 * s->n_shape, M->bop,
+                                                         M->bop32, ctx->d_err);
     if (int r = cuda_check(cudaGetLastError(), "pack shapelets")) return r;
   }
   return WN_OK;

@@ -119,6 +119,7 @@ static void free_model(Model* M) {
   cudaFree(M->raw);
   cudaFree(M->s_meta);
   cudaFree(M->s_coeff);
+  cudaFree(M->dmeta);
   delete M;
 }
 
@@ -359,6 +360,7 @@ int wn_sky_upload(wn_ctx* ctx, const wn_sky* s, int* model_id, void* stream) {
   if (e == cudaSuccess) e = dalloc(&M->raw, std::max<size_t>(n_raw, 1), total);
   if (e == cudaSuccess) e = dalloc(&M->s_meta, 2 * (size_t)s->n_shape + 1 + 2 * (size_t)M->nnz, total);
   if (e == cudaSuccess) e = dalloc(&M->s_coeff, (size_t)M->nnz, total);
+  if (e == cudaSuccess) e = dalloc(&M->dmeta, 3 * (size_t)s->n_shape, total);
   if (e != cudaSuccess) {
     free_model(M);
     return set_error(WN_ENOMEM, std::string("model allocation: ") + cudaGetErrorString(e));
@@ -422,6 +424,56 @@ int wn_sky_upload(wn_ctx* ctx, const wn_sky* s, int* model_id, void* stream) {
   const int id = ctx->next_id++;
   ctx->models[id] = M;
   *model_id = id;
+  return ok();
+}
+
+int wn_sky_update(wn_ctx* ctx, int model_id, const wn_sky* s, void* stream) {
+  TraceRange trace_range(ctx, "wn_sky_update");
+  if (!ctx || !s) return set_error(WN_EINVAL, "NULL argument");
+  Model* M = find_model(ctx, model_id);
+  if (!M) return set_error(WN_ENOTFOUND, "unknown model id");
+  if (s->n_point != M->n_point || s->n_gauss != M->n_gauss || s->n_shape != M->n_shape)
+    return set_error(WN_EINVAL, "wn_sky_update: component counts differ from the resident model's");
+  const long long n_comp = (long long)M->n_comp();
+  if (n_comp > 0 && (!s->l || !s->m || !s->flux || !s->alpha || !s->nu_ref))
+    return set_error(WN_EINVAL, "sky has a NULL per-component array");
+  if (M->n_gauss > 0 && (!s->g_maj || !s->g_min || !s->g_pa)) return set_error(WN_EINVAL, "sky has a NULL Gaussian array");
+  if (M->n_shape > 0 && (!s->s_beta1 || !s->s_beta2 || !s->s_pa)) return set_error(WN_EINVAL, "sky has a NULL shapelet array");
+  if (M->nnz > 0 && !s->s_coeff) return set_error(WN_EINVAL, "sky has NULL shapelet coefficients");
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  auto cp = [&](double* dst, const double* src, size_t n) {
+    if (n) cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  };
+  // the raw FP64 tables (the FP64 form and the adjoint read these) and the coefficients
+  cp(M->raw, s->l, n_comp);
+  cp(M->raw + n_comp, s->m, n_comp);
+  cp(M->raw + 2 * n_comp, s->flux, n_comp);
+  cp(M->raw + 3 * n_comp, s->alpha, n_comp);
+  cp(M->raw + 4 * n_comp, s->nu_ref, n_comp);
+  cp(M->raw + 5 * n_comp, s->g_maj, M->n_gauss);
+  cp(M->raw + 5 * n_comp + M->n_gauss, s->g_min, M->n_gauss);
+  cp(M->raw + 5 * n_comp + 2 * M->n_gauss, s->g_pa, M->n_gauss);
+  cp(M->raw + 5 * n_comp + 3 * M->n_gauss, s->s_beta1, M->n_shape);
+  cp(M->raw + 5 * n_comp + 3 * M->n_gauss + M->n_shape, s->s_beta2, M->n_shape);
+  cp(M->raw + 5 * n_comp + 3 * M->n_gauss + 2 * M->n_shape, s->s_pa, M->n_shape);
+  cp(M->s_coeff, s->s_coeff, M->nnz);
+  // re-pack with the model's own shapelet structure (effective orders, offsets, triples)
+  wn_sky sp = *s;
+  if (M->n_shape > 0) {
+    sp.s_nmax = M->m_nmax();
+    sp.s_off = M->m_off();
+    sp.s_n1 = M->m_n1();
+    sp.s_n2 = M->m_n2();
+    sp.s_coeff = M->s_coeff;
+  }
+  if (int r = launch_repack(ctx, &sp, M, st)) return r;
+  if (M->n_shape > 0) {
+    // the launch planning reads each shapelet's amplitude terms from the host copy of its header
+    cudaError_t e = cudaMemcpyAsync(M->sh_host.data(), M->sh, sizeof(ShapeRec) * M->n_shape, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "read shapelet headers");
+  }
   return ok();
 }
 

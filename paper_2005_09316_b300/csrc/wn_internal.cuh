@@ -80,6 +80,7 @@ struct Model {
   double* raw = nullptr;           // l, m, flux, alpha, nu_ref [n_comp] each; g_maj,g_min,g_pa; s_b1,s_b2,s_pa
   int* s_meta = nullptr;           // s_nmax [n_shape], s_off [n_shape+1], s_n1 [nnz], s_n2 [nnz]
   double* s_coeff = nullptr;       // [nnz]
+  int* dmeta = nullptr;            // [3][n_shape]: each shapelet's b_off, k_pad, n_pad (the packers read these)
   std::vector<int> s_off_host, s_nmax_host;
   size_t bytes = 0;
   int n_comp() const { return n_point + n_gauss + n_shape; }
@@ -381,6 +382,7 @@ struct ObsDev {
   bool uniform;
 };
 int launch_pack(wn_ctx* ctx, const wn_sky* sky, Model* M, cudaStream_t st);
+int launch_repack(wn_ctx* ctx, const wn_sky* sky, Model* M, cudaStream_t st);
 int launch_phasor_mixed(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, int mode, const PeelArgs& pa,
                         cudaStream_t st);
 int launch_phasor_table(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, int mode, const PeelArgs& pa,
