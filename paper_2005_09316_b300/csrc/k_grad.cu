@@ -849,10 +849,11 @@ static int cuda_err(const char* what) {
 
 int run_model_peel(wn_ctx* ctx, const ObsDev& d, const Model* M, float2* out, const PeelArgs& pa, cudaStream_t st);
 
-static int g_grad_consts[64] = {0};
-
-static int grad_constants(int device, cudaStream_t st) {
-  if (device >= 0 && device < 64 && g_grad_consts[device]) return WN_OK;
+// The Hermite derivative and recurrence constants of the shapelet adjoint, uploaded synchronously at
+// context creation (wn_create, the context's device current), so that every later launch, on any
+// stream, reads them complete; a context created after a device reset uploads them again.
+int grad_constants_setup(wn_ctx* ctx) {
+  (void)ctx;
   float lo[kNmaxLimit + 2], hi[kNmaxLimit + 2], ra[kNmaxLimit + 2], rb[kNmaxLimit + 2];
   for (int n = 0; n <= kNmaxLimit + 1; ++n) {
     lo[n] = (float)std::sqrt(0.5 * n);
@@ -860,18 +861,16 @@ static int grad_constants(int device, cudaStream_t st) {
     ra[n] = (float)std::sqrt(2.0 / (n + 1));
     rb[n] = (float)std::sqrt((double)n / (n + 1));
   }
-  cudaError_t e = cudaMemcpyToSymbolAsync(c_dn_lo, lo, sizeof(lo), 0, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_dn_hi, hi, sizeof(hi), 0, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_ra, ra, sizeof(ra), 0, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_rb, rb, sizeof(rb), 0, cudaMemcpyHostToDevice, st);
+  cudaError_t e = cudaMemcpyToSymbol(c_dn_lo, lo, sizeof(lo));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_dn_hi, hi, sizeof(hi));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_ra, ra, sizeof(ra));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_rb, rb, sizeof(rb));
   if (e != cudaSuccess) return set_error(WN_ECUDA, std::string("adjoint constants: ") + cudaGetErrorString(e));
-  if (device >= 0 && device < 64) g_grad_consts[device] = 1;
   return WN_OK;
 }
 
 int launch_grad(wn_ctx* ctx, const ObsDev& o, const Model* M, const PeelArgs& pa, float2* resid,
                 const wn_sky_grad* g, double* loss, cudaStream_t st) {
-  if (int r = grad_constants(ctx->device, st)) return r;
   // 1. forward: resid = data - G V
   if (int r = run_model_peel(ctx, o, M, resid, pa, st)) return r;
   // workspace: loss partials, point/Gaussian partials, shapelet tables and partials
@@ -1027,7 +1026,6 @@ int launch_grad(wn_ctx* ctx, const ObsDev& o, const Model* M, const PeelArgs& pa
 // -gcoeff / 2 is the adjoint of the linear map C -> G V_shapelets(C) applied to R.
 int launch_grad_shape_coeff(wn_ctx* ctx, const ObsDev& o, const Model* M, const PeelArgs& pa, const float2* resid,
                             double* gcoeff, cudaStream_t st) {
-  if (int r = grad_constants(ctx->device, st)) return r;
   int max_nnz = 0;
   for (int q = 0; q < M->n_shape; ++q) max_nnz = std::max(max_nnz, M->s_off_host[q + 1] - M->s_off_host[q]);
   const int sgrid = ctx->num_sms * 4;

@@ -197,7 +197,9 @@ int wn_create(wn_ctx** out, int device) {
     delete c;
     return cuda_fail(e, "cudaMalloc(phasor tail partial sums)");
   }
-  if (int r = static_scratch_setup(c)) {  // device address of wn_predict_static's array, this device current
+  int r = static_scratch_setup(c);  // device address of wn_predict_static's array, this device current
+  if (r == WN_OK) r = grad_constants_setup(c);  // the shapelet adjoint's constants
+  if (r != WN_OK) {
     cudaFree(c->k1_part);
     cudaFree(c->d_err);
     delete c;
