@@ -438,6 +438,7 @@ struct K4SArgs {
   double* part_c;   // [grid][nnz]
   unsigned* err;
   int coef_only = 0;  // only the coefficient gradients (the fit's A^T r): no factorised sums, part_s zero
+  int skip_coef = 0;  // no coefficient gradients (the tensor-core kernel k4_coeff_mma forms them)
 };
 
 __device__ void hermite_scaled_row(float x, int nmax1, float* out) {
@@ -494,7 +495,7 @@ struct K4SSmem {
   int ld, phx, phy, fg, toff, w, accd, blocks, total;
 };
 __host__ __device__ inline bool k4s_reg_acc(int nmax, int T) { return k4s_nblocks(nmax) <= T; }
-__host__ __device__ inline K4SSmem k4s_layout(int nmax, int nnz, int T) {
+__host__ __device__ inline K4SSmem k4s_layout(int nmax, int nnz, int T, bool skip_coef = false) {
   (void)nnz;
   K4SSmem s;
   // entries 0 .. n + 3 (the blocks read up to n2 = 4J + 3); at least 20, so that one thread's row of the
@@ -508,8 +509,8 @@ __host__ __device__ inline K4SSmem k4s_layout(int nmax, int nnz, int T) {
   s.toff = s.fg + nfg * 8;
   s.w = (s.toff + (k4s_rows(nmax) + 1) * 4 + 7) & ~7;
   s.accd = s.w + T * 8;
-  s.blocks = s.accd + (k4s_reg_acc(nmax, T) ? 0 : nfg * 8);
-  s.total = s.blocks + k4s_nblocks(nmax) * 4;
+  s.blocks = s.accd + (k4s_reg_acc(nmax, T) || skip_coef ? 0 : nfg * 8);
+  s.total = s.blocks + (skip_coef ? 0 : k4s_nblocks(nmax) * 4);
   return s;
 }
 
@@ -517,7 +518,8 @@ __global__ void __launch_bounds__(K4S_T) k4_grad_shape(const K4SArgs a) {
   extern __shared__ __align__(16) unsigned char sm[];
   const int n = a.nmax;
   const int T = blockDim.x;  // 128, or 64 for the largest n_max
-  const K4SSmem lay = k4s_layout(n, a.nnz, T);
+  const bool coef = !a.skip_coef;
+  const K4SSmem lay = k4s_layout(n, a.nnz, T, !coef);
   const int ld = lay.ld;
   float* phx = reinterpret_cast<float*>(sm + lay.phx);
   float* phy = reinterpret_cast<float*>(sm + lay.phy);
@@ -539,9 +541,9 @@ __global__ void __launch_bounds__(K4S_T) k4_grad_shape(const K4SArgs a) {
   const int nfg = k4s_nfg(n);
   for (int i = t; i < nfg; i += T) {
     fg[i] = make_float2(0.f, 0.f);
-    if (!reg_acc) accd[i] = 0.0;
+    if (!reg_acc && coef) accd[i] = 0.0;
   }
-  if (t == 0) {  // (2I, 4J) blocks of the triangle, J outer
+  if (t == 0 && coef) {  // (2I, 4J) blocks of the triangle, J outer
     int c = 0;
     for (int J = 0; 4 * J <= n; ++J)
       for (int I = 0; 2 * I <= n - 4 * J; ++I) blocks[c++] = make_ushort2((unsigned short)(2 * I), (unsigned short)(4 * J));
@@ -702,7 +704,7 @@ __global__ void __launch_bounds__(K4S_T) k4_grad_shape(const K4SArgs a) {
     // parity of n1 + n2 selects Re or Im (fixed within a block, since n1 starts even and n2 at 4J), the
     // sign follows when the block is added to the FP64 sums.
     const int nv = (int)min((long long)T, a.n_vis - tile * T);
-    for (int bk = t; bk < nblk; bk += T) {
+    for (int bk = t; coef && bk < nblk; bk += T) {
       const int na0 = blocks[bk].x, nb0 = blocks[bk].y;
       float s[2][4];
 #pragma unroll
@@ -736,7 +738,7 @@ __global__ void __launch_bounds__(K4S_T) k4_grad_shape(const K4SArgs a) {
     }
     __syncthreads();
   }
-  if (reg_acc) {  // the basis rows are free now: the sums go to the folded triangle there
+  if (reg_acc && coef) {  // the basis rows are free now: the sums go to the folded triangle there
     if (t < nblk) {
       const int na0 = blocks[t].x, nb0 = blocks[t].y;
 #pragma unroll
@@ -748,7 +750,7 @@ __global__ void __launch_bounds__(K4S_T) k4_grad_shape(const K4SArgs a) {
     __syncthreads();
   }
   // per-CTA partials (the flux factor of every group but the flux one is applied here, in FP64)
-  for (int k = t; k < a.nnz; k += T)
+  for (int k = t; coef && k < a.nnz; k += T)
     a.part_c[(size_t)blockIdx.x * a.nnz + k] = accd[toff[__ldg(a.n1 + k)] + __ldg(a.n2 + k)] * flux;
   double* red = reinterpret_cast<double*>(sm + lay.phy);  // [T][K4S_NS], in the second basis-row area
   for (int i = 0; i < K4S_NS; ++i) red[t * K4S_NS + i] = (accs[i] + (double)acc32[i]) * (i == 0 ? 1.0 : flux);
@@ -762,7 +764,7 @@ __global__ void __launch_bounds__(K4S_T) k4_grad_shape(const K4SArgs a) {
 
 // One warp per output (coefficient or scalar group): lanes add strided per-CTA partials, then a fixed
 // butterfly; deterministic.
-__global__ void k4_reduce_shape(const double* part_s, const double* part_c, int grid, int nnz, int j, int q,
+__global__ void k4_reduce_shape(const double* part_s, const double* part_c, int grid, int grid_c, int nnz, int j, int q,
                                 double* gflux, double* galpha, double* gl, double* gm, double* gb1, double* gb2,
                                 double* gpa, double* gcoeff, int coeff_off, int first) {
   const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
@@ -772,7 +774,7 @@ __global__ void k4_reduce_shape(const double* part_s, const double* part_c, int 
   };
   double s = 0.0;
   if (t < nnz) {
-    for (int c = lane; c < grid; c += 32) s += part_c[(size_t)c * nnz + t];
+    for (int c = lane; c < grid_c; c += 32) s += part_c[(size_t)c * nnz + t];
   } else {
     for (int c = lane; c < grid; c += 32) s += part_s[(size_t)c * K4S_NS + (t - nnz)];
   }
@@ -1000,22 +1002,26 @@ int launch_grad(wn_ctx* ctx, const ObsDev& o, const Model* M, const PeelArgs& pa
     a.part_s = shpart;
     a.part_c = shpart + (size_t)sgrid * K4S_NS;
     a.err = ctx->d_err;
+    a.skip_coef = 1;  // the coefficient gradients come from the tensor-core kernel below
     const size_t smax = 227 * 1024;
     int T = K4S_T;
-    size_t smem = (size_t)k4s_layout(h.nmax, a.nnz, T).total;
+    size_t smem = (size_t)k4s_layout(h.nmax, a.nnz, T, true).total;
     if (smem > smax) {
       T = K4S_T / 2;
-      smem = (size_t)k4s_layout(h.nmax, a.nnz, T).total;
+      smem = (size_t)k4s_layout(h.nmax, a.nnz, T, true).total;
     }
     if (smem > smax) return set_error(WN_EINVAL, "adjoint: shapelet too large for the shared-memory reduction");
     if (cudaError_t ea = allow_max_dynamic_smem(reinterpret_cast<const void*>(k4_grad_shape)))
       return set_error(WN_ECUDA, std::string("adjoint attribute: ") + cudaGetErrorString(ea));
     k4_grad_shape<<<sgrid, T, smem, st>>>(a);
-    const int nout = a.nnz + K4S_NS;
-    k4_reduce_shape<<<(nout * 32 + 255) / 256, 256, 0, st>>>(shpart, shpart + (size_t)sgrid * K4S_NS, sgrid, a.nnz, j,
-                                                            q, g->flux, g->alpha, g->l, g->m, g->s_beta1, g->s_beta2,
-                                                            g->s_pa, g->s_coeff, M->s_off_host[q], 1);
     if (int r = cuda_err("shapelet adjoint")) return r;
+    int cgrid = 0;
+    if (int r = launch_coeff_mma(ctx, o, M, q, pa, resid, rowinfo, chaninfo, a.part_c, &cgrid, st)) return r;
+    const int nout = a.nnz + K4S_NS;
+    k4_reduce_shape<<<(nout * 32 + 255) / 256, 256, 0, st>>>(shpart, a.part_c, sgrid, cgrid, a.nnz, j, q, g->flux,
+                                                            g->alpha, g->l, g->m, g->s_beta1, g->s_beta2, g->s_pa,
+                                                            g->s_coeff, M->s_off_host[q], 1);
+    if (int r = cuda_err("shapelet adjoint reduction")) return r;
   }
   return WN_OK;
 }
@@ -1085,22 +1091,11 @@ int launch_grad_shape_coeff(wn_ctx* ctx, const ObsDev& o, const Model* M, const 
     a.part_s = shpart;
     a.part_c = shpart + (size_t)sgrid * K4S_NS;
     a.err = ctx->d_err;
-    a.coef_only = 1;
-    const size_t smax = 227 * 1024;
-    int T = K4S_T;
-    size_t smem = (size_t)k4s_layout(h.nmax, a.nnz, T).total;
-    if (smem > smax) {
-      T = K4S_T / 2;
-      smem = (size_t)k4s_layout(h.nmax, a.nnz, T).total;
-    }
-    if (smem > smax) return set_error(WN_EINVAL, "adjoint: shapelet too large for the shared-memory reduction");
-    if (cudaError_t ea = allow_max_dynamic_smem(reinterpret_cast<const void*>(k4_grad_shape)))
-      return set_error(WN_ECUDA, std::string("adjoint attribute: ") + cudaGetErrorString(ea));
-    k4_grad_shape<<<sgrid, T, smem, st>>>(a);
-    const int nout = a.nnz + K4S_NS;
-    k4_reduce_shape<<<(nout * 32 + 255) / 256, 256, 0, st>>>(shpart, shpart + (size_t)sgrid * K4S_NS, sgrid, a.nnz, j,
-                                                            q, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-                                                            nullptr, gcoeff, M->s_off_host[q], 1);
+    int cgrid = 0;
+    if (int r = launch_coeff_mma(ctx, o, M, q, pa, resid, rowinfo, chaninfo, a.part_c, &cgrid, st)) return r;
+    k4_reduce_shape<<<(a.nnz * 32 + 255) / 256, 256, 0, st>>>(shpart, a.part_c, sgrid, cgrid, a.nnz, j, q, nullptr,
+                                                             nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                             gcoeff, M->s_off_host[q], 1);
     if (int r = cuda_err("shapelet coefficient adjoint")) return r;
   }
   return WN_OK;

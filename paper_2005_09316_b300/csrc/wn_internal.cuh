@@ -398,6 +398,8 @@ int launch_shapelets_static(wn_ctx* ctx, const ObsDev& o, const Model* M, float2
 size_t static_scratch_entries();
 int static_scratch_setup(wn_ctx* ctx);
 int grad_constants_setup(wn_ctx* ctx);
+int launch_coeff_mma(wn_ctx* ctx, const ObsDev& o, const Model* M, int q, const PeelArgs& pa, const float2* resid,
+                     const float4* rowinfo, const float4* chaninfo, double* part_c, int* grid_out, cudaStream_t st);
 int launch_grad(wn_ctx* ctx, const ObsDev& o, const Model* M, const PeelArgs& pa, float2* resid,
                 const wn_sky_grad* g, double* loss, cudaStream_t st);
 int k1_batched_smem();
