@@ -408,10 +408,9 @@ __global__ void k4_reduce_pg(const double* partials, int chunks, int n_point, in
 // coefficients (phi_b' = sqrt(b/2) phi_b-1 - sqrt((b+1)/2) phi_b+1), so both sums run over the same
 // phi_b(y) and T'_a takes the opposite real/imaginary part.  Each thread keeps its phi_n(x), phi_n(y)
 // rows in shared memory (rows of an odd count of 16-byte quarters: float4 reads conflict-free) and runs
-// the sums over K4S_RA rows a at once.  The CTA then sums the coefficient gradients
-// sum_vis w phi_a(x) phi_b(y) over the tile (w = Re or Im of conj(W) S P by the parity of a+b) in 2 x 4
-// blocks, one per thread, into FP64 sums (in the thread's registers when it owns one block, else in
-// shared memory).
+// the sums over K4S_RA rows a at once.  The coefficient gradients
+// sum_vis w phi_a(x) phi_b(y) (w = Re or Im of conj(W) S P by the parity of a+b) are a contraction over
+// the visibilities and run on the tensor cores (k4_coeff_mma, k_grad_mma.cu).
 // ---------------------------------------------------------------------------------------------
 constexpr int K4S_T = 128;
 constexpr int K4S_NS = 7;  // flux, alpha, l, m, beta1, beta2, pa
@@ -435,10 +434,7 @@ struct K4SArgs {
   const float2* resid;
   PeelArgs peel;
   double* part_s;   // [grid][K4S_NS]
-  double* part_c;   // [grid][nnz]
   unsigned* err;
-  int coef_only = 0;  // only the coefficient gradients (the fit's A^T r): no factorised sums, part_s zero
-  int skip_coef = 0;  // no coefficient gradients (the tensor-core kernel k4_coeff_mma forms them)
 };
 
 __device__ void hermite_scaled_row(float x, int nmax1, float* out) {
@@ -461,14 +457,6 @@ __device__ void hermite_scaled_row(float x, int nmax1, float* out) {
   }
 }
 
-// The coefficient gradients are summed in blocks of 2 n1 x 4 n2 (n1 from 2I, n2 from 4J) covering the
-// triangle n1 + n2 <= n; the number of such blocks.
-__host__ __device__ inline int k4s_nblocks(int nmax) {
-  int c = 0;
-  for (int J = 0; 4 * J <= nmax; ++J) c += (nmax - 4 * J) / 2 + 1;
-  return c;
-}
-
 // The factorised sums run over K4S_RA rows a of the folded triangle at once, so each thread's phi(y)
 // entries are read once per group of rows instead of once per row.
 constexpr int K4S_RA = 4;
@@ -487,19 +475,15 @@ __host__ __device__ inline int k4s_nfg(int nmax) { return k4s_row_off(nmax, k4s_
 
 // Shared-memory layout of k4_grad_shape (bytes): basis rows (a multiple of 4 floats with an odd count of
 // 16-byte quarters, so per-thread rows read as float4 without bank conflicts), folded coefficient pairs
-// (f, g) per triangle row a (b = 0..n-a+1), row offsets, tile weights (Re, Im) Y, the FP64
-// coefficient-gradient sums over the same folded triangle, and the list of (n1, n2) blocks.  When every
-// thread owns at most one block (k4s_nblocks(n) <= T) the sums stay in its registers and accd is empty;
-// at the end the basis rows' area holds them and the scalar reduction.
+// (f, g) per triangle row a (b = 0..n-a+1) and the row offsets.  At the end the second basis-row area holds
+// the scalar reduction.
 struct K4SSmem {
-  int ld, phx, phy, fg, toff, w, accd, blocks, total;
+  int ld, phx, phy, fg, toff, total;
 };
-__host__ __device__ inline bool k4s_reg_acc(int nmax, int T) { return k4s_nblocks(nmax) <= T; }
-__host__ __device__ inline K4SSmem k4s_layout(int nmax, int nnz, int T, bool skip_coef = false) {
-  (void)nnz;
+__host__ __device__ inline K4SSmem k4s_layout(int nmax, int T) {
   K4SSmem s;
-  // entries 0 .. n + 3 (the blocks read up to n2 = 4J + 3); at least 20, so that one thread's row of the
-  // second area holds its K4S_NS doubles of the final reduction
+  // entries 0 .. n + 3 (the sums read up to b = n + 1, and float4 reads one past); at least 20, so that
+  // one thread's row of the second area holds its K4S_NS doubles of the final reduction
   s.ld = max((nmax + 4 + 3) & ~3, 20);
   if (((s.ld >> 2) & 1) == 0) s.ld += 4;
   const int nfg = k4s_nfg(nmax);
@@ -507,10 +491,7 @@ __host__ __device__ inline K4SSmem k4s_layout(int nmax, int nnz, int T, bool ski
   s.phy = s.phx + T * s.ld * 4;
   s.fg = (s.phy + T * s.ld * 4 + 15) & ~15;
   s.toff = s.fg + nfg * 8;
-  s.w = (s.toff + (k4s_rows(nmax) + 1) * 4 + 7) & ~7;
-  s.accd = s.w + T * 8;
-  s.blocks = s.accd + (k4s_reg_acc(nmax, T) || skip_coef ? 0 : nfg * 8);
-  s.total = s.blocks + (skip_coef ? 0 : k4s_nblocks(nmax) * 4);
+  s.total = s.toff + (k4s_rows(nmax) + 1) * 4;
   return s;
 }
 
@@ -518,20 +499,12 @@ __global__ void __launch_bounds__(K4S_T) k4_grad_shape(const K4SArgs a) {
   extern __shared__ __align__(16) unsigned char sm[];
   const int n = a.nmax;
   const int T = blockDim.x;  // 128, or 64 for the largest n_max
-  const bool coef = !a.skip_coef;
-  const K4SSmem lay = k4s_layout(n, a.nnz, T, !coef);
+  const K4SSmem lay = k4s_layout(n, T);
   const int ld = lay.ld;
   float* phx = reinterpret_cast<float*>(sm + lay.phx);
   float* phy = reinterpret_cast<float*>(sm + lay.phy);
   float2* fg = reinterpret_cast<float2*>(sm + lay.fg);
   int* toff = reinterpret_cast<int*>(sm + lay.toff);
-  float2* wy = reinterpret_cast<float2*>(sm + lay.w);
-  const bool reg_acc = k4s_reg_acc(n, T);
-  // [folded triangle] coefficient-gradient sums: in shared memory, or (reg_acc) in registers until the end
-  double* accd = reinterpret_cast<double*>(sm + (reg_acc ? lay.phx : lay.accd));
-  ushort2* blocks = reinterpret_cast<ushort2*>(sm + lay.blocks);
-  const int nblk = k4s_nblocks(n);
-  double accr[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};  // reg_acc: this thread's block
   const int t = threadIdx.x;
   const double flux = *a.flux, beta1 = *a.beta1, beta2 = *a.beta2;
 
@@ -539,15 +512,7 @@ __global__ void __launch_bounds__(K4S_T) k4_grad_shape(const K4SArgs a) {
   const int n_rows_fg = k4s_rows(n);
   for (int aa = t; aa <= n_rows_fg; aa += T) toff[aa] = k4s_row_off(n, aa);
   const int nfg = k4s_nfg(n);
-  for (int i = t; i < nfg; i += T) {
-    fg[i] = make_float2(0.f, 0.f);
-    if (!reg_acc && coef) accd[i] = 0.0;
-  }
-  if (t == 0 && coef) {  // (2I, 4J) blocks of the triangle, J outer
-    int c = 0;
-    for (int J = 0; 4 * J <= n; ++J)
-      for (int I = 0; 2 * I <= n - 4 * J; ++I) blocks[c++] = make_ushort2((unsigned short)(2 * I), (unsigned short)(4 * J));
-  }
+  for (int i = t; i < nfg; i += T) fg[i] = make_float2(0.f, 0.f);
   __syncthreads();
   for (int k = t; k < a.nnz; k += T) {
     const int na = __ldg(a.n1 + k), nb = __ldg(a.n2 + k);
@@ -598,10 +563,9 @@ __global__ void __launch_bounds__(K4S_T) k4_grad_shape(const K4SArgs a) {
     // flux derivative); contributions are -2 S_ref Re(Y * dxi)
     const float S = valid ? ex2_approx(fmaf(a.alpha, ci.z, a.c_amp)) : 0.f;
     const float yr = S * (W.x * P.x + W.y * P.y), yi = S * (W.x * P.y - W.y * P.x);
-    wy[t] = make_float2(yr, yi);
-    // xi, dxi/dx, dxi/dy by the factorised sums (not needed for the coefficient gradients alone)
+    // xi, dxi/dx, dxi/dy by the factorised sums
     float xr = 0.f, xi = 0.f, dxr = 0.f, dxi = 0.f, dyr = 0.f, dyi = 0.f;
-    if (!a.coef_only) {
+    {
       // phi_a(x) for a = 0 .. n + 1 (entries n + 2, n + 3 are zero; rows past n + 1 read entry n + 3)
       auto phx_at = [&](int aa) { return px[min(aa, n + 3)]; };
       float pa_prev = 0.f, pa_cur = px[0];
@@ -673,7 +637,7 @@ __global__ void __launch_bounds__(K4S_T) k4_grad_shape(const K4SArgs a) {
         }
       }
     }
-    if (valid && !a.coef_only) {
+    if (valid) {
       // Re(Y * (pr + i pi)) = yr pr - yi pi
       const float re_xi = yr * xr - yi * xi;  // Re(conj(W) V) / S_ref
       const float im_xi = yr * xi + yi * xr;  // Im(conj(W) V) / S_ref
@@ -697,61 +661,10 @@ __global__ void __launch_bounds__(K4S_T) k4_grad_shape(const K4SArgs a) {
       }
       nacc = 0;
     }
-    __syncthreads();
-    // coefficient gradients for this tile, for every (n1, n2) of the triangle in blocks of 2 x 4: one
-    // thread per block sums sum_v Re or Im (Y_v) phi_n1(x_v) phi_n2(y_v) over the tile's visibilities.
-    // -2 Re(Y s) phi phi with s = (-i)^(n1+n2) = 1, -i, -1, i takes Re(Y), Im(Y), -Re(Y), -Im(Y): the
-    // parity of n1 + n2 selects Re or Im (fixed within a block, since n1 starts even and n2 at 4J), the
-    // sign follows when the block is added to the FP64 sums.
-    const int nv = (int)min((long long)T, a.n_vis - tile * T);
-    for (int bk = t; coef && bk < nblk; bk += T) {
-      const int na0 = blocks[bk].x, nb0 = blocks[bk].y;
-      float s[2][4];
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int jj = 0; jj < 4; ++jj) s[i][jj] = 0.f;
-      for (int vv = 0; vv < nv; ++vv) {
-        const float2 w2 = wy[vv];
-        const float wr = w2.x, wi = w2.y;
-        const float2 px = *reinterpret_cast<const float2*>(phx + vv * ld + na0);
-        const float4 py4 = *reinterpret_cast<const float4*>(phy + vv * ld + nb0);
-        const float xr0 = wr * px.x, xi0 = wi * px.x, xr1 = wr * px.y, xi1 = wi * px.y;
-        s[0][0] = fmaf(xr0, py4.x, s[0][0]);
-        s[0][1] = fmaf(xi0, py4.y, s[0][1]);
-        s[0][2] = fmaf(xr0, py4.z, s[0][2]);
-        s[0][3] = fmaf(xi0, py4.w, s[0][3]);
-        s[1][0] = fmaf(xi1, py4.x, s[1][0]);
-        s[1][1] = fmaf(xr1, py4.y, s[1][1]);
-        s[1][2] = fmaf(xi1, py4.z, s[1][2]);
-        s[1][3] = fmaf(xr1, py4.w, s[1][3]);
-      }
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int jj = 0; jj < 4; ++jj) {
-          const int na = na0 + i, nb = nb0 + jj;
-          const double d = (double)((((na + nb) & 3) >= 2 ? 2.0f : -2.0f) * s[i][jj]);
-          if (reg_acc) accr[i][jj] += d;
-          else if (na + nb <= n) accd[toff[na] + nb] += d;
-        }
-    }
-    __syncthreads();
   }
-  if (reg_acc && coef) {  // the basis rows are free now: the sums go to the folded triangle there
-    if (t < nblk) {
-      const int na0 = blocks[t].x, nb0 = blocks[t].y;
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int jj = 0; jj < 4; ++jj)
-          if (na0 + i + nb0 + jj <= n) accd[toff[na0 + i] + nb0 + jj] = accr[i][jj];
-    }
-    __syncthreads();
-  }
-  // per-CTA partials (the flux factor of every group but the flux one is applied here, in FP64)
-  for (int k = t; coef && k < a.nnz; k += T)
-    a.part_c[(size_t)blockIdx.x * a.nnz + k] = accd[toff[__ldg(a.n1 + k)] + __ldg(a.n2 + k)] * flux;
+  // per-CTA partials of the scalar groups (the flux factor of every group but the flux one is applied
+  // here, in FP64); every thread is past its basis rows before the reduction reuses them
+  __syncthreads();
   double* red = reinterpret_cast<double*>(sm + lay.phy);  // [T][K4S_NS], in the second basis-row area
   for (int i = 0; i < K4S_NS; ++i) red[t * K4S_NS + i] = (accs[i] + (double)acc32[i]) * (i == 0 ? 1.0 : flux);
   __syncthreads();
@@ -894,7 +807,8 @@ int launch_grad(wn_ctx* ctx, const ObsDev& o, const Model* M, const PeelArgs& pa
   const size_t loss_bytes = ((size_t)loss_blocks * 8 + 255) & ~(size_t)255;
   const size_t pg_bytes = ((size_t)chunks * n_pg * K4_NG * 8 + 255) & ~(size_t)255;
   const size_t sh_bytes = M->n_shape ? (((size_t)sgrid * (K4S_NS + max_nnz) * 8 + 255) & ~(size_t)255) : 0;
-  const size_t need = chan_bytes + row_bytes + uvp_bytes + loss_bytes + pg_bytes + sh_bytes;
+  const size_t rowg_bytes = ((size_t)o.n_rows * sizeof(float2) + 255) & ~(size_t)255;
+  const size_t need = chan_bytes + row_bytes + uvp_bytes + loss_bytes + pg_bytes + sh_bytes + rowg_bytes;
   if (ctx->ws2_bytes < need) {
     if (ctx->ws2) {
       cudaStreamSynchronize(st);
@@ -913,6 +827,7 @@ int launch_grad(wn_ctx* ctx, const ObsDev& o, const Model* M, const PeelArgs& pa
   double* lpart = reinterpret_cast<double*>(ws + chan_bytes + row_bytes + uvp_bytes);
   double* pgpart = reinterpret_cast<double*>(ws + chan_bytes + row_bytes + uvp_bytes + loss_bytes);
   double* shpart = reinterpret_cast<double*>(ws + chan_bytes + row_bytes + uvp_bytes + loss_bytes + pg_bytes);
+  float2* rowg = reinterpret_cast<float2*>(ws + chan_bytes + row_bytes + uvp_bytes + loss_bytes + pg_bytes + sh_bytes);
   k4_split_uvw<<<(3 * o.n_rows + 255) / 256, 256, 0, st>>>(o.uvw, o.n_rows, uvp);
   if (int r = cuda_err("uvw split")) return r;
 
@@ -1000,15 +915,14 @@ int launch_grad(wn_ctx* ctx, const ObsDev& o, const Model* M, const PeelArgs& pa
     a.resid = resid;
     a.peel = pa;
     a.part_s = shpart;
-    a.part_c = shpart + (size_t)sgrid * K4S_NS;
     a.err = ctx->d_err;
-    a.skip_coef = 1;  // the coefficient gradients come from the tensor-core kernel below
+    double* part_c = shpart + (size_t)sgrid * K4S_NS;  // the tensor-core kernel's coefficient partials
     const size_t smax = 227 * 1024;
     int T = K4S_T;
-    size_t smem = (size_t)k4s_layout(h.nmax, a.nnz, T, true).total;
+    size_t smem = (size_t)k4s_layout(h.nmax, T).total;
     if (smem > smax) {
       T = K4S_T / 2;
-      smem = (size_t)k4s_layout(h.nmax, a.nnz, T, true).total;
+      smem = (size_t)k4s_layout(h.nmax, T).total;
     }
     if (smem > smax) return set_error(WN_EINVAL, "adjoint: shapelet too large for the shared-memory reduction");
     if (cudaError_t ea = allow_max_dynamic_smem(reinterpret_cast<const void*>(k4_grad_shape)))
@@ -1016,9 +930,9 @@ int launch_grad(wn_ctx* ctx, const ObsDev& o, const Model* M, const PeelArgs& pa
     k4_grad_shape<<<sgrid, T, smem, st>>>(a);
     if (int r = cuda_err("shapelet adjoint")) return r;
     int cgrid = 0;
-    if (int r = launch_coeff_mma(ctx, o, M, q, pa, resid, rowinfo, chaninfo, a.part_c, &cgrid, st)) return r;
+    if (int r = launch_coeff_mma(ctx, o, M, q, pa, resid, rowinfo, chaninfo, rowg, part_c, &cgrid, st)) return r;
     const int nout = a.nnz + K4S_NS;
-    k4_reduce_shape<<<(nout * 32 + 255) / 256, 256, 0, st>>>(shpart, a.part_c, sgrid, cgrid, a.nnz, j, q, g->flux,
+    k4_reduce_shape<<<(nout * 32 + 255) / 256, 256, 0, st>>>(shpart, part_c, sgrid, cgrid, a.nnz, j, q, g->flux,
                                                             g->alpha, g->l, g->m, g->s_beta1, g->s_beta2, g->s_pa,
                                                             g->s_coeff, M->s_off_host[q], 1);
     if (int r = cuda_err("shapelet adjoint reduction")) return r;
@@ -1037,9 +951,9 @@ int launch_grad_shape_coeff(wn_ctx* ctx, const ObsDev& o, const Model* M, const 
   const int sgrid = ctx->num_sms * 4;
   const size_t chan_bytes = ((size_t)o.n_chan * sizeof(float4) + 255) & ~(size_t)255;
   const size_t row_bytes = ((size_t)o.n_rows * sizeof(float4) + 255) & ~(size_t)255;
-  const size_t uvp_bytes = ((size_t)o.n_rows * 6 * sizeof(float) + 255) & ~(size_t)255;
   const size_t sh_bytes = (((size_t)sgrid * (K4S_NS + max_nnz) * 8 + 255) & ~(size_t)255);
-  const size_t need = chan_bytes + row_bytes + uvp_bytes + sh_bytes;
+  const size_t rowg_bytes = ((size_t)o.n_rows * sizeof(float2) + 255) & ~(size_t)255;
+  const size_t need = chan_bytes + row_bytes + sh_bytes + rowg_bytes;
   if (ctx->ws2_bytes < need) {
     if (ctx->ws2) {
       cudaStreamSynchronize(st);
@@ -1054,48 +968,18 @@ int launch_grad_shape_coeff(wn_ctx* ctx, const ObsDev& o, const Model* M, const 
   char* ws = static_cast<char*>(ctx->ws2);
   float4* chaninfo = reinterpret_cast<float4*>(ws);
   float4* rowinfo = reinterpret_cast<float4*>(ws + chan_bytes);
-  float* uvp = reinterpret_cast<float*>(ws + chan_bytes + row_bytes);
-  double* shpart = reinterpret_cast<double*>(ws + chan_bytes + row_bytes + uvp_bytes);
-  k4_split_uvw<<<(3 * o.n_rows + 255) / 256, 256, 0, st>>>(o.uvw, o.n_rows, uvp);
-  if (int r = cuda_err("uvw split")) return r;
-  const double L0 = std::log2(o.nu0);
+  double* shpart = reinterpret_cast<double*>(ws + chan_bytes + row_bytes);
+  float2* rowg = reinterpret_cast<float2*>(ws + chan_bytes + row_bytes + sh_bytes);
   const int n_pg = M->n_point + M->n_gauss;
-  const size_t n_vis = (size_t)o.n_rows * o.n_chan;
   for (int q = 0; q < M->n_shape; ++q) {
     if (int r = launch_shapelet_prep(ctx, o, M, q, chaninfo, rowinfo, q == 0, st)) return r;
-    const ShapeRec& h = M->sh_host[q];
-    const int j = n_pg + q;
-    K4SArgs a;
-    a.rowinfo = rowinfo;
-    a.chaninfo = chaninfo;
-    a.uvw_pairs = uvp;
-    a.n_rows = o.n_rows;
-    a.n_chan = o.n_chan;
-    a.n_base = o.n_base;
-    a.n_vis = (long long)n_vis;
-    a.nmax = h.nmax;
-    a.nnz = M->s_off_host[q + 1] - M->s_off_host[q];
-    a.n1 = M->m_n1() + M->s_off_host[q];
-    a.n2 = M->m_n2() + M->s_off_host[q];
-    a.coeff = M->s_coeff + M->s_off_host[q];
-    a.lnref_nu0_f = (float)((L0 - h.lref) * 0.6931471805599453);
-    a.l_over_n = (float)(h.l / (1.0 + h.nm1));
-    a.m_over_n = (float)(h.m / (1.0 + h.nm1));
-    a.c_amp = (float)((double)h.alpha * (L0 - h.lref));
-    a.alpha = h.alpha;
-    a.flux = M->r_flux() + j;
-    a.beta1 = M->r_sb1() + q;
-    a.beta2 = M->r_sb2() + q;
-    a.resid = resid;
-    a.peel = pa;
-    a.part_s = shpart;
-    a.part_c = shpart + (size_t)sgrid * K4S_NS;
-    a.err = ctx->d_err;
+    const int nnz = M->s_off_host[q + 1] - M->s_off_host[q];
+    double* part_c = shpart + (size_t)sgrid * K4S_NS;
     int cgrid = 0;
-    if (int r = launch_coeff_mma(ctx, o, M, q, pa, resid, rowinfo, chaninfo, a.part_c, &cgrid, st)) return r;
-    k4_reduce_shape<<<(a.nnz * 32 + 255) / 256, 256, 0, st>>>(shpart, a.part_c, sgrid, cgrid, a.nnz, j, q, nullptr,
-                                                             nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-                                                             gcoeff, M->s_off_host[q], 1);
+    if (int r = launch_coeff_mma(ctx, o, M, q, pa, resid, rowinfo, chaninfo, rowg, part_c, &cgrid, st)) return r;
+    k4_reduce_shape<<<(nnz * 32 + 255) / 256, 256, 0, st>>>(shpart, part_c, sgrid, cgrid, nnz, n_pg + q, q, nullptr,
+                                                           nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, gcoeff,
+                                                           M->s_off_host[q], 1);
     if (int r = cuda_err("shapelet coefficient adjoint")) return r;
   }
   return WN_OK;

@@ -43,6 +43,7 @@ struct K4MArgs {
   const float4* chaninfo;  // per channel: (nu/c hi, nu/c lo, log2(nu/nu0), nu)
   const float2* resid;     // R = D - G V
   PeelArgs peel;           // gains and antenna indices
+  const float2* rowg;      // [n_rows] gain product of frequency-independent gains, or nullptr
   long long n_vis;
   int n_chan, n_base;
   int nmax, k_pad, n_mblk, groups, n_tiles;
@@ -64,8 +65,8 @@ __host__ __device__ inline K4MLayout k4m_layout(int k_pad, int n_mblk, int group
   L.bz_bytes = n_mblk * 128 * K4M_TV * 2 * 2;
   L.av_bytes = k_pad * K4M_TV * 2 * 2;
   L.buf_bytes = (L.bz_bytes + L.av_bytes + 1023) & ~1023;
-  L.coef = groups * L.buf_bytes;
-  L.bars = L.coef + 2 * (kNmaxLimit + 1) * 4;
+  L.coef = groups * L.buf_bytes;  // a_n, b_n (128 floats each), then {a_n, a_n}, {-b_n, -b_n} (128 float2 each)
+  L.bars = L.coef + 2 * (kNmaxLimit + 1) * 4 + 2 * (kNmaxLimit + 1) * 8;
   L.total = L.bars + 64;  // afull[2], mdone[2], dfin, TMEM address slot
   return L;
 }
@@ -122,6 +123,8 @@ __global__ void __launch_bounds__(K4M_THREADS, 1) k4_coeff_mma(const K4MArgs a) 
   const K4MLayout lay = k4m_layout(a.k_pad, a.n_mblk, ng);
   float* ca = reinterpret_cast<float*>(smem + lay.coef);
   float* cb = ca + (kNmaxLimit + 1);
+  float2* ca2 = reinterpret_cast<float2*>(cb + (kNmaxLimit + 1));
+  float2* cb2 = ca2 + (kNmaxLimit + 1);
   uint64_t* afull = reinterpret_cast<uint64_t*>(smem + lay.bars);  // [parity] producers -> MMA: tile written
   uint64_t* mdone = afull + 2;                                      // [parity] MMA -> producers: tile read
   uint64_t* dfin = mdone + 2;                                       // MMA -> all: every MMA complete
@@ -139,8 +142,11 @@ __global__ void __launch_bounds__(K4M_THREADS, 1) k4_coeff_mma(const K4MArgs a) 
   }
   if (threadIdx.x <= kNmaxLimit) {  // sqrt(2 / (n + 1)), sqrt(n / (n + 1)), correctly rounded via FP64
     const double np1 = (double)(threadIdx.x + 1);
-    ca[threadIdx.x] = (float)sqrt(2.0 / np1);
-    cb[threadIdx.x] = (float)sqrt((double)threadIdx.x / np1);
+    const float fa = (float)sqrt(2.0 / np1), fb = (float)sqrt((double)threadIdx.x / np1);
+    ca[threadIdx.x] = fa;
+    cb[threadIdx.x] = fb;
+    ca2[threadIdx.x] = make_float2(fa, fa);
+    cb2[threadIdx.x] = make_float2(-fb, -fb);
   }
   if (warp == K4M_MMA_WARP) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)), "r"(ncols)
@@ -194,60 +200,108 @@ __global__ void __launch_bounds__(K4M_THREADS, 1) k4_coeff_mma(const K4MArgs a) 
     const int sp = warp >> 2;
     if (sp < ng) {
       unsigned char* buf = smem + sp * lay.buf_bytes;
+      unsigned char* av = buf + lay.bz_bytes;
+      unsigned char* av_lo = av + a.k_pad * K4M_TV * 2;
+      unsigned char* bz_lo = buf + a.n_mblk * 128 * K4M_TV * 2;
       const float xcut = sqrtf(2.0f * a.nmax + 1.0f) + 10.0f;
-      for (int it = sp, j = 0; it < n_it; it += ng, ++j) {
+      const int nb1 = a.nmax + 1;
+      const int nca = a.k_pad >> 3, ncb = (nb1 + 7) >> 3;  // chunks of 8 of phi(x) and of phi(y)
+      // this visibility's place in the A and Bz tiles: K core t / 8, core-matrix row t % 8
+      const uint32_t a_off = (uint32_t)(t >> 3) * skb + (uint32_t)(t & 7) * 16u;
+      const uint32_t z_off = (uint32_t)(t >> 3) * 2048u + (uint32_t)(t & 7) * 16u;
+      auto bz_at = [&](int c) { return (uint32_t)(c >> 4) * (128u * K4M_TV * 2u) + z_off + (uint32_t)(c & 15) * 128u; };
+      // Bz rows of orders above those present are zero in every tile: written once here
+      for (int c = 2 * ncb; c < 16 * a.n_mblk; ++c) {
+        *reinterpret_cast<uint4*>(buf + bz_at(c)) = make_uint4(0, 0, 0, 0);
+        *reinterpret_cast<uint4*>(bz_lo + bz_at(c)) = make_uint4(0, 0, 0, 0);
+      }
+      auto store_a = [&](int c, const float (&v)[8]) {
+        uint4 hi, lo;
+        bf16_pack8(v, hi, lo);
+        *reinterpret_cast<uint4*>(av + a_off + (uint32_t)c * 128u) = hi;
+        *reinterpret_cast<uint4*>(av_lo + a_off + (uint32_t)c * 128u) = lo;
+      };
+      // chunk c8 of phi(y) (b = 8 c8 ..) fills Bz chunks 2 c8, 2 c8 + 1: rows 2b (Re Y), 2b + 1 (Im Y)
+      auto store_b = [&](int c8, const float (&v)[8], float yr, float yi) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int c = 2 * c8 + h;
+          float z[8];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const float ph = 4 * c + i < nb1 ? v[4 * h + i] : 0.f;
+            z[2 * i] = ph * yr;
+            z[2 * i + 1] = ph * yi;
+          }
+          uint4 hi, lo;
+          bf16_pack8(z, hi, lo);
+          *reinterpret_cast<uint4*>(buf + bz_at(c)) = hi;
+          *reinterpret_cast<uint4*>(bz_lo + bz_at(c)) = lo;
+        }
+      };
+      // inputs of one tile's visibility, loaded a tile ahead of their use
+      struct In {
+        float4 ri, ci;
+        float2 R, G;
+        bool valid;
+      };
+      auto load_in = [&](int it) {
+        In v;
         const long long vis = (long long)(blockIdx.x + (long long)it * gridDim.x) * K4M_TV + t;
-        const bool valid = vis < a.n_vis;
-        const int row = valid ? (int)(vis / a.n_chan) : 0;
-        const int f = valid ? (int)(vis - (long long)row * a.n_chan) : 0;
-        const float4 ri = __ldg(a.rowinfo + row), ci = __ldg(a.chaninfo + f);
-        const float x = ri.x * ci.w, y = ri.y * ci.w;
+        v.valid = it < n_it && vis < a.n_vis;
+        const int row = v.valid ? (int)(vis / a.n_chan) : 0;
+        const int f = v.valid ? (int)(vis - (long long)row * a.n_chan) : 0;
+        v.ri = __ldg(a.rowinfo + row);
+        v.ci = __ldg(a.chaninfo + f);
+        v.R = v.valid ? __ldg(a.resid + vis) : make_float2(0.f, 0.f);
+        v.G = make_float2(0.f, 0.f);
+        if (v.valid) {
+          if (a.rowg) v.G = __ldg(a.rowg + row);
+          else if (!gain_product(a.peel, row, a.n_base, f, v.G)) atomicOr(a.err, WN_DEVERR_ANTENNA);
+        }
+        return v;
+      };
+      In cur = load_in(sp);
+      for (int it = sp, j = 0; it < n_it; it += ng, ++j) {
+        const In nxt = load_in(it + ng);
+        const float x = cur.ri.x * cur.ci.w, y = cur.ri.y * cur.ci.w;
         float yr = 0.f, yi = 0.f;
-        if (valid) {
-          float2 G;
-          if (!gain_product(a.peel, row, a.n_base, f, G)) atomicOr(a.err, WN_DEVERR_ANTENNA);
-          const float2 R = __ldg(a.resid + vis);
-          const float2 W = make_float2(G.x * R.x + G.y * R.y, G.x * R.y - G.y * R.x);  // conj(G) R
-          const float2 P = phasor_fast(reduce_turns(ri.z, ri.w, ci.x, ci.y));
-          const float S = ex2_approx(fmaf(a.alpha, ci.z, a.c_amp));
+        if (cur.valid) {
+          const float2 W = make_float2(cur.G.x * cur.R.x + cur.G.y * cur.R.y, cur.G.x * cur.R.y - cur.G.y * cur.R.x);
+          const float2 P = phasor_fast(reduce_turns(cur.ri.z, cur.ri.w, cur.ci.x, cur.ci.y));
+          const float S = ex2_approx(fmaf(a.alpha, cur.ci.z, a.c_amp));
           yr = S * (W.x * P.x + W.y * P.y);  // Y = conj(W) S P
           yi = S * (W.x * P.y - W.y * P.x);
         }
         if (j > 0 && !mbar_wait_bounded(&mdone[sp], (j - 1) & 1, a.err)) break;  // MMA(j-1) has read the buffer
-        // A = phi_a(x): chunk c (a = 8c .. 8c + 7) of visibility t at K core t / 8, MN core c, row t % 8
-        unsigned char* av = buf + lay.bz_bytes;
-        unsigned char* av_lo = av + a.k_pad * K4M_TV * 2;
-        const uint32_t a_off = (uint32_t)(t >> 3) * skb + (uint32_t)(t & 7) * 16u;
-        hermite_chunks(x, !valid, xcut, a.k_pad >> 3, ca, cb, [&](int c, const float (&v)[8]) {
-          uint4 hi, lo;
-          bf16_pack8(v, hi, lo);
-          *reinterpret_cast<uint4*>(av + a_off + (uint32_t)c * 128u) = hi;
-          *reinterpret_cast<uint4*>(av_lo + a_off + (uint32_t)c * 128u) = lo;
-        });
-        // Bz: rows n = 2b (Re Y), 2b + 1 (Im Y); chunk c8 of phi(y) (b = 8 c8 ..) fills Bz chunks 2 c8, 2 c8 + 1
-        unsigned char* bz_lo = buf + a.n_mblk * 128 * K4M_TV * 2;
-        const uint32_t z_off = (uint32_t)(t >> 3) * 2048u + (uint32_t)(t & 7) * 16u;
-        const int nb1 = a.nmax + 1;
-        hermite_chunks(y, !valid, xcut, a.n_mblk * 8, ca, cb, [&](int c8, const float (&v)[8]) {
+        const bool zx = !cur.valid || !(fabsf(x) <= xcut), zy = !cur.valid || !(fabsf(y) <= xcut);
+        if ((zx || fabsf(x) <= 12.5f) && (zy || fabsf(y) <= 12.5f)) {
+          // both recurrences unscaled, as one f32x2 recurrence {phi(x), phi(y)}
+          const float2 X = make_float2(x, y);
+          float2 P = make_float2(zx ? 0.f : exp2f(-0.5f * x * x * 1.4426950408889634f),
+                                 zy ? 0.f : exp2f(-0.5f * y * y * 1.4426950408889634f));
+          float2 Pp = make_float2(0.f, 0.f);
+          const int nc = max(nca, ncb);
+          for (int c = 0; c < nc; ++c) {
+            float vx[8], vy[8];
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int c = 2 * c8 + h;  // Bz chunk: n = 8c .. 8c + 7, b = 4c .. 4c + 3
-            float z[8];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              const float ph = 4 * c + i < nb1 ? v[4 * h + i] : 0.f;
-              z[2 * i] = ph * yr;
-              z[2 * i + 1] = ph * yi;
+            for (int i = 0; i < 8; ++i) {
+              vx[i] = P.x;
+              vy[i] = P.y;
+              const float2 Pn = __ffma2_rn(__fmul2_rn(ca2[8 * c + i], X), P, __fmul2_rn(cb2[8 * c + i], Pp));
+              Pp = P;
+              P = Pn;
             }
-            uint4 hi, lo;
-            bf16_pack8(z, hi, lo);
-            const uint32_t off = (uint32_t)(c >> 4) * (128u * K4M_TV * 2u) + z_off + (uint32_t)(c & 15) * 128u;
-            *reinterpret_cast<uint4*>(buf + off) = hi;
-            *reinterpret_cast<uint4*>(bz_lo + off) = lo;
+            if (c < nca) store_a(c, vx);
+            if (c < ncb) store_b(c, vy, yr, yi);
           }
-        });
+        } else {
+          hermite_chunks(x, !cur.valid, xcut, nca, ca, cb, [&](int c, const float (&v)[8]) { store_a(c, v); });
+          hermite_chunks(y, !cur.valid, xcut, ncb, ca, cb, [&](int c8, const float (&v)[8]) { store_b(c8, v, yr, yi); });
+        }
         fence_async_smem();
         mbar_arrive(&afull[sp]);
+        cur = nxt;
       }
     }
   }
@@ -287,15 +341,23 @@ __global__ void __launch_bounds__(K4M_THREADS, 1) k4_coeff_mma(const K4MArgs a) 
 }
 
 // Launch for shapelet q of M: coefficient-gradient partial sums [grid][nnz] into part_c (grid returned),
-// from the residual and the per-row / per-channel tables the shapelet prep wrote (rowinfo, chaninfo).
+// from the residual and the per-row / per-channel tables the shapelet prep wrote (rowinfo, chaninfo);
+// rowg_ws (n_rows float2, or nullptr) receives the per-row gain products when the gains do not depend
+// on frequency.
 int launch_coeff_mma(wn_ctx* ctx, const ObsDev& o, const Model* M, int q, const PeelArgs& pa, const float2* resid,
-                     const float4* rowinfo, const float4* chaninfo, double* part_c, int* grid_out, cudaStream_t st) {
+                     const float4* rowinfo, const float4* chaninfo, float2* rowg_ws, double* part_c, int* grid_out,
+                     cudaStream_t st) {
   const ShapeRec& h = M->sh_host[q];
   K4MArgs a;
   a.rowinfo = rowinfo;
   a.chaninfo = chaninfo;
   a.resid = resid;
   a.peel = pa;
+  a.rowg = nullptr;
+  if (rowg_ws && pa.gf == 1) {  // frequency-independent gains: one product per row, read without dependent loads
+    launch_rowgain(pa, o.n_rows, o.n_base, rowg_ws, ctx->d_err, st);
+    a.rowg = rowg_ws;
+  }
   a.n_vis = (long long)o.n_rows * o.n_chan;
   a.n_chan = o.n_chan;
   a.n_base = o.n_base;

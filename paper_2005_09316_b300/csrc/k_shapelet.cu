@@ -735,6 +735,10 @@ __global__ void k2_rowgain(PeelArgs p, int n_rows, int n_base, float2* out, unsi
   out[r] = G;
 }
 
+void launch_rowgain(const PeelArgs& pa, int n_rows, int n_base, float2* out, unsigned* err, cudaStream_t st) {
+  k2_rowgain<<<(n_rows + 255) / 256, 256, 0, st>>>(pa, n_rows, n_base, out, err);
+}
+
 template <int KP, int R, int FORM>
 static cudaError_t k2_launch_t(const K2Args& a, int grid, int smem, cudaStream_t st) {
   auto fn = k2_shapelet<KP, R, FORM>;

@@ -399,7 +399,11 @@ size_t static_scratch_entries();
 int static_scratch_setup(wn_ctx* ctx);
 int grad_constants_setup(wn_ctx* ctx);
 int launch_coeff_mma(wn_ctx* ctx, const ObsDev& o, const Model* M, int q, const PeelArgs& pa, const float2* resid,
-                     const float4* rowinfo, const float4* chaninfo, double* part_c, int* grid_out, cudaStream_t st);
+                     const float4* rowinfo, const float4* chaninfo, float2* rowg_ws, double* part_c, int* grid_out,
+                     cudaStream_t st);
+// Per-row gain product g[ant1] conj(g[ant2]) of frequency-independent gains (NaN and the antenna flag for
+// an index out of range).
+void launch_rowgain(const PeelArgs& pa, int n_rows, int n_base, float2* out, unsigned* err, cudaStream_t st);
 int launch_grad(wn_ctx* ctx, const ObsDev& o, const Model* M, const PeelArgs& pa, float2* resid,
                 const wn_sky_grad* g, double* loss, cudaStream_t st);
 int k1_batched_smem();
