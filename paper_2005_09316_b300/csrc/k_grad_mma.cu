@@ -129,7 +129,8 @@ __global__ void __launch_bounds__(K4M_THREADS, 1) k4_coeff_mma(const K4MArgs a) 
   uint64_t* mdone = afull + 2;                                      // [parity] MMA -> producers: tile read
   uint64_t* dfin = mdone + 2;                                       // MMA -> all: every MMA complete
   uint32_t* tslot = reinterpret_cast<uint32_t*>(dfin + 1);
-  const int warp = threadIdx.x >> 5, t = threadIdx.x & 127;
+  // warp index and TMEM base broadcast from lane 0: warp-uniform values for the tcgen05 operands
+  const int warp = __shfl_sync(0xffffffffu, (int)(threadIdx.x >> 5), 0), t = threadIdx.x & 127;
   const int acc_cols = a.n_mblk * a.k_pad;
   const uint32_t ncols = acc_cols <= 32 ? 32 : (acc_cols <= 64 ? 64 : (acc_cols <= 128 ? 128 : 256));
   if (threadIdx.x == 0) {
@@ -156,18 +157,20 @@ __global__ void __launch_bounds__(K4M_THREADS, 1) k4_coeff_mma(const K4MArgs a) 
   }
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem = *tslot;
+  const uint32_t tmem = __shfl_sync(0xffffffffu, *tslot, 0);
   const int n_it = a.n_tiles > (int)blockIdx.x ? (a.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   const uint32_t skb = (uint32_t)(a.k_pad >> 3) << 7;  // A: bytes between core matrices adjacent in K
 
   if (warp == K4M_MMA_WARP) {
     // ---------------- MMA issue: every tile into the one accumulator ----------------
-    if ((threadIdx.x & 31) == 0) {
+    // The whole warp runs the loop (warp-uniform descriptors); the elected lane issues.
+    {
+      const uint32_t lead = elect_lane();
       const uint32_t idesc = umma_idesc_bf16(a.k_pad, true, true);
       bool ok = true;
       for (int it = 0; ok && it < n_it; ++it) {
         const int sp = it % ng, j = it / ng;
-        if (!mbar_wait_bounded(&afull[sp], j & 1, a.err)) {
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&afull[sp], j & 1, a.err))) {
           ok = false;
           break;
         }
@@ -186,13 +189,13 @@ __global__ void __launch_bounds__(K4M_THREADS, 1) k4_coeff_mma(const K4MArgs a) 
               // Bz (MMA A): K cores 2048 B apart, 8-row MN cores 128 B apart; A (MMA B): K cores skb apart
               const uint64_t da = umma_desc(aa + (uint32_t)(2 * kk) * 2048u, 2048u, 128u);
               const uint64_t db = umma_desc(bb + (uint32_t)(2 * kk) * skb, skb, 128u);
-              umma_bf16(d, da, db, idesc, (it > 0 || p > 0 || kk > 0) ? 1u : 0u);
+              umma_bf16_by(lead, d, da, db, idesc, (it > 0 || p > 0 || kk > 0) ? 1u : 0u);
             }
           }
         }
-        umma_commit(&mdone[sp]);
+        umma_commit_by(lead, &mdone[sp]);
       }
-      umma_commit(dfin);  // completes once every MMA issued above has completed
+      umma_commit_by(lead, dfin);  // completes once every MMA issued above has completed
     }
     __syncwarp();
   } else {

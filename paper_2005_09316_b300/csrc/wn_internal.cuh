@@ -416,6 +416,8 @@ cudaError_t k1_batched_setup();
 int k1_batched_args(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, int mode, const PeelArgs& pa,
                     K1Args* args, int* grid_x, int* grid_y);
 cudaError_t k1_batched_launch(const K1Args* reqs, const K1Work* work, const int* n_work, int grid, cudaStream_t st);
+// Shapelet launches with caller-supplied tables: chaninfo [n_chan] and rowinfo [rowinfo_cap >= n_rows] float4
+// (room for rowinfo_cap / n_rows shapelets' row tables; more shapelets per launch when there is room).
 int launch_shapelets_ws(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, int mode, const PeelArgs& pa,
-                        float4* chaninfo, float4* rowinfo, cudaStream_t st, float2* rowg = nullptr);
+                        float4* chaninfo, float4* rowinfo, size_t rowinfo_cap, cudaStream_t st, float2* rowg = nullptr);
 }  // namespace wn

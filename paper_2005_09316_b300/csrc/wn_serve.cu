@@ -149,6 +149,9 @@ static void pool_free(wn_server* s, size_t off, size_t bytes) {
 
 static size_t round_bytes(size_t b) { return (b + 255) & ~(size_t)255; }
 
+// Shapelet row tables a slot holds: a request's shapelets are summed this many per launch.
+constexpr int kSlotRowTables = 4;
+
 static bool has_pg(const ServeReq& r) { return r.M->n_point + r.M->n_gauss > 0 || r.M->n_shape == 0; }
 
 // Launch on slot k the work table in the slot's pinned staging (nwork entries), the shapelets of the
@@ -163,7 +166,7 @@ static void launch_slot(wn_server* s, int k, int nwork, const std::vector<uint64
     ServeReq& r = s->reqs[t];
     const int smode = r.M->n_point + r.M->n_gauss > 0 ? (r.mode == OUT_PEEL ? OUT_SUBG : OUT_ACCUM) : r.mode;
     if (launch_shapelets_ws(s->ctx, r.od, r.M, reinterpret_cast<float2*>(s->pool + r.off), smode, r.pa, sl.chaninfo,
-                            sl.rowinfo, sl.st) != WN_OK) {
+                            sl.rowinfo, (size_t)kSlotRowTables * s->max_rows, sl.st) != WN_OK) {
       r.state = RQ_FAILED;
       r.error = WN_ECUDA;
     }
@@ -450,7 +453,7 @@ int wn_server_create(wn_ctx* ctx, int n_streams, size_t pool_bytes, int max_infl
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = dev_malloc(&sl.d_table, s->table_bytes);
     if (e == cudaSuccess) e = cudaHostAlloc(&sl.h_table, s->table_bytes, cudaHostAllocDefault);
-    if (e == cudaSuccess) e = dev_malloc(&sl.chaninfo, chan_bytes + (size_t)max_rows * sizeof(float4));
+    if (e == cudaSuccess) e = dev_malloc(&sl.chaninfo, chan_bytes + (size_t)kSlotRowTables * max_rows * sizeof(float4));
     if (e == cudaSuccess) sl.rowinfo = reinterpret_cast<float4*>(reinterpret_cast<char*>(sl.chaninfo) + chan_bytes);
     if (e == cudaSuccess) {
       // graph per stream: copy of the work table from pinned memory, then the batched kernel

@@ -339,3 +339,58 @@ def test_fornax_full_size_tf32_split_mode(wn, ctx):
     assert np.max(np.abs(got - ref)) <= 2e-4 * np.max(np.abs(V))
     assert ctx.device_errors() == 0
     m.free()
+
+
+@pytest.mark.parametrize("mode_name,tol", [("WN_SHAPE_BF16X3", 2e-4), ("WN_SHAPE_LUT_BF16X3", 1e-3),
+                                           ("WN_SHAPE_TF32", 1e-3), ("WN_SHAPE_TF32X3", 2e-4)])
+def test_many_shapelets_summed_in_runs(wn, ctx, mode_name, tol):
+    """Eleven shapelets of mixed orders (more than one launch sums, so two runs of launches) on an odd
+    channel count and a ragged visibility count: prediction and fused peel against the oracle, element
+    by element, in every shapelet mode; the peel's gains depend on frequency (per-visibility gain
+    products) and on time."""
+    nmaxs = [0, 3, 7, 12, 20, 33, 47, 60, 5, 16, 1]
+    obs = synth.make_obs(41, 13, 3, synth.uniform_channels(167e6, 80e3, 37), layout="mwa", max_baseline=5000.0,
+                         dec0=-37.2 * synth.DEG)
+    sky = shapelet_sky(42, nmaxs, n_point=7)
+    rows = np.arange(obs.n_rows)
+    V = oracle_rows(obs, sky, rows)
+    data = V + synth.complex_noise(3, V.shape, 0.05)
+    gains = synth.make_gains(4, obs.n_ant, obs.n_time, obs.n_chan)
+    ref = oracle_peel_rows(obs, rows, gains, data, V)
+    ctx.set_precision(0, getattr(wn, mode_name))
+    try:
+        d = wn.obs_to_device(obs)
+        m = ctx.upload(sky)
+        got = ctx.predict(d, m).cpu().numpy().reshape(obs.n_rows, obs.n_chan)
+        gd = torch.as_tensor(gains.astype(np.complex64)).cuda()
+        dd = torch.as_tensor(data.astype(np.complex64).reshape(obs.n_time, obs.n_base, obs.n_chan)).cuda()
+        r = ctx.peel(d, m, gd, dd).cpu().numpy().reshape(obs.n_rows, obs.n_chan)
+        m.free()
+    finally:
+        ctx.set_precision(0, 0)
+    assert ctx.device_errors() == 0
+    scale = np.max(np.abs(V))
+    assert np.max(np.abs(got - V)) <= tol * scale, np.max(np.abs(got - V)) / scale
+    assert np.max(np.abs(r - ref)) <= tol * scale, np.max(np.abs(r - ref)) / scale
+
+
+def test_large_operands_split_into_runs(wn, ctx):
+    """Three full n_max = 80 shapelets (k_pad 96, n_pad 176): two operands do not fit in shared memory beside
+    one launch's A buffers, so each is its own launch, the later ones subtracting from the first's
+    output; peel against the oracle."""
+    obs = synth.make_obs(43, 12, 2, synth.uniform_channels(167e6, 1e6, 24), layout="mwa", max_baseline=3000.0,
+                         dec0=-30 * synth.DEG)
+    sky = shapelet_sky(44, [80, 80, 80])
+    rows = np.arange(obs.n_rows)
+    V = oracle_rows(obs, sky, rows)
+    data = V + synth.complex_noise(5, V.shape, 0.05)
+    gains = synth.make_gains(6, obs.n_ant, obs.n_time, 1)
+    ref = oracle_peel_rows(obs, rows, gains, data, V)
+    d = wn.obs_to_device(obs)
+    m = ctx.upload(sky)
+    gd = torch.as_tensor(gains.astype(np.complex64)).cuda()
+    dd = torch.as_tensor(data.astype(np.complex64).reshape(obs.n_time, obs.n_base, obs.n_chan)).cuda()
+    r = ctx.peel(d, m, gd, dd).cpu().numpy().reshape(obs.n_rows, obs.n_chan)
+    m.free()
+    assert ctx.device_errors() == 0
+    assert np.max(np.abs(r - ref)) <= 2e-4 * np.max(np.abs(V))
