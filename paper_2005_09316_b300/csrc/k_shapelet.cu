@@ -23,10 +23,10 @@
 //    products hi*hi + hi*lo + lo*hi in the split mode; one M = 128 block per r) into the parity's TMEM
 //    accumulators and commits to an mbarrier, alternating the parities item by item;
 //  * epilogue warpgroups E0, E1 (warps 8-11, 12-15) read their accumulator rows from TMEM (warp w
-//    reaches lanes 32 (w % 4) ..), stream phi_n(y) against them, release TMEM, weight the dot products
-//    by the shapelet's spectrum and phasor and sum them over the tile's items.  The epilogue keeps
-//    the sums of rows 0 .. RE-1; those of rows RE .. R-1 go to the producers through shared memory,
-//    which keep their sums and write those rows' output while the next item's MMA runs.
+//    reaches lanes 32 (w % 4) ..), stream phi_n(y) against them, release TMEM and hand the dot products
+//    to the producers through shared memory;
+//  * the producers, while the next item's MMA runs, weight the dot products by the shapelet's spectrum
+//    and phasor, sum them over the tile's items and write the tile's output after its last item.
 //  R = 2 when two parities of the doubled A buffers and 4 n_pad TMEM columns fit (n_pad <= 128),
 //  else R = 1.
 //  Per parity: P(k+1) waits for MMA(k) to finish reading A, MMA(k+1) for E(k) to release TMEM.
@@ -45,8 +45,6 @@ constexpr int K2_GROUPS = 2;                     // tile parities in flight
 constexpr int K2_THREADS = 32 * (8 * K2_GROUPS + 1);
 constexpr int K2_MMA_WARP = 8 * K2_GROUPS;
 constexpr int K2_MAXS = 8;                       // shapelets summed in one launch
-// Rows per thread whose output the epilogue forms itself (the rest go to the producers): half of them.
-#define K2_RE(R) ((R) / 2)
 
 // The normalised Hermite recurrence phi_{n+1} = a_n x phi_n - b_n phi_{n-1}, a_n = sqrt(2/(n+1)),
 // b_n = sqrt(n/(n+1)).
@@ -476,7 +474,6 @@ __device__ __forceinline__ void k2_mma_ksteps(uint32_t lead, uint32_t d, uint64_
 template <int R, int FORM>
 __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
   constexpr bool LUT = FORM == 1, TF32 = FORM == 2;
-  constexpr int RE = K2_RE(R);
   constexpr int TV = K2_M * R;  // visibilities per tile
   extern __shared__ __align__(1024) unsigned char smem[];
   const int ng = a.groups;  // tile parities in flight (2, or 1 when two A buffers do not fit)
@@ -619,9 +616,9 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
     };
     float xs[R], nu[R];
     load_x(cur, 0, xs, nu);
-    // The output step of an item for rows RE .. R-1: the item's weight times the epilogue's dot products,
-    // summed over the tile's items; the tile's output once its last item is in.  The loads are issued first
-    // and arrive while the epilogue finishes.
+    // The output step of an item: its weight times the epilogue's dot products, summed over the tile's
+    // items; the tile's output once its last item is in.  The loads are issued first and arrive while
+    // the epilogue finishes.
     float2 z[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) z[r] = make_float2(0.f, 0.f);
@@ -630,7 +627,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
       float4 ri[R], ci[R];
       K2Base b[R];
 #pragma unroll
-      for (int r = RE; r < R; ++r) {
+      for (int r = 0; r < R; ++r) {
         const bool v = c[r].row < a.n_rows;
         ri[r] = v ? __ldg(a.rowinfo + (size_t)q * a.n_rows + c[r].row) : make_float4(0.f, 0.f, 0.f, 0.f);
         ci[r] = v ? __ldg(a.chaninfo + c[r].f) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -638,14 +635,14 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
       }
       if (!k2_wait(&xfull[sp], jo & 1, a.err)) return false;
 #pragma unroll
-      for (int r = RE; r < R; ++r) {
+      for (int r = 0; r < R; ++r) {
         const float2 d = xfer[r * K2_M];
         z[r] = k2_sum(z[r], q == 0, k2_weight(shs[q], ri[r].z, ri[r].w, ci[r]), d.x, d.y);
       }
       mbar_arrive(&xempty[sp]);
       if (last) {
 #pragma unroll
-        for (int r = RE; r < R; ++r) k2_store(a, c[r], b[r], z[r]);
+        for (int r = 0; r < R; ++r) k2_store(a, c[r], b[r], z[r]);
       }
       return true;
     };
@@ -691,7 +688,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
     }
     if (pq >= 0 && len > 0) out_item(pc, pq, len - 1);
   } else {
-    // ---------------- epilogues: xi = sum_n2 T[., n2] phi_n2(y), weighted and summed over the items ----------------
+    // ---------------- epilogues: xi = sum_n2 T[., n2] phi_n2(y), handed to the producers ----------------
     const int sp = (warp - 4 * K2_GROUPS) >> 2;
     if (sp >= ng) goto done;
     const int m = threadIdx.x & 127;
@@ -701,44 +698,25 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
     VisCur cur[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) cur[r] = vc_start(first_vis(sp, r), a.n_chan);
-    // per item: the row table entry (ys for every row; tau too for the rows whose output is formed here)
-    // and the channel entry, loaded one item ahead
-    auto load_y = [&](const VisCur (&c)[R], int q, float4 (&ri)[R], float4 (&ci)[R]) {
+    // per item: the row table's ys and the channel's nu, loaded one item ahead
+    auto load_y = [&](const VisCur (&c)[R], int q, float (&ys)[R], float (&nu)[R]) {
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const bool v = c[r].row < a.n_rows;
-        const float4* rp = a.rowinfo + (size_t)q * a.n_rows + c[r].row;
-        if (r < RE) {
-          ri[r] = v ? __ldg(rp) : make_float4(0.f, 0.f, 0.f, 0.f);
-          ci[r] = v ? __ldg(a.chaninfo + c[r].f) : make_float4(0.f, 0.f, 0.f, 1.f);
-        } else {
-          ri[r].y = v ? __ldg(&rp->y) : 0.f;
-          ci[r].w = v ? __ldg(&a.chaninfo[c[r].f].w) : 1.f;
-        }
+        ys[r] = v ? __ldg(&a.rowinfo[(size_t)q * a.n_rows + c[r].row].y) : 0.f;
+        nu[r] = v ? __ldg(&a.chaninfo[c[r].f].w) : 1.f;
       }
     };
-    float4 ri[R], ci[R];
-    load_y(cur, 0, ri, ci);
-    float2 z[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) z[r] = make_float2(0.f, 0.f);
+    float ys[R], nu[R];
+    load_y(cur, 0, ys, nu);
     int q = 0;
     for (int jj = 0; jj < len; ++jj) {
-      const bool last = q == S - 1;
       bool valid[R];
       float y[R];
-      float4 rw[R], cw[R];  // this item's entries, kept for the weight
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         valid[r] = cur[r].row < a.n_rows;
-        y[r] = ri[r].y * ci[r].w;
-        rw[r] = ri[r];
-        cw[r] = ci[r];
-      }
-      K2Base b[R];  // the inputs of this thread's own outputs, in flight during the wait
-      if (last) {
-#pragma unroll
-        for (int r = 0; r < RE; ++r) k2_base_load(a, cur[r], b[r]);
+        y[r] = ys[r] * nu[r];
       }
       const int n_pad = __shfl_sync(0xffffffffu, shs[q].n_pad, 0), nmax = shs[q].nmax;
       VisCur nc[R];
@@ -751,7 +729,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
         for (int r = 0; r < R; ++r) vc_next(nc[r], a);
       }
       if (!k2_wait(&mdone[sp], jj & 1, a.err)) break;
-      if (jj + 1 < len) load_y(nc, nq, ri, ci);  // the next item's entries in flight
+      if (jj + 1 < len) load_y(nc, nq, ys, nu);  // the next item's entries in flight
       tc_fence_after();
       const float ycut = sqrtf(2.0f * nmax + 1.0f) + 10.0f;
       float qv[R], q_prev[R], scale[R], xr[R], xi[R];
@@ -829,13 +807,8 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
       if (!released) release();
       if (jj > 0 && !k2_wait(&xempty[sp], (jj - 1) & 1, a.err)) break;  // the producers have read item jj-1's
 #pragma unroll
-      for (int r = RE; r < R; ++r) xfer[r * K2_M] = valid[r] ? make_float2(xr[r], xi[r]) : make_float2(0.f, 0.f);
+      for (int r = 0; r < R; ++r) xfer[r * K2_M] = valid[r] ? make_float2(xr[r], xi[r]) : make_float2(0.f, 0.f);
       mbar_arrive(&xfull[sp]);
-#pragma unroll
-      for (int r = 0; r < RE; ++r) {
-        z[r] = k2_sum(z[r], q == 0, k2_weight(shs[q], rw[r].z, rw[r].w, cw[r]), xr[r], xi[r]);
-        if (last) k2_store(a, cur[r], b[r], z[r]);
-      }
 #pragma unroll
       for (int r = 0; r < R; ++r) cur[r] = nc[r];
       q = nq;
