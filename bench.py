@@ -284,7 +284,9 @@ def bench_shapelets(wn, ctx, local, P, torch):
             "roofline": {"bound": "tensor", "achieved": round(tf, 2), "peak": peak, "unit": "TFLOP/s",
                          "frac": round(tf / peak, 4),
                          "traffic": traffic_record("k2_shapelet_fornax_traffic.json"),
-                         "traffic_unit": "bytes per launch (one shapelet; ncu dram__bytes_read + write, full size)",
+                         "traffic_unit": "bytes per launch (one launch sums both shapelets and writes the residual "
+                                         "once; ncu dram__bytes_read + write, full size)",
+                         "algorithmic_bytes": 16 * obs.n_vis,
                          "useful_achieved": round(tf_useful, 2), "useful_frac": round(tf_useful / peak, 4),
                          "note": "issued bf16 flops (2 k_pad n_pad x 3 products per visibility); useful: "
                                  "2 nnz per visibility"},
