@@ -360,7 +360,13 @@ def summary_block(line: dict) -> dict:
         "serving": {"p50_ms": g("serving", "p50_ms"), "p99_ms": g("serving", "p99_ms"),
                     "one_at_a_time_p50_ms": g("serving", "one_at_a_time_p50_ms"),
                     "one_at_a_time_p99_ms": g("serving", "one_at_a_time_p99_ms"),
-                    "max_batch_requests": g("serving", "max_batch_requests")},
+                    "large_p99_ms": g("serving", "p99_by_class", "20ms_and_above", "p99_ms"),
+                    "large_one_at_a_time_p99_ms": g("serving", "p99_by_class", "20ms_and_above", "one_at_a_time_p99_ms"),
+                    "small_p99_ms": g("serving", "p99_by_class", "below_20ms", "p99_ms"),
+                    "small_one_at_a_time_p99_ms": g("serving", "p99_by_class", "below_20ms", "one_at_a_time_p99_ms"),
+                    "max_batch_requests": g("serving", "max_batch_requests"),
+                    "burst_gain": g("serving", "burst", "throughput_gain"),
+                    "burst_max_batch_requests": g("serving", "burst", "max_batch_requests")},
         "e2e": g("e2e", "value"), "cpu_baseline": g("cpu_baseline", "value"),
     }
 
@@ -551,14 +557,18 @@ def bench_adjoint(wn, ctx, local, torch):
             "autograd_fit_step_ms": step_ms}
 
 
-def bench_serving(wn, ctx, local, torch, n_req=1000, n_templates=48, seed=17, policy=None):
+def bench_serving(wn, ctx, local, torch, n_req=1000, n_templates=48, seed=17, policy=None, n_burst=256,
+                  detail=None, extra_policies=((1, 0.0),)):
     """Seeded Poisson stream of predict/peel requests of uneven size (16-128 tiles, 1-14 steps, 32-384
     channels, 100-50,000 P/G, 0-3 shapelets with n_max 10-80), models resident.  Requests are drawn
     uniformly from n_templates distinct (observation, sky, data) sets; the arrival rate is set for ~70%
-    GPU busy from the measured one-at-a-time service times.  The one-at-a-time reference is a FIFO in
-    front of single-request calls, played with the measured service time of each request alone.
-    policy: (large requests in flight, wait limit in s) for Server.set_policy; None keeps the defaults."""
-    from paper_2005_09316_b300.serve import Server, latency_summary, poisson_arrivals, run_stream
+    GPU busy from the measured one-at-a-time service times.  The one-at-a-time reference is measured: the
+    same requests at the same arrival times run one after another through the single-request calls.  A
+    burst phase submits n_burst requests of the sets that take under 5 ms alone at once, so that batches
+    of several requests form, and compares the wall time with the same burst run one at a time.
+    policy: (large requests in flight, wait limit in s) for Server.set_policy; None keeps the defaults.
+    extra_policies: further policies the same stream is played under (latencies only)."""
+    from paper_2005_09316_b300.serve import Server, latency_summary, poisson_arrivals, run_sequential, run_stream
     rng = np.random.default_rng(seed)
     temps, models = [], []
     for i in range(n_templates):
@@ -580,7 +590,7 @@ def bench_serving(wn, ctx, local, torch, n_req=1000, n_templates=48, seed=17, po
             data = torch.randn((n_time, obs.n_base, n_chan), dtype=torch.complex64, device=f"cuda:{local}",
                                generator=torch.Generator(device=f"cuda:{local}").manual_seed(i))
         temps.append((d, m, gains, data))
-    # one-at-a-time service time of each template (each alone, synchronously; median of 3)
+    # one-at-a-time service time of each template (each alone, synchronously; median of 3), for the rate
     svc_t = []
     for d, m, gains, data in temps:
         ts = []
@@ -593,46 +603,91 @@ def bench_serving(wn, ctx, local, torch, n_req=1000, n_templates=48, seed=17, po
         svc_t.append(float(np.median(ts)))
     pick = np.random.default_rng(seed + 1).integers(0, n_templates, size=n_req)
     reqs = [temps[k] for k in pick]
-    svc = [svc_t[k] for k in pick]
+    svc = np.array([svc_t[k] for k in pick])
     mean_s = float(np.mean(svc))
     rate = 0.7 / mean_s
     arrivals = poisson_arrivals(np.random.default_rng(seed), rate, n_req)
-    lat_serial, t_free = [], 0.0
-    for a, s_ in zip(arrivals, svc):
-        start = max(a, t_free)
-        t_free = start + s_
-        lat_serial.append(t_free - a)
     max_rows = max(r[0].n_rows for r in temps)
-    srv = Server(ctx, n_streams=6, pool_bytes=6 << 30, max_inflight=32, max_rows=max_rows, max_chan=384)
-    if policy is not None:
-        srv.set_policy(*policy)
+
+    def server():
+        srv = Server(ctx, n_streams=6, pool_bytes=6 << 30, max_inflight=32, max_rows=max_rows, max_chan=384)
+        if policy is not None:
+            srv.set_policy(*policy)
+        return srv
+
+    srv = server()
     results, wall = run_stream(srv, reqs, arrivals)
     st = srv.stats()
     srv.close()
-    for m in models:
-        m.free()
+    lat_seq, svc_seq, wall_seq = run_sequential(ctx, reqs, arrivals)
+    seq_a = np.array(lat_seq)
+
+    def classes(res):
+        lat_a = np.array([r.latency for r in res])
+        out = {}
+        for name, sel in (("below_20ms", svc < 0.02), ("20ms_and_above", svc >= 0.02)):
+            out[name] = {"n": int(sel.sum()), "p50_ms": round(1e3 * float(np.percentile(lat_a[sel], 50)), 3),
+                         "p99_ms": round(1e3 * float(np.percentile(lat_a[sel], 99)), 3),
+                         "one_at_a_time_p50_ms": round(1e3 * float(np.percentile(seq_a[sel], 50)), 3),
+                         "one_at_a_time_p99_ms": round(1e3 * float(np.percentile(seq_a[sel], 99)), 3)}
+        return out
+
+    # the same stream under the other admission order of large requests (arrival order, one at a time)
+    others = []
+    for pol in extra_policies:
+        srv = server()
+        srv.set_policy(*pol)
+        res_p, _ = run_stream(srv, reqs, arrivals)
+        st_p = srv.stats()
+        srv.close()
+        lat_p = latency_summary(res_p)
+        others.append({"max_large_inflight": pol[0], "max_large_wait_s": pol[1], "p50_ms": round(lat_p["p50_ms"], 3),
+                       "p99_ms": round(lat_p["p99_ms"], 3), "p99_by_class": classes(res_p),
+                       "max_batch_requests": st_p["max_batch_requests"]})
+    if detail is not None:  # per request: (template, service alone, server result, one-at-a-time latency)
+        detail.extend(zip(pick.tolist(), svc.tolist(), results, lat_seq))
     total_evals = sum(r[0].n_vis * r[1].n_comp for r in reqs)
     lat = latency_summary(results)
-    # p99 by request class (service time alone below / at or above 20 ms): large requests start least
-    # work first, which shortens the wait of all but the largest and lengthens theirs
-    svc_a, lat_a, ser_a = np.array(svc), np.array([r.latency for r in results]), np.array(lat_serial)
-    by_class = {}
-    for name, sel in (("below_20ms", svc_a < 0.02), ("20ms_and_above", svc_a >= 0.02)):
-        by_class[name] = {"n": int(sel.sum()), "p99_ms": round(1e3 * float(np.percentile(lat_a[sel], 99)), 3),
-                          "one_at_a_time_p99_ms": round(1e3 * float(np.percentile(ser_a[sel], 99)), 3)}
+    # p99 by request class (service time alone below / at or above 20 ms), each against the measured
+    # one-at-a-time run of the same stream
+    by_class = classes(results)
+    # burst: n_burst requests of the sets under 5 ms alone, at once
+    small = [k for k in range(n_templates) if svc_t[k] < 0.005]
+    bpick = np.random.default_rng(seed + 2).choice(small, size=n_burst)
+    breqs = [temps[k] for k in bpick]
+    bzero = np.zeros(n_burst)
+    srv = server()
+    bres, bwall = run_stream(srv, breqs, bzero)
+    bst = srv.stats()
+    srv.close()
+    _, _, bwall_seq = run_sequential(ctx, breqs, bzero)
+    bevals = sum(r[0].n_vis * r[1].n_comp for r in breqs)
+    blat = latency_summary(bres)
+    for m in models:
+        m.free()
     return {"workload": f"serving: {n_req} Poisson requests drawn from {n_templates} uneven request sets "
                         "(16-128 tiles, 1-14 steps, 32-384 ch, 100-50000 P/G + 0-3 shapelets n_max 10-80)",
             "policy": {"max_large_inflight": (policy or (1, 1.0))[0], "max_large_wait_s": (policy or (1, 1.0))[1]},
             "rate_hz": round(rate, 2), "mean_service_ms": round(1e3 * mean_s, 3),
             "p50_ms": round(lat["p50_ms"], 3), "p99_ms": round(lat["p99_ms"], 3),
-            "one_at_a_time_p50_ms": round(1e3 * float(np.percentile(lat_serial, 50)), 3),
-            "one_at_a_time_p99_ms": round(1e3 * float(np.percentile(lat_serial, 99)), 3),
+            "one_at_a_time_p50_ms": round(1e3 * float(np.percentile(lat_seq, 50)), 3),
+            "one_at_a_time_p99_ms": round(1e3 * float(np.percentile(lat_seq, 99)), 3),
+            "one_at_a_time": "measured: the same stream run one request at a time through predict / peel",
             "p99_by_class": by_class,
-            "service_alone_p50_ms": round(1e3 * float(np.percentile(svc, 50)), 3),
-            "service_alone_p99_ms": round(1e3 * float(np.percentile(svc, 99)), 3),
+            "other_policies": others,
+            "service_alone_p50_ms": round(1e3 * float(np.percentile(svc_seq, 50)), 3),
+            "service_alone_p99_ms": round(1e3 * float(np.percentile(svc_seq, 99)), 3),
             "throughput_evals_per_s": total_evals / wall, "wall_s": round(wall, 3),
+            "one_at_a_time_throughput_evals_per_s": total_evals / wall_seq,
             "batches": st["batches"], "max_batches_in_flight": st["max_batches_in_flight"],
-            "max_batch_requests": st["max_batch_requests"]}
+            "max_batch_requests": st["max_batch_requests"],
+            "burst": {"requests": n_burst, "sets": "the request sets under 5 ms alone, all submitted at once",
+                      "wall_s": round(bwall, 4), "one_at_a_time_wall_s": round(bwall_seq, 4),
+                      "throughput_evals_per_s": bevals / bwall, "one_at_a_time_throughput_evals_per_s": bevals / bwall_seq,
+                      "throughput_gain": round(bwall_seq / bwall, 3), "p50_ms": round(blat["p50_ms"], 3),
+                      "p99_ms": round(blat["p99_ms"], 3), "batches": bst["batches"],
+                      "max_batch_requests": bst["max_batch_requests"],
+                      "max_batches_in_flight": bst["max_batches_in_flight"]}}
 
 
 def run_case(case: str):

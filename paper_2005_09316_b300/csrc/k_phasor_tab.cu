@@ -439,10 +439,10 @@ static double ks_cost(long rows, int F, int log2L, int K) {
   return (double)ctas * (double)rpc * ((double)cb * (1.0 + 1.3 / K) + 12.0);
 }
 
-int launch_phasor_table(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, int mode, const PeelArgs& pa,
-                        cudaStream_t st) {
-  if (M->n_point + M->n_gauss == 0) return launch_phasor_mixed(ctx, o, M, out, mode, pa, st);
-  int log2L = 5, K = 12;
+// Launch shape (L = 2^log2L lanes per row pair, K channels per lane) of the cheapest estimated cost.
+static void ks_choose(const ObsDev& o, int& log2L, int& K) {
+  log2L = 5;
+  K = 12;
   double best = -1.0;
   for (int li = 5; li >= 3; --li)
     for (int kk : {12, 8, 4}) {
@@ -453,6 +453,44 @@ int launch_phasor_table(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* ou
         K = kk;
       }
     }
+}
+
+size_t phasor_table_spec_bytes(const ObsDev& o, const Model* M) {
+  int log2L, K;
+  ks_choose(o, log2L, K);
+  const int cb = K << log2L, n_cb = (o.n_chan + cb - 1) / cb;
+  const long long n_grp = (M->n_point + KS_GC - 1) / KS_GC + (M->n_gauss + KS_GC - 1) / KS_GC;
+  return (size_t)n_cb * n_grp * KS_GC * cb * sizeof(float);
+}
+
+int launch_phasor_table(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, int mode, const PeelArgs& pa,
+                        cudaStream_t st) {
+  if (M->n_point + M->n_gauss == 0) return launch_phasor_mixed(ctx, o, M, out, mode, pa, st);
+  // the spectrum table, in the context's grow-only workspace
+  const size_t bytes = phasor_table_spec_bytes(o, M);
+  if (ctx->ws_spec_bytes < bytes) {
+    if (ctx->ws_spec) {
+      cudaStreamSynchronize(st);
+      cudaFree(ctx->ws_spec);
+      ctx->ws_spec = nullptr;
+      ctx->ws_spec_bytes = 0;
+    }
+    cudaError_t e = dev_malloc(&ctx->ws_spec, bytes);
+    if (e != cudaSuccess) return set_error(WN_ENOMEM, std::string("spectrum table workspace: ") + cudaGetErrorString(e));
+    ctx->ws_spec_bytes = bytes;
+  }
+  KsWork w;
+  w.spec = ctx->ws_spec;
+  w.spec_bytes = ctx->ws_spec_bytes;
+  w.part = ctx->k1_part;
+  return launch_phasor_table_ws(ctx, o, M, out, mode, pa, w, st);
+}
+
+int launch_phasor_table_ws(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, int mode, const PeelArgs& pa,
+                           KsWork& w, cudaStream_t st) {
+  if (M->n_point + M->n_gauss == 0) return launch_phasor_mixed(ctx, o, M, out, mode, pa, st);
+  int log2L, K;
+  ks_choose(o, log2L, K);
   KSArgs A;
   K1Args& a = A.k;
   a.uvw = o.uvw;
@@ -482,23 +520,17 @@ int launch_phasor_table(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* ou
   const long n_cta = (long)a.grid_x * n_cb;
   if (n_cta > INT_MAX / 2) return set_error(WN_EINVAL, "observation too large for one phasor launch");
 
-  // the spectrum table, in the context's grow-only workspace
+  // the spectrum table: built here unless w already holds this model's table for this channel block
   const long long n_entries = (long long)n_cb * A.n_grp * KS_GC * cb;
   const size_t bytes = (size_t)n_entries * sizeof(float);
-  if (ctx->ws_spec_bytes < bytes) {
-    if (ctx->ws_spec) {
-      cudaStreamSynchronize(st);
-      cudaFree(ctx->ws_spec);
-      ctx->ws_spec = nullptr;
-      ctx->ws_spec_bytes = 0;
-    }
-    cudaError_t e = dev_malloc(&ctx->ws_spec, bytes);
-    if (e != cudaSuccess) return set_error(WN_ENOMEM, std::string("spectrum table workspace: ") + cudaGetErrorString(e));
-    ctx->ws_spec_bytes = bytes;
+  if (!w.spec || w.spec_bytes < bytes) return set_error(WN_EINVAL, "spectrum table workspace too small");
+  A.spec = w.spec;
+  if (!(w.spec_model == M && w.spec_cb == cb)) {
+    ks_spectrum<<<(unsigned)((n_entries + 255) / 256), 256, 0, st>>>(M->pg, M->n_point, M->n_gauss, A.n_grp_pt, A.n_grp,
+                                                                    o.freq, o.n_chan, o.nu0, cb, n_entries, w.spec);
+    w.spec_model = M;
+    w.spec_cb = cb;
   }
-  A.spec = ctx->ws_spec;
-  ks_spectrum<<<(unsigned)((n_entries + 255) / 256), 256, 0, st>>>(M->pg, M->n_point, M->n_gauss, A.n_grp_pt, A.n_grp,
-                                                                  o.freq, o.n_chan, o.nu0, cb, n_entries, ctx->ws_spec);
 
   // tail split: the last n_cta mod slots tiles (one resident CTA per SM) are split into parts over
   // group ranges so that they fill the last wave
@@ -508,9 +540,9 @@ int launch_phasor_table(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* ou
   a.n_main = (int)n_cta;
   a.tail_parts = 1;
   a.tail_ct = A.n_grp;
-  a.part = ctx->k1_part;
+  a.part = w.part;
   int n_tail = 0;
-  if (rem > 0 && A.n_grp >= 2 && ctx->k1_part) {
+  if (rem > 0 && A.n_grp >= 2 && w.part) {
     const int parts = std::min(slots / rem, A.n_grp);
     if (parts >= 2) {
       a.tail_ct = (A.n_grp + parts - 1) / parts;

@@ -387,6 +387,19 @@ int launch_phasor_mixed(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* ou
                         cudaStream_t st);
 int launch_phasor_table(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, int mode, const PeelArgs& pa,
                         cudaStream_t st);
+// Workspace of a table-form launch: the spectrum table (spec_bytes of room) and the split tail's partial
+// sums (k1_part_bytes).  spec_model / spec_cb name the table spec holds (a launch for the same model and
+// channel block, e.g. the next time steps of one observation, reuses it; nullptr / 0: none).
+struct KsWork {
+  float* spec = nullptr;
+  size_t spec_bytes = 0;
+  float2* part = nullptr;
+  const Model* spec_model = nullptr;
+  int spec_cb = 0;
+};
+size_t phasor_table_spec_bytes(const ObsDev& o, const Model* M);
+int launch_phasor_table_ws(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, int mode, const PeelArgs& pa,
+                           KsWork& w, cudaStream_t st);
 int launch_phasor_fp64(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, int mode, const PeelArgs& pa,
                        bool include_shapelets, cudaStream_t st);
 int launch_peel_model(wn_ctx* ctx, const ObsDev& o, const PeelArgs& pa, const float2* model, float2* resid,

@@ -12,15 +12,17 @@
 //    admitted as memory and slots free up and go out in the next batch on a free stream, so their
 //    work overlaps the batches in flight;
 //  * time slicing: a batch carries at most ~kBatchBudget of estimated GPU work; a request larger than
-//    that takes a low-priority stream of its own and is issued there chunk by chunk (its shapelets with
-//    the last chunk), so small requests keep flowing on the other streams between its chunks.  Its
-//    point/Gaussian table is also cut into component ranges of at most ~kTileEvals evaluations per
-//    CTA tile (range 0 stores or peels, later ranges add or subtract on the same stream), so no CTA
-//    of a large request holds an SM for more than a few milliseconds;
+//    that takes the lowest-priority free stream and runs there in chunks of whole time steps (about
+//    kBatchBudget each and at least two waves of the phasor kernel, back to back) through the
+//    single-request kernels, the table-form phasor kernel
+//    and the shapelet kernel, with that stream's own workspaces: the same work the request does alone.
+//    While it runs, small requests go out one batch at a time on another stream, so the ones that
+//    arrive meanwhile are packed into the next batch;
 //  * completion: an event per batch, polled without blocking; the caller reads the result in place
 //    and releases it, which returns its pool space.
-// Every tile is computed by the same code in the same order as a single-request launch, so a request's
-// result does not depend on what it was batched with.
+// A batched tile is computed by the same code in the same order as a single-request launch of the
+// batched kernel's form, and a chunk of a large request by the single-request kernels on its rows, so
+// a request's result does not depend on what it was batched with.
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -36,25 +38,24 @@ enum ReqState { RQ_PENDING = 0, RQ_ADMITTED = 1, RQ_RUNNING = 2, RQ_DONE = 3, RQ
 
 constexpr double kBatchBudget = 0.02;   // seconds of estimated GPU work per batch / chunk
 // Large requests in flight at once.  They share the GPU with each other and with the small batches, so
-// more of them at once stretches every one of them.  One at a time, started least work first (below),
-// the queue of large requests drains fastest for all but the largest; the small ones keep the remaining
-// streams (measured on the serving bench: p99 372-495 ms with one, 492-536 ms with two, 600-620 ms
-// with two in arrival order).
+// more of them at once stretches every one of them.  Measured on the serving bench (1,000 requests at
+// 70 % load), p99 of the requests of 20 ms or more / of the others, against 0.48 s / 0.48 s one at a
+// time: one in flight started least work first with the 1 s wait limit, 0.95 s / 0.13 s; one in
+// arrival order, 0.59 s / 0.38 s; two in arrival order, 0.83 s / 0.51 s.
 constexpr int kMaxLargeInFlight = 1;  // default; wn_server_set_policy changes it per server
 // Large requests start in order of estimated work, least first, which keeps a burst of them from
 // holding back the many mid-sized ones behind the few largest; a request that has waited this long
 // since submission starts before any younger one, so the largest are passed over for a bounded time.
 constexpr double kMaxLargeWait = 1.0;  // seconds; default, as above
 constexpr double kEvalRate = 3.0e12;    // component-visibility evaluations per second (estimate)
-constexpr double kTileEvals = 2.4e7;    // evaluations per CTA tile of a large request (~2 ms on one CTA)
 
 struct ServeReq {
   uint64_t ticket = 0;
   K1Args k1;              // batched-kernel arguments (set at admission)
   int gx = 0, gy = 0;     // tile grid of the phasor kernel
-  long tiles = 0, issued = 0;  // tiles of one component range; work items issued (range-major)
-  int n_cc = 1, cc = 0;        // component ranges and components per range (large requests only)
-  double tile_cost = 0;        // estimated GPU seconds per tile of one component range
+  long tiles = 0, issued = 0;  // tiles of the batched kernel's grid; work issued (0: not started)
+  int t_next = 0;              // a large request's next time step to issue
+  double tile_cost = 0;        // estimated GPU seconds per tile
   int owner_slot = -1;    // slot that issues a large request's chunks
   ObsDev od;
   const Model* M = nullptr;
@@ -80,8 +81,7 @@ struct ServeSlot {
   bool busy = false;
   int priority = 0;                // CUDA stream priority (lower number runs first)
   uint64_t owner = 0;              // large request whose chunks this slot issues (0: none)
-  bool chunk_next = true;          // an owning slot's next launch: a chunk (else a small batch)
-  bool shapes = false;             // the launch in flight carries shapelet kernels
+  KsWork ks;                       // table-form workspaces of the large requests this slot runs
 };
 
 }  // namespace wn
@@ -154,6 +154,8 @@ constexpr int kSlotRowTables = 4;
 
 static bool has_pg(const ServeReq& r) { return r.M->n_point + r.M->n_gauss > 0 || r.M->n_shape == 0; }
 
+static void finish_launch(wn_server* s, int k, const std::vector<uint64_t>& complete, cudaError_t e);
+
 // Launch on slot k the work table in the slot's pinned staging (nwork entries), the shapelets of the
 // requests in `shapes`, and the completion event that completes the requests in `complete`.  Called
 // with the lock held.
@@ -171,9 +173,15 @@ static void launch_slot(wn_server* s, int k, int nwork, const std::vector<uint64
       r.error = WN_ECUDA;
     }
   }
+  finish_launch(s, k, complete, e);
+}
+
+// The completion event of slot k's launch, which completes the requests in `complete`.  Called with
+// the lock held.
+static void finish_launch(wn_server* s, int k, const std::vector<uint64_t>& complete, cudaError_t e) {
+  ServeSlot& sl = s->slots[k];
   if (e == cudaSuccess) e = cudaEventRecord(sl.done, sl.st);
   sl.reqs = complete;
-  sl.shapes = !shapes.empty();
   if (e != cudaSuccess)
     for (uint64_t t : sl.reqs) {
       s->reqs[t].state = RQ_FAILED;
@@ -194,22 +202,8 @@ static int add_tiles(ServeReq& r, int slot_req, long from, long to, K1Work* work
   return nwork;
 }
 
-static double large_cost(const ServeReq& r) { return r.tile_cost * r.tiles * r.n_cc; }
+static double large_cost(const ServeReq& r) { return r.tile_cost * r.tiles; }
 static bool is_large(const ServeReq& r) { return r.tiles > 0 && large_cost(r) > kBatchBudget; }
-
-// Kernel arguments of component range c of a request: the point/Gaussian table is points then
-// Gaussians, so a range is a contiguous slice with its own point / Gaussian counts.
-static K1Args range_args(const ServeReq& r, int c) {
-  K1Args a = r.k1;
-  if (r.n_cc <= 1) return a;
-  const int n_pg = r.k1.n_point + r.k1.n_gauss;
-  const int c0 = c * r.cc, c1 = std::min(n_pg, c0 + r.cc);
-  a.comps = r.k1.comps + c0;
-  a.n_point = std::max(0, std::min(r.k1.n_point, c1) - c0);
-  a.n_gauss = (c1 - c0) - a.n_point;
-  if (c > 0) a.mode = r.mode == OUT_PEEL ? OUT_SUBG : OUT_ACCUM;
-  return a;
-}
 
 // An admitted request that no launch has taken yet.
 static bool unstarted(const ServeReq& r) { return r.state == RQ_ADMITTED && r.issued == 0 && r.owner_slot < 0; }
@@ -225,28 +219,63 @@ static K1Work* slot_work(wn_server* s, ServeSlot& sl) {
   return reinterpret_cast<K1Work*>(sl.h_table + 16 + sizeof(K1Args) * s->max_reqs);
 }
 
-// Launch on slot k the next ~kBatchBudget of tiles of the large request the slot owns; the last chunk
-// carries the request's shapelets and completes it.  Called with the lock held.
+// Launch on slot k the next chunk of the large request the slot owns: its next time steps (about
+// kBatchBudget of estimated work) as one observation through the single-request kernels, the
+// table-form phasor kernel with the slot's workspaces and then the shapelet kernel with the slot's
+// tables.  Chunks cover disjoint rows, so each applies the request's mode.  The last chunk completes the
+// request.  Called with the lock held; the slot is idle.
 static void launch_chunk(wn_server* s, int k) {
   ServeSlot& sl = s->slots[k];
   ServeReq& r = s->reqs[sl.owner];
-  std::vector<uint64_t> complete, shapes;
-  const long per = std::max(1L, std::min((long)s->max_work, (long)(kBatchBudget / std::max(r.tile_cost, 1e-12))));
-  // one component range per launch: two ranges of a tile must not run at once (they add to it in turn)
-  const int c = (int)(r.issued / r.tiles);
-  const long from = r.issued % r.tiles, to = std::min(r.tiles, from + per);
-  slot_args(s, sl)[0] = range_args(r, c);
-  const int nwork = add_tiles(r, 0, from, to, slot_work(s, sl), 0);
-  r.issued += to - from;
-  if (r.issued == r.tiles * r.n_cc) {
-    r.state = RQ_RUNNING;
+  std::vector<uint64_t> complete;
+  const int T = r.od.n_time, B = r.od.n_base, F = r.od.n_chan;
+  // about kBatchBudget of estimated work, and at least two waves of the phasor kernel's row tiles (32 rows,
+  // one CTA per SM) so that a chunk fills the GPU
+  const double per_step = large_cost(r) / T;
+  const int min_steps = (2 * 32 * s->ctx->num_sms + B - 1) / B;
+  const int steps = std::max(1, std::min(T - r.t_next, std::max(min_steps, (int)(kBatchBudget / std::max(per_step, 1e-12)))));
+  const int t0 = r.t_next;
+  ObsDev o = r.od;
+  o.n_time = steps;
+  o.n_rows = steps * B;
+  o.uvw = r.od.uvw + (size_t)3 * t0 * B;
+  float2* out = reinterpret_cast<float2*>(s->pool + r.off) + (size_t)t0 * B * F;
+  PeelArgs pa = r.pa;
+  if (r.mode == OUT_PEEL) {
+    pa.data = r.pa.data + (size_t)t0 * B * F;
+    if (r.pa.gt > 1) pa.gains = r.pa.gains + (size_t)t0 * r.pa.gf * r.pa.n_ant;  // per-step gains
+  }
+  int rc = WN_OK;
+  cudaError_t e = cudaSuccess;
+  // the spectrum table depends on the observation's channels too: a request's first chunk builds it
+  if (t0 == 0) sl.ks.spec_model = nullptr;
+  const size_t need = phasor_table_spec_bytes(o, r.M);
+  if (sl.ks.spec_bytes < need) {  // grow-only; the slot's stream is idle
+    cudaFree(sl.ks.spec);
+    sl.ks = KsWork{nullptr, 0, sl.ks.part, nullptr, 0};
+    e = dev_malloc(&sl.ks.spec, need);
+    if (e == cudaSuccess) sl.ks.spec_bytes = need;
+  }
+  if (e == cudaSuccess && !sl.ks.part) e = dev_malloc(&sl.ks.part, k1_part_bytes(s->ctx->num_sms));
+  if (e != cudaSuccess) rc = set_error(WN_ENOMEM, std::string("serving workspace: ") + cudaGetErrorString(e));
+  if (rc == WN_OK) rc = launch_phasor_table_ws(s->ctx, o, r.M, out, r.mode, pa, sl.ks, sl.st);
+  if (rc == WN_OK && r.M->n_shape > 0)
+    rc = launch_shapelets_ws(s->ctx, o, r.M, out, r.mode == OUT_PEEL ? OUT_SUBG : OUT_ACCUM, pa, sl.chaninfo, sl.rowinfo,
+                             (size_t)kSlotRowTables * s->max_rows, sl.st);
+  r.issued = 1;
+  r.t_next = t0 + steps;
+  if (rc != WN_OK) {
+    r.state = RQ_FAILED;
+    r.error = rc;
+  }
+  if (r.t_next == T || rc != WN_OK) {
+    if (rc == WN_OK) r.state = RQ_RUNNING;
     r.batch = s->batches;
     r.owner_slot = -1;
     sl.owner = 0;
     complete.push_back(r.ticket);
-    if (r.M->n_shape > 0) shapes.push_back(r.ticket);
   }
-  launch_slot(s, k, nwork, complete, shapes);
+  finish_launch(s, k, complete, cudaSuccess);
 }
 
 // Launch on slot k one batch of small unstarted requests, in ticket order, up to kBatchBudget of
@@ -279,11 +308,9 @@ static void launch_small(wn_server* s, int k) {
   if (!complete.empty()) launch_slot(s, k, nwork, complete, shapes);
 }
 
-// Fill the free slots.  Large requests claim the lowest-priority free slots (at most kMaxLargeInFlight,
-// and never the last free one, so small requests always have a stream); small batches take the highest-priority free ones; a slot that owns a
-// large request alternates between its chunks and small batches while small requests wait.  While a
-// launch with shapelet kernels is on the GPU no new chunk starts: the shapelet kernel needs a whole SM,
-// which the phasor CTAs of back-to-back chunks would otherwise never leave free.
+// Fill the free slots.  Large requests claim the lowest-priority free slots (at most max_large_inflight,
+// and never the last free one, so small requests always have a stream) and issue their chunks back to
+// back; small batches take the other free slots, one batch at a time while a large request runs.
 static bool launch_ready(wn_server* s) {
   bool progress = false;
   const int ns = (int)s->slots.size();
@@ -312,28 +339,24 @@ static bool launch_ready(wn_server* s) {
     r.owner_slot = k;
     r.t_launch = now_s(s);
     s->slots[k].owner = r.ticket;
-    s->slots[k].chunk_next = true;
     ++owners;
   }
+  // while a large request runs, small batches go out one at a time (they keep batching while it runs)
+  int small_busy = 0;
+  for (auto& sl : s->slots) small_busy += (sl.busy && !sl.owner) ? 1 : 0;
+
   for (int k = 0; k < ns; ++k) {
     ServeSlot& sl = s->slots[k];
     if (sl.busy || sl.owner || !small_waiting(s)) continue;
+    if (owners > 0 && small_busy >= 1) break;
     launch_small(s, k);
+    ++small_busy;
     progress = true;
   }
-  bool shapes_waiting = false;
-  for (auto& sl : s->slots) shapes_waiting |= sl.busy && sl.shapes;
   for (int k = 0; k < ns; ++k) {
     ServeSlot& sl = s->slots[k];
     if (sl.busy || !sl.owner) continue;
-    if (shapes_waiting && (sl.chunk_next || !small_waiting(s))) continue;
-    if (!sl.chunk_next && small_waiting(s)) {
-      launch_small(s, k);
-      sl.chunk_next = true;
-    } else {
-      launch_chunk(s, k);
-      sl.chunk_next = false;
-    }
+    launch_chunk(s, k);
     progress = true;
   }
   return progress;
@@ -385,17 +408,7 @@ static void scheduler(wn_server* s) {
             r.tiles = (long)r.gx * r.gy;
             const double rows_tile = (double)r.od.n_rows / r.gx, chans_tile = (double)r.od.n_chan / r.gy;
             const int n_pg = r.M->n_point + r.M->n_gauss;
-            r.n_cc = 1;
-            r.cc = n_pg;
-            if (rows_tile * chans_tile * n_pg * r.tiles / kEvalRate > kBatchBudget) {
-              // large: component ranges of whole 32-component TMA stages, at most kTileEvals per tile
-              const int cc = std::max(1024, (int)(kTileEvals / (rows_tile * chans_tile)) & ~31);
-              if (cc < n_pg) {
-                r.cc = cc;
-                r.n_cc = (n_pg + cc - 1) / cc;
-              }
-            }
-            r.tile_cost = rows_tile * chans_tile * r.cc / kEvalRate;
+            r.tile_cost = rows_tile * chans_tile * n_pg / kEvalRate;
           }
         }
         r.t_admit = now_s(s);
@@ -479,6 +492,8 @@ int wn_server_create(wn_ctx* ctx, int n_streams, size_t pool_bytes, int max_infl
       cudaFree(sl.d_table);
       if (sl.h_table) cudaFreeHost(sl.h_table);
       cudaFree(sl.chaninfo);
+      cudaFree(sl.ks.spec);
+      cudaFree(sl.ks.part);
     }
     cudaFree(s->pool);
     delete s;
@@ -506,6 +521,8 @@ void wn_server_destroy(wn_server* s) {
     cudaFree(sl.d_table);
     cudaFreeHost(sl.h_table);
     cudaFree(sl.chaninfo);
+    cudaFree(sl.ks.spec);
+    cudaFree(sl.ks.part);
   }
   cudaFree(s->pool);
   delete s;

@@ -182,3 +182,27 @@ def run_stream(server: Server, requests, arrivals, release=True, timeout=120.0):
     if errors:
         raise errors[0]
     return [results[i] for i in range(len(requests))], time.perf_counter() - t0
+
+
+def run_sequential(ctx: Context, requests, arrivals):
+    """The one-at-a-time reference, measured: the same requests at the same arrival times, each run alone
+    through the single-request calls (predict, or peel when the request carries data) and waited for
+    before the next starts, in arrival order.  Returns (latencies in s, service times in s, wall s)."""
+    import torch
+
+    lat, svc = [], []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for (obs, model, gains, data), ta in zip(requests, arrivals):
+        while time.perf_counter() - t0 < ta:
+            time.sleep(min(2e-4, max(0.0, ta - (time.perf_counter() - t0))))
+        ts = time.perf_counter()
+        if data is None:
+            ctx.predict(obs, model)
+        else:
+            ctx.peel(obs, model, gains, data)
+        torch.cuda.synchronize()
+        te = time.perf_counter()
+        svc.append(te - ts)
+        lat.append(te - t0 - ta)
+    return lat, svc, time.perf_counter() - t0

@@ -149,17 +149,18 @@ def test_cancel_and_bounded_wait(wn, ctx):
 
 
 @pytest.mark.parametrize("peel", [False, True])
-def test_large_request_in_component_ranges(wn, ctx, peel):
-    """A request above the batch work budget is served in time slices over row tiles and component
-    ranges (range 0 stores or peels, later ranges add or subtract); its result matches the single call."""
+def test_large_request_in_time_step_chunks(wn, ctx, peel):
+    """A request above the batch work budget is served in chunks of whole time steps through the
+    single-request kernels (each chunk applies the request's mode to its own rows, per-step data and
+    gains offset to them); its result matches the single call."""
     from paper_2005_09316_b300.serve import Server
-    obs = synth.make_obs(71, 128, 3, synth.uniform_channels(167e6, 80e3, 384), layout="mwa")
+    obs = synth.make_obs(71, 128, 5, synth.uniform_channels(167e6, 80e3, 384), layout="mwa")
     sky = synth.make_sky(72, 16000, 4000, 1, fov=15 * synth.DEG, shape_nmax=20)
     d = wn.obs_to_device(obs)
     m = ctx.upload(sky)
     gains = data = None
     if peel:
-        gains = torch.as_tensor(synth.make_gains(73, obs.n_ant).astype(np.complex64)).cuda()
+        gains = torch.as_tensor(synth.make_gains(73, obs.n_ant, obs.n_time, 1).astype(np.complex64)).cuda()
         data = torch.randn(obs.n_time, obs.n_base, obs.n_chan, dtype=torch.complex64, device="cuda",
                            generator=torch.Generator(device="cuda").manual_seed(74))
     srv = Server(ctx, n_streams=2, pool_bytes=1 << 30, max_inflight=4, max_rows=obs.n_rows, max_chan=384)
@@ -169,7 +170,7 @@ def test_large_request_in_component_ranges(wn, ctx, peel):
     srv.release(t)
     st = srv.stats()
     srv.close()
-    assert st["batches"] >= 4, st            # several launches: tile chunks of several component ranges
+    assert st["batches"] >= 3, st            # several launches: chunks of the time steps
     ref = solo(ctx, (d, m, gains, data))
     assert e_norm(got, ref) <= 1e-5
     assert ctx.device_errors() == 0
@@ -308,10 +309,10 @@ def test_mixed_stream_matches_oracle(wn, ctx):
 
 
 @pytest.mark.parametrize("peel", [False, True])
-def test_large_request_in_component_ranges_matches_oracle(wn, ctx, peel):
+def test_large_request_in_time_step_chunks_matches_oracle(wn, ctx, peel):
     """A request above the batch work budget (128 tiles x 3 steps x 384 ch, 16,000 P + 4,000 G + one
-    n_max 20 shapelet), served in slices over row tiles and component ranges, with five small requests
-    submitted behind it: every result equals the oracle's on sampled rows."""
+    n_max 20 shapelet), served in chunks of time steps, with five small requests submitted behind it:
+    every result equals the oracle's on sampled rows."""
     from paper_2005_09316_b300.serve import Server
     big = _host_request(wn, ctx, 71, 128, 3, 384, 20000, [20], peel)
     small = [_host_request(wn, ctx, 700 + 10 * i, 24, 2, 64, 400, [8] if i == 2 else [], peel=bool(i % 2))
@@ -321,7 +322,7 @@ def test_large_request_in_component_ranges_matches_oracle(wn, ctx, peel):
     for t in tickets:
         assert srv.wait(t, 120).state == 3
     st = srv.stats()
-    assert st["batches"] >= 4, st            # the large request ran in several launches
+    assert st["batches"] >= 3, st            # the large request ran in several launches
     _check_against_oracle(srv, tickets[0], big, n_rows=10, seed=1)
     for i, (t, r) in enumerate(zip(tickets[1:], small)):
         _check_against_oracle(srv, t, r, seed=2 + i)
