@@ -243,11 +243,13 @@ WN_API int wn_predict_grad(wn_ctx* ctx, const wn_obs* obs, int model_id, const v
 
 /* ---- continuous-batching server (requests of uneven size) ------------------------------------ */
 
-/* A scheduler thread admits predict / peel requests by memory, packs the tiles of every admitted
- * request into one batch run by a persistent phasor kernel replayed from a CUDA graph (shapelets
+/* A scheduler thread admits predict / peel requests by memory, packs the tiles of admitted small
+ * requests into one batch run by a persistent phasor kernel replayed from a CUDA graph (shapelets
  * follow per request on the same stream), and keeps up to n_streams batches on the GPU, so requests
  * that arrive while others run are admitted as slots and pool memory free up and their work overlaps.
- * Results do not depend on the batch a request ran in (same tiles, same order). */
+ * A request above one batch's work budget runs on a stream of its own in chunks of whole time steps
+ * through the single-request kernels, with that stream's own workspaces.  Results do not depend on the
+ * batch a request ran in (same tiles, same order). */
 typedef struct wn_server wn_server;
 
 /* Request states reported by wn_server_poll. */
@@ -260,8 +262,10 @@ typedef struct wn_server wn_server;
 
 /* Create a server on ctx: n_streams batch slots (1..16), a device pool of pool_bytes for the requests'
  * outputs, at most max_inflight admitted requests, observations of at most max_rows (T*B) rows and
- * max_chan channels.  Allocates the pool, per-stream tables and pinned staging, and captures one
- * graph per stream.  Resident models must not be freed while requests that use them are unreleased. */
+ * max_chan channels.  Allocates the pool, per-stream tables (room for four shapelets' row tables) and
+ * pinned staging, and captures one graph per stream; a stream that runs a large request allocates its
+ * spectrum table (grown to the largest request it runs) and tail-sum workspace on first use.  Resident
+ * models must not be freed while requests that use them are unreleased. */
 WN_API int wn_server_create(wn_ctx* ctx, int n_streams, size_t pool_bytes, int max_inflight, int max_rows,
                             int max_chan, wn_server** out);
 /* Stop the scheduler and free everything the server owns (waits for batches on the GPU). */
