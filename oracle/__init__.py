@@ -59,6 +59,8 @@ def lib():
             _lib.or_hermite.argtypes = [i, d, P]
             _lib.or_shapelet_frame.restype = None
             _lib.or_shapelet_frame.argtypes = [d, d, d, P]
+            _lib.or_shapelet_frame_grad.restype = None
+            _lib.or_shapelet_frame_grad.argtypes = [d, d, d, P, P]
             _lib.or_max_threads.restype = i
             _lib.or_predict.restype = None
             _lib.or_predict.argtypes = [i, P, i, P, d, i, i, i] + [P] * 16 + [P, i]
@@ -107,6 +109,14 @@ def shapelet_frame(l: float, m: float, dec0: float) -> np.ndarray:
     out = np.zeros(9)
     lib().or_shapelet_frame(float(l), float(m), float(dec0), _p(out))
     return out.reshape(3, 3)
+
+
+def shapelet_frame_grad(l: float, m: float, dec0: float):
+    """(dF/dl, dF/dm) of shapelet_frame, 3 x 3 each, by the chain rule through the centre's declination
+    and right ascension (the frame follows the shapelet's position)."""
+    fl, fm = np.zeros(9), np.zeros(9)
+    lib().or_shapelet_frame_grad(float(l), float(m), float(dec0), _p(fl), _p(fm))
+    return fl.reshape(3, 3), fm.reshape(3, 3)
 
 
 class _SkyArgs:

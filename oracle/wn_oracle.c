@@ -96,6 +96,23 @@ static void or_uvw_rotation(double h, double dec, double r[9])
     r[6] = cd * ch;   r[7] = -cd * sh;  r[8] = sd;
 }
 
+/* Derivatives of R(H, dec) with respect to H and to dec (differentiating or_uvw_rotation entry by entry). */
+static void or_uvw_rotation_dh(double h, double dec, double r[9])
+{
+    double sh = sin(h), ch = cos(h), sd = sin(dec), cd = cos(dec);
+    r[0] = ch;        r[1] = -sh;       r[2] = 0.0;
+    r[3] = sd * sh;   r[4] = sd * ch;   r[5] = 0.0;
+    r[6] = -cd * sh;  r[7] = -cd * ch;  r[8] = 0.0;
+}
+
+static void or_uvw_rotation_ddec(double h, double dec, double r[9])
+{
+    double sh = sin(h), ch = cos(h), sd = sin(dec), cd = cos(dec);
+    r[0] = 0.0;       r[1] = 0.0;       r[2] = 0.0;
+    r[3] = -cd * ch;  r[4] = cd * sh;   r[5] = -sd;
+    r[6] = -sd * ch;  r[7] = sd * sh;   r[8] = cd;
+}
+
 /* Frame that re-phases (u, v, w) from the phase centre (H0, dec0) to a shapelet centred at (l, m)
  * (Sec. 3.2, the u_{i,j}, v_{i,j} of eq:scale-shape-x/y).  The centre (RA_j, dec_j) follows from
  * (l, m) by inverting the orthographic projection: sin dec_j = m cos dec0 + n sin dec0,
@@ -114,6 +131,39 @@ void or_shapelet_frame(double l, double m, double dec0, double f[9])
             double s = 0.0;
             for (int k = 0; k < 3; ++k) s += rj[3 * a + k] * r0[3 * b + k];
             f[3 * a + b] = s;
+        }
+}
+
+/* Derivatives of that frame with respect to l and m.  The centre moves with (l, m): dec_j through
+ * sin dec_j = m cos dec0 + n sin dec0 and RA_j - RA_0 = atan2(l, X), X = n cos dec0 - m sin dec0,
+ * n = sqrt(1 - l^2 - m^2); with F = R(-dra, dec_j) R(0, dec0)^T the chain rule gives
+ * dF/dl = (-dR/dH d(dra)/dl + dR/ddec d(dec_j)/dl) R(0, dec0)^T, and likewise for m. */
+void or_shapelet_frame_grad(double l, double m, double dec0, double fl[9], double fm[9])
+{
+    double n = sqrt(1.0 - l * l - m * m);
+    double dn_dl = -l / n, dn_dm = -m / n;
+    double s = m * cos(dec0) + n * sin(dec0);
+    double dec_j = asin(s), c = sqrt(1.0 - s * s);
+    double ddec_dl = dn_dl * sin(dec0) / c, ddec_dm = (cos(dec0) + dn_dm * sin(dec0)) / c;
+    double X = n * cos(dec0) - m * sin(dec0);
+    double dX_dl = dn_dl * cos(dec0), dX_dm = dn_dm * cos(dec0) - sin(dec0);
+    double dra = atan2(l, X), den = X * X + l * l;
+    double ddra_dl = (X - l * dX_dl) / den, ddra_dm = -l * dX_dm / den;
+    double rh[9], rd[9], r0[9];
+    or_uvw_rotation_dh(-dra, dec_j, rh);
+    or_uvw_rotation_ddec(-dra, dec_j, rd);
+    or_uvw_rotation(0.0, dec0, r0);
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double sl = 0.0, sm = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                double gl = -rh[3 * a + k] * ddra_dl + rd[3 * a + k] * ddec_dl;
+                double gm = -rh[3 * a + k] * ddra_dm + rd[3 * a + k] * ddec_dm;
+                sl += gl * r0[3 * b + k];
+                sm += gm * r0[3 * b + k];
+            }
+            fl[3 * a + b] = sl;
+            fm[3 * a + b] = sm;
         }
 }
 
@@ -237,7 +287,9 @@ void or_peel(int n_rows, const int* row_t, const int* row_b, const int* ant1, co
  * The paper fits in image space and gives no derivatives; they follow from differentiating
  * eq:env_visi_def term by term:
  *   dV_j/dS_ref = V_j / S_ref;  dV_j/dalpha = ln(nu/nu_ref) V_j;
- *   dV_j/dl = -2 pi i (u - w l / n) V_j  (likewise m; the shapelet frame is held fixed);
+ *   dV_j/dl = -2 pi i (u - w l / n) V_j  (likewise m); for a shapelet also S P dxi/dl through its
+ *     re-phasing frame: dxi/dl = dxi/dx beta1 dkx/dl + dxi/dy beta2 dky/dl, with (dup/dl, dvp/dl) from
+ *     or_shapelet_frame_grad (eq:scale-shape-x/y take u, v in the shapelet's own frame);
  *   Gaussian: dxi/dmaj = -2E maj kx^2 xi, dxi/dmin = -2E min ky^2 xi, dxi/dpa = -2E (maj^2-min^2) kx ky xi;
  *   Shapelet: with x = beta1 kx, y = beta2 ky and phi_n' = sqrt(n/2) phi_{n-1} - sqrt((n+1)/2) phi_{n+1},
  *     dxi/dbeta1 = sum c s phi_n1'(x) kx phi_n2(y);  dxi/dbeta2 = sum c s phi_n1(x) phi_n2'(y) ky;
@@ -297,13 +349,15 @@ void or_grad(int n_rows, const double* uvw, int n_chan, const double* freq, doub
                         dx[q] = (q > 0 ? sqrt(q / 2.0) * px[q - 1] : 0.0) - sqrt((q + 1) / 2.0) * px[q + 1];
                         dy[q] = (q > 0 ? sqrt(q / 2.0) * py[q - 1] : 0.0) - sqrt((q + 1) / 2.0) * py[q + 1];
                     }
-                    double complex dxi_b1 = 0.0, dxi_b2 = 0.0, dxi_pa = 0.0;
+                    double complex dxi_b1 = 0.0, dxi_b2 = 0.0, dxi_pa = 0.0, dxi_x = 0.0, dxi_y = 0.0;
                     xi = 0.0;
                     double complex base = cw * S * P;
                     for (int q = s_off[s]; q < s_off[s + 1]; ++q) {
                         int a = s_n1[q], c2 = s_n2[q];
                         double complex ph = or_minus_i_pow(a + c2);
                         xi += s_c[q] * ph * px[a] * py[c2];
+                        dxi_x += s_c[q] * ph * dx[a] * py[c2];
+                        dxi_y += s_c[q] * ph * px[a] * dy[c2];
                         dxi_b1 += s_c[q] * ph * dx[a] * kx * py[c2];
                         dxi_b2 += s_c[q] * ph * px[a] * dy[c2] * ky;
                         dxi_pa += s_c[q] * ph * (dx[a] * b1 * ky * py[c2] - px[a] * dy[c2] * b2 * kx);
@@ -312,6 +366,15 @@ void or_grad(int n_rows, const double* uvw, int n_chan, const double* freq, doub
                     g_shape[3 * s + 0] += -2.0 * creal(base * dxi_b1);
                     g_shape[3 * s + 1] += -2.0 * creal(base * dxi_b2);
                     g_shape[3 * s + 2] += -2.0 * creal(base * dxi_pa);
+                    /* the position moves the frame: (up, vp) and so (x, y) depend on (l, m) */
+                    double Fl[9], Fm[9];
+                    or_shapelet_frame_grad(l[j], m[j], dec0, Fl, Fm);
+                    double dup_l = Fl[0] * u + Fl[1] * v + Fl[2] * w, dvp_l = Fl[3] * u + Fl[4] * v + Fl[5] * w;
+                    double dup_m = Fm[0] * u + Fm[1] * v + Fm[2] * w, dvp_m = Fm[3] * u + Fm[4] * v + Fm[5] * w;
+                    double dkx_l = K * (cos(pa) * dvp_l + sin(pa) * dup_l), dky_l = K * (-sin(pa) * dvp_l + cos(pa) * dup_l);
+                    double dkx_m = K * (cos(pa) * dvp_m + sin(pa) * dup_m), dky_m = K * (-sin(pa) * dvp_m + cos(pa) * dup_m);
+                    g_comp[4 * j + 2] += -2.0 * creal(base * (dxi_x * b1 * dkx_l + dxi_y * b2 * dky_l));
+                    g_comp[4 * j + 3] += -2.0 * creal(base * (dxi_x * b1 * dkx_m + dxi_y * b2 * dky_m));
                 }
                 double complex Vj = S * xi * P;
                 double complex t = cw * Vj;

@@ -27,6 +27,9 @@ MUTATIONS = {
                        "double K = OR_PI / sqrt(log(2.0));\n    double kx = K"),
     "gradient_l_sign": ("(u - w * l[j] / n)", "(u + w * l[j] / n)"),
     "n_minus_1": ("return -r2 / (1.0 + sqrt(1.0 - r2));", "return -r2 / (2.0);"),
+    "frame_derivative_dropped": ("g_comp[4 * j + 2] += -2.0 * creal(base * (dxi_x * b1 * dkx_l + dxi_y * b2 * dky_l));",
+                                 ";"),
+    "frame_derivative_ra_sign": ("double gl = -rh[3 * a + k] * ddra_dl", "double gl = rh[3 * a + k] * ddra_dl"),
 }
 
 

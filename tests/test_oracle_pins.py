@@ -378,9 +378,7 @@ def test_gradient_matches_central_finite_differences():
               ("g_pa", 1e-6), ("s_beta1", 1e-9), ("s_beta2", 1e-9), ("s_pa", 1e-6), ("s_coeff", 1e-6)]
     for name, h in checks:
         arr = getattr(sky, name)
-        for i in range(arr.size):
-            if name in ("l", "m") and i >= sky.n_point + sky.n_gauss:
-                continue  # shapelet position: the frame is held fixed in the analytic derivative
+        for i in range(arr.size):  # the shapelets' l and m too: their frame moves with them
             keep = arr[i]
             arr[i] = keep + h
             lp = _loss(obs, sky, rt, rb, gains, data)
@@ -443,3 +441,15 @@ def test_tf32_split_operand_pair():
     assert np.all(np.abs(both - f) <= 2.0 ** -21 * np.abs(f))
     only_hi = np.abs(hi.view(np.float32).astype(np.float64) - f)
     assert np.max(only_hi / np.maximum(np.abs(f), 1e-300)) > 2.0 ** -14    # hi alone is much coarser
+
+
+def test_shapelet_frame_derivative_matches_finite_differences():
+    """oracle.shapelet_frame_grad (chain rule through dec_j and RA_j) against central differences of
+    oracle.shapelet_frame itself, off-centre and near the pole of the frame, at several declinations."""
+    for l, m, dec0 in [(0.01, -0.02, -0.5), (0.2, 0.15, -1.1), (-0.3, 0.05, 0.3), (0.0, 0.0, -0.65), (0.05, 0.6, 0.1)]:
+        fl, fm = oracle.shapelet_frame_grad(l, m, dec0)
+        h = 1e-6
+        dl = (oracle.shapelet_frame(l + h, m, dec0) - oracle.shapelet_frame(l - h, m, dec0)) / (2 * h)
+        dm = (oracle.shapelet_frame(l, m + h, dec0) - oracle.shapelet_frame(l, m - h, dec0)) / (2 * h)
+        assert np.max(np.abs(fl - dl)) <= 1e-8, (l, m, dec0, np.max(np.abs(fl - dl)))
+        assert np.max(np.abs(fm - dm)) <= 1e-8, (l, m, dec0, np.max(np.abs(fm - dm)))
