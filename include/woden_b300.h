@@ -137,7 +137,7 @@ typedef struct {
 typedef struct {
     double* flux;      /* [n_comp] dL/dS_ref */
     double* alpha;     /* [n_comp] dL/dalpha */
-    double* l;         /* [n_comp] dL/dl (shapelets: re-phasing frame held fixed) */
+    double* l;         /* [n_comp] dL/dl (shapelets: including the re-phasing frame's motion) */
     double* m;         /* [n_comp] dL/dm */
     double* g_maj;     /* [n_gauss] */
     double* g_min;     /* [n_gauss] */

@@ -3,7 +3,8 @@
 // The paper fits in image space and gives no derivatives; they follow term by term from
 // eq:env_visi_def, eq:gauss-env and eq:shape-env (V_j = S_j xi_j e^{-2 pi i tau_j nu / c}):
 //   dV_j/dS_ref = V_j / S_ref,  dV_j/dalpha = ln(nu / nu_ref) V_j,
-//   dV_j/dl = -2 pi i (nu/c) (u - w l / n) V_j (likewise m; the shapelet re-phasing frame is held fixed),
+//   dV_j/dl = -2 pi i (nu/c) (u - w l / n) V_j (likewise m), plus for a shapelet S P (dxi/dx dx/dl +
+//             dxi/dy dy/dl): its (u', v') are re-phased to its own centre (Sec. 3.2), so x and y move with it,
 //   Gaussian: dxi/dmaj = -2E (nu/c)^2 maj kx^2 xi, dxi/dmin = -2E (nu/c)^2 min ky^2 xi,
 //             dxi/dpa = -2E (nu/c)^2 (maj^2 - min^2) kx ky xi   (kx, ky in metres, E = pi^2 / (4 ln 2)),
 //   Shapelet: x = beta1 kx, y = beta2 ky;  phi_n' = sqrt(n/2) phi_{n-1} - sqrt((n+1)/2) phi_{n+1};
@@ -432,6 +433,7 @@ struct K4SArgs {
   const double *flux, *beta1, *beta2;      // device scalars of this shapelet (raw FP64 tables)
   float c_amp, alpha;
   const float2* resid;
+  const float4* rowframe;  // per row: (dx/dl, dy/dl, dx/dm, dy/dm) / nu, the frame's share of the position gradient
   PeelArgs peel;
   double* part_s;   // [grid][K4S_NS]
   unsigned* err;
@@ -647,8 +649,10 @@ __global__ void __launch_bounds__(K4S_T) k4_grad_shape(const K4SArgs a) {
       const float u = __ldg(xu), v = __ldg(xu + 2), w = __ldg(xu + 4);
       acc32[0] += -2.0f * re_xi;
       acc32[1] += -2.0f * re_xi * fmaf(ci.z, 0.6931471805599453f, a.lnref_nu0_f);
-      acc32[2] += -4.0f * (float)kPi * nuc * (u - w * a.l_over_n) * im_xi;
-      acc32[3] += -4.0f * (float)kPi * nuc * (v - w * a.m_over_n) * im_xi;
+      // the position moves the phase centre of the term and the shapelet's re-phasing frame
+      const float4 rf = __ldg(a.rowframe + row);
+      acc32[2] += -4.0f * (float)kPi * nuc * (u - w * a.l_over_n) * im_xi - 2.0f * ci.w * (re_dx * rf.x + re_dy * rf.y);
+      acc32[3] += -4.0f * (float)kPi * nuc * (v - w * a.m_over_n) * im_xi - 2.0f * ci.w * (re_dx * rf.z + re_dy * rf.w);
       acc32[4] += -2.0f * re_dx * x * ib1;
       acc32[5] += -2.0f * re_dy * y * ib2;
       acc32[6] += -2.0f * (re_dx * rb * y - re_dy * rb2 * x);
@@ -753,6 +757,54 @@ __global__ void k4_loss_final(const double* part, int n, double* out) {
   if (lane == 0 && blockIdx.x == 0) *out = s;
 }
 
+// Derivatives of rows 0 and 1 of the re-phasing frame (shapelet_frame) with respect to the shapelet's l and
+// m.  The frame's entries are algebraic in (l, m): with n = sqrt(1 - l^2 - m^2), sin dec_j = m cos dec0 +
+// n sin dec0, y = n cos dec0 - m sin dec0, cos dec_j = sqrt(l^2 + y^2), sin H_j = -l / cos dec_j and
+// cos H_j = y / cos dec_j; each is differentiated in turn.  Zero when the centre sits on the frame's pole.
+__device__ void shapelet_frame_dlm(double l, double m, double sd0, double cd0, double Fl[6], double Fm[6]) {
+  const double n = sqrt(1.0 - l * l - m * m);
+  const double sdj = m * cd0 + n * sd0, y = n * cd0 - m * sd0;
+  const double cdj = sqrt(l * l + y * y);
+  for (int i = 0; i < 6; ++i) Fl[i] = Fm[i] = 0.0;
+  if (!(cdj > 0.0)) return;
+  const double shj = -l / cdj, chj = y / cdj;
+  const double r0[9] = {0.0, 1.0, 0.0, -sd0, 0.0, cd0, cd0, 0.0, sd0};
+  for (int which = 0; which < 2; ++which) {  // 0: d/dl, 1: d/dm
+    const double dn = which == 0 ? -l / n : -m / n;
+    const double dsdj = which == 0 ? dn * sd0 : cd0 + dn * sd0;
+    const double dy = which == 0 ? dn * cd0 : dn * cd0 - sd0;
+    const double dcdj = ((which == 0 ? l : 0.0) + y * dy) / cdj;
+    const double dshj = which == 0 ? (-cdj + l * dcdj) / (cdj * cdj) : l * dcdj / (cdj * cdj);
+    const double dchj = (dy * cdj - y * dcdj) / (cdj * cdj);
+    const double d0[3] = {dshj, dchj, 0.0};
+    const double d1[3] = {-(dsdj * chj + sdj * dchj), dsdj * shj + sdj * dshj, dcdj};
+    double* out = which == 0 ? Fl : Fm;
+    for (int b = 0; b < 3; ++b) {
+      out[b] = d0[0] * r0[3 * b] + d0[1] * r0[3 * b + 1] + d0[2] * r0[3 * b + 2];
+      out[3 + b] = d1[0] * r0[3 * b] + d1[1] * r0[3 * b + 1] + d1[2] * r0[3 * b + 2];
+    }
+  }
+}
+
+// Per row of shapelet sh: (dx/dl, dy/dl, dx/dm, dy/dm) per unit frequency, x = (kx_u u' + kx_v v') nu/c and
+// y likewise, through the frame's derivatives (FP64, stored as float).
+__global__ void k4_rowframe(const double* uvw, int n_rows, const ShapeRec* sh, double sd0, double cd0, float4* out) {
+  __shared__ double D[12];
+  if (threadIdx.x == 0) shapelet_frame_dlm(sh->l, sh->m, sd0, cd0, D, D + 6);
+  __syncthreads();
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_rows) return;
+  const double u = uvw[3 * (size_t)r], v = uvw[3 * (size_t)r + 1], w = uvw[3 * (size_t)r + 2];
+  double o[4];
+  for (int which = 0; which < 2; ++which) {
+    const double* F = D + 6 * which;
+    const double dup = F[0] * u + F[1] * v + F[2] * w, dvp = F[3] * u + F[4] * v + F[5] * w;
+    o[2 * which] = ((double)sh->kx_u * dup + (double)sh->kx_v * dvp) / kC;
+    o[2 * which + 1] = ((double)sh->ky_u * dup + (double)sh->ky_v * dvp) / kC;
+  }
+  out[r] = make_float4((float)o[0], (float)o[1], (float)o[2], (float)o[3]);
+}
+
 int launch_shapelet_prep(wn_ctx* ctx, const ObsDev& o, const Model* M, int q, float4* chaninfo, float4* rowinfo,
                          bool chan, cudaStream_t st);
 
@@ -808,7 +860,8 @@ int launch_grad(wn_ctx* ctx, const ObsDev& o, const Model* M, const PeelArgs& pa
   const size_t pg_bytes = ((size_t)chunks * n_pg * K4_NG * 8 + 255) & ~(size_t)255;
   const size_t sh_bytes = M->n_shape ? (((size_t)sgrid * (K4S_NS + max_nnz) * 8 + 255) & ~(size_t)255) : 0;
   const size_t rowg_bytes = ((size_t)o.n_rows * sizeof(float2) + 255) & ~(size_t)255;
-  const size_t need = chan_bytes + row_bytes + uvp_bytes + loss_bytes + pg_bytes + sh_bytes + rowg_bytes;
+  const size_t frame_bytes = M->n_shape ? row_bytes : 0;
+  const size_t need = chan_bytes + row_bytes + uvp_bytes + loss_bytes + pg_bytes + sh_bytes + rowg_bytes + frame_bytes;
   if (ctx->ws2_bytes < need) {
     if (ctx->ws2) {
       cudaStreamSynchronize(st);
@@ -828,6 +881,8 @@ int launch_grad(wn_ctx* ctx, const ObsDev& o, const Model* M, const PeelArgs& pa
   double* pgpart = reinterpret_cast<double*>(ws + chan_bytes + row_bytes + uvp_bytes + loss_bytes);
   double* shpart = reinterpret_cast<double*>(ws + chan_bytes + row_bytes + uvp_bytes + loss_bytes + pg_bytes);
   float2* rowg = reinterpret_cast<float2*>(ws + chan_bytes + row_bytes + uvp_bytes + loss_bytes + pg_bytes + sh_bytes);
+  float4* rowframe =
+      reinterpret_cast<float4*>(ws + chan_bytes + row_bytes + uvp_bytes + loss_bytes + pg_bytes + sh_bytes + rowg_bytes);
   k4_split_uvw<<<(3 * o.n_rows + 255) / 256, 256, 0, st>>>(o.uvw, o.n_rows, uvp);
   if (int r = cuda_err("uvw split")) return r;
 
@@ -889,6 +944,8 @@ int launch_grad(wn_ctx* ctx, const ObsDev& o, const Model* M, const PeelArgs& pa
   const double L0 = std::log2(o.nu0);
   for (int q = 0; q < M->n_shape; ++q) {
     if (int r = launch_shapelet_prep(ctx, o, M, q, chaninfo, rowinfo, q == 0, st)) return r;
+    k4_rowframe<<<(o.n_rows + 255) / 256, 256, 0, st>>>(o.uvw, o.n_rows, M->sh + q, std::sin(o.dec0), std::cos(o.dec0),
+                                                        rowframe);
     const ShapeRec& h = M->sh_host[q];
     const int j = n_pg + q;
     K4SArgs a;
@@ -913,6 +970,7 @@ int launch_grad(wn_ctx* ctx, const ObsDev& o, const Model* M, const PeelArgs& pa
     a.beta1 = M->r_sb1() + q;
     a.beta2 = M->r_sb2() + q;
     a.resid = resid;
+    a.rowframe = rowframe;
     a.peel = pa;
     a.part_s = shpart;
     a.err = ctx->d_err;

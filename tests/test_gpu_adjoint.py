@@ -159,3 +159,37 @@ def test_time_slices_add_up_to_the_whole_observation(wn, ctx):
         assert rel(s, full[k].cpu().numpy()) <= 1e-5, k
     m.free()
     assert ctx.device_errors() == 0
+
+
+@pytest.mark.parametrize("lm", [(0.01, -0.02), (0.2, 0.15)])
+def test_shapelet_position_gradient_follows_the_frame(wn, ctx, lm):
+    """A shapelet's (u', v') are re-phased to its own centre, so its position gradient has a share through
+    the frame besides the phase term (0.2-0.5 % of the l gradient here).  Where that share is at least 1e-3
+    of the gradient, the GPU gradient must match the oracle's, which includes it, to well under the share
+    itself: |g_gpu - g_oracle| <= 0.2 |g_oracle - g_phase_only|, with the phase-only term written out here
+    from the predicted visibilities."""
+    obs = synth.make_obs(5, 32, 2, synth.uniform_channels(167e6, 1e6, 16), layout="mwa", max_baseline=3000.0,
+                         dec0=-1.0)
+    sky = synth.make_sky(7, 0, 0, 1, fov=2 * synth.DEG, shape_nmax=np.array([20]), shape_lm=[lm])
+    uvw = obs.uvw.reshape(-1, 3)
+    V = oracle.predict(uvw, obs.freq, obs.dec0, sky)
+    rng = np.random.default_rng(1)
+    data = V + 0.3 * np.abs(V).max() * (rng.standard_normal(V.shape) + 1j * rng.standard_normal(V.shape))
+    gains = np.ones((1, 1, obs.n_ant), dtype=np.complex128)
+    W = data - V
+    ref = oracle.grad(uvw, obs.freq, obs.dec0, sky, W)
+    got = gpu_grad(wn, ctx, obs, sky, gains, data)
+    l, m = sky.l[0], sky.m[0]
+    n = np.sqrt(1.0 - l * l - m * m)
+    lam = obs.freq[None, :] / 299792458.0
+    u, v, w = uvw[:, 0:1] * lam, uvw[:, 1:2] * lam, uvw[:, 2:3] * lam
+    phase_only = {"l": np.sum(-2 * np.real(np.conj(W) * V * (-2j * np.pi) * (u - w * l / n))),
+                  "m": np.sum(-2 * np.real(np.conj(W) * V * (-2j * np.pi) * (v - w * m / n)))}
+    checked = 0
+    for name in ("l", "m"):
+        share = abs(ref[name][0] - phase_only[name])
+        if share < 1e-3 * abs(ref[name][0]):  # below what the FP32 sums resolve (about 4e-5 of the value)
+            continue
+        checked += 1
+        assert abs(got[name][0] - ref[name][0]) <= 0.2 * share, (name, got[name][0], ref[name][0], phase_only[name])
+    assert checked >= 1
