@@ -394,3 +394,31 @@ def test_large_operands_split_into_runs(wn, ctx):
     m.free()
     assert ctx.device_errors() == 0
     assert np.max(np.abs(r - ref)) <= 2e-4 * np.max(np.abs(V))
+
+
+@pytest.mark.parametrize("n_ant,n_time,n_chan", [(4, 1, 1), (2, 1, 997), (9, 3, 1), (3, 2, 257)])
+def test_shapelet_visibility_cursor_edge_shapes(wn, ctx, n_ant, n_time, n_chan):
+    """The kernel moves each thread's (row, channel) position between its tiles by whole rows and channels
+    instead of dividing per visibility: one channel, a single baseline with a prime channel count (the
+    channel step wraps), and visibility counts below one tile.  Three shapelets of mixed orders, fused peel
+    with frequency-dependent gains, against the oracle."""
+    obs = synth.make_obs(50 + n_chan, n_ant, n_time, synth.uniform_channels(167e6, 40e3, n_chan), layout="mwa",
+                         max_baseline=3000.0, dec0=-30 * synth.DEG)
+    sky = shapelet_sky(60 + n_chan, [3, 17, 9])
+    rows = np.arange(obs.n_rows)
+    V = oracle_rows(obs, sky, rows)
+    data = V + synth.complex_noise(7, V.shape, 0.05)
+    gains = synth.make_gains(8, obs.n_ant, obs.n_time, obs.n_chan)
+    ref = oracle_peel_rows(obs, rows, gains, data, V)
+    d = wn.obs_to_device(obs)
+    m = ctx.upload(sky)
+    got = ctx.predict(d, m).cpu().numpy().reshape(obs.n_rows, obs.n_chan)
+    gd = torch.as_tensor(gains.astype(np.complex64)).cuda()
+    dd = torch.as_tensor(data.astype(np.complex64).reshape(obs.n_time, obs.n_base, obs.n_chan)).cuda()
+    r = ctx.peel(d, m, gd, dd).cpu().numpy().reshape(obs.n_rows, obs.n_chan)
+    m.free()
+    assert ctx.device_errors() == 0
+    scale = np.max(np.abs(V))
+    assert np.max(np.abs(got - V)) <= 2e-4 * scale
+    # the residual also carries the data's complex64 rounding (the model can be tiny on one baseline)
+    assert np.max(np.abs(r - ref)) <= 2e-4 * scale + 1e-6 * np.max(np.abs(data))
