@@ -309,7 +309,9 @@ WN_API int wn_server_stats(wn_server* srv, double* stats);
  * of 2^18 float4 entries (4 MiB, held by every GPU that loads the library until exit) instead of the
  * context's growable workspace, and nothing in the call allocates.
  * Limits: n_chan rounded up to a multiple of 16, plus n_time * n_base, must not exceed 262144;
- * larger observations are rejected with WN_EINVAL.
+ * larger observations are rejected with WN_EINVAL.  The row tables of as many shapelets as the rest of
+ * the array holds (up to eight) are summed per launch; a model with more takes further launches that
+ * add to the output.
  * The array's device address is looked up once, when the context is created (wn_create, with the
  * context's device current), and kept in the context; the call itself only launches kernels.
  * Each device has its own copy of the array.  Every call on one device shares that copy, which keeps
