@@ -468,7 +468,9 @@ constexpr int K1B_MIN_LOG2L = 3;
 __global__ void __launch_bounds__(K1_THREADS, 2) k1_batched(const K1Args* reqs, const K1Work* work,
                                                             const int* n_work) {
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ K1Args args;
+  // raw storage: K1Args has default member initialisers, which a __shared__ variable cannot run
+  __shared__ __align__(16) unsigned char args_raw[sizeof(K1Args)];
+  K1Args& args = *reinterpret_cast<K1Args*>(args_raw);
   const int n = *n_work;
   for (int e = blockIdx.x; e < n; e += gridDim.x) {
     const K1Work w = work[e];
@@ -476,6 +478,7 @@ __global__ void __launch_bounds__(K1_THREADS, 2) k1_batched(const K1Args* reqs, 
     __syncthreads();
     if (args.chan_block == (12 << args.log2L)) k1_tile<12, true>(args, w.bx, w.by, 0, INT_MAX, nullptr, smem);
     else k1_tile<8, true>(args, w.bx, w.by, 0, INT_MAX, nullptr, smem);
+    // k1_tile ends with a barrier, so every thread is done with args before the next entry's write
   }
 }
 
