@@ -7,7 +7,9 @@
 //  * batching: admitted requests that are not yet running are packed into one work table of
 //    (request, row tile, channel block) entries and run by the persistent batched phasor kernel,
 //    replayed from a CUDA graph captured once per stream; shapelet components follow per request on
-//    the same stream, with that stream's own tables;
+//    the same stream, with that stream's own tables.  A small request that batching would not help
+//    (more than a millisecond of work, or a short grid of long tiles) runs alone on a stream through
+//    the single-request kernels instead;
 //  * overlap: there are n_streams batch slots; requests that arrive while batches are on the GPU are
 //    admitted as memory and slots free up and go out in the next batch on a free stream, so their
 //    work overlaps the batches in flight;
@@ -38,10 +40,11 @@ enum ReqState { RQ_PENDING = 0, RQ_ADMITTED = 1, RQ_RUNNING = 2, RQ_DONE = 3, RQ
 
 constexpr double kBatchBudget = 0.02;   // seconds of estimated GPU work per batch / chunk
 // Large requests in flight at once.  They share the GPU with each other and with the small batches, so
-// more of them at once stretches every one of them.  Measured on the serving bench (1,000 requests at
-// 70 % load), p99 of the requests of 20 ms or more / of the others, against 0.48 s / 0.48 s one at a
-// time: one in flight started least work first with the 1 s wait limit, 0.95 s / 0.13 s; one in
-// arrival order, 0.59 s / 0.38 s; two in arrival order, 0.83 s / 0.51 s.
+// more of them at once stretches every one of them.  A large request keeps its place until its last
+// chunk has completed.  Measured on the serving bench (1,000 requests at 70 % load), p99 of the
+// requests of 20 ms or more / of the others, against 0.48 s / 0.48 s one at a time: one in flight
+// started least work first with the 1 s wait limit, 0.93 s / 0.09 s; one in arrival order,
+// 0.53 s / 0.18 s.
 constexpr int kMaxLargeInFlight = 1;  // default; wn_server_set_policy changes it per server
 // Large requests start in order of estimated work, least first, which keeps a burst of them from
 // holding back the many mid-sized ones behind the few largest; a request that has waited this long
@@ -214,27 +217,18 @@ static bool small_waiting(wn_server* s) {
   return false;
 }
 
-static K1Args* slot_args(wn_server* s, ServeSlot& sl) { return reinterpret_cast<K1Args*>(sl.h_table + 16); }
+static K1Args* slot_args(wn_server*, ServeSlot& sl) { return reinterpret_cast<K1Args*>(sl.h_table + 16); }
 static K1Work* slot_work(wn_server* s, ServeSlot& sl) {
   return reinterpret_cast<K1Work*>(sl.h_table + 16 + sizeof(K1Args) * s->max_reqs);
 }
 
-// Launch on slot k the next chunk of the large request the slot owns: its next time steps (about
-// kBatchBudget of estimated work) as one observation through the single-request kernels, the
-// table-form phasor kernel with the slot's workspaces and then the shapelet kernel with the slot's
-// tables.  Chunks cover disjoint rows, so each applies the request's mode.  The last chunk completes the
-// request.  Called with the lock held; the slot is idle.
-static void launch_chunk(wn_server* s, int k) {
+// Launch on slot k time steps [t0, t0 + steps) of request r as one observation through the
+// single-request kernels: the table-form phasor kernel with the slot's workspaces, then the shapelet
+// kernel with the slot's tables.  Step ranges are disjoint rows, so each applies the request's mode.
+// Called with the lock held; the slot is idle.  Returns a WN_ status.
+static int launch_steps(wn_server* s, int k, ServeReq& r, int t0, int steps) {
   ServeSlot& sl = s->slots[k];
-  ServeReq& r = s->reqs[sl.owner];
-  std::vector<uint64_t> complete;
-  const int T = r.od.n_time, B = r.od.n_base, F = r.od.n_chan;
-  // about kBatchBudget of estimated work, and at least two waves of the phasor kernel's row tiles (32 rows,
-  // one CTA per SM) so that a chunk fills the GPU
-  const double per_step = large_cost(r) / T;
-  const int min_steps = (2 * 32 * s->ctx->num_sms + B - 1) / B;
-  const int steps = std::max(1, std::min(T - r.t_next, std::max(min_steps, (int)(kBatchBudget / std::max(per_step, 1e-12)))));
-  const int t0 = r.t_next;
+  const int B = r.od.n_base, F = r.od.n_chan;
   ObsDev o = r.od;
   o.n_time = steps;
   o.n_rows = steps * B;
@@ -247,7 +241,7 @@ static void launch_chunk(wn_server* s, int k) {
   }
   int rc = WN_OK;
   cudaError_t e = cudaSuccess;
-  // the spectrum table depends on the observation's channels too: a request's first chunk builds it
+  // the spectrum table depends on the observation's channels too: a request's first steps build it
   if (t0 == 0) sl.ks.spec_model = nullptr;
   const size_t need = phasor_table_spec_bytes(o, r.M);
   if (sl.ks.spec_bytes < need) {  // grow-only; the slot's stream is idle
@@ -262,6 +256,23 @@ static void launch_chunk(wn_server* s, int k) {
   if (rc == WN_OK && r.M->n_shape > 0)
     rc = launch_shapelets_ws(s->ctx, o, r.M, out, r.mode == OUT_PEEL ? OUT_SUBG : OUT_ACCUM, pa, sl.chaninfo, sl.rowinfo,
                              (size_t)kSlotRowTables * s->max_rows, sl.st);
+  return rc;
+}
+
+// Launch on slot k the next chunk of the large request the slot owns: its next time steps, about
+// kBatchBudget of estimated work and at least two waves of the phasor kernel's row tiles (32 rows, one
+// CTA per SM) so that a chunk fills the GPU.  The last chunk completes the request.  Called with the
+// lock held; the slot is idle.
+static void launch_chunk(wn_server* s, int k) {
+  ServeSlot& sl = s->slots[k];
+  ServeReq& r = s->reqs[sl.owner];
+  std::vector<uint64_t> complete;
+  const int T = r.od.n_time, B = r.od.n_base;
+  const double per_step = large_cost(r) / T;
+  const int min_steps = (2 * 32 * s->ctx->num_sms + B - 1) / B;
+  const int steps = std::max(1, std::min(T - r.t_next, std::max(min_steps, (int)(kBatchBudget / std::max(per_step, 1e-12)))));
+  const int t0 = r.t_next;
+  const int rc = launch_steps(s, k, r, t0, steps);
   r.issued = 1;
   r.t_next = t0 + steps;
   if (rc != WN_OK) {
@@ -271,15 +282,39 @@ static void launch_chunk(wn_server* s, int k) {
   if (r.t_next == T || rc != WN_OK) {
     if (rc == WN_OK) r.state = RQ_RUNNING;
     r.batch = s->batches;
-    r.owner_slot = -1;
-    sl.owner = 0;
+    r.owner_slot = -1;  // every chunk is issued; the slot stays the request's until the last completes
     complete.push_back(r.ticket);
   }
   finish_launch(s, k, complete, cudaSuccess);
 }
 
+// A small request runs alone, through the single-request kernels, when batching would gain it nothing:
+//  * its estimated work is above kSoloCost, where a launch's fixed cost is negligible and the
+//    table-form phasor kernel is faster than the batched per-warp form;
+//  * or the batched kernel would run it on less than one wave of its tiles with enough work that those
+//    tiles would run long (few rows and channels, many components), while the single-request kernels
+//    split a short grid's tiles over component ranges so that the request fills the GPU.
+constexpr double kSoloCost = 1.0e-3;     // seconds of estimated work
+constexpr double kSoloMinCost = 2.0e-4;  // seconds of estimated work
+static bool is_solo(const wn_server* s, const ServeReq& r) {
+  const double cost = r.tile_cost * r.tiles;
+  return r.tiles > 0 && (cost > kSoloCost || (r.tiles < 2L * s->ctx->num_sms && cost > kSoloMinCost));
+}
+
+// Launch small request r alone on slot k (is_solo).  Called with the lock held; the slot is idle.
+static void launch_solo(wn_server* s, int k, ServeReq& r) {
+  const int rc = launch_steps(s, k, r, 0, r.od.n_time);
+  r.issued = 1;
+  r.state = rc == WN_OK ? RQ_RUNNING : RQ_FAILED;
+  if (rc != WN_OK) r.error = rc;
+  r.batch = s->batches;
+  r.t_launch = now_s(s);
+  finish_launch(s, k, std::vector<uint64_t>{r.ticket}, cudaSuccess);
+}
+
 // Launch on slot k one batch of small unstarted requests, in ticket order, up to kBatchBudget of
-// estimated work (the first always goes).  Called with the lock held.
+// estimated work (the first always goes), or the first of them alone when it is a solo request.
+// Called with the lock held.
 static void launch_small(wn_server* s, int k) {
   ServeSlot& sl = s->slots[k];
   K1Args* args = slot_args(s, sl);
@@ -290,6 +325,11 @@ static void launch_small(wn_server* s, int k) {
   for (auto& kv : s->reqs) {
     ServeReq& r = kv.second;
     if (!unstarted(r) || is_large(r)) continue;
+    if (is_solo(s, r)) {
+      if (!complete.empty()) continue;  // it takes a slot of its own
+      launch_solo(s, k, r);
+      return;
+    }
     const double cost = r.tile_cost * r.tiles;
     if (nreq == s->max_reqs || (!complete.empty() && (cost > budget || nwork + r.tiles > s->max_work))) continue;
     if (r.tiles > 0) {
@@ -355,7 +395,7 @@ static bool launch_ready(wn_server* s) {
   }
   for (int k = 0; k < ns; ++k) {
     ServeSlot& sl = s->slots[k];
-    if (sl.busy || !sl.owner) continue;
+    if (sl.busy || !sl.owner || s->reqs[sl.owner].owner_slot != k) continue;
     launch_chunk(s, k);
     progress = true;
   }
@@ -383,6 +423,9 @@ static void scheduler(wn_server* s) {
       }
       sl.reqs.clear();
       sl.busy = false;
+      // a large request holds its slot (and its place among max_large_inflight) until its last chunk
+      // has completed, so the next one does not start beside that chunk and hold it back
+      if (sl.owner && s->reqs[sl.owner].owner_slot < 0) sl.owner = 0;
       progress = true;
     }
     // admission by slots and memory, in arrival order (a request that does not fit yet does not

@@ -332,3 +332,36 @@ def test_large_request_in_time_step_chunks_matches_oracle(wn, ctx, peel):
     assert ctx.device_errors() == 0
     for r in [big] + small:
         r["m"].free()
+
+
+def test_solo_requests_run_alone_and_match_the_oracle(wn, ctx):
+    """Small requests that batching would not help run alone through the single-request kernels: one
+    with few rows and channels but many components (a short grid of long tiles, 1 step x 1,830
+    baselines x 88 ch x 13,000 P/G) and one of more than 1 ms of estimated work (2 steps x 2,016
+    baselines x 128 ch x 8,000 P/G, peeled).  Each runs in a launch of its own, its result is the
+    single-request call's bit for bit, and it equals the oracle's on sampled rows; three tiny
+    requests submitted with them are served as before."""
+    from paper_2005_09316_b300.serve import Server
+    short = _host_request(wn, ctx, 1300, 61, 1, 88, 13000, [], peel=False)
+    heavy = _host_request(wn, ctx, 1310, 64, 2, 128, 8000, [], peel=True)
+    tiny = [_host_request(wn, ctx, 1320 + 10 * i, 24, 2, 64, 400, [6] if i == 1 else [], peel=bool(i % 2))
+            for i in range(3)]
+    reqs = [short, heavy] + tiny
+    srv = Server(ctx, n_streams=3, pool_bytes=1 << 30, max_inflight=8, max_rows=2 * 2016, max_chan=128)
+    tickets = [srv.submit(r["d"], r["m"], r["gd"], r["dd"]) for r in reqs]
+    for t in tickets:
+        assert srv.wait(t, 60).state == 3
+    batches = [srv.poll(t).batch for t in tickets]
+    for k in (0, 1):
+        assert batches.count(batches[k]) == 1, batches     # a launch of its own
+    for i, (t, r) in enumerate(zip(tickets, reqs)):
+        _check_against_oracle(srv, t, r, seed=20 + i)
+    for t, r in zip(tickets[:2], reqs[:2]):
+        got = srv.result_tensor(t, r["d"]).cpu().numpy()
+        assert np.array_equal(got, solo(ctx, (r["d"], r["m"], r["gd"], r["dd"])))
+    for t in tickets:
+        srv.release(t)
+    srv.close()
+    assert ctx.device_errors() == 0
+    for r in reqs:
+        r["m"].free()
