@@ -635,6 +635,9 @@ def bench_serving(wn, ctx, local, torch, n_req=1000, n_templates=48, seed=17, po
         lat_a = np.array([r.latency for r in res])
         out = {}
         for name, sel in (("below_20ms", svc < 0.02), ("20ms_and_above", svc >= 0.02)):
+            if not sel.any():  # a stream without requests of this class
+                out[name] = {"n": 0}
+                continue
             out[name] = {"n": int(sel.sum()), "p50_ms": round(1e3 * float(np.percentile(lat_a[sel], 50)), 3),
                          "p99_ms": round(1e3 * float(np.percentile(lat_a[sel], 99)), 3),
                          "one_at_a_time_p50_ms": round(1e3 * float(np.percentile(seq_a[sel], 50)), 3),

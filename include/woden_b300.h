@@ -248,8 +248,11 @@ WN_API int wn_predict_grad(wn_ctx* ctx, const wn_obs* obs, int model_id, const v
  * follow per request on the same stream), and keeps up to n_streams batches on the GPU, so requests
  * that arrive while others run are admitted as slots and pool memory free up and their work overlaps.
  * A request above one batch's work budget runs on a stream of its own in chunks of whole time steps
- * through the single-request kernels, with that stream's own workspaces.  Results do not depend on the
- * batch a request ran in (same tiles, same order). */
+ * through the single-request kernels, with that stream's own workspaces, and keeps the stream until
+ * its last chunk has completed.  A small request that batching would not help (more than about 1 ms of
+ * estimated work, or few tiles with long ones) runs alone through the same kernels, all its steps at
+ * once.  Results do not depend on the batch a request ran in (same tiles, same order); a request run
+ * alone gives the single-request call's result. */
 typedef struct wn_server wn_server;
 
 /* Request states reported by wn_server_poll. */
@@ -263,8 +266,9 @@ typedef struct wn_server wn_server;
 /* Create a server on ctx: n_streams batch slots (1..16), a device pool of pool_bytes for the requests'
  * outputs, at most max_inflight admitted requests, observations of at most max_rows (T*B) rows and
  * max_chan channels.  Allocates the pool, per-stream tables (room for four shapelets' row tables) and
- * pinned staging, and captures one graph per stream; a stream that runs a large request allocates its
- * spectrum table (grown to the largest request it runs) and tail-sum workspace on first use.  Resident
+ * pinned staging, and captures one graph per stream; a stream that runs a request through the
+ * single-request kernels allocates its spectrum table (grown to the largest request it runs) and
+ * tail-sum workspace on first use.  Resident
  * models must not be freed while requests that use them are unreleased. */
 WN_API int wn_server_create(wn_ctx* ctx, int n_streams, size_t pool_bytes, int max_inflight, int max_rows,
                             int max_chan, wn_server** out);
