@@ -296,12 +296,16 @@ __device__ __forceinline__ void ks_tile(const KSArgs& A, const int bx, const int
     const float4* Rg = rec + 3 * g;
     const float* tb = spec + sub * K;
     if (UNIFORM) {
+      // four components per loop trip: the compiler interleaves one component's start (reduction, MUFU
+      // sin/cos) with another's recurrence (measured 1.2 % faster than one per trip)
       if (gauss) {
+#pragma unroll 4
         for (int j = 0; j < cnt; ++j) {
           const float4* R = Rg + 3 * groups * j;
           ks_comp_uniform<K, true>(R[0], R[1], R[2], tb + j * cb, a0h, a0l, wg, Vre, Vim);
         }
       } else {
+#pragma unroll 4
         for (int j = 0; j < cnt; ++j) {
           const float4* R = Rg + 3 * groups * j;
           ks_comp_uniform<K, false>(R[0], R[1], R[2], tb + j * cb, a0h, a0l, wg, Vre, Vim);

@@ -101,10 +101,12 @@ __global__ void __launch_bounds__(KP_LOOP_THREADS, 1) kp_loop(float* out, int pa
   for (int it = 0; it < passes; ++it) {
     for (int t = 0; t < KP_LOOP_GROUPS; ++t) {
       if (t == KP_LOOP_GROUPS - 1) {
+#pragma unroll 4
         for (int j = 0; j < 16; ++j)
           ks_comp_uniform<KP_LOOP_K, true>(rec[3 * j], rec[3 * j + 1], rec[3 * j + 2], tb + j * 384, a0h, a0l, wg,
                                            Vre, Vim);
       } else {
+#pragma unroll 4
         for (int j = 0; j < 16; ++j)
           ks_comp_uniform<KP_LOOP_K, false>(rec[3 * j], rec[3 * j + 1], rec[3 * j + 2], tb + j * 384, a0h, a0l, wg,
                                             Vre, Vim);
