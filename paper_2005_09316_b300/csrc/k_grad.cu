@@ -221,25 +221,31 @@ __host__ __device__ inline K4USmem k4u_layout(int f_cnt) {
 // s2 = sum (nu/c) Im z, s3 = sum (nu/c)^2 Re z with z = conj(W) V / S_ref.  GAUSS = false (a tile of
 // points only) leaves out the Gaussian envelope's exponent term and s3, which only Gaussians use.
 template <bool GAUSS>
+__device__ __forceinline__ void k4u_channel(const float4 c, const float2 W, float q, float alpha, float cj, float2 D,
+                                            float2& P, float& s0, float& s1, float& s2, float& s3) {
+  // channel sums use the amplitude without the flux: dV/dS_ref = V / S_ref holds for S_ref = 0 too
+  const float e = fmaf(alpha, c.x, cj);
+  const float A = ex2_approx(GAUSS ? fmaf(-q, c.y, e) : e);
+  const float vr = A * P.x, vi = A * P.y;
+  const float zr = W.x * vr + W.y * vi, zi = W.x * vi - W.y * vr;  // z = conj(W) V
+  s0 += zr;
+  s1 = fmaf(c.x, zr, s1);
+  s2 = fmaf(c.z, zi, s2);
+  if (GAUSS) s3 = fmaf(c.w, zr, s3);
+  P = make_float2(P.x * D.x - P.y * D.y, P.x * D.y + P.y * D.x);
+}
+
+template <bool GAUSS>
 __device__ __forceinline__ void k4u_channels(int F, float th, float tl, float q, float alpha, float cj, float2 D,
                                              const float2* nh, const float4* cc, const float2* myw, float& s0,
                                              float& s1, float& s2, float& s3) {
   for (int fb = 0; fb < F; fb += K4U_RS) {
     float2 P = phasor_fast(reduce_turns(th, tl, nh[fb].x, nh[fb].y));
-    const int fe = min(fb + K4U_RS, F);
-    for (int f = fb; f < fe; ++f) {
-      const float4 c = cc[f];
-      const float2 W = myw[f];
-      // channel sums use the amplitude without the flux: dV/dS_ref = V / S_ref holds for S_ref = 0 too
-      const float e = fmaf(alpha, c.x, cj);
-      const float A = ex2_approx(GAUSS ? fmaf(-q, c.y, e) : e);
-      const float vr = A * P.x, vi = A * P.y;
-      const float zr = W.x * vr + W.y * vi, zi = W.x * vi - W.y * vr;  // z = conj(W) V
-      s0 += zr;
-      s1 = fmaf(c.x, zr, s1);
-      s2 = fmaf(c.z, zi, s2);
-      if (GAUSS) s3 = fmaf(c.w, zr, s3);
-      P = make_float2(P.x * D.x - P.y * D.y, P.x * D.y + P.y * D.x);
+    if (fb + K4U_RS <= F) {  // a whole block: unrolled, constant offsets
+#pragma unroll
+      for (int i = 0; i < K4U_RS; ++i) k4u_channel<GAUSS>(cc[fb + i], myw[fb + i], q, alpha, cj, D, P, s0, s1, s2, s3);
+    } else {
+      for (int f = fb; f < F; ++f) k4u_channel<GAUSS>(cc[f], myw[f], q, alpha, cj, D, P, s0, s1, s2, s3);
     }
   }
 }
