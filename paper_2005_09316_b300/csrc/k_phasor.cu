@@ -392,7 +392,9 @@ static cudaError_t k1_launch(const K1Args& a, int n_tail, int smem, cudaStream_t
   return cudaGetLastError();
 }
 
-size_t k1_part_bytes(int num_sms) { return (size_t)2 * num_sms * 2 * 16 * K1_THREADS * sizeof(float2); }
+// Partial sums of the split tail tiles: room for 4 * num_sms parts of the per-warp form at K = 16 (it uses
+// at most 2 * num_sms, one per resident CTA), which the single-launch form's split also draws on.
+size_t k1_part_bytes(int num_sms) { return (size_t)4 * num_sms * 2 * 16 * K1_THREADS * sizeof(float2); }
 
 int launch_phasor_mixed(wn_ctx* ctx, const ObsDev& o, const Model* M, float2* out, int mode, const PeelArgs& pa,
                         cudaStream_t st) {

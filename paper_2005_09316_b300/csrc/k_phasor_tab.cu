@@ -537,7 +537,11 @@ int launch_phasor_table_ws(wn_ctx* ctx, const ObsDev& o, const Model* M, float2*
   }
 
   // tail split: the last n_cta mod slots tiles (one resident CTA per SM) are split into parts over
-  // group ranges so that they fill the last wave
+  // group ranges so that they fill the last wave.  The part count p minimises the tail's estimated
+  // time in tiles, ceil(rem p / slots) (1 / p + h), within the partial-sum workspace, where h is a
+  // part's fixed cost (its start, its partial sums written and summed again: taken as 5e5
+  // evaluations, about 15 us of an SM) over a tile's evaluations.  With rem = 80 of 148 slots and long
+  // tiles, 3 parts (two waves of thirds) take 0.67 of a tile instead of 1; short tiles split less.
   const int smem = ks_smem_layout(log2L, K).total;
   const int slots = ctx->num_sms;
   const int rem = (int)(n_cta % slots);
@@ -547,7 +551,18 @@ int launch_phasor_table_ws(wn_ctx* ctx, const ObsDev& o, const Model* M, float2*
   a.part = w.part;
   int n_tail = 0;
   if (rem > 0 && A.n_grp >= 2 && w.part) {
-    const int parts = std::min(slots / rem, A.n_grp);
+    const long cap = (long)(k1_part_bytes(slots) / ((size_t)2 * K * KS_THREADS * sizeof(float2)));
+    const double tile_evals = (double)rows_per_cta * cb * (double)(M->n_point + M->n_gauss);
+    const double h = 5.0e5 / std::max(tile_evals, 1.0);
+    int parts = 1;
+    double best = 1.0;
+    for (int p = 2; p <= A.n_grp && (long)rem * p <= cap; ++p) {
+      const double t = (double)((rem * p + slots - 1) / slots) * (1.0 / p + h);
+      if (t < best - 1e-9) {
+        best = t;
+        parts = p;
+      }
+    }
     if (parts >= 2) {
       a.tail_ct = (A.n_grp + parts - 1) / parts;
       a.tail_parts = (A.n_grp + a.tail_ct - 1) / a.tail_ct;  // no empty part
