@@ -395,7 +395,9 @@ static bool launch_ready(wn_server* s) {
   }
   for (int k = 0; k < ns; ++k) {
     ServeSlot& sl = s->slots[k];
-    if (sl.busy || !sl.owner || s->reqs[sl.owner].owner_slot != k) continue;
+    if (sl.busy || !sl.owner) continue;
+    auto it = s->reqs.find(sl.owner);
+    if (it == s->reqs.end() || it->second.owner_slot != k) continue;
     launch_chunk(s, k);
     progress = true;
   }
@@ -425,7 +427,10 @@ static void scheduler(wn_server* s) {
       sl.busy = false;
       // a large request holds its slot (and its place among max_large_inflight) until its last chunk
       // has completed, so the next one does not start beside that chunk and hold it back
-      if (sl.owner && s->reqs[sl.owner].owner_slot < 0) sl.owner = 0;
+      if (sl.owner) {
+        auto it = s->reqs.find(sl.owner);
+        if (it == s->reqs.end() || it->second.owner_slot < 0) sl.owner = 0;
+      }
       progress = true;
     }
     // admission by slots and memory, in arrival order (a request that does not fit yet does not
