@@ -980,7 +980,8 @@ def main():
                         "d2h_bytes_per_step": int(pipes[0]["res"].numel() * 8), "ms_per_step": round(t_e2e * 1e3, 3),
                         "pipeline": "2 contexts x 2 streams: each step's copies overlap the other step's compute"}
 
-        if not args.no_extras:
+        # the long reports and the CPU baseline run at N = 1 only: a scaling run holds every GPU meanwhile
+        if not args.no_extras and ws == 1:
             for key, fn in (("shapelet", lambda: bench_shapelets(wn, ctx, local, P, torch)),
                             ("adjoint", lambda: bench_adjoint(wn, ctx, local, torch)),
                             ("calibration", lambda: bench_calibration(wn, ctx, local, torch)),
@@ -992,7 +993,7 @@ def main():
                 except Exception as exc:  # an extra report must not hide the headline number
                     extra[key] = {"error": f"{type(exc).__name__}: {exc}"}
 
-        if not args.no_cpu_baseline:
+        if not args.no_cpu_baseline and ws == 1:
             rate, smp = oracle_rate(obs, sky, args.cpu_seconds)
             extra["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
                                      "sample": f"{smp['rows']} random rows x 384 ch x 25000 comps "
