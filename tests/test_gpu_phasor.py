@@ -238,10 +238,10 @@ def test_bitwise_reproducible(wn, ctx):
 
 @pytest.mark.parametrize("n_time,n_chan,uniform", [(2, 384, True), (1, 384, True), (2, 700, False), (3, 96, True)])
 def test_split_tail_tiles_every_mode(wn, ctx, n_time, n_chan, uniform):
-    """A 128-tile array at 1-3 time steps: 2 steps at 384 channels leave 128 of 1,016 tiles for a last
-    wave of 296 resident CTAs, which the launch splits over component ranges and sums in a second
-    kernel; 1 step leaves 212 (no split).  Rows from the whole tiles and from the split tail, in the
-    store, accumulate and peel modes, against the oracle."""
+    """A 128-tile array at 1-3 time steps: 2 steps at 384 channels make 508 tiles of 32 rows and leave 64
+    for a last wave of 148 CTAs, which the launch splits over component ranges and sums in a second
+    kernel; 1 step leaves 106, too many for parts to shorten the tail (no split).  Rows from the whole
+    tiles and from the split tail, in the store, accumulate and peel modes, against the oracle."""
     rng = np.random.default_rng(n_chan + n_time)
     freq = (synth.uniform_channels(167e6, 80e3, n_chan) if uniform
             else np.sort(rng.uniform(150e6, 190e6, size=n_chan)))
@@ -270,6 +270,41 @@ def test_split_tail_tiles_every_mode(wn, ctx, n_time, n_chan, uniform):
     ref = oracle_peel_rows(obs, rows, gains.astype(np.complex64), dat, V)
     assert np.max(np.abs(r - ref)) <= 1e-5 * np.max(np.abs(V))
     # the whole output is the same in every call (fixed summation order of the parts)
+    v2 = ctx.predict(d, m).reshape(obs.n_rows, obs.n_chan)
+    assert torch.equal(v, v2)
+    assert ctx.device_errors() == 0
+    m.free()
+
+
+def test_split_tail_over_more_than_one_wave(wn, ctx):
+    """72 antennas (2,556 baselines) x 1 step x 384 channels, 4,000 points + 1,000 Gaussians: 80 tiles of
+    32 rows, all of them the tail, each split into 3 component ranges (240 CTAs, two waves on 148 SMs)
+    and summed in part order.  Rows of every tile, in the store, accumulate and peel modes, against the
+    oracle; the output is the same in every call."""
+    obs = small_obs(72, 72, 1, synth.uniform_channels(167e6, 80e3, 384), layout="mwa")
+    sky = synth.make_sky(73, 4000, 1000, 0, fov=20 * synth.DEG)
+    rng = np.random.default_rng(72)
+    rows = np.unique(np.concatenate([np.arange(0, obs.n_rows, 32), rng.choice(obs.n_rows, 8, replace=False),
+                                     [obs.n_rows - 1]]))
+    V = oracle_rows(obs, sky, rows)
+    d = wn.obs_to_device(obs)
+    m = ctx.upload(sky)
+    rt = torch.as_tensor(rows).cuda()
+    v = ctx.predict(d, m).reshape(obs.n_rows, obs.n_chan)
+    assert e_norm(v[rt].cpu().numpy(), V) <= 1e-5
+    shape = (obs.n_time, obs.n_base, obs.n_chan)
+    data = torch.zeros(shape, dtype=torch.complex64, device="cuda")
+    data.real.normal_(generator=torch.Generator(device="cuda").manual_seed(72))
+    acc = data.clone()
+    ctx.predict(d, m, out=acc, accumulate=True)
+    dat = data.reshape(obs.n_rows, obs.n_chan)[rt].cpu().numpy()
+    got = acc.reshape(obs.n_rows, obs.n_chan)[rt].cpu().numpy()
+    assert np.max(np.abs(got - (dat + V))) <= 1e-5 * np.max(np.abs(V))
+    gains = synth.make_gains(72, obs.n_ant, obs.n_time, 1)
+    gd = torch.as_tensor(gains.astype(np.complex64)).cuda()
+    r = ctx.peel(d, m, gd, data).reshape(obs.n_rows, obs.n_chan)[rt].cpu().numpy()
+    ref = oracle_peel_rows(obs, rows, gains.astype(np.complex64), dat, V)
+    assert np.max(np.abs(r - ref)) <= 1e-5 * np.max(np.abs(V))
     v2 = ctx.predict(d, m).reshape(obs.n_rows, obs.n_chan)
     assert torch.equal(v, v2)
     assert ctx.device_errors() == 0
