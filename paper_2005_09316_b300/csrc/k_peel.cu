@@ -1,7 +1,7 @@
 // K3': standalone streaming peel of an already predicted model (Sec. 5.1):
 //   resid = data - g[ant1] conj(g[ant2]) model.
 // HBM-bound: reads data and model, writes resid (24 bytes per visibility) plus gains that stay in
-// L1/L2, with streaming (evict-first) loads and stores; the grid is a multiple of the SM count.
+// L1/L2, with streaming (evict-first) loads and stores; the grid is one wave of resident blocks.
 #include "wn_internal.cuh"
 
 namespace wn {
@@ -32,14 +32,29 @@ __global__ void __launch_bounds__(256) k3_peel(PeelArgs p, int n_base, int n_cha
       const float4* d4 = reinterpret_cast<const float4*>(p.data + base);
       const float4* m4 = reinterpret_cast<const float4*>(model + base);
       float4* r4 = reinterpret_cast<float4*>(resid + base);
-      for (int k = lane; k < (n_chan >> 1); k += 32) {
-        const float4 d = __ldcs(d4 + k);
-        const float4 v = __ldcs(m4 + k);
-        const float2 Ga = p.gf == 1 ? G0 : row_gain(p, row, n_base, 2 * k, err);
-        const float2 Gb = p.gf == 1 ? G0 : row_gain(p, row, n_base, 2 * k + 1, err);
-        const float2 a = peel_sub(make_float2(d.x, d.y), make_float2(v.x, v.y), Ga);
-        const float2 b = peel_sub(make_float2(d.z, d.w), make_float2(v.z, v.w), Gb);
-        __stcs(r4 + k, make_float4(a.x, a.y, b.x, b.y));
+      // four 16-byte pairs per lane loaded before any is stored, so that eight loads are in flight
+      // per lane (resid may alias data: every element is read before its own store)
+      const int n2 = n_chan >> 1;
+      for (int k0 = lane; k0 < n2; k0 += 4 * 32) {
+        float4 d[4], v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int k = k0 + 32 * u;
+          if (k < n2) {
+            d[u] = __ldcs(d4 + k);
+            v[u] = __ldcs(m4 + k);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int k = k0 + 32 * u;
+          if (k >= n2) break;
+          const float2 Ga = p.gf == 1 ? G0 : row_gain(p, row, n_base, 2 * k, err);
+          const float2 Gb = p.gf == 1 ? G0 : row_gain(p, row, n_base, 2 * k + 1, err);
+          const float2 a = peel_sub(make_float2(d[u].x, d[u].y), make_float2(v[u].x, v[u].y), Ga);
+          const float2 b = peel_sub(make_float2(d[u].z, d[u].w), make_float2(v[u].z, v[u].w), Gb);
+          __stcs(r4 + k, make_float4(a.x, a.y, b.x, b.y));
+        }
       }
     } else {
       for (int f = lane; f < n_chan; f += 32) {
@@ -55,7 +70,9 @@ int launch_peel_model(wn_ctx* ctx, const ObsDev& o, const PeelArgs& pa, const fl
   if (((uintptr_t)pa.data | (uintptr_t)model | (uintptr_t)resid) & 15)
     return set_error(WN_EINVAL, "wn_peel_model: data, model and resid must be 16-byte aligned");
   const int want = (o.n_rows + 7) / 8;  // 8 warps (rows) per block
-  const int blocks = std::max(1, std::min(want, ctx->num_sms * 8));
+  int per_sm = 0;                       // resident blocks per SM: the grid is one wave of them
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3_peel, 256, 0) != cudaSuccess || per_sm < 1) per_sm = 4;
+  const int blocks = std::max(1, std::min(want, ctx->num_sms * per_sm));
   k3_peel<<<blocks, 256, 0, st>>>(pa, o.n_base, o.n_chan, o.n_rows, model, resid, ctx->d_err);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(WN_ECUDA, std::string("peel kernel launch: ") + cudaGetErrorString(e));
