@@ -78,14 +78,44 @@ def test_two_shapelets_fit_the_data_like_the_oracle(wn, ctx):
     assert info["resid2"] <= 1e-6 * info["resid2_start"], info
 
 
+def _design(obs, sky, G):
+    """The oracle's design matrix of the shapelet coefficients (gains applied), one column per
+    coefficient, and the data less the fixed points and Gaussians: V = V_pg + A c (eq:shape-env is
+    linear in the coefficients)."""
+    uvw = obs.uvw.reshape(-1, 3)
+    n = len(sky.s_coeff)
+    cols = []
+    for k in range(n):
+        s2 = sky.__class__(**sky.__dict__)
+        s2.flux = np.array(sky.flux, float).copy()
+        s2.flux[:sky.n_point + sky.n_gauss] = 0.0
+        e = np.zeros(n)
+        e[k] = 1.0
+        s2.s_coeff = e
+        cols.append((G * oracle.predict(uvw, obs.freq, obs.dec0, s2)).ravel())
+    pg = sky.__class__(**sky.__dict__)
+    pg.flux = np.array(sky.flux, float).copy()
+    pg.flux[sky.n_point + sky.n_gauss:] = 0.0
+    return np.array(cols).T, (G * oracle.predict(uvw, obs.freq, obs.dec0, pg)).ravel()
+
+
 def test_noisy_fit_matches_oracle_least_squares(wn, ctx):
+    """n_max 7 (36 coefficients) under noise.  The least-squares problem has condition number about 280,
+    so its coefficients are determined only to about cond^2 times the FP32 rounding of the products
+    (~1e-7): the fit must reach the oracle's least-squares objective within 1e-4, and its coefficients
+    must equal the oracle's within 1e-2 of the largest."""
     obs, sky, gains, G, D = problem(21, nmax=(7,), noise=0.5)
     c, info, flags, vfit = gpu_fit(wn, ctx, obs, sky, gains, D)
     assert flags == 0
     uvw = obs.uvw.reshape(-1, 3)
     ref = oracle.fit_shapelet_coeffs(uvw, obs.freq, obs.dec0, sky, G, D)
+    A, vpg = _design(obs, sky, G)
+    b = D.ravel() - vpg
+    f_gpu = np.sum(np.abs(b - A @ c) ** 2)
+    f_ref = np.sum(np.abs(b - A @ ref) ** 2)
+    assert f_gpu <= f_ref * (1 + 1e-4), (f_gpu, f_ref, info)
     err = np.abs(c - ref).max() / np.abs(ref).max()
-    assert err <= 2e-3, (err, info)
+    assert err <= 1e-2, (err, info)
     # the model keeps the fitted coefficients
     fitted = sky.__class__(**sky.__dict__)
     fitted.s_coeff = ref
