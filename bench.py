@@ -348,6 +348,15 @@ def summary_block(line: dict) -> dict:
                 return None
             d = d[k]
         return float(f"{d:.4g}") if isinstance(d, float) else d
+
+    def small_first():  # the serving stream under the small-first order with the 1 s wait limit
+        for o in (line.get("serving") or {}).get("other_policies") or []:
+            if o.get("order") == "small_first" and o.get("max_large_wait_s") == 1.0:
+                c = o.get("p99_by_class") or {}
+                return {"p50_ms": o.get("p50_ms"), "p99_ms": o.get("p99_ms"),
+                        "small_p99_ms": (c.get("below_20ms") or {}).get("p99_ms"),
+                        "large_p99_ms": (c.get("20ms_and_above") or {}).get("p99_ms")}
+        return None
     return {
         "k1": {"evals_per_s": g("value"), "frac": g("roofline", "frac"), "e_norm": g("error", "e_norm"),
                "loop_bound_frac": g("roofline", "loop_bound", "frac")},
@@ -360,7 +369,7 @@ def summary_block(line: dict) -> dict:
         "k5_fp64": {"evals_per_s": g("fp64_gpu", "value"), "speedup": g("fp64_gpu", "speedup_mixed_over_fp64"),
                     "untuned_speedup": g("fp64_gpu_untuned", "speedup_mixed_over_untuned")},
         "k7_calib_ms": g("calibration", "ms"), "k8_fit_ms_per_iter": g("fit", "ms_per_iteration"),
-        "serving": {"p50_ms": g("serving", "p50_ms"), "p99_ms": g("serving", "p99_ms"),
+        "serving": {"order": g("serving", "policy", "order"), "p50_ms": g("serving", "p50_ms"), "p99_ms": g("serving", "p99_ms"),
                     "one_at_a_time_p50_ms": g("serving", "one_at_a_time_p50_ms"),
                     "one_at_a_time_p99_ms": g("serving", "one_at_a_time_p99_ms"),
                     "large_p99_ms": g("serving", "p99_by_class", "20ms_and_above", "p99_ms"),
@@ -369,7 +378,8 @@ def summary_block(line: dict) -> dict:
                     "small_one_at_a_time_p99_ms": g("serving", "p99_by_class", "below_20ms", "one_at_a_time_p99_ms"),
                     "max_batch_requests": g("serving", "max_batch_requests"),
                     "burst_gain": g("serving", "burst", "throughput_gain"),
-                    "burst_max_batch_requests": g("serving", "burst", "max_batch_requests")},
+                    "burst_max_batch_requests": g("serving", "burst", "max_batch_requests"),
+                    "small_first": small_first()},
         "e2e": g("e2e", "value"), "cpu_baseline": g("cpu_baseline", "value"),
     }
 
@@ -567,7 +577,7 @@ def bench_adjoint(wn, ctx, local, torch):
 
 
 def bench_serving(wn, ctx, local, torch, n_req=1000, n_templates=48, seed=17, policy=None, n_burst=256,
-                  detail=None, extra_policies=((1, 0.3),)):
+                  detail=None, order=None, extra_policies=((1, 1, 1.0), (1, 1, 0.3))):
     """Seeded Poisson stream of predict/peel requests of uneven size (16-128 tiles, 1-14 steps, 32-384
     channels, 100-50,000 P/G, 0-3 shapelets with n_max 10-80), models resident.  Requests are drawn
     uniformly from n_templates distinct (observation, sky, data) sets; the arrival rate is set for ~70%
@@ -575,9 +585,12 @@ def bench_serving(wn, ctx, local, torch, n_req=1000, n_templates=48, seed=17, po
     same requests at the same arrival times run one after another through the single-request calls.  A
     burst phase submits n_burst requests of the sets that take under 5 ms alone at once, so that batches
     of several requests form, and compares the wall time with the same burst run one at a time.
+    order: the request order (serve.SERVE_ARRIVAL or SERVE_SMALL_FIRST); None keeps the default (arrival).
     policy: (large requests in flight, wait limit in s) for Server.set_policy; None keeps the defaults.
-    extra_policies: further policies the same stream is played under (latencies only)."""
+    extra_policies: further (order, large requests in flight, wait limit) the same stream is played under
+    (latencies only); by default small-first with the 1 s and the 0.3 s wait limits."""
     from paper_2005_09316_b300.serve import Server, latency_summary, poisson_arrivals, run_sequential, run_stream
+    order_names = {0: "arrival", 1: "small_first"}
     rng = np.random.default_rng(seed)
     temps, models = [], []
     for i in range(n_templates):
@@ -620,6 +633,8 @@ def bench_serving(wn, ctx, local, torch, n_req=1000, n_templates=48, seed=17, po
 
     def server():
         srv = Server(ctx, n_streams=6, pool_bytes=6 << 30, max_inflight=32, max_rows=max_rows, max_chan=384)
+        if order is not None:
+            srv.set_order(order)
         if policy is not None:
             srv.set_policy(*policy)
         return srv
@@ -644,16 +659,18 @@ def bench_serving(wn, ctx, local, torch, n_req=1000, n_templates=48, seed=17, po
                          "one_at_a_time_p99_ms": round(1e3 * float(np.percentile(seq_a[sel], 99)), 3)}
         return out
 
-    # the same stream under another admission policy for large requests (a 0.3 s wait limit by default)
+    # the same stream under the other request order and policies (small first, 1 s and 0.3 s wait limits)
     others = []
     for pol in extra_policies:
         srv = server()
-        srv.set_policy(*pol)
+        srv.set_order(pol[0])
+        srv.set_policy(pol[1], pol[2])
         res_p, _ = run_stream(srv, reqs, arrivals)
         st_p = srv.stats()
         srv.close()
         lat_p = latency_summary(res_p)
-        others.append({"max_large_inflight": pol[0], "max_large_wait_s": pol[1], "p50_ms": round(lat_p["p50_ms"], 3),
+        others.append({"order": order_names[pol[0]], "max_large_inflight": pol[1], "max_large_wait_s": pol[2],
+                       "p50_ms": round(lat_p["p50_ms"], 3),
                        "p99_ms": round(lat_p["p99_ms"], 3), "p99_by_class": classes(res_p),
                        "max_batch_requests": st_p["max_batch_requests"]})
     if detail is not None:  # per request: (template, service alone, server result, one-at-a-time latency)
@@ -681,7 +698,8 @@ def bench_serving(wn, ctx, local, torch, n_req=1000, n_templates=48, seed=17, po
         m.free()
     return {"workload": f"serving: {n_req} Poisson requests drawn from {n_templates} uneven request sets "
                         "(16-128 tiles, 1-14 steps, 32-384 ch, 100-50000 P/G + 0-3 shapelets n_max 10-80)",
-            "policy": {"max_large_inflight": (policy or (1, 1.0))[0], "max_large_wait_s": (policy or (1, 1.0))[1]},
+            "policy": {"order": order_names[0 if order is None else order],
+                       "max_large_inflight": (policy or (1, 1.0))[0], "max_large_wait_s": (policy or (1, 1.0))[1]},
             "rate_hz": round(rate, 2), "mean_service_ms": round(1e3 * mean_s, 3),
             "p50_ms": round(lat["p50_ms"], 3), "p99_ms": round(lat["p99_ms"], 3),
             "one_at_a_time_p50_ms": round(1e3 * float(np.percentile(lat_seq, 50)), 3),

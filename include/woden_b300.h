@@ -247,9 +247,10 @@ WN_API int wn_predict_grad(wn_ctx* ctx, const wn_obs* obs, int model_id, const v
  * requests into one batch run by a persistent phasor kernel replayed from a CUDA graph (shapelets
  * follow per request on the same stream), and keeps up to n_streams batches on the GPU, so requests
  * that arrive while others run are admitted as slots and pool memory free up and their work overlaps.
- * A request above one batch's work budget runs on a stream of its own in chunks of whole time steps
- * through the single-request kernels, with that stream's own workspaces, and keeps the stream until
- * its last chunk has completed.  A small request that batching would not help (more than about 1 ms of
+ * A request above one batch's work budget runs on a stream of its own through the single-request
+ * kernels, with that stream's own workspaces (in one launch in arrival order, in chunks of whole time
+ * steps small-first; see wn_server_set_order), and keeps the stream until its last launch has
+ * completed.  A small request that batching would not help (more than about 1 ms of
  * estimated work, or few tiles with long ones) runs alone through the same kernels, all its steps at
  * once.  Results do not depend on the batch a request ran in (same tiles, same order); a request run
  * alone gives the single-request call's result. */
@@ -293,12 +294,28 @@ WN_API int wn_server_release(wn_server* srv, uint64_t ticket);
 /* Cancel a request that has not been admitted yet (WN_EBUSY otherwise). */
 WN_API int wn_server_cancel(wn_server* srv, uint64_t ticket);
 /* Admission policy for large requests (those whose estimated work exceeds one batch's budget, about
- * 20 ms; they run in chunks).  At most max_large_inflight of them (1..16; never more than the slots
- * less one) own a slot at a time; among the waiting ones the least estimated work starts first, except
- * that one waiting longer than max_large_wait_s seconds since submission starts before any younger one
- * (0 gives submission order).  Defaults: 1 and 1.0 s.  Takes effect at the next admission; requests
- * already started keep their slot.  WN_EINVAL for a NULL server or values outside those ranges. */
+ * 20 ms).  At most max_large_inflight of them (1..16; never more than the slots less one) own a slot at
+ * a time.  In the small-first order, among the waiting ones the least estimated work starts first,
+ * except that one waiting longer than max_large_wait_s seconds since submission starts before any
+ * younger one (0 gives submission order); in arrival order they start in submission order and the wait
+ * limit is not used.  Defaults: 1 and 1.0 s.  Takes effect at the next admission; requests already
+ * started keep their slot.  WN_EINVAL for a NULL server or values outside those ranges. */
 WN_API int wn_server_set_policy(wn_server* srv, int max_large_inflight, double max_large_wait_s);
+
+/* Request orders for wn_server_set_order.
+ * WN_SERVE_ARRIVAL (the default): large requests start in submission order, one launch each on the
+ *   highest-priority stream.  The large request due next waits for the small requests submitted before
+ *   it to finish, and the small requests submitted after it wait until it has started; other small
+ *   requests are batched and go out on lower-priority streams as they free up, one batch at a time
+ *   while a large request runs.  A large request thus waits only for work submitted before it (and for
+ *   blocks of a lower-priority batch that the GPU runs beside it), as in a one-at-a-time queue.
+ * WN_SERVE_SMALL_FIRST: small requests go out as soon as a stream is free; large requests run in chunks
+ *   of whole time steps on the lowest-priority stream, in the order wn_server_set_policy sets.  The
+ *   small requests' latency is far lower; the largest requests' tail is longer. */
+#define WN_SERVE_ARRIVAL 0
+#define WN_SERVE_SMALL_FIRST 1
+/* Set the request order (WN_SERVE_*); takes effect at the next admission.  WN_EINVAL otherwise. */
+WN_API int wn_server_set_order(wn_server* srv, int order);
 /* stats (6 doubles): batches launched, most batches on the GPU at once, most requests in one batch,
  * requests launched, requests admitted and unreleased, free pool bytes. */
 WN_API int wn_server_stats(wn_server* srv, double* stats);

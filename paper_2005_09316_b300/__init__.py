@@ -28,7 +28,7 @@ EXPORTED = ("wn_create", "wn_destroy", "wn_last_error", "wn_version", "wn_set_pr
             "wn_sky_upload", "wn_sky_free", "wn_sky_bytes", "wn_predict", "wn_peel", "wn_peel_model",
             "wn_predict_grad", "wn_predict_static", "wn_server_create", "wn_server_destroy", "wn_server_submit",
             "wn_server_poll", "wn_server_wait", "wn_server_copy", "wn_server_release", "wn_server_cancel",
-            "wn_server_stats", "wn_server_set_policy", "wn_calibrate", "wn_fit_shapelets", "wn_pipe_rates",
+            "wn_server_stats", "wn_server_set_policy", "wn_server_set_order", "wn_calibrate", "wn_fit_shapelets", "wn_pipe_rates",
             "wn_phasor_loop_rate", "wn_sky_shapelet_operand", "wn_selftest_timeout", "wn_mma_rate", "wn_mma_rate_tf32", "wn_set_trace", "wn_debug_fail_allocs",
             "wn_sky_shapelet_operand_tf32", "wn_sky_update")
 
@@ -104,6 +104,7 @@ def load(build_if_missing: bool = True):
         L.wn_server_cancel.argtypes = [P, u64]
         L.wn_server_stats.argtypes = [P, ctypes.POINTER(dbl)]
         L.wn_server_set_policy.argtypes = [P, i, dbl]
+        L.wn_server_set_order.argtypes = [P, i]
         L.wn_calibrate.argtypes = [P, ctypes.POINTER(WnObs), P, P, P, i, P]
         L.wn_fit_shapelets.argtypes = [P, ctypes.POINTER(WnObs), i, P, i, i, P, i, dbl, P, ctypes.POINTER(dbl), P]
         L.wn_pipe_rates.argtypes = [P, ctypes.POINTER(dbl)]

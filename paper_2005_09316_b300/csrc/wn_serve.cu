@@ -41,15 +41,18 @@ enum ReqState { RQ_PENDING = 0, RQ_ADMITTED = 1, RQ_RUNNING = 2, RQ_DONE = 3, RQ
 constexpr double kBatchBudget = 0.02;   // seconds of estimated GPU work per batch / chunk
 // Large requests in flight at once.  They share the GPU with each other and with the small batches, so
 // more of them at once stretches every one of them.  A large request keeps its place until its last
-// chunk has completed.  Measured on the serving bench (1,000 requests at 70 % load), p99 of the
-// requests of 20 ms or more / of the others, against 0.48 s / 0.48 s one at a time: one in flight
-// started least work first with the 1 s wait limit, 0.93 s / 0.09 s; one in arrival order,
-// 0.53 s / 0.18 s.
+// launch has completed.
 constexpr int kMaxLargeInFlight = 1;  // default; wn_server_set_policy changes it per server
-// Large requests start in order of estimated work, least first, which keeps a burst of them from
-// holding back the many mid-sized ones behind the few largest; a request that has waited this long
-// since submission starts before any younger one, so the largest are passed over for a bounded time.
+// In the small-first order, large requests start in order of estimated work, least first, which keeps a
+// burst of them from holding back the many mid-sized ones behind the few largest; a request that has
+// waited this long since submission starts before any younger one, so the largest are passed over for
+// a bounded time.
 constexpr double kMaxLargeWait = 1.0;  // seconds; default, as above
+// Request orders (wn_server_set_order).  Measured on the serving bench (1,000 requests at 70 % load),
+// p99 of the requests of 20 ms or more / of the others, against 0.48 s / 0.47 s one at a time:
+//  * arrival order (the default): 0.47 s / 0.43 s (overall p99 0.45 s, p50 24 ms against 35 ms);
+//  * small requests first, large ones least work first with the 1 s wait limit: 0.93 s / 0.09 s
+//    (overall p99 0.27 s, p50 8 ms); with a 0.3 s wait limit 0.54-0.59 s / 0.09 s.
 constexpr double kEvalRate = 3.0e12;    // component-visibility evaluations per second (estimate)
 
 struct ServeReq {
@@ -98,6 +101,7 @@ struct wn_server {
   int max_rows = 0, max_chan = 0;
   int max_large_inflight = wn::kMaxLargeInFlight;  // admission policy (wn_server_set_policy)
   double max_large_wait = wn::kMaxLargeWait;
+  int order = WN_SERVE_ARRIVAL;                    // request order (wn_server_set_order)
   char* pool = nullptr;
   size_t pool_bytes = 0;
   std::map<size_t, size_t> free_list;  // offset -> size
@@ -211,9 +215,12 @@ static bool is_large(const ServeReq& r) { return r.tiles > 0 && large_cost(r) > 
 // An admitted request that no launch has taken yet.
 static bool unstarted(const ServeReq& r) { return r.state == RQ_ADMITTED && r.issued == 0 && r.owner_slot < 0; }
 
-static bool small_waiting(wn_server* s) {
-  for (auto& kv : s->reqs)
+// A small request submitted before ticket `bar` (all of them when bar is UINT64_MAX) waits for a launch.
+static bool small_waiting(wn_server* s, uint64_t bar) {
+  for (auto& kv : s->reqs) {
+    if (kv.first >= bar) break;
     if (unstarted(kv.second) && !is_large(kv.second)) return true;
+  }
   return false;
 }
 
@@ -259,18 +266,21 @@ static int launch_steps(wn_server* s, int k, ServeReq& r, int t0, int steps) {
   return rc;
 }
 
-// Launch on slot k the next chunk of the large request the slot owns: its next time steps, about
-// kBatchBudget of estimated work and at least two waves of the phasor kernel's row tiles (32 rows, one
-// CTA per SM) so that a chunk fills the GPU.  The last chunk completes the request.  Called with the
-// lock held; the slot is idle.
+// Launch on slot k the next chunk of the large request the slot owns.  In arrival order the chunk is the
+// whole request; small-first, it is its next time steps, about kBatchBudget of estimated work and at
+// least two waves of the phasor kernel's row tiles (32 rows, one CTA per SM) so that a chunk fills the
+// GPU.  The last chunk completes the request.  Called with the lock held; the slot is idle.
 static void launch_chunk(wn_server* s, int k) {
   ServeSlot& sl = s->slots[k];
   ServeReq& r = s->reqs[sl.owner];
   std::vector<uint64_t> complete;
   const int T = r.od.n_time, B = r.od.n_base;
-  const double per_step = large_cost(r) / T;
-  const int min_steps = (2 * 32 * s->ctx->num_sms + B - 1) / B;
-  const int steps = std::max(1, std::min(T - r.t_next, std::max(min_steps, (int)(kBatchBudget / std::max(per_step, 1e-12)))));
+  int steps = T - r.t_next;
+  if (s->order == WN_SERVE_SMALL_FIRST) {
+    const double per_step = large_cost(r) / T;
+    const int min_steps = (2 * 32 * s->ctx->num_sms + B - 1) / B;
+    steps = std::max(1, std::min(steps, std::max(min_steps, (int)(kBatchBudget / std::max(per_step, 1e-12)))));
+  }
   const int t0 = r.t_next;
   const int rc = launch_steps(s, k, r, t0, steps);
   r.issued = 1;
@@ -312,10 +322,10 @@ static void launch_solo(wn_server* s, int k, ServeReq& r) {
   finish_launch(s, k, std::vector<uint64_t>{r.ticket}, cudaSuccess);
 }
 
-// Launch on slot k one batch of small unstarted requests, in ticket order, up to kBatchBudget of
-// estimated work (the first always goes), or the first of them alone when it is a solo request.
-// Called with the lock held.
-static void launch_small(wn_server* s, int k) {
+// Launch on slot k one batch of small unstarted requests submitted before ticket `bar`, in ticket order,
+// up to kBatchBudget of estimated work (the first always goes), or the first of them alone when it is a
+// solo request.  Called with the lock held.
+static void launch_small(wn_server* s, int k, uint64_t bar) {
   ServeSlot& sl = s->slots[k];
   K1Args* args = slot_args(s, sl);
   K1Work* work = slot_work(s, sl);
@@ -324,6 +334,7 @@ static void launch_small(wn_server* s, int k) {
   double budget = kBatchBudget;
   for (auto& kv : s->reqs) {
     ServeReq& r = kv.second;
+    if (kv.first >= bar) break;
     if (!unstarted(r) || is_large(r)) continue;
     if (is_solo(s, r)) {
       if (!complete.empty()) continue;  // it takes a slot of its own
@@ -348,25 +359,44 @@ static void launch_small(wn_server* s, int k) {
   if (!complete.empty()) launch_slot(s, k, nwork, complete, shapes);
 }
 
-// Fill the free slots.  Large requests claim the lowest-priority free slots (at most max_large_inflight,
-// and never the last free one, so small requests always have a stream) and issue their chunks back to
-// back; small batches take the other free slots, one batch at a time while a large request runs.
+// Fill the free slots (slot 0 has the highest stream priority).
+//  * Arrival order: large requests start in submission order.  One that is due takes the
+//    highest-priority free slot, waits for the small requests submitted before it to be launched and
+//    to finish, and then runs in one launch; small requests submitted after it wait until it has
+//    started.  Small batches take the lowest-priority free slots, whose blocks the GPU dispatches after
+//    a running large request's, one batch at a time while a large request runs.
+//  * Small first: small batches take the highest-priority free slots as soon as there is work, one
+//    batch at a time while a large request runs; large requests take the lowest-priority free slots,
+//    least estimated work first with the wait limit, and run in chunks back to back.
+// At most max_large_inflight large requests hold a slot, never the last free one.
 static bool launch_ready(wn_server* s) {
   bool progress = false;
+  const bool arrival = s->order == WN_SERVE_ARRIVAL;
   const int ns = (int)s->slots.size();
+  auto free_slot = [&](bool highest) {
+    for (int j = 0; j < ns; ++j) {
+      const int k = highest ? j : ns - 1 - j;
+      if (!s->slots[k].busy && !s->slots[k].owner) return k;
+    }
+    return -1;
+  };
   int owners = 0;
   for (auto& sl : s->slots) owners += sl.owner ? 1 : 0;
   const double t_now = now_s(s);
   while (owners < std::min(s->max_large_inflight, std::max(1, ns - 1))) {
-    int k = ns - 1;
-    while (k >= 0 && (s->slots[k].busy || s->slots[k].owner)) --k;
+    const int k = free_slot(arrival);
     if (k < 0) break;
-    // the oldest request past the wait limit, else the least estimated work (ties: ticket order)
+    // arrival order: the first submitted; small first: the oldest request past the wait limit, else
+    // the least estimated work (ties: ticket order)
     ServeReq* pick = nullptr;
     bool pick_old = false;
     for (auto& kv : s->reqs) {
       ServeReq& q = kv.second;
       if (!unstarted(q) || !is_large(q)) continue;
+      if (arrival) {
+        pick = &q;
+        break;
+      }
       const bool old = t_now - q.t_submit > s->max_large_wait;
       if (pick_old && !old) continue;
       if (!pick || (old && !pick_old) || (!old && large_cost(q) < large_cost(*pick))) {
@@ -381,24 +411,43 @@ static bool launch_ready(wn_server* s) {
     s->slots[k].owner = r.ticket;
     ++owners;
   }
-  // while a large request runs, small batches go out one at a time (they keep batching while it runs)
   int small_busy = 0;
   for (auto& sl : s->slots) small_busy += (sl.busy && !sl.owner) ? 1 : 0;
-
-  for (int k = 0; k < ns; ++k) {
-    ServeSlot& sl = s->slots[k];
-    if (sl.busy || sl.owner || !small_waiting(s)) continue;
-    if (owners > 0 && small_busy >= 1) break;
-    launch_small(s, k);
+  // arrival order: small requests submitted after a large request that holds a slot but has not started
+  // wait for it
+  uint64_t bar = UINT64_MAX;
+  if (arrival)
+    for (auto& sl : s->slots)
+      if (sl.owner) {
+        auto it = s->reqs.find(sl.owner);
+        if (it != s->reqs.end() && it->second.issued == 0) bar = std::min(bar, sl.owner);
+      }
+  while (small_waiting(s, bar)) {
+    // while a large request runs, small batches go out one at a time (they keep batching while it runs)
+    if (bar == UINT64_MAX && owners > 0 && small_busy >= 1) break;
+    const int k = free_slot(!arrival);
+    if (k < 0) break;
+    launch_small(s, k, bar);
     ++small_busy;
     progress = true;
   }
   for (int k = 0; k < ns; ++k) {
-    ServeSlot& sl = s->slots[k];
-    if (sl.busy || !sl.owner) continue;
-    auto it = s->reqs.find(sl.owner);
+    if (s->slots[k].busy || !s->slots[k].owner) continue;
+    auto it = s->reqs.find(s->slots[k].owner);
     if (it == s->reqs.end() || it->second.owner_slot != k) continue;
-    launch_chunk(s, k);
+    int kk = k;
+    if (arrival && it->second.issued == 0) {
+      // the small requests submitted before it go first; then it moves to the highest-priority free slot
+      if (small_busy > 0 || small_waiting(s, it->first)) continue;
+      const int j = free_slot(true);
+      if (j >= 0 && j < k) {
+        s->slots[j].owner = it->first;
+        s->slots[k].owner = 0;
+        it->second.owner_slot = j;
+        kk = j;
+      }
+    }
+    launch_chunk(s, kk);
     progress = true;
   }
   return progress;
@@ -706,6 +755,17 @@ int wn_server_cancel(wn_server* s, uint64_t ticket) {
   if (it == s->reqs.end()) return set_error(WN_ENOTFOUND, "unknown ticket");
   if (it->second.state != RQ_PENDING) return set_error(WN_EBUSY, "request already admitted");
   it->second.state = RQ_CANCELLED;
+  return WN_OK;
+}
+
+int wn_server_set_order(wn_server* s, int order) {
+  if (!s) return set_error(WN_EINVAL, "NULL argument");
+  if (order != WN_SERVE_ARRIVAL && order != WN_SERVE_SMALL_FIRST) return set_error(WN_EINVAL, "unknown request order");
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->order = order;
+  }
+  s->cv.notify_all();
   return WN_OK;
 }
 

@@ -16,6 +16,7 @@ import numpy as np
 from . import Context, DeviceObs, Model, _check, load
 
 REQ_PENDING, REQ_ADMITTED, REQ_RUNNING, REQ_DONE, REQ_CANCELLED, REQ_FAILED = range(6)
+SERVE_ARRIVAL, SERVE_SMALL_FIRST = 0, 1   # request orders (wn_server_set_order)
 
 
 @dataclass
@@ -97,10 +98,16 @@ class Server:
         _check(load().wn_server_cancel(self.h, ticket))
 
     def set_policy(self, max_large_inflight: int = 1, max_large_wait_s: float = 1.0):
-        """Admission of large (chunked) requests: how many own a slot at once, and after how many
-        seconds of waiting one starts ahead of any younger one (least estimated work first otherwise;
-        0 gives submission order)."""
+        """Admission of large requests: how many own a slot at once, and (small-first order) after how
+        many seconds of waiting one starts ahead of any younger one (least estimated work first
+        otherwise; 0 gives submission order)."""
         _check(load().wn_server_set_policy(self.h, int(max_large_inflight), float(max_large_wait_s)))
+
+    def set_order(self, order: int = SERVE_ARRIVAL):
+        """Request order: SERVE_ARRIVAL (default; submission order, small requests batched, large ones in
+        one launch on the highest-priority stream) or SERVE_SMALL_FIRST (small requests first, large
+        ones in time-step chunks)."""
+        _check(load().wn_server_set_order(self.h, int(order)))
 
     def stats(self) -> dict:
         v = (ctypes.c_double * 6)()

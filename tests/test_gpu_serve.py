@@ -150,10 +150,10 @@ def test_cancel_and_bounded_wait(wn, ctx):
 
 @pytest.mark.parametrize("peel", [False, True])
 def test_large_request_in_time_step_chunks(wn, ctx, peel):
-    """A request above the batch work budget is served in chunks of whole time steps through the
-    single-request kernels (each chunk applies the request's mode to its own rows, per-step data and
-    gains offset to them); its result matches the single call."""
-    from paper_2005_09316_b300.serve import Server
+    """Small-first order: a request above the batch work budget is served in chunks of whole time steps
+    through the single-request kernels (each chunk applies the request's mode to its own rows, per-step
+    data and gains offset to them); its result matches the single call."""
+    from paper_2005_09316_b300.serve import SERVE_SMALL_FIRST, Server
     obs = synth.make_obs(71, 128, 5, synth.uniform_channels(167e6, 80e3, 384), layout="mwa")
     sky = synth.make_sky(72, 16000, 4000, 1, fov=15 * synth.DEG, shape_nmax=20)
     d = wn.obs_to_device(obs)
@@ -164,6 +164,7 @@ def test_large_request_in_time_step_chunks(wn, ctx, peel):
         data = torch.randn(obs.n_time, obs.n_base, obs.n_chan, dtype=torch.complex64, device="cuda",
                            generator=torch.Generator(device="cuda").manual_seed(74))
     srv = Server(ctx, n_streams=2, pool_bytes=1 << 30, max_inflight=4, max_rows=obs.n_rows, max_chan=384)
+    srv.set_order(SERVE_SMALL_FIRST)
     t = srv.submit(d, m, gains, data)
     assert srv.wait(t, 120).state == 3
     got = srv.result_tensor(t, d).cpu().numpy()
@@ -178,15 +179,16 @@ def test_large_request_in_time_step_chunks(wn, ctx, peel):
 
 
 def test_large_requests_start_least_work_first(wn, ctx):
-    """Queued large requests start in order of estimated work, least first (one at a time here): with a
-    large request running, a larger one and then a smaller one are submitted; the smaller starts first.
-    Each result still matches the single call."""
-    from paper_2005_09316_b300.serve import Server
+    """Small-first order: queued large requests start in order of estimated work, least first (one at a
+    time here): with a large request running, a larger one and then a smaller one are submitted; the
+    smaller starts first.  Each result still matches the single call."""
+    from paper_2005_09316_b300.serve import SERVE_SMALL_FIRST, Server
     obs = synth.make_obs(81, 128, 4, synth.uniform_channels(167e6, 80e3, 384), layout="mwa")
     d = wn.obs_to_device(obs)
     models = [ctx.upload(synth.make_sky(82 + i, n * 4 // 5, n // 5, 0, fov=15 * synth.DEG))
               for i, n in enumerate((20000, 20000, 8000))]
     srv = Server(ctx, n_streams=2, pool_bytes=1 << 30, max_inflight=4, max_rows=obs.n_rows, max_chan=384)
+    srv.set_order(SERVE_SMALL_FIRST)
     tickets = [srv.submit(d, m) for m in models]   # running, then larger, then smaller
     res = [srv.wait(t, 120) for t in tickets]
     assert all(r.state == 3 for r in res)
@@ -203,10 +205,10 @@ def test_large_requests_start_least_work_first(wn, ctx):
 
 
 def test_policy_with_no_age_limit_starts_large_requests_in_submission_order(wn, ctx):
-    """With the wait limit at 0 every queued large request counts as overdue, so they start in
-    submission order: the same submissions as above, and now the larger (earlier) one starts first.
-    Values outside the documented ranges are refused."""
-    from paper_2005_09316_b300.serve import Server
+    """Small-first order with the wait limit at 0: every queued large request counts as overdue, so they
+    start in submission order: the same submissions as above, and now the larger (earlier) one starts
+    first.  Values outside the documented ranges are refused."""
+    from paper_2005_09316_b300.serve import SERVE_SMALL_FIRST, Server
     obs = synth.make_obs(81, 128, 4, synth.uniform_channels(167e6, 80e3, 384), layout="mwa")
     d = wn.obs_to_device(obs)
     models = [ctx.upload(synth.make_sky(82 + i, n * 4 // 5, n // 5, 0, fov=15 * synth.DEG))
@@ -215,6 +217,7 @@ def test_policy_with_no_age_limit_starts_large_requests_in_submission_order(wn, 
     for bad in ((0, 1.0), (17, 1.0), (1, -1.0), (1, float("nan"))):
         with pytest.raises(wn.WnError):
             srv.set_policy(*bad)
+    srv.set_order(SERVE_SMALL_FIRST)
     srv.set_policy(1, 0.0)
     tickets = [srv.submit(d, m) for m in models]
     res = [srv.wait(t, 120) for t in tickets]
@@ -311,27 +314,65 @@ def test_mixed_stream_matches_oracle(wn, ctx):
 @pytest.mark.parametrize("peel", [False, True])
 def test_large_request_in_time_step_chunks_matches_oracle(wn, ctx, peel):
     """A request above the batch work budget (128 tiles x 3 steps x 384 ch, 16,000 P + 4,000 G + one
-    n_max 20 shapelet), served in chunks of time steps, with five small requests submitted behind it:
-    every result equals the oracle's on sampled rows."""
-    from paper_2005_09316_b300.serve import Server
+    n_max 20 shapelet) with five small requests submitted behind it, in both request orders (served in
+    chunks of time steps small-first, in one launch in arrival order): every result equals the oracle's
+    on sampled rows."""
+    from paper_2005_09316_b300.serve import SERVE_ARRIVAL, SERVE_SMALL_FIRST, Server
     big = _host_request(wn, ctx, 71, 128, 3, 384, 20000, [20], peel)
     small = [_host_request(wn, ctx, 700 + 10 * i, 24, 2, 64, 400, [8] if i == 2 else [], peel=bool(i % 2))
              for i in range(5)]
-    srv = Server(ctx, n_streams=3, pool_bytes=1 << 30, max_inflight=8, max_rows=big["obs"].n_rows, max_chan=384)
-    tickets = [srv.submit(r["d"], r["m"], r["gd"], r["dd"]) for r in [big] + small]
-    for t in tickets:
-        assert srv.wait(t, 120).state == 3
-    st = srv.stats()
-    assert st["batches"] >= 3, st            # the large request ran in several launches
-    _check_against_oracle(srv, tickets[0], big, n_rows=10, seed=1)
-    for i, (t, r) in enumerate(zip(tickets[1:], small)):
-        _check_against_oracle(srv, t, r, seed=2 + i)
-    for t in tickets:
-        srv.release(t)
-    srv.close()
+    for order in (SERVE_SMALL_FIRST, SERVE_ARRIVAL):
+        srv = Server(ctx, n_streams=3, pool_bytes=1 << 30, max_inflight=8, max_rows=big["obs"].n_rows,
+                     max_chan=384)
+        srv.set_order(order)
+        tickets = [srv.submit(r["d"], r["m"], r["gd"], r["dd"]) for r in [big] + small]
+        for t in tickets:
+            assert srv.wait(t, 120).state == 3
+        st = srv.stats()
+        batches = [srv.poll(t).batch for t in tickets]
+        if order == SERVE_SMALL_FIRST:
+            assert st["batches"] >= 3, st                     # the large request ran in several launches
+        else:
+            assert batches.count(batches[0]) == 1, batches    # the large request: a launch of its own
+        _check_against_oracle(srv, tickets[0], big, n_rows=10, seed=1)
+        for i, (t, r) in enumerate(zip(tickets[1:], small)):
+            _check_against_oracle(srv, t, r, seed=2 + i)
+        for t in tickets:
+            srv.release(t)
+        srv.close()
     assert ctx.device_errors() == 0
     for r in [big] + small:
         r["m"].free()
+
+
+def test_arrival_order_starts_large_requests_in_submission_order(wn, ctx):
+    """The default (arrival) order: with a large request running, a larger one and then a smaller one are
+    submitted, and they start in submission order whatever their size, each in one launch; results match
+    the single call.  An unknown order is refused."""
+    from paper_2005_09316_b300.serve import Server
+    obs = synth.make_obs(81, 128, 4, synth.uniform_channels(167e6, 80e3, 384), layout="mwa")
+    d = wn.obs_to_device(obs)
+    models = [ctx.upload(synth.make_sky(82 + i, n * 4 // 5, n // 5, 0, fov=15 * synth.DEG))
+              for i, n in enumerate((20000, 20000, 8000))]
+    srv = Server(ctx, n_streams=2, pool_bytes=1 << 30, max_inflight=4, max_rows=obs.n_rows, max_chan=384)
+    for bad in (-1, 2):
+        with pytest.raises(wn.WnError):
+            srv.set_order(bad)
+    tickets = [srv.submit(d, m) for m in models]
+    res = [srv.wait(t, 120) for t in tickets]
+    assert all(r.state == 3 for r in res)
+    got = [srv.result_tensor(t, d).cpu().numpy() for t in tickets]
+    for t in tickets:
+        srv.release(t)
+    st = srv.stats()
+    srv.close()
+    assert res[0].t_launch <= res[1].t_launch < res[2].t_launch, [(r.t_submit, r.t_launch) for r in res]
+    assert st["batches"] == 3, st
+    for g, m in zip(got, models):
+        assert e_norm(g, ctx.predict(d, m).cpu().numpy()) <= 1e-5
+    assert ctx.device_errors() == 0
+    for m in models:
+        m.free()
 
 
 def test_solo_requests_run_alone_and_match_the_oracle(wn, ctx):
