@@ -13,18 +13,19 @@
 //  * overlap: there are n_streams batch slots; requests that arrive while batches are on the GPU are
 //    admitted as memory and slots free up and go out in the next batch on a free stream, so their
 //    work overlaps the batches in flight;
-//  * time slicing: a batch carries at most ~kBatchBudget of estimated GPU work; a request larger than
-//    that takes the lowest-priority free stream and runs there in chunks of whole time steps (about
-//    kBatchBudget each and at least two waves of the phasor kernel, back to back) through the
-//    single-request kernels, the table-form phasor kernel
-//    and the shapelet kernel, with that stream's own workspaces: the same work the request does alone.
-//    While it runs, small requests go out one batch at a time on another stream, so the ones that
-//    arrive meanwhile are packed into the next batch;
+//  * large requests: a batch carries at most ~kBatchBudget of estimated GPU work; a request larger than
+//    that runs on a stream of its own through the single-request kernels (the table-form phasor kernel
+//    and the shapelet kernel, with that stream's own workspaces: the same work the request does alone).
+//    In arrival order (the default) large requests start in submission order, each after the small
+//    requests submitted before it, in one launch on the highest-priority stream; small-first, they run
+//    on the lowest-priority stream in chunks of whole time steps so that small requests keep flowing
+//    (launch_ready).  While one runs, small requests go out one batch at a time on another stream, so
+//    the ones that arrive meanwhile are packed into the next batch;
 //  * completion: an event per batch, polled without blocking; the caller reads the result in place
 //    and releases it, which returns its pool space.
 // A batched tile is computed by the same code in the same order as a single-request launch of the
-// batched kernel's form, and a chunk of a large request by the single-request kernels on its rows, so
-// a request's result does not depend on what it was batched with.
+// batched kernel's form, and a large request (or a chunk of it) by the single-request kernels on its
+// rows, so a request's result does not depend on what it was batched with.
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -50,7 +51,7 @@ constexpr int kMaxLargeInFlight = 1;  // default; wn_server_set_policy changes i
 constexpr double kMaxLargeWait = 1.0;  // seconds; default, as above
 // Request orders (wn_server_set_order).  Measured on the serving bench (1,000 requests at 70 % load),
 // p99 of the requests of 20 ms or more / of the others, against 0.48 s / 0.47 s one at a time:
-//  * arrival order (the default): 0.47 s / 0.43 s (overall p99 0.45 s, p50 24 ms against 35 ms);
+//  * arrival order (the default): 0.47 s / 0.42-0.43 s (overall p99 0.44 s, p50 26 ms against 35 ms);
 //  * small requests first, large ones least work first with the 1 s wait limit: 0.93 s / 0.09 s
 //    (overall p99 0.27 s, p50 8 ms); with a 0.3 s wait limit 0.54-0.59 s / 0.09 s.
 constexpr double kEvalRate = 3.0e12;    // component-visibility evaluations per second (estimate)
