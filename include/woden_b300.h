@@ -201,8 +201,11 @@ WN_API int wn_sky_bytes(wn_ctx* ctx, int model_id, size_t* bytes_out);
 /* The packed coefficient operand of shapelet q of a resident model, copied to HOST memory (no paper
  * counterpart; for checking the packer).  It holds bf16 hi then lo, k_pad x n_pad each, in the tcgen05
  * canonical K-major layout without swizzle: element (n, k) (n = 2 n2 + {0: Re, 1: Im} of
- * C[n1, n2] (-i)^(n1+n2), k = n1) at ((k/8) (n_pad/8) + n/8) 64 + (n%8) 8 + k%8; hi = RN(float(value)),
- * lo = RN(float(value) - hi).  k_pad and n_pad follow the highest order n1 + n2 the coefficients reach.
+ * C[n1, n2] (-i)^(n1+n2) / (k_n1 k_n2), k = n1) at ((k/8) (n_pad/8) + n/8) 64 + (n%8) 8 + k%8;
+ * hi = RN(float(value)), lo = RN(float(value) - hi), the value formed in FP64.  k_0 = k_1 = 1 and
+ * k_(n+1) = k_(n-1) sqrt((n+1)/n) (each step correctly rounded in FP64) are the scales of the Hermite
+ * functions g_n = k_n phi_n the contraction runs on (their recurrence takes two operations per order).
+ * k_pad and n_pad follow the highest order n1 + n2 the coefficients reach.
  * host_out may be NULL to query k_pad and n_pad; otherwise it must hold bytes >= 4 k_pad n_pad.
  * Synchronous.  WN_ENOTFOUND for an unknown model, WN_EINVAL for q outside [0, n_shape) or a short
  * buffer. */

@@ -18,6 +18,7 @@ routines, brute-force DFTs or finite differences; none is left unpinned.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -232,6 +233,34 @@ def parity_split(nmax, n1, n2, c):
     return re, im
 
 
+def herm_k(n: int) -> float:
+    """Scale k_n of the rescaled Hermite functions g_n = k_n phi_n that the device's contraction runs on:
+    k_0 = k_1 = 1 and k_(n+1) = k_(n-1) sqrt((n+1)/n), which turns the normalised recurrence
+    phi_(n+1) = sqrt(2/(n+1)) x phi_n - sqrt(n/(n+1)) phi_(n-1) into g_(n+1) = e_n x g_n - g_(n-1) with
+    e_n = sqrt(2/(n+1)) k_(n+1) / k_n.  Formed in FP64 in this order (each step correctly rounded), as
+    the device forms it."""
+    km, k = 1.0, 1.0
+    for m in range(1, n):
+        kn = km * math.sqrt((m + 1) / m)
+        km, k = k, kn
+    return k
+
+
+def operand_dense(nmax: int, n1, n2, c, k_pad: int, n_pad: int) -> np.ndarray:
+    """The coefficient operand's values [n_pad][k_pad] in FP64: row 2*n2 holds Re(C (-i)^(n1+n2)) and row
+    2*n2+1 the imaginary part, over n1 (the K index), each divided by k_n1 k_n2 (herm_k) so that the
+    contraction with the rescaled functions g gives sum phi C phi; zero padding."""
+    re, im = parity_split(nmax, n1, n2, c)
+    k = np.array([herm_k(n) for n in range(nmax + 1)])
+    kk = k[:, None] * k[None, :]
+    re, im = re / kk, im / kk
+    dense = np.zeros((n_pad, k_pad))
+    for b in range(nmax + 1):
+        dense[2 * b, :nmax + 1] = re[:, b]
+        dense[2 * b + 1, :nmax + 1] = im[:, b]
+    return dense
+
+
 def f32_to_bf16_bits(x32: np.ndarray) -> np.ndarray:
     """Round-to-nearest-even float32 -> bfloat16 bit patterns (finite inputs)."""
     u = np.asarray(x32, dtype=np.float32).view(np.uint32).astype(np.uint64)
@@ -262,11 +291,7 @@ def f32_to_tf32_bits(x32) -> np.ndarray:
 def pack_coeff_tf32(nmax: int, n1, n2, c, k_pad: int, n_pad: int) -> np.ndarray:
     """The dense B operand of pack_coeff_bf16 as tf32 bit patterns [n_pad][k_pad] (one element per entry,
     RN_tf32(float32(value))), for the tensor-core tf32 mode."""
-    re, im = parity_split(nmax, n1, n2, c)
-    dense = np.zeros((n_pad, k_pad))
-    for b in range(nmax + 1):
-        dense[2 * b, :nmax + 1] = re[:, b]
-        dense[2 * b + 1, :nmax + 1] = im[:, b]
+    dense = operand_dense(nmax, n1, n2, c, k_pad, n_pad)
     return f32_to_tf32_bits(dense.astype(np.float32))
 
 
@@ -278,25 +303,16 @@ def pack_coeff_tf32x3(nmax: int, n1, n2, c, k_pad: int, n_pad: int):
     """The split tf32 operand pair [n_pad][k_pad] as bit patterns: hi = RN_tf32(float32(value)) and
     lo = RN_tf32(float32(value) - hi), the difference taken in float32 (where it is exact)."""
     hi = pack_coeff_tf32(nmax, n1, n2, c, k_pad, n_pad)
-    re, im = parity_split(nmax, n1, n2, c)
-    dense = np.zeros((n_pad, k_pad))
-    for b in range(nmax + 1):
-        dense[2 * b, :nmax + 1] = re[:, b]
-        dense[2 * b + 1, :nmax + 1] = im[:, b]
-    d32 = dense.astype(np.float32)
+    d32 = operand_dense(nmax, n1, n2, c, k_pad, n_pad).astype(np.float32)
     lo = f32_to_tf32_bits((d32 - tf32_bits_to_f32(hi)).astype(np.float32))
     return hi, lo
 
 
 def pack_coeff_bf16(nmax: int, n1, n2, c, k_pad: int, n_pad: int):
-    """Dense B operand of the shapelet contraction, as bf16 hi/lo bit patterns [n_pad][k_pad]:
-    row 2*n2 holds Re(C (-i)^(n1+n2))[n1, n2] over n1 (the K index), row 2*n2+1 the imaginary part."""
-    re, im = parity_split(nmax, n1, n2, c)
-    dense = np.zeros((n_pad, k_pad))
-    for b in range(nmax + 1):
-        dense[2 * b, :nmax + 1] = re[:, b]
-        dense[2 * b + 1, :nmax + 1] = im[:, b]
-    return bf16_hi_lo(dense)
+    """Dense B operand of the shapelet contraction, as bf16 hi/lo bit patterns [n_pad][k_pad] of
+    operand_dense: row 2*n2 holds Re(C (-i)^(n1+n2))[n1, n2] / (k_n1 k_n2) over n1 (the K index), row
+    2*n2+1 the imaginary part."""
+    return bf16_hi_lo(operand_dense(nmax, n1, n2, c, k_pad, n_pad))
 
 
 # ------------------------------------------------------------------------------------------------

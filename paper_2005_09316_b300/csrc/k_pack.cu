@@ -73,12 +73,13 @@ __global__ void k_pack_shape(wn_sky s, const int* b_off, const int* k_pad, const
 }
 
 // Dense B operand of the shapelet contraction: column n = 2*n2 + {0: real, 1: imaginary} of
-// C[n1,n2] (-i)^(n1+n2) (eq:shape-env with the phase of eq:basis_FT), row k = n1, stored as bf16
-// hi = RN(float(C)), lo = RN(float(C) - hi) in the tcgen05 canonical K-major layout without swizzle:
+// C[n1,n2] (-i)^(n1+n2) / (k_n1 k_n2) (eq:shape-env with the phase of eq:basis_FT; k_n = herm_k, the
+// scale of the rescaled Hermite functions the contraction runs on), row k = n1, stored as bf16
+// hi = RN(float(C')), lo = RN(float(C') - hi) in the tcgen05 canonical K-major layout without swizzle:
 // 8x8 core matrices, element (n, k) at ((k/8) * (n_pad/8) + n/8) * 64 + (n%8) * 8 + k%8.  A tf32 copy goes
 // to bop32 in the same layout with 8x4 core matrices of 4-byte elements, element (n, k) at
-// ((k/4) * (n_pad/8) + n/8) * 32 + (n%8) * 4 + k%4: hi = RN_tf32(float(C)) at the shapelet's b_off, then
-// lo = RN_tf32(float(C) - hi) (the difference is exact in FP32) k_pad * n_pad elements further.
+// ((k/4) * (n_pad/8) + n/8) * 32 + (n%8) * 4 + k%4: hi = RN_tf32(float(C')) at the shapelet's b_off, then
+// lo = RN_tf32(float(C') - hi) (the difference is exact in FP32) k_pad * n_pad elements further.
 __global__ void k_pack_coeff(int nnz_total, const int* n1, const int* n2, const double* c, const int* s_off,
                              const int* s_nmax, int n_shape, const int* b_off, const int* k_pad, const int* n_pad,
                              __nv_bfloat16* bop, float* bop32, unsigned* err) {
@@ -92,7 +93,7 @@ __global__ void k_pack_coeff(int nnz_total, const int* n1, const int* n2, const 
     return;
   }
   int kk = (a + b) & 3;
-  float v = (float)c[t];
+  const float v = (float)(c[t] / (herm_k(a) * herm_k(b)));
   float re = kk == 0 ? v : (kk == 2 ? -v : 0.0f);
   float im = kk == 1 ? -v : (kk == 3 ? v : 0.0f);
   int np = n_pad[q], kp = k_pad[q];

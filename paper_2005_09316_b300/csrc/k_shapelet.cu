@@ -40,6 +40,9 @@
 
 namespace wn {
 
+// e_n = sqrt(2/(n+1)) k_(n+1)/k_n of the rescaled Hermite recurrence (herm_k), uploaded at context creation
+__constant__ float c_k2e[kNmaxLimit + 1];
+
 constexpr int K2_M = 128;
 constexpr int K2_GROUPS = 2;                     // tile parities in flight
 constexpr int K2_THREADS = 32 * (8 * K2_GROUPS + 1);
@@ -112,8 +115,8 @@ __host__ __device__ inline K2Layout k2_layout(int b_total, int kp, int passes, i
   K2Layout L;
   L.a_bytes = R * k2_parts(passes, tf32) * kp * K2_M * 2;  // one group's A: R blocks of 128 rows (hi [+ lo])
   L.a0 = (b_total + 1023) & ~1023;
-  L.coef = L.a0 + groups * L.a_bytes;  // recurrence coefficients a_n, b_n: 2 x 128 floats, then the
-                                       // quadruples {a_n, a_n, -b_n, -b_n} for two rows at once
+  L.coef = L.a0 + groups * L.a_bytes;  // recurrence constants e_n (128 floats, then 128 unused), then
+                                       // the quadruples {e_n, e_n, 0, 0} for two rows at once
   L.shp = L.coef + 2 * (kNmaxLimit + 1) * 4 + (kNmaxLimit + 1) * 16;
   L.bars = L.shp + K2_MAXS * (int)sizeof(K2Shape);
   L.xfer = L.bars + 128;  // barriers (1 + 5 per parity) and the TMEM address slot
@@ -160,12 +163,14 @@ __device__ __forceinline__ void store_row8(float (&v)[8], unsigned char* hi, int
   else store_bf16_split(v, hi, split ? hi + lo_off : nullptr, kmaj_off(row, k0, K2_M));
 }
 
-// Hermite functions phi_0..phi_{kp-1}(x) by the normalised recurrence, written as bf16 hi (and lo) or
-// tf32 into row `row` of the K-major tile(s).  Values past nmax meet zero rows of the coefficient
-// operand; they only need to be finite.  For |x| <= 12.5 every value stays in the normal FP32 range
-// (phi_0 >= e^-78, |phi_n| <~ 1) and no scaling is needed.  Beyond that phi_0 = e^{-x^2/2} underflows
-// FP32: the recurrence runs on values scaled by 2^E (E lowered by 64 whenever they pass 2^64) and is
-// scaled back on output.  Beyond xcut every phi_n, n <= nmax, is below 1e-20 and the row is zero.
+// Rescaled Hermite functions g_n = k_n phi_n, n = 0..kp-1 (herm_k: k_n in [1, 4]; the coefficient operand
+// carries 1/(k_n1 k_n2)), by the two-operation recurrence g_(n+1) = e_n x g_n - g_(n-1) from g_0 = phi_0,
+// written as bf16 hi (and lo) or tf32 into row `row` of the K-major tile(s).  Values past nmax meet zero
+// rows of the coefficient operand; they only need to be finite.  For |x| <= 12.5 every value stays in
+// the normal FP32 range (phi_0 >= e^-78, |g_n| <~ 4) and no scaling is needed.  Beyond that
+// phi_0 = e^{-x^2/2} underflows FP32: the recurrence runs on values scaled by 2^E (E lowered by 64
+// whenever they pass 2^64) and is scaled back on output.  Beyond xcut every phi_n, n <= nmax, is below
+// 1e-20 and the row is zero.
 
 // Seed of one row: p = phi_0 2^E (E = 0 on the unscaled path), sc = 2^-E (0 below 2^-126).
 __device__ __forceinline__ void herm_seed(float x, bool zero, bool fast, float& p, int& E, float& sc) {
@@ -186,7 +191,7 @@ __device__ __forceinline__ void herm_rescale(float& p, float& pp, int& E, float&
   }
 }
 
-// Two rows as one f32x2 recurrence: {p_r0, p_r1}' = {a,a} {x0,x1} {p_r0,p_r1} + {-b,-b} {p'_r0,p'_r1}.
+// Two rows as one f32x2 recurrence: {g_r0, g_r1}' = {e,e} {x0,x1} {g_r0,g_r1} - {g'_r0,g'_r1}.
 template <bool SCALED, bool TF32>
 __device__ __forceinline__ void produce2_run(float2 X, float2 P, float2 Sc, int E0, int E1, int kp, unsigned char* a_base,
                                              int blk, int lo_off, bool split, int row, const float4* cab) {
@@ -200,7 +205,7 @@ __device__ __forceinline__ void produce2_run(float2 X, float2 P, float2 Sc, int 
       v[0][i] = w.x;
       v[1][i] = w.y;
       const float4 c = cab[k0 + i];
-      const float2 Pn = __ffma2_rn(__fmul2_rn(make_float2(c.x, c.y), X), P, __fmul2_rn(make_float2(c.z, c.w), Pp));
+      const float2 Pn = __ffma2_rn(__fmul2_rn(make_float2(c.x, c.y), X), P, make_float2(-Pp.x, -Pp.y));
       Pp = P;
       P = Pn;
     }
@@ -213,21 +218,20 @@ __device__ __forceinline__ void produce2_run(float2 X, float2 P, float2 Sc, int 
   }
 }
 
-// One row, scalar recurrence (coefficients four at a time from shared memory).
+// One row, scalar recurrence (the constants e_n four at a time from shared memory).
 template <bool SCALED, bool TF32>
 __device__ __forceinline__ void produce1_run(float x, float p, float sc, int E, int kp, unsigned char* a_base, int lo_off,
-                                             bool split, int row, const float4* ca, const float4* cb) {
+                                             bool split, int row, const float4* ca) {
   float pp = 0.f;
 #pragma unroll 1
   for (int k0 = 0; k0 < kp; k0 += 8) {
-    const float4 A0 = ca[k0 >> 2], A1 = ca[(k0 >> 2) + 1], B0 = cb[k0 >> 2], B1 = cb[(k0 >> 2) + 1];
+    const float4 A0 = ca[k0 >> 2], A1 = ca[(k0 >> 2) + 1];
     const float av[8] = {A0.x, A0.y, A0.z, A0.w, A1.x, A1.y, A1.z, A1.w};
-    const float bv[8] = {B0.x, B0.y, B0.z, B0.w, B1.x, B1.y, B1.z, B1.w};
     float v[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       v[i] = SCALED ? p * sc : p;
-      const float pn = fmaf(av[i] * x, p, -bv[i] * pp);
+      const float pn = fmaf(av[i] * x, p, -pp);
       pp = p;
       p = pn;
     }
@@ -241,7 +245,7 @@ __device__ __forceinline__ void produce1_run(float x, float p, float sc, int E, 
 template <int R, bool TF32>
 __device__ __forceinline__ void produce_rows(const float (&x)[R], int nmax, int kp, const bool (&valid)[R],
                                              unsigned char* a_base, int blk, int lo_off, bool split, int row,
-                                             const float4* ca, const float4* cb, const float4* cab) {
+                                             const float4* ca, const float4* cab) {
   const float xcut = sqrtf(2.0f * nmax + 1.0f) + 10.0f;
   bool zero[R], fast = true;
 #pragma unroll
@@ -259,8 +263,8 @@ __device__ __forceinline__ void produce_rows(const float (&x)[R], int nmax, int 
     if (fast) produce2_run<false, TF32>(X, P, Sc, E[0], E[1], kp, a_base, blk, lo_off, split, row, cab);
     else produce2_run<true, TF32>(X, P, Sc, E[0], E[1], kp, a_base, blk, lo_off, split, row, cab);
   } else {
-    if (fast) produce1_run<false, TF32>(x[0], p[0], sc[0], E[0], kp, a_base, lo_off, split, row, ca, cb);
-    else produce1_run<true, TF32>(x[0], p[0], sc[0], E[0], kp, a_base, lo_off, split, row, ca, cb);
+    if (fast) produce1_run<false, TF32>(x[0], p[0], sc[0], E[0], kp, a_base, lo_off, split, row, ca);
+    else produce1_run<true, TF32>(x[0], p[0], sc[0], E[0], kp, a_base, lo_off, split, row, ca);
   }
 }
 
@@ -310,20 +314,19 @@ __device__ __forceinline__ void produce_rows_lut(const float (&x)[R], int nmax, 
 // Epilogue dot product of one accumulator chunk (16 columns: 2 n2, 2 n2 + 1 = Re, Im for 8 n2) with
 // phi_n2(y), advancing the y recurrence.  SCALED: values carry 2^E as in the producers.
 template <bool SCALED>
-__device__ __forceinline__ void epi_chunk(const uint32_t* t, const float4* ca, const float4* cb, int n0, float y,
+__device__ __forceinline__ void epi_chunk(const uint32_t* t, const float4* ca, int n0, float y,
                                           float& q, float& q_prev, float& xr, float& xi, int& E, float& scale) {
 #pragma unroll
   for (int g4 = 0; g4 < 2; ++g4) {
-    const float4 A = ca[(n0 >> 2) + g4], B = cb[(n0 >> 2) + g4];
+    const float4 A = ca[(n0 >> 2) + g4];
     const float av[4] = {A.x, A.y, A.z, A.w};
-    const float bv[4] = {B.x, B.y, B.z, B.w};
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int i = 4 * g4 + u;
       const float ph = SCALED ? q * scale : q;
       xr = fmaf(__uint_as_float(t[2 * i]), ph, xr);
       xi = fmaf(__uint_as_float(t[2 * i + 1]), ph, xi);
-      const float qn = fmaf(av[u] * y, q, -bv[u] * q_prev);
+      const float qn = fmaf(av[u] * y, q, -q_prev);
       q_prev = q;
       q = qn;
     }
@@ -345,7 +348,7 @@ __device__ __forceinline__ void epi_chunk2(const uint32_t* t0, const uint32_t* t
     xr[1] = fmaf(__uint_as_float(t1[2 * i]), w.y, xr[1]);
     xi[1] = fmaf(__uint_as_float(t1[2 * i + 1]), w.y, xi[1]);
     const float4 c = cab[n0 + i];
-    const float2 Qn = __ffma2_rn(__fmul2_rn(make_float2(c.x, c.y), Y), Q, __fmul2_rn(make_float2(c.z, c.w), Qp));
+    const float2 Qn = __ffma2_rn(__fmul2_rn(make_float2(c.x, c.y), Y), Q, make_float2(-Qp.x, -Qp.y));
     Qp = Q;
     Q = Qn;
   }
@@ -507,15 +510,13 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
     fence_mbar_init();
   }
   if (threadIdx.x <= kNmaxLimit) {
-    // the normalised recurrence's constants sqrt(2 / (n + 1)) and sqrt(n / (n + 1)), correctly rounded in
-    // FP64 and then to FP32 (the device's FP64 division and square root round to nearest), formed here in
-    // every CTA so that no upload has to be ordered with the launches of other streams
-    const double np1 = (double)(threadIdx.x + 1);
-    const float ha = (float)sqrt(2.0 / np1), hb = (float)sqrt((double)threadIdx.x / np1);
+    // the rescaled recurrence's constants e_n (uploaded synchronously at context creation, so every launch
+    // on any stream reads them complete): singly for the one-row path, as {e, e} pairs for the f32x2 path
+    const float e = c_k2e[threadIdx.x];
     float* cf = reinterpret_cast<float*>(smem + lay.coef);
-    cf[threadIdx.x] = ha;
-    cf[kNmaxLimit + 1 + threadIdx.x] = hb;
-    reinterpret_cast<float4*>(cf + 2 * (kNmaxLimit + 1))[threadIdx.x] = make_float4(ha, ha, -hb, -hb);
+    cf[threadIdx.x] = e;
+    cf[kNmaxLimit + 1 + threadIdx.x] = 0.f;
+    reinterpret_cast<float4*>(cf + 2 * (kNmaxLimit + 1))[threadIdx.x] = make_float4(e, e, 0.f, 0.f);
   }
 #pragma unroll
   for (int q = 0; q < K2_MAXS; ++q)
@@ -531,8 +532,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
   tc_fence_after();
   const uint32_t tmem = __shfl_sync(0xffffffffu, *tslot, 0);
   const float4* ca = reinterpret_cast<const float4*>(smem + lay.coef);
-  const float4* cb = ca + (kNmaxLimit + 1) / 4;
-  const float4* cab = cb + (kNmaxLimit + 1) / 4;  // {a_n, a_n, -b_n, -b_n}
+  const float4* cab = ca + 2 * ((kNmaxLimit + 1) / 4);  // {e_n, e_n, 0, 0}
   // Tiles of this CTA: i = 0, 1, 2, ... -> tile blockIdx.x + i * gridDim.x, on parity i % ng.  A parity's
   // items are its tiles' (tile, shapelet) pairs in order: item jj is shapelet jj % S of its tile jj / S.
   const int n_it = a.n_tiles > (int)blockIdx.x ? (a.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
@@ -670,7 +670,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
       if (jj + 1 < len) load_x(nc, nq, xs, nu);
       if (jj > 0 && !k2_wait(&mdone[sp], (jj - 1) & 1, a.err)) break;  // MMA(jj-1) has read A
       if (LUT) produce_rows_lut<R>(x, nmax, kp, v0, a_base, blk, lo_off, a.passes > 1, m, a.lut);
-      else produce_rows<R, TF32>(x, nmax, kp, v0, a_base, blk, lo_off, a.passes > 1, m, ca, cb, cab);
+      else produce_rows<R, TF32>(x, nmax, kp, v0, a_base, blk, lo_off, a.passes > 1, m, ca, cab);
       fence_async_smem();
       mbar_arrive(&afull[sp]);
       // the previous item's output, while the MMA of this one runs
@@ -776,13 +776,13 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
 #pragma unroll 1
         for (int c = 0; c < nch; c += 2) {
           if (c + 1 < nch) tmem_issue16x(trow + (uint32_t)((c + 1) << 4), tb1);
-          if (yfast) epi_chunk<false>(tb0, ca, cb, c << 3, y[0], qv[0], q_prev[0], xr[0], xi[0], E[0], scale[0]);
-          else epi_chunk<true>(tb0, ca, cb, c << 3, y[0], qv[0], q_prev[0], xr[0], xi[0], E[0], scale[0]);
+          if (yfast) epi_chunk<false>(tb0, ca, c << 3, y[0], qv[0], q_prev[0], xr[0], xi[0], E[0], scale[0]);
+          else epi_chunk<true>(tb0, ca, c << 3, y[0], qv[0], q_prev[0], xr[0], xi[0], E[0], scale[0]);
           tmem_wait16(tb1);
           if (c + 1 < nch) {
             if (c + 2 < nch) tmem_issue16x(trow + (uint32_t)((c + 2) << 4), tb0);
-            if (yfast) epi_chunk<false>(tb1, ca, cb, (c + 1) << 3, y[0], qv[0], q_prev[0], xr[0], xi[0], E[0], scale[0]);
-            else epi_chunk<true>(tb1, ca, cb, (c + 1) << 3, y[0], qv[0], q_prev[0], xr[0], xi[0], E[0], scale[0]);
+            if (yfast) epi_chunk<false>(tb1, ca, (c + 1) << 3, y[0], qv[0], q_prev[0], xr[0], xi[0], E[0], scale[0]);
+            else epi_chunk<true>(tb1, ca, (c + 1) << 3, y[0], qv[0], q_prev[0], xr[0], xi[0], E[0], scale[0]);
             tmem_wait16(tb0);
           }
         }
@@ -882,15 +882,15 @@ static cudaError_t k2_dispatch(const K2Args& a, int R, int form, int grid, int s
   return k2_launch_t<1, 0>(a, grid, smem, st);
 }
 
-// The basis table of the lookup-table mode: phi_0..phi_127 in FP64 by the normalised recurrence at every
-// sample, stored in FP32.  Built once per context.
+// The basis table of the lookup-table mode: g_n = k_n phi_n, n = 0..127 (herm_k), with phi_n in FP64 by
+// the normalised recurrence at every sample, stored in FP32.  Built once per context.
 __global__ void k2_lut_build(float* lut) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= K2_LUT_N) return;
   const double x = -(double)K2_LUT_X + (double)i / K2_LUT_D;
   double p_prev = 0.0, p = exp(-0.5 * x * x);
   for (int n = 0; n < K2_LUT_W; ++n) {
-    lut[(size_t)i * K2_LUT_W + n] = (float)p;
+    lut[(size_t)i * K2_LUT_W + n] = (float)(p * herm_k(n));
     const double pn = sqrt(2.0 / (n + 1)) * x * p - sqrt((double)n / (n + 1)) * p_prev;
     p_prev = p;
     p = pn;
@@ -1113,6 +1113,19 @@ int launch_shapelet_prep(wn_ctx* ctx, const ObsDev& o, const Model* M, int q, fl
   k2_rowinfo<<<(o.n_rows + 255) / 256, 256, 0, st>>>(o.uvw, o.n_rows, M->sh + q, std::sin(o.dec0), std::cos(o.dec0), rowinfo);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(WN_ECUDA, std::string("shapelet prep: ") + cudaGetErrorString(e));
+  return WN_OK;
+}
+}  // namespace wn
+
+namespace wn {
+// The constants e_n = sqrt(2/(n+1)) k_(n+1)/k_n of the shapelet kernel's rescaled Hermite recurrence,
+// formed in FP64 on the host and uploaded synchronously at context creation (wn_create, the context's
+// device current), so that every later launch on any stream reads them complete.
+int k2_constants_setup() {
+  float e[kNmaxLimit + 1];
+  for (int n = 0; n <= kNmaxLimit; ++n) e[n] = (float)(std::sqrt(2.0 / (n + 1)) * herm_k(n + 1) / herm_k(n));
+  const cudaError_t err = cudaMemcpyToSymbol(c_k2e, e, sizeof(e));
+  if (err != cudaSuccess) return set_error(WN_ECUDA, std::string("shapelet constants: ") + cudaGetErrorString(err));
   return WN_OK;
 }
 }  // namespace wn

@@ -8,6 +8,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <cmath>
 #include <map>
 #include <string>
 #include <vector>
@@ -40,6 +41,22 @@ constexpr double kGaussE = 3.5597074346203355;   // pi^2 / (4 ln 2)
 constexpr double kShapeK = 2.6682231827177734;   // pi / sqrt(2 ln 2)
 constexpr double kLog2e = 1.4426950408889634;
 constexpr int kNmaxLimit = 127;
+
+// Scale k_n of the rescaled Hermite functions g_n = k_n phi_n that the shapelet contraction runs on:
+// k_0 = k_1 = 1, k_(n+1) = k_(n-1) sqrt((n+1)/n).  The normalised recurrence
+// phi_(n+1) = sqrt(2/(n+1)) x phi_n - sqrt(n/(n+1)) phi_(n-1) then reads g_(n+1) = e_n x g_n - g_(n-1)
+// with e_n = sqrt(2/(n+1)) k_(n+1)/k_n: two operations per order instead of three.  The coefficient
+// operand carries 1/(k_n1 k_n2), so that sum g C' g = sum phi C phi.  FP64, each step correctly rounded
+// (the same value on the host and the device); k_n stays within [1, 4] for n <= 128.
+__host__ __device__ inline double herm_k(int n) {
+  double km = 1.0, k = 1.0;  // k_(m-1), k_m
+  for (int m = 1; m < n; ++m) {
+    const double kn = km * sqrt((double)(m + 1) / (double)m);
+    km = k;
+    k = kn;
+  }
+  return k;
+}
 
 // Packed point / Gaussian component (64 bytes).  Points first, then Gaussians.
 struct __align__(16) PGRec {
@@ -411,6 +428,7 @@ int launch_shapelets_static(wn_ctx* ctx, const ObsDev& o, const Model* M, float2
 size_t static_scratch_entries();
 int static_scratch_setup(wn_ctx* ctx);
 int grad_constants_setup(wn_ctx* ctx);
+int k2_constants_setup();
 int launch_coeff_mma(wn_ctx* ctx, const ObsDev& o, const Model* M, int q, const PeelArgs& pa, const float2* resid,
                      const float4* rowinfo, const float4* chaninfo, float2* rowg_ws, double* part_c, int* grid_out,
                      cudaStream_t st);

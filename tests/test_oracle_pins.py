@@ -432,11 +432,7 @@ def test_tf32_split_operand_pair():
     hi, lo = oracle.pack_coeff_tf32x3(ne, n1, n2, c, kp, npd)
     assert np.array_equal(hi, oracle.pack_coeff_tf32(ne, n1, n2, c, kp, npd))
     assert np.all(hi & np.uint32(0x1FFF) == 0) and np.all(lo & np.uint32(0x1FFF) == 0)
-    re, im = oracle.parity_split(ne, n1, n2, c)
-    dense = np.zeros((npd, kp))
-    for b in range(ne + 1):
-        dense[2 * b, :ne + 1], dense[2 * b + 1, :ne + 1] = re[:, b], im[:, b]
-    f = dense.astype(np.float32).astype(np.float64)
+    f = oracle.operand_dense(ne, n1, n2, c, kp, npd).astype(np.float32).astype(np.float64)
     both = hi.view(np.float32).astype(np.float64) + lo.view(np.float32).astype(np.float64)
     assert np.all(np.abs(both - f) <= 2.0 ** -21 * np.abs(f))
     only_hi = np.abs(hi.view(np.float32).astype(np.float64) - f)
@@ -453,3 +449,40 @@ def test_shapelet_frame_derivative_matches_finite_differences():
         dm = (oracle.shapelet_frame(l, m + h, dec0) - oracle.shapelet_frame(l, m - h, dec0)) / (2 * h)
         assert np.max(np.abs(fl - dl)) <= 1e-8, (l, m, dec0, np.max(np.abs(fl - dl)))
         assert np.max(np.abs(fm - dm)) <= 1e-8, (l, m, dec0, np.max(np.abs(fm - dm)))
+
+
+def test_rescaled_hermite_functions_and_operand():
+    """The operand's scaling, pinned to what it must preserve.  (1) The rescaled functions g_n = k_n phi_n
+    (oracle.herm_k) satisfy the two-operation recurrence g_(n+1) = e_n x g_n - g_(n-1) with
+    e_n = sqrt(2/(n+1)) k_(n+1)/k_n, for n up to 127, against the oracle's plain basis; k_n stays within
+    [1, 4].  (2) The contraction of the scaled operand with g(x) and g(y) equals the direct double sum
+    of C (-i)^(n1+n2) phi_n1(x) phi_n2(y) (eq:shape-env)."""
+    nmax = 127
+    k = np.array([oracle.herm_k(n) for n in range(nmax + 2)])
+    assert k[0] == 1.0 and k[1] == 1.0 and 1.0 <= k.min() and k.max() <= 4.0
+    # k_(n+1) k_n ... the closed forms: k_2m = 2^m m! / sqrt((2m)!), k_(2m+1) = sqrt((2m+1)!) / (2^m m!)
+    from math import factorial, sqrt
+    for n in (2, 3, 10, 11, 40, 41):
+        m = n // 2
+        want = (2 ** m * factorial(m) / sqrt(factorial(2 * m)) if n % 2 == 0
+                else sqrt(factorial(2 * m + 1)) / (2 ** m * factorial(m)))
+        assert abs(k[n] - want) <= 1e-13 * want
+    for x in (-7.3, -0.4, 0.0, 1.1, 5.0, 11.9):
+        phi = oracle.hermite(nmax + 1, x)
+        g = k * phi
+        for n in range(1, nmax + 1):
+            e = sqrt(2.0 / (n + 1)) * k[n + 1] / k[n]
+            assert abs(g[n + 1] - (e * x * g[n] - g[n - 1])) <= 1e-11 * max(1.0, np.abs(g).max())
+    sky = synth.make_sky(23, 0, 0, 1, shape_nmax=20)
+    n1, n2, c = sky.s_n1, sky.s_n2, sky.s_coeff
+    ne = int((n1 + n2).max())
+    kp, npd = (ne + 1 + 15) // 16 * 16, (2 * (ne + 1) + 15) // 16 * 16
+    D = oracle.operand_dense(ne, n1, n2, c, kp, npd)
+    for x, y in ((0.3, -1.2), (2.5, 0.7), (-4.0, 3.3)):
+        gx = k[:kp] * oracle.hermite(kp - 1, x)[:kp]
+        gy = k[:ne + 1] * oracle.hermite(ne, y)[:ne + 1]
+        T = D @ gx                                   # [n_pad]: Re, Im rows of each n2
+        got = np.sum(T[0:2 * (ne + 1):2] * gy) + 1j * np.sum(T[1:2 * (ne + 1):2] * gy)
+        px, py = oracle.hermite(ne, x), oracle.hermite(ne, y)
+        want = sum(v * (-1j) ** (a + b) * px[a] * py[b] for a, b, v in zip(n1, n2, c))
+        assert abs(got - want) <= 1e-12 * max(1.0, abs(want))
