@@ -80,6 +80,9 @@ __global__ void k_pack_shape(wn_sky s, const int* b_off, const int* k_pad, const
 // to bop32 in the same layout with 8x4 core matrices of 4-byte elements, element (n, k) at
 // ((k/4) * (n_pad/8) + n/8) * 32 + (n%8) * 4 + k%4: hi = RN_tf32(float(C')) at the shapelet's b_off, then
 // lo = RN_tf32(float(C') - hi) (the difference is exact in FP32) k_pad * n_pad elements further.
+// k_n (herm_k) for n = 0..kNmaxLimit, formed on the host in FP64 and uploaded at context creation.
+__constant__ double c_herm_k[kNmaxLimit + 1];
+
 __global__ void k_pack_coeff(int nnz_total, const int* n1, const int* n2, const double* c, const int* s_off,
                              const int* s_nmax, int n_shape, const int* b_off, const int* k_pad, const int* n_pad,
                              __nv_bfloat16* bop, float* bop32, unsigned* err) {
@@ -93,7 +96,7 @@ __global__ void k_pack_coeff(int nnz_total, const int* n1, const int* n2, const 
     return;
   }
   int kk = (a + b) & 3;
-  const float v = (float)(c[t] / (herm_k(a) * herm_k(b)));
+  const float v = (float)(c[t] / (c_herm_k[a] * c_herm_k[b]));
   float re = kk == 0 ? v : (kk == 2 ? -v : 0.0f);
   float im = kk == 1 ? -v : (kk == 3 ? v : 0.0f);
   int np = n_pad[q], kp = k_pad[q];
@@ -121,6 +124,14 @@ __global__ void k_pack_coeff(int nnz_total, const int* n1, const int* n2, const 
 static int cuda_check(cudaError_t e, const char* what) {
   if (e == cudaSuccess) return WN_OK;
   return set_error(WN_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// The scales k_n of the packer, uploaded synchronously at context creation (wn_create, the context's
+// device current), so that every later upload, on any stream, reads them complete.
+int pack_constants_setup() {
+  double k[kNmaxLimit + 1];
+  for (int n = 0; n <= kNmaxLimit; ++n) k[n] = herm_k(n);
+  return cuda_check(cudaMemcpyToSymbol(c_herm_k, k, sizeof(k)), "packer constants");
 }
 
 // Pack a new model: its records, shapelet headers and dense coefficient operands.  M->dmeta (device) and

@@ -200,6 +200,7 @@ int wn_create(wn_ctx** out, int device) {
   int r = static_scratch_setup(c);  // device address of wn_predict_static's array, this device current
   if (r == WN_OK) r = grad_constants_setup(c);  // the shapelet adjoint's constants
   if (r == WN_OK) r = k2_constants_setup();      // the shapelet contraction's recurrence constants
+  if (r == WN_OK) r = pack_constants_setup();    // the coefficient packer's scales
   if (r != WN_OK) {
     cudaFree(c->k1_part);
     cudaFree(c->d_err);

@@ -429,6 +429,7 @@ size_t static_scratch_entries();
 int static_scratch_setup(wn_ctx* ctx);
 int grad_constants_setup(wn_ctx* ctx);
 int k2_constants_setup();
+int pack_constants_setup();
 int launch_coeff_mma(wn_ctx* ctx, const ObsDev& o, const Model* M, int q, const PeelArgs& pa, const float2* resid,
                      const float4* rowinfo, const float4* chaninfo, float2* rowg_ws, double* part_c, int* grid_out,
                      cudaStream_t st);
