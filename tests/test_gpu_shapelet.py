@@ -56,6 +56,20 @@ def test_single_shapelet_orders(wn, ctx, nmax):
     assert e_norm(got, ref) <= 2e-4, e_norm(got, ref)
 
 
+@pytest.mark.parametrize("nmax", [20, 80])
+def test_wide_shapelet_on_long_baselines_every_recurrence_regime(wn, ctx, nmax):
+    """A wide shapelet (beta 20-25 arcmin) on baselines up to 5 km: |x| and |y| run from 0 past 12.5, where
+    the rescaled recurrence starts on values scaled by powers of two because phi_0 underflows FP32, and
+    past the cut beyond which every basis function is below 1e-20 and the row is zero.  Every
+    visibility against the oracle."""
+    obs = synth.make_obs(90 + nmax, 24, 2, synth.uniform_channels(160e6, 1.5e6, 40), layout="mwa",
+                         max_baseline=5000.0, dec0=-30 * synth.DEG)
+    sky = shapelet_sky(91 + nmax, [nmax], beta=(20 * synth.ARCMIN, 25 * synth.ARCMIN), lm=[(0.005, 0.01)])
+    ref = oracle_rows(obs, sky, np.arange(obs.n_rows))
+    got = predict(wn, ctx, obs, sky)
+    assert e_norm(got, ref) <= 2e-4, e_norm(got, ref)
+
+
 @pytest.mark.parametrize("seed,nmaxs,keep", [(5, (10,), None), (6, (80,), 1500), (7, (33, 3), 200), (8, (127,), None)])
 def test_packed_operand_bit_exact_with_the_oracle_packer(wn, ctx, seed, nmaxs, keep):
     """The coefficient operand the device packs on upload equals the oracle's restatement of it
