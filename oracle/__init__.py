@@ -7,10 +7,10 @@ TEST INFRASTRUCTURE ONLY: imported by tests/, by ``__graft_entry__.smoke()`` and
 The arithmetic lives in ``wn_oracle.c`` (plain C, FP64, loops in the paper's order); this module
 builds it with gcc, loads it with ctypes and marshals numpy arrays.  The calibration loop is numpy
 (design matrix written out, numpy's solve for the normal equations).  The truncation rule of
-Sec. 6.2 is plain Python over weights from a Gauss-Legendre quadrature of the Hermite functions.  It also holds the oracle's own
-packers (triangular coefficient index, parity split of the (-i)^(n1+n2) phase, bf16 hi/lo split, tf32
-rounding),
-written from the same definitions the CUDA packer follows, so the two can be compared bit for bit.
+Sec. 6.2 is plain Python over weights from a Gauss-Legendre quadrature of the Hermite functions.  It
+also holds the oracle's own packers (triangular coefficient index, parity split of the (-i)^(n1+n2)
+phase, the Hermite scales k_n the operand is divided by, bf16 hi/lo split, tf32 rounding), written from
+the same definitions the CUDA packer follows, so the two can be compared bit for bit.
 
 Parity pins (tests/test_oracle_pins.py) tie every function here to closed forms, library
 routines, brute-force DFTs or finite differences; none is left unpinned.
