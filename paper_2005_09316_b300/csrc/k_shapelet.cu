@@ -4,9 +4,10 @@
 //   xi = sum_{n1+n2<=nmax} C[n1,n2] (-i)^(n1+n2) phi_n1(x) phi_n2(y),
 //   x = beta1 K (sin pa u' + cos pa v') nu/c,  y = beta2 K (cos pa u' - sin pa v') nu/c   (eq:scale-shape-x/y)
 // with (u', v') re-phased to the shapelet centre and phi_n the peak-normalised Hermite functions.
-// Writing A[vis, n1] = phi_n1(x) and splitting C (-i)^(n1+n2) into real and imaginary parts gives a
-// dense contraction T = A [C_re | C_im] (M = visibilities, K = n1, N = 2 (nmax+1)) followed by a
-// per-row dot product xi = sum_n2 T[., n2] phi_n2(y).  Each shapelet's contribution is
+// With the rescaled functions g_n = k_n phi_n (herm_k), writing A[vis, n1] = g_n1(x) and splitting
+// C (-i)^(n1+n2) / (k_n1 k_n2) into real and imaginary parts gives a dense contraction
+// T = A [C_re | C_im] (M = visibilities, K = n1, N = 2 (nmax+1)) followed by a per-row dot product
+// xi = sum_n2 T[., n2] g_n2(y).  Each shapelet's contribution is
 // S(nu) xi exp(-2 pi i tau nu/c); a launch sums those of up to K2_MAXS shapelets per visibility and
 // writes the output once: stored, added, or subtracted as G times the sum for the peel (Sec. 5.1).
 //
@@ -14,8 +15,9 @@
 // unit of work is an item, one (tile, shapelet) pair; the items of a tile follow each other on the same
 // parity, and the output of a tile is written after its last item.
 //  * producer warpgroups P0, P1 (warps 0-3, 4-7) take the items of the even / odd tiles: thread i
-//    computes phi_n(x) of rows i, i + 128, ... (R of them, their recurrences run as one f32x2
-//    recurrence when R = 2) by the normalised Hermite recurrence (FP32, rescaled to stay in range) and
+//    computes g_n(x) of rows i, i + 128, ... (R of them, their recurrences run as one f32x2
+//    recurrence when R = 2) by the two-operation recurrence (FP32, scaled by powers of two to stay in
+//    range) and
 //    writes them as bf16 hi/lo into that parity's A buffer (one 128-row block per r) in the canonical
 //    K-major shared-memory layout (8x8 core matrices, no swizzle);
 //  * warp 16 allocates TMEM, loads the packed coefficient operands of all the launch's shapelets with
@@ -23,7 +25,7 @@
 //    products hi*hi + hi*lo + lo*hi in the split mode; one M = 128 block per r) into the parity's TMEM
 //    accumulators and commits to an mbarrier, alternating the parities item by item;
 //  * epilogue warpgroups E0, E1 (warps 8-11, 12-15) read their accumulator rows from TMEM (warp w
-//    reaches lanes 32 (w % 4) ..), stream phi_n(y) against them, release TMEM and hand the dot products
+//    reaches lanes 32 (w % 4) ..), stream g_n(y) against them, release TMEM and hand the dot products
 //    to the producers through shared memory;
 //  * the producers, while the next item's MMA runs, weight the dot products by the shapelet's spectrum
 //    and phasor, sum them over the tile's items and write the tile's output after its last item.
@@ -50,9 +52,10 @@ constexpr int K2_MMA_WARP = 8 * K2_GROUPS;
 constexpr int K2_MAXS = 8;                       // shapelets summed in one launch
 
 // The normalised Hermite recurrence phi_{n+1} = a_n x phi_n - b_n phi_{n-1}, a_n = sqrt(2/(n+1)),
-// b_n = sqrt(n/(n+1)).
+// b_n = sqrt(n/(n+1)), becomes g_{n+1} = e_n x g_n - g_{n-1} for g_n = k_n phi_n (herm_k), with
+// e_n = a_n k_{n+1}/k_n (c_k2e).
 
-// Lookup-table form of the basis (the 1-D tables of Sec. 3.2): phi_0..phi_127 at x_i = -K2_LUT_X + i / K2_LUT_D,
+// Lookup-table form of the basis (the 1-D tables of Sec. 3.2): g_0..g_127 at x_i = -K2_LUT_X + i / K2_LUT_D,
 // row i of 128 floats, interpolated linearly.  |x| beyond sqrt(2 * 127 + 1) + 10 < K2_LUT_X is zero.
 constexpr float K2_LUT_X = 26.0f;
 constexpr int K2_LUT_D = 256;                                   // samples per unit of x
@@ -312,7 +315,7 @@ __device__ __forceinline__ void produce_rows_lut(const float (&x)[R], int nmax, 
 }
 
 // Epilogue dot product of one accumulator chunk (16 columns: 2 n2, 2 n2 + 1 = Re, Im for 8 n2) with
-// phi_n2(y), advancing the y recurrence.  SCALED: values carry 2^E as in the producers.
+// g_n2(y), advancing the y recurrence.  SCALED: values carry 2^E as in the producers.
 template <bool SCALED>
 __device__ __forceinline__ void epi_chunk(const uint32_t* t, const float4* ca, int n0, float y,
                                           float& q, float& q_prev, float& xr, float& xi, int& E, float& scale) {
@@ -358,7 +361,7 @@ __device__ __forceinline__ void epi_chunk2(const uint32_t* t0, const uint32_t* t
   }
 }
 
-// Epilogue dot product of one 16-column chunk with table-interpolated phi_n2(y), n2 = n0 .. n0 + 7.
+// Epilogue dot product of one 16-column chunk with table-interpolated g_n2(y), n2 = n0 .. n0 + 7.
 __device__ __forceinline__ void epi_chunk_lut(const uint32_t* t, const float* lut, int iy, float ty, int n0, float& xr,
                                               float& xi) {
   if (iy < 0) return;
@@ -595,7 +598,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
     if (done1 > 0) k2_wait(&mdone[1], (done1 - 1) & 1, a.err);
     __syncwarp();
   } else if (warp < 4 * K2_GROUPS) {
-    // ---------------- producers: phi_n(x) into the parity's A buffer ----------------
+    // ---------------- producers: g_n(x) into the parity's A buffer ----------------
     const int sp = warp >> 2;
     if (sp >= ng) goto done;
     const int m = threadIdx.x & 127;
@@ -688,7 +691,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
     }
     if (pq >= 0 && len > 0) out_item(pc, pq, len - 1);
   } else {
-    // ---------------- epilogues: xi = sum_n2 T[., n2] phi_n2(y), handed to the producers ----------------
+    // ---------------- epilogues: xi = sum_n2 T[., n2] g_n2(y), handed to the producers ----------------
     const int sp = (warp - 4 * K2_GROUPS) >> 2;
     if (sp >= ng) goto done;
     const int m = threadIdx.x & 127;
@@ -753,7 +756,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_shapelet(const K2Args a) {
         mbar_arrive(&tfree[sp]);
         released = true;
       };
-      if (LUT) {  // table-interpolated phi_n2(y): one chunk of every row at a time
+      if (LUT) {  // table-interpolated g_n2(y): one chunk of every row at a time
         int iy[R];
         float ty[R];
 #pragma unroll
